@@ -1,0 +1,179 @@
+"""Seeded synthetic graph generators (input data only).
+
+The paper evaluates on twelve real social and web graphs (Table 1), which are
+not available here.  These generators produce seeded stand-ins of the same
+shape: Erdos-Renyi G(n, m), Chung-Lu power-law graphs and R-MAT graphs (in C,
+``gen.c``), plus small closed-form graphs whose triangle counts are known
+(complete graphs, wheels, stars, trees, cycles, complete bipartite graphs).
+
+Every function returns a canonical edge list: a ``(m, 2)`` uint32 numpy array
+of pairs ``(u, v)`` with ``u < v``, sorted, without duplicates or self-loops.
+Nothing here counts triangles or samples edges for the method; the outputs
+are inputs to both the CPU oracle and the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen.c")
+_LIB = os.path.join(_HERE, "libgen.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gen.c into libgen.so next to it (plain C, no GPU)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        lib.gen_er.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, u32p]
+        lib.gen_er.restype = ctypes.c_int64
+        lib.gen_chung_lu.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_uint64, u32p]
+        lib.gen_chung_lu.restype = ctypes.c_int64
+        lib.gen_rmat.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_uint64, u32p]
+        lib.gen_rmat.restype = ctypes.c_int64
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+def er(n: int, m: int, seed: int) -> np.ndarray:
+    """Erdos-Renyi G(n, m): m distinct uniform edges among n vertices."""
+    out = np.empty((max(m, 1), 2), dtype=np.uint32)
+    r = _load().gen_er(n, m, seed, _ptr(out))
+    if r < 0:
+        raise ValueError("gen_er failed (%d) for n=%d m=%d" % (r, n, m))
+    return out[:r]
+
+
+def chung_lu(n: int, m: int, gamma: float, wmax: float, seed: int) -> np.ndarray:
+    """Chung-Lu power-law graph with exactly m distinct edges, degree exponent
+    gamma and maximum expected degree wmax, vertex ids seeded-permuted."""
+    out = np.empty((max(m, 1), 2), dtype=np.uint32)
+    r = _load().gen_chung_lu(n, m, gamma, wmax, seed, _ptr(out))
+    if r < 0:
+        raise ValueError("gen_chung_lu failed (%d)" % r)
+    return out[:r]
+
+
+def rmat(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+         seed: int = 1) -> np.ndarray:
+    """R-MAT graph on 2**scale vertices from edge_factor * 2**scale draws,
+    symmetrised and deduplicated (the returned m is smaller than the draws)."""
+    draws = edge_factor << scale
+    out = np.empty((max(draws, 1), 2), dtype=np.uint32)
+    r = _load().gen_rmat(scale, edge_factor, a, b, c, seed, _ptr(out))
+    if r < 0:
+        raise ValueError("gen_rmat failed (%d)" % r)
+    return np.ascontiguousarray(out[:r])
+
+
+# ---------------------------------------------------------------- closed forms
+
+def canonical(pairs) -> np.ndarray:
+    """Canonical form of an arbitrary pair list: (min, max), no self-loops,
+    sorted, unique.  Input-side helper for the closed-form builders."""
+    a = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    a = a[a[:, 0] != a[:, 1]]
+    a = np.stack([a.min(axis=1), a.max(axis=1)], axis=1)
+    if len(a) == 0:
+        return np.zeros((0, 2), dtype=np.uint32)
+    a = np.unique(a, axis=0)
+    return a.astype(np.uint32)
+
+
+def complete(k: int, offset: int = 0) -> np.ndarray:
+    """K_k on vertices offset..offset+k-1 (C(k, 3) triangles)."""
+    return canonical([(offset + i, offset + j) for i in range(k) for j in range(i + 1, k)])
+
+
+def wheel(k: int) -> np.ndarray:
+    """Wheel W_k: hub 0 joined to a k-cycle 1..k (k triangles for k >= 4)."""
+    rim = [(1 + i, 1 + (i + 1) % k) for i in range(k)]
+    return canonical([(0, 1 + i) for i in range(k)] + rim)
+
+
+def star(k: int) -> np.ndarray:
+    """Star with k leaves (no triangles)."""
+    return canonical([(0, 1 + i) for i in range(k)])
+
+
+def cycle(k: int) -> np.ndarray:
+    """Cycle C_k (one triangle when k == 3, none otherwise)."""
+    return canonical([(i, (i + 1) % k) for i in range(k)])
+
+
+def random_tree(n: int, seed: int) -> np.ndarray:
+    """Random recursive tree on n vertices (no triangles)."""
+    rng = np.random.default_rng(seed)
+    return canonical([(i, int(rng.integers(0, i))) for i in range(1, n)])
+
+
+def complete_bipartite(a: int, b: int) -> np.ndarray:
+    """K_{a,b} (no triangles)."""
+    return canonical([(i, a + j) for i in range(a) for j in range(b)])
+
+
+def disjoint_union(*graphs) -> tuple[np.ndarray, int]:
+    """Disjoint union of canonical edge lists; returns (edges, n)."""
+    parts, off = [], 0
+    for g in graphs:
+        g = np.asarray(g, dtype=np.int64).reshape(-1, 2)
+        nv = int(g.max()) + 1 if len(g) else 0
+        parts.append(g + off)
+        off += nv
+    return canonical(np.concatenate(parts) if parts else np.zeros((0, 2))), off
+
+
+def num_vertices(edges: np.ndarray) -> int:
+    return int(edges.max()) + 1 if len(edges) else 0
+
+
+# ---------------------------------------------------------------- batch mix
+
+def batch_specs(count: int, seed: int = 1):
+    """Descriptions of `count` small uneven graphs: n log-uniform in
+    [100, 50000], average degree uniform in [4, 64] (below n - 1), alternating
+    Erdos-Renyi and Chung-Lu (exponent 2.3), p drawn from {0.1, 0.5, 1.0},
+    sampling seed = index + 1."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        n = int(math.floor(math.exp(rng.uniform(math.log(100), math.log(50000)))))
+        avg = min(float(rng.uniform(4, 64)), n - 1.0)
+        m = int(n * avg / 2)
+        kind = "er" if i % 2 == 0 else "chung_lu"
+        if kind == "chung_lu":
+            m = min(m, n * (n - 1) // 4)
+        p = float(rng.choice([0.1, 0.5, 1.0]))
+        specs.append({"kind": kind, "n": n, "m": m, "p": p, "seed": i + 1, "gseed": seed * 1000003 + i})
+    return specs
+
+
+def batch_graph(spec) -> np.ndarray:
+    """Edges of one graph described by batch_specs."""
+    if spec["kind"] == "er":
+        return er(spec["n"], spec["m"], spec["gseed"])
+    avg = 2.0 * spec["m"] / spec["n"]
+    wmax = max(2.0, min(spec["n"] / 4.0, 10.0 * avg))
+    return chung_lu(spec["n"], spec["m"], 2.3, wmax, spec["gseed"])
