@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     """Compile gen.c into libgen.so next to it (plain C, no GPU)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -86,6 +86,31 @@ def rmat(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: floa
     if r < 0:
         raise ValueError("gen_rmat failed (%d)" % r)
     return np.ascontiguousarray(out[:r])
+
+
+def cached(kind: str, fn, *args) -> np.ndarray:
+    """fn(*args), memoised as an .npy file under $TC_GEN_CACHE (default
+    /tmp/tc_gen_cache) keyed by the generator and its arguments."""
+    d = os.environ.get("TC_GEN_CACHE", "/tmp/tc_gen_cache")
+    import hashlib
+    with open(_SRC, "rb") as f:
+        src_hash = hashlib.sha1(f.read()).hexdigest()[:12]
+    key = "%s_%s_%s" % (kind, "_".join(repr(a) for a in args), src_hash)
+    path = os.path.join(d, "".join(c if c.isalnum() or c in "._-" else "_" for c in key) + ".npy")
+    if os.path.exists(path):
+        try:
+            return np.load(path)
+        except Exception:
+            pass
+    out = fn(*args)
+    try:
+        os.makedirs(d, exist_ok=True)
+        tmp = path + ".tmp%d.npy" % os.getpid()
+        np.save(tmp, out)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return out
 
 
 # ---------------------------------------------------------------- closed forms

@@ -39,6 +39,36 @@ static inline uint64_t g_rand(uint64_t seed, uint64_t stream, uint64_t ctr)
     return g_fmix64(s ^ (ctr * 0x9fb21c651e98df25ULL + 0x632be59bd9b4e019ULL));
 }
 
+/* ------------------------------------------------ portable log / exp / pow
+   Built from IEEE basic operations only (compiled without FMA contraction),
+   so every platform produces bit-identical graphs; libm's pow may differ in
+   the last ulp between C libraries. */
+
+/* natural log: x = f 2^e with f in [sqrt(1/2), sqrt(2)), then
+   log f = 2 atanh(s), s = (f - 1)/(f + 1), by its odd power series */
+static double g_log(double x)
+{
+    int e;
+    double f = frexp(x, &e); /* exact: f in [0.5, 1) */
+    if (f < 0.70710678118654752440) { f *= 2.0; e -= 1; }
+    const double s = (f - 1.0) / (f + 1.0), s2 = s * s;
+    double term = s, sum = 0.0;
+    for (int k = 1; k <= 41; k += 2) { sum += term / k; term *= s2; }
+    return 2.0 * sum + e * 0.69314718055994530942;
+}
+
+/* exp: y = k ln2 + r, |r| <= ln2 / 2, exp(r) by its Taylor series */
+static double g_exp(double y)
+{
+    const double k = floor(y / 0.69314718055994530942 + 0.5);
+    const double r = y - k * 0.69314718055994530942;
+    double term = 1.0, sum = 1.0;
+    for (int i = 1; i <= 24; ++i) { term = term * r / i; sum += term; }
+    return ldexp(sum, (int)k);
+}
+
+static double g_pow(double x, double y) { return g_exp(y * g_log(x)); }
+
 /* uniform in [0, 1) with 53 random bits */
 static inline double g_unit(uint64_t r) { return (double)(r >> 11) * (1.0 / 9007199254740992.0); }
 
@@ -161,6 +191,36 @@ int64_t gen_er(uint32_t n, uint64_t m, uint64_t seed, uint32_t *out_pairs)
 
 /* ------------------------------------------------------- Chung-Lu */
 
+/*
+ * Walker's alias table (Vose's construction) for weights w[0..n) summing to
+ * total: afterwards drawing i uniformly and keeping it with probability
+ * w'[i] (stored back into w) else taking alias[i] samples proportionally to
+ * w.  Deterministic: only IEEE basic operations and a fixed visiting order.
+ */
+static int g_alias_build(double *w, uint32_t *alias, uint32_t n, double total)
+{
+    uint32_t *small = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    uint32_t *large = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    if (!small || !large) { free(small); free(large); return -1; }
+    uint32_t ns = 0, nl = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        w[i] = w[i] * (double)n / total;
+        alias[i] = i;
+        if (w[i] < 1.0) small[ns++] = i; else large[nl++] = i;
+    }
+    while (ns > 0 && nl > 0) {
+        uint32_t s = small[--ns], l = large[nl - 1];
+        alias[s] = l;
+        w[l] = (w[l] + w[s]) - 1.0;
+        if (w[l] < 1.0) { --nl; small[ns++] = l; }
+    }
+    while (nl > 0) w[large[--nl]] = 1.0;
+    while (ns > 0) w[small[--ns]] = 1.0;
+    free(small);
+    free(large);
+    return 0;
+}
+
 /* seeded Fisher-Yates permutation of [0, n) */
 static void g_perm(uint32_t *perm, uint32_t n, uint64_t seed, uint64_t stream)
 {
@@ -190,27 +250,39 @@ int64_t gen_chung_lu(uint32_t n, uint64_t m, double gamma, double wmax, uint64_t
     double lo = 1e-9, hi = 1e12;
     for (int it = 0; it < 200; ++it) {
         double mid = sqrt(lo * hi);
-        double D = pow((double)n + mid, e) - pow(mid, e);
-        double f = 2.0 * (double)m * e / (pow(mid, a) * D);
+        double D = g_pow((double)n + mid, e) - g_pow(mid, e);
+        double f = 2.0 * (double)m * e / (g_pow(mid, a) * D);
         if (f > wmax) lo = mid; else hi = mid;
     }
     const double i0 = sqrt(lo * hi);
-    const double base = pow(i0, e), D = pow((double)n + i0, e) - base;
+    /* vertex i carries the weight of [i, i+1) under w: F(i+1) - F(i) with
+       F(x) = (x + i0)^e up to a constant factor */
+    double *prob = (double *)malloc((size_t)n * sizeof(double));
+    uint32_t *alias = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
     uint32_t *perm = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
     g_set set;
     uint64_t *keys = (uint64_t *)malloc((m ? m : 1) * sizeof(uint64_t));
-    if (!perm || !keys || g_set_init(&set, m)) { free(perm); free(keys); return -3; }
+    if (!prob || !alias || !perm || !keys || g_set_init(&set, m)) {
+        free(prob); free(alias); free(perm); free(keys);
+        return -3;
+    }
+    double prev = g_pow(i0, e), total = 0.0;
+    for (uint32_t i = 0; i < n; ++i) {
+        double cur = g_pow((double)i + 1.0 + i0, e);
+        prob[i] = cur - prev;
+        total += prob[i];
+        prev = cur;
+    }
+    if (g_alias_build(prob, alias, n, total)) { free(prob); free(alias); free(perm); free(keys); free(set.slot); return -3; }
     g_perm(perm, n, seed, 7);
     uint64_t got = 0;
     for (uint64_t ctr = 0; got < m; ++ctr) {
         uint32_t ends[2];
         for (int s = 0; s < 2; ++s) {
-            double u = g_unit(g_rand(seed, 2 + s, ctr));
-            double x = pow(base + u * D, 1.0 / e) - i0;
-            int64_t ix = (int64_t)x;
-            if (ix < 0) ix = 0;
-            if (ix >= (int64_t)n) ix = n - 1;
-            ends[s] = perm[ix];
+            uint64_t r = g_rand(seed, 2 + s, ctr);
+            uint32_t i = g_below((uint32_t)(r >> 32), n);
+            double u = ((double)(uint32_t)r + 0.5) * (1.0 / 4294967296.0);
+            ends[s] = perm[u < prob[i] ? i : alias[i]];
         }
         if (ends[0] == ends[1]) continue;
         uint64_t k = g_key(ends[0], ends[1]);
@@ -218,6 +290,8 @@ int64_t gen_chung_lu(uint32_t n, uint64_t m, double gamma, double wmax, uint64_t
     }
     free(set.slot);
     free(perm);
+    free(prob);
+    free(alias);
     int64_t res = g_finish(keys, got, n, out_pairs, m);
     free(keys);
     return res;

@@ -1,0 +1,181 @@
+/*
+ * tc.h -- C ABI of libtc.so, a GPU (sm_103a) implementation of the
+ * edge-sampled, degree-partitioned triangle counter of Kolountzakis, Miller,
+ * Peng and Tsourakakis, "Efficient Triangle Counting in Large Graphs via
+ * Degree-based Vertex Partitioning".
+ *
+ * Problem (Section 1 and Table of symbols): G([n], E) is a simple undirected
+ * graph with m edges and t triangles; p is the sparsification parameter.
+ * The library
+ *   1. keeps every edge independently with probability p (Section 3.1) by a
+ *      counter-based hash of the edge and the seed:
+ *        keep (u, v), u < v  <=>  (splitmix64(key ^ splitmix64(seed)) >> 11)
+ *                                  < floor(p * 2^53),   key = u << 32 | v,
+ *      so a given (graph, p, seed) always draws the same sample;
+ *   2. splits the vertices of the sampled graph (m_p edges, degrees deg_p)
+ *      into heavy (deg_p^2 > m_p) and light (Section 3.2);
+ *   3. counts exactly the sampled triangles with at least one light vertex
+ *      (t_light) and with three heavy vertices (t_heavy) (Section 3.2);
+ *   4. returns estimate = t_light / p^3 + t_heavy / p^3 in float64
+ *      (Section 3.1: a triangle survives with probability p^3).
+ * With p = 1 the estimate is the exact triangle count.
+ *
+ * Conventions
+ *   - Vertex ids are uint32 in [0, n).  Edge lists are arrays of m uint32
+ *     pairs {u0, v0, u1, v1, ...} (row-major m x 2).  Pair order, pair
+ *     orientation, repeats and self-loops are all allowed on input; the graph
+ *     keeps the canonical simple graph (pairs (min, max), no self-loops, no
+ *     repeats), as in Section 4.1.
+ *   - Sizes: n < 2^32 - 1 and at most 2^32 - 2 canonical edges.
+ *   - Every call returns a tc_status; nothing aborts, traps or prints.  A
+ *     failed call leaves its outputs unspecified and the graph usable unless
+ *     the status is TC_ECUDA (the CUDA context itself reported an error).
+ *   - All device work is stream-ordered on the graph's stream (given at
+ *     create; NULL means the legacy default stream).  Calls on one graph must
+ *     not overlap; different graphs may be used from different host threads.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TC_OK = 0,
+    TC_EINVAL = 1,   /* bad argument: NULL pointer, p outside (0, 1], endpoint >= n, size limit */
+    TC_ENOMEM = 2,   /* device or pinned host allocation failed */
+    TC_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    TC_ETIMEOUT = 4, /* a bounded device-side wait gave up (the work was abandoned) */
+    TC_EBUSY = 5     /* the object is in use by an unfinished asynchronous call */
+} tc_status;
+
+/* Opaque graph: owns the canonical edge list and all scratch on the device. */
+typedef struct tc_graph tc_graph;
+
+/* Result of one count.  ms[] holds device times of the phases in
+   milliseconds when timing is enabled (tc_graph_set_timing) and the call was
+   blocking, else zeros: [0] sample + degrees + partition, [1] orientation +
+   CSR build + source buckets, [2] sorted-list intersections, [3] heavy
+   block, [4] total.  The work counters give the exact amount of list data
+   the intersections read, for bandwidth accounting. */
+typedef struct {
+    uint64_t m;         /* canonical edges of the graph */
+    uint64_t m_sampled; /* kept edges m_p */
+    uint32_t n;         /* vertices */
+    uint32_t n_heavy;   /* vertices with deg_p^2 > m_p */
+    uint64_t t_light;   /* sampled triangles with >= 1 light vertex */
+    uint64_t t_heavy;   /* sampled triangles with 3 heavy vertices */
+    double estimate;    /* t_light / p^3 + t_heavy / p^3 */
+    uint64_t src_elems; /* sum of d+(u) over intersected sources u */
+    uint64_t nbr_elems; /* sum over those u of sum_{v in N+(u)} d+(v) */
+    float ms[8];
+} tc_result;
+
+/* Optional device allocator used for every device allocation the library
+   makes (for example a framework's caching allocator).  alloc returns NULL
+   on failure.  Pass NULLs to restore cudaMalloc/cudaFree.  Not thread-safe
+   with concurrent graph creation/destruction. */
+typedef void *(*tc_alloc_fn)(uint64_t bytes, void *stream, void *ctx);
+typedef void (*tc_free_fn)(void *ptr, void *stream, void *ctx);
+void tc_set_allocator(tc_alloc_fn alloc, tc_free_fn free_fn, void *ctx);
+
+/*
+ * Build a graph from m_in uint32 pairs (Section 4.1 canonical simple graph).
+ *   edges           m_in pairs; host memory (edges_on_device = 0, any host
+ *                   memory, pinned is fastest) or device memory of the
+ *                   current device (edges_on_device = 1).  Borrowed: the
+ *                   library copies what it needs before returning.
+ *   n               number of vertices; every endpoint must be < n.
+ *   cuda_stream     cudaStream_t for all work of this graph (NULL = default).
+ *   out             receives the graph (NULL on failure).
+ * Errors: TC_EINVAL for NULL out, NULL edges with m_in > 0, n == 0, n or m
+ * beyond the size limits, an endpoint >= n (nothing stays allocated);
+ * TC_ENOMEM; TC_ECUDA.  Blocks until the graph is ready.
+ */
+tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int edges_on_device,
+                          void *cuda_stream, tc_graph **out);
+
+/* NULL-safe.  Waits for the graph's pending work, then frees everything. */
+void tc_graph_destroy(tc_graph *g);
+
+uint64_t tc_graph_num_edges(const tc_graph *g);    /* canonical m */
+uint32_t tc_graph_num_vertices(const tc_graph *g); /* n */
+uint64_t tc_graph_device_bytes(const tc_graph *g); /* device memory held */
+
+/* Record per-phase device times (adds CUDA event records to every count).
+   Blocking counts report them in tc_result.ms; every count, blocking or
+   asynchronous, also leaves them in a ring of TC_TIMING_RING entries that
+   tc_graph_timing_drain reads. */
+#define TC_TIMING_RING 256
+tc_status tc_graph_set_timing(tc_graph *g, int on);
+
+/* After tc_graph_sync: copy the phase times (8 floats per count, layout of
+   tc_result.ms) of the counts completed since the last drain, oldest first,
+   at most max_counts of them (older ones beyond the ring are lost).  Returns
+   the number of counts written, or -1 on bad arguments / CUDA error. */
+int tc_graph_timing_drain(tc_graph *g, float *ms_out, uint32_t max_counts);
+
+/*
+ * The hot path: sample with (p, seed), partition, count both classes,
+ * rescale (Sections 3.1-3.2).  Blocking: returns when *out is filled.
+ * Errors: TC_EINVAL (NULL, p not in (0, 1] or NaN), TC_ECUDA, TC_ETIMEOUT.
+ */
+tc_status tc_count(tc_graph *g, double p, uint64_t seed, tc_result *out);
+
+/*
+ * Same computation, enqueued on the graph's stream without waiting.  The
+ * result (including the float64 estimate, computed on the device) is
+ * written to *out when the stream reaches that point; *out should be pinned
+ * host memory (cudaMallocHost) for the copy to be asynchronous.  Call
+ * tc_graph_sync before reading it.  ms[] is not filled.
+ */
+tc_status tc_count_async(tc_graph *g, double p, uint64_t seed, tc_result *out);
+
+/* Wait for all enqueued work of the graph; reports a device-side error or
+   timeout raised by that work. */
+tc_status tc_graph_sync(tc_graph *g);
+
+/*
+ * Test and inspection entry points (not on the hot path).  They run the
+ * sampling and partition of tc_count for (p, seed) and copy intermediate
+ * results to host memory:
+ *   kept_pairs_host  2 * m_sampled uint32: kept canonical edges in
+ *                    canonical (sorted) order; may be NULL.  Must hold
+ *                    2 * tc_graph_num_edges(g) uint32.
+ *   heavy_host       n bytes, 1 for heavy vertices; may be NULL.
+ *   deg_host         n uint32 sampled degrees; may be NULL.
+ *   m_sampled        receives m_p; may be NULL.
+ */
+tc_status tc_graph_export_sample(tc_graph *g, double p, uint64_t seed, uint32_t *kept_pairs_host,
+                                 uint8_t *heavy_host, uint32_t *deg_host, uint64_t *m_sampled);
+
+/*
+ * The degree-oriented CSR of the sampled graph that the counting kernels
+ * use: every kept edge once, directed from the endpoint of lower
+ * (deg_p, id) to the higher one, rows sorted by id.
+ *   rowptr_host  n + 1 uint32;  col_host  m_sampled uint32 (capacity m).
+ */
+tc_status tc_graph_export_csr(tc_graph *g, double p, uint64_t seed, uint32_t *rowptr_host,
+                              uint32_t *col_host, uint64_t *m_sampled);
+
+/* The canonical edge list held by the graph (2 * m uint32, sorted). */
+tc_status tc_graph_export_edges(tc_graph *g, uint32_t *pairs_host);
+
+/* Static description of a status code. */
+const char *tc_status_str(tc_status s);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int tc_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+   graphs, all threads); for launch accounting in benchmarks. */
+uint64_t tc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

@@ -1,0 +1,153 @@
+// Device-side helpers shared by the libtc kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tc.h"
+
+namespace tcg {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int NUM_SMS_HINT = 152;
+
+// ---------------------------------------------------------------- errors
+// Bits of DevState::err raised by kernels; the host maps them to statuses.
+enum : unsigned {
+    ERR_ENDPOINT = 1u,   // an input endpoint >= n
+    ERR_TIMEOUT = 2u,    // a bounded wait gave up
+    ERR_OVERFLOW = 4u,   // an internal capacity was exceeded
+};
+
+// Per-graph device state: counters written by the kernels of one count.
+struct DevState {
+    unsigned long long m_sampled;  // kept edges m_p
+    unsigned long long t_light;    // light-class triangles
+    unsigned long long t_heavy;    // heavy-class triangles
+    unsigned int n_heavy;          // heavy vertices
+    unsigned int err;              // ERR_* bits
+    unsigned int nlist[4];         // sizes of the source buckets
+    unsigned int cursor[4];        // dynamic work cursors (one per kernel)
+    unsigned long long src_elems;  // sum of d+(u) over intersected sources
+    unsigned long long nbr_elems;  // sum over them of sum_{v in N+(u)} d+(v)
+    unsigned long long m_canon;    // canonical edges (create only)
+    unsigned int unsorted;         // create: adjacent pairs out of order
+    unsigned int pad;
+};
+
+// ---------------------------------------------------------------- splitmix64
+// Steele, Lea and Flood's splitmix64 in the form Vigna published:
+// z = x + golden gamma, then two xor-shift-multiply rounds and a final
+// xor-shift, all modulo 2^64.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// Section 3.1 edge sparsification as a counter-based draw: the canonical
+// edge key (u << 32 | v), u < v, is kept iff its hash, reduced to 53 bits,
+// falls below floor(p * 2^53).  seed_mix = splitmix64(seed).
+__device__ __forceinline__ bool keep_edge(uint64_t key, uint64_t seed_mix, uint64_t thr)
+{
+    return (splitmix64(key ^ seed_mix) >> 11) < thr;
+}
+
+// Degree-ordered orientation: the edge goes from the endpoint with the
+// smaller (deg, id) to the larger.  For a canonical edge u < v this is u -> v
+// iff deg[u] <= deg[v].  Returns (src << 32 | dst).
+__device__ __forceinline__ uint64_t orient(uint64_t key, const uint32_t *__restrict__ deg)
+{
+    uint32_t u = (uint32_t)(key >> 32), v = (uint32_t)key;
+    uint32_t du = __ldg(deg + u), dv = __ldg(deg + v);
+    return du <= dv ? key : (((uint64_t)v << 32) | u);
+}
+
+// ---------------------------------------------------------------- warp / block
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T x)
+{
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(FULL, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+// Exclusive scan of one value per thread across the block (blockDim.x a
+// multiple of 32).  `warp_tot` is shared scratch of 33 entries.  Returns the
+// exclusive prefix; *total receives the block sum.  Contains __syncthreads.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T x, T *warp_tot, T *total)
+{
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T inc = warp_incl_scan(x);
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T t = lane < nw ? warp_tot[lane] : T(0);
+        T ti = warp_incl_scan(t);
+        if (lane < nw) warp_tot[lane] = ti - t;
+        if (lane == nw - 1) warp_tot[32] = ti;
+    }
+    __syncthreads();
+    T res = inc - x + warp_tot[warp];
+    *total = warp_tot[32];
+    __syncthreads();
+    return res;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T x, T *warp_tot)
+{
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    x = warp_sum(x);
+    if (lane == 0) warp_tot[warp] = x;
+    __syncthreads();
+    T r = T(0);
+    if (warp == 0) {
+        r = lane < nw ? warp_tot[lane] : T(0);
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;  // valid in thread 0 (and all of warp 0)
+}
+
+__device__ __forceinline__ uint64_t ld_stream_u64(const uint64_t *p)
+{
+    uint64_t r;
+    asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(r) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ ulonglong2 ld_stream_u64x2(const ulonglong2 *p)
+{
+    ulonglong2 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];"
+                 : "=l"(r.x), "=l"(r.y)
+                 : "l"(p));
+    return r;
+}
+
+}  // namespace tcg

@@ -1,0 +1,84 @@
+// Host-side launchers of the libtc device kernels (internal interface).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace tcg {
+
+// ---------------------------------------------------------------- prims.cu
+constexpr int RX_THREADS = 256;                  // 8 warps per tile
+constexpr int RX_ITEMS = 16;                     // items per thread
+constexpr int RX_TILE = RX_THREADS * RX_ITEMS;   // 4096 items per tile
+constexpr int RX_MAX_BITS = 8;                   // digit width limit
+constexpr int RX_BINS = 1 << RX_MAX_BITS;
+constexpr int SC_CHUNK = 4096;                   // scan elements per block
+
+inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// Process-wide count of kernel launches made by the library (api.cu).
+void note_launch();
+
+// Scratch (uint32 entries) needed by scan_excl_u32 for `len` elements.
+uint64_t scan_scratch_elems(uint64_t len);
+
+// In-place exclusive prefix sum of a[0, len).  If total is non-NULL the
+// sum of all elements is written there (device pointer).  scratch holds
+// scan_scratch_elems(len) uint32.
+void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s);
+
+// Source of the items of a radix pass.
+struct ItemSource {
+    enum Kind { PLAIN = 0, SAMPLE_ORIENT = 1 } kind;
+    const uint64_t *in;                 // PLAIN: items; SAMPLE_ORIENT: canonical keys
+    uint64_t n_host;                    // item count when n_dev is NULL
+    const unsigned long long *n_dev;    // device item count (e.g. m_p), or NULL
+    const uint32_t *deg;                // SAMPLE_ORIENT: sampled degrees
+    uint64_t seed_mix, thr;             // SAMPLE_ORIENT: keep test
+};
+
+// One stable LSD radix pass over 64-bit items on bits [shift, shift+width),
+// width <= 8.  Tiles of RX_TILE items; hist holds (1 << width) * ntiles
+// uint32 (digit-major), ntiles = ceil(n_max / RX_TILE).  If dplus is
+// non-NULL the count kernel also histograms (item >> 32) into it.  The
+// scatter writes the full items to out, or when out_low32 is non-NULL only
+// their low 32 bits there.
+void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
+                uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
+                cudaStream_t s);
+
+// Canonical keys from raw pairs: (min << 32 | max), self-loops become
+// ~0ull; endpoints >= n raise ERR_ENDPOINT; pairs that are not strictly
+// increasing in order are counted into st->unsorted.
+void canon_keys(const uint32_t *pairs, uint64_t m_in, uint32_t n, uint64_t *keys, DevState *st,
+                cudaStream_t s);
+
+// Stable removal of repeats and ~0ull from sorted keys; the count goes to
+// st->m_canon.  tile_cnt holds ceil(m_in / RX_TILE) + 1 uint32.
+void unique_keys(const uint64_t *keys, uint64_t m_in, uint64_t *out, uint32_t *tile_cnt,
+                 uint32_t *scan_scratch, DevState *st, cudaStream_t s);
+
+// ---------------------------------------------------------------- count.cu
+struct CountBuffers {
+    const uint64_t *ekey;   // canonical keys [m]
+    uint64_t m;
+    uint32_t n;
+    uint32_t *deg;          // [n]
+    uint8_t *heavy;         // [n]
+    uint32_t *rowptr;       // [n + 1]
+    uint32_t *col;          // [m]
+    uint32_t *list;         // [n] source buckets
+    DevState *st;
+};
+
+void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaStream_t s);
+void partition(const CountBuffers &b, cudaStream_t s);
+void compact_kept(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out,
+                  uint32_t *tile_cnt, uint32_t *scan_scratch, cudaStream_t s);
+void build_buckets(const CountBuffers &b, cudaStream_t s);
+void intersect(const CountBuffers &b, int max_smem_bytes, cudaStream_t s);
+void finalize(const CountBuffers &b, double p, tc_result *out_dev, cudaStream_t s);
+
+}  // namespace tcg

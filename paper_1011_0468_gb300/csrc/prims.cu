@@ -1,0 +1,304 @@
+// Data-movement primitives of libtc: device-wide exclusive scan, stable LSD
+// radix passes over 64-bit items, and the canonicalisation of raw edge lists.
+//
+// The CSR of the sampled graph is built by a stable radix sort of the
+// oriented kept edges (src << 32 | dst) on the src bits only.  The first pass
+// reads the canonical edge list directly and fuses the edge sampling of
+// Section 3.1 and the degree orientation into its loader, so the kept-edge
+// list is never materialised.  Because the canonical list is sorted by
+// (min, max), a stable sort on src alone leaves every row sorted by dst.
+#include "kernels.h"
+
+namespace tcg {
+
+// ======================================================================
+// Exclusive scan (reduce -> spine -> downsweep), 4096 elements per block.
+// ======================================================================
+
+constexpr int SC_THREADS = 1024;
+constexpr int SC_ITEMS = SC_CHUNK / SC_THREADS;  // 4
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ a, uint64_t len,
+                                                            uint32_t *__restrict__ part)
+{
+    __shared__ uint32_t wt[33];
+    const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        uint64_t i = base + (uint64_t)j * SC_THREADS + threadIdx.x;
+        if (i < len) s += a[i];
+    }
+    s = block_sum(s, wt);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// One block scans the per-block sums in place (exclusive); writes the
+// grand total to total_out when non-NULL.
+__global__ void __launch_bounds__(SC_THREADS) k_scan_spine(uint32_t *part, uint64_t nparts, uint32_t *total_out)
+{
+    __shared__ uint32_t wt[33];
+    uint32_t carry = 0;
+    for (uint64_t base = 0; base < nparts; base += SC_THREADS) {
+        uint64_t i = base + threadIdx.x;
+        uint32_t x = i < nparts ? part[i] : 0u;
+        uint32_t tot;
+        uint32_t ex = block_excl_scan(x, wt, &tot);
+        if (i < nparts) part[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down(uint32_t *a, uint64_t len, const uint32_t *__restrict__ part)
+{
+    __shared__ uint32_t wt[33];
+    const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
+    uint32_t carry = part[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        uint64_t i = base + (uint64_t)j * SC_THREADS + threadIdx.x;
+        uint32_t x = i < len ? a[i] : 0u;
+        uint32_t tot;
+        uint32_t ex = block_excl_scan(x, wt, &tot);
+        if (i < len) a[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+uint64_t scan_scratch_elems(uint64_t len) { return ceil_div(len, SC_CHUNK) + 1; }
+
+void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s)
+{
+    if (len == 0) {
+        if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+        return;
+    }
+    const uint64_t nb = ceil_div(len, SC_CHUNK);
+    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
+    k_scan_spine<<<1, SC_THREADS, 0, s>>>(scratch, nb, total); note_launch();
+    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
+}
+
+// ======================================================================
+// Stable LSD radix pass.
+// ======================================================================
+
+// Loads item i of a pass; returns false when the item does not take part
+// (an edge that the sampling drops).
+__device__ __forceinline__ bool load_item(const ItemSource &src, uint64_t i, uint64_t &item)
+{
+    if (src.kind == ItemSource::PLAIN) {
+        item = ld_stream_u64(src.in + i);
+        return true;
+    }
+    const uint64_t key = ld_stream_u64(src.in + i);
+    if (!keep_edge(key, src.seed_mix, src.thr)) return false;
+    item = orient(key, src.deg);
+    return true;
+}
+
+__global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int shift, int width,
+                                                            uint32_t *__restrict__ hist, uint32_t ntiles,
+                                                            uint32_t *__restrict__ dplus)
+{
+    __shared__ uint32_t cnt[RX_BINS];
+    const uint64_t n = src.n_dev ? *src.n_dev : src.n_host;
+    const uint32_t tile = blockIdx.x;
+    const int nb = 1 << width;
+    for (int d = threadIdx.x; d < nb; d += RX_THREADS) cnt[d] = 0;
+    __syncthreads();
+    const uint64_t base = (uint64_t)tile * RX_TILE;
+    if (base < n) {
+        const uint32_t mask = (uint32_t)nb - 1;
+        for (int j = 0; j < RX_ITEMS; ++j) {
+            const uint64_t i = base + (uint64_t)j * RX_THREADS + threadIdx.x;
+            uint64_t item = 0;
+            const bool valid = i < n && load_item(src, i, item);
+            const uint32_t d = valid ? ((uint32_t)(item >> shift) & mask) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(FULL, d);
+            if (valid) {
+                if (lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+                if (dplus) atomicAdd(dplus + (item >> 32), 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += RX_THREADS) hist[(uint64_t)d * ntiles + tile] = cnt[d];
+}
+
+__global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, int shift, int width,
+                                                              const uint32_t *__restrict__ offs, uint32_t ntiles,
+                                                              uint64_t *__restrict__ out,
+                                                              uint32_t *__restrict__ out_low32)
+{
+    constexpr int NW = RX_THREADS / 32;
+    __shared__ uint32_t whist[NW][RX_BINS];
+    __shared__ uint32_t tbase[RX_BINS];
+    const uint64_t n = src.n_dev ? *src.n_dev : src.n_host;
+    const uint32_t tile = blockIdx.x;
+    const uint64_t base = (uint64_t)tile * RX_TILE;
+    if (base >= n) return;  // uniform across the block
+    const int nb = 1 << width;
+    const uint32_t mask = (uint32_t)nb - 1;
+    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    for (int i = threadIdx.x; i < NW * RX_BINS; i += RX_THREADS) (&whist[0][0])[i] = 0;
+    for (int d = threadIdx.x; d < nb; d += RX_THREADS) tbase[d] = offs[(uint64_t)d * ntiles + tile];
+    __syncthreads();
+
+    uint64_t items[RX_ITEMS];
+    uint32_t packed[RX_ITEMS];  // digit << 16 | rank within (warp, digit); ~0 = absent
+    const uint64_t seg = base + (uint64_t)warp * 32 * RX_ITEMS;
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < RX_ITEMS; ++j) {
+        const uint64_t i = seg + (uint64_t)j * 32 + lane;
+        items[j] = 0;
+        const bool valid = i < n && load_item(src, i, items[j]);
+        const uint32_t d = valid ? ((uint32_t)(items[j] >> shift) & mask) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(FULL, d);
+        uint32_t r = 0;
+        if (valid) r = whist[warp][d] + (uint32_t)__popc(peers & lt);
+        __syncwarp();
+        if (valid && lane == (unsigned)(__ffs(peers) - 1)) whist[warp][d] += (uint32_t)__popc(peers);
+        __syncwarp();
+        packed[j] = valid ? ((d << 16) | r) : 0xffffffffu;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += RX_THREADS) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t c = whist[w][d];
+            whist[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RX_ITEMS; ++j) {
+        if (packed[j] == 0xffffffffu) continue;
+        const uint32_t d = packed[j] >> 16, r = packed[j] & 0xffffu;
+        const uint32_t pos = tbase[d] + whist[warp][d] + r;
+        if (out_low32)
+            out_low32[pos] = (uint32_t)items[j];
+        else
+            out[pos] = items[j];
+    }
+}
+
+void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
+                uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
+                cudaStream_t s)
+{
+    const uint64_t ntiles = ceil_div(n_max, RX_TILE);
+    if (ntiles == 0) return;
+    k_radix_count<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, dplus); note_launch();
+    scan_excl_u32(hist, ntiles << width, nullptr, scan_scratch, s);
+    k_radix_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, out,
+                                                            out_low32); note_launch();
+}
+
+// ======================================================================
+// Canonicalisation of raw pairs (graph creation).
+// ======================================================================
+
+__global__ void k_canon_keys(const uint32_t *__restrict__ pairs, uint64_t m_in, uint32_t n,
+                             uint64_t *__restrict__ keys, DevState *st)
+{
+    unsigned bad = 0, unsorted = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_in; i += stride) {
+        const uint2 e = make_uint2(pairs[2 * i], pairs[2 * i + 1]);  // 4-byte alignment suffices
+        uint64_t k;
+        if (e.x >= n || e.y >= n) {
+            bad = 1;
+            k = ~0ull;
+        } else if (e.x == e.y) {
+            k = ~0ull;
+        } else {
+            const uint32_t u = min(e.x, e.y), v = max(e.x, e.y);
+            k = ((uint64_t)u << 32) | v;
+        }
+        keys[i] = k;
+        // the list is already canonical iff every pair is (u < v) and the
+        // sequence strictly increases
+        if (e.x >= e.y) {
+            unsorted++;
+        } else if (i > 0) {
+            const uint2 q = make_uint2(pairs[2 * i - 2], pairs[2 * i - 1]);
+            if (!(q.x < e.x || (q.x == e.x && q.y < e.y))) unsorted++;
+        }
+    }
+    if (__any_sync(FULL, bad) && lane_id() == 0) atomicOr(&st->err, ERR_ENDPOINT);
+    unsorted = warp_sum(unsorted);
+    if (unsorted && lane_id() == 0) atomicAdd(&st->unsorted, unsorted);
+}
+
+void canon_keys(const uint32_t *pairs, uint64_t m_in, uint32_t n, uint64_t *keys, DevState *st,
+                cudaStream_t s)
+{
+    if (m_in == 0) return;
+    const uint64_t blocks = std::min<uint64_t>(ceil_div(m_in, 256), 152ull * 16);
+    k_canon_keys<<<(unsigned)blocks, 256, 0, s>>>(pairs, m_in, n, keys, st); note_launch();
+}
+
+constexpr int UQ_THREADS = 1024;
+constexpr int UQ_ITEMS = RX_TILE / UQ_THREADS;  // 4
+
+__device__ __forceinline__ bool unique_flag(const uint64_t *keys, uint64_t i)
+{
+    const uint64_t k = keys[i];
+    return k != ~0ull && (i == 0 || keys[i - 1] != k);
+}
+
+__global__ void __launch_bounds__(UQ_THREADS) k_unique_count(const uint64_t *__restrict__ keys, uint64_t m,
+                                                             uint32_t *__restrict__ tile_cnt)
+{
+    __shared__ uint32_t wt[33];
+    const uint64_t base = (uint64_t)blockIdx.x * RX_TILE;
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < UQ_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * UQ_THREADS + threadIdx.x;
+        if (i < m && unique_flag(keys, i)) ++c;
+    }
+    c = block_sum(c, wt);
+    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(UQ_THREADS) k_unique_scatter(const uint64_t *__restrict__ keys, uint64_t m,
+                                                               const uint32_t *__restrict__ tile_off,
+                                                               uint64_t *__restrict__ out)
+{
+    __shared__ uint32_t wt[33];
+    const uint64_t base = (uint64_t)blockIdx.x * RX_TILE;
+    uint32_t carry = tile_off[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < UQ_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * UQ_THREADS + threadIdx.x;
+        const bool f = i < m && unique_flag(keys, i);
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan((uint32_t)f, wt, &tot);
+        if (f) out[carry + ex] = keys[i];
+        carry += tot;
+    }
+}
+
+__global__ void k_store_count(const uint32_t *total, DevState *st) { st->m_canon = *total; }
+
+void unique_keys(const uint64_t *keys, uint64_t m_in, uint64_t *out, uint32_t *tile_cnt,
+                 uint32_t *scan_scratch, DevState *st, cudaStream_t s)
+{
+    const uint64_t nt = ceil_div(m_in, RX_TILE);
+    if (nt == 0) {
+        cudaMemsetAsync(&st->m_canon, 0, sizeof(st->m_canon), s);
+        return;
+    }
+    k_unique_count<<<(unsigned)nt, UQ_THREADS, 0, s>>>(keys, m_in, tile_cnt); note_launch();
+    scan_excl_u32(tile_cnt, nt, tile_cnt + nt, scan_scratch, s);
+    k_unique_scatter<<<(unsigned)nt, UQ_THREADS, 0, s>>>(keys, m_in, tile_cnt, out); note_launch();
+    k_store_count<<<1, 1, 0, s>>>(tile_cnt + nt, st); note_launch();
+}
+
+}  // namespace tcg

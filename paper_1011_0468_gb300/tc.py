@@ -1,0 +1,282 @@
+"""ctypes binding of libtc.so (the C ABI declared in include/tc.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libtc.so.  The functions carry the C names (``tc_graph_create``,
+``tc_count``, ...); ``Graph`` wraps them for convenience.  PyTorch is used,
+when present, only for device memory (edge lists already on the GPU) and
+streams.  If libtc.so is missing this module raises instead of falling back
+to any CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtc.so")
+
+TC_OK, TC_EINVAL, TC_ENOMEM, TC_ECUDA, TC_ETIMEOUT, TC_EBUSY = range(6)
+_STATUS = {0: "TC_OK", 1: "TC_EINVAL", 2: "TC_ENOMEM", 3: "TC_ECUDA", 4: "TC_ETIMEOUT", 5: "TC_EBUSY"}
+PHASES = ("sample", "csr", "light", "heavy", "total")
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s" % (what, _STATUS.get(status, status)))
+        self.status = status
+
+
+class tc_result(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_uint64), ("m_sampled", ctypes.c_uint64), ("n", ctypes.c_uint32),
+                ("n_heavy", ctypes.c_uint32), ("t_light", ctypes.c_uint64), ("t_heavy", ctypes.c_uint64),
+                ("estimate", ctypes.c_double), ("src_elems", ctypes.c_uint64), ("nbr_elems", ctypes.c_uint64),
+                ("ms", ctypes.c_float * 8)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms"}
+        d["ms"] = {name: float(self.ms[i]) for i, name in enumerate(PHASES)}
+        return d
+
+
+_lib = None
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_vp = ctypes.c_void_p
+
+# (name, restype, argtypes) of every exported entry point of include/tc.h
+SIGNATURES = [
+    ("tc_set_allocator", None, [_vp, _vp, _vp]),
+    ("tc_graph_create", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, _vp,
+                                       ctypes.POINTER(_vp)]),
+    ("tc_graph_destroy", None, [_vp]),
+    ("tc_graph_num_edges", ctypes.c_uint64, [_vp]),
+    ("tc_graph_num_vertices", ctypes.c_uint32, [_vp]),
+    ("tc_graph_device_bytes", ctypes.c_uint64, [_vp]),
+    ("tc_graph_set_timing", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("tc_graph_timing_drain", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32]),
+    ("tc_count", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(tc_result)]),
+    ("tc_count_async", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp]),
+    ("tc_graph_sync", ctypes.c_int, [_vp]),
+    ("tc_graph_export_sample", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _u32p, _u8p, _u32p, _u64p]),
+    ("tc_graph_export_csr", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _u32p, _u32p, _u64p]),
+    ("tc_graph_export_edges", ctypes.c_int, [_vp, _u32p]),
+    ("tc_status_str", ctypes.c_char_p, [ctypes.c_int]),
+    ("tc_version", ctypes.c_int, []),
+    ("tc_launch_count", ctypes.c_uint64, []),
+]
+
+
+def lib():
+    """The loaded libtc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtc.so is not built (%s); run __graft_entry__.build() or "
+                               "python paper_1011_0468_gb300/_build.py" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != TC_OK:
+        raise TCError(status, what)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+# ---------------------------------------------------------------- C names
+
+def tc_graph_create(edges, m_in: int, n: int, edges_on_device: bool, stream=None) -> int:
+    """edges: address (int) of m_in uint32 pairs in host or device memory."""
+    g = _vp()
+    _check(lib().tc_graph_create(edges, m_in, n, 1 if edges_on_device else 0, _stream_handle(stream),
+                                 ctypes.byref(g)), "tc_graph_create")
+    return g.value
+
+
+def tc_graph_destroy(g: int) -> None:
+    lib().tc_graph_destroy(g)
+
+
+def tc_count(g: int, p: float, seed: int) -> tc_result:
+    r = tc_result()
+    _check(lib().tc_count(g, p, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(r)), "tc_count")
+    return r
+
+
+def tc_count_async(g: int, p: float, seed: int, out_addr: int) -> None:
+    _check(lib().tc_count_async(g, p, seed & 0xFFFFFFFFFFFFFFFF, out_addr), "tc_count_async")
+
+
+def tc_graph_sync(g: int) -> None:
+    _check(lib().tc_graph_sync(g), "tc_graph_sync")
+
+
+def tc_graph_set_timing(g: int, on: bool) -> None:
+    _check(lib().tc_graph_set_timing(g, 1 if on else 0), "tc_graph_set_timing")
+
+
+def tc_status_str(s: int) -> str:
+    return lib().tc_status_str(s).decode()
+
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_torch_hooks = None
+
+
+def use_torch_allocator(on: bool = True) -> None:
+    """Route every device allocation of libtc through PyTorch's caching
+    allocator (tc_set_allocator), so graphs share torch's memory pool."""
+    global _torch_hooks
+    if not on:
+        lib().tc_set_allocator(None, None, None)
+        _torch_hooks = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream) if stream else None)
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _torch_hooks = (_ALLOC_T(_alloc), _FREE_T(_free))
+    lib().tc_set_allocator(ctypes.cast(_torch_hooks[0], _vp), ctypes.cast(_torch_hooks[1], _vp), None)
+
+
+def tc_launch_count() -> int:
+    return int(lib().tc_launch_count())
+
+
+# ---------------------------------------------------------------- wrapper
+
+def _as_pairs(edges):
+    """Host uint32 (m, 2) array, or a CUDA tensor; returns (addr, m, on_device, keepalive)."""
+    try:
+        import torch
+        if isinstance(edges, torch.Tensor):
+            if edges.dtype not in (torch.int32, torch.uint32) and str(edges.dtype) != "torch.uint32":
+                raise TypeError("edge tensor must be int32/uint32")
+            t = edges.contiguous().view(-1, 2) if edges.numel() else edges.reshape(0, 2)
+            return t.data_ptr(), t.shape[0], bool(t.is_cuda), t
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(np.asarray(edges, dtype=np.uint32).reshape(-1, 2))
+    return a.ctypes.data, a.shape[0], False, a
+
+
+class Graph:
+    """A graph resident on the GPU (tc_graph_create ... tc_graph_destroy)."""
+
+    def __init__(self, edges, n: int, stream=None):
+        addr, m_in, on_dev, keep = _as_pairs(edges)
+        self._h = tc_graph_create(addr if m_in else None, m_in, n, on_dev, stream)
+        del keep
+
+    @classmethod
+    def from_address(cls, addr: int, m_in: int, n: int, on_device: bool, stream=None) -> "Graph":
+        """Graph from m_in uint32 pairs at a raw host or device address."""
+        self = cls.__new__(cls)
+        self._h = tc_graph_create(addr if m_in else None, m_in, n, on_device, stream)
+        return self
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("graph is closed")
+        return self._h
+
+    @property
+    def m(self) -> int:
+        return int(lib().tc_graph_num_edges(self.handle))
+
+    @property
+    def n(self) -> int:
+        return int(lib().tc_graph_num_vertices(self.handle))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().tc_graph_device_bytes(self.handle))
+
+    def set_timing(self, on: bool = True):
+        tc_graph_set_timing(self.handle, on)
+
+    def timing_drain(self, max_counts: int = 256) -> np.ndarray:
+        """Phase times (counts x 8, ms) of the timed counts since the last drain."""
+        buf = np.zeros((max_counts, 8), dtype=np.float32)
+        k = lib().tc_graph_timing_drain(self.handle, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), max_counts)
+        if k < 0:
+            raise TCError(TC_ECUDA, "tc_graph_timing_drain")
+        return buf[:k]
+
+    def count(self, p: float, seed: int) -> dict:
+        return tc_count(self.handle, p, seed).as_dict()
+
+    def count_async(self, p: float, seed: int, out_addr: int) -> None:
+        tc_count_async(self.handle, p, seed, out_addr)
+
+    def sync(self):
+        tc_graph_sync(self.handle)
+
+    def export_sample(self, p: float, seed: int):
+        """(kept pairs in canonical order, heavy flags, sampled degrees)."""
+        m, n = self.m, self.n
+        kept = np.empty((max(m, 1), 2), dtype=np.uint32)
+        heavy = np.empty(max(n, 1), dtype=np.uint8)
+        deg = np.empty(max(n, 1), dtype=np.uint32)
+        mp = ctypes.c_uint64(0)
+        _check(lib().tc_graph_export_sample(self.handle, p, seed & 0xFFFFFFFFFFFFFFFF,
+                                            kept.ctypes.data_as(_u32p), heavy.ctypes.data_as(_u8p),
+                                            deg.ctypes.data_as(_u32p), ctypes.byref(mp)), "tc_graph_export_sample")
+        return kept[:mp.value], heavy[:n], deg[:n]
+
+    def export_csr(self, p: float, seed: int):
+        """(rowptr[n+1], col[m_p]) of the degree-oriented sampled graph."""
+        m, n = self.m, self.n
+        rowptr = np.empty(n + 1, dtype=np.uint32)
+        col = np.empty(max(m, 1), dtype=np.uint32)
+        mp = ctypes.c_uint64(0)
+        _check(lib().tc_graph_export_csr(self.handle, p, seed & 0xFFFFFFFFFFFFFFFF, rowptr.ctypes.data_as(_u32p),
+                                         col.ctypes.data_as(_u32p), ctypes.byref(mp)), "tc_graph_export_csr")
+        return rowptr, col[:mp.value]
+
+    def export_edges(self):
+        out = np.empty((max(self.m, 1), 2), dtype=np.uint32)
+        _check(lib().tc_graph_export_edges(self.handle, out.ctypes.data_as(_u32p)), "tc_graph_export_edges")
+        return out[:self.m]
+
+    def close(self):
+        if self._h:
+            tc_graph_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

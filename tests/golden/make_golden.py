@@ -1,0 +1,70 @@
+"""Writes the stored oracle results used by the full-size parity tests.
+
+Calls only gen/ (seeded inputs) and oracle/ (the CPU oracle); nothing here
+touches the CUDA library.  Run from the repository root:
+
+    python tests/golden/make_golden.py [chung_lu_4m]
+
+chung_lu_4m: Chung-Lu power-law graph, n = 2^22 vertices, exactly 2^26
+undirected edges, degree exponent 2.1, maximum expected degree 1e5, seed 1
+(the multi-million-edge social-network shape of the paper's Table 1).  The
+oracle result is stored for p = 1 (exact count) and p in {0.1, 0.01} with
+seeds 1..3, with a checksum of the generated edge list so that a changed
+generator is detected instead of compared against stale numbers.
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+import gen  # noqa: E402
+import oracle  # noqa: E402
+
+WORKLOADS = {
+    "chung_lu_4m": dict(kind="chung_lu", n=1 << 22, m=1 << 26, gamma=2.1, wmax=1e5, seed=1,
+                        runs=[(1.0, 1)] + [(p, s) for p in (0.1, 0.01) for s in (1, 2, 3)]),
+}
+
+
+def make_graph(spec):
+    if spec["kind"] == "chung_lu":
+        return gen.chung_lu(spec["n"], spec["m"], spec["gamma"], spec["wmax"], spec["seed"])
+    raise ValueError(spec["kind"])
+
+
+def checksum(edges: np.ndarray) -> str:
+    """Order-sensitive 64-bit checksum of the canonical edge list."""
+    e = edges.astype(np.uint64)
+    k = (e[:, 0] << np.uint64(32)) | e[:, 1]
+    w = np.arange(1, len(k) + 1, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+    with np.errstate(over="ignore"):
+        return "%016x" % int(np.bitwise_xor.reduce(k * w) if len(k) else 0)
+
+
+def main(names):
+    for name in names:
+        spec = WORKLOADS[name]
+        t0 = time.time()
+        edges = make_graph(spec)
+        rec = {"workload": name, "spec": {k: v for k, v in spec.items() if k != "runs"},
+               "m": int(len(edges)), "checksum": checksum(edges), "runs": []}
+        print(name, "generated", len(edges), "edges in %.1fs" % (time.time() - t0), flush=True)
+        for p, seed in spec["runs"]:
+            t0 = time.time()
+            r = oracle.run(edges, spec["n"], p, seed)
+            r["p"], r["seed"] = p, seed
+            r["estimate_hex"] = float(r["estimate"]).hex()
+            r["oracle_seconds"] = round(time.time() - t0, 2)
+            rec["runs"].append(r)
+            print(name, p, seed, r, flush=True)
+        with open(os.path.join(HERE, name + ".json"), "w") as f:
+            json.dump(rec, f, indent=1)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(WORKLOADS))

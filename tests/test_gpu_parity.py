@@ -1,0 +1,216 @@
+"""GPU parity: libtc (through its C ABI) against the CPU oracle.
+
+Integer outputs (kept edge set, sampled degrees, heavy flags, m_p, n_heavy,
+T_L, T_H) must be bit-exact; the float64 estimate must agree to a relative
+1e-12 (both sides compute T_L/p^3 + T_H/p^3 with IEEE round-to-nearest
+operations in the same order, so in practice it is identical).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+INT_KEYS = ("m", "m_sampled", "n", "n_heavy", "t_light", "t_heavy")
+
+
+@pytest.fixture(scope="module")
+def tc():
+    from paper_1011_0468_gb300 import _build, tc as _tc
+    _build.build()
+    return _tc
+
+
+def assert_same(got, want, ctx=""):
+    for k in INT_KEYS:
+        assert got[k] == want[k], (ctx, k, got[k], want[k])
+    e, w = got["estimate"], want["estimate"]
+    assert e == w or abs(e - w) <= 1e-12 * abs(w), (ctx, e, w)
+
+
+def check_graph(tc, edges, n, runs, sample=True):
+    with tc.Graph(edges, n) as g:
+        assert g.m == len(edges)
+        for p, seed in runs:
+            want = oracle.run(edges, n, p, seed, want_sample=sample)
+            got = g.count(p, seed)
+            assert_same(got, want, (p, seed))
+            if sample:
+                kept, heavy, deg = g.export_sample(p, seed)
+                assert np.array_equal(kept, want["kept"]), (p, seed)
+                assert np.array_equal(heavy, want["heavy"]), (p, seed)
+                assert np.array_equal(deg, oracle.degrees(want["kept"], n)), (p, seed)
+
+
+# ------------------------------------------------------------ configs
+
+def test_er_2000_20000_exact_and_sampled(tc):
+    """Erdos-Renyi G(2000, 20000), seed 1: p = 1 and p = 0.1 with seeds 1..10."""
+    e = gen.er(2000, 20000, 1)
+    check_graph(tc, e, 2000, [(1.0, 1)] + [(0.1, s) for s in range(1, 11)])
+
+
+@pytest.mark.parametrize("n,m,wmax", [(100_000, 1_000_000, 5000.0), (300_000, 3_000_000, 20000.0)])
+def test_chung_lu_power_law(tc, n, m, wmax):
+    """Power-law graphs with heavy vertices; many radix tiles, ragged tails."""
+    e = gen.chung_lu(n, m, 2.1, wmax, 5)
+    check_graph(tc, e, n, [(1.0, 1), (0.5, 2), (0.1, 3), (0.01, 4)])
+
+
+def test_rmat_small(tc):
+    e = gen.rmat(16, 16, seed=3)
+    check_graph(tc, e, 1 << 16, [(1.0, 1), (0.05, 2)])
+
+
+def test_dense_core_heavy_block(tc):
+    """A dense core (many heavy vertices, large T_H) inside a sparse graph."""
+    core = gen.er(1500, 1500 * 1499 // 2 // 3, 11)  # density 1/3
+    rest = gen.er(200_000, 400_000, 12).astype(np.int64) + 1500
+    e = gen.canonical(np.concatenate([core.astype(np.int64), rest,
+                                      np.stack([np.arange(1500), 1500 + np.arange(1500) * 7], 1)]))
+    n = 201_500
+    r = oracle.run(e, n, 1.0, 1)
+    assert r["n_heavy"] > 100 and r["t_heavy"] > 0
+    check_graph(tc, e, n, [(1.0, 1), (0.7, 2)], sample=False)
+
+
+# ------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("k", [3, 4, 5, 17, 33, 34, 65, 130])
+def test_complete_graphs(tc, k):
+    e = gen.complete(k)
+    with tc.Graph(e, k) as g:
+        r = g.count(1.0, 1)
+    assert (r["t_light"], r["t_heavy"], r["n_heavy"]) == (0, math.comb(k, 3), k)
+
+
+@pytest.mark.parametrize("k", [4, 5, 6, 40, 100])
+def test_wheels(tc, k):
+    with tc.Graph(gen.wheel(k), k + 1) as g:
+        r = g.count(1.0, 9)
+    assert r["t_light"] + r["t_heavy"] == k
+    assert r["t_heavy"] == (4 if k == 4 else 0)
+
+
+def test_strict_threshold(tc):
+    e, n = gen.disjoint_union(gen.complete(4), [[0, 1]], [[0, 1]], [[0, 1]])
+    with tc.Graph(e, n) as g:
+        r = g.count(1.0, 1)
+    assert (r["m"], r["n_heavy"], r["t_light"], r["t_heavy"]) == (9, 0, 4, 0)
+
+
+@pytest.mark.parametrize("edges", [gen.star(1000), gen.random_tree(5000, 2), gen.complete_bipartite(40, 60),
+                                   gen.cycle(1000)])
+def test_triangle_free(tc, edges):
+    n = gen.num_vertices(edges)
+    with tc.Graph(edges, n) as g:
+        r = g.count(1.0, 3)
+    assert (r["t_light"], r["t_heavy"], r["estimate"]) == (0, 0, 0.0)
+
+
+# ------------------------------------------------------------ edges / inputs
+
+def test_raw_input_is_canonicalised(tc):
+    rng = np.random.default_rng(7)
+    n = 3000
+    raw = rng.integers(0, n, size=(60_000, 2)).astype(np.uint32)  # repeats, loops, both orders
+    want_edges = oracle.canonicalize(raw, n)
+    with tc.Graph(raw, n) as g:
+        assert np.array_equal(g.export_edges(), want_edges)
+        for p, s in ((1.0, 1), (0.3, 2)):
+            assert_same(g.count(p, s), oracle.run(want_edges, n, p, s))
+
+
+def test_device_input(tc):
+    import torch
+    rng = np.random.default_rng(8)
+    n = 5000
+    raw = rng.integers(0, n, size=(80_000, 2)).astype(np.int32)
+    dev = torch.from_numpy(raw).cuda()
+    want_edges = oracle.canonicalize(raw.astype(np.uint32), n)
+    with tc.Graph(dev, n) as g:
+        assert np.array_equal(g.export_edges(), want_edges)
+        assert_same(g.count(0.5, 5), oracle.run(want_edges, n, 0.5, 5))
+
+
+def test_empty_and_tiny(tc):
+    for edges, n in ((np.zeros((0, 2), np.uint32), 1), (np.zeros((0, 2), np.uint32), 100_000),
+                     (np.array([[0, 1]], np.uint32), 2), (gen.complete(3), 3)):
+        with tc.Graph(edges, n) as g:
+            for p, s in ((1.0, 1), (0.5, 2)):
+                assert_same(g.count(p, s), oracle.run(edges, n, p, s))
+
+
+def test_everything_dropped(tc):
+    e = gen.er(1000, 5000, 4)
+    with tc.Graph(e, 1000) as g:
+        r = g.count(2.0 ** -53, 1)
+    assert (r["m_sampled"], r["t_light"], r["t_heavy"], r["n_heavy"]) == (0, 0, 0, 0)
+
+
+def test_invalid_arguments(tc):
+    e = gen.er(100, 300, 4)
+    with tc.Graph(e, 100) as g:
+        for p in (0.0, -1.0, 1.0000001, float("nan"), float("inf")):
+            with pytest.raises(tc.TCError) as ei:
+                g.count(p, 1)
+            assert ei.value.status == tc.TC_EINVAL
+        # the graph stays usable after rejected calls
+        assert_same(g.count(1.0, 1), oracle.run(e, 100, 1.0, 1))
+    with pytest.raises(tc.TCError) as ei:
+        tc.Graph(np.array([[0, 1], [2, 100]], np.uint32), 100)
+    assert ei.value.status == tc.TC_EINVAL
+
+
+def test_async_matches_blocking(tc):
+    import ctypes
+    import torch
+    e = gen.chung_lu(50_000, 400_000, 2.1, 2000.0, 9)
+    buf = torch.empty(ctypes.sizeof(tc.tc_result), dtype=torch.uint8, pin_memory=True)
+    with tc.Graph(e, 50_000) as g:
+        want = g.count(0.4, 3)
+        g.count_async(0.4, 3, buf.data_ptr())
+        g.sync()
+        got = tc.tc_result.from_address(buf.data_ptr()).as_dict()
+    for k in INT_KEYS + ("estimate",):
+        assert got[k] == want[k]
+
+
+def test_repeat_is_deterministic(tc):
+    e = gen.chung_lu(100_000, 800_000, 2.1, 4000.0, 10)
+    with tc.Graph(e, 100_000) as g:
+        a = [g.count(0.3, 5) for _ in range(3)]
+    for r in a[1:]:
+        for k in INT_KEYS + ("estimate",):
+            assert r[k] == a[0][k]
+
+
+# ------------------------------------------------------------ CSR properties
+
+def test_csr_is_degree_oriented_and_sorted(tc):
+    n = 100_000
+    e = gen.chung_lu(n, 1_000_000, 2.1, 5000.0, 6)
+    for p, s in ((1.0, 1), (0.2, 2)):
+        want = oracle.run(e, n, p, s, want_sample=True)
+        kept, deg = want["kept"], oracle.degrees(want["kept"], n)
+        with tc.Graph(e, n) as g:
+            rowptr, col = g.export_csr(p, s)
+        assert rowptr[0] == 0 and rowptr[-1] == len(kept) == len(col)
+        assert np.all(np.diff(rowptr.astype(np.int64)) >= 0)
+        src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr.astype(np.int64)))
+        dst = col.astype(np.int64)
+        # every row strictly increasing
+        same = src[1:] == src[:-1]
+        assert np.all(dst[1:][same] > dst[:-1][same])
+        # orientation: (deg, id) of src below that of dst
+        ds, dd = deg[src].astype(np.int64), deg[dst].astype(np.int64)
+        assert np.all((ds < dd) | ((ds == dd) & (src < dst)))
+        # the undirected edge set is exactly the kept set
+        und = np.sort(np.stack([np.minimum(src, dst), np.maximum(src, dst)], 1), axis=0)
+        keys = und[:, 0] * (1 << 32) + und[:, 1]
+        kk = kept.astype(np.int64)
+        assert np.array_equal(np.sort(keys), kk[:, 0] * (1 << 32) + kk[:, 1])
