@@ -79,7 +79,11 @@ struct tc_graph {
     uint32_t *deg = nullptr;    // [n]
     uint32_t *rowptr = nullptr; // [n + 1]
     uint8_t *heavy = nullptr;   // [n]
-    uint32_t *list = nullptr;   // [n]
+    uint32_t *inptr = nullptr;  // [n + 2] in-list offsets (see InListArgs)
+    uint32_t *col = nullptr;    // CSR columns (inside bufA or bufB)
+    uint32_t *inlist = nullptr; // in-lists (second half of the same buffer)
+    uint64_t *items = nullptr;  // owner work items, all buckets [items_cap]
+    uint64_t items_cap = 0;
     uint32_t *hist = nullptr;   // [RX_BINS * ntiles(m)]
     uint32_t *scan = nullptr;   // scan scratch
     DevState *st = nullptr;
@@ -148,16 +152,27 @@ void enqueue_sample(tc_graph *g, uint64_t seed_mix, uint64_t thr, const CountBuf
     partition(b, g->stream);
 }
 
+// Radix passes of the CSR build: at least two, so that the out-degree counts
+// (histogrammed by the first pass) are complete when the last pass runs and
+// builds the in-lists.
+std::vector<int> csr_pass_widths(int bits)
+{
+    std::vector<int> w = pass_widths(bits);
+    if (w.size() == 1) w = {(bits + 1) / 2, bits / 2};
+    return w;
+}
+
 // Degree-oriented CSR of the sampled graph by stable LSD radix sort of
-// (src << 32 | dst) on the src bits; returns the column array.
-uint32_t *enqueue_csr(tc_graph *g, uint64_t seed_mix, uint64_t thr)
+// (src << 32 | dst) on the src bits, plus the in-lists of the pairs whose
+// source has the smaller out-degree.  Fills g->col / g->inlist / g->inptr.
+void enqueue_csr(tc_graph *g, uint64_t seed_mix, uint64_t thr)
 {
     cudaMemsetAsync(g->rowptr, 0, ((size_t)g->n + 1) * 4, g->stream);
-    const std::vector<int> widths = pass_widths(g->nbits);
+    cudaMemsetAsync(g->inptr, 0, ((size_t)g->n + 2) * 4, g->stream);
+    const std::vector<int> widths = csr_pass_widths(g->nbits);
     uint64_t *bufs[2] = {g->bufA, g->bufB};
     const uint64_t *in = g->ekey;
     int cur = 0, shift = 32;
-    uint32_t *col = nullptr;
     for (size_t p = 0; p < widths.size(); ++p) {
         const bool last = p + 1 == widths.size();
         ItemSource src;
@@ -167,15 +182,21 @@ uint32_t *enqueue_csr(tc_graph *g, uint64_t seed_mix, uint64_t thr)
             src = ItemSource{ItemSource::PLAIN, in, 0, &g->st->m_sampled, nullptr, 0, 0};
         }
         uint64_t *out = bufs[cur];
-        if (last) col = reinterpret_cast<uint32_t *>(out);
+        InListArgs il{g->rowptr, g->inptr, nullptr, g->n};
+        if (last) {
+            // col takes the first 4 m bytes of the output buffer, the in-lists
+            // the second half; the input buffer is still being read
+            g->col = reinterpret_cast<uint32_t *>(out);
+            g->inlist = reinterpret_cast<uint32_t *>(out) + g->m;
+            il.inlist = g->inlist;
+        }
         radix_pass(src, g->m, shift, widths[p], g->hist, g->scan, p == 0 ? g->rowptr : nullptr,
-                   last ? nullptr : out, last ? col : nullptr, g->stream);
+                   last ? nullptr : out, last ? g->col : nullptr, last ? &il : nullptr, g->stream);
         in = out;
         cur ^= 1;
         shift += widths[p];
     }
     scan_excl_u32(g->rowptr, (uint64_t)g->n + 1, nullptr, g->scan, g->stream);
-    return col;
 }
 
 CountBuffers buffers_of(tc_graph *g)
@@ -187,8 +208,11 @@ CountBuffers buffers_of(tc_graph *g)
     b.deg = g->deg;
     b.heavy = g->heavy;
     b.rowptr = g->rowptr;
-    b.col = nullptr;
-    b.list = g->list;
+    b.col = g->col;
+    b.inptr = g->inptr;
+    b.inlist = g->inlist;
+    b.items = g->items;
+    b.items_cap = g->items_cap;
     b.st = g->st;
     return b;
 }
@@ -225,8 +249,9 @@ tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bo
     enqueue_sample(g, seed_mix, thr, b);
     record(g, timing, 1);
     if (g->m > 0) {
-        b.col = enqueue_csr(g, seed_mix, thr);
-        build_buckets(b, g->stream);
+        enqueue_csr(g, seed_mix, thr);
+        b = buffers_of(g);
+        build_items(b, g->stream);
     }
     record(g, timing, 2);
     if (g->m > 0) intersect(b, g->smem_bytes, g->stream);
@@ -348,7 +373,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
                 int shift = half ? 32 : 0;
                 for (int w : pass_widths(g->nbits)) {
                     ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
-                    radix_pass(src, m_in, shift, w, hist, scan, nullptr, b, nullptr, s);
+                    radix_pass(src, m_in, shift, w, hist, scan, nullptr, b, nullptr, nullptr, s);
                     std::swap(a, b);
                     shift += w;
                 }
@@ -374,10 +399,13 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     g->deg = (uint32_t *)g->alloc((uint64_t)n * 4);
     g->rowptr = (uint32_t *)g->alloc(((uint64_t)n + 1) * 4);
     g->heavy = (uint8_t *)g->alloc((uint64_t)n);
-    g->list = (uint32_t *)g->alloc((uint64_t)n * 4);
+    g->inptr = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
+    g->items_cap = items_capacity(n, m);
+    g->items = (uint64_t *)g->alloc(g->items_cap * 8);
     g->hist = (uint32_t *)g->alloc(hist_len * 4);
     g->scan = (uint32_t *)g->alloc(scan_scratch_elems(std::max<uint64_t>(hist_len, (uint64_t)n + 1)) * 4);
-    if (!g->bufA || !g->bufB || !g->deg || !g->rowptr || !g->heavy || !g->list || !g->hist || !g->scan) {
+    if (!g->bufA || !g->bufB || !g->deg || !g->rowptr || !g->heavy || !g->inptr || !g->items || !g->hist ||
+        !g->scan) {
         free_graph(g);
         return TC_ENOMEM;
     }
@@ -385,10 +413,14 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
         g->ekey = (uint64_t *)g->alloc(8);
         if (!g->ekey) { free_graph(g); return TC_ENOMEM; }
     }
-    // shared-memory staging of N+(u) in the block-per-source kernel: every
-    // out-degree of the degree-oriented graph is at most sqrt(2 m_p)
-    const uint64_t cap = (uint64_t)std::sqrt(2.0 * (double)std::max<uint64_t>(m, 1)) + 2;
-    g->smem_bytes = (int)std::min<uint64_t>(cap * 4, 160 * 1024);
+    // hash table of the owners with d+ > 1024: every out-degree of the
+    // degree-oriented graph is at most sqrt(2 m_p); a table of >= 2 d+ slots
+    // up to 32768 slots (128 KiB) stays on chip, larger rows are searched in
+    // place
+    const uint64_t dmax = (uint64_t)std::sqrt(2.0 * (double)std::max<uint64_t>(m, 1)) + 2;
+    uint64_t slots = 4096;
+    while (slots < 2 * dmax && slots < 32768) slots <<= 1;
+    g->smem_bytes = (int)(slots * 4);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         free_graph(g);
         return TC_ECUDA;
@@ -501,9 +533,8 @@ tc_status tc_graph_export_csr(tc_graph *g, double p, uint64_t seed, uint32_t *ro
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
     CountBuffers b = buffers_of(g);
     enqueue_sample(g, seed_mix, thr, b);
-    uint32_t *col = nullptr;
     if (g->m > 0) {
-        col = enqueue_csr(g, seed_mix, thr);
+        enqueue_csr(g, seed_mix, thr);
     } else {
         cudaMemsetAsync(g->rowptr, 0, ((size_t)g->n + 1) * 4, g->stream);
     }
@@ -514,7 +545,7 @@ tc_status tc_graph_export_csr(tc_graph *g, double p, uint64_t seed, uint32_t *ro
     if (m_sampled) *m_sampled = mp;
     if (rowptr_host)
         cudaMemcpyAsync(rowptr_host, g->rowptr, ((size_t)g->n + 1) * 4, cudaMemcpyDeviceToHost, g->stream);
-    if (col_host && mp > 0) cudaMemcpyAsync(col_host, col, mp * 4, cudaMemcpyDeviceToHost, g->stream);
+    if (col_host && mp > 0) cudaMemcpyAsync(col_host, g->col, mp * 4, cudaMemcpyDeviceToHost, g->stream);
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) { cudaGetLastError(); return TC_ECUDA; }
     return TC_OK;
 }

@@ -29,7 +29,8 @@ struct DevState {
     unsigned int nlist[4];         // sizes of the source buckets
     unsigned int cursor[4];        // dynamic work cursors (one per kernel)
     unsigned long long src_elems;  // sum of d+(u) over intersected sources
-    unsigned long long nbr_elems;  // sum over them of sum_{v in N+(u)} d+(v)
+    unsigned long long nbr_elems;  // list elements streamed through the tables
+    unsigned long long partners;   // (owner, partner) pairs processed
     unsigned long long m_canon;    // canonical edges (create only)
     unsigned int unsorted;         // create: adjacent pairs out of order
     unsigned int pad;

@@ -135,45 +135,109 @@ void compact_kept(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64
 }
 
 // ======================================================================
-// Source buckets by out-degree d+ (sources with d+ < 2 close no triangle)
-//   bucket 0: 2 <= d+ <= 32  -> one warp per source, list front
-//   bucket 1: d+ > 32        -> one block per source, list back
+// Owner work items.
+//
+// Every oriented pair (a -> b) closes |N+(a) n N+(b)| triangles.  The pair
+// is handled by the endpoint with the LONGER out-list as the "owner": its
+// list is put into a shared-memory hash table and the shorter list is
+// streamed through it, so each pair reads min(d+(a), d+(b)) list elements.
+//   owner x, partner v in N+(x) with d+(v) <= d+(x)   (class of x)
+//   owner x, partner u in in-list(x): d+(u) < d+(x)   (class of u)
+// The class of a triangle is the class of its lowest vertex, which is the
+// source of the pair: x in the first case, u in the second.
+//
+// An item is (segment << 32 | owner); segment s covers partners
+// [s * SEG, (s + 1) * SEG) of the owner's partner sequence (its d+(x)
+// out-neighbours, then its in-list).  Owners are bucketed by d+(x), which
+// sizes their table: 2..32 (one warp), 33..1024 (one block, static table),
+// > 1024 (one block, dynamic table).  Owners with d+ < 2 close nothing.
 // ======================================================================
 
-constexpr uint32_t SMALL_MAX = 32;
+constexpr uint32_t SEG = 256;
+constexpr uint32_t WARP_MAX = 32, MID_MAX = 1024;
+constexpr uint32_t EMPTY = 0xffffffffu;
 
-__global__ void k_buckets(const uint32_t *__restrict__ rowptr, uint32_t n, uint32_t *__restrict__ list,
-                          DevState *st)
+uint64_t items_capacity(uint32_t n, uint64_t m)
+{
+    // warp + mid items: <= owners + (m_p + in-list) / SEG; large items after
+    const uint64_t wm = (uint64_t)n + 2 * m / SEG + 64;
+    const uint64_t large = m / MID_MAX + 2 * m / SEG + 64;
+    return wm + large;
+}
+
+static uint64_t wm_capacity(uint32_t n, uint64_t m) { return (uint64_t)n + 2 * m / SEG + 64; }
+
+__device__ __forceinline__ uint32_t bucket_of(uint32_t d) { return d <= WARP_MAX ? 0u : (d <= MID_MAX ? 1u : 2u); }
+
+__global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ inptr, uint32_t n,
+                        uint64_t *__restrict__ items, uint64_t wm_cap, uint64_t cap, DevState *st)
 {
     const unsigned lane = lane_id();
-    const unsigned lt = lanemask_lt();
     const uint64_t wstride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += wstride) {
-        const uint64_t u = base + lane;
-        uint32_t d = 0;
-        if (u < n) d = rowptr[u + 1] - rowptr[u];
-        const bool b0 = d >= 2 && d <= SMALL_MAX, b1 = d > SMALL_MAX;
-        const unsigned m0 = __ballot_sync(FULL, b0), m1 = __ballot_sync(FULL, b1);
-        uint32_t o0 = 0, o1 = 0;
-        if (lane == 0) {
-            if (m0) o0 = atomicAdd(&st->nlist[0], (unsigned)__popc(m0));
-            if (m1) o1 = atomicAdd(&st->nlist[1], (unsigned)__popc(m1));
+        const uint64_t x = base + lane;
+        uint32_t d = 0, np = 0;
+        if (x < n) {
+            d = rowptr[x + 1] - rowptr[x];
+            if (d >= 2) np = d + (inptr[x + 1] - inptr[x]);
         }
-        o0 = __shfl_sync(FULL, o0, 0);
-        o1 = __shfl_sync(FULL, o1, 0);
-        if (b0) list[o0 + __popc(m0 & lt)] = (uint32_t)u;
-        if (b1) list[n - 1 - (o1 + __popc(m1 & lt))] = (uint32_t)u;
+        const uint32_t nseg = (np + SEG - 1) / SEG, b = bucket_of(d);
+#pragma unroll
+        for (uint32_t bb = 0; bb < 3; ++bb) {
+            const uint32_t c = b == bb ? nseg : 0u;
+            const uint32_t inc = warp_incl_scan(c);
+            uint32_t off = 0;
+            if (lane == 31 && inc) off = atomicAdd(&st->nlist[bb], inc);
+            off = __shfl_sync(FULL, off, 31) + inc - c;
+            for (uint32_t s = 0; s < c; ++s) {
+                const uint64_t idx = (uint64_t)off + s;
+                const uint64_t pos = bb == 0 ? idx : (bb == 1 ? wm_cap - 1 - idx : wm_cap + idx);
+                const bool ok = bb == 2 ? pos < cap : idx < wm_cap;
+                if (ok)
+                    items[pos] = ((uint64_t)s << 32) | (uint32_t)x;
+                else
+                    atomicOr(&st->err, ERR_OVERFLOW);
+            }
+        }
     }
 }
 
-void build_buckets(const CountBuffers &b, cudaStream_t s)
+void build_items(const CountBuffers &b, cudaStream_t s)
 {
-    k_buckets<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.n, b.list, b.st); note_launch();
+    const uint64_t wm = wm_capacity(b.n, b.m);
+    k_items<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.inptr, b.n, b.items, wm, b.items_cap, b.st); note_launch();
 }
 
 // ======================================================================
-// Intersections
+// Shared-memory hash set of an out-list (open addressing, linear probing,
+// at most half full, so every probe sequence meets an empty slot).
 // ======================================================================
+
+__device__ __forceinline__ uint32_t tab_hash(uint32_t y, uint32_t shift) { return (y * 0x9e3779b1u) >> shift; }
+
+// Both loops visit at most every slot once (the table is never more than half
+// full, so they normally stop after one or two slots).
+__device__ __forceinline__ void tab_insert(uint32_t *tab, uint32_t mask, uint32_t shift, uint32_t y)
+{
+    uint32_t h = tab_hash(y, shift);
+    for (uint32_t it = 0; it <= mask; ++it) {
+        const uint32_t prev = atomicCAS(tab + h, EMPTY, y);
+        if (prev == EMPTY || prev == y) return;
+        h = (h + 1) & mask;
+    }
+}
+
+__device__ __forceinline__ bool tab_probe(const uint32_t *tab, uint32_t mask, uint32_t shift, uint32_t y)
+{
+    uint32_t h = tab_hash(y, shift);
+    for (uint32_t it = 0; it <= mask; ++it) {
+        const uint32_t k = tab[h];
+        if (k == y) return true;
+        if (k == EMPTY) return false;
+        h = (h + 1) & mask;
+    }
+    return false;
+}
 
 // Largest i in [0, cnt) with pre[i] <= e, for non-decreasing pre with
 // pre[0] = 0 <= e.
@@ -188,157 +252,221 @@ __device__ __forceinline__ uint32_t seg_of(const uint32_t *pre, uint32_t cnt, ui
 }
 
 // Is w in the sorted list a[0, len)?
-__device__ __forceinline__ bool contains(const uint32_t *a, uint32_t len, uint32_t w)
+__device__ __forceinline__ bool sorted_contains(const uint32_t *a, uint32_t len, uint32_t w)
 {
     uint32_t lo = 0, hi = len;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (a[mid] < w) lo = mid + 1; else hi = mid;
+        if (__ldg(a + mid) < w) lo = mid + 1; else hi = mid;
     }
-    return lo < len && a[lo] == w;
+    return lo < len && __ldg(a + lo) == w;
 }
 
-constexpr int IW_THREADS = 256;
-constexpr int IW_WARPS = IW_THREADS / 32;
+struct Tally {
+    unsigned long long light = 0, heavy = 0, table = 0, stream = 0, partners = 0;
+};
 
-// One warp per source u with 2 <= d+(u) <= 32.  N+(u) is staged in shared
-// memory; the concatenation of N+(v) over v in N+(u) is walked 32 elements
-// at a time (one per lane, coalesced within each list) and every element w
-// is binary-searched in N+(u).
-__global__ void __launch_bounds__(IW_THREADS) k_isect_warp(const uint32_t *__restrict__ rowptr,
+__device__ __forceinline__ void flush_tally(Tally t, unsigned long long *red /* 33 */, DevState *st)
+{
+    unsigned long long v[5] = {t.light, t.heavy, t.table, t.stream, t.partners};
+    unsigned long long *dst[5] = {&st->t_light, &st->t_heavy, &st->src_elems, &st->nbr_elems, &st->partners};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const unsigned long long s = block_sum(v[i], red);
+        if (threadIdx.x == 0 && s) atomicAdd(dst[i], s);
+    }
+}
+
+// Partner j of owner x (j < d: out-neighbour, else in-list entry): the
+// start and length of the list to stream and the class of the pair's
+// triangles; len = 0 when the pair is handled elsewhere or closes nothing.
+__device__ __forceinline__ void partner(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ inlist,
+                                        const uint8_t *__restrict__ heavy, uint32_t d, uint32_t ib, uint8_t hx,
+                                        uint32_t j, uint32_t y, bool is_out, uint32_t &start, uint32_t &len,
+                                        uint32_t &cls)
+{
+    (void)j;
+    (void)inlist;
+    const uint32_t yb = rowptr[y], dy = rowptr[y + 1] - yb;
+    start = yb;
+    if (is_out) {
+        len = (dy >= 1 && dy <= d) ? dy : 0u;
+        cls = hx;
+    } else {
+        len = dy >= 2 ? dy : 0u;
+        cls = len ? heavy[y] : 0u;
+    }
+    (void)ib;
+}
+
+// ---------------------------------------------------------------- warp items
+
+constexpr int PW_THREADS = 256;
+constexpr int PW_WARPS = PW_THREADS / 32;
+constexpr uint32_t WTAB = 64;  // table slots for d+ <= 32
+
+__global__ void __launch_bounds__(PW_THREADS) k_probe_warp(const uint32_t *__restrict__ rowptr,
                                                            const uint32_t *__restrict__ col,
-                                                           const uint32_t *__restrict__ list,
+                                                           const uint32_t *__restrict__ inptr,
+                                                           const uint32_t *__restrict__ inlist,
+                                                           const uint64_t *__restrict__ items, uint64_t wm_cap,
                                                            const uint8_t *__restrict__ heavy, DevState *st)
 {
-    __shared__ uint32_t s_nu[IW_WARPS][SMALL_MAX];
-    __shared__ uint32_t s_vb[IW_WARPS][SMALL_MAX];
-    __shared__ uint32_t s_pre[IW_WARPS][SMALL_MAX + 1];
-    __shared__ unsigned long long s_red[4][IW_WARPS];
+    __shared__ uint32_t s_tab[PW_WARPS][WTAB];
+    __shared__ uint32_t s_pre[PW_WARPS][32];
+    __shared__ uint32_t s_beg[PW_WARPS][32];
+    __shared__ unsigned long long red[33];
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
-    const uint32_t nl = st->nlist[0];
-    const uint32_t gw = blockIdx.x * IW_WARPS + w, nwarps = gridDim.x * IW_WARPS;
-    unsigned long long cl = 0, ch = 0, ws = 0, wn = 0;
-    for (uint32_t idx = gw; idx < nl; idx += nwarps) {
-        const uint32_t u = list[idx];
-        const uint32_t beg = rowptr[u], d = rowptr[u + 1] - beg;
-        uint32_t x = 0, vb = 0, len = 0;
+    const uint32_t nitems = (uint32_t)min((unsigned long long)st->nlist[0], (unsigned long long)wm_cap);
+    constexpr uint32_t shift = 32 - 6;  // log2(WTAB) = 6
+    Tally t;
+    for (;;) {
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(&st->cursor[0], 1u);
+        idx = __shfl_sync(FULL, idx, 0);
+        if (idx >= nitems) break;
+        const uint64_t item = items[idx];
+        const uint32_t x = (uint32_t)item, seg = (uint32_t)(item >> 32);
+        const uint32_t beg = rowptr[x], d = rowptr[x + 1] - beg;
+        if (d > WARP_MAX) {  // cannot happen unless the item list overflowed
+            if (lane == 0) atomicOr(&st->err, ERR_OVERFLOW);
+            continue;
+        }
+        const uint8_t hx = heavy[x];
+        s_tab[w][lane] = EMPTY;
+        s_tab[w][lane + 32] = EMPTY;
+        __syncwarp();
+        uint32_t own = 0;
         if (lane < d) {
-            x = col[beg + lane];
-            vb = rowptr[x];
-            len = rowptr[x + 1] - vb;
+            own = col[beg + lane];
+            tab_insert(s_tab[w], WTAB - 1, shift, own);
         }
-        s_nu[w][lane] = x;
-        s_vb[w][lane] = vb;
-        const uint32_t inc = warp_incl_scan(len);
-        s_pre[w][lane] = inc - len;
-        const uint32_t W = __shfl_sync(FULL, inc, 31);
         __syncwarp();
-        uint32_t c = 0;
-        for (uint32_t e = lane; e < W; e += 32) {
-            const uint32_t i = seg_of(s_pre[w], d, e);
-            const uint32_t y = col[s_vb[w][i] + (e - s_pre[w][i])];
-            c += contains(s_nu[w], d, y);
+        if (seg == 0) t.table += d;
+        const uint32_t ib = inptr[x], np = d + (inptr[x + 1] - ib);
+        const uint32_t p0 = seg * SEG, p1 = min(np, p0 + SEG);
+        for (uint32_t c0 = p0; c0 < p1; c0 += 32) {
+            const uint32_t j = c0 + lane;
+            uint32_t start = 0, len = 0, cls = 0;
+            if (j < p1) {
+                // out-partners only occur in the first chunk (d <= 32), where j == lane
+                const bool is_out = j < d;
+                const uint32_t y = is_out ? own : inlist[ib + j - d];
+                partner(rowptr, inlist, heavy, d, ib, hx, j, y, is_out, start, len, cls);
+            }
+            const uint32_t inc = warp_incl_scan(len);
+            const uint32_t W = __shfl_sync(FULL, inc, 31);
+            const unsigned clsmask = __ballot_sync(FULL, cls != 0);
+            const unsigned live = __ballot_sync(FULL, len != 0);
+            if (lane == 0) t.partners += __popc(live);
+            s_pre[w][lane] = inc - len;
+            s_beg[w][lane] = start;
+            __syncwarp();
+            for (uint32_t e = lane; e < W; e += 32) {
+                const uint32_t i = seg_of(s_pre[w], 32, e);
+                const uint32_t y = col[s_beg[w][i] + (e - s_pre[w][i])];
+                if (tab_probe(s_tab[w], WTAB - 1, shift, y)) {
+                    if ((clsmask >> i) & 1u) ++t.heavy; else ++t.light;
+                }
+            }
+            if (lane == 0) t.stream += W;
+            __syncwarp();
         }
-        c = warp_sum(c);
-        if (heavy[u]) ch += c; else cl += c;
-        ws += d;
-        wn += W;
-        __syncwarp();
     }
-    if (lane == 0) {
-        s_red[0][w] = cl;
-        s_red[1][w] = ch;
-        s_red[2][w] = ws;
-        s_red[3][w] = wn;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        unsigned long long t = 0;
-        for (int i = 0; i < IW_WARPS; ++i) t += s_red[threadIdx.x][i];
-        unsigned long long *dst[4] = {&st->t_light, &st->t_heavy, &st->src_elems, &st->nbr_elems};
-        if (t) atomicAdd(dst[threadIdx.x], t);
-    }
+    if (lane != 0) t.table = 0;  // counted once per warp
+    flush_tally(t, red, st);
 }
 
-constexpr int IB_THREADS = 256;
+// ---------------------------------------------------------------- block items
 
-// One block per source u with d+(u) > 32, taken from a global work cursor.
-// N+(u) is staged in shared memory when it fits (cap elements), otherwise
-// searched in place.  Chunks of IB_THREADS out-neighbours v are processed at
-// a time: a block scan of d+(v) lays the chunk's lists end to end and the
-// block walks that concatenation, one element per thread.
-__global__ void __launch_bounds__(IB_THREADS) k_isect_block(const uint32_t *__restrict__ rowptr,
+constexpr int PB_THREADS = 256;
+constexpr uint32_t MID_TAB = 2048;  // slots, >= 2 * MID_MAX
+
+template <bool DYN>
+__global__ void __launch_bounds__(PB_THREADS) k_probe_block(const uint32_t *__restrict__ rowptr,
                                                             const uint32_t *__restrict__ col,
-                                                            const uint32_t *__restrict__ list, uint32_t n,
+                                                            const uint32_t *__restrict__ inptr,
+                                                            const uint32_t *__restrict__ inlist,
+                                                            const uint64_t *__restrict__ items, uint64_t wm_cap,
                                                             const uint8_t *__restrict__ heavy, DevState *st,
-                                                            uint32_t cap)
+                                                            uint32_t tab_slots, uint64_t cap)
 {
-    extern __shared__ uint32_t s_nu[];
-    __shared__ uint32_t s_pre[IB_THREADS];
-    __shared__ uint32_t s_vb[IB_THREADS];
+    extern __shared__ uint32_t s_dyn[];
+    __shared__ uint32_t s_static[DYN ? 1 : MID_TAB];
+    uint32_t *tab = DYN ? s_dyn : s_static;
+    __shared__ uint32_t s_pre[PB_THREADS];
+    __shared__ uint32_t s_beg[PB_THREADS];
+    __shared__ uint8_t s_cls[PB_THREADS];
     __shared__ uint32_t wt[33];
-    __shared__ unsigned long long wr[33];
+    __shared__ unsigned long long red[33];
     __shared__ uint32_t s_idx;
-    const uint32_t nl = st->nlist[1];
-    unsigned long long cl = 0, ch = 0, ws = 0, wn = 0;
+    const uint32_t b = DYN ? 2 : 1;
+    const uint32_t nitems =
+        (uint32_t)min((unsigned long long)st->nlist[b], (unsigned long long)(DYN ? cap - wm_cap : wm_cap));
+    Tally t;
     for (;;) {
-        if (threadIdx.x == 0) s_idx = atomicAdd(&st->cursor[1], 1u);
+        if (threadIdx.x == 0) s_idx = atomicAdd(&st->cursor[b], 1u);
         __syncthreads();
         const uint32_t idx = s_idx;
-        if (idx >= nl) break;
-        const uint32_t u = list[n - 1 - idx];
-        const uint32_t beg = rowptr[u], d = rowptr[u + 1] - beg;
-        const uint32_t *nu = col + beg;
-        if (d <= cap) {
-            for (uint32_t i = threadIdx.x; i < d; i += IB_THREADS) s_nu[i] = col[beg + i];
-            nu = s_nu;
+        if (idx >= nitems) break;
+        const uint64_t item = DYN ? items[wm_cap + idx] : items[wm_cap - 1 - idx];
+        const uint32_t x = (uint32_t)item, seg = (uint32_t)(item >> 32);
+        const uint32_t beg = rowptr[x], d = rowptr[x + 1] - beg;
+        const uint8_t hx = heavy[x];
+        // table size: a power of two >= 2 d; fall back to a binary search of
+        // the sorted row when it does not fit
+        uint32_t slots = 64;
+        while (slots < 2 * d && slots < (1u << 30)) slots <<= 1;
+        const bool use_tab = slots <= tab_slots && (uint64_t)slots >= 2ull * d;
+        const uint32_t shift = 32 - (31 - __clz(slots));
+        if (use_tab) {
+            for (uint32_t i = threadIdx.x; i < slots; i += PB_THREADS) tab[i] = EMPTY;
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < d; i += PB_THREADS) tab_insert(tab, slots - 1, shift, col[beg + i]);
         }
+        if (seg == 0 && threadIdx.x == 0) t.table += d;
+        const uint32_t ib = inptr[x], np = d + (inptr[x + 1] - ib);
+        const uint32_t p0 = seg * SEG, p1 = min(np, p0 + SEG);
+        const uint32_t j = p0 + threadIdx.x;
+        uint32_t start = 0, len = 0, cls = 0;
+        if (j < p1) {
+            const bool is_out = j < d;
+            const uint32_t y = is_out ? col[beg + j] : inlist[ib + j - d];
+            partner(rowptr, inlist, heavy, d, ib, hx, j, y, is_out, start, len, cls);
+        }
+        t.partners += len != 0;
+        uint32_t W;
+        const uint32_t ex = block_excl_scan(len, wt, &W);  // also orders the table build
+        s_pre[threadIdx.x] = ex;
+        s_beg[threadIdx.x] = start;
+        s_cls[threadIdx.x] = (uint8_t)cls;
         __syncthreads();
-        uint32_t c = 0;
-        for (uint32_t c0 = 0; c0 < d; c0 += IB_THREADS) {
-            const uint32_t t = c0 + threadIdx.x;
-            uint32_t vb = 0, len = 0;
-            if (t < d) {
-                const uint32_t x = nu[t];
-                vb = rowptr[x];
-                len = rowptr[x + 1] - vb;
+        for (uint32_t e = threadIdx.x; e < W; e += PB_THREADS) {
+            const uint32_t i = seg_of(s_pre, PB_THREADS, e);
+            const uint32_t y = col[s_beg[i] + (e - s_pre[i])];
+            const bool hit = use_tab ? tab_probe(tab, slots - 1, shift, y) : sorted_contains(col + beg, d, y);
+            if (hit) {
+                if (s_cls[i]) ++t.heavy; else ++t.light;
             }
-            uint32_t W;
-            const uint32_t ex = block_excl_scan(len, wt, &W);
-            wn += W;
-            s_pre[threadIdx.x] = ex;
-            s_vb[threadIdx.x] = vb;
-            __syncthreads();
-            const uint32_t cnt = min((uint32_t)IB_THREADS, d - c0);
-            for (uint32_t e = threadIdx.x; e < W; e += IB_THREADS) {
-                const uint32_t i = seg_of(s_pre, cnt, e);
-                const uint32_t y = col[s_vb[i] + (e - s_pre[i])];
-                c += contains(nu, d, y);
-            }
-            __syncthreads();
         }
-        if (heavy[u]) ch += c; else cl += c;
-        ws += d;
-        __syncthreads();  // s_idx and s_nu are rewritten by the next source
+        if (threadIdx.x == 0) t.stream += W;
+        __syncthreads();  // s_idx, the table and the chunk arrays are rewritten next
     }
-    cl = block_sum(cl, wr);
-    if (threadIdx.x == 0 && cl) atomicAdd(&st->t_light, cl);
-    ch = block_sum(ch, wr);
-    if (threadIdx.x == 0 && ch) atomicAdd(&st->t_heavy, ch);
-    // ws and wn are block-uniform: thread 0 reports them
-    if (threadIdx.x == 0 && ws) atomicAdd(&st->src_elems, ws);
-    if (threadIdx.x == 0 && wn) atomicAdd(&st->nbr_elems, wn);
+    flush_tally(t, red, st);
 }
 
-void intersect(const CountBuffers &b, int max_smem_bytes, cudaStream_t s)
+void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
 {
     if (b.n == 0 || b.m == 0) return;
-    k_isect_warp<<<152 * 8, IW_THREADS, 0, s>>>(b.rowptr, b.col, b.list, b.heavy, b.st); note_launch();
-    if (max_smem_bytes > 48 * 1024)
-        cudaFuncSetAttribute(k_isect_block, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
-    const uint32_t cap = (uint32_t)(max_smem_bytes / 4);
-    k_isect_block<<<152 * 4, IB_THREADS, (size_t)cap * 4, s>>>(b.rowptr, b.col, b.list, b.n, b.heavy, b.st,
-                                                              cap); note_launch();
+    const uint64_t wm = wm_capacity(b.n, b.m);
+    k_probe_warp<<<152 * 8, PW_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy, b.st); note_launch();
+    k_probe_block<false><<<152 * 6, PB_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy,
+                                                         b.st, MID_TAB, b.items_cap); note_launch();
+    if (dyn_smem_bytes > 48 * 1024)
+        cudaFuncSetAttribute(k_probe_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_bytes);
+    k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm,
+                                                                b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
+                                                                b.items_cap); note_launch();
 }
 
 // ======================================================================
@@ -357,6 +485,7 @@ __global__ void k_finalize(const DevState *st, uint64_t m, uint32_t n, double p,
     out->estimate = __dadd_rn(__ddiv_rn((double)st->t_light, p3), __ddiv_rn((double)st->t_heavy, p3));
     out->src_elems = st->src_elems;
     out->nbr_elems = st->nbr_elems;
+    out->partners = st->partners;
     for (int i = 0; i < 8; ++i) out->ms[i] = 0.0f;
 }
 

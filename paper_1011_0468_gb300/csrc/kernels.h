@@ -39,15 +39,28 @@ struct ItemSource {
     uint64_t seed_mix, thr;             // SAMPLE_ORIENT: keep test
 };
 
+// Optional by-product of a radix pass over oriented edges (src << 32 | dst):
+// the in-lists of the pairs whose source has the strictly smaller
+// out-degree, grouped by dst.  dplus holds the complete out-degree counts.
+// P has n + 2 entries and must be zero on entry; afterwards the in-list of
+// vertex v is inlist[P[v] .. P[v + 1]) (in no particular order).
+struct InListArgs {
+    const uint32_t *dplus;
+    uint32_t *P;
+    uint32_t *inlist;
+    uint32_t n;
+};
+
 // One stable LSD radix pass over 64-bit items on bits [shift, shift+width),
 // width <= 8.  Tiles of RX_TILE items; hist holds (1 << width) * ntiles
 // uint32 (digit-major), ntiles = ceil(n_max / RX_TILE).  If dplus is
 // non-NULL the count kernel also histograms (item >> 32) into it.  The
 // scatter writes the full items to out, or when out_low32 is non-NULL only
-// their low 32 bits there.
+// their low 32 bits there.  With `in` non-NULL the pass also builds the
+// in-lists described above.
 void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
                 uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
-                cudaStream_t s);
+                const InListArgs *in, cudaStream_t s);
 
 // Canonical keys from raw pairs: (min << 32 | max), self-loops become
 // ~0ull; endpoints >= n raise ERR_ENDPOINT; pairs that are not strictly
@@ -68,8 +81,11 @@ struct CountBuffers {
     uint32_t *deg;          // [n]
     uint8_t *heavy;         // [n]
     uint32_t *rowptr;       // [n + 1]
-    uint32_t *col;          // [m]
-    uint32_t *list;         // [n] source buckets
+    uint32_t *col;          // [m_p] CSR columns
+    uint32_t *inptr;        // [n + 2] in-list offsets
+    uint32_t *inlist;       // in-lists
+    uint64_t *items;        // owner work items [items_cap]
+    uint64_t items_cap;
     DevState *st;
 };
 
@@ -77,8 +93,11 @@ void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaS
 void partition(const CountBuffers &b, cudaStream_t s);
 void compact_kept(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out,
                   uint32_t *tile_cnt, uint32_t *scan_scratch, cudaStream_t s);
-void build_buckets(const CountBuffers &b, cudaStream_t s);
-void intersect(const CountBuffers &b, int max_smem_bytes, cudaStream_t s);
+// Capacity (entries) of the owner work-item array for a graph of n, m.
+uint64_t items_capacity(uint32_t n, uint64_t m);
+void build_items(const CountBuffers &b, cudaStream_t s);
+// dyn_smem_bytes: shared memory of the hash table for owners with d+ > 1024
+void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s);
 void finalize(const CountBuffers &b, double p, tc_result *out_dev, cudaStream_t s);
 
 }  // namespace tcg

@@ -98,9 +98,16 @@ __device__ __forceinline__ bool load_item(const ItemSource &src, uint64_t i, uin
     return true;
 }
 
+// The in-list by-product: pair (src -> dst) belongs to dst's in-list iff
+// d+(src) < d+(dst).
+__device__ __forceinline__ bool in_pair(const InListArgs &in, uint64_t item)
+{
+    return __ldg(in.dplus + (item >> 32)) < __ldg(in.dplus + (uint32_t)item);
+}
+
 __global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int shift, int width,
                                                             uint32_t *__restrict__ hist, uint32_t ntiles,
-                                                            uint32_t *__restrict__ dplus)
+                                                            uint32_t *__restrict__ dplus, InListArgs in)
 {
     __shared__ uint32_t cnt[RX_BINS];
     const uint64_t n = src.n_dev ? *src.n_dev : src.n_host;
@@ -120,6 +127,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int 
             if (valid) {
                 if (lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
                 if (dplus) atomicAdd(dplus + (item >> 32), 1u);
+                if (in.P && in_pair(in, item)) atomicAdd(in.P + (uint32_t)item + 1, 1u);
             }
         }
     }
@@ -130,7 +138,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int 
 __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, int shift, int width,
                                                               const uint32_t *__restrict__ offs, uint32_t ntiles,
                                                               uint64_t *__restrict__ out,
-                                                              uint32_t *__restrict__ out_low32)
+                                                              uint32_t *__restrict__ out_low32, InListArgs in)
 {
     constexpr int NW = RX_THREADS / 32;
     __shared__ uint32_t whist[NW][RX_BINS];
@@ -184,19 +192,26 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
             out_low32[pos] = (uint32_t)items[j];
         else
             out[pos] = items[j];
+        if (in.P && in_pair(in, items[j])) {
+            const uint32_t q = atomicAdd(in.P + (uint32_t)items[j] + 1, 1u);
+            in.inlist[q] = (uint32_t)(items[j] >> 32);
+        }
     }
 }
 
 void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
                 uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
-                cudaStream_t s)
+                const InListArgs *in, cudaStream_t s)
 {
+    const InListArgs inl = in ? *in : InListArgs{nullptr, nullptr, nullptr, 0};
     const uint64_t ntiles = ceil_div(n_max, RX_TILE);
     if (ntiles == 0) return;
-    k_radix_count<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, dplus); note_launch();
+    k_radix_count<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, dplus, inl); note_launch();
     scan_excl_u32(hist, ntiles << width, nullptr, scan_scratch, s);
+    // in-list offsets: P[1 .. n+1] = exclusive scan of the counts, P[0] = 0
+    if (inl.P) scan_excl_u32(inl.P + 1, (uint64_t)inl.n + 1, nullptr, scan_scratch, s);
     k_radix_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, out,
-                                                            out_low32); note_launch();
+                                                            out_low32, inl); note_launch();
 }
 
 // ======================================================================

@@ -1,0 +1,98 @@
+"""Full-size parity on the benchmark workload (Chung-Lu, n = 2^22, m = 2^26,
+gamma 2.1, max expected degree 1e5, seed 1), in the launch configuration
+bench.py times.  Expected values come from tests/golden/chung_lu_4m.json,
+written by tests/golden/make_golden.py from the CPU oracle (the p = 1 run
+takes minutes single-threaded, so it is stored rather than recomputed).
+At p = 0.01 the oracle is fast enough to also re-run here.
+"""
+import importlib.util
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden", "chung_lu_4m.json")
+
+
+def _make_golden():
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(HERE, "golden", "make_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.fixture(scope="module")
+def workload():
+    mg = _make_golden()
+    rec = json.load(open(GOLDEN))
+    s = rec["spec"]
+    edges = gen.cached("chung_lu", gen.chung_lu, s["n"], s["m"], s["gamma"], s["wmax"], s["seed"])
+    assert len(edges) == rec["m"]
+    assert mg.checksum(edges) == rec["checksum"], "generator output differs from the stored workload"
+    return rec, edges
+
+
+@pytest.fixture(scope="module")
+def graph(workload):
+    from paper_1011_0468_gb300 import _build, tc
+    _build.build()
+    rec, edges = workload
+    g = tc.Graph(edges, rec["spec"]["n"])
+    yield g
+    g.close()
+
+
+def test_stored_oracle_results(workload, graph):
+    rec, _ = workload
+    assert graph.m == rec["m"]
+    for r in rec["runs"]:
+        got = graph.count(r["p"], r["seed"])
+        for k in ("m_sampled", "n_heavy", "t_light", "t_heavy"):
+            assert got[k] == r[k], (r["p"], r["seed"], k, got[k], r[k])
+        assert got["estimate"] == float.fromhex(r["estimate_hex"])
+
+
+def test_oracle_rerun_at_small_p(workload, graph):
+    rec, edges = workload
+    n = rec["spec"]["n"]
+    want = oracle.run(edges, n, 0.01, 77, want_sample=True)
+    got = graph.count(0.01, 77)
+    for k in ("m_sampled", "n_heavy", "t_light", "t_heavy", "estimate"):
+        assert got[k] == want[k], k
+    kept, heavy, deg = graph.export_sample(0.01, 77)
+    assert np.array_equal(kept, want["kept"])
+    assert np.array_equal(heavy, want["heavy"])
+
+
+def test_exact_degrees_and_partition_at_p1(workload, graph):
+    rec, edges = workload
+    n = rec["spec"]["n"]
+    _, heavy, deg = graph.export_sample(1.0, 1)
+    want_deg = oracle.degrees(edges, n)
+    assert np.array_equal(deg, want_deg)
+    assert np.array_equal(heavy, oracle.partition(want_deg, len(edges)))
+
+
+def test_async_sweep_matches_blocking(workload, graph):
+    """The bench's launch pattern: three asynchronous counts back to back."""
+    import ctypes
+    import torch
+    from paper_1011_0468_gb300 import tc
+    ps = [1.0, 0.1, 0.01]
+    buf = torch.zeros((3, ctypes.sizeof(tc.tc_result)), dtype=torch.uint8, pin_memory=True)
+    for j, p in enumerate(ps):
+        graph.count_async(p, 1, buf[j].data_ptr())
+    graph.sync()
+    rec, _ = workload
+    by_key = {(r["p"], r["seed"]): r for r in rec["runs"]}
+    for j, p in enumerate(ps):
+        got = tc.tc_result.from_address(buf[j].data_ptr()).as_dict()
+        want = by_key[(p, 1)]
+        assert (got["t_light"], got["t_heavy"], got["m_sampled"]) == (want["t_light"], want["t_heavy"],
+                                                                       want["m_sampled"])

@@ -67,9 +67,11 @@ def test_rmat_small(tc):
 
 
 def test_dense_core_heavy_block(tc):
-    """A dense core (many heavy vertices, large T_H) inside a sparse graph."""
-    core = gen.er(1500, 1500 * 1499 // 2 // 3, 11)  # density 1/3
-    rest = gen.er(200_000, 400_000, 12).astype(np.int64) + 1500
+    """A dense core (many heavy vertices, large T_H) inside a sparse graph.
+    Core vertices of a c-vertex core at density q have degree ~ c q and are
+    heavy when (c q)^2 > c^2 q / 2 + m_rest, which needs q > 1/2."""
+    core = gen.er(1500, 1500 * 1499 * 4 // 10, 11)  # density 0.8
+    rest = gen.er(200_000, 200_000, 12).astype(np.int64) + 1500
     e = gen.canonical(np.concatenate([core.astype(np.int64), rest,
                                       np.stack([np.arange(1500), 1500 + np.arange(1500) * 7], 1)]))
     n = 201_500
@@ -210,7 +212,6 @@ def test_csr_is_degree_oriented_and_sorted(tc):
         ds, dd = deg[src].astype(np.int64), deg[dst].astype(np.int64)
         assert np.all((ds < dd) | ((ds == dd) & (src < dst)))
         # the undirected edge set is exactly the kept set
-        und = np.sort(np.stack([np.minimum(src, dst), np.maximum(src, dst)], 1), axis=0)
-        keys = und[:, 0] * (1 << 32) + und[:, 1]
+        keys = np.minimum(src, dst) * (1 << 32) + np.maximum(src, dst)
         kk = kept.astype(np.int64)
         assert np.array_equal(np.sort(keys), kk[:, 0] * (1 << 32) + kk[:, 1])
