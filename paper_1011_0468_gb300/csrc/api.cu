@@ -413,13 +413,13 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
         g->ekey = (uint64_t *)g->alloc(8);
         if (!g->ekey) { free_graph(g); return TC_ENOMEM; }
     }
-    // hash table of the owners with d+ > 1024: every out-degree of the
-    // degree-oriented graph is at most sqrt(2 m_p); a table of >= 2 d+ slots
+    // hash set of the owners with d+ > 1024: every out-degree of the
+    // degree-oriented graph is at most sqrt(2 m_p); a set of >= 4 d+ slots
     // up to 32768 slots (128 KiB) stays on chip, larger rows are searched in
     // place
     const uint64_t dmax = (uint64_t)std::sqrt(2.0 * (double)std::max<uint64_t>(m, 1)) + 2;
-    uint64_t slots = 4096;
-    while (slots < 2 * dmax && slots < 32768) slots <<= 1;
+    uint64_t slots = 8192;
+    while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     g->smem_bytes = (int)(slots * 4);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         free_graph(g);

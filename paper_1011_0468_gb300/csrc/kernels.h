@@ -21,6 +21,9 @@ inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 // Process-wide count of kernel launches made by the library (api.cu).
 void note_launch();
 
+// Blocks for `work` items at `threads` per block, at most `cap` (count.cu).
+unsigned grid_for(uint64_t work, int threads, unsigned cap);
+
 // Scratch (uint32 entries) needed by scan_excl_u32 for `len` elements.
 uint64_t scan_scratch_elems(uint64_t len);
 
