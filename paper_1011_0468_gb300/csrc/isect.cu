@@ -458,8 +458,9 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
     k_probe_block<false><<<152 * 8, PB_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy,
                                                          b.st, MID_TAB, b.items_cap);
     note_launch();
-    if (dyn_smem_bytes > 48 * 1024)
-        cudaFuncSetAttribute(k_probe_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_bytes);
+    // static + dynamic shared memory must fit the function's opt-in limit,
+    // which starts at 48 KiB in every process
+    cudaFuncSetAttribute(k_probe_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_bytes);
     k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm,
                                                                 b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
                                                                 b.items_cap);

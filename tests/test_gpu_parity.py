@@ -182,6 +182,25 @@ def test_async_matches_blocking(tc):
         assert got[k] == want[k]
 
 
+def test_small_graph_in_fresh_process():
+    """Per-function launch limits start at their defaults in every process:
+    a small graph counted first thing in a new process must work too."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import gen, oracle\n"
+            "from paper_1011_0468_gb300 import tc\n"
+            "e = gen.chung_lu(20000, 200000, 2.1, 3000.0, 3)\n"
+            "with tc.Graph(e, 20000) as g:\n"
+            "    r = g.count(1.0, 1)\n"
+            "w = oracle.run(e, 20000, 1.0, 1)\n"
+            "assert (r['t_light'], r['t_heavy']) == (w['t_light'], w['t_heavy'])\n" % root)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout + out.stderr
+
+
 def test_repeat_is_deterministic(tc):
     e = gen.chung_lu(100_000, 800_000, 2.1, 4000.0, 10)
     with tc.Graph(e, 100_000) as g:
