@@ -168,6 +168,32 @@ tc_status tc_graph_export_csr(tc_graph *g, double p, uint64_t seed, uint32_t *ro
 /* The canonical edge list held by the graph (2 * m uint32, sorted). */
 tc_status tc_graph_export_edges(tc_graph *g, uint32_t *pairs_host);
 
+/*
+ * Count without allocating (the paper has no counterpart: this exists for
+ * callers that cannot allocate device memory, such as a host framework
+ * whose memory pool already owns the GPU, or code where a device allocation
+ * would synchronise the device or is not permitted).  Same computation and
+ * result as tc_graph_create + tc_count + tc_graph_destroy, for graphs of at
+ * most TC_NOALLOC_MAX_EDGES input pairs and TC_NOALLOC_MAX_VERTICES
+ * vertices; larger inputs return TC_EINVAL.
+ *   edges_dev    m_in uint32 pairs in device memory of the current device
+ *                (any order, repeats and self-loops allowed, as in create).
+ *   out_host     receives the result (host memory); ms[] is zero.
+ *   cuda_stream  stream for the work (NULL = default); the call blocks
+ *                until the result is in *out_host.
+ * All scratch lives in one fixed __device__ array inside the library
+ * (about 12 MiB), held by every GPU that loads it until the process exits.
+ * The first call on a device looks up that array's device address; make
+ * this first call before any stream capture.  Calls share the array (each
+ * clears what must start at zero), so calls that overlap on the GPU race:
+ * serialise them.  Nothing is allocated: no cudaMalloc, no cudaFree, no
+ * allocator callback.
+ */
+#define TC_NOALLOC_MAX_EDGES (1ull << 18)
+#define TC_NOALLOC_MAX_VERTICES (1u << 18)
+tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, uint32_t n, double p, uint64_t seed,
+                           tc_result *out_host, void *cuda_stream);
+
 /* Static description of a status code. */
 const char *tc_status_str(tc_status s);
 

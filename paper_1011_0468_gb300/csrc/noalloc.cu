@@ -1,0 +1,218 @@
+// tc_count_noalloc: the whole count for small graphs without any device
+// allocation.
+//
+// Some callers cannot call cudaMalloc: a host framework whose memory pool
+// already owns the device memory (a second allocator would fragment it or
+// fail), code that runs where a device allocation would synchronise the GPU
+// or is simply not permitted (latency-critical loops, plugin hosts that only
+// hand out buffers).  For them this entry point keeps all its scratch in one
+// file-scope __device__ array of fixed size, which every GPU that loads the
+// library holds until the process exits.  The caller passes the edge list
+// (device memory) and receives the result in host memory.
+//
+// The array is shared by all calls: each call clears what must start at
+// zero, and calls that overlap on the GPU (different streams or host
+// threads) race on it.
+#include <mutex>
+#include <utility>
+
+#include "kernels.h"
+
+namespace {
+
+using namespace tcg;
+
+constexpr uint64_t NA_M = TC_NOALLOC_MAX_EDGES;
+constexpr uint64_t NA_N = TC_NOALLOC_MAX_VERTICES;
+constexpr uint64_t NA_ALIGN = 256;
+constexpr uint64_t na_round(uint64_t b) { return (b + NA_ALIGN - 1) / NA_ALIGN * NA_ALIGN; }
+constexpr uint64_t NA_TILES = (NA_M + RX_TILE - 1) / RX_TILE;
+constexpr uint64_t NA_HIST = NA_TILES << RX_MAX_BITS;  // uint32 entries
+constexpr uint64_t NA_SCAN = (NA_HIST > NA_N + 2 ? NA_HIST : NA_N + 2) / SC_CHUNK + 2;
+constexpr uint64_t NA_ITEMS = NA_N + 2 * NA_M / 256 + NA_M / 512 + 256;  // >= items_capacity(N, M)
+constexpr uint64_t NA_BYTES = 3 * na_round(8 * NA_M)                     // ekey, bufA, bufB
+                              + na_round(4 * NA_HIST) + na_round(4 * NA_SCAN)
+                              + 2 * na_round(4 * (NA_N + 2))             // deg, rowptr
+                              + na_round(NA_N)                           // heavy
+                              + na_round(4 * (NA_N + 2))                 // inptr
+                              + na_round(8 * NA_ITEMS) + na_round(sizeof(DevState)) + na_round(sizeof(tc_result));
+
+static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
+
+// Device address of g_na_scratch per device, looked up once per device (the
+// host-side symbol is only a stand-in, never a device address).
+std::mutex g_na_mutex;
+void *g_na_addr[64] = {};
+
+tc_status na_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return TC_ECUDA;
+        }
+        g_na_addr[dev] = p;
+    }
+    *out = g_na_addr[dev];
+    return TC_OK;
+}
+
+struct Carver {
+    unsigned char *p;
+    uint64_t used = 0;
+    template <typename T>
+    T *take(uint64_t count)
+    {
+        T *r = reinterpret_cast<T *>(p + used);
+        used += na_round(count * sizeof(T));
+        return r;
+    }
+};
+
+int na_bits(uint32_t n)
+{
+    int b = 1;
+    while (b < 32 && (1ull << b) < n) ++b;
+    return b;
+}
+
+// Digit widths of the radix passes over `bits` bits (at most 8 each, as even
+// as possible; at least two passes when asked).  Returns the pass count.
+int na_widths(int bits, bool at_least_two, int w[4])
+{
+    int P = (bits + RX_MAX_BITS - 1) / RX_MAX_BITS;
+    for (int i = 0; i < P; ++i) w[i] = bits / P + (i < bits % P ? 1 : 0);
+    if (at_least_two && P == 1) {
+        w[0] = (bits + 1) / 2;
+        w[1] = bits / 2;
+        P = 2;
+    }
+    return P;
+}
+
+}  // namespace
+
+extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, uint32_t n, double p, uint64_t seed,
+                                      tc_result *out_host, void *cuda_stream)
+{
+    if (!out_host || n == 0 || (m_in > 0 && !edges_dev) || !(p > 0.0 && p <= 1.0)) return TC_EINVAL;
+    if (m_in > NA_M || n > NA_N) return TC_EINVAL;
+    void *base = nullptr;
+    tc_status status = na_scratch(&base);
+    if (status != TC_OK) return status;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+
+    Carver c{(unsigned char *)base};
+    uint64_t *ekey = c.take<uint64_t>(NA_M);
+    uint64_t *bufA = c.take<uint64_t>(NA_M);
+    uint64_t *bufB = c.take<uint64_t>(NA_M);
+    uint32_t *hist = c.take<uint32_t>(NA_HIST);
+    uint32_t *scan = c.take<uint32_t>(NA_SCAN);
+    uint32_t *deg = c.take<uint32_t>(NA_N + 2);
+    uint32_t *rowptr = c.take<uint32_t>(NA_N + 2);
+    uint8_t *heavy = c.take<uint8_t>(NA_N);
+    uint32_t *inptr = c.take<uint32_t>(NA_N + 2);
+    uint64_t *items = c.take<uint64_t>(NA_ITEMS);
+    DevState *st = c.take<DevState>(1);
+    tc_result *res = c.take<tc_result>(1);
+    if (c.used > NA_BYTES || items_capacity(n, m_in) > NA_ITEMS) return TC_ECUDA;
+
+    // ---- canonical keys: (min, max), no self-loops or repeats, sorted
+    cudaMemsetAsync(st, 0, sizeof(DevState), s);
+    DevState hs;
+    uint64_t m = 0;
+    if (m_in > 0) {
+        canon_keys(edges_dev, m_in, n, bufA, st, s);
+        uint64_t *a = bufA, *b = bufB;
+        const int nbits = na_bits(n);
+        for (int half = 0; half < 2; ++half) {
+            int shift = half ? 32 : 0;
+            int wd[4];
+            const int np = na_widths(nbits, false, wd);
+            for (int k = 0; k < np; ++k) {
+                const int w = wd[k];
+                ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
+                radix_pass(src, m_in, shift, w, hist, scan, nullptr, b, nullptr, nullptr, s);
+                std::swap(a, b);
+                shift += w;
+            }
+        }
+        unique_keys(a, m_in, ekey, hist, scan, st, s);
+        if (cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return TC_ECUDA;
+        }
+        if (hs.err & ERR_ENDPOINT) return TC_EINVAL;
+        m = hs.m_canon;
+    }
+
+    // ---- the count (Sections 3.1-3.2), every buffer inside the array
+    const uint64_t seed_mix = splitmix64(seed), thr = (uint64_t)(p * 9007199254740992.0);
+    CountBuffers cb;
+    cb.ekey = ekey;
+    cb.m = m;
+    cb.n = n;
+    cb.deg = deg;
+    cb.heavy = heavy;
+    cb.rowptr = rowptr;
+    cb.col = nullptr;
+    cb.inptr = inptr;
+    cb.inlist = nullptr;
+    cb.items = items;
+    cb.items_cap = items_capacity(n, m);
+    cb.st = st;
+    cudaMemsetAsync(st, 0, sizeof(DevState), s);
+    cudaMemsetAsync(deg, 0, (size_t)n * 4, s);
+    sample_degree(cb, seed_mix, thr, s);
+    partition(cb, s);
+    if (m > 0) {
+        cudaMemsetAsync(rowptr, 0, ((size_t)n + 1) * 4, s);
+        cudaMemsetAsync(inptr, 0, ((size_t)n + 2) * 4, s);
+        int widths[4];
+        const int npass = na_widths(na_bits(n), true, widths);
+        uint64_t *bufs[2] = {bufA, bufB};
+        const uint64_t *in = ekey;
+        int cur = 0, shift = 32;
+        for (int k = 0; k < npass; ++k) {
+            const bool last = k + 1 == npass;
+            ItemSource src = k == 0 ? ItemSource{ItemSource::SAMPLE_ORIENT, ekey, m, nullptr, deg, seed_mix, thr}
+                                    : ItemSource{ItemSource::PLAIN, in, 0, &st->m_sampled, nullptr, 0, 0};
+            uint64_t *outb = bufs[cur];
+            InListArgs il{rowptr, inptr, nullptr, n};
+            if (last) {
+                cb.col = reinterpret_cast<uint32_t *>(outb);
+                cb.inlist = reinterpret_cast<uint32_t *>(outb) + m;
+                il.inlist = cb.inlist;
+            }
+            radix_pass(src, m, shift, widths[k], hist, scan, k == 0 ? rowptr : nullptr, last ? nullptr : outb,
+                       last ? cb.col : nullptr, last ? &il : nullptr, s);
+            in = outb;
+            cur ^= 1;
+            shift += widths[k];
+        }
+        scan_excl_u32(rowptr, (uint64_t)n + 1, nullptr, scan, s);
+        build_items(cb, s);
+        // every out-degree is at most sqrt(2 m) <= 725 here: the smallest
+        // table of the large-owner kernel (8192 slots) always suffices
+        intersect(cb, 8192 * 4, s);
+    }
+    finalize(cb, p, res, s);
+    if (cudaGetLastError() != cudaSuccess) return TC_ECUDA;  // a launch was rejected
+    if (cudaMemcpyAsync(out_host, res, sizeof(tc_result), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    if (hs.err & ERR_ENDPOINT) return TC_EINVAL;
+    if (hs.err) return TC_ECUDA;
+    return TC_OK;
+}

@@ -66,7 +66,13 @@ SIGNATURES = [
     ("tc_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tc_version", ctypes.c_int, []),
     ("tc_launch_count", ctypes.c_uint64, []),
+    ("tc_count_noalloc", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
+                                        ctypes.POINTER(tc_result), _vp]),
 ]
+
+# limits of tc_count_noalloc (include/tc.h)
+TC_NOALLOC_MAX_EDGES = 1 << 18
+TC_NOALLOC_MAX_VERTICES = 1 << 18
 
 
 def lib():
@@ -165,6 +171,19 @@ def use_torch_allocator(on: bool = True) -> None:
 
 def tc_launch_count() -> int:
     return int(lib().tc_launch_count())
+
+
+def tc_count_noalloc(edges_addr: int, m_in: int, n: int, p: float, seed: int, stream=None) -> tc_result:
+    """Count without any device allocation, for callers that cannot allocate
+    device memory (their framework's pool owns the GPU, or allocating would
+    synchronise the device).  edges_addr: device address of m_in uint32
+    pairs.  Inputs above TC_NOALLOC_MAX_EDGES / TC_NOALLOC_MAX_VERTICES raise
+    TCError(TC_EINVAL).  Uses one fixed scratch array inside the library, so
+    concurrent calls must be serialised by the caller."""
+    r = tc_result()
+    _check(lib().tc_count_noalloc(edges_addr if m_in else None, m_in, n, p, seed & 0xFFFFFFFFFFFFFFFF,
+                                  ctypes.byref(r), _stream_handle(stream)), "tc_count_noalloc")
+    return r
 
 
 # ---------------------------------------------------------------- wrapper
