@@ -62,6 +62,20 @@ def make_graph():
     return gen.cached("chung_lu", gen.chung_lu, w["n"], w["m"], w["gamma"], w["wmax"], w["graph_seed"])
 
 
+def recorded_traffic():
+    """DRAM bytes of the intersection kernels from the committed ncu capture
+    (profiles/traffic.json), or None when the kernel source has changed."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        if hashlib.sha1(src).hexdigest()[:12] != rec["source_sha1_12"]:
+            return None
+        return float(rec["dram_bytes"])
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -229,28 +243,26 @@ def our_arm(args):
     elapsed_ms = float(t.item())
     value = ws * args.steps * len(ps) * m / (elapsed_ms / 1000.0)
 
-    # ---- roofline of the dominant phase (per-count device times, live)
+    # ---- roofline of the dominant launch group: the intersection kernels
+    # (k_probe_warp + k_probe_block) of the p = 1 count, timed live per count
+    # with CUDA events on the graph's stream
     peaks, peak_src = measured_peaks()
-    ph = np.asarray(phases, dtype=np.float64) if len(phases) else np.zeros((1, 8))
-    per_leg = {}
-    for j, p in enumerate(ps):
-        rows = ph[j::len(ps)]
-        per_leg[p] = rows.mean(axis=0)
-    light_ms = float(np.mean([per_leg[p][2] for p in ps]))
-    sample_ms = float(np.mean([per_leg[p][0] for p in ps]))
-    csr_ms = float(np.mean([per_leg[p][1] for p in ps]))
-    # algorithmic bytes per count, averaged over the sweep
-    b_light = float(np.mean([4.0 * (r["src_elems"] + r["nbr_elems"]) for r in results]))
-    b_sample = 8.0 * m + 5.0 * n
-    dom = max([("light", light_ms, b_light), ("sample", sample_ms, b_sample)], key=lambda x: x[1])
-    achieved = dom[2] / (dom[1] / 1000.0) / 1e9 if dom[1] > 0 else 0.0
+    ph = np.asarray(phases, dtype=np.float64) if len(phases) else np.zeros((len(ps), 8))
+    per_leg = {p: ph[j::len(ps)].mean(axis=0) for j, p in enumerate(ps)}
+    j1 = ps.index(1.0)
+    t_isect = float(per_leg[1.0][2]) / 1000.0
+    b_isect = 4.0 * (results[j1]["src_elems"] + results[j1]["nbr_elems"])
+    achieved = b_isect / t_isect / 1e9 if t_isect > 0 else 0.0
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    roofline = {"bound": "hbm", "kernel": {"light": "k_isect_warp+k_isect_block",
-                                            "sample": "k_sample_degree+k_partition"}[dom[0]],
+    traffic = recorded_traffic()
+    roofline = {"bound": "hbm", "kernel": "k_probe_warp+k_probe_block (p=1 count)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": None,
-                "phase_ms": {"sample": sample_ms, "csr": csr_ms, "light": light_ms},
-                "algorithmic_bytes_per_launch": dom[2]}
+                "peak_source": peak_src, "traffic": traffic,
+                "algorithmic_bytes_per_launch": b_isect, "launch_ms": t_isect * 1000.0,
+                "phase_ms": {str(p): {"sample": float(per_leg[p][0]), "csr": float(per_leg[p][1]),
+                                      "intersect": float(per_leg[p][2])} for p in ps}}
+    if traffic:
+        roofline["traffic_gbs"] = traffic / t_isect / 1e9
 
     # ---- end to end through the C ABI from pinned host memory
     e2e_steps = max(1, min(5, args.steps))
