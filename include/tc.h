@@ -75,6 +75,7 @@ typedef struct {
     uint64_t src_elems; /* list elements loaded into hash sets */
     uint64_t nbr_elems; /* list elements streamed through them */
     uint64_t partners;  /* oriented pairs resolved */
+    uint64_t heavy_mma_flops; /* tensor-core flops of the dense heavy block (0 when not used) */
     float ms[8];
 } tc_result;
 

@@ -86,6 +86,7 @@ struct tc_graph {
     uint64_t items_cap = 0;
     uint32_t *hist = nullptr;   // [RX_BINS * ntiles(m)]
     uint32_t *scan = nullptr;   // scan scratch
+    HeavyBuffers hb;            // dense heavy block (hb.hcap == 0: not used)
     DevState *st = nullptr;
     tc_result *res_dev = nullptr;
     // pinned host
@@ -251,11 +252,13 @@ tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bo
     if (g->m > 0) {
         enqueue_csr(g, seed_mix, thr);
         b = buffers_of(g);
+        heavy_prepare(b, g->hb, g->stream);
         build_items(b, g->stream);
     }
     record(g, timing, 2);
     if (g->m > 0) intersect(b, g->smem_bytes, g->stream);
     record(g, timing, 3);
+    if (g->m > 0 && g->hb.hcap) heavy_contract(b, g->hb, g->stream);
     record(g, timing, 4);
     finalize(b, p, g->res_dev, g->stream);
     record(g, timing, 5);
@@ -421,6 +424,29 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     uint64_t slots = 8192;
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     g->smem_bytes = (int)(slots * 4);
+    // dense heavy block: at most 2 m^(1/2) heavy vertices, padded to the
+    // 128-row tile and capped at 32768 (2 x 2 GiB of bf16); without room for
+    // it the intersection kernels count the heavy class instead
+    if (m > 0) {
+        const uint64_t hbound = (uint64_t)(2.0 * std::sqrt((double)m)) + 2;
+        const uint64_t hcap = std::min<uint64_t>((hbound + 127) / 128 * 128, 32768);
+        g->hb.hlist_cap = (uint32_t)hbound;
+        g->hb.hlist = (uint32_t *)g->alloc(hbound * 4);
+        g->hb.hidx = (uint32_t *)g->alloc((uint64_t)n * 4);
+        if (!g->hb.hlist || !g->hb.hidx) {
+            free_graph(g);
+            return TC_ENOMEM;
+        }
+        g->hb.U = (uint16_t *)g->alloc(hcap * hcap * 2);
+        g->hb.UT = g->hb.U ? (uint16_t *)g->alloc(hcap * hcap * 2) : nullptr;
+        g->hb.hcap = (uint32_t)hcap;
+        if (!g->hb.U || !g->hb.UT || !heavy_make_maps(g->hb)) {
+            if (g->hb.U) g->release(g->hb.U);
+            if (g->hb.UT) g->release(g->hb.UT);
+            g->hb.U = g->hb.UT = nullptr;
+            g->hb.hcap = 0;
+        }
+    }
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         free_graph(g);
         return TC_ECUDA;

@@ -31,6 +31,9 @@ struct DevState {
     unsigned long long src_elems;  // sum of d+(u) over intersected sources
     unsigned long long nbr_elems;  // list elements streamed through the tables
     unsigned long long partners;   // (owner, partner) pairs processed
+    unsigned long long heavy_kchunks;  // 64-wide K chunks multiplied by the heavy contraction
+    unsigned int dense;            // 1: the heavy class is counted by the dense tensor path
+    unsigned int h_listed;         // heavy vertices listed for the dense path
     unsigned long long m_canon;    // canonical edges (create only)
     unsigned int unsorted;         // create: adjacent pairs out of order
     unsigned int pad;

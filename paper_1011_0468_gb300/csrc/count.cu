@@ -147,6 +147,7 @@ __global__ void k_finalize(const DevState *st, uint64_t m, uint32_t n, double p,
     out->src_elems = st->src_elems;
     out->nbr_elems = st->nbr_elems;
     out->partners = st->partners;
+    out->heavy_mma_flops = st->heavy_kchunks * 2ull * 128ull * 128ull * 64ull;
     for (int i = 0; i < 8; ++i) out->ms[i] = 0.0f;
 }
 

@@ -1,0 +1,441 @@
+// The heavy class on the tensor cores.
+//
+// Heavy vertices (deg_p^2 > m_p, Section 3.2) number at most 2 m_p^(1/2).
+// Ordered by rank (deg_p, id) they give a strictly upper-triangular 0/1
+// matrix U, U[i][k] = 1 for every kept edge i -> k between heavy vertices
+// (every out-neighbour of a heavy vertex is heavy).  Each all-heavy triangle
+// a < b < c (in rank) is exactly one term of
+//     T_H = sum_{i < k} U[i][k] * (U U)[i][k],
+// the matrix-product route of Alon, Yuster and Zwick that the paper builds
+// on.  U and U^T are packed as bf16 0/1 matrices and the product runs on
+// tcgen05 (kind::f16, FP32 accumulation in tensor memory), exact because
+// every partial sum is an integer no larger than h < 2^24.  Only output
+// tiles on or above the diagonal, and only the j-tiles between them, are
+// multiplied; the epilogue masks D = U U with U and sums.
+//
+// sm_103a has no INT8 tcgen05 MMA (.kind::i8 is rejected for this target),
+// hence bf16 operands.
+#include <cuda.h>
+
+#include "kernels.h"
+
+namespace tcg {
+
+// ======================================================================
+// Ranking and packing
+// ======================================================================
+
+__global__ void k_heavy_list(const uint8_t *__restrict__ heavy, uint32_t n, uint32_t *__restrict__ hlist,
+                             uint32_t hlist_cap, DevState *st)
+{
+    const unsigned lane = lane_id();
+    const uint64_t wstride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += wstride) {
+        const uint64_t u = base + lane;
+        const bool f = u < n && heavy[u];
+        const unsigned mask = __ballot_sync(FULL, f);
+        uint32_t off = 0;
+        if (lane == 0 && mask) off = atomicAdd(&st->h_listed, (unsigned)__popc(mask));
+        off = __shfl_sync(FULL, off, 0);
+        if (f) {
+            const uint32_t pos = off + __popc(mask & lanemask_lt());
+            if (pos < hlist_cap) hlist[pos] = (uint32_t)u;
+        }
+    }
+}
+
+constexpr int HR_THREADS = 256;
+
+// Dense index of each heavy vertex = its rank by (deg_p, id) among the heavy
+// vertices (O(h^2) comparisons, h <= 2 m_p^(1/2)).  Also decides whether the
+// dense path runs: 2 <= h <= hcap.
+__global__ void __launch_bounds__(HR_THREADS) k_heavy_rank(const uint32_t *__restrict__ deg,
+                                                           const uint32_t *__restrict__ hlist,
+                                                           uint32_t *__restrict__ hidx, uint32_t hcap,
+                                                           uint32_t hlist_cap, DevState *st)
+{
+    __shared__ unsigned long long s_key[HR_THREADS];
+    const uint32_t h = st->n_heavy;
+    const bool dense = h >= 2 && h <= hcap && h <= hlist_cap && st->h_listed == h;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->dense = dense ? 1u : 0u;
+    if (!dense || blockIdx.x * HR_THREADS >= h) return;  // uniform per block
+    const uint32_t i = blockIdx.x * HR_THREADS + threadIdx.x;
+    unsigned long long mine = ~0ull;
+    uint32_t v = 0;
+    if (i < h) {
+        v = hlist[i];
+        mine = ((unsigned long long)deg[v] << 32) | v;
+    }
+    uint32_t rank = 0;
+    for (uint32_t j0 = 0; j0 < h; j0 += HR_THREADS) {
+        const uint32_t j = j0 + threadIdx.x;
+        s_key[threadIdx.x] = j < h ? ((unsigned long long)deg[hlist[j]] << 32) | hlist[j] : ~0ull;
+        __syncthreads();
+        const uint32_t cnt = min((uint32_t)HR_THREADS, h - j0);
+        for (uint32_t q = 0; q < cnt; ++q) rank += s_key[q] < mine;
+        __syncthreads();
+    }
+    if (i < h) hidx[v] = rank;
+}
+
+// Zero the used corner [0, hp) x [0, hp) of U and U^T, hp = h rounded up to 128.
+__global__ void k_heavy_clear(uint16_t *__restrict__ U, uint16_t *__restrict__ UT, uint32_t hcap, DevState *st)
+{
+    if (!st->dense) return;
+    const uint32_t hp = (st->n_heavy + 127) & ~127u;
+    const uint64_t per_row = hp / 8;  // uint4 per row
+    const uint64_t total = (uint64_t)hp * per_row;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const uint64_t r = t / per_row, c = t % per_row;
+        reinterpret_cast<uint4 *>(U + r * hcap)[c] = make_uint4(0, 0, 0, 0);
+        reinterpret_cast<uint4 *>(UT + r * hcap)[c] = make_uint4(0, 0, 0, 0);
+    }
+}
+
+// One warp per heavy source: U[rank(v)][rank(w)] = U^T[rank(w)][rank(v)] = 1
+// for every out-neighbour w.
+__global__ void k_heavy_pack(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+                             const uint8_t *__restrict__ heavy, const uint32_t *__restrict__ hlist,
+                             const uint32_t *__restrict__ hidx, uint16_t *__restrict__ U, uint16_t *__restrict__ UT,
+                             uint32_t hcap, DevState *st)
+{
+    if (!st->dense) return;
+    const uint32_t h = st->n_heavy;
+    const unsigned lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    constexpr uint16_t ONE = 0x3f80;  // bf16 1.0
+    for (uint32_t i = gw; i < h; i += nw) {
+        const uint32_t v = hlist[i], r = hidx[v];
+        const uint32_t b = rowptr[v], e = rowptr[v + 1];
+        for (uint32_t q = b + lane; q < e; q += 32) {
+            const uint32_t w = col[q];
+            if (!heavy[w]) {  // cannot happen: heavy vertices point to heavy vertices
+                atomicOr(&st->err, ERR_OVERFLOW);
+                continue;
+            }
+            const uint32_t c = hidx[w];
+            if (r >= hcap || c >= hcap) continue;
+            U[(uint64_t)r * hcap + c] = ONE;
+            UT[(uint64_t)c * hcap + r] = ONE;
+        }
+    }
+}
+
+// ======================================================================
+// tcgen05 contraction
+// ======================================================================
+
+constexpr int TC_THREADS = 128;  // 4 warps: TMA producer (warp 0), MMA issuer (warp 1), all 4 epilogue
+constexpr int TC_STAGES = 4;
+constexpr uint32_t TC_TILE = 128;                        // M = N = 128
+constexpr uint32_t TC_KC = 64;                           // bf16 elements per K chunk = one 128-B row
+constexpr uint32_t TC_TILE_BYTES = TC_TILE * TC_KC * 2;  // 16 KiB per operand tile
+constexpr uint32_t TC_STAGE_BYTES = 2 * TC_TILE_BYTES;
+constexpr uint32_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;  // + alignment slack
+constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // bounded waits: 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait until the phase of the given parity has completed; false after
+// TC_WAIT_NS without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > TC_WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored with the
+// 128-byte swizzle (rows of 128 B, 8-row groups 1024 B apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3fffu);  // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8-row groups
+    d |= (uint64_t)1 << 46;                   // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D f32, A and B bf16, both K-major, M = N = 128.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((TC_TILE >> 3) << 17) | ((TC_TILE >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Output tile t (heaviest first): tiles with K - I = o, o from T-1 down to 0.
+__device__ __forceinline__ void tile_of(uint32_t t, uint32_t T, uint32_t &I, uint32_t &K)
+{
+    uint32_t o = T - 1;
+    for (;;) {
+        const uint32_t cnt = T - o;  // tiles on this diagonal
+        if (t < cnt || o == 0) break;
+        t -= cnt;
+        --o;
+    }
+    I = t;
+    K = t + o;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constant__ CUtensorMap mapA,
+                                                            const __grid_constant__ CUtensorMap mapB,
+                                                            const uint16_t *__restrict__ U, uint32_t hcap,
+                                                            DevState *st)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+    __shared__ uint32_t s_tmem, s_tile, s_abort;
+    __shared__ unsigned long long s_sum[4];
+    if (!st->dense) return;  // uniform: written before this launch
+    const uint32_t h = st->n_heavy;
+    const uint32_t T = (h + TC_TILE - 1) / TC_TILE, ntiles = T * (T + 1) / 2;
+    const unsigned warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "n"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+
+    uint32_t it_prod = 0, it_mma = 0, tiles_done = 0;
+    unsigned long long flops_k = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&st->cursor[3], 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= ntiles || s_abort) break;
+        uint32_t I, K;
+        tile_of(t, T, I, K);
+        const uint32_t c0 = I * (TC_TILE / TC_KC), c1 = (K + 1) * (TC_TILE / TC_KC);  // j chunks [c0, c1)
+        if (warp == 0 && lane == 0) {
+            // TMA producer
+            for (uint32_t c = c0; c < c1; ++c, ++it_prod) {
+                const uint32_t s = it_prod % TC_STAGES, ph = (it_prod / TC_STAGES) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u)) {
+                    atomicOr(&st->err, ERR_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+                const uint32_t a = base + s * TC_STAGE_BYTES;
+                tma_load_2d(a, &mapA, &full[s], (int)(c * TC_KC), (int)(I * TC_TILE));
+                tma_load_2d(a + TC_TILE_BYTES, &mapB, &full[s], (int)(c * TC_KC), (int)(K * TC_TILE));
+            }
+        } else if (warp == 1 && lane == 0) {
+            // MMA issuer
+            for (uint32_t c = c0; c < c1; ++c, ++it_mma) {
+                const uint32_t s = it_mma % TC_STAGES, ph = (it_mma / TC_STAGES) & 1u;
+                if (!mbar_wait(&full[s], ph)) {
+                    atomicOr(&st->err, ERR_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a = base + s * TC_STAGE_BYTES;
+                const uint64_t da = sw128_desc(a), db = sw128_desc(a + TC_TILE_BYTES);
+#pragma unroll
+                for (uint32_t kk = 0; kk < TC_KC / 16; ++kk)  // 16 bf16 = 32 B per MMA
+                    mma_bf16(tmem, da + 2 * kk, db + 2 * kk, (c > c0 || kk > 0) ? 1u : 0u);
+                mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+            }
+            mma_commit(&done);  // accumulator complete
+            flops_k += c1 - c0;
+        }
+        __syncwarp();
+        // epilogue: rows 32 w .. 32 w + 31 of the tile, D masked by U
+        const bool ok = mbar_wait(&done, tiles_done & 1u);
+        if (!ok) {
+            if (lane == 0) atomicOr(&st->err, ERR_TIMEOUT);
+            s_abort = 1;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned long long sum = 0;
+        if (__all_sync(FULL, ok)) {
+            const uint32_t row = I * TC_TILE + warp * 32 + lane;
+            const uint16_t *urow = U + (uint64_t)row * hcap + (uint64_t)K * TC_TILE;
+#pragma unroll 1
+            for (uint32_t q = 0; q < TC_TILE / 32; ++q) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((warp * 32u) << 16) + q * 32, r);
+                const uint4 *m4 = reinterpret_cast<const uint4 *>(urow + q * 32);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const uint4 mv = m4[v];
+                    const uint32_t w[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const uint32_t bits = (w[e >> 1] >> ((e & 1) * 16)) & 0xffffu;
+                        if (bits) sum += (uint32_t)__uint_as_float(r[v * 8 + e]);
+                    }
+                }
+            }
+        }
+        sum = warp_sum(sum);
+        if (lane == 0) s_sum[warp] = sum;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // TMEM is read: the next tile may overwrite it
+        if (threadIdx.x == 0) {
+            const unsigned long long tot = s_sum[0] + s_sum[1] + s_sum[2] + s_sum[3];
+            if (tot) atomicAdd(&st->t_heavy, tot);
+        }
+        ++tiles_done;
+    }
+    if (warp == 1 && lane == 0 && flops_k) atomicAdd(&st->heavy_kchunks, flops_k);
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ======================================================================
+// Host side
+// ======================================================================
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+bool heavy_make_maps(HeavyBuffers &hb)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || !hb.U || !hb.UT || hb.hcap == 0) return false;
+    const cuuint64_t dims[2] = {hb.hcap, hb.hcap};
+    const cuuint64_t strides[1] = {(cuuint64_t)hb.hcap * 2};
+    const cuuint32_t box[2] = {TC_KC, TC_TILE};
+    const cuuint32_t estr[2] = {1, 1};
+    CUtensorMap *maps[2] = {reinterpret_cast<CUtensorMap *>(hb.mapA), reinterpret_cast<CUtensorMap *>(hb.mapB)};
+    void *bufs[2] = {hb.U, hb.UT};
+    for (int i = 0; i < 2; ++i) {
+        if (enc(maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bufs[i], dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s)
+{
+    k_heavy_list<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.heavy, b.n, hb.hlist, hb.hlist_cap, b.st);
+    note_launch();
+    k_heavy_rank<<<(unsigned)ceil_div(hb.hlist_cap, HR_THREADS), HR_THREADS, 0, s>>>(b.deg, hb.hlist, hb.hidx,
+                                                                                   hb.hcap, hb.hlist_cap, b.st);
+    note_launch();
+    k_heavy_clear<<<152 * 8, 256, 0, s>>>(hb.U, hb.UT, hb.hcap, b.st);
+    note_launch();
+    k_heavy_pack<<<152 * 4, 256, 0, s>>>(b.rowptr, b.col, b.heavy, hb.hlist, hb.hidx, hb.U, hb.UT, hb.hcap, b.st);
+    note_launch();
+}
+
+void heavy_contract(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s)
+{
+    cudaFuncSetAttribute(k_heavy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    const CUtensorMap *ma = reinterpret_cast<const CUtensorMap *>(hb.mapA);
+    const CUtensorMap *mb = reinterpret_cast<const CUtensorMap *>(hb.mapB);
+    k_heavy_tc<<<152, TC_THREADS, TC_SMEM, s>>>(*ma, *mb, hb.U, hb.hcap, b.st);
+    note_launch();
+}
+
+}  // namespace tcg

@@ -147,11 +147,12 @@ __device__ __forceinline__ void flush_tally(const Tally &t, unsigned long long *
 }
 
 // Partner y of owner x: where its out-list starts, how many elements to
-// stream (0 when the pair is resolved by the other endpoint or closes no
-// triangle) and the class of the pair's triangles.
+// stream (0 when the pair is resolved by the other endpoint, closes no
+// triangle, or is heavy-class while the dense tensor path counts that class)
+// and the class of the pair's triangles.
 __device__ __forceinline__ void partner_of(const uint32_t *__restrict__ rowptr, const uint8_t *__restrict__ heavy,
-                                           uint32_t d, uint8_t hx, uint32_t y, bool is_out, uint32_t &start,
-                                           uint32_t &len, uint32_t &cls)
+                                           uint32_t d, uint8_t hx, uint32_t y, bool is_out, bool skip_heavy,
+                                           uint32_t &start, uint32_t &len, uint32_t &cls)
 {
     const uint32_t yb = rowptr[y], dy = rowptr[y + 1] - yb;
     start = yb;
@@ -162,6 +163,7 @@ __device__ __forceinline__ void partner_of(const uint32_t *__restrict__ rowptr, 
         len = dy >= 2 ? dy : 0u;
         cls = len ? heavy[y] : 0u;
     }
+    if (cls && skip_heavy) len = 0;  // the dense tensor path counts this class
 }
 
 // Streams the out-lists of up to 32 partners (one per lane: start, len, cls)
@@ -272,6 +274,7 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
     __shared__ unsigned long long red[33];
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     const uint32_t nitems = (uint32_t)min((unsigned long long)st->nlist[0], (unsigned long long)wm_cap);
+    const bool skip_heavy = st->dense != 0;
     uint32_t *tab = s_tab[w];
     Tally t;
     for (;;) {
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
                 if (j < p1) {
                     const bool is_out = j < d;
                     const uint32_t y = is_out ? __ldg(col + beg + j) : __ldg(inlist + ib + j - d);
-                    partner_of(rowptr, heavy, d, hx, y, is_out, start, len, cls);
+                    partner_of(rowptr, heavy, d, hx, y, is_out, skip_heavy, start, len, cls);
                 }
                 stream_partners(col, set, start, len, cls, s_beg[w], s_pre[w], t);
             }
@@ -354,6 +357,7 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_probe_block(const uint32_t *_
     const uint32_t b = DYN ? 2 : 1;
     const uint32_t nitems =
         (uint32_t)min((unsigned long long)st->nlist[b], (unsigned long long)(DYN ? cap - wm_cap : wm_cap));
+    const bool skip_heavy = st->dense != 0;
     Tally t;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_probe_block(const uint32_t *_
             if (j < p1) {
                 const bool is_out = j < d;
                 const uint32_t y = is_out ? __ldg(col + beg + j) : __ldg(inlist + ib + j - d);
-                partner_of(rowptr, heavy, d, hx, y, is_out, pstart[q], plen[q], pcls[q]);
+                partner_of(rowptr, heavy, d, hx, y, is_out, skip_heavy, pstart[q], plen[q], pcls[q]);
             }
             if (plen[q]) {
                 mine += plen[q] >= LONG_LIST ? (1u << 16) : 1u;

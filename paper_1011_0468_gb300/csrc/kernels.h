@@ -103,4 +103,26 @@ void build_items(const CountBuffers &b, cudaStream_t s);
 void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s);
 void finalize(const CountBuffers &b, double p, tc_result *out_dev, cudaStream_t s);
 
+// ---------------------------------------------------------------- heavy.cu
+// Dense heavy block: U and U^T (hcap x hcap bf16, row stride hcap), the
+// heavy vertex list and each heavy vertex's dense index, and the TMA
+// descriptors of U and U^T (CUtensorMap storage).  hcap == 0 disables the
+// dense path (the intersection kernels then count the heavy class).
+struct HeavyBuffers {
+    uint16_t *U = nullptr;
+    uint16_t *UT = nullptr;
+    uint32_t hcap = 0;
+    uint32_t *hlist = nullptr;
+    uint32_t hlist_cap = 0;
+    uint32_t *hidx = nullptr;  // [n]
+    alignas(64) unsigned char mapA[128];
+    alignas(64) unsigned char mapB[128];
+};
+
+bool heavy_make_maps(HeavyBuffers &hb);
+// after the CSR: list, rank and pack the heavy vertices; sets DevState::dense
+void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s);
+// T_H += sum_{i<k} U_ik (U U)_ik on tcgen05 (no-op unless DevState::dense)
+void heavy_contract(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s);
+
 }  // namespace tcg

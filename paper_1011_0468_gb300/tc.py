@@ -32,7 +32,7 @@ class tc_result(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint64), ("m_sampled", ctypes.c_uint64), ("n", ctypes.c_uint32),
                 ("n_heavy", ctypes.c_uint32), ("t_light", ctypes.c_uint64), ("t_heavy", ctypes.c_uint64),
                 ("estimate", ctypes.c_double), ("src_elems", ctypes.c_uint64), ("nbr_elems", ctypes.c_uint64),
-                ("partners", ctypes.c_uint64), ("ms", ctypes.c_float * 8)]
+                ("partners", ctypes.c_uint64), ("heavy_mma_flops", ctypes.c_uint64), ("ms", ctypes.c_float * 8)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms"}

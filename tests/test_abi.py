@@ -66,5 +66,5 @@ def test_argument_errors_without_device(lib):
 def test_result_struct_layout():
     from paper_1011_0468_gb300 import tc
     # uint64 m, m_sampled; uint32 n, n_heavy; uint64 t_light, t_heavy; double;
-    # uint64 src_elems, nbr_elems, partners; float[8]
-    assert ctypes.sizeof(tc.tc_result) == 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 + 8 + 8 + 32
+    # uint64 src_elems, nbr_elems, partners, heavy_mma_flops; float[8]
+    assert ctypes.sizeof(tc.tc_result) == 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 32

@@ -78,6 +78,8 @@ def test_dense_core_heavy_block(tc):
     r = oracle.run(e, n, 1.0, 1)
     assert r["n_heavy"] > 100 and r["t_heavy"] > 0
     check_graph(tc, e, n, [(1.0, 1), (0.7, 2)], sample=False)
+    with tc.Graph(e, n) as g:
+        assert g.count(1.0, 1)["heavy_mma_flops"] > 0  # the tensor-core path ran
 
 
 # ------------------------------------------------------------ closed forms
