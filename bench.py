@@ -33,8 +33,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = {"workload": "chung_lu_n4M_m64M_gamma2.1", "n": 1 << 22, "m": 1 << 26, "gamma": 2.1,
-            "wmax": 1e5, "graph_seed": 1, "p_sweep": [1.0, 0.1, 0.01]}
+WORKLOADS = {
+    # the headline workload: power-law graph shaped like the paper's social networks
+    "chung_lu": {"workload": "chung_lu_n4M_m64M_gamma2.1", "kind": "chung_lu", "n": 1 << 22, "m": 1 << 26,
+                 "gamma": 2.1, "wmax": 1e5, "graph_seed": 1, "p_sweep": [1.0, 0.1, 0.01]},
+    # heavy-block stress: 16384-vertex core at pair density 0.7 (all heavy) in a
+    # sparse 2^20-vertex graph; measures the tensor-core contraction
+    "dense_core": {"workload": "dense_core_n1M_core16384_q0.7", "kind": "dense_core", "n": 1 << 20,
+                   "core": 16384, "q": 0.7, "m_rest": 4 << 20, "graph_seed": 1, "p_sweep": [1.0]},
+}
+WORKLOAD = WORKLOADS["chung_lu"]
 METRIC = "sampled edges/s"
 UNIT = "edges/s"
 
@@ -46,6 +54,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu")
     return ap.parse_args()
 
 
@@ -59,6 +68,8 @@ def dist_env():
 def make_graph():
     import gen
     w = WORKLOAD
+    if w["kind"] == "dense_core":
+        return gen.cached("planted_core", gen.planted_core, w["n"], w["core"], w["q"], w["m_rest"], w["graph_seed"])
     return gen.cached("chung_lu", gen.chung_lu, w["n"], w["m"], w["gamma"], w["wmax"], w["graph_seed"])
 
 
@@ -260,9 +271,25 @@ def our_arm(args):
                 "peak_source": peak_src, "traffic": traffic,
                 "algorithmic_bytes_per_launch": b_isect, "launch_ms": t_isect * 1000.0,
                 "phase_ms": {str(p): {"sample": float(per_leg[p][0]), "csr": float(per_leg[p][1]),
-                                      "intersect": float(per_leg[p][2])} for p in ps}}
+                                      "intersect": float(per_leg[p][2]), "heavy": float(per_leg[p][3])}
+                             for p in ps}}
     if traffic:
         roofline["traffic_gbs"] = traffic / t_isect / 1e9
+    if WORKLOAD["kind"] == "dense_core":
+        # the heavy block dominates: tensor-core roofline of k_heavy_tc
+        t_heavy = float(per_leg[1.0][3]) / 1000.0
+        flops = float(results[j1]["heavy_mma_flops"])
+        h = float(results[j1]["n_heavy"])
+        tf = float(peaks.get("bf16_tflops", 1900.0))
+        roofline = {"bound": "tensor", "kernel": "k_heavy_tc (p=1 count)",
+                    "achieved": flops / t_heavy / 1e12 if t_heavy > 0 else 0.0, "peak": tf,
+                    "unit": "TFLOP/s", "frac": (flops / t_heavy / 1e12) / tf if t_heavy > 0 else 0.0,
+                    "peak_source": peak_src + " bf16 burst (kernel of a few ms inside one count)",
+                    "traffic": None, "executed_flops_per_launch": flops,
+                    "useful_flops_per_launch": h * (h - 1) * (h - 2) / 3.0, "launch_ms": t_heavy * 1000.0,
+                    "phase_ms": {str(p): {"sample": float(per_leg[p][0]), "csr": float(per_leg[p][1]),
+                                          "intersect": float(per_leg[p][2]), "heavy": float(per_leg[p][3])}
+                                 for p in ps}}
 
     # ---- end to end through the C ABI from pinned host memory
     e2e_steps = max(1, min(5, args.steps))
@@ -282,7 +309,7 @@ def our_arm(args):
     g.close()
     if rank == 0:
         cpu = None
-        if ws == 1 and not args.no_cpu_baseline:
+        if ws == 1 and not args.no_cpu_baseline and WORKLOAD["kind"] == "chung_lu":
             cpu = cpu_baseline(edges, n)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -306,7 +333,9 @@ def our_arm(args):
 
 
 def main():
+    global WORKLOAD
     args = parse_args()
+    WORKLOAD = WORKLOADS[args.workload]
     if args.impl == "reference":
         reference_arm(args)
     else:

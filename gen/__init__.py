@@ -49,6 +49,9 @@ def _load():
         lib.gen_rmat.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_uint64, u32p]
         lib.gen_rmat.restype = ctypes.c_int64
+        lib.gen_planted_core.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
+                                         ctypes.c_uint64, u32p]
+        lib.gen_planted_core.restype = ctypes.c_int64
         _lib = lib
     return _lib
 
@@ -85,6 +88,18 @@ def rmat(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: floa
     r = _load().gen_rmat(scale, edge_factor, a, b, c, seed, _ptr(out))
     if r < 0:
         raise ValueError("gen_rmat failed (%d)" % r)
+    return np.ascontiguousarray(out[:r])
+
+
+def planted_core(n: int, core: int, q: float, m_rest: int, seed: int) -> np.ndarray:
+    """A dense core (core vertices, pair density q) inside a sparse uniform
+    graph of m_rest edges on n vertices, ids scrambled.  Core vertices are
+    heavy (degree above m^(1/2)) when q is well above 1/2."""
+    cap = core * (core - 1) // 2 + m_rest
+    out = np.empty((max(cap, 1), 2), dtype=np.uint32)
+    r = _load().gen_planted_core(n, core, q, m_rest, seed, _ptr(out))
+    if r < 0:
+        raise ValueError("gen_planted_core failed (%d)" % r)
     return np.ascontiguousarray(out[:r])
 
 

@@ -297,6 +297,40 @@ int64_t gen_chung_lu(uint32_t n, uint64_t m, double gamma, double wmax, uint64_t
     return res;
 }
 
+/* ------------------------------------------------------- planted core */
+
+/*
+ * A dense core planted in a sparse graph: `core` vertices joined pairwise
+ * with probability q (one counter-based draw per pair), plus m_rest uniform
+ * random edges among all n vertices; vertex ids are scrambled by a seeded
+ * permutation.  out_pairs must hold core*(core-1)/2 + m_rest pairs.  Returns
+ * the number of distinct edges.
+ */
+int64_t gen_planted_core(uint32_t n, uint32_t core, double q, uint64_t m_rest, uint64_t seed, uint32_t *out_pairs)
+{
+    if (core > n || q < 0.0 || q > 1.0 || n < 2) return -1;
+    const uint64_t cap = (uint64_t)core * (core - 1) / 2 + m_rest;
+    uint64_t *keys = (uint64_t *)malloc((cap ? cap : 1) * sizeof(uint64_t));
+    uint32_t *perm = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    if (!keys || !perm) { free(keys); free(perm); return -3; }
+    g_perm(perm, n, seed, 13);
+    const uint64_t thr = q >= 1.0 ? ~0ULL : (uint64_t)(q * 18446744073709551616.0);
+    uint64_t cnt = 0;
+    for (uint32_t i = 0; i < core; ++i)
+        for (uint32_t j = i + 1; j < core; ++j)
+            if (g_rand(seed, 17, (uint64_t)i * core + j) < thr || q >= 1.0) keys[cnt++] = g_key(perm[i], perm[j]);
+    for (uint64_t e = 0; e < m_rest; ++e) {
+        uint64_t r = g_rand(seed, 19, e);
+        uint32_t a = g_below((uint32_t)(r >> 32), n), b = g_below((uint32_t)r, n);
+        if (a == b) continue;
+        keys[cnt++] = g_key(perm[a], perm[b]);
+    }
+    free(perm);
+    int64_t res = g_finish(keys, cnt, n, out_pairs, cap);
+    free(keys);
+    return res;
+}
+
 /* ------------------------------------------------------- R-MAT */
 
 /*

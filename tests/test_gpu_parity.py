@@ -82,6 +82,18 @@ def test_dense_core_heavy_block(tc):
         assert g.count(1.0, 1)["heavy_mma_flops"] > 0  # the tensor-core path ran
 
 
+def test_planted_core_spans_many_tensor_tiles(tc):
+    """2048 heavy vertices: the dense block is 16 x 16 tiles of 128, with a
+    ragged edge once sampling thins the core (p = 0.9)."""
+    n = 100_000
+    e = gen.planted_core(n, 2048, 0.7, 200_000, 21)
+    r = oracle.run(e, n, 1.0, 1)
+    assert r["n_heavy"] >= 2000
+    check_graph(tc, e, n, [(1.0, 1), (0.9, 5)], sample=False)
+    with tc.Graph(e, n) as g:
+        assert g.count(1.0, 1)["heavy_mma_flops"] > 0
+
+
 # ------------------------------------------------------------ closed forms
 
 @pytest.mark.parametrize("k", [3, 4, 5, 17, 33, 34, 65, 130])
