@@ -170,6 +170,37 @@ tc_status tc_graph_export_csr(tc_graph *g, double p, uint64_t seed, uint32_t *ro
 tc_status tc_graph_export_edges(tc_graph *g, uint32_t *pairs_host);
 
 /*
+ * Batched counting: k independent graphs resident together and counted by
+ * one launch (a CUDA graph captured on the first tc_batch_count and replayed
+ * afterwards).  Every graph gets exactly the result that
+ * tc_graph_create + tc_count would give it (same sample, partition,
+ * classes and estimate); the batch only changes how the work is launched.
+ * The dense tensor-core path of the heavy class is not used in batches (the
+ * intersection kernels count that class).
+ *
+ * tc_batch_create
+ *   edges         the graphs' pair lists concatenated (graph 0 first), each
+ *                 in its own local ids [0, n_g); host or device memory
+ *                 (edges_on_device); same input rules as tc_graph_create.
+ *   m_per_graph   k pair counts; n_per_graph  k vertex counts (each >= 1).
+ *   k             1 .. 65535 graphs; sum of n_g below 2^32 - 1 and at most
+ *                 2^32 - 2 canonical edges in total.
+ *   cuda_stream   stream for all work (NULL: the batch creates its own).
+ * Errors: TC_EINVAL (bad sizes, an endpoint >= its n_g), TC_ENOMEM, TC_ECUDA.
+ *
+ * tc_batch_count  p[k], seed[k] per graph; out[k] results (host memory).
+ * Blocking.  TC_EINVAL if any p is outside (0, 1].
+ */
+typedef struct tc_batch tc_batch;
+tc_status tc_batch_create(const uint32_t *edges, const uint64_t *m_per_graph, const uint32_t *n_per_graph, uint32_t k,
+                          int edges_on_device, void *cuda_stream, tc_batch **out);
+tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_result *out);
+void tc_batch_destroy(tc_batch *b); /* NULL-safe */
+uint32_t tc_batch_size(const tc_batch *b);
+uint64_t tc_batch_num_edges(const tc_batch *b);    /* canonical edges of all graphs */
+uint64_t tc_batch_device_bytes(const tc_batch *b);
+
+/*
  * Count without allocating (the paper has no counterpart: this exists for
  * callers that cannot allocate device memory, such as a host framework
  * whose memory pool already owns the GPU, or code where a device allocation

@@ -63,6 +63,7 @@ std::atomic<unsigned long long> g_launches{0};
 }  // namespace
 
 void tcg::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void tcg::add_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 struct tc_graph {
     uint32_t n = 0;
@@ -153,51 +154,27 @@ void enqueue_sample(tc_graph *g, uint64_t seed_mix, uint64_t thr, const CountBuf
     partition(b, g->stream);
 }
 
-// Radix passes of the CSR build: at least two, so that the out-degree counts
-// (histogrammed by the first pass) are complete when the last pass runs and
-// builds the in-lists.
-std::vector<int> csr_pass_widths(int bits)
-{
-    std::vector<int> w = pass_widths(bits);
-    if (w.size() == 1) w = {(bits + 1) / 2, bits / 2};
-    return w;
-}
-
 // Degree-oriented CSR of the sampled graph by stable LSD radix sort of
 // (src << 32 | dst) on the src bits, plus the in-lists of the pairs whose
 // source has the smaller out-degree.  Fills g->col / g->inlist / g->inptr.
 void enqueue_csr(tc_graph *g, uint64_t seed_mix, uint64_t thr)
 {
-    cudaMemsetAsync(g->rowptr, 0, ((size_t)g->n + 1) * 4, g->stream);
-    cudaMemsetAsync(g->inptr, 0, ((size_t)g->n + 2) * 4, g->stream);
-    const std::vector<int> widths = csr_pass_widths(g->nbits);
-    uint64_t *bufs[2] = {g->bufA, g->bufB};
-    const uint64_t *in = g->ekey;
-    int cur = 0, shift = 32;
-    for (size_t p = 0; p < widths.size(); ++p) {
-        const bool last = p + 1 == widths.size();
-        ItemSource src;
-        if (p == 0) {
-            src = ItemSource{ItemSource::SAMPLE_ORIENT, g->ekey, g->m, nullptr, g->deg, seed_mix, thr};
-        } else {
-            src = ItemSource{ItemSource::PLAIN, in, 0, &g->st->m_sampled, nullptr, 0, 0};
-        }
-        uint64_t *out = bufs[cur];
-        InListArgs il{g->rowptr, g->inptr, nullptr, g->n};
-        if (last) {
-            // col takes the first 4 m bytes of the output buffer, the in-lists
-            // the second half; the input buffer is still being read
-            g->col = reinterpret_cast<uint32_t *>(out);
-            g->inlist = reinterpret_cast<uint32_t *>(out) + g->m;
-            il.inlist = g->inlist;
-        }
-        radix_pass(src, g->m, shift, widths[p], g->hist, g->scan, p == 0 ? g->rowptr : nullptr,
-                   last ? nullptr : out, last ? g->col : nullptr, last ? &il : nullptr, g->stream);
-        in = out;
-        cur ^= 1;
-        shift += widths[p];
-    }
-    scan_excl_u32(g->rowptr, (uint64_t)g->n + 1, nullptr, g->scan, g->stream);
+    CsrArgs a;
+    a.ekey = g->ekey;
+    a.m = g->m;
+    a.n = g->n;
+    a.nbits = g->nbits;
+    a.deg = g->deg;
+    a.seed_mix = seed_mix;
+    a.thr = thr;
+    a.m_sampled_dev = &g->st->m_sampled;
+    a.bufA = g->bufA;
+    a.bufB = g->bufB;
+    a.rowptr = g->rowptr;
+    a.inptr = g->inptr;
+    a.hist = g->hist;
+    a.scan = g->scan;
+    csr_build(a, &g->col, &g->inlist, g->stream);
 }
 
 CountBuffers buffers_of(tc_graph *g)
@@ -252,7 +229,7 @@ tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bo
     if (g->m > 0) {
         enqueue_csr(g, seed_mix, thr);
         b = buffers_of(g);
-        heavy_prepare(b, g->hb, g->stream);
+        if (g->hb.hcap) heavy_prepare(b, g->hb, g->stream);
         build_items(b, g->stream);
     }
     record(g, timing, 2);
@@ -425,9 +402,10 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     g->smem_bytes = (int)(slots * 4);
     // dense heavy block: at most 2 m^(1/2) heavy vertices, padded to the
-    // 128-row tile and capped at 32768 (2 x 2 GiB of bf16); without room for
-    // it the intersection kernels count the heavy class instead
-    if (m > 0) {
+    // 128-row tile and capped at 32768 (2 x 2 GiB of bf16).  Graphs below
+    // 2^20 edges, or without room for the block, have the intersection
+    // kernels count the heavy class instead.
+    if (m >= (1ull << 20)) {
         const uint64_t hbound = (uint64_t)(2.0 * std::sqrt((double)m)) + 2;
         const uint64_t hcap = std::min<uint64_t>((hbound + 127) / 128 * 128, 32768);
         g->hb.hlist_cap = (uint32_t)hbound;

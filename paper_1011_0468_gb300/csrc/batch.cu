@@ -1,0 +1,412 @@
+// Batched counting: many independent graphs counted by one launch.
+//
+// The graphs are stored as one disjoint union (graph g owns vertices
+// [voff[g], voff[g+1]) and edges [eoff[g], eoff[g+1]) of the union's sorted
+// canonical key array), so every kernel of the count runs once over all of
+// them.  Each edge is sampled with its own graph's (p, seed) on its
+// graph-local key, each vertex is split against its own graph's m_p, and the
+// class counts go to per-graph counters: every graph gets exactly the
+// result a separate tc_count would give.  The whole sequence (parameter
+// upload, ~40 kernels, result download) is captured once into a CUDA graph
+// and replayed by each tc_batch_count.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace tcg;
+
+namespace {
+
+int batch_bits(uint32_t n)
+{
+    int b = 1;
+    while (b < 32 && (1ull << b) < n) ++b;
+    return b;
+}
+
+// Union keys of the input pairs: graph g's local pair (a, b) becomes
+// (min + voff[g]) << 32 | (max + voff[g]); self-loops become ~0; endpoints
+// outside their graph raise ERR_ENDPOINT.
+__global__ void k_batch_keys(const uint32_t *__restrict__ pairs, uint64_t m_in, const uint64_t *__restrict__ in_off,
+                             const uint32_t *__restrict__ voff, uint32_t k, uint64_t *__restrict__ keys, DevState *st)
+{
+    const unsigned lane = lane_id();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    unsigned bad = 0;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m_in; base += stride) {
+        const uint64_t i = base + lane, ii = i < m_in ? i : m_in - 1;
+        const uint32_t g = find_part_warp(in_off, k, ii);
+        if (i >= m_in) continue;
+        const uint32_t a = pairs[2 * i], b = pairs[2 * i + 1];
+        const uint32_t vo = voff[g], ng = voff[g + 1] - vo;
+        uint64_t key = ~0ull;
+        if (a >= ng || b >= ng) {
+            bad = 1;
+        } else if (a != b) {
+            key = ((uint64_t)(min(a, b) + vo) << 32) | (uint64_t)(max(a, b) + vo);
+        }
+        keys[i] = key;
+    }
+    if (bad) atomicOr(&st->err, ERR_ENDPOINT);
+}
+
+// eoff[g] = first union key of graph g (keys sorted by source vertex).
+__global__ void k_batch_eoff(const uint64_t *__restrict__ keys, uint64_t m, const uint32_t *__restrict__ voff,
+                             uint32_t k, uint64_t *__restrict__ eoff)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g > k) return;
+    if (g == k) {
+        eoff[k] = m;
+        return;
+    }
+    const uint64_t target = (uint64_t)voff[g] << 32;
+    uint64_t lo = 0, hi = m;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    eoff[g] = lo;
+}
+
+void *batch_alloc(std::vector<void *> &allocs, uint64_t &total, uint64_t bytes)
+{
+    void *p = nullptr;
+    bytes = std::max<uint64_t>(bytes, 256);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    allocs.push_back(p);
+    total += bytes;
+    return p;
+}
+
+}  // namespace
+
+struct tc_batch {
+    uint32_t k = 0, n = 0;
+    uint64_t m = 0;
+    int nbits = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int smem_bytes = 0;
+    uint64_t bytes = 0;
+    std::vector<void *> allocs;
+    // union and scratch
+    uint64_t *ekey = nullptr, *bufA = nullptr, *bufB = nullptr, *items = nullptr;
+    uint64_t items_cap = 0;
+    uint32_t *deg = nullptr, *rowptr = nullptr, *inptr = nullptr, *hist = nullptr, *scan = nullptr;
+    uint32_t *col = nullptr, *inlist = nullptr;
+    uint8_t *heavy = nullptr;
+    DevState *st = nullptr;
+    // per graph
+    uint64_t *eoff = nullptr, *thr = nullptr, *seed_mix = nullptr;
+    uint32_t *voff = nullptr;
+    double *p = nullptr;
+    unsigned long long *counters = nullptr;  // m_p[k], t_light[k], t_heavy[k], then n_heavy[k] (uint32)
+    tc_result *res_dev = nullptr;
+    // pinned staging
+    uint64_t *h_thr = nullptr, *h_seed_mix = nullptr;
+    double *h_p = nullptr;
+    tc_result *h_res = nullptr;
+    DevState *h_st = nullptr;
+    // captured launch
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches_per_run = 0;
+
+    void *alloc(uint64_t b) { return batch_alloc(allocs, bytes, b); }
+};
+
+namespace {
+
+void free_batch(tc_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (void *p : b->allocs) cudaFree(p);
+    cudaFreeHost(b->h_thr);
+    cudaFreeHost(b->h_seed_mix);
+    cudaFreeHost(b->h_p);
+    cudaFreeHost(b->h_res);
+    cudaFreeHost(b->h_st);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+BatchView view_of(tc_batch *b)
+{
+    BatchView bv;
+    bv.k = b->k;
+    bv.eoff = b->eoff;
+    bv.voff = b->voff;
+    bv.thr = b->thr;
+    bv.seed_mix = b->seed_mix;
+    bv.m_p = b->counters;
+    bv.t_light = b->counters + b->k;
+    bv.t_heavy = b->counters + 2 * (uint64_t)b->k;
+    bv.n_heavy = reinterpret_cast<unsigned int *>(b->counters + 3 * (uint64_t)b->k);
+    return bv;
+}
+
+// The whole batched count, stream-ordered (captured into a CUDA graph).
+void enqueue_batch(tc_batch *b)
+{
+    cudaStream_t s = b->stream;
+    const uint64_t k = b->k;
+    cudaMemsetAsync(b->st, 0, sizeof(DevState), s);
+    cudaMemsetAsync(b->deg, 0, (size_t)b->n * 4, s);
+    cudaMemsetAsync(b->counters, 0, k * 28, s);
+    cudaMemcpyAsync(b->thr, b->h_thr, k * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->seed_mix, b->h_seed_mix, k * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->p, b->h_p, k * 8, cudaMemcpyHostToDevice, s);
+    CountBuffers cb;
+    cb.ekey = b->ekey;
+    cb.m = b->m;
+    cb.n = b->n;
+    cb.deg = b->deg;
+    cb.heavy = b->heavy;
+    cb.rowptr = b->rowptr;
+    cb.col = nullptr;
+    cb.inptr = b->inptr;
+    cb.inlist = nullptr;
+    cb.items = b->items;
+    cb.items_cap = b->items_cap;
+    cb.st = b->st;
+    cb.bv = view_of(b);
+    if (b->m > 0) {
+        sample_degree(cb, 0, 0, s);
+        partition(cb, s);
+        CsrArgs a;
+        a.ekey = b->ekey;
+        a.m = b->m;
+        a.n = b->n;
+        a.nbits = b->nbits;
+        a.deg = b->deg;
+        a.seed_mix = 0;
+        a.thr = 0;
+        a.bv = cb.bv;
+        a.m_sampled_dev = &b->st->m_sampled;
+        a.bufA = b->bufA;
+        a.bufB = b->bufB;
+        a.rowptr = b->rowptr;
+        a.inptr = b->inptr;
+        a.hist = b->hist;
+        a.scan = b->scan;
+        csr_build(a, &b->col, &b->inlist, s);
+        cb.col = b->col;
+        cb.inlist = b->inlist;
+        build_items(cb, s);
+        intersect(cb, b->smem_bytes, s);
+    }
+    finalize_batch(cb, b->p, b->res_dev, s);
+    cudaMemcpyAsync(b->h_res, b->res_dev, k * sizeof(tc_result), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(b->h_st, b->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+}
+
+tc_status status_of(unsigned err)
+{
+    if (err & ERR_ENDPOINT) return TC_EINVAL;
+    if (err & ERR_TIMEOUT) return TC_ETIMEOUT;
+    if (err) return TC_ECUDA;
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_batch_create(const uint32_t *edges, const uint64_t *m_per_graph, const uint32_t *n_per_graph, uint32_t k,
+                          int edges_on_device, void *cuda_stream, tc_batch **out)
+{
+    if (!out) return TC_EINVAL;
+    *out = nullptr;
+    if (k == 0 || k > 0xffffu || !m_per_graph || !n_per_graph) return TC_EINVAL;
+    std::vector<uint64_t> in_off(k + 1, 0);
+    std::vector<uint32_t> voff(k + 1, 0);
+    uint64_t n_total = 0;
+    for (uint32_t g = 0; g < k; ++g) {
+        if (n_per_graph[g] == 0) return TC_EINVAL;
+        in_off[g + 1] = in_off[g] + m_per_graph[g];
+        n_total += n_per_graph[g];
+        if (n_total >= 0xffffffffull) return TC_EINVAL;
+        voff[g + 1] = (uint32_t)n_total;
+    }
+    const uint64_t m_in = in_off[k];
+    if (m_in > 0xfffffffeull || (m_in > 0 && !edges)) return TC_EINVAL;
+
+    tc_batch *b = new (std::nothrow) tc_batch;
+    if (!b) return TC_ENOMEM;
+    b->k = k;
+    b->n = (uint32_t)n_total;
+    b->nbits = batch_bits(b->n);
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return TC_ECUDA;
+        }
+        b->own_stream = true;
+    }
+    cudaStream_t s = b->stream;
+    if (cudaMallocHost((void **)&b->h_thr, k * 8) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_seed_mix, k * 8) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_p, k * 8) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_res, k * sizeof(tc_result)) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_st, sizeof(DevState)) != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        return TC_ENOMEM;
+    }
+    b->st = (DevState *)b->alloc(sizeof(DevState));
+    b->voff = (uint32_t *)b->alloc((k + 1) * 4ull);
+    b->eoff = (uint64_t *)b->alloc((k + 1) * 8ull);
+    if (!b->st || !b->voff || !b->eoff) { free_batch(b); return TC_ENOMEM; }
+    cudaMemsetAsync(b->st, 0, sizeof(DevState), s);
+    cudaMemcpyAsync(b->voff, voff.data(), (k + 1) * 4ull, cudaMemcpyHostToDevice, s);
+
+    // ---- union keys: offset, canonicalise, sort, deduplicate
+    uint64_t m = 0;
+    if (m_in > 0) {
+        std::vector<void *> tmp;
+        uint64_t tmp_bytes = 0;
+        const uint32_t *dpairs = edges;
+        if (!edges_on_device) {
+            void *p = batch_alloc(tmp, tmp_bytes, m_in * 8);
+            if (!p) { free_batch(b); return TC_ENOMEM; }
+            cudaMemcpyAsync(p, edges, m_in * 8, cudaMemcpyHostToDevice, s);
+            dpairs = (const uint32_t *)p;
+        }
+        uint64_t *d_in_off = (uint64_t *)batch_alloc(tmp, tmp_bytes, (k + 1) * 8ull);
+        uint64_t *keys = (uint64_t *)batch_alloc(tmp, tmp_bytes, m_in * 8);
+        uint64_t *keys2 = (uint64_t *)batch_alloc(tmp, tmp_bytes, m_in * 8);
+        const uint64_t nt = ceil_div(m_in, RX_TILE);
+        uint32_t *hist = (uint32_t *)batch_alloc(tmp, tmp_bytes, (nt << RX_MAX_BITS) * 4);
+        uint32_t *scan = (uint32_t *)batch_alloc(tmp, tmp_bytes, scan_scratch_elems(nt << RX_MAX_BITS) * 4);
+        b->ekey = (uint64_t *)b->alloc(m_in * 8);
+        auto drop_tmp = [&]() { cudaStreamSynchronize(s); for (void *p : tmp) cudaFree(p); tmp.clear(); };
+        if (!d_in_off || !keys || !keys2 || !hist || !scan || !b->ekey) { drop_tmp(); free_batch(b); return TC_ENOMEM; }
+        cudaMemcpyAsync(d_in_off, in_off.data(), (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
+        k_batch_keys<<<grid_for(m_in, 256, 152 * 16), 256, 0, s>>>(dpairs, m_in, d_in_off, b->voff, k, keys, b->st);
+        note_launch();
+        uint64_t *a = keys, *c = keys2;
+        for (int half = 0; half < 2; ++half) {
+            int shift = half ? 32 : 0;
+            const int P = (b->nbits + RX_MAX_BITS - 1) / RX_MAX_BITS;
+            for (int i = 0; i < P; ++i) {
+                const int w = b->nbits / P + (i < b->nbits % P ? 1 : 0);
+                ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
+                radix_pass(src, m_in, shift, w, hist, scan, nullptr, c, nullptr, nullptr, s);
+                std::swap(a, c);
+                shift += w;
+            }
+        }
+        unique_keys(a, m_in, b->ekey, hist, scan, b->st, s);
+        cudaMemcpyAsync(b->h_st, b->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); drop_tmp(); free_batch(b); return TC_ECUDA; }
+        drop_tmp();
+        if (b->h_st->err & ERR_ENDPOINT) { free_batch(b); return TC_EINVAL; }
+        m = b->h_st->m_canon;
+    } else {
+        b->ekey = (uint64_t *)b->alloc(8);
+        if (!b->ekey) { free_batch(b); return TC_ENOMEM; }
+    }
+    b->m = m;
+    k_batch_eoff<<<(k + 1 + 127) / 128, 128, 0, s>>>(b->ekey, m, b->voff, k, b->eoff);
+    note_launch();
+
+    // ---- scratch of the count, sized for p = 1
+    const uint64_t nt = std::max<uint64_t>(ceil_div(m, RX_TILE), 1);
+    const uint64_t hist_len = nt << RX_MAX_BITS;
+    b->bufA = (uint64_t *)b->alloc(std::max<uint64_t>(m, 1) * 8);
+    b->bufB = (uint64_t *)b->alloc(std::max<uint64_t>(m, 1) * 8);
+    b->deg = (uint32_t *)b->alloc((uint64_t)b->n * 4);
+    b->rowptr = (uint32_t *)b->alloc(((uint64_t)b->n + 1) * 4);
+    b->inptr = (uint32_t *)b->alloc(((uint64_t)b->n + 2) * 4);
+    b->heavy = (uint8_t *)b->alloc(b->n);
+    b->items_cap = items_capacity(b->n, m);
+    b->items = (uint64_t *)b->alloc(b->items_cap * 8);
+    b->hist = (uint32_t *)b->alloc(hist_len * 4);
+    b->scan = (uint32_t *)b->alloc(scan_scratch_elems(std::max<uint64_t>(hist_len, (uint64_t)b->n + 2)) * 4);
+    b->thr = (uint64_t *)b->alloc(k * 8ull);
+    b->seed_mix = (uint64_t *)b->alloc(k * 8ull);
+    b->p = (double *)b->alloc(k * 8ull);
+    b->counters = (unsigned long long *)b->alloc(k * 28ull + 8);
+    b->res_dev = (tc_result *)b->alloc(k * sizeof(tc_result));
+    if (!b->bufA || !b->bufB || !b->deg || !b->rowptr || !b->inptr || !b->heavy || !b->items || !b->hist ||
+        !b->scan || !b->thr || !b->seed_mix || !b->p || !b->counters || !b->res_dev) {
+        free_batch(b);
+        return TC_ENOMEM;
+    }
+    // largest out-degree of any graph is below sqrt(2 m)
+    const uint64_t dmax = (uint64_t)std::sqrt(2.0 * (double)std::max<uint64_t>(m, 1)) + 2;
+    uint64_t slots = 8192;
+    while (slots < 4 * dmax && slots < 32768) slots <<= 1;
+    b->smem_bytes = (int)(slots * 4);
+    intersect_prepare(b->smem_bytes);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        free_batch(b);
+        return TC_ECUDA;
+    }
+    *out = b;
+    return TC_OK;
+}
+
+void tc_batch_destroy(tc_batch *b) { free_batch(b); }
+
+uint32_t tc_batch_size(const tc_batch *b) { return b ? b->k : 0; }
+uint64_t tc_batch_num_edges(const tc_batch *b) { return b ? b->m : 0; }
+uint64_t tc_batch_device_bytes(const tc_batch *b) { return b ? b->bytes : 0; }
+
+tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_result *out)
+{
+    if (!b || !p || !seed || !out) return TC_EINVAL;
+    for (uint32_t g = 0; g < b->k; ++g)
+        if (!(p[g] > 0.0 && p[g] <= 1.0)) return TC_EINVAL;
+    for (uint32_t g = 0; g < b->k; ++g) {
+        b->h_p[g] = p[g];
+        b->h_thr[g] = (uint64_t)(p[g] * 9007199254740992.0);
+        b->h_seed_mix[g] = splitmix64(seed[g]);
+    }
+    if (!b->exec) {
+        // capture the whole sequence once; replays reuse it
+        const uint64_t l0 = tc_launch_count();
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return TC_ECUDA;
+        }
+        enqueue_batch(b);
+        if (cudaStreamEndCapture(b->stream, &graph) != cudaSuccess || !graph) {
+            cudaGetLastError();
+            return TC_ECUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            cudaGetLastError();
+            b->exec = nullptr;
+            return TC_ECUDA;
+        }
+        b->launches_per_run = tc_launch_count() - l0;
+    } else {
+        add_launches(b->launches_per_run);
+    }
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    const tc_status st = status_of(b->h_st->err);
+    if (st != TC_OK) return st;
+    std::copy(b->h_res, b->h_res + b->k, out);
+    return TC_OK;
+}
+
+}  // extern "C"

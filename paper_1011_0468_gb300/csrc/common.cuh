@@ -39,6 +39,49 @@ struct DevState {
     unsigned int pad;
 };
 
+// A batch of independent graphs laid out as one disjoint union: graph g owns
+// edges [eoff[g], eoff[g+1]) of the union's canonical key array and vertices
+// [voff[g], voff[g+1]).  Keys hold union vertex ids; the sampling hash uses
+// the graph-local key, so every graph draws the sample it would draw alone.
+// k == 0 means a single graph (all per-graph arrays unused).
+struct BatchView {
+    uint32_t k = 0;
+    const uint64_t *eoff = nullptr;      // [k + 1]
+    const uint32_t *voff = nullptr;      // [k + 1]
+    const uint64_t *thr = nullptr;       // [k] floor(p * 2^53)
+    const uint64_t *seed_mix = nullptr;  // [k] splitmix64(seed)
+    unsigned long long *m_p = nullptr;   // [k] kept edges
+    unsigned int *n_heavy = nullptr;     // [k]
+    unsigned long long *t_light = nullptr;
+    unsigned long long *t_heavy = nullptr;
+};
+
+// Largest g in [0, k) with off[g] <= i (off non-decreasing, off[0] = 0).
+template <typename T>
+__device__ __forceinline__ uint32_t find_part(const T *off, uint32_t k, T i)
+{
+    uint32_t lo = 0, hi = k;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// find_part for 32 non-decreasing indices held by the lanes of a full warp:
+// two searches for the end lanes, and per-lane searches only when the warp
+// straddles a part boundary.
+template <typename T>
+__device__ __forceinline__ uint32_t find_part_warp(const T *off, uint32_t k, T i)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    uint32_t g = 0;
+    if (lane == 0 || lane == 31) g = find_part(off, k, i);
+    const uint32_t g0 = __shfl_sync(0xffffffffu, g, 0), g1 = __shfl_sync(0xffffffffu, g, 31);
+    if (g0 == g1) return g0;
+    return g0 + find_part(off + g0, g1 - g0 + 1, i);
+}
+
 // ---------------------------------------------------------------- splitmix64
 // Steele, Lea and Flood's splitmix64 in the form Vigna published:
 // z = x + golden gamma, then two xor-shift-multiply rounds and a final
@@ -57,6 +100,15 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 __device__ __forceinline__ bool keep_edge(uint64_t key, uint64_t seed_mix, uint64_t thr)
 {
     return (splitmix64(key ^ seed_mix) >> 11) < thr;
+}
+
+// The same decision for edge i of a batch union: graph g of the edge, its
+// local key, its own (p, seed).
+__device__ __forceinline__ bool keep_edge_batch(const BatchView &bv, uint64_t i, uint64_t key, uint32_t &g)
+{
+    g = find_part(bv.eoff, bv.k, (uint64_t)i);
+    const uint64_t vo = __ldg(bv.voff + g);
+    return keep_edge(key - ((vo << 32) | vo), __ldg(bv.seed_mix + g), __ldg(bv.thr + g));
 }
 
 // Degree-ordered orientation: the edge goes from the endpoint with the

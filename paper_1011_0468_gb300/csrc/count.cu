@@ -20,18 +20,40 @@ __device__ __forceinline__ uint32_t sample_one(uint64_t k, uint64_t seed_mix, ui
 
 __global__ void __launch_bounds__(256) k_sample_degree(const uint64_t *__restrict__ ekey, uint64_t m,
                                                        uint64_t seed_mix, uint64_t thr,
-                                                       uint32_t *__restrict__ deg, DevState *st)
+                                                       uint32_t *__restrict__ deg, DevState *st, BatchView bv)
 {
     uint32_t kept = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const ulonglong2 *e2 = reinterpret_cast<const ulonglong2 *>(ekey);
-    for (uint64_t i = tid; i < m / 2; i += stride) {
-        const ulonglong2 k = ld_stream_u64x2(e2 + i);
-        kept += sample_one(k.x, seed_mix, thr, deg);
-        kept += sample_one(k.y, seed_mix, thr, deg);
+    if (bv.k == 0) {
+        const ulonglong2 *e2 = reinterpret_cast<const ulonglong2 *>(ekey);
+        for (uint64_t i = tid; i < m / 2; i += stride) {
+            const ulonglong2 k = ld_stream_u64x2(e2 + i);
+            kept += sample_one(k.x, seed_mix, thr, deg);
+            kept += sample_one(k.y, seed_mix, thr, deg);
+        }
+        if ((m & 1) && tid == 0) kept += sample_one(ekey[m - 1], seed_mix, thr, deg);
+    } else {
+        // batch: each edge with its own graph's (p, seed); kept edges are
+        // also counted per graph
+        const unsigned lane = lane_id();
+        for (uint64_t base = tid - lane; base < m; base += stride) {
+            const uint64_t i = base + lane, ii = i < m ? i : m - 1;
+            const uint64_t key = ld_stream_u64(ekey + ii);
+            uint32_t g;
+            g = find_part_warp(bv.eoff, bv.k, ii);
+            const uint64_t vo = __ldg(bv.voff + g);
+            const bool f = i < m && keep_edge(key - ((vo << 32) | vo), __ldg(bv.seed_mix + g), __ldg(bv.thr + g));
+            if (f) {
+                atomicAdd(deg + (key >> 32), 1u);
+                atomicAdd(deg + (uint32_t)key, 1u);
+                ++kept;
+            }
+            const unsigned peers = __match_any_sync(FULL, g);
+            const unsigned c = __popc(__ballot_sync(FULL, f) & peers);
+            if (c && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(bv.m_p + g, (unsigned long long)c);
+        }
     }
-    if ((m & 1) && tid == 0) kept += sample_one(ekey[m - 1], seed_mix, thr, deg);
     kept = warp_sum(kept);
     if (lane_id() == 0 && kept) atomicAdd(&st->m_sampled, (unsigned long long)kept);
 }
@@ -47,7 +69,7 @@ void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaS
 {
     if (b.m == 0) return;
     k_sample_degree<<<grid_for(b.m / 2 + 1, 256, 152 * 8), 256, 0, s>>>(b.ekey, b.m, seed_mix, thr, b.deg,
-                                                                        b.st);
+                                                                        b.st, b.bv);
     note_launch();
 }
 
@@ -56,16 +78,33 @@ void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaS
 // ======================================================================
 
 __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevState *st,
-                            uint8_t *__restrict__ heavy)
+                            uint8_t *__restrict__ heavy, BatchView bv)
 {
-    const unsigned long long mp = st->m_sampled;
     uint32_t h = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
-        const unsigned long long d = deg[u];
-        const uint8_t f = d * d > mp;
-        heavy[u] = f;
-        h += f;
+    if (bv.k == 0) {
+        const unsigned long long mp = st->m_sampled;
+        for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+            const unsigned long long d = deg[u];
+            const uint8_t f = d * d > mp;
+            heavy[u] = f;
+            h += f;
+        }
+    } else {
+        // batch: each vertex against its own graph's m_p
+        const unsigned lane = lane_id();
+        for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+            const uint64_t u = base + lane;
+            const uint32_t uu = (uint32_t)(u < n ? u : n - 1);
+            const uint32_t g = find_part_warp(bv.voff, bv.k, uu);
+            const unsigned long long d = deg[uu], mp = bv.m_p[g];
+            const bool f = u < n && d * d > mp;
+            if (u < n) heavy[u] = f;
+            h += f;
+            const unsigned peers = __match_any_sync(FULL, g);
+            const unsigned c = __popc(__ballot_sync(FULL, f) & peers);
+            if (c && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(bv.n_heavy + g, c);
+        }
     }
     h = warp_sum(h);
     if (lane_id() == 0 && h) atomicAdd(&st->n_heavy, h);
@@ -73,7 +112,7 @@ __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevSta
 
 void partition(const CountBuffers &b, cudaStream_t s)
 {
-    k_partition<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.deg, b.n, b.st, b.heavy);
+    k_partition<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.deg, b.n, b.st, b.heavy, b.bv);
     note_launch();
 }
 
@@ -154,6 +193,32 @@ __global__ void k_finalize(const DevState *st, uint64_t m, uint32_t n, double p,
 void finalize(const CountBuffers &b, double p, tc_result *out_dev, cudaStream_t s)
 {
     k_finalize<<<1, 1, 0, s>>>(b.st, b.m, b.n, p, out_dev);
+    note_launch();
+}
+
+// One result per graph of a batch (same float64 rescale per graph).
+__global__ void k_finalize_batch(BatchView bv, const double *__restrict__ p, tc_result *__restrict__ out)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= bv.k) return;
+    const double pg = p[g];
+    const double p3 = __dmul_rn(__dmul_rn(pg, pg), pg);
+    tc_result r;
+    r.m = bv.eoff[g + 1] - bv.eoff[g];
+    r.m_sampled = bv.m_p[g];
+    r.n = bv.voff[g + 1] - bv.voff[g];
+    r.n_heavy = bv.n_heavy[g];
+    r.t_light = bv.t_light[g];
+    r.t_heavy = bv.t_heavy[g];
+    r.estimate = __dadd_rn(__ddiv_rn((double)r.t_light, p3), __ddiv_rn((double)r.t_heavy, p3));
+    r.src_elems = r.nbr_elems = r.partners = r.heavy_mma_flops = 0;
+    for (int i = 0; i < 8; ++i) r.ms[i] = 0.0f;
+    out[g] = r;
+}
+
+void finalize_batch(const CountBuffers &b, const double *p_dev, tc_result *out_dev, cudaStream_t s)
+{
+    k_finalize_batch<<<grid_for(b.bv.k, 128, 1u << 20), 128, 0, s>>>(b.bv, p_dev, out_dev);
     note_launch();
 }
 

@@ -418,6 +418,7 @@ bool heavy_make_maps(HeavyBuffers &hb)
 
 void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s)
 {
+    if (hb.hcap == 0 || hb.hlist_cap == 0 || b.n == 0) return;  // no dense block: DevState::dense stays 0
     k_heavy_list<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.heavy, b.n, hb.hlist, hb.hlist_cap, b.st);
     note_launch();
     k_heavy_rank<<<(unsigned)ceil_div(hb.hlist_cap, HR_THREADS), HR_THREADS, 0, s>>>(b.deg, hb.hlist, hb.hidx,

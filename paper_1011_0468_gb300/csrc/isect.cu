@@ -41,9 +41,24 @@ uint64_t items_capacity(uint32_t n, uint64_t m)
 
 __device__ __forceinline__ uint32_t bucket_of(uint32_t d) { return d <= WARP_MAX ? 0u : (d <= MID_MAX ? 1u : 2u); }
 
-__global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ inptr, uint32_t n,
-                        uint64_t *__restrict__ items, uint64_t wm_cap, uint64_t cap, DevState *st)
+// Item layout: owner in bits 0..31; single graph: segment in bits 32..63;
+// batch union: segment in bits 32..47 and the owner's graph in bits 48..63.
+__device__ __forceinline__ uint64_t make_item(uint32_t x, uint32_t seg, uint32_t g, bool batch)
 {
+    return batch ? (((uint64_t)g << 48) | ((uint64_t)seg << 32) | x) : (((uint64_t)seg << 32) | x);
+}
+
+__device__ __forceinline__ void split_item(uint64_t item, bool batch, uint32_t &x, uint32_t &seg, uint32_t &g)
+{
+    x = (uint32_t)item;
+    seg = batch ? (uint32_t)((item >> 32) & 0xffffu) : (uint32_t)(item >> 32);
+    g = batch ? (uint32_t)(item >> 48) : 0u;
+}
+
+__global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ inptr, uint32_t n,
+                        uint64_t *__restrict__ items, uint64_t wm_cap, uint64_t cap, DevState *st, BatchView bv)
+{
+    const bool batch = bv.k != 0;
     const unsigned lane = lane_id();
     const uint64_t wstride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += wstride) {
@@ -53,8 +68,13 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
             d = rowptr[x + 1] - rowptr[x];
             if (d >= 2) np = d + (inptr[x + 1] - inptr[x]);
         }
+        const uint32_t gx = batch ? find_part_warp(bv.voff, bv.k, (uint32_t)(x < n ? x : n - 1)) : 0u;
         const uint32_t b = bucket_of(d), seg = b == 0 ? SEG_W : SEG_B;
-        const uint32_t nseg = (np + seg - 1) / seg;
+        uint32_t nseg = (np + seg - 1) / seg;
+        if (batch && nseg > 0x10000u) {  // segment index must fit 16 bits
+            atomicOr(&st->err, ERR_OVERFLOW);
+            nseg = 0x10000u;
+        }
 #pragma unroll
         for (uint32_t bb = 0; bb < 3; ++bb) {
             const uint32_t c = b == bb ? nseg : 0u;
@@ -67,7 +87,7 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
                 const uint64_t pos = bb == 0 ? idx : (bb == 1 ? wm_cap - 1 - idx : wm_cap + idx);
                 const bool ok = bb == 2 ? pos < cap : idx < wm_cap;
                 if (ok)
-                    items[pos] = ((uint64_t)s << 32) | (uint32_t)x;
+                    items[pos] = make_item((uint32_t)x, s, gx, batch);
                 else
                     atomicOr(&st->err, ERR_OVERFLOW);
             }
@@ -78,7 +98,8 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
 void build_items(const CountBuffers &b, cudaStream_t s)
 {
     const uint64_t wm = wm_capacity(b.n, b.m);
-    k_items<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.inptr, b.n, b.items, wm, b.items_cap, b.st);
+    k_items<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.inptr, b.n, b.items, wm, b.items_cap, b.st,
+                                                          b.bv);
     note_launch();
 }
 
@@ -134,6 +155,17 @@ struct SortedRow {
 struct Tally {
     unsigned long long light = 0, heavy = 0, table = 0, stream = 0, partners = 0;
 };
+
+// Batch unions: move this warp's class counts into graph g's counters.
+__device__ __forceinline__ void flush_graph_counts(Tally &t, const BatchView &bv, uint32_t g)
+{
+    const unsigned long long l = warp_sum(t.light), h = warp_sum(t.heavy);
+    if (lane_id() == 0) {
+        if (l) atomicAdd(bv.t_light + g, l);
+        if (h) atomicAdd(bv.t_heavy + g, h);
+    }
+    t.light = t.heavy = 0;
+}
 
 __device__ __forceinline__ void flush_tally(const Tally &t, unsigned long long *red /* 33 */, DevState *st)
 {
@@ -266,7 +298,8 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
                                                            const uint32_t *__restrict__ inptr,
                                                            const uint32_t *__restrict__ inlist,
                                                            const uint64_t *__restrict__ items, uint64_t wm_cap,
-                                                           const uint8_t *__restrict__ heavy, DevState *st)
+                                                           const uint8_t *__restrict__ heavy, DevState *st,
+                                                           BatchView bv)
 {
     __shared__ uint32_t s_tab[PW_WARPS][WTAB];
     __shared__ uint32_t s_pre[PW_WARPS][32];
@@ -276,6 +309,8 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
     const uint32_t nitems = (uint32_t)min((unsigned long long)st->nlist[0], (unsigned long long)wm_cap);
     const bool skip_heavy = st->dense != 0;
     uint32_t *tab = s_tab[w];
+    const bool batch = bv.k != 0;
+    uint32_t cur_g = 0;  // graph whose counts this warp holds (batch)
     Tally t;
     for (;;) {
         uint32_t first = 0;
@@ -284,8 +319,12 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
         if (first >= nitems) break;
         const uint32_t last = min(first + GRAB, nitems);
         for (uint32_t idx = first; idx < last; ++idx) {
-            const uint64_t item = items[idx];
-            const uint32_t x = (uint32_t)item, seg = (uint32_t)(item >> 32);
+            uint32_t x, seg, g;
+            split_item(items[idx], batch, x, seg, g);
+            if (batch && g != cur_g) {
+                flush_graph_counts(t, bv, cur_g);
+                cur_g = g;
+            }
             const uint32_t beg = rowptr[x], d = rowptr[x + 1] - beg;
             if (d > WARP_MAX) {  // cannot happen unless the item list overflowed
                 if (lane == 0) atomicOr(&st->err, ERR_OVERFLOW);
@@ -316,6 +355,7 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
             __syncwarp();  // the table is rewritten by the next item
         }
     }
+    if (batch) flush_graph_counts(t, bv, cur_g);
     flush_tally(t, red, st);
 }
 
@@ -339,7 +379,7 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_probe_block(const uint32_t *_
                                                             const uint32_t *__restrict__ inlist,
                                                             const uint64_t *__restrict__ items, uint64_t wm_cap,
                                                             const uint8_t *__restrict__ heavy, DevState *st,
-                                                            uint32_t tab_slots, uint64_t cap)
+                                                            uint32_t tab_slots, uint64_t cap, BatchView bv)
 {
     extern __shared__ uint32_t s_dyn[];
     __shared__ uint32_t s_static[DYN ? 1 : MID_TAB];
@@ -368,8 +408,8 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_probe_block(const uint32_t *_
         __syncthreads();
         const uint32_t idx = s_idx;
         if (idx >= nitems) break;
-        const uint64_t item = DYN ? items[wm_cap + idx] : items[wm_cap - 1 - idx];
-        const uint32_t x = (uint32_t)item, seg = (uint32_t)(item >> 32);
+        uint32_t x, seg, g;
+        split_item(DYN ? items[wm_cap + idx] : items[wm_cap - 1 - idx], bv.k != 0, x, seg, g);
         const uint32_t beg = rowptr[x], d = rowptr[x + 1] - beg;
         const uint8_t hx = heavy[x];
         // a power of two >= 4 d slots, when that fits
@@ -448,26 +488,42 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_probe_block(const uint32_t *_
             else
                 stream_group(col, SortedRow{col + beg, d}, start, len, cls, s_beg[w], s_pre[w], t, false);
         }
+        if (bv.k != 0) flush_graph_counts(t, bv, g);
         __syncthreads();  // every warp is done with this owner
     }
     flush_tally(t, red, st);
+}
+
+// Static + dynamic shared memory of the large-owner kernel must fit the
+// function's opt-in limit, which starts at 48 KiB in every process: raise it
+// once per process and device to the largest size requested so far.
+void intersect_prepare(int dyn_smem_bytes)
+{
+    static int set_bytes[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || dyn_smem_bytes > set_bytes[dev]) {
+        if (cudaFuncSetAttribute(k_probe_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_bytes) ==
+                cudaSuccess &&
+            dev >= 0 && dev < 64)
+            set_bytes[dev] = dyn_smem_bytes;
+    }
 }
 
 void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
 {
     if (b.n == 0 || b.m == 0) return;
     const uint64_t wm = wm_capacity(b.n, b.m);
-    k_probe_warp<<<152 * 8, PW_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy, b.st);
+    k_probe_warp<<<152 * 8, PW_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy, b.st,
+                                                b.bv);
     note_launch();
     k_probe_block<false><<<152 * 8, PB_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy,
-                                                         b.st, MID_TAB, b.items_cap);
+                                                         b.st, MID_TAB, b.items_cap, b.bv);
     note_launch();
-    // static + dynamic shared memory must fit the function's opt-in limit,
-    // which starts at 48 KiB in every process
-    cudaFuncSetAttribute(k_probe_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_bytes);
+    intersect_prepare(dyn_smem_bytes);
     k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm,
                                                                 b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
-                                                                b.items_cap);
+                                                                b.items_cap, b.bv);
     note_launch();
 }
 

@@ -18,8 +18,10 @@ constexpr int SC_CHUNK = 4096;                   // scan elements per block
 
 inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
-// Process-wide count of kernel launches made by the library (api.cu).
+// Process-wide count of kernel launches made by the library (api.cu);
+// add_launches accounts for the kernels of a replayed CUDA graph.
 void note_launch();
+void add_launches(unsigned long long n);
 
 // Blocks for `work` items at `threads` per block, at most `cap` (count.cu).
 unsigned grid_for(uint64_t work, int threads, unsigned cap);
@@ -39,7 +41,8 @@ struct ItemSource {
     uint64_t n_host;                    // item count when n_dev is NULL
     const unsigned long long *n_dev;    // device item count (e.g. m_p), or NULL
     const uint32_t *deg;                // SAMPLE_ORIENT: sampled degrees
-    uint64_t seed_mix, thr;             // SAMPLE_ORIENT: keep test
+    uint64_t seed_mix, thr;             // SAMPLE_ORIENT: keep test (single graph)
+    BatchView bv;                       // SAMPLE_ORIENT over a batch union (bv.k > 0)
 };
 
 // Optional by-product of a radix pass over oriented edges (src << 32 | dst):
@@ -64,6 +67,25 @@ struct InListArgs {
 void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
                 uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
                 const InListArgs *in, cudaStream_t s);
+
+// Degree-oriented CSR of the sampled graph (single graph or batch union):
+// stable LSD radix sort of (src << 32 | dst) on the src bits (at least two
+// passes), the first pass sampling and orienting the canonical keys, the
+// last one also building the in-lists.  rowptr [n + 1] and inptr [n + 2]
+// are zeroed here; col and inlist are placed in bufA / bufB.
+struct CsrArgs {
+    const uint64_t *ekey;
+    uint64_t m;
+    uint32_t n;
+    int nbits;  // bits of a vertex id
+    const uint32_t *deg;
+    uint64_t seed_mix, thr;  // single graph
+    BatchView bv;            // batch union (bv.k > 0)
+    const unsigned long long *m_sampled_dev;
+    uint64_t *bufA, *bufB;
+    uint32_t *rowptr, *inptr, *hist, *scan;
+};
+void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t s);
 
 // Canonical keys from raw pairs: (min << 32 | max), self-loops become
 // ~0ull; endpoints >= n raise ERR_ENDPOINT; pairs that are not strictly
@@ -90,6 +112,7 @@ struct CountBuffers {
     uint64_t *items;        // owner work items [items_cap]
     uint64_t items_cap;
     DevState *st;
+    BatchView bv;           // k > 0: the graph is a batch union
 };
 
 void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaStream_t s);
@@ -101,7 +124,12 @@ uint64_t items_capacity(uint32_t n, uint64_t m);
 void build_items(const CountBuffers &b, cudaStream_t s);
 // dyn_smem_bytes: shared memory of the hash table for owners with d+ > 1024
 void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s);
+// Raise the launch limit that intersect needs (called by intersect; call it
+// ahead of a stream capture so that the capture contains stream work only).
+void intersect_prepare(int dyn_smem_bytes);
 void finalize(const CountBuffers &b, double p, tc_result *out_dev, cudaStream_t s);
+// batch union: one tc_result per graph, p_dev[k] the graphs' sampling rates
+void finalize_batch(const CountBuffers &b, const double *p_dev, tc_result *out_dev, cudaStream_t s);
 
 // ---------------------------------------------------------------- heavy.cu
 // Dense heavy block: U and U^T (hcap x hcap bf16, row stride hcap), the

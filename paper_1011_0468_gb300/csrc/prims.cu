@@ -86,16 +86,30 @@ void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch
 
 // Loads item i of a pass; returns false when the item does not take part
 // (an edge that the sampling drops).
-__device__ __forceinline__ bool load_item(const ItemSource &src, uint64_t i, uint64_t &item)
+// g: the batch graph of item i (batch unions only).
+__device__ __forceinline__ bool load_item(const ItemSource &src, uint64_t i, uint64_t &item, uint32_t g)
 {
     if (src.kind == ItemSource::PLAIN) {
         item = ld_stream_u64(src.in + i);
         return true;
     }
     const uint64_t key = ld_stream_u64(src.in + i);
-    if (!keep_edge(key, src.seed_mix, src.thr)) return false;
+    if (src.bv.k == 0) {
+        if (!keep_edge(key, src.seed_mix, src.thr)) return false;
+    } else {
+        const uint64_t vo = __ldg(src.bv.voff + g);
+        if (!keep_edge(key - ((vo << 32) | vo), __ldg(src.bv.seed_mix + g), __ldg(src.bv.thr + g))) return false;
+    }
     item = orient(key, src.deg);
     return true;
+}
+
+// Batch graph of item i for every lane of a full warp (indices consecutive
+// across lanes); 0 unless the source samples a batch union.
+__device__ __forceinline__ uint32_t item_graph(const ItemSource &src, uint64_t i, uint64_t n)
+{
+    if (src.kind != ItemSource::SAMPLE_ORIENT || src.bv.k == 0) return 0;
+    return find_part_warp(src.bv.eoff, src.bv.k, i < n ? i : n - 1);
 }
 
 // The in-list by-product: pair (src -> dst) belongs to dst's in-list iff
@@ -121,7 +135,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int 
         for (int j = 0; j < RX_ITEMS; ++j) {
             const uint64_t i = base + (uint64_t)j * RX_THREADS + threadIdx.x;
             uint64_t item = 0;
-            const bool valid = i < n && load_item(src, i, item);
+            const uint32_t g = item_graph(src, i, n);
+            const bool valid = i < n && load_item(src, i, item, g);
             const uint32_t d = valid ? ((uint32_t)(item >> shift) & mask) : 0xffffffffu;
             const unsigned peers = __match_any_sync(FULL, d);
             if (valid) {
@@ -162,7 +177,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
     for (int j = 0; j < RX_ITEMS; ++j) {
         const uint64_t i = seg + (uint64_t)j * 32 + lane;
         items[j] = 0;
-        const bool valid = i < n && load_item(src, i, items[j]);
+        const uint32_t g = item_graph(src, i, n);
+        const bool valid = i < n && load_item(src, i, items[j], g);
         const uint32_t d = valid ? ((uint32_t)(items[j] >> shift) & mask) : 0xffffffffu;
         const unsigned peers = __match_any_sync(FULL, d);
         uint32_t r = 0;
@@ -314,6 +330,52 @@ void unique_keys(const uint64_t *keys, uint64_t m_in, uint64_t *out, uint32_t *t
     scan_excl_u32(tile_cnt, nt, tile_cnt + nt, scan_scratch, s);
     k_unique_scatter<<<(unsigned)nt, UQ_THREADS, 0, s>>>(keys, m_in, tile_cnt, out); note_launch();
     k_store_count<<<1, 1, 0, s>>>(tile_cnt + nt, st); note_launch();
+}
+
+}  // namespace tcg
+
+namespace tcg {
+
+void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t s)
+{
+    cudaMemsetAsync(a.rowptr, 0, ((size_t)a.n + 1) * 4, s);
+    cudaMemsetAsync(a.inptr, 0, ((size_t)a.n + 2) * 4, s);
+    // digit widths: at most RX_MAX_BITS each, as even as possible, >= 2 passes
+    int P = (a.nbits + RX_MAX_BITS - 1) / RX_MAX_BITS, widths[8];
+    for (int i = 0; i < P; ++i) widths[i] = a.nbits / P + (i < a.nbits % P ? 1 : 0);
+    if (P == 1) {
+        widths[0] = (a.nbits + 1) / 2;
+        widths[1] = a.nbits / 2;
+        P = 2;
+    }
+    uint64_t *bufs[2] = {a.bufA, a.bufB};
+    const uint64_t *in = a.ekey;
+    int cur = 0, shift = 32;
+    for (int p = 0; p < P; ++p) {
+        const bool last = p + 1 == P;
+        ItemSource src;
+        if (p == 0) {
+            src = ItemSource{ItemSource::SAMPLE_ORIENT, a.ekey, a.m, nullptr, a.deg, a.seed_mix, a.thr};
+            src.bv = a.bv;
+        } else {
+            src = ItemSource{ItemSource::PLAIN, in, 0, a.m_sampled_dev, nullptr, 0, 0};
+        }
+        uint64_t *out = bufs[cur];
+        InListArgs il{a.rowptr, a.inptr, nullptr, a.n};
+        if (last) {
+            // col in the first 4 m bytes of the output buffer, the in-lists in
+            // the second half (the input buffer is still being read)
+            *col = reinterpret_cast<uint32_t *>(out);
+            *inlist = reinterpret_cast<uint32_t *>(out) + a.m;
+            il.inlist = *inlist;
+        }
+        radix_pass(src, a.m, shift, widths[p], a.hist, a.scan, p == 0 ? a.rowptr : nullptr, last ? nullptr : out,
+                   last ? *col : nullptr, last ? &il : nullptr, s);
+        in = out;
+        cur ^= 1;
+        shift += widths[p];
+    }
+    scan_excl_u32(a.rowptr, (uint64_t)a.n + 1, nullptr, a.scan, s);
 }
 
 }  // namespace tcg

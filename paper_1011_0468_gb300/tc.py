@@ -68,7 +68,18 @@ SIGNATURES = [
     ("tc_launch_count", ctypes.c_uint64, []),
     ("tc_count_noalloc", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
                                         ctypes.POINTER(tc_result), _vp]),
+    ("tc_batch_create", ctypes.c_int, [_vp, _u64p, _u32p, ctypes.c_uint32, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    ("tc_batch_count", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _u64p, _vp]),
+    ("tc_batch_destroy", None, [_vp]),
+    ("tc_batch_size", ctypes.c_uint32, [_vp]),
+    ("tc_batch_num_edges", ctypes.c_uint64, [_vp]),
+    ("tc_batch_device_bytes", ctypes.c_uint64, [_vp]),
 ]
+
+# numpy view of tc_result (same layout as the C struct)
+RESULT_DTYPE = np.dtype([("m", "<u8"), ("m_sampled", "<u8"), ("n", "<u4"), ("n_heavy", "<u4"), ("t_light", "<u8"),
+                         ("t_heavy", "<u8"), ("estimate", "<f8"), ("src_elems", "<u8"), ("nbr_elems", "<u8"),
+                         ("partners", "<u8"), ("heavy_mma_flops", "<u8"), ("ms", "<f4", (8,))])
 
 # limits of tc_count_noalloc (include/tc.h)
 TC_NOALLOC_MAX_EDGES = 1 << 18
@@ -286,6 +297,65 @@ class Graph:
     def close(self):
         if self._h:
             tc_graph_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """k independent graphs resident together and counted by one launch
+    (tc_batch_create / tc_batch_count / tc_batch_destroy).  graphs: list of
+    (edges, n) with edges an (m_g, 2) uint32 array in the graph's own ids."""
+
+    def __init__(self, graphs, stream=None):
+        k = len(graphs)
+        m_per = np.array([len(np.asarray(e).reshape(-1, 2)) for e, _ in graphs], dtype=np.uint64)
+        n_per = np.array([n for _, n in graphs], dtype=np.uint32)
+        parts = [np.asarray(e, dtype=np.uint32).reshape(-1, 2) for e, _ in graphs]
+        edges = np.ascontiguousarray(np.concatenate(parts) if parts else np.zeros((0, 2), np.uint32))
+        h = _vp()
+        _check(lib().tc_batch_create(edges.ctypes.data if len(edges) else None, m_per.ctypes.data_as(_u64p),
+                                     n_per.ctypes.data_as(_u32p), k, 0, _stream_handle(stream), ctypes.byref(h)),
+               "tc_batch_create")
+        self._h = h.value
+        self.k = k
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("batch is closed")
+        return self._h
+
+    @property
+    def m(self) -> int:
+        return int(lib().tc_batch_num_edges(self.handle))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().tc_batch_device_bytes(self.handle))
+
+    def count(self, p, seed) -> np.ndarray:
+        """Results of all graphs as a numpy array of RESULT_DTYPE."""
+        pa = np.ascontiguousarray(np.broadcast_to(np.asarray(p, dtype=np.float64), (self.k,)))
+        sa = np.ascontiguousarray(np.broadcast_to(np.asarray(seed, dtype=np.uint64), (self.k,)))
+        out = np.zeros(self.k, dtype=RESULT_DTYPE)
+        _check(lib().tc_batch_count(self.handle, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    sa.ctypes.data_as(_u64p), out.ctypes.data), "tc_batch_count")
+        return out
+
+    def close(self):
+        if self._h:
+            lib().tc_batch_destroy(self._h)
             self._h = None
 
     def __enter__(self):
