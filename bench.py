@@ -41,6 +41,8 @@ WORKLOADS = {
     # sparse 2^20-vertex graph; measures the tensor-core contraction
     "dense_core": {"workload": "dense_core_n1M_core16384_q0.7", "kind": "dense_core", "n": 1 << 20,
                    "core": 16384, "q": 0.7, "m_rest": 4 << 20, "graph_seed": 1, "p_sweep": [1.0]},
+    # batched counting: 10000 small uneven graphs, each with its own p and seed
+    "batch": {"workload": "batch_10000_er_chunglu2.3", "kind": "batch", "graphs": 10000, "graph_seed": 1},
 }
 WORKLOAD = WORKLOADS["chung_lu"]
 METRIC = "sampled edges/s"
@@ -332,10 +334,98 @@ def our_arm(args):
         dist.destroy_process_group()
 
 
+def make_batch_graphs(count: int, seed: int = 1):
+    """The batched workload: `count` graphs, n log-uniform in [100, 50000],
+    average degree uniform in [4, 64], alternating Erdos-Renyi and Chung-Lu
+    (exponent 2.3), p from {0.1, 0.5, 1.0}, sampling seed = index + 1."""
+    from concurrent.futures import ThreadPoolExecutor
+    import gen
+    specs = gen.batch_specs(count, seed=seed)
+    with ThreadPoolExecutor(max(4, os.cpu_count() or 4)) as ex:
+        graphs = list(ex.map(gen.batch_graph, specs))
+    return specs, graphs
+
+
+def batch_arm(args):
+    """Batched counting (tc_batch_*) against the plain one-count-per-graph
+    path on the same GPU, same graphs, same (p, seed): graphs per second."""
+    import numpy as np
+    import torch
+    from paper_1011_0468_gb300 import tc
+
+    torch.cuda.set_device(0)
+    tc.lib()
+    w = WORKLOAD
+    specs, graphs = make_batch_graphs(w["graphs"], w["graph_seed"])
+    k = len(graphs)
+    p = np.array([s["p"] for s in specs], dtype=np.float64)
+    seeds = np.array([s["seed"] for s in specs], dtype=np.uint64)
+    batch = tc.Batch([(g, s["n"]) for g, s in zip(graphs, specs)])
+    m_total = batch.m
+    schedule = batch.autotune(p, seeds)
+    for i in range(args.warmup):
+        batch.count(p, seeds + np.uint64(i))
+    l0 = tc.tc_launch_count()
+    with ClockSampler(0) as clocks:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            res = batch.count(p, seeds + np.uint64(i))
+        t_batch = time.perf_counter() - t0
+    launches = tc.tc_launch_count() - l0
+    batch.close()
+
+    # plain path: the same graphs resident one per object, one count per call
+    tc.use_torch_allocator(True)
+    objs = [tc.Graph(g, s["n"]) for g, s in zip(graphs, specs)]
+    buf = torch.zeros((k, ctypes.sizeof(tc.tc_result)), dtype=torch.uint8, pin_memory=True)
+    for i in range(1):
+        for j, o in enumerate(objs):
+            o.count_async(float(p[j]), int(seeds[j]), buf[j].data_ptr())
+        for o in objs:
+            o.sync()
+    plain_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for i in range(plain_steps):
+        for j, o in enumerate(objs):
+            o.count_async(float(p[j]), int(seeds[j]) + i, buf[j].data_ptr())
+        for o in objs:
+            o.sync()
+    t_plain = time.perf_counter() - t0
+    plain = np.frombuffer(buf.numpy().tobytes(), dtype=tc.RESULT_DTYPE)
+    # the last plain step used seed + (plain_steps - 1); compare with a batch
+    # count at the same seeds
+    with tc.Batch([(g, s["n"]) for g, s in zip(graphs, specs)]) as b2:
+        ref = b2.count(p, seeds + np.uint64(plain_steps - 1))
+    identical = bool(all(np.array_equal(ref[f], plain[f]) for f in ("m_sampled", "n_heavy", "t_light", "t_heavy",
+                                                                      "estimate")))
+    for o in objs:
+        o.close()
+
+    value = args.steps * k / t_batch
+    plain_value = plain_steps * k / t_plain
+    line = {"metric": "batched graphs/s", "value": value, "unit": "graphs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t_batch / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": w["workload"], "graphs": k, "m_total": int(m_total),
+                       "n_total": int(sum(s["n"] for s in specs)), "schedule": schedule},
+            "edges_per_s": args.steps * m_total / t_batch,
+            "plain": {"value": plain_value, "unit": "graphs/s", "ms_per_step": 1000 * t_plain / plain_steps,
+                      "path": "one tc_count_async per graph, graphs resident"},
+            "speedup_vs_plain": value / plain_value, "identical_to_plain": identical,
+            "gpu_launches": int(launches), "clocks": clocks.summary(),
+            "t_total_estimate_sum": float(np.sum(res["estimate"]))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global WORKLOAD
     args = parse_args()
     WORKLOAD = WORKLOADS[args.workload]
+    if WORKLOAD["kind"] == "batch":
+        if args.impl == "ours":
+            batch_arm(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

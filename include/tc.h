@@ -195,6 +195,17 @@ typedef struct tc_batch tc_batch;
 tc_status tc_batch_create(const uint32_t *edges, const uint64_t *m_per_graph, const uint32_t *n_per_graph, uint32_t k,
                           int edges_on_device, void *cuda_stream, tc_batch **out);
 tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_result *out);
+
+/*
+ * Autotune the batch's intersection schedule: time the candidate schedules
+ * (warp-per-owner cutoff on the owner's out-degree 64 / 128 / 256, work-item
+ * sizes of the warp and block kernels) on this batch with these (p, seed),
+ * keep the fastest for the batch's later counts and remember it for batches
+ * of the same shape (log2 of edges, vertices, graphs and average degree)
+ * created later in this process.  Counts are identical under every
+ * schedule.  desc (may be NULL) receives a short description of the choice.
+ */
+tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, char *desc, uint32_t desc_len);
 void tc_batch_destroy(tc_batch *b); /* NULL-safe */
 uint32_t tc_batch_size(const tc_batch *b);
 uint64_t tc_batch_num_edges(const tc_batch *b);    /* canonical edges of all graphs */

@@ -11,6 +11,9 @@
 // and replayed by each tc_batch_count.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -114,9 +117,10 @@ struct tc_batch {
     double *h_p = nullptr;
     tc_result *h_res = nullptr;
     DevState *h_st = nullptr;
-    // captured launch
+    // captured launch and its intersection schedule
     cudaGraphExec_t exec = nullptr;
     unsigned long long launches_per_run = 0;
+    IsectConfig cfg;
 
     void *alloc(uint64_t b) { return batch_alloc(allocs, bytes, b); }
 };
@@ -179,6 +183,7 @@ void enqueue_batch(tc_batch *b)
     cb.items_cap = b->items_cap;
     cb.st = b->st;
     cb.bv = view_of(b);
+    cb.cfg = b->cfg;
     if (b->m > 0) {
         sample_degree(cb, 0, 0, s);
         partition(cb, s);
@@ -207,6 +212,26 @@ void enqueue_batch(tc_batch *b)
     finalize_batch(cb, b->p, b->res_dev, s);
     cudaMemcpyAsync(b->h_res, b->res_dev, k * sizeof(tc_result), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(b->h_st, b->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+}
+
+// ---- schedule autotuning
+// Shape signature of a batch: floor(log2) of total edges, vertices, graphs
+// and average degree.  Tuned schedules are remembered per signature for the
+// rest of the process.
+uint64_t shape_signature(const tc_batch *b)
+{
+    auto lg = [](uint64_t x) { int r = 0; while (x > 1) { x >>= 1; ++r; } return (uint64_t)r; };
+    const uint64_t avg = b->n ? (2 * b->m) / b->n : 0;
+    return (lg(b->m) << 24) | (lg(b->n) << 16) | (lg(b->k) << 8) | lg(avg);
+}
+
+std::mutex g_tune_mutex;
+std::map<uint64_t, IsectConfig> g_tuned;
+
+void drop_exec(tc_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
 }
 
 tc_status status_of(unsigned err)
@@ -351,6 +376,11 @@ tc_status tc_batch_create(const uint32_t *edges, const uint64_t *m_per_graph, co
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     b->smem_bytes = (int)(slots * 4);
     intersect_prepare(b->smem_bytes);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tuned.find(shape_signature(b));
+        if (it != g_tuned.end()) b->cfg = it->second;
+    }
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         free_batch(b);
         return TC_ECUDA;
@@ -365,9 +395,12 @@ uint32_t tc_batch_size(const tc_batch *b) { return b ? b->k : 0; }
 uint64_t tc_batch_num_edges(const tc_batch *b) { return b ? b->m : 0; }
 uint64_t tc_batch_device_bytes(const tc_batch *b) { return b ? b->bytes : 0; }
 
-tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_result *out)
+}  // extern "C"
+
+namespace {
+
+tc_status stage_params(tc_batch *b, const double *p, const uint64_t *seed)
 {
-    if (!b || !p || !seed || !out) return TC_EINVAL;
     for (uint32_t g = 0; g < b->k; ++g)
         if (!(p[g] > 0.0 && p[g] <= 1.0)) return TC_EINVAL;
     for (uint32_t g = 0; g < b->k; ++g) {
@@ -375,6 +408,12 @@ tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_
         b->h_thr[g] = (uint64_t)(p[g] * 9007199254740992.0);
         b->h_seed_mix[g] = splitmix64(seed[g]);
     }
+    return TC_OK;
+}
+
+// Capture (if needed) and run the batched count once; blocks.
+tc_status run_once(tc_batch *b)
+{
     if (!b->exec) {
         // capture the whole sequence once; replays reuse it
         const uint64_t l0 = tc_launch_count();
@@ -403,9 +442,74 @@ tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_
         cudaGetLastError();
         return TC_ECUDA;
     }
-    const tc_status st = status_of(b->h_st->err);
+    return status_of(b->h_st->err);
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_result *out)
+{
+    if (!b || !p || !seed || !out) return TC_EINVAL;
+    tc_status st = stage_params(b, p, seed);
+    if (st != TC_OK) return st;
+    st = run_once(b);
     if (st != TC_OK) return st;
     std::copy(b->h_res, b->h_res + b->k, out);
+    return TC_OK;
+}
+
+tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, char *desc, uint32_t desc_len)
+{
+    if (!b || !p || !seed) return TC_EINVAL;
+    tc_status st = stage_params(b, p, seed);
+    if (st != TC_OK) return st;
+    const uint32_t warp_maxes[3] = {64, 128, 256}, seg_ws[2] = {256, 512}, seg_bs[2] = {1024, 2048};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    IsectConfig best = b->cfg;
+    float best_ms = 1e30f;
+    for (uint32_t wm : warp_maxes)
+        for (uint32_t sw : seg_ws)
+            for (uint32_t sb : seg_bs) {
+                b->cfg = IsectConfig{wm, sw, sb};
+                drop_exec(b);
+                st = run_once(b);  // capture + warm-up
+                if (st != TC_OK) break;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    cudaEventRecord(e0, b->stream);
+                    add_launches(b->launches_per_run);
+                    cudaGraphLaunch(b->exec, b->stream);
+                    cudaEventRecord(e1, b->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { st = TC_ECUDA; break; }
+                    float t = 0;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    ms = std::min(ms, t);
+                }
+                if (st != TC_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = b->cfg;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    b->cfg = best;
+    drop_exec(b);
+    if (st != TC_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tuned[shape_signature(b)] = best;
+    }
+    if (desc && desc_len)
+        snprintf(desc, desc_len, "warp_max=%u seg_w=%u seg_b=%u best_ms=%.3f", best.warp_max, best.seg_w, best.seg_b,
+                 best_ms);
     return TC_OK;
 }
 

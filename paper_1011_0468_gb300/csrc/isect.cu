@@ -24,22 +24,26 @@
 
 namespace tcg {
 
-constexpr uint32_t SEG_W = 512;   // partners per warp item
-constexpr uint32_t SEG_B = 2048;  // partners per block item
-constexpr uint32_t WARP_MAX = 256, MID_MAX = 1024;
+constexpr uint32_t SEG_B = 2048;     // largest partners per block item (IsectConfig::seg_b)
+constexpr uint32_t WARP_MAX = 256;   // largest warp-owner out-degree (IsectConfig::warp_max)
+constexpr uint32_t MID_MAX = 1024;
 constexpr uint32_t EMPTY = 0xffffffffu;
 constexpr uint32_t GRAB = 8;  // warp items taken per work-cursor atomic
 
-// warp + mid items <= owners + (m_p + in-list entries) / SEG_W
-static uint64_t wm_capacity(uint32_t n, uint64_t m) { return (uint64_t)n + 2 * m / SEG_W + 64; }
+// warp + mid items <= owners + (m_p + in-list entries) / SEG_MIN, for any
+// schedule
+static uint64_t wm_capacity(uint32_t n, uint64_t m) { return (uint64_t)n + 2 * m / SEG_MIN + 64; }
 
 uint64_t items_capacity(uint32_t n, uint64_t m)
 {
     // large items (d+ > MID_MAX, at most m / MID_MAX owners) after the rest
-    return wm_capacity(n, m) + m / MID_MAX + 2 * m / SEG_B + 64;
+    return wm_capacity(n, m) + m / MID_MAX + 2 * m / 256 + 64;
 }
 
-__device__ __forceinline__ uint32_t bucket_of(uint32_t d) { return d <= WARP_MAX ? 0u : (d <= MID_MAX ? 1u : 2u); }
+__device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t warp_max)
+{
+    return d <= warp_max ? 0u : (d <= MID_MAX ? 1u : 2u);
+}
 
 // Item layout: owner in bits 0..31; single graph: segment in bits 32..63;
 // batch union: segment in bits 32..47 and the owner's graph in bits 48..63.
@@ -56,7 +60,8 @@ __device__ __forceinline__ void split_item(uint64_t item, bool batch, uint32_t &
 }
 
 __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ inptr, uint32_t n,
-                        uint64_t *__restrict__ items, uint64_t wm_cap, uint64_t cap, DevState *st, BatchView bv)
+                        uint64_t *__restrict__ items, uint64_t wm_cap, uint64_t cap, DevState *st, BatchView bv,
+                        IsectConfig cfg)
 {
     const bool batch = bv.k != 0;
     const unsigned lane = lane_id();
@@ -69,7 +74,7 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
             if (d >= 2) np = d + (inptr[x + 1] - inptr[x]);
         }
         const uint32_t gx = batch ? find_part_warp(bv.voff, bv.k, (uint32_t)(x < n ? x : n - 1)) : 0u;
-        const uint32_t b = bucket_of(d), seg = b == 0 ? SEG_W : SEG_B;
+        const uint32_t b = bucket_of(d, cfg.warp_max), seg = b == 0 ? cfg.seg_w : cfg.seg_b;
         uint32_t nseg = (np + seg - 1) / seg;
         if (batch && nseg > 0x10000u) {  // segment index must fit 16 bits
             atomicOr(&st->err, ERR_OVERFLOW);
@@ -99,7 +104,7 @@ void build_items(const CountBuffers &b, cudaStream_t s)
 {
     const uint64_t wm = wm_capacity(b.n, b.m);
     k_items<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.inptr, b.n, b.items, wm, b.items_cap, b.st,
-                                                          b.bv);
+                                                          b.bv, b.cfg);
     note_launch();
 }
 
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
                                                            const uint32_t *__restrict__ inlist,
                                                            const uint64_t *__restrict__ items, uint64_t wm_cap,
                                                            const uint8_t *__restrict__ heavy, DevState *st,
-                                                           BatchView bv)
+                                                           BatchView bv, IsectConfig cfg)
 {
     __shared__ uint32_t s_tab[PW_WARPS][WTAB];
     __shared__ uint32_t s_pre[PW_WARPS][32];
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
                 cur_g = g;
             }
             const uint32_t beg = rowptr[x], d = rowptr[x + 1] - beg;
-            if (d > WARP_MAX) {  // cannot happen unless the item list overflowed
+            if (d > cfg.warp_max || d > WARP_MAX) {  // cannot happen unless the item list overflowed
                 if (lane == 0) atomicOr(&st->err, ERR_OVERFLOW);
                 continue;
             }
@@ -341,7 +346,7 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
             __syncwarp();
             if (seg == 0 && lane == 0) t.table += d;
             const uint32_t ib = inptr[x], np = d + (inptr[x + 1] - ib);
-            const uint32_t p0 = seg * SEG_W, p1 = min(np, p0 + SEG_W);
+            const uint32_t p0 = seg * cfg.seg_w, p1 = min(np, p0 + cfg.seg_w);
             for (uint32_t c0 = p0; c0 < p1; c0 += 32) {
                 const uint32_t j = c0 + lane;
                 uint32_t start = 0, len = 0, cls = 0;
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
 
 constexpr int PB_THREADS = 256;
 constexpr int PB_WARPS = PB_THREADS / 32;
-constexpr uint32_t PB_PER_THREAD = SEG_B / PB_THREADS;  // partners set up per thread
+constexpr uint32_t PB_PER_THREAD = SEG_B / PB_THREADS;  // partner slots set up per thread (at most)
 constexpr uint32_t MID_TAB = 4096;                      // >= 4 * MID_MAX slots
 
 // One block resolves one item: up to SEG_B partners of one owner.  Partner
@@ -379,7 +384,8 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_probe_block(const uint32_t *_
                                                             const uint32_t *__restrict__ inlist,
                                                             const uint64_t *__restrict__ items, uint64_t wm_cap,
                                                             const uint8_t *__restrict__ heavy, DevState *st,
-                                                            uint32_t tab_slots, uint64_t cap, BatchView bv)
+                                                            uint32_t tab_slots, uint64_t cap, BatchView bv,
+                                                            IsectConfig cfg)
 {
     extern __shared__ uint32_t s_dyn[];
     __shared__ uint32_t s_static[DYN ? 1 : MID_TAB];
@@ -424,17 +430,18 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_probe_block(const uint32_t *_
         }
         if (seg == 0 && threadIdx.x == 0) t.table += d;
         const uint32_t ib = inptr[x], np = d + (inptr[x + 1] - ib);
-        const uint32_t p0 = seg * SEG_B, p1 = min(np, p0 + SEG_B);
+        const uint32_t p0 = seg * cfg.seg_b, p1 = min(np, p0 + cfg.seg_b);
+        const uint32_t per = cfg.seg_b / PB_THREADS;  // <= PB_PER_THREAD
         // set up this thread's PB_PER_THREAD consecutive partners
         uint32_t pstart[PB_PER_THREAD], plen[PB_PER_THREAD], pcls[PB_PER_THREAD];
         uint32_t mine = 0;  // (long count << 16) | short count
 #pragma unroll
         for (uint32_t q = 0; q < PB_PER_THREAD; ++q) {
-            const uint32_t j = p0 + threadIdx.x * PB_PER_THREAD + q;
+            const uint32_t j = p0 + threadIdx.x * per + q;
             pstart[q] = 0;
             plen[q] = 0;
             pcls[q] = 0;
-            if (j < p1) {
+            if (q < per && j < p1) {
                 const bool is_out = j < d;
                 const uint32_t y = is_out ? __ldg(col + beg + j) : __ldg(inlist + ib + j - d);
                 partner_of(rowptr, heavy, d, hx, y, is_out, skip_heavy, pstart[q], plen[q], pcls[q]);
@@ -515,15 +522,15 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
     if (b.n == 0 || b.m == 0) return;
     const uint64_t wm = wm_capacity(b.n, b.m);
     k_probe_warp<<<152 * 8, PW_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy, b.st,
-                                                b.bv);
+                                                b.bv, b.cfg);
     note_launch();
     k_probe_block<false><<<152 * 8, PB_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy,
-                                                         b.st, MID_TAB, b.items_cap, b.bv);
+                                                         b.st, MID_TAB, b.items_cap, b.bv, b.cfg);
     note_launch();
     intersect_prepare(dyn_smem_bytes);
     k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm,
                                                                 b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
-                                                                b.items_cap, b.bv);
+                                                                b.items_cap, b.bv, b.cfg);
     note_launch();
 }
 

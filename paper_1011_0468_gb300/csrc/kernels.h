@@ -99,6 +99,17 @@ void unique_keys(const uint64_t *keys, uint64_t m_in, uint64_t *out, uint32_t *t
                  uint32_t *scan_scratch, DevState *st, cudaStream_t s);
 
 // ---------------------------------------------------------------- count.cu
+// Schedule of the intersection kernels (isect.cu); any choice gives the same
+// counts.  warp_max: owners with 2 <= d+ <= warp_max are resolved by one warp
+// (32 .. 256); seg_w / seg_b: partners per work item of the warp / block
+// kernels (seg_w in [SEG_MIN, 1024], seg_b in [256, 2048], powers of two).
+constexpr uint32_t SEG_MIN = 128;
+struct IsectConfig {
+    uint32_t warp_max = 256;
+    uint32_t seg_w = 512;
+    uint32_t seg_b = 2048;
+};
+
 struct CountBuffers {
     const uint64_t *ekey;   // canonical keys [m]
     uint64_t m;
@@ -113,6 +124,7 @@ struct CountBuffers {
     uint64_t items_cap;
     DevState *st;
     BatchView bv;           // k > 0: the graph is a batch union
+    IsectConfig cfg;        // intersection schedule
 };
 
 void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaStream_t s);

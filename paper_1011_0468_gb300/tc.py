@@ -70,6 +70,8 @@ SIGNATURES = [
                                         ctypes.POINTER(tc_result), _vp]),
     ("tc_batch_create", ctypes.c_int, [_vp, _u64p, _u32p, ctypes.c_uint32, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     ("tc_batch_count", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _u64p, _vp]),
+    ("tc_batch_autotune", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _u64p, ctypes.c_char_p,
+                                         ctypes.c_uint32]),
     ("tc_batch_destroy", None, [_vp]),
     ("tc_batch_size", ctypes.c_uint32, [_vp]),
     ("tc_batch_num_edges", ctypes.c_uint64, [_vp]),
@@ -343,6 +345,15 @@ class Batch:
     @property
     def device_bytes(self) -> int:
         return int(lib().tc_batch_device_bytes(self.handle))
+
+    def autotune(self, p, seed) -> str:
+        """tc_batch_autotune: pick the fastest intersection schedule."""
+        pa = np.ascontiguousarray(np.broadcast_to(np.asarray(p, dtype=np.float64), (self.k,)))
+        sa = np.ascontiguousarray(np.broadcast_to(np.asarray(seed, dtype=np.uint64), (self.k,)))
+        desc = ctypes.create_string_buffer(256)
+        _check(lib().tc_batch_autotune(self.handle, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       sa.ctypes.data_as(_u64p), desc, 256), "tc_batch_autotune")
+        return desc.value.decode()
 
     def count(self, p, seed) -> np.ndarray:
         """Results of all graphs as a numpy array of RESULT_DTYPE."""

@@ -71,6 +71,20 @@ def test_batch_against_oracle_sample(tc):
             assert res[key][g] == want[key], (g, key)
 
 
+def test_autotuned_schedule_gives_identical_counts(tc):
+    graphs = mixed_graphs()
+    k = len(graphs)
+    p = np.full(k, 0.5)
+    seed = np.arange(7, 7 + k, dtype=np.uint64)
+    with tc.Batch(graphs) as b:
+        before = b.count(p, seed)
+        desc = b.autotune(p, seed)
+        assert "warp_max=" in desc
+        after = b.count(p, seed)
+    for key in KEYS:
+        assert np.array_equal(before[key], after[key]), key
+
+
 def test_batch_rejects_bad_input(tc):
     with pytest.raises(tc.TCError) as e:
         tc.Batch([(np.array([[0, 1]], np.uint32), 2), (np.array([[0, 5]], np.uint32), 5)])
