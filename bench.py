@@ -43,6 +43,13 @@ WORKLOADS = {
                    "core": 16384, "q": 0.7, "m_rest": 4 << 20, "graph_seed": 1, "p_sweep": [1.0]},
     # batched counting: 10000 small uneven graphs, each with its own p and seed
     "batch": {"workload": "batch_10000_er_chunglu2.3", "kind": "batch", "graphs": 10000, "graph_seed": 1},
+    # served counting: Poisson request stream over a pool of resident graphs
+    # drawn like the batched workload plus 1% requests on Chung-Lu m = 2^23
+    "serve": {"workload": "serve_poisson2000_pool2000_plus_chunglu_m8M", "kind": "serve", "rate": 2000.0,
+              "small_graphs": 2000, "large": {"n": 1 << 20, "m": 1 << 23, "gamma": 2.1, "wmax": 35000.0},
+              "large_graphs": 4, "large_frac": 0.01, "budget": 120 * 10 ** 9, "slots": 3,
+              "slot_edges": 1 << 25, "slot_vertices": 1 << 24, "slot_requests": 4096,
+              "saturation_requests": 30000, "graph_seed": 2},
 }
 WORKLOAD = WORKLOADS["chung_lu"]
 METRIC = "sampled edges/s"
@@ -57,6 +64,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of Poisson arrivals")
     return ap.parse_args()
 
 
@@ -418,10 +426,163 @@ def batch_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_requests(w, n_small, duration, seed=7):
+    """The request stream: Poisson arrivals at w["rate"] per second for
+    `duration` seconds; each request names a graph (a large one with
+    probability w["large_frac"], else a uniform small one), p from
+    {0.1, 0.5, 1.0} and a seed."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    k = int(rng.poisson(w["rate"] * duration))
+    t = np.sort(rng.uniform(0.0, duration, size=k))
+    large = rng.random(k) < w["large_frac"]
+    gid = np.where(large, n_small + rng.integers(0, w["large_graphs"], size=k), rng.integers(0, n_small, size=k))
+    p = rng.choice([0.1, 0.5, 1.0], size=k)
+    sd = rng.integers(1, 2 ** 63, size=k, dtype=np.uint64)
+    return t, gid, p, sd
+
+
+def _sleep_until(t_abs):
+    while True:
+        dt = t_abs - time.perf_counter()
+        if dt <= 0:
+            return
+        if dt > 3e-4:
+            time.sleep(dt - 2e-4)
+
+
+def _pct(x, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
+def serve_arm(args):
+    """Served counting (tc_server_*) under a Poisson request stream, against
+    the plain path (one blocking tc_count per request, in arrival order) on
+    the same stream; then both at saturation."""
+    import queue
+    import threading
+    import numpy as np
+    import torch
+    import gen
+    from paper_1011_0468_gb300 import tc
+
+    torch.cuda.set_device(0)
+    tc.lib()
+    w = WORKLOAD
+    specs, small = make_batch_graphs(w["small_graphs"], w["graph_seed"])
+    L = w["large"]
+    large = [gen.cached("chung_lu", gen.chung_lu, L["n"], L["m"], L["gamma"], L["wmax"], 100 + i)
+             for i in range(w["large_graphs"])]
+    pool = [(g, s["n"]) for g, s in zip(small, specs)] + [(g, L["n"]) for g in large]
+    t_arr, gid, p, sd = serve_requests(w, len(small), args.duration)
+    R = len(t_arr)
+    KEYS = ("m_sampled", "n_heavy", "t_light", "t_heavy", "estimate")
+
+    srv = tc.Server(w["budget"], slots=w["slots"], slot_edges=w["slot_edges"], slot_vertices=w["slot_vertices"],
+                    slot_requests=w["slot_requests"])
+    t0 = time.perf_counter()
+    for e, n in pool:
+        srv.add_graph(e, n)
+    t_add = time.perf_counter() - t0
+    # warm-up: every large graph and a few small ones once
+    for t in [srv.submit(len(small) + i, 1.0, 1) for i in range(len(large))] + \
+             [srv.submit(i, 0.5, 1) for i in range(0, len(small), 50)]:
+        srv.wait(t)
+
+    # ---- served: Poisson arrivals, a collector thread waits in ticket order
+    tickets = queue.Queue()
+    served = [None] * R
+
+    def collect():
+        for i in range(R):
+            served[i] = srv.wait(tickets.get(), 600000)
+
+    col = threading.Thread(target=collect)
+    col.start()
+    l0 = tc.tc_launch_count()
+    s0 = srv.stats()
+    with ClockSampler(0) as clocks:
+        base = time.perf_counter() + 0.05
+        for i in range(R):
+            _sleep_until(base + t_arr[i])
+            tickets.put(srv.submit(int(gid[i]), float(p[i]), int(sd[i])))
+        col.join()
+    launches = tc.tc_launch_count() - l0
+    st = srv.stats()
+    lat = np.array([(r["t_done_us"] - r["t_submit_us"]) / 1000.0 for r in served])
+    qwait = np.array([(r["t_admit_us"] - r["t_submit_us"]) / 1000.0 for r in served])
+    span = (max(r["t_done_us"] for r in served) - min(r["t_submit_us"] for r in served)) / 1e6
+    waves = st["waves"] - s0["waves"]
+
+    # ---- plain: one blocking tc_count per request in arrival order
+    objs = [tc.Graph(e, n) for e, n in pool]
+    for o in objs[len(small):]:
+        o.count(1.0, 1)
+    plain_lat = np.zeros(R)
+    plain_res = [None] * R
+    base = time.perf_counter() + 0.05
+    for i in range(R):
+        arr = base + t_arr[i]
+        _sleep_until(arr)
+        plain_res[i] = objs[gid[i]].count(float(p[i]), int(sd[i]))
+        plain_lat[i] = (time.perf_counter() - arr) * 1000.0
+    plain_span = time.perf_counter() - base
+    identical = all(served[i]["status"] == 0 and all(served[i][k] == plain_res[i][k] for k in KEYS)
+                    for i in range(R))
+
+    # ---- saturation: the first S requests all at once
+    S = min(R, w["saturation_requests"])
+    t0 = time.perf_counter()
+    tk = [srv.submit(int(gid[i]), float(p[i]), int(sd[i])) for i in range(S)]
+    sat = [srv.wait(t, 600000) for t in tk]
+    t_sat = time.perf_counter() - t0
+    sat_identical = all(sat[i][k] == served[i][k] for i in range(S) for k in KEYS)
+    buf = torch.zeros((S, ctypes.sizeof(tc.tc_result)), dtype=torch.uint8, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(S):
+        objs[gid[i]].count_async(float(p[i]), int(sd[i]), buf[i].data_ptr())
+    for o in objs:
+        o.sync()
+    t_plain_sat = time.perf_counter() - t0
+    for o in objs:
+        o.close()
+    srv.close()
+
+    edges = np.array([len(e) for e, _ in pool], dtype=np.float64)
+    line = {"metric": "served requests/s", "value": R / span, "unit": "requests/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": 1000.0 * span, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": w["workload"], "requests": R, "rate_per_s": w["rate"],
+                       "duration_s": args.duration, "pool_graphs": len(pool),
+                       "pool_input_edges": int(edges.sum()), "large_frac": w["large_frac"],
+                       "budget_bytes": w["budget"], "slots": w["slots"], "slot_edges": w["slot_edges"],
+                       "slot_requests": w["slot_requests"]},
+            "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "mean": float(lat.mean()),
+                           "max": float(lat.max()), "queue_p50": _pct(qwait, 50), "queue_p99": _pct(qwait, 99)},
+            "plain": {"latency_ms": {"p50": _pct(plain_lat, 50), "p99": _pct(plain_lat, 99),
+                                     "mean": float(plain_lat.mean()), "max": float(plain_lat.max())},
+                      "value": R / plain_span, "path": "one blocking tc_count per request, arrival order"},
+            "identical_to_plain": bool(identical),
+            "saturation": {"requests": S, "served_per_s": S / t_sat, "plain_per_s": S / t_plain_sat,
+                           "speedup_vs_plain": t_plain_sat / t_sat, "identical": bool(sat_identical),
+                           "plain_path": "one tc_count_async per request, graphs resident"},
+            "server": {"waves": waves, "mean_wave": R / max(waves, 1), "max_wave": st["max_wave"],
+                       "resident_bytes": st["resident_bytes"], "slot_bytes": st["slot_bytes"],
+                       "uploads": st["uploads"], "evictions": st["evictions"], "add_graph_s": t_add},
+            "gpu_launches": int(launches), "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global WORKLOAD
     args = parse_args()
     WORKLOAD = WORKLOADS[args.workload]
+    if WORKLOAD["kind"] == "serve":
+        if args.impl == "ours":
+            serve_arm(args)
+        return
     if WORKLOAD["kind"] == "batch":
         if args.impl == "ours":
             batch_arm(args)

@@ -212,6 +212,83 @@ uint64_t tc_batch_num_edges(const tc_batch *b);    /* canonical edges of all gra
 uint64_t tc_batch_device_bytes(const tc_batch *b);
 
 /*
+ * Serving: count requests (graph, p, seed) as they arrive, with continuous
+ * batching.  The paper states the problem for one graph and one (p, seed)
+ * at a time (Sections 1 and 3.1); the server only changes how many such
+ * problems share a launch, never a result: every request gets exactly what
+ * tc_graph_create + tc_count on its graph would return.
+ *
+ * Graphs are registered once (tc_server_add_graph) and kept resident in
+ * device memory as canonical edge lists, with a pinned host copy.  A
+ * worker thread owns `slots` count slots, each with its own stream and
+ * scratch for a union of up to slot_edges edges, slot_vertices vertices and
+ * slot_requests requests.  Whenever a slot is free and requests are queued,
+ * the worker admits the longest prefix of the queue (first come, first
+ * served) that fits the slot and whose graphs are (or can be made)
+ * resident, gathers their edge lists into the slot's union and runs the
+ * batched count there; requests that arrive meanwhile wait for the next
+ * free slot, and the slots' counts overlap on the device.
+ *
+ * HBM budget: slot scratch plus resident graphs never exceed budget_bytes.
+ * A graph that is not resident when a request needs it is uploaded again
+ * from its host copy, first evicting the least recently used graphs that no
+ * slot is using; if that still leaves no room, the request waits in the
+ * queue until running counts release their graphs.
+ *
+ * tc_server_create
+ *   budget_bytes   device bytes the server may hold (slots + graphs)
+ *   slots          1 .. 8
+ *   slot_edges     canonical edges of one slot's union (>= 1)
+ *   slot_vertices  vertices of one slot's union (1 .. 2^32 - 2)
+ *   slot_requests  requests of one slot's union (1 .. 65535)
+ * Errors: TC_EINVAL (bad sizes), TC_ENOMEM (the slots alone exceed the
+ * budget, or an allocation failed), TC_ECUDA.
+ *
+ * tc_server_add_graph  edges as for tc_graph_create (host or device
+ *   memory, local ids [0, n), repeats and self-loops allowed); blocks until
+ *   the graph is canonical and stored; *gid receives its id.  TC_EINVAL
+ *   also when the graph alone exceeds a slot's edge or vertex capacity,
+ *   TC_ENOMEM when it exceeds the budget left after the slots.
+ *
+ * tc_server_submit  queue one request; returns at once with *ticket.
+ *   TC_EINVAL for an unknown gid or p outside (0, 1].
+ *
+ * tc_server_poll  TC_OK: the request is done and *info holds its result
+ *   (info->status is its own status; the ticket is then released);
+ *   TC_EBUSY: still queued or running; TC_EINVAL: unknown ticket.
+ * tc_server_wait  as poll, blocking up to timeout_ms (TC_EBUSY after it).
+ *
+ * Times in tc_request_info are microseconds since tc_server_create on the
+ * host's steady clock: t_submit when submit was called, t_admit when its
+ * slot launch was enqueued, t_done when the worker saw that launch finish.
+ */
+typedef struct tc_server tc_server;
+typedef struct {
+    tc_result res;       /* ms[] is zero */
+    int32_t status;      /* tc_status of this request */
+    uint32_t wave_size;  /* requests counted in the same slot launch */
+    double t_submit_us, t_admit_us, t_done_us;
+} tc_request_info;
+typedef struct {
+    uint64_t submitted, completed, queued;  /* queued: submitted, not yet admitted */
+    uint64_t waves, max_wave;               /* slot launches; most requests in one */
+    uint64_t resident_graphs, resident_bytes, graphs;
+    uint64_t slot_bytes, budget_bytes;
+    uint64_t uploads, evictions;            /* re-uploads after eviction; evictions */
+} tc_server_stats;
+tc_status tc_server_create(uint64_t budget_bytes, uint32_t slots, uint64_t slot_edges, uint32_t slot_vertices,
+                           uint32_t slot_requests, tc_server **out);
+tc_status tc_server_add_graph(tc_server *srv, const uint32_t *edges, uint64_t m_in, uint32_t n, int edges_on_device,
+                              uint32_t *gid);
+tc_status tc_server_submit(tc_server *srv, uint32_t gid, double p, uint64_t seed, uint64_t *ticket);
+tc_status tc_server_poll(tc_server *srv, uint64_t ticket, tc_request_info *info);
+tc_status tc_server_wait(tc_server *srv, uint64_t ticket, uint32_t timeout_ms, tc_request_info *info);
+tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *out);
+/* Stops the worker after the requests already admitted finish; queued ones
+   are dropped.  NULL-safe. */
+void tc_server_destroy(tc_server *srv);
+
+/*
  * Count without allocating (the paper has no counterpart: this exists for
  * callers that cannot allocate device memory, such as a host framework
  * whose memory pool already owns the GPU, or code where a device allocation

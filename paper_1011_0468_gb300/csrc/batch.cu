@@ -6,9 +6,9 @@
 // them.  Each edge is sampled with its own graph's (p, seed) on its
 // graph-local key, each vertex is split against its own graph's m_p, and the
 // class counts go to per-graph counters: every graph gets exactly the
-// result a separate tc_count would give.  The whole sequence (parameter
-// upload, ~40 kernels, result download) is captured once into a CUDA graph
-// and replayed by each tc_batch_count.
+// result a separate tc_count would give.  For tc_batch the whole sequence
+// (parameter upload, ~33 kernels, result download) is captured once into a
+// CUDA graph and replayed by each tc_batch_count.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -75,7 +75,7 @@ __global__ void k_batch_eoff(const uint64_t *__restrict__ keys, uint64_t m, cons
     eoff[g] = lo;
 }
 
-void *batch_alloc(std::vector<void *> &allocs, uint64_t &total, uint64_t bytes)
+void *dev_alloc_track(std::vector<void *> &allocs, uint64_t &total, uint64_t bytes)
 {
     void *p = nullptr;
     bytes = std::max<uint64_t>(bytes, 256);
@@ -88,30 +88,120 @@ void *batch_alloc(std::vector<void *> &allocs, uint64_t &total, uint64_t bytes)
     return p;
 }
 
+BatchView view_of(const UnionScratch &u, uint32_t k)
+{
+    BatchView bv;
+    bv.k = k;
+    bv.eoff = u.eoff;
+    bv.voff = u.voff;
+    bv.thr = u.thr;
+    bv.seed_mix = u.seed_mix;
+    bv.m_p = u.counters;
+    bv.t_light = u.counters + u.k_cap;
+    bv.t_heavy = u.counters + 2 * (uint64_t)u.k_cap;
+    bv.n_heavy = reinterpret_cast<unsigned int *>(u.counters + 3 * (uint64_t)u.k_cap);
+    return bv;
+}
+
 }  // namespace
+
+namespace tcg {
+
+bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32_t k_cap, std::vector<void *> &allocs,
+                         uint64_t &bytes)
+{
+    u.m_cap = m_cap;
+    u.n_cap = n_cap;
+    u.k_cap = k_cap;
+    const uint64_t m1 = std::max<uint64_t>(m_cap, 1);
+    const uint64_t nt = std::max<uint64_t>(ceil_div(m1, RX_TILE), 1);
+    const uint64_t hist_len = nt << RX_MAX_BITS;
+    u.ekey = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
+    u.bufA = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
+    u.bufB = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
+    u.deg = (uint32_t *)dev_alloc_track(allocs, bytes, (uint64_t)n_cap * 4);
+    u.rowptr = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)n_cap + 1) * 4);
+    u.inptr = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)n_cap + 2) * 4);
+    u.heavy = (uint8_t *)dev_alloc_track(allocs, bytes, n_cap);
+    u.items_cap = items_capacity(n_cap, m1);
+    u.items = (uint64_t *)dev_alloc_track(allocs, bytes, u.items_cap * 8);
+    u.hist = (uint32_t *)dev_alloc_track(allocs, bytes, hist_len * 4);
+    u.scan = (uint32_t *)dev_alloc_track(allocs, bytes,
+                                         scan_scratch_elems(std::max<uint64_t>(hist_len, (uint64_t)n_cap + 2)) * 4);
+    u.st = (DevState *)dev_alloc_track(allocs, bytes, sizeof(DevState));
+    u.eoff = (uint64_t *)dev_alloc_track(allocs, bytes, ((uint64_t)k_cap + 1) * 8);
+    u.voff = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)k_cap + 1) * 4);
+    u.thr = (uint64_t *)dev_alloc_track(allocs, bytes, (uint64_t)k_cap * 8);
+    u.seed_mix = (uint64_t *)dev_alloc_track(allocs, bytes, (uint64_t)k_cap * 8);
+    u.p = (double *)dev_alloc_track(allocs, bytes, (uint64_t)k_cap * 8);
+    u.counters = (unsigned long long *)dev_alloc_track(allocs, bytes, (uint64_t)k_cap * 28 + 8);
+    u.res_dev = (tc_result *)dev_alloc_track(allocs, bytes, (uint64_t)k_cap * sizeof(tc_result));
+    // every out-degree of any graph of the union is below sqrt(2 m_cap)
+    const uint64_t dmax = (uint64_t)std::sqrt(2.0 * (double)m1) + 2;
+    uint64_t slots = 8192;
+    while (slots < 4 * dmax && slots < 32768) slots <<= 1;
+    u.smem_bytes = (int)(slots * 4);
+    intersect_prepare(u.smem_bytes);
+    return u.ekey && u.bufA && u.bufB && u.deg && u.rowptr && u.inptr && u.heavy && u.items && u.hist && u.scan &&
+           u.st && u.eoff && u.voff && u.thr && u.seed_mix && u.p && u.counters && u.res_dev;
+}
+
+void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const IsectConfig &cfg, cudaStream_t s)
+{
+    cudaMemsetAsync(u.st, 0, sizeof(DevState), s);
+    cudaMemsetAsync(u.deg, 0, (size_t)n * 4, s);
+    cudaMemsetAsync(u.counters, 0, (uint64_t)u.k_cap * 28, s);
+    CountBuffers cb;
+    cb.ekey = u.ekey;
+    cb.m = m;
+    cb.n = n;
+    cb.deg = u.deg;
+    cb.heavy = u.heavy;
+    cb.rowptr = u.rowptr;
+    cb.col = nullptr;
+    cb.inptr = u.inptr;
+    cb.inlist = nullptr;
+    cb.items = u.items;
+    cb.items_cap = items_capacity(n, std::max<uint64_t>(m, 1));
+    cb.st = u.st;
+    cb.bv = view_of(u, k);
+    cb.cfg = cfg;
+    if (m > 0) {
+        sample_degree(cb, 0, 0, s);
+        partition(cb, s);
+        CsrArgs a;
+        a.ekey = u.ekey;
+        a.m = m;
+        a.n = n;
+        a.nbits = batch_bits(n);
+        a.deg = u.deg;
+        a.seed_mix = 0;
+        a.thr = 0;
+        a.bv = cb.bv;
+        a.m_sampled_dev = &u.st->m_sampled;
+        a.bufA = u.bufA;
+        a.bufB = u.bufB;
+        a.rowptr = u.rowptr;
+        a.inptr = u.inptr;
+        a.hist = u.hist;
+        a.scan = u.scan;
+        csr_build(a, &cb.col, &cb.inlist, s);
+        build_items(cb, s);
+        intersect(cb, u.smem_bytes, s);
+    }
+    finalize_batch(cb, u.p, u.res_dev, s);
+}
+
+}  // namespace tcg
 
 struct tc_batch {
     uint32_t k = 0, n = 0;
     uint64_t m = 0;
-    int nbits = 1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int smem_bytes = 0;
     uint64_t bytes = 0;
     std::vector<void *> allocs;
-    // union and scratch
-    uint64_t *ekey = nullptr, *bufA = nullptr, *bufB = nullptr, *items = nullptr;
-    uint64_t items_cap = 0;
-    uint32_t *deg = nullptr, *rowptr = nullptr, *inptr = nullptr, *hist = nullptr, *scan = nullptr;
-    uint32_t *col = nullptr, *inlist = nullptr;
-    uint8_t *heavy = nullptr;
-    DevState *st = nullptr;
-    // per graph
-    uint64_t *eoff = nullptr, *thr = nullptr, *seed_mix = nullptr;
-    uint32_t *voff = nullptr;
-    double *p = nullptr;
-    unsigned long long *counters = nullptr;  // m_p[k], t_light[k], t_heavy[k], then n_heavy[k] (uint32)
-    tc_result *res_dev = nullptr;
+    UnionScratch u;
     // pinned staging
     uint64_t *h_thr = nullptr, *h_seed_mix = nullptr;
     double *h_p = nullptr;
@@ -121,8 +211,6 @@ struct tc_batch {
     cudaGraphExec_t exec = nullptr;
     unsigned long long launches_per_run = 0;
     IsectConfig cfg;
-
-    void *alloc(uint64_t b) { return batch_alloc(allocs, bytes, b); }
 };
 
 namespace {
@@ -143,75 +231,17 @@ void free_batch(tc_batch *b)
     delete b;
 }
 
-BatchView view_of(tc_batch *b)
-{
-    BatchView bv;
-    bv.k = b->k;
-    bv.eoff = b->eoff;
-    bv.voff = b->voff;
-    bv.thr = b->thr;
-    bv.seed_mix = b->seed_mix;
-    bv.m_p = b->counters;
-    bv.t_light = b->counters + b->k;
-    bv.t_heavy = b->counters + 2 * (uint64_t)b->k;
-    bv.n_heavy = reinterpret_cast<unsigned int *>(b->counters + 3 * (uint64_t)b->k);
-    return bv;
-}
-
 // The whole batched count, stream-ordered (captured into a CUDA graph).
 void enqueue_batch(tc_batch *b)
 {
     cudaStream_t s = b->stream;
     const uint64_t k = b->k;
-    cudaMemsetAsync(b->st, 0, sizeof(DevState), s);
-    cudaMemsetAsync(b->deg, 0, (size_t)b->n * 4, s);
-    cudaMemsetAsync(b->counters, 0, k * 28, s);
-    cudaMemcpyAsync(b->thr, b->h_thr, k * 8, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(b->seed_mix, b->h_seed_mix, k * 8, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(b->p, b->h_p, k * 8, cudaMemcpyHostToDevice, s);
-    CountBuffers cb;
-    cb.ekey = b->ekey;
-    cb.m = b->m;
-    cb.n = b->n;
-    cb.deg = b->deg;
-    cb.heavy = b->heavy;
-    cb.rowptr = b->rowptr;
-    cb.col = nullptr;
-    cb.inptr = b->inptr;
-    cb.inlist = nullptr;
-    cb.items = b->items;
-    cb.items_cap = b->items_cap;
-    cb.st = b->st;
-    cb.bv = view_of(b);
-    cb.cfg = b->cfg;
-    if (b->m > 0) {
-        sample_degree(cb, 0, 0, s);
-        partition(cb, s);
-        CsrArgs a;
-        a.ekey = b->ekey;
-        a.m = b->m;
-        a.n = b->n;
-        a.nbits = b->nbits;
-        a.deg = b->deg;
-        a.seed_mix = 0;
-        a.thr = 0;
-        a.bv = cb.bv;
-        a.m_sampled_dev = &b->st->m_sampled;
-        a.bufA = b->bufA;
-        a.bufB = b->bufB;
-        a.rowptr = b->rowptr;
-        a.inptr = b->inptr;
-        a.hist = b->hist;
-        a.scan = b->scan;
-        csr_build(a, &b->col, &b->inlist, s);
-        cb.col = b->col;
-        cb.inlist = b->inlist;
-        build_items(cb, s);
-        intersect(cb, b->smem_bytes, s);
-    }
-    finalize_batch(cb, b->p, b->res_dev, s);
-    cudaMemcpyAsync(b->h_res, b->res_dev, k * sizeof(tc_result), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(b->h_st, b->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(b->u.thr, b->h_thr, k * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->u.seed_mix, b->h_seed_mix, k * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->u.p, b->h_p, k * 8, cudaMemcpyHostToDevice, s);
+    union_count(b->u, b->m, b->n, b->k, b->cfg, s);
+    cudaMemcpyAsync(b->h_res, b->u.res_dev, k * sizeof(tc_result), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(b->h_st, b->u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
 }
 
 // ---- schedule autotuning
@@ -220,7 +250,14 @@ void enqueue_batch(tc_batch *b)
 // rest of the process.
 uint64_t shape_signature(const tc_batch *b)
 {
-    auto lg = [](uint64_t x) { int r = 0; while (x > 1) { x >>= 1; ++r; } return (uint64_t)r; };
+    auto lg = [](uint64_t x) {
+        uint64_t r = 0;
+        while (x > 1) {
+            x >>= 1;
+            ++r;
+        }
+        return r;
+    };
     const uint64_t avg = b->n ? (2 * b->m) / b->n : 0;
     return (lg(b->m) << 24) | (lg(b->n) << 16) | (lg(b->k) << 8) | lg(avg);
 }
@@ -242,163 +279,6 @@ tc_status status_of(unsigned err)
     return TC_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-tc_status tc_batch_create(const uint32_t *edges, const uint64_t *m_per_graph, const uint32_t *n_per_graph, uint32_t k,
-                          int edges_on_device, void *cuda_stream, tc_batch **out)
-{
-    if (!out) return TC_EINVAL;
-    *out = nullptr;
-    if (k == 0 || k > 0xffffu || !m_per_graph || !n_per_graph) return TC_EINVAL;
-    std::vector<uint64_t> in_off(k + 1, 0);
-    std::vector<uint32_t> voff(k + 1, 0);
-    uint64_t n_total = 0;
-    for (uint32_t g = 0; g < k; ++g) {
-        if (n_per_graph[g] == 0) return TC_EINVAL;
-        in_off[g + 1] = in_off[g] + m_per_graph[g];
-        n_total += n_per_graph[g];
-        if (n_total >= 0xffffffffull) return TC_EINVAL;
-        voff[g + 1] = (uint32_t)n_total;
-    }
-    const uint64_t m_in = in_off[k];
-    if (m_in > 0xfffffffeull || (m_in > 0 && !edges)) return TC_EINVAL;
-
-    tc_batch *b = new (std::nothrow) tc_batch;
-    if (!b) return TC_ENOMEM;
-    b->k = k;
-    b->n = (uint32_t)n_total;
-    b->nbits = batch_bits(b->n);
-    if (cuda_stream) {
-        b->stream = (cudaStream_t)cuda_stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            delete b;
-            return TC_ECUDA;
-        }
-        b->own_stream = true;
-    }
-    cudaStream_t s = b->stream;
-    if (cudaMallocHost((void **)&b->h_thr, k * 8) != cudaSuccess ||
-        cudaMallocHost((void **)&b->h_seed_mix, k * 8) != cudaSuccess ||
-        cudaMallocHost((void **)&b->h_p, k * 8) != cudaSuccess ||
-        cudaMallocHost((void **)&b->h_res, k * sizeof(tc_result)) != cudaSuccess ||
-        cudaMallocHost((void **)&b->h_st, sizeof(DevState)) != cudaSuccess) {
-        cudaGetLastError();
-        free_batch(b);
-        return TC_ENOMEM;
-    }
-    b->st = (DevState *)b->alloc(sizeof(DevState));
-    b->voff = (uint32_t *)b->alloc((k + 1) * 4ull);
-    b->eoff = (uint64_t *)b->alloc((k + 1) * 8ull);
-    if (!b->st || !b->voff || !b->eoff) { free_batch(b); return TC_ENOMEM; }
-    cudaMemsetAsync(b->st, 0, sizeof(DevState), s);
-    cudaMemcpyAsync(b->voff, voff.data(), (k + 1) * 4ull, cudaMemcpyHostToDevice, s);
-
-    // ---- union keys: offset, canonicalise, sort, deduplicate
-    uint64_t m = 0;
-    if (m_in > 0) {
-        std::vector<void *> tmp;
-        uint64_t tmp_bytes = 0;
-        const uint32_t *dpairs = edges;
-        if (!edges_on_device) {
-            void *p = batch_alloc(tmp, tmp_bytes, m_in * 8);
-            if (!p) { free_batch(b); return TC_ENOMEM; }
-            cudaMemcpyAsync(p, edges, m_in * 8, cudaMemcpyHostToDevice, s);
-            dpairs = (const uint32_t *)p;
-        }
-        uint64_t *d_in_off = (uint64_t *)batch_alloc(tmp, tmp_bytes, (k + 1) * 8ull);
-        uint64_t *keys = (uint64_t *)batch_alloc(tmp, tmp_bytes, m_in * 8);
-        uint64_t *keys2 = (uint64_t *)batch_alloc(tmp, tmp_bytes, m_in * 8);
-        const uint64_t nt = ceil_div(m_in, RX_TILE);
-        uint32_t *hist = (uint32_t *)batch_alloc(tmp, tmp_bytes, (nt << RX_MAX_BITS) * 4);
-        uint32_t *scan = (uint32_t *)batch_alloc(tmp, tmp_bytes, scan_scratch_elems(nt << RX_MAX_BITS) * 4);
-        b->ekey = (uint64_t *)b->alloc(m_in * 8);
-        auto drop_tmp = [&]() { cudaStreamSynchronize(s); for (void *p : tmp) cudaFree(p); tmp.clear(); };
-        if (!d_in_off || !keys || !keys2 || !hist || !scan || !b->ekey) { drop_tmp(); free_batch(b); return TC_ENOMEM; }
-        cudaMemcpyAsync(d_in_off, in_off.data(), (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
-        k_batch_keys<<<grid_for(m_in, 256, 152 * 16), 256, 0, s>>>(dpairs, m_in, d_in_off, b->voff, k, keys, b->st);
-        note_launch();
-        uint64_t *a = keys, *c = keys2;
-        for (int half = 0; half < 2; ++half) {
-            int shift = half ? 32 : 0;
-            const int P = (b->nbits + RX_MAX_BITS - 1) / RX_MAX_BITS;
-            for (int i = 0; i < P; ++i) {
-                const int w = b->nbits / P + (i < b->nbits % P ? 1 : 0);
-                ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
-                radix_pass(src, m_in, shift, w, hist, scan, nullptr, c, nullptr, nullptr, s);
-                std::swap(a, c);
-                shift += w;
-            }
-        }
-        unique_keys(a, m_in, b->ekey, hist, scan, b->st, s);
-        cudaMemcpyAsync(b->h_st, b->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); drop_tmp(); free_batch(b); return TC_ECUDA; }
-        drop_tmp();
-        if (b->h_st->err & ERR_ENDPOINT) { free_batch(b); return TC_EINVAL; }
-        m = b->h_st->m_canon;
-    } else {
-        b->ekey = (uint64_t *)b->alloc(8);
-        if (!b->ekey) { free_batch(b); return TC_ENOMEM; }
-    }
-    b->m = m;
-    k_batch_eoff<<<(k + 1 + 127) / 128, 128, 0, s>>>(b->ekey, m, b->voff, k, b->eoff);
-    note_launch();
-
-    // ---- scratch of the count, sized for p = 1
-    const uint64_t nt = std::max<uint64_t>(ceil_div(m, RX_TILE), 1);
-    const uint64_t hist_len = nt << RX_MAX_BITS;
-    b->bufA = (uint64_t *)b->alloc(std::max<uint64_t>(m, 1) * 8);
-    b->bufB = (uint64_t *)b->alloc(std::max<uint64_t>(m, 1) * 8);
-    b->deg = (uint32_t *)b->alloc((uint64_t)b->n * 4);
-    b->rowptr = (uint32_t *)b->alloc(((uint64_t)b->n + 1) * 4);
-    b->inptr = (uint32_t *)b->alloc(((uint64_t)b->n + 2) * 4);
-    b->heavy = (uint8_t *)b->alloc(b->n);
-    b->items_cap = items_capacity(b->n, m);
-    b->items = (uint64_t *)b->alloc(b->items_cap * 8);
-    b->hist = (uint32_t *)b->alloc(hist_len * 4);
-    b->scan = (uint32_t *)b->alloc(scan_scratch_elems(std::max<uint64_t>(hist_len, (uint64_t)b->n + 2)) * 4);
-    b->thr = (uint64_t *)b->alloc(k * 8ull);
-    b->seed_mix = (uint64_t *)b->alloc(k * 8ull);
-    b->p = (double *)b->alloc(k * 8ull);
-    b->counters = (unsigned long long *)b->alloc(k * 28ull + 8);
-    b->res_dev = (tc_result *)b->alloc(k * sizeof(tc_result));
-    if (!b->bufA || !b->bufB || !b->deg || !b->rowptr || !b->inptr || !b->heavy || !b->items || !b->hist ||
-        !b->scan || !b->thr || !b->seed_mix || !b->p || !b->counters || !b->res_dev) {
-        free_batch(b);
-        return TC_ENOMEM;
-    }
-    // largest out-degree of any graph is below sqrt(2 m)
-    const uint64_t dmax = (uint64_t)std::sqrt(2.0 * (double)std::max<uint64_t>(m, 1)) + 2;
-    uint64_t slots = 8192;
-    while (slots < 4 * dmax && slots < 32768) slots <<= 1;
-    b->smem_bytes = (int)(slots * 4);
-    intersect_prepare(b->smem_bytes);
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tuned.find(shape_signature(b));
-        if (it != g_tuned.end()) b->cfg = it->second;
-    }
-    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-        free_batch(b);
-        return TC_ECUDA;
-    }
-    *out = b;
-    return TC_OK;
-}
-
-void tc_batch_destroy(tc_batch *b) { free_batch(b); }
-
-uint32_t tc_batch_size(const tc_batch *b) { return b ? b->k : 0; }
-uint64_t tc_batch_num_edges(const tc_batch *b) { return b ? b->m : 0; }
-uint64_t tc_batch_device_bytes(const tc_batch *b) { return b ? b->bytes : 0; }
-
-}  // extern "C"
-
-namespace {
-
 tc_status stage_params(tc_batch *b, const double *p, const uint64_t *seed)
 {
     for (uint32_t g = 0; g < b->k; ++g)
@@ -415,7 +295,6 @@ tc_status stage_params(tc_batch *b, const double *p, const uint64_t *seed)
 tc_status run_once(tc_batch *b)
 {
     if (!b->exec) {
-        // capture the whole sequence once; replays reuse it
         const uint64_t l0 = tc_launch_count();
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -449,6 +328,123 @@ tc_status run_once(tc_batch *b)
 
 extern "C" {
 
+tc_status tc_batch_create(const uint32_t *edges, const uint64_t *m_per_graph, const uint32_t *n_per_graph, uint32_t k,
+                          int edges_on_device, void *cuda_stream, tc_batch **out)
+{
+    if (!out) return TC_EINVAL;
+    *out = nullptr;
+    if (k == 0 || k > 0xffffu || !m_per_graph || !n_per_graph) return TC_EINVAL;
+    std::vector<uint64_t> in_off(k + 1, 0);
+    std::vector<uint32_t> voff(k + 1, 0);
+    uint64_t n_total = 0;
+    for (uint32_t g = 0; g < k; ++g) {
+        if (n_per_graph[g] == 0) return TC_EINVAL;
+        in_off[g + 1] = in_off[g] + m_per_graph[g];
+        n_total += n_per_graph[g];
+        if (n_total >= 0xffffffffull) return TC_EINVAL;
+        voff[g + 1] = (uint32_t)n_total;
+    }
+    const uint64_t m_in = in_off[k];
+    if (m_in > 0xfffffffeull || (m_in > 0 && !edges)) return TC_EINVAL;
+
+    tc_batch *b = new (std::nothrow) tc_batch;
+    if (!b) return TC_ENOMEM;
+    b->k = k;
+    b->n = (uint32_t)n_total;
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return TC_ECUDA;
+        }
+        b->own_stream = true;
+    }
+    cudaStream_t s = b->stream;
+    if (cudaMallocHost((void **)&b->h_thr, k * 8) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_seed_mix, k * 8) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_p, k * 8) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_res, k * sizeof(tc_result)) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_st, sizeof(DevState)) != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        return TC_ENOMEM;
+    }
+    // scratch of the count, sized for p = 1 (m_in bounds the canonical m)
+    if (!union_scratch_alloc(b->u, m_in, b->n, k, b->allocs, b->bytes)) {
+        free_batch(b);
+        return TC_ENOMEM;
+    }
+    cudaMemsetAsync(b->u.st, 0, sizeof(DevState), s);
+    cudaMemcpyAsync(b->u.voff, voff.data(), (k + 1) * 4ull, cudaMemcpyHostToDevice, s);
+
+    // ---- union keys: offset, canonicalise, sort, deduplicate (into u.ekey)
+    uint64_t m = 0;
+    if (m_in > 0) {
+        std::vector<void *> tmp;
+        uint64_t tmp_bytes = 0;
+        const uint32_t *dpairs = edges;
+        if (!edges_on_device) {
+            void *p = dev_alloc_track(tmp, tmp_bytes, m_in * 8);
+            if (!p) { free_batch(b); return TC_ENOMEM; }
+            cudaMemcpyAsync(p, edges, m_in * 8, cudaMemcpyHostToDevice, s);
+            dpairs = (const uint32_t *)p;
+        }
+        uint64_t *d_in_off = (uint64_t *)dev_alloc_track(tmp, tmp_bytes, (k + 1) * 8ull);
+        auto drop_tmp = [&]() {
+            cudaStreamSynchronize(s);
+            for (void *p : tmp) cudaFree(p);
+            tmp.clear();
+        };
+        if (!d_in_off) { drop_tmp(); free_batch(b); return TC_ENOMEM; }
+        cudaMemcpyAsync(d_in_off, in_off.data(), (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
+        // keys go to bufA, the sort ping-pongs with bufB, unique writes ekey
+        k_batch_keys<<<grid_for(m_in, 256, 152 * 16), 256, 0, s>>>(dpairs, m_in, d_in_off, b->u.voff, k, b->u.bufA,
+                                                                   b->u.st);
+        note_launch();
+        uint64_t *a = b->u.bufA, *c = b->u.bufB;
+        const int nbits = batch_bits(b->n);
+        for (int half = 0; half < 2; ++half) {
+            int shift = half ? 32 : 0;
+            const int P = (nbits + RX_MAX_BITS - 1) / RX_MAX_BITS;
+            for (int i = 0; i < P; ++i) {
+                const int w = nbits / P + (i < nbits % P ? 1 : 0);
+                ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
+                radix_pass(src, m_in, shift, w, b->u.hist, b->u.scan, nullptr, c, nullptr, nullptr, s);
+                std::swap(a, c);
+                shift += w;
+            }
+        }
+        unique_keys(a, m_in, b->u.ekey, b->u.hist, b->u.scan, b->u.st, s);
+        cudaMemcpyAsync(b->h_st, b->u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); drop_tmp(); free_batch(b); return TC_ECUDA; }
+        drop_tmp();
+        if (b->h_st->err & ERR_ENDPOINT) { free_batch(b); return TC_EINVAL; }
+        m = b->h_st->m_canon;
+    }
+    b->m = m;
+    k_batch_eoff<<<(k + 1 + 127) / 128, 128, 0, s>>>(b->u.ekey, m, b->u.voff, k, b->u.eoff);
+    note_launch();
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tuned.find(shape_signature(b));
+        if (it != g_tuned.end()) b->cfg = it->second;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        free_batch(b);
+        return TC_ECUDA;
+    }
+    *out = b;
+    return TC_OK;
+}
+
+void tc_batch_destroy(tc_batch *b) { free_batch(b); }
+
+uint32_t tc_batch_size(const tc_batch *b) { return b ? b->k : 0; }
+uint64_t tc_batch_num_edges(const tc_batch *b) { return b ? b->m : 0; }
+uint64_t tc_batch_device_bytes(const tc_batch *b) { return b ? b->bytes : 0; }
+
 tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_result *out)
 {
     if (!b || !p || !seed || !out) return TC_EINVAL;
@@ -476,6 +472,7 @@ tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, 
     for (uint32_t wm : warp_maxes)
         for (uint32_t sw : seg_ws)
             for (uint32_t sb : seg_bs) {
+                if (st != TC_OK) break;
                 b->cfg = IsectConfig{wm, sw, sb};
                 drop_exec(b);
                 st = run_once(b);  // capture + warm-up
@@ -486,13 +483,15 @@ tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, 
                     add_launches(b->launches_per_run);
                     cudaGraphLaunch(b->exec, b->stream);
                     cudaEventRecord(e1, b->stream);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) { st = TC_ECUDA; break; }
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        st = TC_ECUDA;
+                        break;
+                    }
                     float t = 0;
                     cudaEventElapsedTime(&t, e0, e1);
                     ms = std::min(ms, t);
                 }
-                if (st != TC_OK) break;
-                if (ms < best_ms) {
+                if (st == TC_OK && ms < best_ms) {
                     best_ms = ms;
                     best = b->cfg;
                 }

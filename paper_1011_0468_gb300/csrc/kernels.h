@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -142,6 +143,33 @@ void intersect_prepare(int dyn_smem_bytes);
 void finalize(const CountBuffers &b, double p, tc_result *out_dev, cudaStream_t s);
 // batch union: one tc_result per graph, p_dev[k] the graphs' sampling rates
 void finalize_batch(const CountBuffers &b, const double *p_dev, tc_result *out_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------- batch.cu
+// Device buffers of one batched count over a union of up to m_cap edges,
+// n_cap vertices and k_cap graphs (batch.cu, server.cu).
+struct UnionScratch {
+    uint64_t m_cap = 0;
+    uint32_t n_cap = 0, k_cap = 0;
+    uint64_t *ekey = nullptr, *bufA = nullptr, *bufB = nullptr, *items = nullptr;
+    uint64_t items_cap = 0;
+    uint32_t *deg = nullptr, *rowptr = nullptr, *inptr = nullptr, *hist = nullptr, *scan = nullptr;
+    uint8_t *heavy = nullptr;
+    DevState *st = nullptr;
+    uint64_t *eoff = nullptr, *thr = nullptr, *seed_mix = nullptr;
+    uint32_t *voff = nullptr;
+    double *p = nullptr;
+    unsigned long long *counters = nullptr;  // m_p[k_cap], t_light[k_cap], t_heavy[k_cap], n_heavy[k_cap] (u32)
+    tc_result *res_dev = nullptr;
+    int smem_bytes = 0;
+};
+// Allocates every buffer (cudaMalloc); false on failure (allocs keeps what
+// was allocated, bytes the total).
+bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32_t k_cap, std::vector<void *> &allocs,
+                         uint64_t &bytes);
+// The count of k graphs whose union (m edges, n vertices) sits in u.ekey,
+// with u.eoff / u.voff / u.thr / u.seed_mix / u.p filled: per-graph results
+// land in u.res_dev.
+void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const IsectConfig &cfg, cudaStream_t s);
 
 // ---------------------------------------------------------------- heavy.cu
 // Dense heavy block: U and U^T (hcap x hcap bf16, row stride hcap), the

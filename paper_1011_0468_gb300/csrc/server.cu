@@ -1,0 +1,681 @@
+// Continuous-batching request server (tc_server_*).
+//
+// A request is (graph, p, seed): one instance of the problem of Section 1
+// with the sample of Section 3.1.  Registered graphs stay resident in device
+// memory as canonical edge lists (sorted u << 32 | v keys, the upper-triangle
+// CSR of the graph), with a pinned host copy from which an evicted graph is
+// uploaded again.  A worker thread owns the count slots; each slot holds the
+// scratch of one batched count (union_count, batch.cu) and its own stream.
+// When a slot is free the worker admits the longest first-come prefix of the
+// queue that fits the slot and the HBM budget, gathers the requests' edge
+// lists into the slot's union (one copy kernel), and enqueues the batched
+// count followed by a host callback that wakes the worker again.  Because
+// the union gives every request its own vertex range, counters and (p,
+// seed), each result equals the one tc_count returns for that graph alone.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace tcg;
+
+namespace {
+
+constexpr uint32_t MAX_SLOTS = 8;
+
+// out[i] = key i of the union: request g's canonical keys, both endpoints
+// shifted by voff[g] (keys stay sorted because the vertex ranges increase).
+__global__ void k_gather(const uint64_t *const *__restrict__ src, const uint64_t *__restrict__ eoff,
+                         const uint32_t *__restrict__ voff, uint32_t k, uint64_t m, uint64_t *__restrict__ out)
+{
+    const unsigned lane = lane_id();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m; base += stride) {
+        const uint64_t i = base + lane, ii = i < m ? i : m - 1;
+        const uint32_t g = find_part_warp(eoff, k, ii);
+        if (i >= m) continue;
+        const uint64_t vo = __ldg(voff + g);
+        out[i] = __ldg(src[g] + (i - __ldg(eoff + g))) + ((vo << 32) | vo);
+    }
+}
+
+int key_bits(uint32_t n)
+{
+    int b = 1;
+    while (b < 32 && (1ull << b) < n) ++b;
+    return b;
+}
+
+double now_us(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+}
+
+struct GraphEntry {
+    uint64_t m = 0;
+    uint32_t n = 0;
+    uint64_t *host = nullptr;   // pinned canonical keys [m]
+    uint64_t *dev = nullptr;    // resident copy (NULL when evicted or m == 0)
+    uint64_t dev_bytes = 0;     // bytes charged to the budget while resident
+    bool resident = false;      // charged (upload may still be in flight)
+    uint32_t pins = 0;          // admitted requests not yet finished
+    std::list<uint32_t>::iterator lru;
+    cudaEvent_t ready = nullptr;  // recorded after each re-upload
+    int upload_slot = -1;
+    uint64_t upload_wave = 0;
+};
+
+struct Req {
+    uint64_t ticket;
+    uint32_t gid;
+    double p;
+    uint64_t seed;
+    double t_submit;
+};
+
+struct Record {
+    tc_request_info info;
+    bool done = false;
+};
+
+struct Slot {
+    UnionScratch u;
+    cudaStream_t s = nullptr;
+    // pinned staging of one wave's parameters and results
+    uint64_t *h_eoff = nullptr, *h_thr = nullptr, *h_seed_mix = nullptr;
+    const uint64_t **h_src = nullptr;
+    uint32_t *h_voff = nullptr;
+    double *h_p = nullptr;
+    tc_result *h_res = nullptr;
+    DevState *h_st = nullptr;
+    const uint64_t **d_src = nullptr;
+    // wave in flight
+    std::vector<Req> wave;
+    std::vector<GraphEntry *> wave_graphs;
+    bool busy = false, finished = false;
+    tc_status launch_status = TC_OK;
+    double t_admit = 0;
+    uint64_t serial = 0;
+};
+
+struct CallbackCtx {
+    tc_server *srv;
+    uint32_t slot;
+};
+
+tc_status status_of(unsigned err)
+{
+    if (err & ERR_ENDPOINT) return TC_EINVAL;
+    if (err & ERR_TIMEOUT) return TC_ETIMEOUT;
+    if (err) return TC_ECUDA;
+    return TC_OK;
+}
+
+}  // namespace
+
+struct tc_server {
+    int device = 0;
+    uint64_t budget = 0, slot_bytes = 0, resident_bytes = 0;
+    uint64_t slot_edges = 0;
+    uint32_t slot_vertices = 0, slot_requests = 0, nslots = 0;
+    std::vector<void *> allocs;  // slot scratch (cudaMalloc)
+    Slot slots[MAX_SLOTS];
+    CallbackCtx cb[MAX_SLOTS];
+
+    std::mutex mu;
+    std::condition_variable work_cv, done_cv;
+    std::vector<std::unique_ptr<GraphEntry>> graphs;
+    std::list<uint32_t> lru;  // resident graphs, least recently used first
+    std::deque<Req> queue;
+    std::unordered_map<uint64_t, Record> records;
+    uint64_t next_ticket = 1, wave_serial = 0;
+    bool stop = false;
+    tc_server_stats stats{};
+
+    std::mutex ingest_mu;
+    cudaStream_t ingest = nullptr;
+    std::thread worker;
+    std::chrono::steady_clock::time_point t0;
+};
+
+namespace {
+
+void CUDART_CB on_slot_done(void *arg)
+{
+    // runs on a CUDA callback thread: no CUDA calls here
+    CallbackCtx *c = static_cast<CallbackCtx *>(arg);
+    {
+        std::lock_guard<std::mutex> lock(c->srv->mu);
+        c->srv->slots[c->slot].finished = true;
+    }
+    c->srv->work_cv.notify_all();
+}
+
+// Under the lock: finish the slot's wave (results to the records, graphs
+// unpinned).
+void complete_wave(tc_server *srv, uint32_t si)
+{
+    Slot &sl = srv->slots[si];
+    tc_status st = sl.launch_status;
+    if (st == TC_OK) st = status_of(sl.h_st->err);
+    const double t_done = now_us(srv->t0);
+    for (size_t j = 0; j < sl.wave.size(); ++j) {
+        auto it = srv->records.find(sl.wave[j].ticket);
+        if (it != srv->records.end()) {
+            tc_request_info &info = it->second.info;
+            if (st == TC_OK) {
+                info.res = sl.h_res[j];
+                std::memset(info.res.ms, 0, sizeof(info.res.ms));
+            }
+            info.status = st;
+            info.wave_size = (uint32_t)sl.wave.size();
+            info.t_admit_us = sl.t_admit;
+            info.t_done_us = t_done;
+            it->second.done = true;
+        }
+    }
+    for (GraphEntry *g : sl.wave_graphs) --g->pins;
+    srv->stats.completed += sl.wave.size();
+    sl.wave.clear();
+    sl.wave_graphs.clear();
+    sl.busy = false;
+    sl.finished = false;
+    srv->done_cv.notify_all();
+}
+
+// Under the lock: admit the longest queue prefix that fits slot si and the
+// budget.  Graphs to (re)upload go to `uploads`, device copies to free to
+// `frees`.  Returns false if nothing could be admitted.
+bool form_wave(tc_server *srv, uint32_t si, std::vector<GraphEntry *> &uploads, std::vector<uint64_t *> &frees)
+{
+    Slot &sl = srv->slots[si];
+    const uint64_t room = srv->budget - srv->slot_bytes;
+    uint64_t m_sum = 0, n_sum = 0;
+    while (!srv->queue.empty() && sl.wave.size() < srv->slot_requests) {
+        const Req &r = srv->queue.front();
+        GraphEntry *g = srv->graphs[r.gid].get();
+        if (m_sum + g->m > srv->slot_edges || n_sum + g->n > srv->slot_vertices) break;
+        if (g->m > 0 && !g->resident) {
+            if (srv->resident_bytes + g->dev_bytes > room) {
+                uint64_t reclaim = 0;  // evict only if that makes enough room
+                for (uint32_t id : srv->lru)
+                    if (!srv->graphs[id]->pins) reclaim += srv->graphs[id]->dev_bytes;
+                if (srv->resident_bytes - reclaim + g->dev_bytes > room) break;  // wait for running slots
+            }
+            // evict least recently used graphs no slot is using
+            auto it = srv->lru.begin();
+            while (srv->resident_bytes + g->dev_bytes > room && it != srv->lru.end()) {
+                GraphEntry *v = srv->graphs[*it].get();
+                if (v->pins) {
+                    ++it;
+                    continue;
+                }
+                if (v->dev) frees.push_back(v->dev);
+                v->dev = nullptr;
+                v->resident = false;
+                srv->resident_bytes -= v->dev_bytes;
+                --srv->stats.resident_graphs;
+                ++srv->stats.evictions;
+                it = srv->lru.erase(it);
+            }
+            if (srv->resident_bytes + g->dev_bytes > room) break;  // wait for running slots
+            g->resident = true;
+            srv->resident_bytes += g->dev_bytes;
+            ++srv->stats.resident_graphs;
+            ++srv->stats.uploads;
+            g->lru = srv->lru.insert(srv->lru.end(), r.gid);
+            uploads.push_back(g);
+        } else if (g->m > 0) {
+            srv->lru.splice(srv->lru.end(), srv->lru, g->lru);  // most recently used
+        }
+        ++g->pins;
+        sl.wave.push_back(r);
+        sl.wave_graphs.push_back(g);
+        m_sum += g->m;
+        n_sum += g->n;
+        srv->queue.pop_front();
+    }
+    return !sl.wave.empty();
+}
+
+// Outside the lock (worker thread only): enqueue the wave of slot si.
+tc_status enqueue_wave(tc_server *srv, uint32_t si, const std::vector<GraphEntry *> &uploads,
+                       const std::vector<uint64_t *> &frees)
+{
+    Slot &sl = srv->slots[si];
+    cudaStream_t s = sl.s;
+    for (uint64_t *ptr : frees) cudaFreeAsync(ptr, s);
+    for (GraphEntry *g : uploads) {
+        if (cudaMallocAsync((void **)&g->dev, g->m * 8, s) != cudaSuccess) {
+            cudaGetLastError();
+            g->dev = nullptr;
+            return TC_ENOMEM;
+        }
+        cudaMemcpyAsync(g->dev, g->host, g->m * 8, cudaMemcpyHostToDevice, s);
+        cudaEventRecord(g->ready, s);
+        g->upload_slot = (int)si;
+        g->upload_wave = sl.serial;
+    }
+    const uint32_t k = (uint32_t)sl.wave.size();
+    uint64_t m = 0, n = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+        GraphEntry *g = sl.wave_graphs[j];
+        // a copy uploaded by another slot's wave that may still be running
+        if (g->upload_slot >= 0 && g->upload_slot != (int)si) {
+            const Slot &o = srv->slots[g->upload_slot];
+            if (o.busy && o.serial == g->upload_wave) cudaStreamWaitEvent(s, g->ready, 0);
+        }
+        const Req &r = sl.wave[j];
+        sl.h_eoff[j] = m;
+        sl.h_voff[j] = (uint32_t)n;
+        sl.h_src[j] = g->dev;
+        sl.h_p[j] = r.p;
+        sl.h_thr[j] = (uint64_t)(r.p * 9007199254740992.0);
+        sl.h_seed_mix[j] = splitmix64(r.seed);
+        m += g->m;
+        n += g->n;
+    }
+    sl.h_eoff[k] = m;
+    sl.h_voff[k] = (uint32_t)n;
+    cudaMemcpyAsync(sl.u.eoff, sl.h_eoff, (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(sl.u.voff, sl.h_voff, (k + 1) * 4ull, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(sl.d_src, sl.h_src, k * 8ull, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(sl.u.p, sl.h_p, k * 8ull, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(sl.u.thr, sl.h_thr, k * 8ull, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(sl.u.seed_mix, sl.h_seed_mix, k * 8ull, cudaMemcpyHostToDevice, s);
+    if (m > 0) {
+        k_gather<<<grid_for(m, 256, 152 * 8), 256, 0, s>>>(sl.d_src, sl.u.eoff, sl.u.voff, k, m, sl.u.ekey);
+        note_launch();
+    }
+    union_count(sl.u, m, (uint32_t)n, k, IsectConfig{}, s);
+    cudaMemcpyAsync(sl.h_res, sl.u.res_dev, k * sizeof(tc_result), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(sl.h_st, sl.u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    if (cudaGetLastError() != cudaSuccess) return TC_ECUDA;
+    if (cudaLaunchHostFunc(s, on_slot_done, &srv->cb[si]) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    return TC_OK;
+}
+
+void worker_main(tc_server *srv)
+{
+    cudaSetDevice(srv->device);
+    std::unique_lock<std::mutex> lock(srv->mu);
+    for (;;) {
+        for (uint32_t i = 0; i < srv->nslots; ++i)
+            if (srv->slots[i].busy && srv->slots[i].finished) complete_wave(srv, i);
+        bool any_busy = false;
+        for (uint32_t i = 0; i < srv->nslots; ++i) any_busy |= srv->slots[i].busy;
+        if (srv->stop && !any_busy) break;
+        bool launched = false;
+        if (!srv->stop) {
+            for (uint32_t i = 0; i < srv->nslots && !srv->queue.empty(); ++i) {
+                Slot &sl = srv->slots[i];
+                if (sl.busy) continue;
+                std::vector<GraphEntry *> uploads;
+                std::vector<uint64_t *> frees;
+                if (!form_wave(srv, i, uploads, frees)) break;  // the head waits for memory
+                sl.busy = true;
+                sl.finished = false;
+                sl.serial = ++srv->wave_serial;
+                sl.t_admit = now_us(srv->t0);
+                srv->stats.waves += 1;
+                srv->stats.max_wave = std::max<uint64_t>(srv->stats.max_wave, sl.wave.size());
+                srv->stats.queued = srv->queue.size();
+                lock.unlock();
+                const tc_status st = enqueue_wave(srv, i, uploads, frees);
+                if (st != TC_OK) cudaStreamSynchronize(sl.s);  // no callback will come
+                lock.lock();
+                if (st != TC_OK) {
+                    sl.launch_status = st;
+                    for (GraphEntry *g : uploads)
+                        if (!g->dev && g->resident) {  // upload failed: uncharge
+                            g->resident = false;
+                            srv->resident_bytes -= g->dev_bytes;
+                            --srv->stats.resident_graphs;
+                            srv->lru.erase(g->lru);
+                        }
+                    complete_wave(srv, i);
+                    sl.launch_status = TC_OK;
+                }
+                launched = true;
+            }
+        }
+        if (!launched) srv->work_cv.wait(lock);
+    }
+}
+
+void free_server(tc_server *srv)
+{
+    if (!srv) return;
+    if (srv->worker.joinable()) {
+        {
+            std::lock_guard<std::mutex> lock(srv->mu);
+            srv->stop = true;
+        }
+        srv->work_cv.notify_all();
+        srv->worker.join();
+    }
+    cudaSetDevice(srv->device);
+    for (uint32_t i = 0; i < srv->nslots; ++i) {
+        Slot &sl = srv->slots[i];
+        if (sl.s) cudaStreamSynchronize(sl.s);
+    }
+    for (auto &g : srv->graphs) {
+        if (g->dev) cudaFreeAsync(g->dev, srv->ingest);
+        if (g->host) cudaFreeHost(g->host);
+        if (g->ready) cudaEventDestroy(g->ready);
+    }
+    if (srv->ingest) {
+        cudaStreamSynchronize(srv->ingest);
+        cudaStreamDestroy(srv->ingest);
+    }
+    for (uint32_t i = 0; i < srv->nslots; ++i) {
+        Slot &sl = srv->slots[i];
+        cudaFreeHost(sl.h_eoff);
+        cudaFreeHost(sl.h_thr);
+        cudaFreeHost(sl.h_seed_mix);
+        cudaFreeHost(sl.h_src);
+        cudaFreeHost(sl.h_voff);
+        cudaFreeHost(sl.h_p);
+        cudaFreeHost(sl.h_res);
+        cudaFreeHost(sl.h_st);
+        if (sl.s) cudaStreamDestroy(sl.s);
+    }
+    for (void *p : srv->allocs) cudaFree(p);
+    cudaGetLastError();
+    delete srv;
+}
+
+template <typename T>
+bool pinned(T **p, uint64_t count)
+{
+    if (cudaMallocHost((void **)p, std::max<uint64_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_server_create(uint64_t budget_bytes, uint32_t slots, uint64_t slot_edges, uint32_t slot_vertices,
+                           uint32_t slot_requests, tc_server **out)
+{
+    if (!out) return TC_EINVAL;
+    *out = nullptr;
+    if (slots == 0 || slots > MAX_SLOTS || slot_edges == 0 || slot_edges > 0xfffffffeull || slot_vertices == 0 ||
+        slot_vertices > 0xfffffffeu || slot_requests == 0 || slot_requests > 0xffffu)
+        return TC_EINVAL;
+    tc_server *srv = new (std::nothrow) tc_server;
+    if (!srv) return TC_ENOMEM;
+    cudaGetDevice(&srv->device);
+    srv->budget = budget_bytes;
+    srv->slot_edges = slot_edges;
+    srv->slot_vertices = slot_vertices;
+    srv->slot_requests = slot_requests;
+    srv->t0 = std::chrono::steady_clock::now();
+    if (cudaStreamCreateWithFlags(&srv->ingest, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        free_server(srv);
+        return TC_ECUDA;
+    }
+    for (uint32_t i = 0; i < slots; ++i) {
+        Slot &sl = srv->slots[i];
+        srv->nslots = i + 1;
+        srv->cb[i] = CallbackCtx{srv, i};
+        if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            free_server(srv);
+            return TC_ECUDA;
+        }
+        const uint64_t k = slot_requests;
+        if (!pinned(&sl.h_eoff, k + 1) || !pinned(&sl.h_thr, k) || !pinned(&sl.h_seed_mix, k) ||
+            !pinned(&sl.h_src, k) || !pinned(&sl.h_voff, k + 1) || !pinned(&sl.h_p, k) || !pinned(&sl.h_res, k) ||
+            !pinned(&sl.h_st, 1)) {
+            free_server(srv);
+            return TC_ENOMEM;
+        }
+        void *dsrc = nullptr;
+        if (cudaMalloc(&dsrc, k * 8) != cudaSuccess) {
+            cudaGetLastError();
+            free_server(srv);
+            return TC_ENOMEM;
+        }
+        srv->allocs.push_back(dsrc);
+        srv->slot_bytes += k * 8;
+        sl.d_src = (const uint64_t **)dsrc;
+        if (!union_scratch_alloc(sl.u, slot_edges, slot_vertices, slot_requests, srv->allocs, srv->slot_bytes)) {
+            free_server(srv);
+            return TC_ENOMEM;
+        }
+    }
+    if (srv->slot_bytes > budget_bytes) {
+        free_server(srv);
+        return TC_ENOMEM;
+    }
+    srv->stats.budget_bytes = budget_bytes;
+    srv->stats.slot_bytes = srv->slot_bytes;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        free_server(srv);
+        return TC_ECUDA;
+    }
+    try {
+        srv->worker = std::thread(worker_main, srv);
+    } catch (...) {
+        free_server(srv);
+        return TC_ENOMEM;
+    }
+    *out = srv;
+    return TC_OK;
+}
+
+void tc_server_destroy(tc_server *srv) { free_server(srv); }
+
+tc_status tc_server_add_graph(tc_server *srv, const uint32_t *edges, uint64_t m_in, uint32_t n, int edges_on_device,
+                              uint32_t *gid)
+{
+    if (!srv || !gid || n == 0 || n == 0xffffffffu || m_in > 0xfffffffeull || (m_in > 0 && !edges))
+        return TC_EINVAL;
+    std::lock_guard<std::mutex> ingest_lock(srv->ingest_mu);
+    cudaSetDevice(srv->device);
+    cudaStream_t s = srv->ingest;
+    auto g = std::make_unique<GraphEntry>();
+    g->n = n;
+    if (cudaEventCreateWithFlags(&g->ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    // ---- canonical keys (as tc_graph_create): map, sort by (u, v), unique
+    std::vector<void *> tmp;
+    auto talloc = [&](uint64_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, std::max<uint64_t>(bytes, 16), s) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        tmp.push_back(p);
+        return p;
+    };
+    auto drop = [&](tc_status st) {
+        for (void *p : tmp) cudaFreeAsync(p, s);
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        if (g->ready) cudaEventDestroy(g->ready);
+        if (g->host) cudaFreeHost(g->host);
+        return st;
+    };
+    uint64_t m = 0;
+    uint64_t *canon = nullptr;
+    if (m_in > 0) {
+        const uint32_t *dpairs = edges;
+        if (!edges_on_device) {
+            void *p = talloc(m_in * 8);
+            if (!p) return drop(TC_ENOMEM);
+            cudaMemcpyAsync(p, edges, m_in * 8, cudaMemcpyHostToDevice, s);
+            dpairs = (const uint32_t *)p;
+        }
+        const uint64_t nt = ceil_div(m_in, RX_TILE);
+        uint64_t *a = (uint64_t *)talloc(m_in * 8), *b = (uint64_t *)talloc(m_in * 8);
+        uint32_t *hist = (uint32_t *)talloc((nt << RX_MAX_BITS) * 4);
+        uint32_t *scan = (uint32_t *)talloc(scan_scratch_elems(nt << RX_MAX_BITS) * 4);
+        DevState *st = (DevState *)talloc(sizeof(DevState));
+        DevState *h_st = nullptr;
+        if (!a || !b || !hist || !scan || !st) return drop(TC_ENOMEM);
+        if (!pinned(&h_st, 1)) return drop(TC_ENOMEM);
+        cudaMemsetAsync(st, 0, sizeof(DevState), s);
+        canon_keys(dpairs, m_in, n, a, st, s);
+        const int nbits = key_bits(n);
+        for (int half = 0; half < 2; ++half) {
+            int shift = half ? 32 : 0;
+            const int P = (nbits + RX_MAX_BITS - 1) / RX_MAX_BITS;
+            for (int i = 0; i < P; ++i) {
+                const int w = nbits / P + (i < nbits % P ? 1 : 0);
+                ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
+                radix_pass(src, m_in, shift, w, hist, scan, nullptr, b, nullptr, nullptr, s);
+                std::swap(a, b);
+                shift += w;
+            }
+        }
+        unique_keys(a, m_in, b, hist, scan, st, s);
+        cudaMemcpyAsync(h_st, st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        const bool ok = cudaStreamSynchronize(s) == cudaSuccess;
+        const DevState hs = *h_st;
+        cudaFreeHost(h_st);
+        if (!ok) return drop(TC_ECUDA);
+        if (hs.err & ERR_ENDPOINT) return drop(TC_EINVAL);
+        m = hs.m_canon;
+        canon = b;
+    }
+    g->m = m;
+    g->dev_bytes = m * 8;
+    if (m > srv->slot_edges || n > srv->slot_vertices) return drop(TC_EINVAL);
+    if (g->dev_bytes > srv->budget - srv->slot_bytes) return drop(TC_ENOMEM);
+    if (m > 0) {
+        if (!pinned(&g->host, m)) return drop(TC_ENOMEM);
+        cudaMemcpyAsync(g->host, canon, m * 8, cudaMemcpyDeviceToHost, s);
+    }
+    // resident right away if that needs no eviction
+    bool keep = false;
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        keep = m > 0 && srv->resident_bytes + g->dev_bytes <= srv->budget - srv->slot_bytes;
+        if (keep) srv->resident_bytes += g->dev_bytes;  // reserve
+    }
+    if (keep) {
+        if (cudaMallocAsync((void **)&g->dev, m * 8, s) == cudaSuccess) {
+            cudaMemcpyAsync(g->dev, canon, m * 8, cudaMemcpyDeviceToDevice, s);
+        } else {
+            cudaGetLastError();
+            g->dev = nullptr;
+        }
+    }
+    for (void *p : tmp) cudaFreeAsync(p, s);
+    tmp.clear();
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        if (keep) {
+            std::lock_guard<std::mutex> lock(srv->mu);
+            srv->resident_bytes -= g->dev_bytes;
+        }
+        if (g->dev) cudaFreeAsync(g->dev, s);
+        g->dev = nullptr;
+        return drop(TC_ECUDA);
+    }
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        if (keep && !g->dev) srv->resident_bytes -= g->dev_bytes;  // allocation failed: upload on demand
+        g->resident = g->dev != nullptr;
+        const uint32_t id = (uint32_t)srv->graphs.size();
+        if (g->resident) {
+            g->lru = srv->lru.insert(srv->lru.end(), id);
+            ++srv->stats.resident_graphs;
+        }
+        srv->graphs.push_back(std::move(g));
+        srv->stats.graphs = srv->graphs.size();
+        *gid = id;
+    }
+    srv->work_cv.notify_all();  // a released reservation may let the queue head in
+    return TC_OK;
+}
+
+tc_status tc_server_submit(tc_server *srv, uint32_t gid, double p, uint64_t seed, uint64_t *ticket)
+{
+    if (!srv || !ticket || !(p > 0.0 && p <= 1.0)) return TC_EINVAL;
+    const double t = now_us(srv->t0);
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        if (gid >= srv->graphs.size() || srv->stop) return TC_EINVAL;
+        const uint64_t id = srv->next_ticket++;
+        Record rec;
+        std::memset(&rec.info, 0, sizeof(rec.info));
+        rec.info.t_submit_us = t;
+        srv->records.emplace(id, rec);
+        srv->queue.push_back(Req{id, gid, p, seed, t});
+        ++srv->stats.submitted;
+        srv->stats.queued = srv->queue.size();
+        *ticket = id;
+    }
+    srv->work_cv.notify_all();
+    return TC_OK;
+}
+
+tc_status tc_server_poll(tc_server *srv, uint64_t ticket, tc_request_info *info)
+{
+    if (!srv || !info) return TC_EINVAL;
+    std::lock_guard<std::mutex> lock(srv->mu);
+    auto it = srv->records.find(ticket);
+    if (it == srv->records.end()) return TC_EINVAL;
+    if (!it->second.done) return TC_EBUSY;
+    *info = it->second.info;
+    srv->records.erase(it);
+    return TC_OK;
+}
+
+tc_status tc_server_wait(tc_server *srv, uint64_t ticket, uint32_t timeout_ms, tc_request_info *info)
+{
+    if (!srv || !info) return TC_EINVAL;
+    std::unique_lock<std::mutex> lock(srv->mu);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+        auto it = srv->records.find(ticket);
+        if (it == srv->records.end()) return TC_EINVAL;
+        if (it->second.done) {
+            *info = it->second.info;
+            srv->records.erase(it);
+            return TC_OK;
+        }
+        if (srv->done_cv.wait_until(lock, deadline) == std::cv_status::timeout) {
+            auto again = srv->records.find(ticket);
+            if (again != srv->records.end() && again->second.done) continue;
+            return TC_EBUSY;
+        }
+    }
+}
+
+tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *out)
+{
+    if (!srv || !out) return TC_EINVAL;
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->stats.resident_bytes = srv->resident_bytes;
+    srv->stats.queued = srv->queue.size();
+    *out = srv->stats;
+    return TC_OK;
+}
+
+}  // extern "C"

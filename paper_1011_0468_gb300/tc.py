@@ -46,6 +46,18 @@ _u8p = ctypes.POINTER(ctypes.c_uint8)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _vp = ctypes.c_void_p
 
+
+class tc_request_info(ctypes.Structure):
+    _fields_ = [("res", tc_result), ("status", ctypes.c_int32), ("wave_size", ctypes.c_uint32),
+                ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+class tc_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "queued", "waves", "max_wave",
+                                                "resident_graphs", "resident_bytes", "graphs", "slot_bytes",
+                                                "budget_bytes", "uploads", "evictions")]
+
+
 # (name, restype, argtypes) of every exported entry point of include/tc.h
 SIGNATURES = [
     ("tc_set_allocator", None, [_vp, _vp, _vp]),
@@ -76,6 +88,14 @@ SIGNATURES = [
     ("tc_batch_size", ctypes.c_uint32, [_vp]),
     ("tc_batch_num_edges", ctypes.c_uint64, [_vp]),
     ("tc_batch_device_bytes", ctypes.c_uint64, [_vp]),
+    ("tc_server_create", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.POINTER(_vp)]),
+    ("tc_server_add_graph", ctypes.c_int, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, _u32p]),
+    ("tc_server_submit", ctypes.c_int, [_vp, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64, _u64p]),
+    ("tc_server_poll", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(tc_request_info)]),
+    ("tc_server_wait", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(tc_request_info)]),
+    ("tc_server_get_stats", ctypes.c_int, [_vp, ctypes.POINTER(tc_server_stats)]),
+    ("tc_server_destroy", None, [_vp]),
 ]
 
 # numpy view of tc_result (same layout as the C struct)
@@ -367,6 +387,83 @@ class Batch:
     def close(self):
         if self._h:
             lib().tc_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (tc_server_*): graphs registered
+    once and kept resident within an HBM budget; requests (graph, p, seed)
+    are counted in batched slot launches as they arrive."""
+
+    def __init__(self, budget_bytes: int, slots: int = 2, slot_edges: int = 1 << 24,
+                 slot_vertices: int = 1 << 22, slot_requests: int = 4096):
+        h = _vp()
+        _check(lib().tc_server_create(budget_bytes, slots, slot_edges, slot_vertices, slot_requests,
+                                      ctypes.byref(h)), "tc_server_create")
+        self._h = h.value
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("server is closed")
+        return self._h
+
+    def add_graph(self, edges, n: int) -> int:
+        addr, m_in, on_dev, keep = _as_pairs(edges)
+        gid = ctypes.c_uint32(0)
+        _check(lib().tc_server_add_graph(self.handle, addr if m_in else None, m_in, n, 1 if on_dev else 0,
+                                         ctypes.byref(gid)), "tc_server_add_graph")
+        del keep
+        return gid.value
+
+    def submit(self, gid: int, p: float, seed: int) -> int:
+        t = ctypes.c_uint64(0)
+        _check(lib().tc_server_submit(self.handle, gid, p, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(t)),
+               "tc_server_submit")
+        return t.value
+
+    @staticmethod
+    def _info(info: tc_request_info) -> dict:
+        d = info.res.as_dict()
+        d.pop("ms")
+        d.update(status=info.status, wave_size=info.wave_size, t_submit_us=info.t_submit_us,
+                 t_admit_us=info.t_admit_us, t_done_us=info.t_done_us)
+        return d
+
+    def poll(self, ticket: int):
+        """The request's result dict once done (the ticket is then released), else None."""
+        info = tc_request_info()
+        st = lib().tc_server_poll(self.handle, ticket, ctypes.byref(info))
+        if st == TC_EBUSY:
+            return None
+        _check(st, "tc_server_poll")
+        return self._info(info)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> dict:
+        info = tc_request_info()
+        _check(lib().tc_server_wait(self.handle, ticket, timeout_ms, ctypes.byref(info)), "tc_server_wait")
+        return self._info(info)
+
+    def stats(self) -> dict:
+        st = tc_server_stats()
+        _check(lib().tc_server_get_stats(self.handle, ctypes.byref(st)), "tc_server_get_stats")
+        return {k: int(getattr(st, k)) for k, _ in st._fields_}
+
+    def close(self):
+        if self._h:
+            lib().tc_server_destroy(self._h)
             self._h = None
 
     def __enter__(self):

@@ -68,3 +68,28 @@ def test_result_struct_layout():
     # uint64 m, m_sampled; uint32 n, n_heavy; uint64 t_light, t_heavy; double;
     # uint64 src_elems, nbr_elems, partners, heavy_mma_flops; float[8]
     assert ctypes.sizeof(tc.tc_result) == 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 + 8 + 8 + 8 + 32
+
+
+def test_server_struct_layout():
+    from paper_1011_0468_gb300 import tc
+    # tc_result; int32 status; uint32 wave_size; double t_submit, t_admit, t_done
+    assert ctypes.sizeof(tc.tc_request_info) == ctypes.sizeof(tc.tc_result) + 4 + 4 + 3 * 8
+    assert tc.tc_request_info.t_submit_us.offset == ctypes.sizeof(tc.tc_result) + 8
+    assert ctypes.sizeof(tc.tc_server_stats) == 12 * 8
+
+
+def test_server_argument_errors_without_device(lib):
+    from paper_1011_0468_gb300 import tc
+    out = ctypes.c_void_p()
+    assert lib.tc_server_create(1 << 30, 2, 1 << 20, 1 << 20, 64, None) == tc.TC_EINVAL
+    assert lib.tc_server_create(1 << 30, 0, 1 << 20, 1 << 20, 64, ctypes.byref(out)) == tc.TC_EINVAL
+    assert lib.tc_server_create(1 << 30, 9, 1 << 20, 1 << 20, 64, ctypes.byref(out)) == tc.TC_EINVAL
+    assert lib.tc_server_create(1 << 30, 2, 0, 1 << 20, 64, ctypes.byref(out)) == tc.TC_EINVAL
+    assert lib.tc_server_create(1 << 30, 2, 1 << 20, 1 << 20, 1 << 16, ctypes.byref(out)) == tc.TC_EINVAL
+    assert out.value is None
+    t = ctypes.c_uint64()
+    assert lib.tc_server_submit(None, 0, 0.5, 1, ctypes.byref(t)) == tc.TC_EINVAL
+    info = tc.tc_request_info()
+    assert lib.tc_server_poll(None, 1, ctypes.byref(info)) == tc.TC_EINVAL
+    assert lib.tc_server_wait(None, 1, 0, ctypes.byref(info)) == tc.TC_EINVAL
+    lib.tc_server_destroy(None)  # NULL-safe
