@@ -81,8 +81,10 @@ struct tc_graph {
     uint32_t *rowptr = nullptr; // [n + 1]
     uint8_t *heavy = nullptr;   // [n]
     uint32_t *inptr = nullptr;  // [n + 2] in-list offsets (see InListArgs)
-    uint32_t *col = nullptr;    // CSR columns (inside bufA or bufB)
-    uint32_t *inlist = nullptr; // in-lists (second half of the same buffer)
+    uint32_t *col = nullptr;    // padded CSR columns (= colp)
+    uint32_t *inlist = nullptr; // in-lists (inside bufA or bufB)
+    uint32_t *colp = nullptr;   // [colp_capacity(n, m)] rows padded to 16 bytes
+    uint32_t *ptrp = nullptr;   // [n + 2] padded row pointers
     uint64_t *items = nullptr;  // owner work items, all buckets [items_cap]
     uint64_t items_cap = 0;
     uint32_t *hist = nullptr;   // [RX_BINS * ntiles(m)]
@@ -174,6 +176,8 @@ void enqueue_csr(tc_graph *g, uint64_t seed_mix, uint64_t thr)
     a.inptr = g->inptr;
     a.hist = g->hist;
     a.scan = g->scan;
+    a.colp = g->colp;
+    a.ptrp = g->ptrp;
     csr_build(a, &g->col, &g->inlist, g->stream);
 }
 
@@ -187,6 +191,7 @@ CountBuffers buffers_of(tc_graph *g)
     b.heavy = g->heavy;
     b.rowptr = g->rowptr;
     b.col = g->col;
+    b.ptrp = g->ptrp;
     b.inptr = g->inptr;
     b.inlist = g->inlist;
     b.items = g->items;
@@ -380,12 +385,14 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     g->rowptr = (uint32_t *)g->alloc(((uint64_t)n + 1) * 4);
     g->heavy = (uint8_t *)g->alloc((uint64_t)n);
     g->inptr = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
+    g->colp = (uint32_t *)g->alloc(colp_capacity(n, m) * 4);
+    g->ptrp = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
     g->items_cap = items_capacity(n, m);
     g->items = (uint64_t *)g->alloc(g->items_cap * 8);
     g->hist = (uint32_t *)g->alloc(hist_len * 4);
     g->scan = (uint32_t *)g->alloc(scan_scratch_elems(std::max<uint64_t>(hist_len, (uint64_t)n + 1)) * 4);
-    if (!g->bufA || !g->bufB || !g->deg || !g->rowptr || !g->heavy || !g->inptr || !g->items || !g->hist ||
-        !g->scan) {
+    if (!g->bufA || !g->bufB || !g->deg || !g->rowptr || !g->heavy || !g->inptr || !g->colp || !g->ptrp ||
+        !g->items || !g->hist || !g->scan) {
         free_graph(g);
         return TC_ENOMEM;
     }
@@ -547,10 +554,25 @@ tc_status tc_graph_export_csr(tc_graph *g, double p, uint64_t seed, uint32_t *ro
     if (st != TC_OK) return st;
     const uint64_t mp = g->st_host->m_sampled;
     if (m_sampled) *m_sampled = mp;
-    if (rowptr_host)
-        cudaMemcpyAsync(rowptr_host, g->rowptr, ((size_t)g->n + 1) * 4, cudaMemcpyDeviceToHost, g->stream);
-    if (col_host && mp > 0) cudaMemcpyAsync(col_host, g->col, mp * 4, cudaMemcpyDeviceToHost, g->stream);
+    std::vector<uint32_t> rp(g->n + 1), pp(g->n + 1), cp;
+    cudaMemcpyAsync(rp.data(), g->rowptr, ((size_t)g->n + 1) * 4, cudaMemcpyDeviceToHost, g->stream);
+    if (g->m > 0) cudaMemcpyAsync(pp.data(), g->ptrp, ((size_t)g->n + 1) * 4, cudaMemcpyDeviceToHost, g->stream);
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) { cudaGetLastError(); return TC_ECUDA; }
+    if (rowptr_host) std::copy(rp.begin(), rp.end(), rowptr_host);
+    if (g->m == 0 || mp == 0) return TC_OK;
+    // the columns are stored padded: check the layout and strip the padding
+    const uint64_t total = pp[g->n];
+    if (total > colp_capacity(g->n, g->m)) return TC_ECUDA;
+    cp.resize(total);
+    cudaMemcpyAsync(cp.data(), g->colp, total * 4, cudaMemcpyDeviceToHost, g->stream);
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) { cudaGetLastError(); return TC_ECUDA; }
+    for (uint32_t x = 0; x < g->n; ++x) {
+        const uint32_t d = rp[x + 1] - rp[x], beg = pp[x] & ~3u, pad = pp[x] & 3u;
+        if (pad != ((4u - (d & 3u)) & 3u) || (pp[x + 1] & ~3u) != beg + d + pad) return TC_ECUDA;
+        for (uint32_t i = 0; i < pad; ++i)
+            if (cp[beg + d + i] != SENT) return TC_ECUDA;
+        if (col_host) std::copy(cp.begin() + beg, cp.begin() + beg + d, col_host + rp[x]);
+    }
     return TC_OK;
 }
 

@@ -122,6 +122,8 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
     u.deg = (uint32_t *)dev_alloc_track(allocs, bytes, (uint64_t)n_cap * 4);
     u.rowptr = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)n_cap + 1) * 4);
     u.inptr = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)n_cap + 2) * 4);
+    u.colp = (uint32_t *)dev_alloc_track(allocs, bytes, colp_capacity(n_cap, m1) * 4);
+    u.ptrp = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)n_cap + 2) * 4);
     u.heavy = (uint8_t *)dev_alloc_track(allocs, bytes, n_cap);
     u.items_cap = items_capacity(n_cap, m1);
     u.items = (uint64_t *)dev_alloc_track(allocs, bytes, u.items_cap * 8);
@@ -142,7 +144,8 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     u.smem_bytes = (int)(slots * 4);
     intersect_prepare(u.smem_bytes);
-    return u.ekey && u.bufA && u.bufB && u.deg && u.rowptr && u.inptr && u.heavy && u.items && u.hist && u.scan &&
+    return u.ekey && u.bufA && u.bufB && u.deg && u.rowptr && u.inptr && u.colp && u.ptrp && u.heavy && u.items &&
+           u.hist && u.scan &&
            u.st && u.eoff && u.voff && u.thr && u.seed_mix && u.p && u.counters && u.res_dev;
 }
 
@@ -159,6 +162,7 @@ void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const Isec
     cb.heavy = u.heavy;
     cb.rowptr = u.rowptr;
     cb.col = nullptr;
+    cb.ptrp = u.ptrp;
     cb.inptr = u.inptr;
     cb.inlist = nullptr;
     cb.items = u.items;
@@ -185,6 +189,8 @@ void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const Isec
         a.inptr = u.inptr;
         a.hist = u.hist;
         a.scan = u.scan;
+        a.colp = u.colp;
+        a.ptrp = u.ptrp;
         csr_build(a, &cb.col, &cb.inlist, s);
         build_items(cb, s);
         intersect(cb, u.smem_bytes, s);

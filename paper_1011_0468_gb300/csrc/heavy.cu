@@ -95,7 +95,7 @@ __global__ void k_heavy_clear(uint16_t *__restrict__ U, uint16_t *__restrict__ U
 
 // One warp per heavy source: U[rank(v)][rank(w)] = U^T[rank(w)][rank(v)] = 1
 // for every out-neighbour w.
-__global__ void k_heavy_pack(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ col,
+__global__ void k_heavy_pack(const uint32_t *__restrict__ ptrp, const uint32_t *__restrict__ col,
                              const uint8_t *__restrict__ heavy, const uint32_t *__restrict__ hlist,
                              const uint32_t *__restrict__ hidx, uint16_t *__restrict__ U, uint16_t *__restrict__ UT,
                              uint32_t hcap, DevState *st)
@@ -107,8 +107,8 @@ __global__ void k_heavy_pack(const uint32_t *__restrict__ rowptr, const uint32_t
     constexpr uint16_t ONE = 0x3f80;  // bf16 1.0
     for (uint32_t i = gw; i < h; i += nw) {
         const uint32_t v = hlist[i], r = hidx[v];
-        const uint32_t b = rowptr[v], e = rowptr[v + 1];
-        for (uint32_t q = b + lane; q < e; q += 32) {
+        const PaddedRow row = padded_row(ptrp, v);
+        for (uint32_t q = row.beg + lane; q < row.beg + row.d; q += 32) {
             const uint32_t w = col[q];
             if (!heavy[w]) {  // cannot happen: heavy vertices point to heavy vertices
                 atomicOr(&st->err, ERR_OVERFLOW);
@@ -426,7 +426,7 @@ void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s
     note_launch();
     k_heavy_clear<<<152 * 8, 256, 0, s>>>(hb.U, hb.UT, hb.hcap, b.st);
     note_launch();
-    k_heavy_pack<<<152 * 4, 256, 0, s>>>(b.rowptr, b.col, b.heavy, hb.hlist, hb.hidx, hb.U, hb.UT, hb.hcap, b.st);
+    k_heavy_pack<<<152 * 4, 256, 0, s>>>(b.ptrp, b.col, b.heavy, hb.hlist, hb.hidx, hb.U, hb.UT, hb.hcap, b.st);
     note_launch();
 }
 

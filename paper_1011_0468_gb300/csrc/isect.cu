@@ -17,9 +17,10 @@
 // Work items are (segment << 32 | owner); a segment is a run of the owner's
 // partner sequence (its d+(x) out-neighbours, then its in-list).  Owners
 // are bucketed by d+(x), which sizes their hash set: 2..256 (one warp per
-// item), 257..1024 (one block, static table), > 1024 (one block, dynamic
+// item), 257..1024 (one block, 8192-slot table), > 1024 (one block, larger
 // table, or a binary search of the sorted row when even that is too
-// small).  Owners with d+ < 2 close no triangle.
+// small).  Owners with d+ < 2 close no triangle.  Rows are stored padded to
+// 16 bytes (kernels.h), so the partners' lists stream as uint4 chunks.
 #include "kernels.h"
 
 namespace tcg {
@@ -28,7 +29,8 @@ constexpr uint32_t SEG_B = 2048;     // largest partners per block item (IsectCo
 constexpr uint32_t WARP_MAX = 256;   // largest warp-owner out-degree (IsectConfig::warp_max)
 constexpr uint32_t MID_MAX = 1024;
 constexpr uint32_t EMPTY = 0xffffffffu;
-constexpr uint32_t GRAB = 8;  // warp items taken per work-cursor atomic
+constexpr uint32_t GRAB = 8;  // warp items taken per work-cursor atomic (at most 32)
+constexpr int NWIN = 2;  // 32-chunk windows in flight per warp step
 
 // warp + mid items <= owners + (m_p + in-list entries) / SEG_MIN, for any
 // schedule
@@ -43,6 +45,15 @@ uint64_t items_capacity(uint32_t n, uint64_t m)
 __device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t warp_max)
 {
     return d <= warp_max ? 0u : (d <= MID_MAX ? 1u : 2u);
+}
+
+// Partners per item of an owner of out-degree d in bucket b (see IsectConfig).
+__device__ __forceinline__ uint32_t seg_len(uint32_t d, uint32_t b, const IsectConfig &cfg)
+{
+    const uint32_t floor = b == 0 ? SEG_MIN : 256u, work = b == 0 ? cfg.work_w : cfg.work_b;
+    uint32_t s = b == 0 ? cfg.seg_w : cfg.seg_b;
+    while (s > floor && (uint64_t)s * d > work) s >>= 1;
+    return s;
 }
 
 // Item layout: owner in bits 0..31; single graph: segment in bits 32..63;
@@ -74,7 +85,7 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
             if (d >= 2) np = d + (inptr[x + 1] - inptr[x]);
         }
         const uint32_t gx = batch ? find_part_warp(bv.voff, bv.k, (uint32_t)(x < n ? x : n - 1)) : 0u;
-        const uint32_t b = bucket_of(d, cfg.warp_max), seg = b == 0 ? cfg.seg_w : cfg.seg_b;
+        const uint32_t b = bucket_of(d, cfg.warp_max), seg = seg_len(d, b, cfg);
         uint32_t nseg = (np + seg - 1) / seg;
         if (batch && nseg > 0x10000u) {  // segment index must fit 16 bits
             atomicOr(&st->err, ERR_OVERFLOW);
@@ -109,44 +120,65 @@ void build_items(const CountBuffers &b, cudaStream_t s)
 }
 
 // ======================================================================
-// Shared-memory hash set of an out-list: open addressing with linear
-// probing, at most a quarter full, so a probe sequence meets an empty slot
-// after ~1.4 slots on average.  Both loops are bounded by the table size.
+// Shared-memory hash set of an out-list: buckets of two slots (one 8-byte
+// load per lookup), filled in slot order, with linear probing over buckets.
+// At most an eighth of the slots are used where the table fits (a quarter
+// otherwise), so a lookup almost always ends at its first bucket: y is
+// absent as soon as a bucket without y has a free slot.  Both loops are
+// bounded by the table size.
 // ======================================================================
 
-__device__ __forceinline__ uint32_t tab_hash(uint32_t y, uint32_t shift) { return (y * 0x9e3779b1u) >> shift; }
+__device__ __forceinline__ uint32_t bucket_hash(uint32_t y, uint32_t shift) { return (y * 0x9e3779b1u) >> shift; }
 
-__device__ __forceinline__ void tab_insert(uint32_t *tab, uint32_t mask, uint32_t shift, uint32_t y)
+// nb = 2^k buckets: mask = nb - 1, shift = 32 - k.
+__device__ __forceinline__ void bucket_insert(uint2 *tab, uint32_t mask, uint32_t shift, uint32_t y)
 {
-    uint32_t h = tab_hash(y, shift);
+    uint32_t b = bucket_hash(y, shift);
     for (uint32_t it = 0; it <= mask; ++it) {
-        const uint32_t prev = atomicCAS(tab + h, EMPTY, y);
+        uint32_t *slot = reinterpret_cast<uint32_t *>(tab + b);
+        uint32_t prev = atomicCAS(slot, EMPTY, y);
         if (prev == EMPTY || prev == y) return;
-        h = (h + 1) & mask;
+        prev = atomicCAS(slot + 1, EMPTY, y);
+        if (prev == EMPTY || prev == y) return;
+        b = (b + 1) & mask;
     }
 }
 
-struct HashSet {
-    const uint32_t *tab;
+struct BucketSet {
+    const uint2 *tab;
     uint32_t mask, shift;
-    __device__ __forceinline__ bool contains(uint32_t y) const
+    __device__ __forceinline__ uint32_t contains(uint32_t y) const
     {
-        uint32_t h = tab_hash(y, shift);
-        uint32_t k = tab[h];
-        for (uint32_t it = 0; k != y && k != EMPTY && it < mask; ++it) {
-            h = (h + 1) & mask;
-            k = tab[h];
+        uint32_t b = bucket_hash(y, shift);
+        uint2 v = tab[b];
+        bool hit = v.x == y || v.y == y;
+        for (uint32_t it = 0; !hit && v.y != EMPTY && it < mask; ++it) {
+            b = (b + 1) & mask;
+            v = tab[b];
+            hit = v.x == y || v.y == y;
         }
-        return k == y;
+        return hit;
     }
 };
+
+// Table size (slots) for an owner of out-degree d: a power of two >= 8 d,
+// at most cap; 0 when even 4 d slots do not fit.
+__device__ __forceinline__ uint32_t table_slots(uint32_t d, uint32_t cap)
+{
+    uint32_t slots = 64;
+    while (slots < 8 * d && slots < cap) slots <<= 1;
+    return (slots <= cap && (uint64_t)slots >= 4ull * d) ? slots : 0u;
+}
+
+// Shift of the bucket hash for a table of `slots` slots (slots / 2 buckets).
+__device__ __forceinline__ uint32_t bucket_shift(uint32_t slots) { return 32u - (31u - __clz(slots >> 1)); }
 
 // Fallback for rows whose hash set does not fit on chip: binary search of
 // the sorted row in global memory.
 struct SortedRow {
     const uint32_t *a;
     uint32_t len;
-    __device__ __forceinline__ bool contains(uint32_t w) const
+    __device__ __forceinline__ uint32_t contains(uint32_t w) const
     {
         uint32_t lo = 0, hi = len;
         while (lo < hi) {
@@ -183,113 +215,104 @@ __device__ __forceinline__ void flush_tally(const Tally &t, unsigned long long *
     }
 }
 
-// Partner y of owner x: where its out-list starts, how many elements to
-// stream (0 when the pair is resolved by the other endpoint, closes no
-// triangle, or is heavy-class while the dense tensor path counts that class)
-// and the class of the pair's triangles.
-__device__ __forceinline__ void partner_of(const uint32_t *__restrict__ rowptr, const uint8_t *__restrict__ heavy,
-                                           uint32_t d, uint8_t hx, uint32_t y, bool is_out, bool skip_heavy,
-                                           uint32_t &start, uint32_t &len, uint32_t &cls)
+// Partner y of owner x (out-degree d, class hx): the chunk range of its
+// padded out-list and the class of the pair's triangles.  The range is empty
+// when the pair is resolved by the other endpoint, closes no triangle, or is
+// heavy-class while the dense tensor path counts that class.  Also counts
+// the partner's list entries into the tally.
+__device__ __forceinline__ void partner_of(const uint32_t *__restrict__ ptrp, const uint8_t *__restrict__ heavy,
+                                           uint32_t d, uint32_t hx, uint32_t y, bool is_out, bool skip_heavy,
+                                           uint32_t &c0, uint32_t &nc, uint32_t &cls, Tally &t)
 {
-    const uint32_t yb = rowptr[y], dy = rowptr[y + 1] - yb;
-    start = yb;
+    const PaddedRow py = padded_row(ptrp, y);
+    uint32_t len;
     if (is_out) {
-        len = (dy >= 1 && dy <= d) ? dy : 0u;
+        len = (py.d >= 1 && py.d <= d) ? py.d : 0u;
         cls = hx;
     } else {
-        len = dy >= 2 ? dy : 0u;
-        cls = len ? heavy[y] : 0u;
+        len = py.d >= 2 ? py.d : 0u;
+        cls = len ? __ldg(heavy + y) : 0u;
     }
     if (cls && skip_heavy) len = 0;  // the dense tensor path counts this class
+    c0 = py.beg >> 2;
+    nc = (len + 3) >> 2;
+    t.stream += len;
+    t.partners += len != 0;
 }
 
-// Streams the out-lists of up to 32 partners (one per lane: start, len, cls)
-// through the owner's set, 32 elements per step.  The partner of element e
-// is found in O(1): a bitmask of the partners whose lists start inside the
-// current 32-element window, plus the count of those that started before.
-// s_beg / s_pre: this warp's 32-entry shared scratch.
-template <class Set>
-__device__ __forceinline__ void stream_group(const uint32_t *__restrict__ col, const Set &set, uint32_t start,
-                                             uint32_t len, uint32_t cls, uint32_t *s_beg, uint32_t *s_pre, Tally &t,
-                                             bool account = true)
+// Lanes [a, b) of the warp hold consecutive parts with cnt >= 1 entries
+// each (other lanes cnt = 0), laid end to end at exclusive offsets pre.
+// Returns the lane of the part that holds entry `e` (< the total), given
+// `starts`, the bitmask of the parts beginning inside e's 32-entry window,
+// and `before`, the parts that began before it.
+__device__ __forceinline__ uint32_t part_lane(uint32_t a, uint32_t before, unsigned starts, unsigned upto)
+{
+    return (a + before + __popc(starts & upto) - 1) & 31u;
+}
+
+// Streams the padded out-lists of up to 32 partners (one per lane: chunks
+// [c0, c0 + nc) of the uint4 view of the columns, triangle class cls)
+// through the owners' sets.  The partners' chunks are laid end to end and
+// every step hands each lane one 16-byte chunk (4 list entries; the SENT
+// padding never matches).  A lane finds the partner of its chunk in O(1):
+// a bitmask of the partners whose chunks start inside the current 32-chunk
+// window, plus the count of those that started before it.  NWIN windows are
+// in flight per step.  MULTI: each partner looks up its own owner's set in
+// the warp's table (tinfo = first bucket | shift << 16); else all use set.
+// s_base / s_tinfo: this warp's 32-entry shared scratch.
+template <bool MULTI, class Set>
+__device__ __forceinline__ void stream_chunks(const uint4 *__restrict__ col4, const Set &set, const uint2 *wtab,
+                                              uint32_t c0, uint32_t nc, uint32_t cls, uint32_t tinfo,
+                                              uint32_t *s_base, uint32_t *s_tinfo, Tally &t)
 {
     const unsigned lane = lane_id();
-    const unsigned live = __ballot_sync(FULL, len != 0);
+    const unsigned live = __ballot_sync(FULL, nc != 0);
     if (!live) return;
-    const uint32_t inc = warp_incl_scan(len);
-    const uint32_t pre = inc - len;
+    const uint32_t inc = warp_incl_scan(nc);
+    const uint32_t pre = inc - nc;  // first chunk of this partner in the window sequence
     const uint32_t W = __shfl_sync(FULL, inc, 31);
     const uint32_t r = __popc(live & lanemask_lt());  // rank among live partners
-    const unsigned heavy_bits = __reduce_or_sync(FULL, (len != 0 && cls != 0) ? (1u << r) : 0u);
-    if (len) {
-        s_beg[r] = start;
-        s_pre[r] = pre;
+    const unsigned heavy_bits = __reduce_or_sync(FULL, (nc != 0 && cls != 0) ? (1u << r) : 0u);
+    if (nc) {
+        s_base[r] = c0 - pre;  // chunk of sequence position e: s_base[rank] + e
+        if (MULTI) s_tinfo[r] = tinfo;
     }
     __syncwarp();
     const unsigned upto = 0xffffffffu >> (31 - lane);  // bits 0..lane
     uint32_t before = 0;  // live partners starting before the window
-    for (uint32_t wb = 0; wb < W; wb += 32) {
-        const bool here = len != 0 && pre >= wb && pre - wb < 32;
-        const unsigned starts = __reduce_or_sync(FULL, here ? (1u << (pre - wb)) : 0u);
-        const uint32_t e = wb + lane;
-        if (e < W) {
-            const uint32_t k = before + __popc(starts & upto) - 1;
-            const uint32_t y = __ldg(col + s_beg[k] + (e - s_pre[k]));
-            const uint32_t hit = set.contains(y);
-            const uint32_t hc = (heavy_bits >> k) & 1u;
-            t.heavy += hit & hc;
-            t.light += hit & (hc ^ 1u);
+    uint32_t hl = 0, hh = 0;
+    for (uint32_t wb = 0; wb < W; wb += 32 * NWIN) {
+        uint32_t e[NWIN], k[NWIN];
+        uint4 q[NWIN];
+#pragma unroll
+        for (int i = 0; i < NWIN; ++i) {
+            const uint32_t off = pre - wb - 32u * i;
+            const unsigned sti = __reduce_or_sync(FULL, (nc != 0 && off < 32u) ? (1u << off) : 0u);
+            e[i] = wb + 32u * i + lane;
+            k[i] = before + __popc(sti & upto) - 1;
+            before += __popc(sti);
         }
-        before += __popc(starts);
+#pragma unroll
+        for (int i = 0; i < NWIN; ++i)
+            if (e[i] < W) q[i] = __ldg(col4 + (s_base[k[i]] + e[i]));
+#pragma unroll
+        for (int i = 0; i < NWIN; ++i) {
+            if (e[i] < W) {
+                uint32_t h;
+                if (MULTI) {
+                    const uint32_t ti = s_tinfo[k[i]], sh = ti >> 16;
+                    const BucketSet ms{wtab + (ti & 0xffffu), (1u << (32u - sh)) - 1u, sh};
+                    h = ms.contains(q[i].x) + ms.contains(q[i].y) + ms.contains(q[i].z) + ms.contains(q[i].w);
+                } else {
+                    h = set.contains(q[i].x) + set.contains(q[i].y) + set.contains(q[i].z) + set.contains(q[i].w);
+                }
+                if ((heavy_bits >> k[i]) & 1u) hh += h; else hl += h;
+            }
+        }
     }
-    if (account && lane == 0) {
-        t.stream += W;
-        t.partners += __popc(live);
-    }
-    __syncwarp();
-}
-
-// ---------------------------------------------------------------- list streaming
-
-// A partner list of at least LONG_LIST elements is streamed by one warp,
-// consecutive lanes on consecutive elements, two elements in flight per lane.
-constexpr uint32_t LONG_LIST = 32;
-
-template <class Set>
-__device__ __forceinline__ void stream_list(const uint32_t *__restrict__ col, const Set &set, uint32_t beg,
-                                            uint32_t len, uint32_t cls, Tally &t)
-{
-    const unsigned lane = lane_id();
-    uint32_t hits = 0;
-    uint32_t e = lane;
-    for (; e + 32 < len; e += 64) {
-        const uint32_t y0 = __ldg(col + beg + e), y1 = __ldg(col + beg + e + 32);
-        hits += set.contains(y0);
-        hits += set.contains(y1);
-    }
-    if (e < len) hits += set.contains(__ldg(col + beg + e));
-    if (cls) t.heavy += hits; else t.light += hits;
-}
-
-// Streams one warp's 32 partners (one per lane): the long lists one after the
-// other with the whole warp, the short ones packed through stream_group.
-template <class Set>
-__device__ __forceinline__ void stream_partners(const uint32_t *__restrict__ col, const Set &set, uint32_t start,
-                                                uint32_t len, uint32_t cls, uint32_t *s_beg, uint32_t *s_pre,
-                                                Tally &t)
-{
-    const bool is_long = len >= LONG_LIST;
-    if (len) {
-        t.stream += len;
-        t.partners += 1;
-    }
-    unsigned lm = __ballot_sync(FULL, is_long);
-    while (lm) {
-        const int k = __ffs(lm) - 1;
-        lm &= lm - 1;
-        stream_list(col, set, __shfl_sync(FULL, start, k), __shfl_sync(FULL, len, k), __shfl_sync(FULL, cls, k), t);
-    }
-    stream_group(col, set, start, is_long ? 0u : len, cls, s_beg, s_pre, t, false);
+    t.light += hl;
+    t.heavy += hh;
+    __syncwarp();  // s_base / s_tinfo are rewritten by the next call
 }
 
 // ---------------------------------------------------------------- warp items
@@ -298,7 +321,13 @@ constexpr int PW_THREADS = 256;
 constexpr int PW_WARPS = PW_THREADS / 32;
 constexpr uint32_t WTAB = 1024;  // per-warp table slots, >= 4 * WARP_MAX
 
-__global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__restrict__ rowptr,
+// A warp takes 32 warp items at a time (one per lane) and resolves them in
+// packs: runs of consecutive items of one graph whose hash sets fit the
+// warp's table together (sum of slots <= WTAB).  A pack's out-lists are
+// inserted, and its partners set up and streamed, as single flattened
+// sequences, so a pack of many small owners costs about what one owner with
+// the same number of partners and list entries costs.
+__global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__restrict__ ptrp,
                                                            const uint32_t *__restrict__ col,
                                                            const uint32_t *__restrict__ inptr,
                                                            const uint32_t *__restrict__ inlist,
@@ -306,14 +335,20 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
                                                            const uint8_t *__restrict__ heavy, DevState *st,
                                                            BatchView bv, IsectConfig cfg)
 {
-    __shared__ uint32_t s_tab[PW_WARPS][WTAB];
-    __shared__ uint32_t s_pre[PW_WARPS][32];
-    __shared__ uint32_t s_beg[PW_WARPS][32];
+    __shared__ uint2 s_tab[PW_WARPS][WTAB / 2];
+    __shared__ uint32_t s_base[PW_WARPS][32];
+    __shared__ uint32_t s_tinfo[PW_WARPS][32];
+    // the 32 items of the current grab, by lane: row start, in-list start,
+    // first partner, and out-degree | class << 31
+    __shared__ uint32_t s_beg[PW_WARPS][32], s_ib[PW_WARPS][32], s_p0[PW_WARPS][32], s_dh[PW_WARPS][32];
+    __shared__ uint32_t s_ti[PW_WARPS][32], s_pre[PW_WARPS][32];  // table info; prefix within the pack
     __shared__ unsigned long long red[33];
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    const unsigned upto = 0xffffffffu >> (31 - lane);
     const uint32_t nitems = (uint32_t)min((unsigned long long)st->nlist[0], (unsigned long long)wm_cap);
     const bool skip_heavy = st->dense != 0;
-    uint32_t *tab = s_tab[w];
+    const uint4 *col4 = reinterpret_cast<const uint4 *>(col);
+    uint2 *tab = s_tab[w];
     const bool batch = bv.k != 0;
     uint32_t cur_g = 0;  // graph whose counts this warp holds (batch)
     Tally t;
@@ -322,42 +357,105 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
         if (lane == 0) first = atomicAdd(&st->cursor[0], GRAB);
         first = __shfl_sync(FULL, first, 0);
         if (first >= nitems) break;
-        const uint32_t last = min(first + GRAB, nitems);
-        for (uint32_t idx = first; idx < last; ++idx) {
-            uint32_t x, seg, g;
-            split_item(items[idx], batch, x, seg, g);
-            if (batch && g != cur_g) {
-                flush_graph_counts(t, bv, cur_g);
-                cur_g = g;
+        const uint32_t got = min(GRAB, nitems - first);
+        // lane i: item first + i
+        uint32_t g = 0, d = 0, slots = 0, npart = 0;
+        if (lane < got) {
+            uint32_t x, seg;
+            split_item(items[first + lane], batch, x, seg, g);
+            const PaddedRow row = padded_row(ptrp, x);
+            d = row.d;
+            slots = d <= cfg.warp_max && d <= WARP_MAX ? table_slots(d, WTAB) : 0u;
+            uint32_t hx = 0, ib = 0, p0 = 0;
+            if (slots && d >= 2) {
+                hx = heavy[x];
+                ib = inptr[x];
+                const uint32_t np = d + (inptr[x + 1] - ib);
+                const uint32_t sl = seg_len(d, 0, cfg);
+                p0 = seg * sl;
+                npart = np > p0 ? min(np - p0, sl) : 0u;
+                if (seg == 0) t.table += d;
             }
-            const uint32_t beg = rowptr[x], d = rowptr[x + 1] - beg;
-            if (d > cfg.warp_max || d > WARP_MAX) {  // cannot happen unless the item list overflowed
-                if (lane == 0) atomicOr(&st->err, ERR_OVERFLOW);
+            if (!slots || d < 2 || !npart) {  // only if the item list overflowed
+                atomicOr(&st->err, ERR_OVERFLOW);
+                slots = 0;
+            }
+            s_beg[w][lane] = row.beg;
+            s_ib[w][lane] = ib;
+            s_p0[w][lane] = p0;
+            s_dh[w][lane] = d | (hx << 31);
+        }
+        const bool good = slots != 0;
+        uint32_t a = 0;
+        while (a < got) {
+            if (!__shfl_sync(FULL, good, a)) {  // skip a bad item
+                ++a;
                 continue;
             }
-            const uint8_t hx = heavy[x];
-            uint32_t slots = 64;
-            while (slots < 4 * d) slots <<= 1;  // <= WTAB since d <= WARP_MAX
-            const uint32_t shift = 32 - (31 - __clz(slots));
-            const HashSet set{tab, slots - 1, shift};
-            for (uint32_t i = lane; i < slots; i += 32) tab[i] = EMPTY;
-            __syncwarp();
-            for (uint32_t i = lane; i < d; i += 32) tab_insert(tab, slots - 1, shift, __ldg(col + beg + i));
-            __syncwarp();
-            if (seg == 0 && lane == 0) t.table += d;
-            const uint32_t ib = inptr[x], np = d + (inptr[x + 1] - ib);
-            const uint32_t p0 = seg * cfg.seg_w, p1 = min(np, p0 + cfg.seg_w);
-            for (uint32_t c0 = p0; c0 < p1; c0 += 32) {
-                const uint32_t j = c0 + lane;
-                uint32_t start = 0, len = 0, cls = 0;
-                if (j < p1) {
-                    const bool is_out = j < d;
-                    const uint32_t y = is_out ? __ldg(col + beg + j) : __ldg(inlist + ib + j - d);
-                    partner_of(rowptr, heavy, d, hx, y, is_out, skip_heavy, start, len, cls);
-                }
-                stream_partners(col, set, start, len, cls, s_beg[w], s_pre[w], t);
+            // the pack: lanes [a, b), one graph, sum of slots <= WTAB
+            const uint32_t ga = __shfl_sync(FULL, g, a);
+            const uint32_t sl = lane >= a && lane < got ? slots : 0u;
+            const uint32_t inc = warp_incl_scan(sl);
+            const bool ok = lane >= a && lane < got && good && inc <= WTAB && (!batch || g == ga);
+            const unsigned notok = ~__ballot_sync(FULL, ok) & (0xffffffffu << a);
+            const uint32_t b = notok ? min((uint32_t)__ffs(notok) - 1, got) : got;
+            const bool in_pack = lane >= a && lane < b;
+            const uint32_t total_buckets = __shfl_sync(FULL, inc, b - 1) >> 1;
+            if (in_pack) s_ti[w][lane] = ((inc - sl) >> 1) | (bucket_shift(slots) << 16);  // first bucket | shift
+            if (batch && ga != cur_g) {
+                flush_graph_counts(t, bv, cur_g);
+                cur_g = ga;
             }
-            __syncwarp();  // the table is rewritten by the next item
+            for (uint32_t i = lane; i < total_buckets; i += 32) tab[i] = make_uint2(EMPTY, EMPTY);
+            // insert the pack's out-lists, one entry per lane per step
+            {
+                const uint32_t c = in_pack ? d : 0u;
+                const uint32_t ic = warp_incl_scan(c), tot = __shfl_sync(FULL, ic, 31);
+                s_pre[w][lane] = ic - c;
+                __syncwarp();
+                const uint32_t pc = ic - c;
+                uint32_t before = 0;
+                for (uint32_t wb = 0; wb < tot; wb += 32) {
+                    const unsigned sts = __reduce_or_sync(FULL, (c != 0 && pc - wb < 32u) ? (1u << (pc - wb)) : 0u);
+                    const uint32_t L = part_lane(a, before, sts, upto);
+                    const uint32_t e = wb + lane;
+                    if (e < tot) {
+                        const uint32_t ti = s_ti[w][L], sh = ti >> 16;
+                        bucket_insert(tab + (ti & 0xffffu), (1u << (32u - sh)) - 1u, sh,
+                                      __ldg(col + s_beg[w][L] + (e - s_pre[w][L])));
+                    }
+                    before += __popc(sts);
+                }
+                __syncwarp();
+            }
+            // partners, 32 per step, each streamed through its owner's set
+            {
+                const uint32_t c = in_pack ? npart : 0u;
+                const uint32_t ic = warp_incl_scan(c), tot = __shfl_sync(FULL, ic, 31);
+                s_pre[w][lane] = ic - c;
+                __syncwarp();
+                const uint32_t pc = ic - c;
+                uint32_t before = 0;
+                for (uint32_t wb = 0; wb < tot; wb += 32) {
+                    const unsigned sts = __reduce_or_sync(FULL, (c != 0 && pc - wb < 32u) ? (1u << (pc - wb)) : 0u);
+                    const uint32_t L = part_lane(a, before, sts, upto);
+                    const uint32_t q = wb + lane;
+                    uint32_t c0 = 0, nc = 0, cls = 0, ti = 0;
+                    if (q < tot) {
+                        const uint32_t dh = s_dh[w][L], Ld = dh & 0x7fffffffu;
+                        const uint32_t j = s_p0[w][L] + (q - s_pre[w][L]);
+                        const bool is_out = j < Ld;
+                        const uint32_t y =
+                            is_out ? __ldg(col + s_beg[w][L] + j) : __ldg(inlist + s_ib[w][L] + j - Ld);
+                        ti = s_ti[w][L];
+                        partner_of(ptrp, heavy, Ld, dh >> 31, y, is_out, skip_heavy, c0, nc, cls, t);
+                    }
+                    stream_chunks<true>(col4, BucketSet{tab, 0, 0}, tab, c0, nc, cls, ti, s_base[w], s_tinfo[w], t);
+                    before += __popc(sts);
+                }
+            }
+            __syncwarp();  // the table and the pack arrays are rewritten next
+            a = b;
         }
     }
     if (batch) flush_graph_counts(t, bv, cur_g);
@@ -369,131 +467,108 @@ __global__ void __launch_bounds__(PW_THREADS, 5) k_probe_warp(const uint32_t *__
 constexpr int PB_THREADS = 256;
 constexpr int PB_WARPS = PB_THREADS / 32;
 constexpr uint32_t PB_PER_THREAD = SEG_B / PB_THREADS;  // partner slots set up per thread (at most)
-constexpr uint32_t MID_TAB = 4096;                      // >= 4 * MID_MAX slots
+constexpr uint32_t MID_TAB = 8192;                      // >= 8 * MID_MAX slots (dynamic shared memory)
 
-// One block resolves one item: up to SEG_B partners of one owner.  Partner
-// lists of at least 32 elements are streamed by one warp each, consecutive
-// lanes on consecutive elements (two in flight per lane); shorter lists are
-// packed 32 partners at a time through stream_group.  Warps take long lists
-// first, then short groups, from shared counters, so they finish within one
-// list of each other.
+// One block resolves one item: up to seg_b partners of one owner.  Every
+// thread sets up its share of the partners; the live ones are compacted
+// into shared memory, and the warps take them 32 at a time (stream_chunks)
+// from a shared counter, so they finish within one group of each other.
+// The owner's hash set sits in dynamic shared memory (tab_slots slots).
 template <bool DYN>
-__global__ void __launch_bounds__(PB_THREADS, 4) k_probe_block(const uint32_t *__restrict__ rowptr,
-                                                            const uint32_t *__restrict__ col,
-                                                            const uint32_t *__restrict__ inptr,
-                                                            const uint32_t *__restrict__ inlist,
-                                                            const uint64_t *__restrict__ items, uint64_t wm_cap,
-                                                            const uint8_t *__restrict__ heavy, DevState *st,
-                                                            uint32_t tab_slots, uint64_t cap, BatchView bv,
-                                                            IsectConfig cfg)
+__global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const uint32_t *__restrict__ ptrp,
+                                                                      const uint32_t *__restrict__ col,
+                                                                      const uint32_t *__restrict__ inptr,
+                                                                      const uint32_t *__restrict__ inlist,
+                                                                      const uint64_t *__restrict__ items,
+                                                                      uint64_t wm_cap,
+                                                                      const uint8_t *__restrict__ heavy,
+                                                                      DevState *st, uint32_t tab_slots,
+                                                                      uint64_t cap, BatchView bv, IsectConfig cfg)
 {
-    extern __shared__ uint32_t s_dyn[];
-    __shared__ uint32_t s_static[DYN ? 1 : MID_TAB];
-    uint32_t *tab = DYN ? s_dyn : s_static;
-    // partners: long lists from the front, short ones from the back
-    __shared__ uint32_t s_pbeg[SEG_B];
-    __shared__ uint32_t s_plen[SEG_B];
-    __shared__ uint8_t s_pcls[SEG_B];
-    __shared__ uint32_t s_pre[PB_WARPS][32];
-    __shared__ uint32_t s_beg[PB_WARPS][32];
+    extern __shared__ uint2 tab[];
+    __shared__ uint32_t s_c0[SEG_B];
+    __shared__ uint32_t s_ncc[SEG_B];  // nc << 1 | cls
+    __shared__ uint32_t s_base[PB_WARPS][32];
     __shared__ uint32_t wt[33];
     __shared__ unsigned long long red[33];
-    __shared__ uint32_t s_idx, s_next_long, s_next_short;
+    __shared__ uint32_t s_idx, s_next;
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     const uint32_t b = DYN ? 2 : 1;
     const uint32_t nitems =
         (uint32_t)min((unsigned long long)st->nlist[b], (unsigned long long)(DYN ? cap - wm_cap : wm_cap));
     const bool skip_heavy = st->dense != 0;
+    const uint4 *col4 = reinterpret_cast<const uint4 *>(col);
     Tally t;
     for (;;) {
         if (threadIdx.x == 0) {
             s_idx = atomicAdd(&st->cursor[b], 1u);
-            s_next_long = 0;
-            s_next_short = 0;
+            s_next = 0;
         }
         __syncthreads();
         const uint32_t idx = s_idx;
         if (idx >= nitems) break;
         uint32_t x, seg, g;
         split_item(DYN ? items[wm_cap + idx] : items[wm_cap - 1 - idx], bv.k != 0, x, seg, g);
-        const uint32_t beg = rowptr[x], d = rowptr[x + 1] - beg;
-        const uint8_t hx = heavy[x];
-        // a power of two >= 4 d slots, when that fits
-        uint32_t slots = 64;
-        while (slots < 4 * d && slots < (1u << 30)) slots <<= 1;
-        const bool use_tab = slots <= tab_slots && (uint64_t)slots >= 4ull * d;
-        const uint32_t shift = 32 - (31 - __clz(slots));
-        if (use_tab) {
-            for (uint32_t i = threadIdx.x; i < slots; i += PB_THREADS) tab[i] = EMPTY;
+        const PaddedRow row = padded_row(ptrp, x);
+        const uint32_t d = row.d;
+        const uint32_t hx = heavy[x];
+        const uint32_t slots = table_slots(d, tab_slots);
+        const BucketSet set{tab, slots ? (slots >> 1) - 1 : 0u, slots ? bucket_shift(slots) : 0u};
+        if (slots) {
+            for (uint32_t i = threadIdx.x; i < (slots >> 1); i += PB_THREADS) tab[i] = make_uint2(EMPTY, EMPTY);
             __syncthreads();
-            for (uint32_t i = threadIdx.x; i < d; i += PB_THREADS) tab_insert(tab, slots - 1, shift, __ldg(col + beg + i));
+            for (uint32_t i = threadIdx.x; i < d; i += PB_THREADS)
+                bucket_insert(tab, set.mask, set.shift, __ldg(col + row.beg + i));
         }
         if (seg == 0 && threadIdx.x == 0) t.table += d;
         const uint32_t ib = inptr[x], np = d + (inptr[x + 1] - ib);
-        const uint32_t p0 = seg * cfg.seg_b, p1 = min(np, p0 + cfg.seg_b);
-        const uint32_t per = cfg.seg_b / PB_THREADS;  // <= PB_PER_THREAD
-        // set up this thread's PB_PER_THREAD consecutive partners
-        uint32_t pstart[PB_PER_THREAD], plen[PB_PER_THREAD], pcls[PB_PER_THREAD];
-        uint32_t mine = 0;  // (long count << 16) | short count
+        const uint32_t sl = seg_len(d, 1, cfg);
+        const uint32_t p0 = seg * sl, p1 = min(np, p0 + sl);
+        const uint32_t per = sl / PB_THREADS;  // <= PB_PER_THREAD
+        // set up this thread's `per` consecutive partners
+        uint32_t pc0[PB_PER_THREAD], pncc[PB_PER_THREAD];
+        uint32_t mine = 0;
 #pragma unroll
         for (uint32_t q = 0; q < PB_PER_THREAD; ++q) {
             const uint32_t j = p0 + threadIdx.x * per + q;
-            pstart[q] = 0;
-            plen[q] = 0;
-            pcls[q] = 0;
+            uint32_t c0 = 0, nc = 0, cls = 0;
             if (q < per && j < p1) {
                 const bool is_out = j < d;
-                const uint32_t y = is_out ? __ldg(col + beg + j) : __ldg(inlist + ib + j - d);
-                partner_of(rowptr, heavy, d, hx, y, is_out, skip_heavy, pstart[q], plen[q], pcls[q]);
+                const uint32_t y = is_out ? __ldg(col + row.beg + j) : __ldg(inlist + ib + j - d);
+                partner_of(ptrp, heavy, d, hx, y, is_out, skip_heavy, c0, nc, cls, t);
             }
-            if (plen[q]) {
-                mine += plen[q] >= LONG_LIST ? (1u << 16) : 1u;
-                t.stream += plen[q];
-                t.partners += 1;
-            }
+            pc0[q] = c0;
+            pncc[q] = (nc << 1) | cls;
+            mine += nc != 0;
         }
-        uint32_t tot;
-        const uint32_t ex = block_excl_scan(mine, wt, &tot);  // also orders the set build
-        uint32_t rl = ex >> 16, rs = SEG_B - 1 - (ex & 0xffffu);
+        uint32_t nlive;
+        uint32_t r = block_excl_scan(mine, wt, &nlive);  // also orders the set build
 #pragma unroll
         for (uint32_t q = 0; q < PB_PER_THREAD; ++q) {
-            if (plen[q]) {
-                const uint32_t r = plen[q] >= LONG_LIST ? rl++ : rs--;
-                s_pbeg[r] = pstart[q];
-                s_plen[r] = plen[q];
-                s_pcls[r] = (uint8_t)pcls[q];
+            if (pncc[q] >> 1) {
+                s_c0[r] = pc0[q];
+                s_ncc[r] = pncc[q];
+                ++r;
             }
         }
-        const uint32_t nlong = tot >> 16, nshort = tot & 0xffffu;
-        const uint32_t nshort_groups = (nshort + 31) / 32;
+        const uint32_t ngroups = (nlive + 31) / 32;
         __syncthreads();  // partners and set are complete
         for (;;) {
-            uint32_t k = 0;
-            if (lane == 0) k = atomicAdd(&s_next_long, 1u);
-            k = __shfl_sync(FULL, k, 0);
-            if (k >= nlong) break;
-            if (use_tab)
-                stream_list(col, HashSet{tab, slots - 1, shift}, s_pbeg[k], s_plen[k], s_pcls[k], t);
-            else
-                stream_list(col, SortedRow{col + beg, d}, s_pbeg[k], s_plen[k], s_pcls[k], t);
-        }
-        for (;;) {
-            uint32_t g = 0;
-            if (lane == 0) g = atomicAdd(&s_next_short, 1u);
-            g = __shfl_sync(FULL, g, 0);
-            if (g >= nshort_groups) break;
-            const uint32_t i = g * 32 + lane;
-            uint32_t start = 0, len = 0, cls = 0;
-            if (i < nshort) {
-                const uint32_t r = SEG_B - 1 - i;
-                start = s_pbeg[r];
-                len = s_plen[r];
-                cls = s_pcls[r];
+            uint32_t grp = 0;
+            if (lane == 0) grp = atomicAdd(&s_next, 1u);
+            grp = __shfl_sync(FULL, grp, 0);
+            if (grp >= ngroups) break;
+            const uint32_t i = grp * 32 + lane;
+            uint32_t c0 = 0, nc = 0, cls = 0;
+            if (i < nlive) {
+                c0 = s_c0[i];
+                nc = s_ncc[i] >> 1;
+                cls = s_ncc[i] & 1u;
             }
-            if (use_tab)
-                stream_group(col, HashSet{tab, slots - 1, shift}, start, len, cls, s_beg[w], s_pre[w], t, false);
+            if (slots)
+                stream_chunks<false>(col4, set, tab, c0, nc, cls, 0u, s_base[w], nullptr, t);
             else
-                stream_group(col, SortedRow{col + beg, d}, start, len, cls, s_beg[w], s_pre[w], t, false);
+                stream_chunks<false>(col4, SortedRow{col + row.beg, d}, tab, c0, nc, cls, 0u, s_base[w], nullptr, t);
         }
         if (bv.k != 0) flush_graph_counts(t, bv, g);
         __syncthreads();  // every warp is done with this owner
@@ -501,18 +576,27 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_probe_block(const uint32_t *_
     flush_tally(t, red, st);
 }
 
-// Static + dynamic shared memory of the large-owner kernel must fit the
+// Static + dynamic shared memory of the block kernels must fit the
 // function's opt-in limit, which starts at 48 KiB in every process: raise it
-// once per process and device to the largest size requested so far.
+// once per process and device (to the largest size requested so far for the
+// large-owner kernel).
 void intersect_prepare(int dyn_smem_bytes)
 {
     static int set_bytes[64] = {};
+    static bool mid_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || dyn_smem_bytes > set_bytes[dev]) {
+    const bool known = dev >= 0 && dev < 64;
+    if (!known || !mid_set[dev]) {
+        if (cudaFuncSetAttribute(k_probe_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(MID_TAB * 4)) == cudaSuccess &&
+            known)
+            mid_set[dev] = true;
+    }
+    if (!known || dyn_smem_bytes > set_bytes[dev]) {
         if (cudaFuncSetAttribute(k_probe_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_bytes) ==
                 cudaSuccess &&
-            dev >= 0 && dev < 64)
+            known)
             set_bytes[dev] = dyn_smem_bytes;
     }
 }
@@ -521,14 +605,14 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
 {
     if (b.n == 0 || b.m == 0) return;
     const uint64_t wm = wm_capacity(b.n, b.m);
-    k_probe_warp<<<152 * 8, PW_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy, b.st,
-                                                b.bv, b.cfg);
-    note_launch();
-    k_probe_block<false><<<152 * 8, PB_THREADS, 0, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm, b.heavy,
-                                                         b.st, MID_TAB, b.items_cap, b.bv, b.cfg);
-    note_launch();
     intersect_prepare(dyn_smem_bytes);
-    k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.rowptr, b.col, b.inptr, b.inlist, b.items, wm,
+    k_probe_warp<<<152 * 4, PW_THREADS, 0, s>>>(b.ptrp, b.col, b.inptr, b.inlist, b.items, wm, b.heavy, b.st, b.bv,
+                                                b.cfg);
+    note_launch();
+    k_probe_block<false><<<152 * 4, PB_THREADS, MID_TAB * 4, s>>>(b.ptrp, b.col, b.inptr, b.inlist, b.items, wm,
+                                                                   b.heavy, b.st, MID_TAB, b.items_cap, b.bv, b.cfg);
+    note_launch();
+    k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.ptrp, b.col, b.inptr, b.inlist, b.items, wm,
                                                                 b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
                                                                 b.items_cap, b.bv, b.cfg);
     note_launch();

@@ -63,17 +63,38 @@ struct InListArgs {
 // uint32 (digit-major), ntiles = ceil(n_max / RX_TILE).  If dplus is
 // non-NULL the count kernel also histograms (item >> 32) into it.  The
 // scatter writes the full items to out, or when out_low32 is non-NULL only
-// their low 32 bits there.  With `in` non-NULL the pass also builds the
-// in-lists described above.
+// their low 32 bits there, at position + padoff[item >> 32] when padoff is
+// non-NULL.  With `in` non-NULL the pass also builds the in-lists described
+// above.
 void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
                 uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
-                const InListArgs *in, cudaStream_t s);
+                const InListArgs *in, cudaStream_t s, const uint32_t *padoff = nullptr);
+
+// Padded rows.  The column array of the counting kernels stores every row
+// from a 16-byte boundary, padded with SENT up to a multiple of 4 entries,
+// so that rows stream as aligned uint4 chunks.  ptrp[x] (x <= n) holds the
+// padded start of row x (a multiple of 4) with the row's pad count
+// (0..3) in its low two bits; ptrp[n] is the padded total.
+constexpr uint32_t SENT = 0xfffffffeu;  // never a vertex id (ids < 2^32 - 2)
+// Capacity (uint32 entries) of the padded column array for n, m.
+inline uint64_t colp_capacity(uint32_t n, uint64_t m) { return m + 3 * (m < n ? m : (uint64_t)n) + 4; }
+struct PaddedRow {
+    uint32_t beg;  // padded start (multiple of 4)
+    uint32_t d;    // out-degree
+};
+__device__ __forceinline__ PaddedRow padded_row(const uint32_t *__restrict__ ptrp, uint32_t x)
+{
+    const uint32_t a = __ldg(ptrp + x), b = __ldg(ptrp + x + 1);
+    return PaddedRow{a & ~3u, (b & ~3u) - (a & ~3u) - (a & 3u)};
+}
 
 // Degree-oriented CSR of the sampled graph (single graph or batch union):
 // stable LSD radix sort of (src << 32 | dst) on the src bits (at least two
 // passes), the first pass sampling and orienting the canonical keys, the
-// last one also building the in-lists.  rowptr [n + 1] and inptr [n + 2]
-// are zeroed here; col and inlist are placed in bufA / bufB.
+// last one also building the in-lists and writing the columns straight into
+// the padded layout.  rowptr [n + 1] and inptr [n + 2] are zeroed here;
+// *col = colp (padded columns, colp_capacity entries), ptrp [n + 2] its row
+// pointers, and the in-lists are placed in bufA / bufB.
 struct CsrArgs {
     const uint64_t *ekey;
     uint64_t m;
@@ -85,6 +106,7 @@ struct CsrArgs {
     const unsigned long long *m_sampled_dev;
     uint64_t *bufA, *bufB;
     uint32_t *rowptr, *inptr, *hist, *scan;
+    uint32_t *colp, *ptrp;
 };
 void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t s);
 
@@ -102,13 +124,18 @@ void unique_keys(const uint64_t *keys, uint64_t m_in, uint64_t *out, uint32_t *t
 // ---------------------------------------------------------------- count.cu
 // Schedule of the intersection kernels (isect.cu); any choice gives the same
 // counts.  warp_max: owners with 2 <= d+ <= warp_max are resolved by one warp
-// (32 .. 256); seg_w / seg_b: partners per work item of the warp / block
-// kernels (seg_w in [SEG_MIN, 1024], seg_b in [256, 2048], powers of two).
-constexpr uint32_t SEG_MIN = 128;
+// (32 .. 256); seg_w / seg_b: most partners per work item of the warp / block
+// kernels (seg_w in [SEG_MIN, 1024], seg_b in [256, 2048], powers of two);
+// work_w / work_b: an owner of out-degree d gets items of the largest power
+// of two <= seg_w (seg_b) partners with partners * d <= work_w (work_b), but
+// at least SEG_MIN (256), which bounds the list entries an item streams.
+constexpr uint32_t SEG_MIN = 64;
 struct IsectConfig {
     uint32_t warp_max = 256;
     uint32_t seg_w = 512;
     uint32_t seg_b = 2048;
+    uint32_t work_w = 1u << 14;
+    uint32_t work_b = 1u << 19;
 };
 
 struct CountBuffers {
@@ -118,7 +145,8 @@ struct CountBuffers {
     uint32_t *deg;          // [n]
     uint8_t *heavy;         // [n]
     uint32_t *rowptr;       // [n + 1]
-    uint32_t *col;          // [m_p] CSR columns
+    uint32_t *col;          // padded CSR columns (see SENT / ptrp)
+    uint32_t *ptrp;         // [n + 2] padded row pointers
     uint32_t *inptr;        // [n + 2] in-list offsets
     uint32_t *inlist;       // in-lists
     uint64_t *items;        // owner work items [items_cap]
@@ -153,6 +181,7 @@ struct UnionScratch {
     uint64_t *ekey = nullptr, *bufA = nullptr, *bufB = nullptr, *items = nullptr;
     uint64_t items_cap = 0;
     uint32_t *deg = nullptr, *rowptr = nullptr, *inptr = nullptr, *hist = nullptr, *scan = nullptr;
+    uint32_t *colp = nullptr, *ptrp = nullptr;
     uint8_t *heavy = nullptr;
     DevState *st = nullptr;
     uint64_t *eoff = nullptr, *thr = nullptr, *seed_mix = nullptr;

@@ -29,12 +29,14 @@ constexpr uint64_t na_round(uint64_t b) { return (b + NA_ALIGN - 1) / NA_ALIGN *
 constexpr uint64_t NA_TILES = (NA_M + RX_TILE - 1) / RX_TILE;
 constexpr uint64_t NA_HIST = NA_TILES << RX_MAX_BITS;  // uint32 entries
 constexpr uint64_t NA_SCAN = (NA_HIST > NA_N + 2 ? NA_HIST : NA_N + 2) / SC_CHUNK + 2;
-constexpr uint64_t NA_ITEMS = NA_N + 2 * NA_M / 256 + NA_M / 512 + 256;  // >= items_capacity(N, M)
+constexpr uint64_t NA_ITEMS = NA_N + 2 * NA_M / SEG_MIN + NA_M / 1024 + 2 * NA_M / 256 + 256;  // >= items_capacity(N, M)
+constexpr uint64_t NA_COLP = NA_M + 3 * NA_M + 4;  // >= colp_capacity(N, M)
 constexpr uint64_t NA_BYTES = 3 * na_round(8 * NA_M)                     // ekey, bufA, bufB
                               + na_round(4 * NA_HIST) + na_round(4 * NA_SCAN)
                               + 2 * na_round(4 * (NA_N + 2))             // deg, rowptr
                               + na_round(NA_N)                           // heavy
                               + na_round(4 * (NA_N + 2))                 // inptr
+                              + na_round(4 * NA_COLP) + na_round(4 * (NA_N + 2))  // colp, ptrp
                               + na_round(8 * NA_ITEMS) + na_round(sizeof(DevState)) + na_round(sizeof(tc_result));
 
 static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
@@ -119,10 +121,12 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     uint32_t *rowptr = c.take<uint32_t>(NA_N + 2);
     uint8_t *heavy = c.take<uint8_t>(NA_N);
     uint32_t *inptr = c.take<uint32_t>(NA_N + 2);
+    uint32_t *colp = c.take<uint32_t>(NA_COLP);
+    uint32_t *ptrp = c.take<uint32_t>(NA_N + 2);
     uint64_t *items = c.take<uint64_t>(NA_ITEMS);
     DevState *st = c.take<DevState>(1);
     tc_result *res = c.take<tc_result>(1);
-    if (c.used > NA_BYTES || items_capacity(n, m_in) > NA_ITEMS) return TC_ECUDA;
+    if (c.used > NA_BYTES || items_capacity(n, m_in) > NA_ITEMS || colp_capacity(n, m_in) > NA_COLP) return TC_ECUDA;
 
     // ---- canonical keys: (min, max), no self-loops or repeats, sorted
     cudaMemsetAsync(st, 0, sizeof(DevState), s);
@@ -164,6 +168,7 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     cb.heavy = heavy;
     cb.rowptr = rowptr;
     cb.col = nullptr;
+    cb.ptrp = ptrp;
     cb.inptr = inptr;
     cb.inlist = nullptr;
     cb.items = items;
@@ -174,31 +179,24 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     sample_degree(cb, seed_mix, thr, s);
     partition(cb, s);
     if (m > 0) {
-        cudaMemsetAsync(rowptr, 0, ((size_t)n + 1) * 4, s);
-        cudaMemsetAsync(inptr, 0, ((size_t)n + 2) * 4, s);
-        int widths[4];
-        const int npass = na_widths(na_bits(n), true, widths);
-        uint64_t *bufs[2] = {bufA, bufB};
-        const uint64_t *in = ekey;
-        int cur = 0, shift = 32;
-        for (int k = 0; k < npass; ++k) {
-            const bool last = k + 1 == npass;
-            ItemSource src = k == 0 ? ItemSource{ItemSource::SAMPLE_ORIENT, ekey, m, nullptr, deg, seed_mix, thr}
-                                    : ItemSource{ItemSource::PLAIN, in, 0, &st->m_sampled, nullptr, 0, 0};
-            uint64_t *outb = bufs[cur];
-            InListArgs il{rowptr, inptr, nullptr, n};
-            if (last) {
-                cb.col = reinterpret_cast<uint32_t *>(outb);
-                cb.inlist = reinterpret_cast<uint32_t *>(outb) + m;
-                il.inlist = cb.inlist;
-            }
-            radix_pass(src, m, shift, widths[k], hist, scan, k == 0 ? rowptr : nullptr, last ? nullptr : outb,
-                       last ? cb.col : nullptr, last ? &il : nullptr, s);
-            in = outb;
-            cur ^= 1;
-            shift += widths[k];
-        }
-        scan_excl_u32(rowptr, (uint64_t)n + 1, nullptr, scan, s);
+        CsrArgs a;
+        a.ekey = ekey;
+        a.m = m;
+        a.n = n;
+        a.nbits = na_bits(n);
+        a.deg = deg;
+        a.seed_mix = seed_mix;
+        a.thr = thr;
+        a.m_sampled_dev = &st->m_sampled;
+        a.bufA = bufA;
+        a.bufB = bufB;
+        a.rowptr = rowptr;
+        a.inptr = inptr;
+        a.hist = hist;
+        a.scan = scan;
+        a.colp = colp;
+        a.ptrp = ptrp;
+        csr_build(a, &cb.col, &cb.inlist, s);
         build_items(cb, s);
         // every out-degree is at most sqrt(2 m) <= 725 here: the smallest
         // table of the large-owner kernel (8192 slots) always suffices

@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int 
 __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, int shift, int width,
                                                               const uint32_t *__restrict__ offs, uint32_t ntiles,
                                                               uint64_t *__restrict__ out,
-                                                              uint32_t *__restrict__ out_low32, InListArgs in)
+                                                              uint32_t *__restrict__ out_low32, InListArgs in,
+                                                              const uint32_t *__restrict__ padoff)
 {
     constexpr int NW = RX_THREADS / 32;
     __shared__ uint32_t whist[NW][RX_BINS];
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
         const uint32_t d = packed[j] >> 16, r = packed[j] & 0xffffu;
         const uint32_t pos = tbase[d] + whist[warp][d] + r;
         if (out_low32)
-            out_low32[pos] = (uint32_t)items[j];
+            out_low32[padoff ? pos + __ldg(padoff + (items[j] >> 32)) : pos] = (uint32_t)items[j];
         else
             out[pos] = items[j];
         if (in.P && in_pair(in, items[j])) {
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
 
 void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
                 uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
-                const InListArgs *in, cudaStream_t s)
+                const InListArgs *in, cudaStream_t s, const uint32_t *padoff)
 {
     const InListArgs inl = in ? *in : InListArgs{nullptr, nullptr, nullptr, 0};
     const uint64_t ntiles = ceil_div(n_max, RX_TILE);
@@ -227,7 +228,7 @@ void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uin
     // in-list offsets: P[1 .. n+1] = exclusive scan of the counts, P[0] = 0
     if (inl.P) scan_excl_u32(inl.P + 1, (uint64_t)inl.n + 1, nullptr, scan_scratch, s);
     k_radix_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, out,
-                                                            out_low32, inl); note_launch();
+                                                            out_low32, inl, padoff); note_launch();
 }
 
 // ======================================================================
@@ -336,6 +337,40 @@ void unique_keys(const uint64_t *keys, uint64_t m_in, uint64_t *out, uint32_t *t
 
 namespace tcg {
 
+// ======================================================================
+// Padded rows (see SENT in kernels.h).
+// ======================================================================
+
+__device__ __forceinline__ uint32_t pad_of(uint32_t d) { return (4u - (d & 3u)) & 3u; }
+
+// ptrp[x] = pad count of row x (x < n), ptrp[n] = 0; rowptr holds the
+// out-degree counts.
+__global__ void k_pad_counts(const uint32_t *__restrict__ dplus, uint32_t n, uint32_t *__restrict__ ptrp)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride)
+        ptrp[x] = x < n ? pad_of(dplus[x]) : 0u;
+}
+
+// ptrp holds the exclusive scan of the pad counts and rowptr the row
+// offsets: write each row's padding and turn ptrp into padded starts
+// tagged with the pad count.
+__global__ void k_pad_finish(const uint32_t *__restrict__ rowptr, uint32_t n, uint32_t *__restrict__ ptrp,
+                             uint32_t *__restrict__ colp)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
+        const uint32_t start = rowptr[x] + ptrp[x];
+        if (x == n) {
+            ptrp[x] = start;
+            continue;
+        }
+        const uint32_t d = rowptr[x + 1] - rowptr[x], pad = pad_of(d);
+        for (uint32_t i = 0; i < pad; ++i) colp[start + d + i] = SENT;
+        ptrp[x] = start | pad;
+    }
+}
+
 void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t s)
 {
     cudaMemsetAsync(a.rowptr, 0, ((size_t)a.n + 1) * 4, s);
@@ -363,19 +398,27 @@ void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t
         uint64_t *out = bufs[cur];
         InListArgs il{a.rowptr, a.inptr, nullptr, a.n};
         if (last) {
-            // col in the first 4 m bytes of the output buffer, the in-lists in
-            // the second half (the input buffer is still being read)
-            *col = reinterpret_cast<uint32_t *>(out);
-            *inlist = reinterpret_cast<uint32_t *>(out) + a.m;
+            // padded columns in colp, the in-lists in the output buffer (the
+            // input buffer is still being read)
+            *col = a.colp;
+            *inlist = reinterpret_cast<uint32_t *>(out);
             il.inlist = *inlist;
         }
         radix_pass(src, a.m, shift, widths[p], a.hist, a.scan, p == 0 ? a.rowptr : nullptr, last ? nullptr : out,
-                   last ? *col : nullptr, last ? &il : nullptr, s);
+                   last ? *col : nullptr, last ? &il : nullptr, s, last ? a.ptrp : nullptr);
+        if (p == 0) {
+            // out-degrees are complete: pad offsets for the last pass
+            k_pad_counts<<<grid_for((uint64_t)a.n + 1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp);
+            note_launch();
+            scan_excl_u32(a.ptrp, (uint64_t)a.n + 1, nullptr, a.scan, s);
+        }
         in = out;
         cur ^= 1;
         shift += widths[p];
     }
     scan_excl_u32(a.rowptr, (uint64_t)a.n + 1, nullptr, a.scan, s);
+    k_pad_finish<<<grid_for((uint64_t)a.n + 1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp, a.colp);
+    note_launch();
 }
 
 }  // namespace tcg
