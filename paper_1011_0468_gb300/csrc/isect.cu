@@ -229,8 +229,8 @@ __device__ __forceinline__ void partner_of(const uint32_t *__restrict__ ptrp, co
     if (is_out) {
         len = (py.d >= 1 && py.d <= d) ? py.d : 0u;
         cls = hx;
-    } else {
-        len = py.d >= 2 ? py.d : 0u;
+    } else {  // in-lists hold every in-neighbour: keep the ones this owner resolves
+        len = (py.d >= 2 && py.d < d) ? py.d : 0u;
         cls = len ? __ldg(heavy + y) : 0u;
     }
     if (cls && skip_heavy) len = 0;  // the dense tensor path counts this class

@@ -46,13 +46,12 @@ struct ItemSource {
     BatchView bv;                       // SAMPLE_ORIENT over a batch union (bv.k > 0)
 };
 
-// Optional by-product of a radix pass over oriented edges (src << 32 | dst):
-// the in-lists of the pairs whose source has the strictly smaller
-// out-degree, grouped by dst.  dplus holds the complete out-degree counts.
-// P has n + 2 entries and must be zero on entry; afterwards the in-list of
-// vertex v is inlist[P[v] .. P[v + 1]) (in no particular order).
+// Optional by-product of the last radix pass over oriented edges
+// (src << 32 | dst): the in-lists, every pair appended to its dst's list.  P
+// has n + 2 entries; on entry P[0] = 0 and P[1 + v] = the start of v's
+// in-list; afterwards the in-list of vertex v is inlist[P[v] .. P[v + 1])
+// (in no particular order).
 struct InListArgs {
-    const uint32_t *dplus;
     uint32_t *P;
     uint32_t *inlist;
     uint32_t n;
@@ -64,8 +63,8 @@ struct InListArgs {
 // non-NULL the count kernel also histograms (item >> 32) into it.  The
 // scatter writes the full items to out, or when out_low32 is non-NULL only
 // their low 32 bits there, at position + padoff[item >> 32] when padoff is
-// non-NULL.  With `in` non-NULL the pass also builds the in-lists described
-// above.
+// non-NULL.  With `in` non-NULL the scatter also fills the in-lists
+// described above.
 void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
                 uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
                 const InListArgs *in, cudaStream_t s, const uint32_t *padoff = nullptr);
@@ -91,8 +90,9 @@ __device__ __forceinline__ PaddedRow padded_row(const uint32_t *__restrict__ ptr
 // Degree-oriented CSR of the sampled graph (single graph or batch union):
 // stable LSD radix sort of (src << 32 | dst) on the src bits (at least two
 // passes), the first pass sampling and orienting the canonical keys, the
-// last one also building the in-lists and writing the columns straight into
-// the padded layout.  rowptr [n + 1] and inptr [n + 2] are zeroed here;
+// last one also filling the in-lists (every kept edge, under its dst; their
+// sizes deg - d+ are known after the first pass) and writing the columns
+// straight into the padded layout.  rowptr [n + 1] and inptr [n + 2] are zeroed here;
 // *col = colp (padded columns, colp_capacity entries), ptrp [n + 2] its row
 // pointers, and the in-lists are placed in bufA / bufB.
 struct CsrArgs {

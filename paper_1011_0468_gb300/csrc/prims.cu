@@ -112,22 +112,19 @@ __device__ __forceinline__ uint32_t item_graph(const ItemSource &src, uint64_t i
     return find_part_warp(src.bv.eoff, src.bv.k, i < n ? i : n - 1);
 }
 
-// The in-list by-product: pair (src -> dst) belongs to dst's in-list iff
-// d+(src) < d+(dst).
-__device__ __forceinline__ bool in_pair(const InListArgs &in, uint64_t item)
-{
-    return __ldg(in.dplus + (item >> 32)) < __ldg(in.dplus + (uint32_t)item);
-}
-
+// Per-tile digit counts (per-warp shared histograms, summed at the end), plus
+// the out-degree histogram (first pass).
 __global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int shift, int width,
                                                             uint32_t *__restrict__ hist, uint32_t ntiles,
-                                                            uint32_t *__restrict__ dplus, InListArgs in)
+                                                            uint32_t *__restrict__ dplus)
 {
-    __shared__ uint32_t cnt[RX_BINS];
+    constexpr int NW = RX_THREADS / 32;
+    __shared__ uint32_t cnt[NW][RX_BINS];
     const uint64_t n = src.n_dev ? *src.n_dev : src.n_host;
     const uint32_t tile = blockIdx.x;
     const int nb = 1 << width;
-    for (int d = threadIdx.x; d < nb; d += RX_THREADS) cnt[d] = 0;
+    const unsigned warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < NW * RX_BINS; i += RX_THREADS) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const uint64_t base = (uint64_t)tile * RX_TILE;
     if (base < n) {
@@ -137,19 +134,29 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int 
             uint64_t item = 0;
             const uint32_t g = item_graph(src, i, n);
             const bool valid = i < n && load_item(src, i, item, g);
-            const uint32_t d = valid ? ((uint32_t)(item >> shift) & mask) : 0xffffffffu;
-            const unsigned peers = __match_any_sync(FULL, d);
-            if (valid) {
-                if (lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
-                if (dplus) atomicAdd(dplus + (item >> 32), 1u);
-                if (in.P && in_pair(in, item)) atomicAdd(in.P + (uint32_t)item + 1, 1u);
+            if (valid) atomicAdd(&cnt[warp][(uint32_t)(item >> shift) & mask], 1u);
+            if (dplus) {
+                // runs of one source are common (canonical order): one atomic per run
+                const uint32_t x = valid ? (uint32_t)(item >> 32) : 0xffffffffu;
+                const unsigned peers = __match_any_sync(FULL, x);
+                if (valid && lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(dplus + x, (uint32_t)__popc(peers));
             }
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < nb; d += RX_THREADS) hist[(uint64_t)d * ntiles + tile] = cnt[d];
+    for (int d = threadIdx.x; d < nb; d += RX_THREADS) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) c += cnt[w][d];
+        hist[(uint64_t)d * ntiles + tile] = c;
+    }
 }
 
+// Stable scatter of one tile: rank every item within its digit (warp
+// order, then item order), sort the tile by digit in shared memory, and
+// write each digit's run to its global offset with consecutive threads on
+// consecutive positions.  With in-lists, each item is also appended to its
+// dst's list; a thread issues all its appends before writing any entry.
 __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, int shift, int width,
                                                               const uint32_t *__restrict__ offs, uint32_t ntiles,
                                                               uint64_t *__restrict__ out,
@@ -157,8 +164,12 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
                                                               const uint32_t *__restrict__ padoff)
 {
     constexpr int NW = RX_THREADS / 32;
+    static_assert(RX_BINS == RX_THREADS, "one digit per thread in the tile scan");
+    __shared__ uint64_t s_items[RX_TILE];
     __shared__ uint32_t whist[NW][RX_BINS];
-    __shared__ uint32_t tbase[RX_BINS];
+    __shared__ uint32_t tstart[RX_BINS];  // first local position of each digit in the sorted tile
+    __shared__ uint32_t tbase[RX_BINS];   // global position of each digit's run
+    __shared__ uint32_t wt[33];
     const uint64_t n = src.n_dev ? *src.n_dev : src.n_host;
     const uint32_t tile = blockIdx.x;
     const uint64_t base = (uint64_t)tile * RX_TILE;
@@ -168,18 +179,22 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     for (int i = threadIdx.x; i < NW * RX_BINS; i += RX_THREADS) (&whist[0][0])[i] = 0;
     for (int d = threadIdx.x; d < nb; d += RX_THREADS) tbase[d] = offs[(uint64_t)d * ntiles + tile];
-    __syncthreads();
 
     uint64_t items[RX_ITEMS];
     uint32_t packed[RX_ITEMS];  // digit << 16 | rank within (warp, digit); ~0 = absent
     const uint64_t seg = base + (uint64_t)warp * 32 * RX_ITEMS;
     const unsigned lt = lanemask_lt();
 #pragma unroll
-    for (int j = 0; j < RX_ITEMS; ++j) {
+    for (int j = 0; j < RX_ITEMS; ++j) {  // all loads first
         const uint64_t i = seg + (uint64_t)j * 32 + lane;
         items[j] = 0;
         const uint32_t g = item_graph(src, i, n);
-        const bool valid = i < n && load_item(src, i, items[j], g);
+        packed[j] = (i < n && load_item(src, i, items[j], g)) ? 0u : 0xffffffffu;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RX_ITEMS; ++j) {
+        const bool valid = packed[j] == 0u;
         const uint32_t d = valid ? ((uint32_t)(items[j] >> shift) & mask) : 0xffffffffu;
         const unsigned peers = __match_any_sync(FULL, d);
         uint32_t r = 0;
@@ -190,29 +205,50 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
         packed[j] = valid ? ((d << 16) | r) : 0xffffffffu;
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < nb; d += RX_THREADS) {
-        uint32_t run = 0;
+    // per digit: offsets of the warps' runs, and the digit's start in the tile
+    uint32_t tot = 0;
+    {
+        const int d = threadIdx.x;  // RX_BINS == RX_THREADS
+        if (d < nb) {
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t c = whist[w][d];
-            whist[w][d] = run;
-            run += c;
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t c = whist[w][d];
+                whist[w][d] = tot;
+                tot += c;
+            }
         }
     }
+    uint32_t count;  // valid items of the tile
+    const uint32_t start = block_excl_scan(tot, wt, &count);
+    tstart[threadIdx.x] = start;
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < RX_ITEMS; ++j) {
         if (packed[j] == 0xffffffffu) continue;
         const uint32_t d = packed[j] >> 16, r = packed[j] & 0xffffu;
-        const uint32_t pos = tbase[d] + whist[warp][d] + r;
-        if (out_low32)
-            out_low32[padoff ? pos + __ldg(padoff + (items[j] >> 32)) : pos] = (uint32_t)items[j];
-        else
-            out[pos] = items[j];
-        if (in.P && in_pair(in, items[j])) {
-            const uint32_t q = atomicAdd(in.P + (uint32_t)items[j] + 1, 1u);
-            in.inlist[q] = (uint32_t)(items[j] >> 32);
+        s_items[tstart[d] + whist[warp][d] + r] = items[j];
+    }
+    __syncthreads();
+    uint32_t q[RX_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RX_ITEMS; ++k) {
+        const uint32_t i = threadIdx.x + k * RX_THREADS;
+        q[k] = 0xffffffffu;
+        if (i < count) {
+            const uint64_t item = s_items[i];
+            const uint32_t d = (uint32_t)(item >> shift) & mask;
+            const uint32_t pos = tbase[d] + (i - tstart[d]);
+            if (out_low32)
+                out_low32[padoff ? pos + __ldg(padoff + (item >> 32)) : pos] = (uint32_t)item;
+            else
+                out[pos] = item;
+            if (in.P) q[k] = atomicAdd(in.P + (uint32_t)item + 1, 1u);
         }
+    }
+    if (in.P) {
+#pragma unroll
+        for (int k = 0; k < RX_ITEMS; ++k)
+            if (q[k] != 0xffffffffu) in.inlist[q[k]] = (uint32_t)(s_items[threadIdx.x + k * RX_THREADS] >> 32);
     }
 }
 
@@ -220,13 +256,11 @@ void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uin
                 uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
                 const InListArgs *in, cudaStream_t s, const uint32_t *padoff)
 {
-    const InListArgs inl = in ? *in : InListArgs{nullptr, nullptr, nullptr, 0};
+    const InListArgs inl = in ? *in : InListArgs{nullptr, nullptr, 0};
     const uint64_t ntiles = ceil_div(n_max, RX_TILE);
     if (ntiles == 0) return;
-    k_radix_count<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, dplus, inl); note_launch();
+    k_radix_count<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, dplus); note_launch();
     scan_excl_u32(hist, ntiles << width, nullptr, scan_scratch, s);
-    // in-list offsets: P[1 .. n+1] = exclusive scan of the counts, P[0] = 0
-    if (inl.P) scan_excl_u32(inl.P + 1, (uint64_t)inl.n + 1, nullptr, scan_scratch, s);
     k_radix_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, out,
                                                             out_low32, inl, padoff); note_launch();
 }
@@ -343,13 +377,19 @@ namespace tcg {
 
 __device__ __forceinline__ uint32_t pad_of(uint32_t d) { return (4u - (d & 3u)) & 3u; }
 
-// ptrp[x] = pad count of row x (x < n), ptrp[n] = 0; rowptr holds the
-// out-degree counts.
-__global__ void k_pad_counts(const uint32_t *__restrict__ dplus, uint32_t n, uint32_t *__restrict__ ptrp)
+// Once the out-degrees d+ are counted (dplus): ptrp[x] = pad count of row x,
+// and P[1 + x] = in-degree deg - d+ of x (x < n); ptrp[n] = P[n + 1] = 0,
+// P[0] = 0.
+__global__ void k_row_counts(const uint32_t *__restrict__ dplus, const uint32_t *__restrict__ deg, uint32_t n,
+                             uint32_t *__restrict__ ptrp, uint32_t *__restrict__ P)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride)
-        ptrp[x] = x < n ? pad_of(dplus[x]) : 0u;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
+        const uint32_t dp = x < n ? dplus[x] : 0u;
+        ptrp[x] = pad_of(dp);
+        P[x + 1] = x < n ? deg[x] - dp : 0u;
+        if (x == 0) P[0] = 0;
+    }
 }
 
 // ptrp holds the exclusive scan of the pad counts and rowptr the row
@@ -396,7 +436,7 @@ void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t
             src = ItemSource{ItemSource::PLAIN, in, 0, a.m_sampled_dev, nullptr, 0, 0};
         }
         uint64_t *out = bufs[cur];
-        InListArgs il{a.rowptr, a.inptr, nullptr, a.n};
+        InListArgs il{a.inptr, nullptr, a.n};
         if (last) {
             // padded columns in colp, the in-lists in the output buffer (the
             // input buffer is still being read)
@@ -407,10 +447,13 @@ void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t
         radix_pass(src, a.m, shift, widths[p], a.hist, a.scan, p == 0 ? a.rowptr : nullptr, last ? nullptr : out,
                    last ? *col : nullptr, last ? &il : nullptr, s, last ? a.ptrp : nullptr);
         if (p == 0) {
-            // out-degrees are complete: pad offsets for the last pass
-            k_pad_counts<<<grid_for((uint64_t)a.n + 1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp);
+            // out-degrees are complete: pad offsets and in-list offsets for
+            // the last pass
+            k_row_counts<<<grid_for((uint64_t)a.n + 1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.deg, a.n, a.ptrp,
+                                                                                   a.inptr);
             note_launch();
             scan_excl_u32(a.ptrp, (uint64_t)a.n + 1, nullptr, a.scan, s);
+            scan_excl_u32(a.inptr + 1, (uint64_t)a.n + 1, nullptr, a.scan, s);
         }
         in = out;
         cur ^= 1;
