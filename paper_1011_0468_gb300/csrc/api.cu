@@ -147,19 +147,28 @@ bool bad_p(double p) { return !(p > 0.0 && p <= 1.0); }
 
 uint64_t threshold_of(double p) { return (uint64_t)(p * 9007199254740992.0); }
 
-// Sampling, degrees and partition (Sections 3.1-3.2) into g->deg/heavy/st.
-void enqueue_sample(tc_graph *g, uint64_t seed_mix, uint64_t thr, const CountBuffers &b)
+CountBuffers buffers_of(tc_graph *g);
+
+// At sampling rates up to this, the kept edges are compacted first and the
+// radix passes run over them alone; above it the first pass samples the
+// whole edge list itself.
+constexpr double COMPACT_P = 0.5;
+
+// Sampling, degrees and partition (Sections 3.1-3.2) into g->deg/heavy/st;
+// with `compact`, also the per-tile kept counts in g->hist.
+void enqueue_sample(tc_graph *g, uint64_t seed_mix, uint64_t thr, const CountBuffers &b, bool compact = false)
 {
     cudaMemsetAsync(g->st, 0, sizeof(DevState), g->stream);
     cudaMemsetAsync(g->deg, 0, (size_t)g->n * 4, g->stream);
-    sample_degree(b, seed_mix, thr, g->stream);
+    sample_degree(b, seed_mix, thr, g->stream, compact ? g->hist : nullptr);
     partition(b, g->stream);
 }
 
 // Degree-oriented CSR of the sampled graph by stable LSD radix sort of
-// (src << 32 | dst) on the src bits, plus the in-lists of the pairs whose
-// source has the smaller out-degree.  Fills g->col / g->inlist / g->inptr.
-void enqueue_csr(tc_graph *g, uint64_t seed_mix, uint64_t thr)
+// (src << 32 | dst) on the src bits, plus the in-lists.  With `compact`
+// (after enqueue_sample with compact) the kept keys are gathered into bufB
+// first.  Fills g->col / g->inlist / g->inptr.
+void enqueue_csr(tc_graph *g, uint64_t seed_mix, uint64_t thr, bool compact = false)
 {
     CsrArgs a;
     a.ekey = g->ekey;
@@ -178,6 +187,10 @@ void enqueue_csr(tc_graph *g, uint64_t seed_mix, uint64_t thr)
     a.scan = g->scan;
     a.colp = g->colp;
     a.ptrp = g->ptrp;
+    if (compact) {
+        kept_scatter(buffers_of(g), seed_mix, thr, g->bufB, g->hist, g->scan, g->stream);
+        a.kept = g->bufB;
+    }
     csr_build(a, &g->col, &g->inlist, g->stream);
 }
 
@@ -227,12 +240,13 @@ void ring_times(tc_graph *g, uint64_t count, float *ms)
 tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bool timing)
 {
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
+    const bool compact = p <= COMPACT_P;
     CountBuffers b = buffers_of(g);
     record(g, timing, 0);
-    enqueue_sample(g, seed_mix, thr, b);
+    enqueue_sample(g, seed_mix, thr, b, compact);
     record(g, timing, 1);
     if (g->m > 0) {
-        enqueue_csr(g, seed_mix, thr);
+        enqueue_csr(g, seed_mix, thr, compact);
         b = buffers_of(g);
         if (g->hb.hcap) heavy_prepare(b, g->hb, g->stream);
         build_items(b, g->stream);

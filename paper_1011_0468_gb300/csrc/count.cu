@@ -20,12 +20,36 @@ __device__ __forceinline__ uint32_t sample_one(uint64_t k, uint64_t seed_mix, ui
 
 __global__ void __launch_bounds__(256) k_sample_degree(const uint64_t *__restrict__ ekey, uint64_t m,
                                                        uint64_t seed_mix, uint64_t thr,
-                                                       uint32_t *__restrict__ deg, DevState *st, BatchView bv)
+                                                       uint32_t *__restrict__ deg, DevState *st, BatchView bv,
+                                                       uint32_t *__restrict__ tile_cnt)
 {
+    __shared__ uint32_t wt[33];
     uint32_t kept = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (bv.k == 0) {
+    if (tile_cnt) {
+        // whole RX_TILE-key tiles per block, with the kept count of each
+        const ulonglong2 *e2 = reinterpret_cast<const ulonglong2 *>(ekey);
+        const uint64_t nt = (m + RX_TILE - 1) / RX_TILE;
+        for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+            uint32_t c = 0;
+            const uint64_t b2 = tile * (RX_TILE / 2);
+#pragma unroll
+            for (int j = 0; j < RX_TILE / 2 / 256; ++j) {
+                const uint64_t i = b2 + (uint64_t)j * 256 + threadIdx.x;
+                if (2 * i + 1 < m) {
+                    const ulonglong2 k = ld_stream_u64x2(e2 + i);
+                    c += sample_one(k.x, seed_mix, thr, deg);
+                    c += sample_one(k.y, seed_mix, thr, deg);
+                } else if (2 * i < m) {
+                    c += sample_one(ekey[2 * i], seed_mix, thr, deg);
+                }
+            }
+            kept += c;
+            c = block_sum(c, wt);
+            if (threadIdx.x == 0) tile_cnt[tile] = c;
+        }
+    } else if (bv.k == 0) {
         const ulonglong2 *e2 = reinterpret_cast<const ulonglong2 *>(ekey);
         for (uint64_t i = tid; i < m / 2; i += stride) {
             const ulonglong2 k = ld_stream_u64x2(e2 + i);
@@ -65,11 +89,11 @@ unsigned grid_for(uint64_t work, int threads, unsigned cap)
     return (unsigned)(b ? b : 1);
 }
 
-void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaStream_t s)
+void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaStream_t s, uint32_t *tile_cnt)
 {
     if (b.m == 0) return;
     k_sample_degree<<<grid_for(b.m / 2 + 1, 256, 152 * 8), 256, 0, s>>>(b.ekey, b.m, seed_mix, thr, b.deg,
-                                                                        b.st, b.bv);
+                                                                        b.st, b.bv, b.bv.k ? nullptr : tile_cnt);
     note_launch();
 }
 
@@ -155,6 +179,16 @@ __global__ void __launch_bounds__(KC_THREADS) k_kept_scatter(const uint64_t *__r
         if (f) out[carry + ex] = k;
         carry += tot;
     }
+}
+
+void kept_scatter(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out, uint32_t *tile_cnt,
+                  uint32_t *scan_scratch, cudaStream_t s)
+{
+    const uint64_t nt = ceil_div(b.m, RX_TILE);
+    if (nt == 0) return;
+    scan_excl_u32(tile_cnt, nt, nullptr, scan_scratch, s);
+    k_kept_scatter<<<(unsigned)nt, KC_THREADS, 0, s>>>(b.ekey, b.m, seed_mix, thr, tile_cnt, out);
+    note_launch();
 }
 
 void compact_kept(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out, uint32_t *tile_cnt,

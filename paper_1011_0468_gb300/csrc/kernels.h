@@ -32,16 +32,21 @@ uint64_t scan_scratch_elems(uint64_t len);
 
 // In-place exclusive prefix sum of a[0, len).  If total is non-NULL the
 // sum of all elements is written there (device pointer).  scratch holds
-// scan_scratch_elems(len) uint32.
-void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s);
+// scan_scratch_elems(len) uint32.  With dyn_items non-NULL only the first
+// dyn_bins * ceil(*dyn_items / RX_TILE) elements (at most len) are scanned:
+// the digit histograms of a radix pass over a device-counted item list.
+void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s,
+                   const unsigned long long *dyn_items = nullptr, uint32_t dyn_bins = 0);
 
 // Source of the items of a radix pass.
 struct ItemSource {
-    enum Kind { PLAIN = 0, SAMPLE_ORIENT = 1 } kind;
-    const uint64_t *in;                 // PLAIN: items; SAMPLE_ORIENT: canonical keys
+    // PLAIN: items as they are; SAMPLE_ORIENT: canonical keys, kept ones
+    // oriented; ORIENT: canonical keys already sampled, all oriented
+    enum Kind { PLAIN = 0, SAMPLE_ORIENT = 1, ORIENT = 2 } kind;
+    const uint64_t *in;                 // PLAIN: items; SAMPLE_ORIENT / ORIENT: canonical keys
     uint64_t n_host;                    // item count when n_dev is NULL
     const unsigned long long *n_dev;    // device item count (e.g. m_p), or NULL
-    const uint32_t *deg;                // SAMPLE_ORIENT: sampled degrees
+    const uint32_t *deg;                // SAMPLE_ORIENT / ORIENT: sampled degrees
     uint64_t seed_mix, thr;             // SAMPLE_ORIENT: keep test (single graph)
     BatchView bv;                       // SAMPLE_ORIENT over a batch union (bv.k > 0)
 };
@@ -107,6 +112,9 @@ struct CsrArgs {
     uint64_t *bufA, *bufB;
     uint32_t *rowptr, *inptr, *hist, *scan;
     uint32_t *colp, *ptrp;
+    // NULL, or the kept keys already compacted in canonical order
+    // (m_sampled_dev of them, not in bufA): the first pass then only orients
+    const uint64_t *kept = nullptr;
 };
 void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t s);
 
@@ -156,7 +164,14 @@ struct CountBuffers {
     IsectConfig cfg;        // intersection schedule
 };
 
-void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaStream_t s);
+// Sampling and sampled degrees.  With tile_cnt non-NULL (single graph only)
+// the kept edges of every RX_TILE-key tile are also counted there.
+void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaStream_t s,
+                   uint32_t *tile_cnt = nullptr);
+// After sample_degree with tile_cnt: the kept keys, in canonical order, to
+// out (tile_cnt is scanned in place; scan_scratch as for scan_excl_u32).
+void kept_scatter(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out, uint32_t *tile_cnt,
+                  uint32_t *scan_scratch, cudaStream_t s);
 void partition(const CountBuffers &b, cudaStream_t s);
 void compact_kept(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out,
                   uint32_t *tile_cnt, uint32_t *scan_scratch, cudaStream_t s);

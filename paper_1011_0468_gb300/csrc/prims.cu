@@ -18,11 +18,23 @@ namespace tcg {
 constexpr int SC_THREADS = 1024;
 constexpr int SC_ITEMS = SC_CHUNK / SC_THREADS;  // 4
 
+// Effective scan length: len, or for a device-counted item list the digit
+// histograms of its tiles only.
+__device__ __forceinline__ uint64_t scan_len(uint64_t len, const unsigned long long *dyn_items, uint32_t dyn_bins)
+{
+    if (!dyn_items) return len;
+    const uint64_t l = (uint64_t)dyn_bins * ((*dyn_items + RX_TILE - 1) / RX_TILE);
+    return l < len ? l : len;
+}
+
 __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ a, uint64_t len,
-                                                            uint32_t *__restrict__ part)
+                                                            uint32_t *__restrict__ part,
+                                                            const unsigned long long *dyn_items, uint32_t dyn_bins)
 {
     __shared__ uint32_t wt[33];
+    len = scan_len(len, dyn_items, dyn_bins);
     const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
+    if (base >= len) return;  // uniform across the block
     uint32_t s = 0;
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
@@ -35,9 +47,11 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__re
 
 // One block scans the per-block sums in place (exclusive); writes the
 // grand total to total_out when non-NULL.
-__global__ void __launch_bounds__(SC_THREADS) k_scan_spine(uint32_t *part, uint64_t nparts, uint32_t *total_out)
+__global__ void __launch_bounds__(SC_THREADS) k_scan_spine(uint32_t *part, uint64_t len, uint32_t *total_out,
+                                                           const unsigned long long *dyn_items, uint32_t dyn_bins)
 {
     __shared__ uint32_t wt[33];
+    const uint64_t nparts = (scan_len(len, dyn_items, dyn_bins) + SC_CHUNK - 1) / SC_CHUNK;
     uint32_t carry = 0;
     for (uint64_t base = 0; base < nparts; base += SC_THREADS) {
         uint64_t i = base + threadIdx.x;
@@ -50,10 +64,13 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_spine(uint32_t *part, uint6
     if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
-__global__ void __launch_bounds__(SC_THREADS) k_scan_down(uint32_t *a, uint64_t len, const uint32_t *__restrict__ part)
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down(uint32_t *a, uint64_t len, const uint32_t *__restrict__ part,
+                                                          const unsigned long long *dyn_items, uint32_t dyn_bins)
 {
     __shared__ uint32_t wt[33];
+    len = scan_len(len, dyn_items, dyn_bins);
     const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
+    if (base >= len) return;  // uniform across the block
     uint32_t carry = part[blockIdx.x];
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
@@ -68,16 +85,17 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_down(uint32_t *a, uint64_t 
 
 uint64_t scan_scratch_elems(uint64_t len) { return ceil_div(len, SC_CHUNK) + 1; }
 
-void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s)
+void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s,
+                   const unsigned long long *dyn_items, uint32_t dyn_bins)
 {
     if (len == 0) {
         if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
         return;
     }
     const uint64_t nb = ceil_div(len, SC_CHUNK);
-    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
-    k_scan_spine<<<1, SC_THREADS, 0, s>>>(scratch, nb, total); note_launch();
-    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
+    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch, dyn_items, dyn_bins); note_launch();
+    k_scan_spine<<<1, SC_THREADS, 0, s>>>(scratch, len, total, dyn_items, dyn_bins); note_launch();
+    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch, dyn_items, dyn_bins); note_launch();
 }
 
 // ======================================================================
@@ -94,6 +112,10 @@ __device__ __forceinline__ bool load_item(const ItemSource &src, uint64_t i, uin
         return true;
     }
     const uint64_t key = ld_stream_u64(src.in + i);
+    if (src.kind == ItemSource::ORIENT) {
+        item = orient(key, src.deg);
+        return true;
+    }
     if (src.bv.k == 0) {
         if (!keep_edge(key, src.seed_mix, src.thr)) return false;
     } else {
@@ -122,6 +144,11 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int 
     __shared__ uint32_t cnt[NW][RX_BINS];
     const uint64_t n = src.n_dev ? *src.n_dev : src.n_host;
     const uint32_t tile = blockIdx.x;
+    if (src.n_dev) {  // device-counted items: only their tiles have histograms
+        const uint64_t nt = (n + RX_TILE - 1) / RX_TILE;
+        if (tile >= nt) return;  // uniform across the block
+        ntiles = (uint32_t)nt;
+    }
     const int nb = 1 << width;
     const unsigned warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < NW * RX_BINS; i += RX_THREADS) (&cnt[0][0])[i] = 0;
@@ -174,6 +201,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
     const uint32_t tile = blockIdx.x;
     const uint64_t base = (uint64_t)tile * RX_TILE;
     if (base >= n) return;  // uniform across the block
+    if (src.n_dev) ntiles = (uint32_t)((n + RX_TILE - 1) / RX_TILE);  // histogram stride of this pass
     const int nb = 1 << width;
     const uint32_t mask = (uint32_t)nb - 1;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
@@ -260,7 +288,7 @@ void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uin
     const uint64_t ntiles = ceil_div(n_max, RX_TILE);
     if (ntiles == 0) return;
     k_radix_count<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, dplus); note_launch();
-    scan_excl_u32(hist, ntiles << width, nullptr, scan_scratch, s);
+    scan_excl_u32(hist, ntiles << width, nullptr, scan_scratch, s, src.n_dev, 1u << width);
     k_radix_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, out,
                                                             out_low32, inl, padoff); note_launch();
 }
@@ -429,7 +457,9 @@ void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t
     for (int p = 0; p < P; ++p) {
         const bool last = p + 1 == P;
         ItemSource src;
-        if (p == 0) {
+        if (p == 0 && a.kept) {
+            src = ItemSource{ItemSource::ORIENT, a.kept, 0, a.m_sampled_dev, a.deg, 0, 0};
+        } else if (p == 0) {
             src = ItemSource{ItemSource::SAMPLE_ORIENT, a.ekey, a.m, nullptr, a.deg, a.seed_mix, a.thr};
             src.bv = a.bv;
         } else {
