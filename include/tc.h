@@ -159,8 +159,10 @@ tc_status tc_graph_export_sample(tc_graph *g, double p, uint64_t seed, uint32_t 
 
 /*
  * The degree-oriented CSR of the sampled graph that the counting kernels
- * use: every kept edge once, directed from the endpoint of lower
- * (deg_p, id) to the higher one, rows sorted by id.
+ * use, in the original vertex ids: every kept edge once, directed from the
+ * endpoint of lower rank to the higher one, where rank = (degree in the
+ * whole graph, id) is fixed when the graph is created; each row lists its
+ * out-neighbours in increasing rank.
  *   rowptr_host  n + 1 uint32;  col_host  m_sampled uint32 (capacity m).
  */
 tc_status tc_graph_export_csr(tc_graph *g, double p, uint64_t seed, uint32_t *rowptr_host,
@@ -229,7 +231,8 @@ uint64_t tc_batch_device_bytes(const tc_batch *b);
  * batched count there; requests that arrive meanwhile wait for the next
  * free slot, and the slots' counts overlap on the device.
  *
- * HBM budget: slot scratch plus resident graphs never exceed budget_bytes.
+ * HBM budget: slot scratch plus resident graphs (16 bytes per canonical
+ * edge) never exceed budget_bytes.
  * A graph that is not resident when a request needs it is uploaded again
  * from its host copy, first evicting the least recently used graphs that no
  * slot is using; if that still leaves no room, the request waits in the
@@ -302,7 +305,7 @@ void tc_server_destroy(tc_server *srv);
  *   cuda_stream  stream for the work (NULL = default); the call blocks
  *                until the result is in *out_host.
  * All scratch lives in one fixed __device__ array inside the library
- * (about 16 MiB), held by every GPU that loads it until the process exits.
+ * (about 20 MiB), held by every GPU that loads it until the process exits.
  * The first call on a device looks up that array's device address; make
  * this first call before any stream capture.  Calls share the array (each
  * clears what must start at zero), so calls that overlap on the GPU race:

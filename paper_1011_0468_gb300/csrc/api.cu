@@ -73,18 +73,22 @@ struct tc_graph {
     int timing = 0;
     int smem_bytes = 0;
     uint64_t bytes = 0;
-    // device
-    uint64_t *ekey = nullptr;   // canonical keys (u << 32 | v), sorted [m]
-    uint64_t *bufA = nullptr;   // radix ping-pong [m]
-    uint64_t *bufB = nullptr;   // radix ping-pong [m]
+    // device: the graph in rank order (csr.cu)
+    uint64_t *rel = nullptr;    // [m] canonical keys in rank ids, sorted
+    uint64_t *orig = nullptr;   // [m] original canonical key of each rel key
+    uint32_t *perm = nullptr;   // [n] original id of each rank id
+    uint32_t *rank = nullptr;   // [n] rank id of each original id
+    // device: scratch of a count (rank ids)
     uint32_t *deg = nullptr;    // [n]
     uint32_t *rowptr = nullptr; // [n + 1]
     uint8_t *heavy = nullptr;   // [n]
-    uint32_t *inptr = nullptr;  // [n + 2] in-list offsets (see InListArgs)
-    uint32_t *col = nullptr;    // padded CSR columns (= colp)
-    uint32_t *inlist = nullptr; // in-lists (inside bufA or bufB)
+    uint32_t *inptr = nullptr;  // [n + 2] in-list offsets
+    uint2 *inlist = nullptr;    // [m] in-list entries
     uint32_t *colp = nullptr;   // [colp_capacity(n, m)] rows padded to 16 bytes
     uint32_t *ptrp = nullptr;   // [n + 2] padded row pointers
+    uint32_t *keepw = nullptr;  // [ceil(m / 32)] keep bits
+    uint32_t *tile_cnt = nullptr;  // [ceil(m / RX_TILE) + 1]
+    uint32_t *spread = nullptr; // [hot_size(n)] per-vertex counters (kernels.h)
     uint64_t *items = nullptr;  // owner work items, all buckets [items_cap]
     uint64_t items_cap = 0;
     uint32_t *hist = nullptr;   // [RX_BINS * ntiles(m)]
@@ -147,63 +151,16 @@ bool bad_p(double p) { return !(p > 0.0 && p <= 1.0); }
 
 uint64_t threshold_of(double p) { return (uint64_t)(p * 9007199254740992.0); }
 
-CountBuffers buffers_of(tc_graph *g);
-
-// At sampling rates up to this, the kept edges are compacted first and the
-// radix passes run over them alone; above it the first pass samples the
-// whole edge list itself.
-constexpr double COMPACT_P = 0.5;
-
-// Sampling, degrees and partition (Sections 3.1-3.2) into g->deg/heavy/st;
-// with `compact`, also the per-tile kept counts in g->hist.
-void enqueue_sample(tc_graph *g, uint64_t seed_mix, uint64_t thr, const CountBuffers &b, bool compact = false)
-{
-    cudaMemsetAsync(g->st, 0, sizeof(DevState), g->stream);
-    cudaMemsetAsync(g->deg, 0, (size_t)g->n * 4, g->stream);
-    sample_degree(b, seed_mix, thr, g->stream, compact ? g->hist : nullptr);
-    partition(b, g->stream);
-}
-
-// Degree-oriented CSR of the sampled graph by stable LSD radix sort of
-// (src << 32 | dst) on the src bits, plus the in-lists.  With `compact`
-// (after enqueue_sample with compact) the kept keys are gathered into bufB
-// first.  Fills g->col / g->inlist / g->inptr.
-void enqueue_csr(tc_graph *g, uint64_t seed_mix, uint64_t thr, bool compact = false)
-{
-    CsrArgs a;
-    a.ekey = g->ekey;
-    a.m = g->m;
-    a.n = g->n;
-    a.nbits = g->nbits;
-    a.deg = g->deg;
-    a.seed_mix = seed_mix;
-    a.thr = thr;
-    a.m_sampled_dev = &g->st->m_sampled;
-    a.bufA = g->bufA;
-    a.bufB = g->bufB;
-    a.rowptr = g->rowptr;
-    a.inptr = g->inptr;
-    a.hist = g->hist;
-    a.scan = g->scan;
-    a.colp = g->colp;
-    a.ptrp = g->ptrp;
-    if (compact) {
-        kept_scatter(buffers_of(g), seed_mix, thr, g->bufB, g->hist, g->scan, g->stream);
-        a.kept = g->bufB;
-    }
-    csr_build(a, &g->col, &g->inlist, g->stream);
-}
-
 CountBuffers buffers_of(tc_graph *g)
 {
     CountBuffers b;
-    b.ekey = g->ekey;
+    b.ekey = g->rel;
     b.m = g->m;
     b.n = g->n;
     b.deg = g->deg;
     b.heavy = g->heavy;
     b.rowptr = g->rowptr;
-    b.col = g->col;
+    b.col = g->colp;
     b.ptrp = g->ptrp;
     b.inptr = g->inptr;
     b.inlist = g->inlist;
@@ -211,6 +168,37 @@ CountBuffers buffers_of(tc_graph *g)
     b.items_cap = g->items_cap;
     b.st = g->st;
     return b;
+}
+
+RowsArgs rows_of(tc_graph *g, uint64_t seed_mix, uint64_t thr)
+{
+    RowsArgs a;
+    a.rel = g->rel;
+    a.orig = g->orig;
+    a.m = g->m;
+    a.n = g->n;
+    a.seed_mix = seed_mix;
+    a.thr = thr;
+    a.deg = g->deg;
+    a.rowptr = g->rowptr;
+    a.inptr = g->inptr;
+    a.ptrp = g->ptrp;
+    a.colp = g->colp;
+    a.inlist = g->inlist;
+    a.keepw = g->keepw;
+    a.tile_cnt = g->tile_cnt;
+    a.scan = g->scan;
+    a.spread = g->spread;
+    a.st = g->st;
+    return a;
+}
+
+// Sampling, degrees and partition (Sections 3.1-3.2) into g->deg/heavy/st.
+void enqueue_sample(tc_graph *g, const RowsArgs &ra)
+{
+    cudaMemsetAsync(g->st, 0, sizeof(DevState), g->stream);
+    sample_rows(ra, g->stream);
+    partition(buffers_of(g), g->stream);
 }
 
 cudaEvent_t &ring_event(tc_graph *g, uint64_t count, int i)
@@ -240,14 +228,13 @@ void ring_times(tc_graph *g, uint64_t count, float *ms)
 tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bool timing)
 {
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
-    const bool compact = p <= COMPACT_P;
-    CountBuffers b = buffers_of(g);
+    const RowsArgs ra = rows_of(g, seed_mix, thr);
+    const CountBuffers b = buffers_of(g);
     record(g, timing, 0);
-    enqueue_sample(g, seed_mix, thr, b, compact);
+    enqueue_sample(g, ra);
     record(g, timing, 1);
     if (g->m > 0) {
-        enqueue_csr(g, seed_mix, thr, compact);
-        b = buffers_of(g);
+        build_rows(ra, g->stream);
         if (g->hb.hcap) heavy_prepare(b, g->hb, g->stream);
         build_items(b, g->stream);
     }
@@ -340,6 +327,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
 
     // ---- canonical keys
     uint64_t m = 0;
+    uint64_t *canon = nullptr;  // canonical keys (original ids), sorted [m]
     if (m_in > 0) {
         const uint32_t *dpairs = edges;
         void *tmp_pairs = nullptr;
@@ -357,7 +345,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
         if (tmp_pairs) g->release(tmp_pairs);
         if (g->st_host->err & ERR_ENDPOINT) { free_graph(g); return TC_EINVAL; }
         if (g->st_host->unsorted == 0) {
-            g->ekey = keys;  // already canonical: every pair u < v, strictly increasing
+            canon = keys;  // already canonical: every pair u < v, strictly increasing
             m = m_in;
         } else {
             // sort by (u, v) on the used bits only, then drop repeats/self-loops
@@ -371,8 +359,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
             for (int half = 0; half < 2; ++half) {
                 int shift = half ? 32 : 0;
                 for (int w : pass_widths(g->nbits)) {
-                    ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
-                    radix_pass(src, m_in, shift, w, hist, scan, nullptr, b, nullptr, nullptr, s);
+                    radix_pass(a, m_in, shift, w, hist, scan, b, s);
                     std::swap(a, b);
                     shift += w;
                 }
@@ -385,34 +372,55 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
             g->release(scan);
             g->release(tcnt);
             g->release(a);
-            g->ekey = b;
+            canon = b;
         }
     }
     g->m = m;
 
-    // ---- scratch for counting, sized for p = 1
-    const uint64_t nt = std::max<uint64_t>(ceil_div(m, RX_TILE), 1);
-    const uint64_t hist_len = nt << RX_MAX_BITS;
-    g->bufA = (uint64_t *)g->alloc(std::max<uint64_t>(m, 1) * 8);
-    g->bufB = (uint64_t *)g->alloc(std::max<uint64_t>(m, 1) * 8);
+    // ---- rank relabeling (csr.cu), then the scratch of a count, sized for p = 1
+    const uint64_t m1 = std::max<uint64_t>(m, 1);
+    const uint64_t hist_len = std::max<uint64_t>(ceil_div(std::max<uint64_t>(m, n), RX_TILE), 1) << RX_MAX_BITS;
+    g->rel = (uint64_t *)g->alloc(m1 * 8);
+    g->orig = (uint64_t *)g->alloc(m1 * 8);
+    g->perm = (uint32_t *)g->alloc((uint64_t)n * 4);
+    g->rank = (uint32_t *)g->alloc((uint64_t)n * 4);
+    g->inlist = (uint2 *)g->alloc(m1 * 8);
     g->deg = (uint32_t *)g->alloc((uint64_t)n * 4);
+    g->hist = (uint32_t *)g->alloc(hist_len * 4);
+    g->scan = (uint32_t *)g->alloc(scan_scratch_elems(std::max<uint64_t>(hist_len, (uint64_t)n + 2)) * 4);
+    if (!g->rel || !g->orig || !g->perm || !g->rank || !g->inlist || !g->deg || !g->hist || !g->scan) {
+        free_graph(g);
+        return TC_ENOMEM;
+    }
+    {
+        uint64_t *kB = (uint64_t *)g->alloc(m1 * 8);
+        uint64_t *vA = (uint64_t *)g->alloc((uint64_t)n * 8), *vB = (uint64_t *)g->alloc((uint64_t)n * 8);
+        if (!kB || !vA || !vB) {
+            free_graph(g);
+            return TC_ENOMEM;
+        }
+        const RelabelScratch sc{reinterpret_cast<uint64_t *>(g->inlist), kB, vA, vB, g->deg, g->hist, g->scan};
+        relabel(canon, m, n, nullptr, 0, Relabeled{g->rel, g->orig, g->perm, g->rank}, sc, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); free_graph(g); return TC_ECUDA; }
+        g->release(kB);
+        g->release(vA);
+        g->release(vB);
+        if (canon) g->release(canon);
+    }
     g->rowptr = (uint32_t *)g->alloc(((uint64_t)n + 1) * 4);
     g->heavy = (uint8_t *)g->alloc((uint64_t)n);
     g->inptr = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
     g->colp = (uint32_t *)g->alloc(colp_capacity(n, m) * 4);
     g->ptrp = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
+    g->keepw = (uint32_t *)g->alloc((m1 + 31) / 32 * 4);
+    g->tile_cnt = (uint32_t *)g->alloc((ceil_div(m1, RX_TILE) + 1) * 4);
+    g->spread = (uint32_t *)g->alloc(hot_size(n) * 4);
     g->items_cap = items_capacity(n, m);
     g->items = (uint64_t *)g->alloc(g->items_cap * 8);
-    g->hist = (uint32_t *)g->alloc(hist_len * 4);
-    g->scan = (uint32_t *)g->alloc(scan_scratch_elems(std::max<uint64_t>(hist_len, (uint64_t)n + 1)) * 4);
-    if (!g->bufA || !g->bufB || !g->deg || !g->rowptr || !g->heavy || !g->inptr || !g->colp || !g->ptrp ||
-        !g->items || !g->hist || !g->scan) {
+    if (!g->rowptr || !g->heavy || !g->inptr || !g->colp || !g->ptrp || !g->keepw || !g->tile_cnt || !g->spread ||
+        !g->items) {
         free_graph(g);
         return TC_ENOMEM;
-    }
-    if (m == 0 && !g->ekey) {
-        g->ekey = (uint64_t *)g->alloc(8);
-        if (!g->ekey) { free_graph(g); return TC_ENOMEM; }
     }
     // hash set of the owners with d+ > 1024: every out-degree of the
     // degree-oriented graph is at most sqrt(2 m_p); a set of >= 4 d+ slots
@@ -527,26 +535,42 @@ tc_status tc_graph_export_sample(tc_graph *g, double p, uint64_t seed, uint32_t 
 {
     if (!g || bad_p(p)) return TC_EINVAL;
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
-    CountBuffers b = buffers_of(g);
-    enqueue_sample(g, seed_mix, thr, b);
-    if (kept_pairs_host && g->m > 0)
-        compact_kept(b, seed_mix, thr, g->bufA, g->hist, g->scan, g->stream);
+    enqueue_sample(g, rows_of(g, seed_mix, thr));
     cudaMemcpyAsync(g->st_host, g->st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream);
     tc_status st = sync_graph(g);
     if (st != TC_OK) return st;
     const uint64_t mp = g->st_host->m_sampled;
     if (m_sampled) *m_sampled = mp;
-    if (heavy_host) cudaMemcpyAsync(heavy_host, g->heavy, g->n, cudaMemcpyDeviceToHost, g->stream);
-    if (deg_host) cudaMemcpyAsync(deg_host, g->deg, (size_t)g->n * 4, cudaMemcpyDeviceToHost, g->stream);
-    std::vector<uint64_t> keys;
-    if (kept_pairs_host && mp > 0) {
-        keys.resize(mp);
-        cudaMemcpyAsync(keys.data(), g->bufA, mp * 8, cudaMemcpyDeviceToHost, g->stream);
+    // the device holds the graph in rank order: map back to original ids
+    const uint32_t n = g->n;
+    std::vector<uint32_t> rank(n), deg(n), keepw;
+    std::vector<uint8_t> heavy(n);
+    std::vector<uint64_t> orig;
+    cudaMemcpyAsync(rank.data(), g->rank, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream);
+    cudaMemcpyAsync(deg.data(), g->deg, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream);
+    cudaMemcpyAsync(heavy.data(), g->heavy, n, cudaMemcpyDeviceToHost, g->stream);
+    if (kept_pairs_host && g->m > 0) {
+        keepw.resize((g->m + 31) / 32);
+        orig.resize(g->m);
+        cudaMemcpyAsync(keepw.data(), g->keepw, keepw.size() * 4, cudaMemcpyDeviceToHost, g->stream);
+        cudaMemcpyAsync(orig.data(), g->orig, g->m * 8, cudaMemcpyDeviceToHost, g->stream);
     }
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) { cudaGetLastError(); return TC_ECUDA; }
-    for (uint64_t i = 0; i < keys.size(); ++i) {
-        kept_pairs_host[2 * i] = (uint32_t)(keys[i] >> 32);
-        kept_pairs_host[2 * i + 1] = (uint32_t)keys[i];
+    for (uint32_t v = 0; v < n; ++v) {
+        if (deg_host) deg_host[v] = deg[rank[v]];
+        if (heavy_host) heavy_host[v] = heavy[rank[v]];
+    }
+    if (kept_pairs_host && g->m > 0) {
+        std::vector<uint64_t> kept;
+        kept.reserve(mp);
+        for (uint64_t i = 0; i < g->m; ++i)
+            if ((keepw[i >> 5] >> (i & 31)) & 1u) kept.push_back(orig[i]);
+        if (kept.size() != mp) return TC_ECUDA;
+        std::sort(kept.begin(), kept.end());  // canonical order of the original ids
+        for (uint64_t i = 0; i < kept.size(); ++i) {
+            kept_pairs_host[2 * i] = (uint32_t)(kept[i] >> 32);
+            kept_pairs_host[2 * i + 1] = (uint32_t)kept[i];
+        }
     }
     return TC_OK;
 }
@@ -556,36 +580,45 @@ tc_status tc_graph_export_csr(tc_graph *g, double p, uint64_t seed, uint32_t *ro
 {
     if (!g || bad_p(p)) return TC_EINVAL;
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
-    CountBuffers b = buffers_of(g);
-    enqueue_sample(g, seed_mix, thr, b);
-    if (g->m > 0) {
-        enqueue_csr(g, seed_mix, thr);
-    } else {
-        cudaMemsetAsync(g->rowptr, 0, ((size_t)g->n + 1) * 4, g->stream);
-    }
+    const RowsArgs ra = rows_of(g, seed_mix, thr);
+    enqueue_sample(g, ra);
+    if (g->m > 0) build_rows(ra, g->stream);
     cudaMemcpyAsync(g->st_host, g->st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream);
     tc_status st = sync_graph(g);
     if (st != TC_OK) return st;
     const uint64_t mp = g->st_host->m_sampled;
     if (m_sampled) *m_sampled = mp;
-    std::vector<uint32_t> rp(g->n + 1), pp(g->n + 1), cp;
-    cudaMemcpyAsync(rp.data(), g->rowptr, ((size_t)g->n + 1) * 4, cudaMemcpyDeviceToHost, g->stream);
-    if (g->m > 0) cudaMemcpyAsync(pp.data(), g->ptrp, ((size_t)g->n + 1) * 4, cudaMemcpyDeviceToHost, g->stream);
+    const uint32_t n = g->n;
+    std::vector<uint32_t> rp(n + 1, 0), pp(n + 1, 0), perm(n), rank(n), cp;
+    cudaMemcpyAsync(perm.data(), g->perm, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream);
+    cudaMemcpyAsync(rank.data(), g->rank, (size_t)n * 4, cudaMemcpyDeviceToHost, g->stream);
+    if (g->m > 0) {
+        cudaMemcpyAsync(rp.data(), g->rowptr, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, g->stream);
+        cudaMemcpyAsync(pp.data(), g->ptrp, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, g->stream);
+    }
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) { cudaGetLastError(); return TC_ECUDA; }
-    if (rowptr_host) std::copy(rp.begin(), rp.end(), rowptr_host);
+    // rows of the original ids: vertex v's row is rank row rank[v]
+    if (rowptr_host) {
+        rowptr_host[0] = 0;
+        for (uint32_t v = 0; v < n; ++v) rowptr_host[v + 1] = rowptr_host[v] + (rp[rank[v] + 1] - rp[rank[v]]);
+    }
     if (g->m == 0 || mp == 0) return TC_OK;
     // the columns are stored padded: check the layout and strip the padding
-    const uint64_t total = pp[g->n];
-    if (total > colp_capacity(g->n, g->m)) return TC_ECUDA;
+    const uint64_t total = pp[n];
+    if (total > colp_capacity(n, g->m)) return TC_ECUDA;
     cp.resize(total);
     cudaMemcpyAsync(cp.data(), g->colp, total * 4, cudaMemcpyDeviceToHost, g->stream);
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) { cudaGetLastError(); return TC_ECUDA; }
-    for (uint32_t x = 0; x < g->n; ++x) {
+    uint64_t out_pos = 0;
+    for (uint32_t v = 0; v < n; ++v) {
+        const uint32_t x = rank[v];
         const uint32_t d = rp[x + 1] - rp[x], beg = pp[x] & ~3u, pad = pp[x] & 3u;
         if (pad != ((4u - (d & 3u)) & 3u) || (pp[x + 1] & ~3u) != beg + d + pad) return TC_ECUDA;
         for (uint32_t i = 0; i < pad; ++i)
             if (cp[beg + d + i] != SENT) return TC_ECUDA;
-        if (col_host) std::copy(cp.begin() + beg, cp.begin() + beg + d, col_host + rp[x]);
+        if (col_host)
+            for (uint32_t i = 0; i < d; ++i) col_host[out_pos + i] = perm[cp[beg + i]];
+        out_pos += d;
     }
     return TC_OK;
 }
@@ -595,8 +628,9 @@ tc_status tc_graph_export_edges(tc_graph *g, uint32_t *pairs_host)
     if (!g || (!pairs_host && g->m > 0)) return TC_EINVAL;
     if (g->m == 0) return TC_OK;
     std::vector<uint64_t> keys(g->m);
-    cudaMemcpyAsync(keys.data(), g->ekey, g->m * 8, cudaMemcpyDeviceToHost, g->stream);
+    cudaMemcpyAsync(keys.data(), g->orig, g->m * 8, cudaMemcpyDeviceToHost, g->stream);
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) { cudaGetLastError(); return TC_ECUDA; }
+    std::sort(keys.begin(), keys.end());
     for (uint64_t i = 0; i < g->m; ++i) {
         pairs_host[2 * i] = (uint32_t)(keys[i] >> 32);
         pairs_host[2 * i + 1] = (uint32_t)keys[i];

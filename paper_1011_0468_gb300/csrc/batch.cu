@@ -2,8 +2,8 @@
 //
 // The graphs are stored as one disjoint union (graph g owns vertices
 // [voff[g], voff[g+1]) and edges [eoff[g], eoff[g+1]) of the union's sorted
-// canonical key array), so every kernel of the count runs once over all of
-// them.  Each edge is sampled with its own graph's (p, seed) on its
+// key array, every graph in its own rank order, csr.cu), so every kernel of
+// the count runs once over all of them.  Each edge is sampled with its own graph's (p, seed) on its
 // graph-local key, each vertex is split against its own graph's m_p, and the
 // class counts go to per-graph counters: every graph gets exactly the
 // result a separate tc_count would give.  For tc_batch the whole sequence
@@ -114,11 +114,13 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
     u.n_cap = n_cap;
     u.k_cap = k_cap;
     const uint64_t m1 = std::max<uint64_t>(m_cap, 1);
-    const uint64_t nt = std::max<uint64_t>(ceil_div(m1, RX_TILE), 1);
-    const uint64_t hist_len = nt << RX_MAX_BITS;
-    u.ekey = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
-    u.bufA = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
-    u.bufB = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
+    const uint64_t hist_len = std::max<uint64_t>(ceil_div(std::max<uint64_t>(m1, n_cap), RX_TILE), 1) << RX_MAX_BITS;
+    u.rel = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
+    u.orig = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
+    u.inlist = (uint2 *)dev_alloc_track(allocs, bytes, m1 * 8);
+    u.keepw = (uint32_t *)dev_alloc_track(allocs, bytes, (m1 + 31) / 32 * 4);
+    u.tile_cnt = (uint32_t *)dev_alloc_track(allocs, bytes, (ceil_div(m1, RX_TILE) + 1) * 4);
+    u.spread = (uint32_t *)dev_alloc_track(allocs, bytes, hot_size(n_cap) * 4);
     u.deg = (uint32_t *)dev_alloc_track(allocs, bytes, (uint64_t)n_cap * 4);
     u.rowptr = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)n_cap + 1) * 4);
     u.inptr = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)n_cap + 2) * 4);
@@ -144,54 +146,54 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     u.smem_bytes = (int)(slots * 4);
     intersect_prepare(u.smem_bytes);
-    return u.ekey && u.bufA && u.bufB && u.deg && u.rowptr && u.inptr && u.colp && u.ptrp && u.heavy && u.items &&
-           u.hist && u.scan &&
+    return u.rel && u.orig && u.inlist && u.keepw && u.tile_cnt && u.spread && u.deg && u.rowptr && u.inptr && u.colp &&
+           u.ptrp && u.heavy && u.items && u.hist && u.scan &&
            u.st && u.eoff && u.voff && u.thr && u.seed_mix && u.p && u.counters && u.res_dev;
 }
 
 void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const IsectConfig &cfg, cudaStream_t s)
 {
     cudaMemsetAsync(u.st, 0, sizeof(DevState), s);
-    cudaMemsetAsync(u.deg, 0, (size_t)n * 4, s);
     cudaMemsetAsync(u.counters, 0, (uint64_t)u.k_cap * 28, s);
     CountBuffers cb;
-    cb.ekey = u.ekey;
+    cb.ekey = u.rel;
     cb.m = m;
     cb.n = n;
     cb.deg = u.deg;
     cb.heavy = u.heavy;
     cb.rowptr = u.rowptr;
-    cb.col = nullptr;
+    cb.col = u.colp;
     cb.ptrp = u.ptrp;
     cb.inptr = u.inptr;
-    cb.inlist = nullptr;
+    cb.inlist = u.inlist;
     cb.items = u.items;
     cb.items_cap = items_capacity(n, std::max<uint64_t>(m, 1));
     cb.st = u.st;
     cb.bv = view_of(u, k);
     cb.cfg = cfg;
+    RowsArgs ra;
+    ra.rel = u.rel;
+    ra.orig = u.orig;
+    ra.m = m;
+    ra.n = n;
+    ra.seed_mix = 0;
+    ra.thr = 0;
+    ra.bv = cb.bv;
+    ra.deg = u.deg;
+    ra.rowptr = u.rowptr;
+    ra.inptr = u.inptr;
+    ra.ptrp = u.ptrp;
+    ra.colp = u.colp;
+    ra.inlist = u.inlist;
+    ra.keepw = u.keepw;
+    ra.tile_cnt = u.tile_cnt;
+    ra.scan = u.scan;
+    ra.spread = u.spread;
+    ra.st = u.st;
+    sample_rows(ra, s);
+    partition(cb, s);
     if (m > 0) {
-        sample_degree(cb, 0, 0, s);
-        partition(cb, s);
-        CsrArgs a;
-        a.ekey = u.ekey;
-        a.m = m;
-        a.n = n;
-        a.nbits = batch_bits(n);
-        a.deg = u.deg;
-        a.seed_mix = 0;
-        a.thr = 0;
-        a.bv = cb.bv;
-        a.m_sampled_dev = &u.st->m_sampled;
-        a.bufA = u.bufA;
-        a.bufB = u.bufB;
-        a.rowptr = u.rowptr;
-        a.inptr = u.inptr;
-        a.hist = u.hist;
-        a.scan = u.scan;
-        a.colp = u.colp;
-        a.ptrp = u.ptrp;
-        csr_build(a, &cb.col, &cb.inlist, s);
+        build_rows(ra, s);
         build_items(cb, s);
         intersect(cb, u.smem_bytes, s);
     }
@@ -385,52 +387,67 @@ tc_status tc_batch_create(const uint32_t *edges, const uint64_t *m_per_graph, co
     cudaMemsetAsync(b->u.st, 0, sizeof(DevState), s);
     cudaMemcpyAsync(b->u.voff, voff.data(), (k + 1) * 4ull, cudaMemcpyHostToDevice, s);
 
-    // ---- union keys: offset, canonicalise, sort, deduplicate (into u.ekey)
+    // ---- union keys: offset, canonicalise, sort, deduplicate, then the rank
+    // relabeling of every graph (into u.rel / u.orig, csr.cu)
     uint64_t m = 0;
-    if (m_in > 0) {
+    {
         std::vector<void *> tmp;
         uint64_t tmp_bytes = 0;
-        const uint32_t *dpairs = edges;
-        if (!edges_on_device) {
-            void *p = dev_alloc_track(tmp, tmp_bytes, m_in * 8);
-            if (!p) { free_batch(b); return TC_ENOMEM; }
-            cudaMemcpyAsync(p, edges, m_in * 8, cudaMemcpyHostToDevice, s);
-            dpairs = (const uint32_t *)p;
-        }
-        uint64_t *d_in_off = (uint64_t *)dev_alloc_track(tmp, tmp_bytes, (k + 1) * 8ull);
         auto drop_tmp = [&]() {
             cudaStreamSynchronize(s);
             for (void *p : tmp) cudaFree(p);
             tmp.clear();
         };
-        if (!d_in_off) { drop_tmp(); free_batch(b); return TC_ENOMEM; }
-        cudaMemcpyAsync(d_in_off, in_off.data(), (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
-        // keys go to bufA, the sort ping-pongs with bufB, unique writes ekey
-        k_batch_keys<<<grid_for(m_in, 256, 152 * 16), 256, 0, s>>>(dpairs, m_in, d_in_off, b->u.voff, k, b->u.bufA,
-                                                                   b->u.st);
-        note_launch();
-        uint64_t *a = b->u.bufA, *c = b->u.bufB;
-        const int nbits = batch_bits(b->n);
-        for (int half = 0; half < 2; ++half) {
-            int shift = half ? 32 : 0;
-            const int P = (nbits + RX_MAX_BITS - 1) / RX_MAX_BITS;
-            for (int i = 0; i < P; ++i) {
-                const int w = nbits / P + (i < nbits % P ? 1 : 0);
-                ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
-                radix_pass(src, m_in, shift, w, b->u.hist, b->u.scan, nullptr, c, nullptr, nullptr, s);
-                std::swap(a, c);
-                shift += w;
+        const uint64_t m1 = std::max<uint64_t>(m_in, 1);
+        uint64_t *ka = (uint64_t *)dev_alloc_track(tmp, tmp_bytes, m1 * 8);
+        uint64_t *kb = (uint64_t *)dev_alloc_track(tmp, tmp_bytes, m1 * 8);
+        uint64_t *va = (uint64_t *)dev_alloc_track(tmp, tmp_bytes, (uint64_t)b->n * 8);
+        uint64_t *vb = (uint64_t *)dev_alloc_track(tmp, tmp_bytes, (uint64_t)b->n * 8);
+        uint32_t *perm = (uint32_t *)dev_alloc_track(tmp, tmp_bytes, (uint64_t)b->n * 4);
+        uint32_t *rank = (uint32_t *)dev_alloc_track(tmp, tmp_bytes, (uint64_t)b->n * 4);
+        if (!ka || !kb || !va || !vb || !perm || !rank) { drop_tmp(); free_batch(b); return TC_ENOMEM; }
+        uint64_t *canon = ka;
+        if (m_in > 0) {
+            const uint32_t *dpairs = edges;
+            if (!edges_on_device) {
+                void *p = dev_alloc_track(tmp, tmp_bytes, m_in * 8);
+                if (!p) { drop_tmp(); free_batch(b); return TC_ENOMEM; }
+                cudaMemcpyAsync(p, edges, m_in * 8, cudaMemcpyHostToDevice, s);
+                dpairs = (const uint32_t *)p;
             }
+            uint64_t *d_in_off = (uint64_t *)dev_alloc_track(tmp, tmp_bytes, (k + 1) * 8ull);
+            if (!d_in_off) { drop_tmp(); free_batch(b); return TC_ENOMEM; }
+            cudaMemcpyAsync(d_in_off, in_off.data(), (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
+            k_batch_keys<<<grid_for(m_in, 256, 152 * 16), 256, 0, s>>>(dpairs, m_in, d_in_off, b->u.voff, k, ka,
+                                                                       b->u.st);
+            note_launch();
+            uint64_t *a = ka, *c = kb;
+            const int nbits = batch_bits(b->n);
+            for (int half = 0; half < 2; ++half) {
+                int shift = half ? 32 : 0;
+                const int P = (nbits + RX_MAX_BITS - 1) / RX_MAX_BITS;
+                for (int i = 0; i < P; ++i) {
+                    const int w = nbits / P + (i < nbits % P ? 1 : 0);
+                    radix_pass(a, m_in, shift, w, b->u.hist, b->u.scan, c, s);
+                    std::swap(a, c);
+                    shift += w;
+                }
+            }
+            unique_keys(a, m_in, c, b->u.hist, b->u.scan, b->u.st, s);
+            canon = c;
+            cudaMemcpyAsync(b->h_st, b->u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); drop_tmp(); free_batch(b); return TC_ECUDA; }
+            if (b->h_st->err & ERR_ENDPOINT) { drop_tmp(); free_batch(b); return TC_EINVAL; }
+            m = b->h_st->m_canon;
         }
-        unique_keys(a, m_in, b->u.ekey, b->u.hist, b->u.scan, b->u.st, s);
-        cudaMemcpyAsync(b->h_st, b->u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); drop_tmp(); free_batch(b); return TC_ECUDA; }
+        uint64_t *spare = canon == ka ? kb : ka;
+        const RelabelScratch sc{reinterpret_cast<uint64_t *>(b->u.inlist), spare, va, vb, b->u.deg, b->u.hist,
+                                b->u.scan};
+        relabel(canon, m, b->n, b->u.voff, k, Relabeled{b->u.rel, b->u.orig, perm, rank}, sc, s);
         drop_tmp();
-        if (b->h_st->err & ERR_ENDPOINT) { free_batch(b); return TC_EINVAL; }
-        m = b->h_st->m_canon;
     }
     b->m = m;
-    k_batch_eoff<<<(k + 1 + 127) / 128, 128, 0, s>>>(b->u.ekey, m, b->u.voff, k, b->u.eoff);
+    k_batch_eoff<<<(k + 1 + 127) / 128, 128, 0, s>>>(b->u.rel, m, b->u.voff, k, b->u.eoff);
     note_launch();
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -467,7 +484,7 @@ tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, 
     if (!b || !p || !seed) return TC_EINVAL;
     tc_status st = stage_params(b, p, seed);
     if (st != TC_OK) return st;
-    const uint32_t warp_maxes[3] = {64, 128, 256}, seg_ws[2] = {256, 512}, seg_bs[2] = {1024, 2048};
+    const uint32_t warp_maxes[3] = {64, 128, 256}, seg_ws[2] = {256, 512}, seg_bs[2] = {512, 1024};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();

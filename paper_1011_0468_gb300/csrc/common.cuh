@@ -36,7 +36,7 @@ struct DevState {
     unsigned int h_listed;         // heavy vertices listed for the dense path
     unsigned long long m_canon;    // canonical edges (create only)
     unsigned int unsorted;         // create: adjacent pairs out of order
-    unsigned int pad;
+    unsigned int light_lim;        // 1 + the largest light vertex with an edge (0: none); ids above are heavy
 };
 
 // A batch of independent graphs laid out as one disjoint union: graph g owns
@@ -100,25 +100,6 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 __device__ __forceinline__ bool keep_edge(uint64_t key, uint64_t seed_mix, uint64_t thr)
 {
     return (splitmix64(key ^ seed_mix) >> 11) < thr;
-}
-
-// The same decision for edge i of a batch union: graph g of the edge, its
-// local key, its own (p, seed).
-__device__ __forceinline__ bool keep_edge_batch(const BatchView &bv, uint64_t i, uint64_t key, uint32_t &g)
-{
-    g = find_part(bv.eoff, bv.k, (uint64_t)i);
-    const uint64_t vo = __ldg(bv.voff + g);
-    return keep_edge(key - ((vo << 32) | vo), __ldg(bv.seed_mix + g), __ldg(bv.thr + g));
-}
-
-// Degree-ordered orientation: the edge goes from the endpoint with the
-// smaller (deg, id) to the larger.  For a canonical edge u < v this is u -> v
-// iff deg[u] <= deg[v].  Returns (src << 32 | dst).
-__device__ __forceinline__ uint64_t orient(uint64_t key, const uint32_t *__restrict__ deg)
-{
-    uint32_t u = (uint32_t)(key >> 32), v = (uint32_t)key;
-    uint32_t du = __ldg(deg + u), dv = __ldg(deg + v);
-    return du <= dv ? key : (((uint64_t)v << 32) | u);
 }
 
 // ---------------------------------------------------------------- warp / block

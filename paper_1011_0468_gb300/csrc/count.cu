@@ -1,100 +1,15 @@
-// Counting kernels of libtc, part 1: edge sampling with degrees
-// (Section 3.1), the degree partition (Section 3.2), the kept-edge export and
-// the float64 rescale.  The intersections are in isect.cu.
+// Counting kernels of libtc, part 1: the degree partition (Section 3.2) and
+// the float64 rescale (Section 3.1).  Sampling and the CSR are in csr.cu, the
+// intersections in isect.cu.
 #include "kernels.h"
 
 namespace tcg {
-
-// ======================================================================
-// Sampling + degrees
-// ======================================================================
-
-__device__ __forceinline__ uint32_t sample_one(uint64_t k, uint64_t seed_mix, uint64_t thr,
-                                               uint32_t *__restrict__ deg)
-{
-    if (!keep_edge(k, seed_mix, thr)) return 0;
-    atomicAdd(deg + (k >> 32), 1u);
-    atomicAdd(deg + (uint32_t)k, 1u);
-    return 1;
-}
-
-__global__ void __launch_bounds__(256) k_sample_degree(const uint64_t *__restrict__ ekey, uint64_t m,
-                                                       uint64_t seed_mix, uint64_t thr,
-                                                       uint32_t *__restrict__ deg, DevState *st, BatchView bv,
-                                                       uint32_t *__restrict__ tile_cnt)
-{
-    __shared__ uint32_t wt[33];
-    uint32_t kept = 0;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tile_cnt) {
-        // whole RX_TILE-key tiles per block, with the kept count of each
-        const ulonglong2 *e2 = reinterpret_cast<const ulonglong2 *>(ekey);
-        const uint64_t nt = (m + RX_TILE - 1) / RX_TILE;
-        for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-            uint32_t c = 0;
-            const uint64_t b2 = tile * (RX_TILE / 2);
-#pragma unroll
-            for (int j = 0; j < RX_TILE / 2 / 256; ++j) {
-                const uint64_t i = b2 + (uint64_t)j * 256 + threadIdx.x;
-                if (2 * i + 1 < m) {
-                    const ulonglong2 k = ld_stream_u64x2(e2 + i);
-                    c += sample_one(k.x, seed_mix, thr, deg);
-                    c += sample_one(k.y, seed_mix, thr, deg);
-                } else if (2 * i < m) {
-                    c += sample_one(ekey[2 * i], seed_mix, thr, deg);
-                }
-            }
-            kept += c;
-            c = block_sum(c, wt);
-            if (threadIdx.x == 0) tile_cnt[tile] = c;
-        }
-    } else if (bv.k == 0) {
-        const ulonglong2 *e2 = reinterpret_cast<const ulonglong2 *>(ekey);
-        for (uint64_t i = tid; i < m / 2; i += stride) {
-            const ulonglong2 k = ld_stream_u64x2(e2 + i);
-            kept += sample_one(k.x, seed_mix, thr, deg);
-            kept += sample_one(k.y, seed_mix, thr, deg);
-        }
-        if ((m & 1) && tid == 0) kept += sample_one(ekey[m - 1], seed_mix, thr, deg);
-    } else {
-        // batch: each edge with its own graph's (p, seed); kept edges are
-        // also counted per graph
-        const unsigned lane = lane_id();
-        for (uint64_t base = tid - lane; base < m; base += stride) {
-            const uint64_t i = base + lane, ii = i < m ? i : m - 1;
-            const uint64_t key = ld_stream_u64(ekey + ii);
-            uint32_t g;
-            g = find_part_warp(bv.eoff, bv.k, ii);
-            const uint64_t vo = __ldg(bv.voff + g);
-            const bool f = i < m && keep_edge(key - ((vo << 32) | vo), __ldg(bv.seed_mix + g), __ldg(bv.thr + g));
-            if (f) {
-                atomicAdd(deg + (key >> 32), 1u);
-                atomicAdd(deg + (uint32_t)key, 1u);
-                ++kept;
-            }
-            const unsigned peers = __match_any_sync(FULL, g);
-            const unsigned c = __popc(__ballot_sync(FULL, f) & peers);
-            if (c && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(bv.m_p + g, (unsigned long long)c);
-        }
-    }
-    kept = warp_sum(kept);
-    if (lane_id() == 0 && kept) atomicAdd(&st->m_sampled, (unsigned long long)kept);
-}
 
 unsigned grid_for(uint64_t work, int threads, unsigned cap)
 {
     uint64_t b = ceil_div(work, (uint64_t)threads);
     if (b > cap) b = cap;
     return (unsigned)(b ? b : 1);
-}
-
-void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaStream_t s, uint32_t *tile_cnt)
-{
-    if (b.m == 0) return;
-    k_sample_degree<<<grid_for(b.m / 2 + 1, 256, 152 * 8), 256, 0, s>>>(b.ekey, b.m, seed_mix, thr, b.deg,
-                                                                        b.st, b.bv, b.bv.k ? nullptr : tile_cnt);
-    note_launch();
 }
 
 // ======================================================================
@@ -108,12 +23,15 @@ __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevSta
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     if (bv.k == 0) {
         const unsigned long long mp = st->m_sampled;
+        uint32_t lim = 0;
         for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
             const unsigned long long d = deg[u];
             const uint8_t f = d * d > mp;
             heavy[u] = f;
             h += f;
+            if (!f && d) lim = (uint32_t)u + 1;
         }
+        if (lim) atomicMax(&st->light_lim, lim);
     } else {
         // batch: each vertex against its own graph's m_p
         const unsigned lane = lane_id();
@@ -125,6 +43,7 @@ __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevSta
             const bool f = u < n && d * d > mp;
             if (u < n) heavy[u] = f;
             h += f;
+            if (u < n && !f && d) atomicMax(&st->light_lim, uu + 1);
             const unsigned peers = __match_any_sync(FULL, g);
             const unsigned c = __popc(__ballot_sync(FULL, f) & peers);
             if (c && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(bv.n_heavy + g, c);
@@ -137,69 +56,6 @@ __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevSta
 void partition(const CountBuffers &b, cudaStream_t s)
 {
     k_partition<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.deg, b.n, b.st, b.heavy, b.bv);
-    note_launch();
-}
-
-// ======================================================================
-// Kept-edge list in canonical order (inspection entry point only)
-// ======================================================================
-
-constexpr int KC_THREADS = 1024;
-constexpr int KC_ITEMS = RX_TILE / KC_THREADS;
-
-__global__ void __launch_bounds__(KC_THREADS) k_kept_count(const uint64_t *__restrict__ ekey, uint64_t m,
-                                                           uint64_t seed_mix, uint64_t thr,
-                                                           uint32_t *__restrict__ tile_cnt)
-{
-    __shared__ uint32_t wt[33];
-    const uint64_t base = (uint64_t)blockIdx.x * RX_TILE;
-    uint32_t c = 0;
-    for (int j = 0; j < KC_ITEMS; ++j) {
-        const uint64_t i = base + (uint64_t)j * KC_THREADS + threadIdx.x;
-        if (i < m && keep_edge(ekey[i], seed_mix, thr)) ++c;
-    }
-    c = block_sum(c, wt);
-    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = c;
-}
-
-__global__ void __launch_bounds__(KC_THREADS) k_kept_scatter(const uint64_t *__restrict__ ekey, uint64_t m,
-                                                             uint64_t seed_mix, uint64_t thr,
-                                                             const uint32_t *__restrict__ tile_off,
-                                                             uint64_t *__restrict__ out)
-{
-    __shared__ uint32_t wt[33];
-    const uint64_t base = (uint64_t)blockIdx.x * RX_TILE;
-    uint32_t carry = tile_off[blockIdx.x];
-    for (int j = 0; j < KC_ITEMS; ++j) {
-        const uint64_t i = base + (uint64_t)j * KC_THREADS + threadIdx.x;
-        const uint64_t k = i < m ? ekey[i] : 0;
-        const bool f = i < m && keep_edge(k, seed_mix, thr);
-        uint32_t tot;
-        const uint32_t ex = block_excl_scan((uint32_t)f, wt, &tot);
-        if (f) out[carry + ex] = k;
-        carry += tot;
-    }
-}
-
-void kept_scatter(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out, uint32_t *tile_cnt,
-                  uint32_t *scan_scratch, cudaStream_t s)
-{
-    const uint64_t nt = ceil_div(b.m, RX_TILE);
-    if (nt == 0) return;
-    scan_excl_u32(tile_cnt, nt, nullptr, scan_scratch, s);
-    k_kept_scatter<<<(unsigned)nt, KC_THREADS, 0, s>>>(b.ekey, b.m, seed_mix, thr, tile_cnt, out);
-    note_launch();
-}
-
-void compact_kept(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out, uint32_t *tile_cnt,
-                  uint32_t *scan_scratch, cudaStream_t s)
-{
-    const uint64_t nt = ceil_div(b.m, RX_TILE);
-    if (nt == 0) return;
-    k_kept_count<<<(unsigned)nt, KC_THREADS, 0, s>>>(b.ekey, b.m, seed_mix, thr, tile_cnt);
-    note_launch();
-    scan_excl_u32(tile_cnt, nt, nullptr, scan_scratch, s);
-    k_kept_scatter<<<(unsigned)nt, KC_THREADS, 0, s>>>(b.ekey, b.m, seed_mix, thr, tile_cnt, out);
     note_launch();
 }
 

@@ -1,0 +1,336 @@
+// The degree-oriented CSR of the sampled graph, built by one compaction.
+//
+// Orientation.  Every edge is directed from its endpoint of lower rank,
+// rank = (degree in the whole graph, id): a total order, so each triangle
+// {a, b, c} with rank(a) < rank(b) < rank(c) is seen exactly once, from the
+// pair (a -> b), as the common out-neighbour c of a and b (the counts of
+// Section 3.2 do not depend on the order; ranking by degree keeps every
+// out-degree below (2 m)^(1/2)).  The rank is fixed when the graph is
+// created, and the graph is stored relabeled in rank order: vertex ids are
+// ranks and the canonical key list (u < v, sorted) is sorted by rank.  The
+// kept keys of a sample, in that order, therefore already are the oriented
+// rows, each sorted by rank, and the CSR of a count is a stream compaction.
+// The sampling hash still reads each edge's original key, so a sample is
+// the one Section 3.1 draws on the original graph.
+#include "kernels.h"
+
+namespace tcg {
+
+// ======================================================================
+// Relabeling (graph creation)
+// ======================================================================
+
+__global__ void k_full_degree(const uint64_t *__restrict__ ekey, uint64_t m, uint32_t *__restrict__ deg)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const uint64_t k = ekey[i];
+        atomicAdd(deg + (k >> 32), 1u);
+        atomicAdd(deg + (uint32_t)k, 1u);
+    }
+}
+
+// Rank sort items of the vertices: single graph (rank key << 32 | id) with
+// the full degree as key; batch union (graph << 48 | min(degree, 65535) << 32
+// | id), so that every graph keeps its contiguous id range.
+__global__ void k_vertex_items(const uint32_t *__restrict__ deg, uint32_t n, const uint32_t *__restrict__ voff,
+                               uint32_t k, uint64_t *__restrict__ items)
+{
+    const unsigned lane = lane_id();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+        const uint64_t v = base + lane;
+        const uint32_t vv = (uint32_t)(v < n ? v : n - 1);
+        uint64_t key;
+        if (k == 0) {
+            key = (uint64_t)deg[vv];
+        } else {
+            const uint32_t g = find_part_warp(voff, k, vv);
+            key = ((uint64_t)g << 16) | (uint64_t)min(deg[vv], 0xffffu);
+        }
+        if (v < n) items[v] = (key << 32) | vv;
+    }
+}
+
+__global__ void k_rank_of(const uint64_t *__restrict__ sorted, uint32_t n, uint32_t *__restrict__ perm,
+                          uint32_t *__restrict__ rank)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const uint32_t v = (uint32_t)sorted[r];
+        perm[r] = v;
+        rank[v] = (uint32_t)r;
+    }
+}
+
+__global__ void k_relabel_keys(const uint64_t *__restrict__ ekey, uint64_t m, const uint32_t *__restrict__ rank,
+                               uint64_t *__restrict__ rel)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const uint64_t k = ekey[i];
+        const uint32_t a = __ldg(rank + (k >> 32)), b = __ldg(rank + (uint32_t)k);
+        rel[i] = ((uint64_t)min(a, b) << 32) | max(a, b);
+    }
+}
+
+__global__ void k_original_keys(const uint64_t *__restrict__ rel, uint64_t m, const uint32_t *__restrict__ perm,
+                                uint64_t *__restrict__ orig)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const uint64_t k = rel[i];
+        const uint32_t a = __ldg(perm + (k >> 32)), b = __ldg(perm + (uint32_t)k);
+        orig[i] = ((uint64_t)min(a, b) << 32) | max(a, b);
+    }
+}
+
+// Stable LSD radix sort of items on bits [lo, hi), ping-ponging between a
+// and b; returns the buffer holding the result.
+static uint64_t *sort_bits(uint64_t *a, uint64_t *b, uint64_t count, int lo, int hi, uint32_t *hist,
+                           uint32_t *scan, cudaStream_t s)
+{
+    const int bits = hi - lo;
+    if (bits <= 0 || count == 0) return a;
+    const int P = (bits + RX_MAX_BITS - 1) / RX_MAX_BITS;
+    int shift = lo;
+    for (int i = 0; i < P; ++i) {
+        const int w = bits / P + (i < bits % P ? 1 : 0);
+        radix_pass(a, count, shift, w, hist, scan, b, s);
+        std::swap(a, b);
+        shift += w;
+    }
+    return a;
+}
+
+static int bits_of(uint64_t x)
+{
+    int b = 1;
+    while (b < 64 && (1ull << b) < x) ++b;
+    return b;
+}
+
+uint64_t *relabel(const uint64_t *ekey, uint64_t m, uint32_t n, const uint32_t *voff, uint32_t k,
+                  const Relabeled &out, const RelabelScratch &sc, cudaStream_t s)
+{
+    cudaMemsetAsync(sc.deg, 0, (size_t)n * 4, s);
+    if (m > 0) {
+        k_full_degree<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(ekey, m, sc.deg);
+        note_launch();
+    }
+    k_vertex_items<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(sc.deg, n, voff, k, sc.vA);
+    note_launch();
+    // stable sort by the rank key: degree bits only (ids are already in order)
+    const int key_bits = k == 0 ? bits_of((uint64_t)std::max<uint64_t>(2 * m, 1) + 1) : 16 + bits_of(k + 1);
+    const uint64_t *sorted = sort_bits(sc.vA, sc.vB, n, 32, 32 + std::min(key_bits, 32), sc.hist, sc.scan, s);
+    k_rank_of<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(sorted, n, out.perm, out.rank);
+    note_launch();
+    if (m == 0) return out.rel;
+    k_relabel_keys<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(ekey, m, out.rank, sc.kA);
+    note_launch();
+    const int nb = bits_of(n);
+    uint64_t *r = sort_bits(sc.kA, sc.kB, m, 0, nb, sc.hist, sc.scan, s);
+    r = sort_bits(r, r == sc.kA ? sc.kB : sc.kA, m, 32, 32 + nb, sc.hist, sc.scan, s);
+    cudaMemcpyAsync(out.rel, r, m * 8, cudaMemcpyDeviceToDevice, s);
+    k_original_keys<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(out.rel, m, out.perm, out.orig);
+    note_launch();
+    return out.rel;
+}
+
+// ======================================================================
+// Sampling, sampled degrees and row counts (one read of the edge list)
+// ======================================================================
+
+// Per RX_TILE-edge tile: the Section 3.1 keep test on the original key of
+// each edge, kept out-degrees (dplus, one atomic per run of a source: the
+// list is sorted by source), kept in-degrees (spread, at hot_index), the
+// tile's kept count and one keep bit per edge (32-edge words, in list order).
+__global__ void __launch_bounds__(256) k_sample_rows(const uint64_t *__restrict__ rel,
+                                                     const uint64_t *__restrict__ orig, uint64_t m,
+                                                     uint64_t seed_mix, uint64_t thr, uint32_t *__restrict__ spread,
+                                                     int hbits, uint32_t *__restrict__ dplus,
+                                                     uint32_t *__restrict__ keepw, uint32_t *__restrict__ tile_cnt,
+                                                     DevState *st, BatchView bv)
+{
+    __shared__ uint32_t wt[33];
+    const unsigned lane = lane_id();
+    const uint64_t nt = (m + RX_TILE - 1) / RX_TILE;
+    uint32_t kept_total = 0;
+    for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        uint32_t c = 0;
+#pragma unroll 4
+        for (int j = 0; j < RX_ITEMS; ++j) {
+            const uint64_t i = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
+            const uint64_t ii = i < m ? i : m - 1;
+            const uint64_t r = ld_stream_u64(rel + ii), o = ld_stream_u64(orig + ii);
+            bool f;
+            uint32_t g = 0;
+            if (bv.k == 0) {
+                f = i < m && keep_edge(o, seed_mix, thr);
+            } else {
+                g = find_part_warp(bv.eoff, bv.k, ii);
+                const uint64_t vo = __ldg(bv.voff + g);
+                f = i < m && keep_edge(o - ((vo << 32) | vo), __ldg(bv.seed_mix + g), __ldg(bv.thr + g));
+            }
+            const unsigned word = __ballot_sync(FULL, f);
+            if (lane == 0 && i - lane < m) keepw[(i - lane) >> 5] = word;
+            const uint32_t u = f ? (uint32_t)(r >> 32) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(FULL, u);
+            if (f) {
+                if (lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(dplus + u, (uint32_t)__popc(peers));
+                atomicAdd(spread + hot_index((uint32_t)r, hbits), 1u);
+                ++c;
+            }
+            if (bv.k != 0) {
+                const unsigned gp = __match_any_sync(FULL, g);
+                const unsigned cg = __popc(word & gp);
+                if (cg && lane == (unsigned)(__ffs(gp) - 1)) atomicAdd(bv.m_p + g, (unsigned long long)cg);
+            }
+        }
+        kept_total += c;
+        c = block_sum(c, wt);
+        if (threadIdx.x == 0) tile_cnt[tile] = c;
+    }
+    kept_total = warp_sum(kept_total);
+    if (lane == 0 && kept_total) atomicAdd(&st->m_sampled, (unsigned long long)kept_total);
+}
+
+// Sampled degree = kept out-degree + kept in-degree.
+__global__ void k_degrees(const uint32_t *__restrict__ dplus, const uint32_t *__restrict__ spread, int hbits,
+                          uint32_t n, uint32_t *__restrict__ deg)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+        deg[x] = dplus[x] + spread[hot_index((uint32_t)x, hbits)];
+}
+
+void sample_rows(const RowsArgs &a, cudaStream_t s)
+{
+    const int hb = hot_bits(a.n);
+    cudaMemsetAsync(a.rowptr, 0, ((size_t)a.n + 1) * 4, s);
+    cudaMemsetAsync(a.spread, 0, hot_size(a.n) * 4, s);
+    if (a.m > 0) {
+        const uint64_t nt = ceil_div(a.m, RX_TILE);
+        k_sample_rows<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.orig, a.m, a.seed_mix, a.thr, a.spread, hb,
+                                                                 a.rowptr, a.keepw, a.tile_cnt, a.st, a.bv);
+        note_launch();
+    }
+    k_degrees<<<grid_for(a.n, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.spread, hb, a.n, a.deg);
+    note_launch();
+}
+
+// ======================================================================
+// The CSR: padded columns and in-lists
+// ======================================================================
+
+__device__ __forceinline__ uint32_t pad_of(uint32_t d) { return (4u - (d & 3u)) & 3u; }
+
+// dplus holds the kept out-degrees: ptrp[x] = pad count of row x and
+// P[x] = in-degree deg - d+ of x (x < n); ptrp[n] = P[n] = 0.
+__global__ void k_row_counts(const uint32_t *__restrict__ dplus, const uint32_t *__restrict__ deg, uint32_t n,
+                             uint32_t *__restrict__ ptrp, uint32_t *__restrict__ P)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
+        const uint32_t dp = x < n ? dplus[x] : 0u;
+        ptrp[x] = pad_of(dp);
+        P[x] = x < n ? deg[x] - dp : 0u;
+    }
+}
+
+// In-list cursors at hot_index: cursor of v = start of v's in-list.
+__global__ void k_cursors(const uint32_t *__restrict__ P, uint32_t n, int hbits, uint32_t *__restrict__ spread)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+        spread[hot_index((uint32_t)x, hbits)] = P[x];
+}
+
+// Writes every kept edge (u -> v) at its place in the padded rows (its
+// index among the kept edges, which is its CSR position, plus the padding
+// before row u) and appends (u, that position) to v's in-list (cursors at
+// hot_index).
+__global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict__ rel, uint64_t m,
+                                                      const uint32_t *__restrict__ keepw,
+                                                      const uint32_t *__restrict__ tile_off,
+                                                      const uint32_t *__restrict__ padoff,
+                                                      uint32_t *__restrict__ colp, uint32_t *__restrict__ cursor,
+                                                      int hbits, uint2 *__restrict__ inlist)
+{
+    constexpr int WORDS = RX_TILE / 32;  // 128 keep words per tile
+    __shared__ uint32_t s_word[WORDS], s_pre[WORDS];
+    __shared__ uint32_t wt[33];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint64_t nt = (m + RX_TILE - 1) / RX_TILE;
+    for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        const uint64_t w0 = tile * WORDS, nw = (m + 31) / 32;
+        uint32_t c = 0;
+        if (threadIdx.x < WORDS) {
+            const uint32_t word = w0 + threadIdx.x < nw ? keepw[w0 + threadIdx.x] : 0u;
+            s_word[threadIdx.x] = word;
+            c = __popc(word);
+        }
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan(c, wt, &tot);  // word order = list order
+        if (threadIdx.x < WORDS) s_pre[threadIdx.x] = ex;
+        __syncthreads();
+        const uint32_t base = tile_off[tile];
+        const unsigned lt = lanemask_lt();
+#pragma unroll 4
+        for (int j = 0; j < RX_ITEMS; ++j) {
+            const uint32_t wi = j * 8 + warp;  // word of this warp's 32 edges
+            const uint32_t word = s_word[wi];
+            if (!((word >> lane) & 1u)) continue;
+            const uint64_t i = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
+            const uint64_t r = ld_stream_u64(rel + i);
+            const uint32_t u = (uint32_t)(r >> 32), v = (uint32_t)r;
+            const uint32_t pos = base + s_pre[wi] + __popc(word & lt) + __ldg(padoff + u);
+            colp[pos] = v;
+            const uint32_t q = atomicAdd(cursor + hot_index(v, hbits), 1u);
+            inlist[q] = make_uint2(u, pos);
+        }
+        __syncthreads();  // s_word / s_pre are rewritten for the next tile
+    }
+}
+
+// Row x's padding (SENT) and ptrp[x] = padded start | pad count; ptrp holds
+// the exclusive scan of the pad counts and rowptr the row offsets.
+__global__ void k_pad_finish(const uint32_t *__restrict__ rowptr, uint32_t n, uint32_t *__restrict__ ptrp,
+                             uint32_t *__restrict__ colp)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
+        const uint32_t start = rowptr[x] + ptrp[x];
+        if (x == n) {
+            ptrp[x] = start;
+            continue;
+        }
+        const uint32_t d = rowptr[x + 1] - rowptr[x], pad = pad_of(d);
+        for (uint32_t i = 0; i < pad; ++i) colp[start + d + i] = SENT;
+        ptrp[x] = start | pad;
+    }
+}
+
+void build_rows(const RowsArgs &a, cudaStream_t s)
+{
+    const uint64_t n1 = (uint64_t)a.n + 1;
+    const int hb = hot_bits(a.n);
+    k_row_counts<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.deg, a.n, a.ptrp, a.inptr);
+    note_launch();
+    scan_excl_u32(a.ptrp, n1, nullptr, a.scan, s);
+    scan_excl_u32(a.inptr, n1, nullptr, a.scan, s);
+    scan_excl_u32(a.rowptr, n1, nullptr, a.scan, s);
+    if (a.m > 0) {
+        const uint64_t nt = ceil_div(a.m, RX_TILE);
+        scan_excl_u32(a.tile_cnt, nt, nullptr, a.scan, s);
+        k_cursors<<<grid_for(a.n, 256, 152 * 8), 256, 0, s>>>(a.inptr, a.n, hb, a.spread);
+        note_launch();
+        k_rows_scatter<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.m, a.keepw, a.tile_cnt, a.ptrp, a.colp,
+                                                                  a.spread, hb, a.inlist);
+        note_launch();
+    }
+    k_pad_finish<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp, a.colp);
+    note_launch();
+}
+
+}  // namespace tcg

@@ -1,10 +1,11 @@
 // The heavy class on the tensor cores.
 //
 // Heavy vertices (deg_p^2 > m_p, Section 3.2) number at most 2 m_p^(1/2).
-// Ordered by rank (deg_p, id) they give a strictly upper-triangular 0/1
-// matrix U, U[i][k] = 1 for every kept edge i -> k between heavy vertices
-// (every out-neighbour of a heavy vertex is heavy).  Each all-heavy triangle
-// a < b < c (in rank) is exactly one term of
+// Ordered by id (the graph is stored in rank order, csr.cu, and every kept
+// edge points from the lower id to the higher) they give a strictly
+// upper-triangular 0/1 matrix U, U[i][k] = 1 for every kept edge i -> k
+// between heavy vertices.  Each all-heavy triangle a < b < c is exactly one
+// term of
 //     T_H = sum_{i < k} U[i][k] * (U U)[i][k],
 // the matrix-product route of Alon, Yuster and Zwick that the paper builds
 // on.  U and U^T are packed as bf16 0/1 matrices and the product runs on
@@ -46,11 +47,11 @@ __global__ void k_heavy_list(const uint8_t *__restrict__ heavy, uint32_t n, uint
 
 constexpr int HR_THREADS = 256;
 
-// Dense index of each heavy vertex = its rank by (deg_p, id) among the heavy
-// vertices (O(h^2) comparisons, h <= 2 m_p^(1/2)).  Also decides whether the
+// Dense index of each heavy vertex = the number of heavy vertices with a
+// smaller id (O(h^2) comparisons, h <= 2 m_p^(1/2)), so that every edge
+// between heavy vertices lands above the diagonal.  Also decides whether the
 // dense path runs: 2 <= h <= hcap.
-__global__ void __launch_bounds__(HR_THREADS) k_heavy_rank(const uint32_t *__restrict__ deg,
-                                                           const uint32_t *__restrict__ hlist,
+__global__ void __launch_bounds__(HR_THREADS) k_heavy_rank(const uint32_t *__restrict__ hlist,
                                                            uint32_t *__restrict__ hidx, uint32_t hcap,
                                                            uint32_t hlist_cap, DevState *st)
 {
@@ -64,12 +65,12 @@ __global__ void __launch_bounds__(HR_THREADS) k_heavy_rank(const uint32_t *__res
     uint32_t v = 0;
     if (i < h) {
         v = hlist[i];
-        mine = ((unsigned long long)deg[v] << 32) | v;
+        mine = v;
     }
     uint32_t rank = 0;
     for (uint32_t j0 = 0; j0 < h; j0 += HR_THREADS) {
         const uint32_t j = j0 + threadIdx.x;
-        s_key[threadIdx.x] = j < h ? ((unsigned long long)deg[hlist[j]] << 32) | hlist[j] : ~0ull;
+        s_key[threadIdx.x] = j < h ? (unsigned long long)hlist[j] : ~0ull;
         __syncthreads();
         const uint32_t cnt = min((uint32_t)HR_THREADS, h - j0);
         for (uint32_t q = 0; q < cnt; ++q) rank += s_key[q] < mine;
@@ -93,8 +94,8 @@ __global__ void k_heavy_clear(uint16_t *__restrict__ U, uint16_t *__restrict__ U
     }
 }
 
-// One warp per heavy source: U[rank(v)][rank(w)] = U^T[rank(w)][rank(v)] = 1
-// for every out-neighbour w.
+// One warp per heavy source: U[idx(v)][idx(w)] = U^T[idx(w)][idx(v)] = 1
+// for every heavy out-neighbour w.
 __global__ void k_heavy_pack(const uint32_t *__restrict__ ptrp, const uint32_t *__restrict__ col,
                              const uint8_t *__restrict__ heavy, const uint32_t *__restrict__ hlist,
                              const uint32_t *__restrict__ hidx, uint16_t *__restrict__ U, uint16_t *__restrict__ UT,
@@ -110,10 +111,7 @@ __global__ void k_heavy_pack(const uint32_t *__restrict__ ptrp, const uint32_t *
         const PaddedRow row = padded_row(ptrp, v);
         for (uint32_t q = row.beg + lane; q < row.beg + row.d; q += 32) {
             const uint32_t w = col[q];
-            if (!heavy[w]) {  // cannot happen: heavy vertices point to heavy vertices
-                atomicOr(&st->err, ERR_OVERFLOW);
-                continue;
-            }
+            if (!heavy[w]) continue;  // an edge to a light vertex: not in U
             const uint32_t c = hidx[w];
             if (r >= hcap || c >= hcap) continue;
             U[(uint64_t)r * hcap + c] = ONE;
@@ -421,7 +419,7 @@ void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s
     if (hb.hcap == 0 || hb.hlist_cap == 0 || b.n == 0) return;  // no dense block: DevState::dense stays 0
     k_heavy_list<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.heavy, b.n, hb.hlist, hb.hlist_cap, b.st);
     note_launch();
-    k_heavy_rank<<<(unsigned)ceil_div(hb.hlist_cap, HR_THREADS), HR_THREADS, 0, s>>>(b.deg, hb.hlist, hb.hidx,
+    k_heavy_rank<<<(unsigned)ceil_div(hb.hlist_cap, HR_THREADS), HR_THREADS, 0, s>>>(hb.hlist, hb.hidx,
                                                                                    hb.hcap, hb.hlist_cap, b.st);
     note_launch();
     k_heavy_clear<<<152 * 8, 256, 0, s>>>(hb.U, hb.UT, hb.hcap, b.st);

@@ -1,18 +1,22 @@
 // Counting kernels of libtc, part 2: the exact triangle counts of the light
 // and heavy classes (Section 3.2) on the degree-oriented CSR.
 //
-// Every kept edge is directed from the endpoint of lower (deg_p, id) to the
-// higher one, so each triangle {a, b, c} with rank(a) < rank(b) < rank(c) is
-// seen exactly once: for the pair (a -> b) as the common out-neighbour c of
-// a and b.  Light vertices have lower degree than heavy ones, so a triangle
-// has a light vertex iff its lowest vertex a is light.
+// Every kept edge is directed from the endpoint of lower rank (csr.cu), so
+// each triangle {a, b, c} with rank(a) < rank(b) < rank(c) is seen exactly
+// once: for the pair (a -> b) as the common out-neighbour c of a and b.  A
+// triangle is heavy iff all three vertices are heavy; a pair with a light
+// endpoint closes light triangles only, and only the (rare) pairs of two
+// heavy vertices look at the third vertex (ids at or above
+// DevState::light_lim are heavy, the rest are looked up).
 //
 // A pair (a -> b) is resolved by the endpoint with the LONGER out-list, the
 // "owner": its list is put into a shared-memory hash set and the shorter
-// list is streamed through it, so each pair reads min(d+(a), d+(b))
-// elements:
-//   owner x, partner v in N+(x) with d+(v) <= d+(x)  (triangle class of x)
-//   owner x, partner u in in-list(x), d+(u) < d+(x)  (triangle class of u)
+// list is streamed through it:
+//   owner x, partner v in N+(x) with d+(v) <= d+(x): stream N+(v)
+//   owner x, partner u in in-list(x), d+(u) < d+(x): stream the part of
+//     N+(u) ranked above x (rows are sorted by rank and the in-list entry
+//     holds the position of x in N+(u))
+// so each pair reads at most min(d+(a), d+(b)) entries.
 //
 // Work items are (segment << 32 | owner); a segment is a run of the owner's
 // partner sequence (its d+(x) out-neighbours, then its in-list).  Owners
@@ -25,7 +29,7 @@
 
 namespace tcg {
 
-constexpr uint32_t SEG_B = 2048;     // largest partners per block item (IsectConfig::seg_b)
+constexpr uint32_t SEG_B = 1024;     // largest partners per block item (IsectConfig::seg_b is capped here)
 constexpr uint32_t WARP_MAX = 256;   // largest warp-owner out-degree (IsectConfig::warp_max)
 constexpr uint32_t MID_MAX = 1024;
 constexpr uint32_t EMPTY = 0xffffffffu;
@@ -51,7 +55,7 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t warp_max)
 __device__ __forceinline__ uint32_t seg_len(uint32_t d, uint32_t b, const IsectConfig &cfg)
 {
     const uint32_t floor = b == 0 ? SEG_MIN : 256u, work = b == 0 ? cfg.work_w : cfg.work_b;
-    uint32_t s = b == 0 ? cfg.seg_w : cfg.seg_b;
+    uint32_t s = b == 0 ? cfg.seg_w : min(cfg.seg_b, SEG_B);
     while (s > floor && (uint64_t)s * d > work) s >>= 1;
     return s;
 }
@@ -215,29 +219,66 @@ __device__ __forceinline__ void flush_tally(const Tally &t, unsigned long long *
     }
 }
 
-// Partner y of owner x (out-degree d, class hx): the chunk range of its
-// padded out-list and the class of the pair's triangles.  The range is empty
-// when the pair is resolved by the other endpoint, closes no triangle, or is
-// heavy-class while the dense tensor path counts that class.  Also counts
-// the partner's list entries into the tally.
-__device__ __forceinline__ void partner_of(const uint32_t *__restrict__ ptrp, const uint8_t *__restrict__ heavy,
-                                           uint32_t d, uint32_t hx, uint32_t y, bool is_out, bool skip_heavy,
-                                           uint32_t &c0, uint32_t &nc, uint32_t &cls, Tally &t)
+// Pair classes and what the kernels need to finish them.
+struct PairCtx {
+    const uint8_t *heavy;
+    uint32_t lim;  // DevState::light_lim
+    bool dense;    // the tensor path counts the all-heavy triangles
+};
+
+// Partner y of owner x (out-degree d, heavy flag hx): the chunk range of the
+// part of y's padded out-list to stream and whether both endpoints of the
+// pair are heavy (hh).  For an in-list partner, qpos is the padded position
+// of x in y's row.  The range is empty when the pair is resolved by the
+// other endpoint, closes no triangle, or (dense) can close no triangle with
+// a light vertex.  Also counts the streamed list entries into the tally.
+__device__ __forceinline__ void partner_of(const uint32_t *__restrict__ ptrp, const PairCtx &pc, uint32_t d,
+                                           uint32_t hx, uint32_t x, uint32_t y, bool is_out, uint32_t qpos,
+                                           uint32_t &c0, uint32_t &nc, uint32_t &hh, Tally &t)
 {
     const PaddedRow py = padded_row(ptrp, y);
-    uint32_t len;
-    if (is_out) {
+    uint32_t len, b;
+    if (is_out) {  // pair (x -> y)
         len = (py.d >= 1 && py.d <= d) ? py.d : 0u;
-        cls = hx;
-    } else {  // in-lists hold every in-neighbour: keep the ones this owner resolves
-        len = (py.d >= 2 && py.d < d) ? py.d : 0u;
-        cls = len ? __ldg(heavy + y) : 0u;
+        c0 = py.beg >> 2;
+        nc = (len + 3) >> 2;
+        b = y;
+    } else {  // pair (y -> x): the entries of N+(y) after x
+        const uint32_t end = py.beg + py.d;
+        len = (py.d >= 2 && py.d < d && qpos + 1 < end) ? end - qpos - 1 : 0u;
+        c0 = (qpos + 1) >> 2;
+        nc = len ? ((end + 3) >> 2) - c0 : 0u;
+        b = x;
     }
-    if (cls && skip_heavy) len = 0;  // the dense tensor path counts this class
-    c0 = py.beg >> 2;
-    nc = (len + 3) >> 2;
+    hh = (len && hx) ? (uint32_t)__ldg(pc.heavy + y) : 0u;
+    if (hh && pc.dense && b >= pc.lim) len = nc = 0;  // every third vertex would be heavy
     t.stream += len;
     t.partners += len != 0;
+}
+
+// Looks up the 4 entries of a chunk; hits go to hl (light triangles), or for
+// a pair of two heavy vertices to hl / hv by the third vertex's class.
+template <class Set>
+__device__ __forceinline__ void probe4(const Set &set, const uint4 &q, bool hh, const PairCtx &pc, uint32_t &hl,
+                                       uint32_t &hv)
+{
+    if (!hh) {
+        hl += set.contains(q.x) + set.contains(q.y) + set.contains(q.z) + set.contains(q.w);
+        return;
+    }
+    const uint32_t y[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (set.contains(y[i])) {
+            if (y[i] >= pc.lim || __ldg(pc.heavy + y[i])) ++hv; else ++hl;
+        }
+    }
+}
+
+__device__ __forceinline__ void add_hits(Tally &t, const PairCtx &pc, uint32_t hl, uint32_t hv)
+{
+    t.light += hl;
+    if (!pc.dense) t.heavy += hv;  // else counted by the tensor path
 }
 
 // Lanes [a, b) of the warp hold consecutive parts with cnt >= 1 entries
@@ -251,7 +292,7 @@ __device__ __forceinline__ uint32_t part_lane(uint32_t a, uint32_t before, unsig
 }
 
 // Streams the padded out-lists of up to 32 partners (one per lane: chunks
-// [c0, c0 + nc) of the uint4 view of the columns, triangle class cls)
+// [c0, c0 + nc) of the uint4 view of the columns; hh: both endpoints heavy)
 // through the owners' sets.  The partners' chunks are laid end to end and
 // every step hands each lane one 16-byte chunk (4 list entries; the SENT
 // padding never matches).  A lane finds the partner of its chunk in O(1):
@@ -262,8 +303,8 @@ __device__ __forceinline__ uint32_t part_lane(uint32_t a, uint32_t before, unsig
 // s_base / s_tinfo: this warp's 32-entry shared scratch.
 template <bool MULTI, class Set>
 __device__ __forceinline__ void stream_chunks(const uint4 *__restrict__ col4, const Set &set, const uint2 *wtab,
-                                              uint32_t c0, uint32_t nc, uint32_t cls, uint32_t tinfo,
-                                              uint32_t *s_base, uint32_t *s_tinfo, Tally &t)
+                                              uint32_t c0, uint32_t nc, uint32_t hh, uint32_t tinfo,
+                                              uint32_t *s_base, uint32_t *s_tinfo, const PairCtx &pc, Tally &t)
 {
     const unsigned lane = lane_id();
     const unsigned live = __ballot_sync(FULL, nc != 0);
@@ -272,7 +313,7 @@ __device__ __forceinline__ void stream_chunks(const uint4 *__restrict__ col4, co
     const uint32_t pre = inc - nc;  // first chunk of this partner in the window sequence
     const uint32_t W = __shfl_sync(FULL, inc, 31);
     const uint32_t r = __popc(live & lanemask_lt());  // rank among live partners
-    const unsigned heavy_bits = __reduce_or_sync(FULL, (nc != 0 && cls != 0) ? (1u << r) : 0u);
+    const unsigned hh_bits = __reduce_or_sync(FULL, (nc != 0 && hh != 0) ? (1u << r) : 0u);
     if (nc) {
         s_base[r] = c0 - pre;  // chunk of sequence position e: s_base[rank] + e
         if (MULTI) s_tinfo[r] = tinfo;
@@ -280,7 +321,7 @@ __device__ __forceinline__ void stream_chunks(const uint4 *__restrict__ col4, co
     __syncwarp();
     const unsigned upto = 0xffffffffu >> (31 - lane);  // bits 0..lane
     uint32_t before = 0;  // live partners starting before the window
-    uint32_t hl = 0, hh = 0;
+    uint32_t hl = 0, hv = 0;
     for (uint32_t wb = 0; wb < W; wb += 32 * NWIN) {
         uint32_t e[NWIN], k[NWIN];
         uint4 q[NWIN];
@@ -298,20 +339,18 @@ __device__ __forceinline__ void stream_chunks(const uint4 *__restrict__ col4, co
 #pragma unroll
         for (int i = 0; i < NWIN; ++i) {
             if (e[i] < W) {
-                uint32_t h;
+                const bool h2 = (hh_bits >> k[i]) & 1u;
                 if (MULTI) {
                     const uint32_t ti = s_tinfo[k[i]], sh = ti >> 16;
                     const BucketSet ms{wtab + (ti & 0xffffu), (1u << (32u - sh)) - 1u, sh};
-                    h = ms.contains(q[i].x) + ms.contains(q[i].y) + ms.contains(q[i].z) + ms.contains(q[i].w);
+                    probe4(ms, q[i], h2, pc, hl, hv);
                 } else {
-                    h = set.contains(q[i].x) + set.contains(q[i].y) + set.contains(q[i].z) + set.contains(q[i].w);
+                    probe4(set, q[i], h2, pc, hl, hv);
                 }
-                if ((heavy_bits >> k[i]) & 1u) hh += h; else hl += h;
             }
         }
     }
-    t.light += hl;
-    t.heavy += hh;
+    add_hits(t, pc, hl, hv);
     __syncwarp();  // s_base / s_tinfo are rewritten by the next call
 }
 
@@ -330,7 +369,7 @@ constexpr uint32_t WTAB = 1024;  // per-warp table slots, >= 4 * WARP_MAX
 __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__restrict__ ptrp,
                                                            const uint32_t *__restrict__ col,
                                                            const uint32_t *__restrict__ inptr,
-                                                           const uint32_t *__restrict__ inlist,
+                                                           const uint2 *__restrict__ inlist,
                                                            const uint64_t *__restrict__ items, uint64_t wm_cap,
                                                            const uint8_t *__restrict__ heavy, DevState *st,
                                                            BatchView bv, IsectConfig cfg)
@@ -339,14 +378,15 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
     __shared__ uint32_t s_base[PW_WARPS][32];
     __shared__ uint32_t s_tinfo[PW_WARPS][32];
     // the 32 items of the current grab, by lane: row start, in-list start,
-    // first partner, and out-degree | class << 31
+    // first partner, owner, and out-degree | heavy flag << 31
     __shared__ uint32_t s_beg[PW_WARPS][32], s_ib[PW_WARPS][32], s_p0[PW_WARPS][32], s_dh[PW_WARPS][32];
+    __shared__ uint32_t s_x[PW_WARPS][32];
     __shared__ uint32_t s_ti[PW_WARPS][32], s_pre[PW_WARPS][32];  // table info; prefix within the pack
     __shared__ unsigned long long red[33];
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     const unsigned upto = 0xffffffffu >> (31 - lane);
     const uint32_t nitems = (uint32_t)min((unsigned long long)st->nlist[0], (unsigned long long)wm_cap);
-    const bool skip_heavy = st->dense != 0;
+    const PairCtx pc{heavy, st->light_lim, st->dense != 0};
     const uint4 *col4 = reinterpret_cast<const uint4 *>(col);
     uint2 *tab = s_tab[w];
     const bool batch = bv.k != 0;
@@ -384,6 +424,7 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
             s_ib[w][lane] = ib;
             s_p0[w][lane] = p0;
             s_dh[w][lane] = d | (hx << 31);
+            s_x[w][lane] = x;
         }
         const bool good = slots != 0;
         uint32_t a = 0;
@@ -413,10 +454,10 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
                 const uint32_t ic = warp_incl_scan(c), tot = __shfl_sync(FULL, ic, 31);
                 s_pre[w][lane] = ic - c;
                 __syncwarp();
-                const uint32_t pc = ic - c;
+                const uint32_t pcs = ic - c;
                 uint32_t before = 0;
                 for (uint32_t wb = 0; wb < tot; wb += 32) {
-                    const unsigned sts = __reduce_or_sync(FULL, (c != 0 && pc - wb < 32u) ? (1u << (pc - wb)) : 0u);
+                    const unsigned sts = __reduce_or_sync(FULL, (c != 0 && pcs - wb < 32u) ? (1u << (pcs - wb)) : 0u);
                     const uint32_t L = part_lane(a, before, sts, upto);
                     const uint32_t e = wb + lane;
                     if (e < tot) {
@@ -434,23 +475,29 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
                 const uint32_t ic = warp_incl_scan(c), tot = __shfl_sync(FULL, ic, 31);
                 s_pre[w][lane] = ic - c;
                 __syncwarp();
-                const uint32_t pc = ic - c;
+                const uint32_t pcs = ic - c;
                 uint32_t before = 0;
                 for (uint32_t wb = 0; wb < tot; wb += 32) {
-                    const unsigned sts = __reduce_or_sync(FULL, (c != 0 && pc - wb < 32u) ? (1u << (pc - wb)) : 0u);
+                    const unsigned sts = __reduce_or_sync(FULL, (c != 0 && pcs - wb < 32u) ? (1u << (pcs - wb)) : 0u);
                     const uint32_t L = part_lane(a, before, sts, upto);
                     const uint32_t q = wb + lane;
-                    uint32_t c0 = 0, nc = 0, cls = 0, ti = 0;
+                    uint32_t c0 = 0, nc = 0, hh = 0, ti = 0;
                     if (q < tot) {
                         const uint32_t dh = s_dh[w][L], Ld = dh & 0x7fffffffu;
                         const uint32_t j = s_p0[w][L] + (q - s_pre[w][L]);
                         const bool is_out = j < Ld;
-                        const uint32_t y =
-                            is_out ? __ldg(col + s_beg[w][L] + j) : __ldg(inlist + s_ib[w][L] + j - Ld);
+                        uint32_t y, qpos = 0;
+                        if (is_out) {
+                            y = __ldg(col + s_beg[w][L] + j);
+                        } else {
+                            const uint2 e = __ldg(inlist + s_ib[w][L] + j - Ld);
+                            y = e.x;
+                            qpos = e.y;
+                        }
                         ti = s_ti[w][L];
-                        partner_of(ptrp, heavy, Ld, dh >> 31, y, is_out, skip_heavy, c0, nc, cls, t);
+                        partner_of(ptrp, pc, Ld, dh >> 31, s_x[w][L], y, is_out, qpos, c0, nc, hh, t);
                     }
-                    stream_chunks<true>(col4, BucketSet{tab, 0, 0}, tab, c0, nc, cls, ti, s_base[w], s_tinfo[w], t);
+                    stream_chunks<true>(col4, BucketSet{tab, 0, 0}, tab, c0, nc, hh, ti, s_base[w], s_tinfo[w], pc, t);
                     before += __popc(sts);
                 }
             }
@@ -468,17 +515,73 @@ constexpr int PB_THREADS = 256;
 constexpr int PB_WARPS = PB_THREADS / 32;
 constexpr uint32_t PB_PER_THREAD = SEG_B / PB_THREADS;  // partner slots set up per thread (at most)
 constexpr uint32_t MID_TAB = 8192;                      // >= 8 * MID_MAX slots (dynamic shared memory)
+constexpr uint32_t UNIT = 128;                          // chunks per unit of block streaming
+constexpr uint32_t PRE_CLS = 0x80000000u;               // class bit beside a partner's chunk prefix
+
+// Streams chunks [wb0, min(wb0 + UNIT, total)) of an item's partner sequence
+// through set.  Live partner k has its chunks at s_c0[k] .. and begins at
+// position s_pre[k] & ~PRE_CLS of the sequence (increasing in k); the warp
+// finds the partner covering wb0 by a 32-way search and then maps chunks to
+// partners window by window as stream_chunks does.
+template <class Set>
+__device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, const Set &set, const uint32_t *s_c0,
+                                            const uint32_t *s_pre, uint32_t nlive, uint32_t total, uint32_t wb0,
+                                            const PairCtx &pc, Tally &t)
+{
+    const unsigned lane = lane_id();
+    const unsigned upto = 0xffffffffu >> (31 - lane);
+    // largest k with pre[k] <= wb0 (pre[0] = 0)
+    uint32_t lo = 0, hi = nlive;
+    while (hi - lo > 1) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t k = lo + lane * step;
+        const bool ok = k < hi && (s_pre[k] & ~PRE_CLS) <= wb0;
+        const unsigned m = __ballot_sync(FULL, ok);  // lanes 0 .. j
+        const uint32_t j = 31 - __clz(m);
+        lo += j * step;
+        hi = min(hi, lo + step);
+    }
+    uint32_t before = lo + ((s_pre[lo] & ~PRE_CLS) < wb0 ? 1u : 0u);  // partners beginning before the window
+    const uint32_t end = min(total, wb0 + UNIT);
+    uint32_t hl = 0, hv = 0;
+    for (uint32_t wb = wb0; wb < end; wb += 32 * NWIN) {
+        uint32_t e[NWIN], k[NWIN], pk[NWIN];
+        uint4 q[NWIN];
+#pragma unroll
+        for (int i = 0; i < NWIN; ++i) {
+            const uint32_t w0 = wb + 32u * i, kk = before + lane;
+            const uint32_t pre = kk < nlive ? (s_pre[kk] & ~PRE_CLS) : 0xffffffffu;
+            const unsigned sti = __reduce_or_sync(FULL, pre - w0 < 32u ? (1u << (pre - w0)) : 0u);
+            e[i] = w0 + lane;
+            k[i] = before + __popc(sti & upto) - 1;
+            before += __popc(sti);
+        }
+#pragma unroll
+        for (int i = 0; i < NWIN; ++i) {
+            if (e[i] < end) {
+                pk[i] = s_pre[k[i]];
+                q[i] = __ldg(col4 + (s_c0[k[i]] + (e[i] - (pk[i] & ~PRE_CLS))));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NWIN; ++i) {
+            if (e[i] < end) probe4(set, q[i], (pk[i] & PRE_CLS) != 0, pc, hl, hv);
+        }
+    }
+    add_hits(t, pc, hl, hv);
+}
 
 // One block resolves one item: up to seg_b partners of one owner.  Every
 // thread sets up its share of the partners; the live ones are compacted
-// into shared memory, and the warps take them 32 at a time (stream_chunks)
-// from a shared counter, so they finish within one group of each other.
-// The owner's hash set sits in dynamic shared memory (tab_slots slots).
+// into shared memory with the prefix of their chunk counts, and the warps
+// take the item's chunk sequence UNIT chunks at a time from a shared
+// counter, so they finish within one unit of each other.  The owner's hash
+// set sits in dynamic shared memory (tab_slots slots).
 template <bool DYN>
 __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const uint32_t *__restrict__ ptrp,
                                                                       const uint32_t *__restrict__ col,
                                                                       const uint32_t *__restrict__ inptr,
-                                                                      const uint32_t *__restrict__ inlist,
+                                                                      const uint2 *__restrict__ inlist,
                                                                       const uint64_t *__restrict__ items,
                                                                       uint64_t wm_cap,
                                                                       const uint8_t *__restrict__ heavy,
@@ -487,16 +590,15 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const u
 {
     extern __shared__ uint2 tab[];
     __shared__ uint32_t s_c0[SEG_B];
-    __shared__ uint32_t s_ncc[SEG_B];  // nc << 1 | cls
-    __shared__ uint32_t s_base[PB_WARPS][32];
-    __shared__ uint32_t wt[33];
+    __shared__ uint32_t s_pre[SEG_B];  // chunk prefix | PRE_CLS (both endpoints heavy)
+    __shared__ unsigned long long wt[33];
     __shared__ unsigned long long red[33];
     __shared__ uint32_t s_idx, s_next;
-    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    const unsigned lane = lane_id();
     const uint32_t b = DYN ? 2 : 1;
     const uint32_t nitems =
         (uint32_t)min((unsigned long long)st->nlist[b], (unsigned long long)(DYN ? cap - wm_cap : wm_cap));
-    const bool skip_heavy = st->dense != 0;
+    const PairCtx pc{heavy, st->light_lim, st->dense != 0};
     const uint4 *col4 = reinterpret_cast<const uint4 *>(col);
     Tally t;
     for (;;) {
@@ -527,48 +629,51 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const u
         const uint32_t per = sl / PB_THREADS;  // <= PB_PER_THREAD
         // set up this thread's `per` consecutive partners
         uint32_t pc0[PB_PER_THREAD], pncc[PB_PER_THREAD];
-        uint32_t mine = 0;
+        unsigned long long mine = 0;  // live partners << 32 | their chunks
 #pragma unroll
         for (uint32_t q = 0; q < PB_PER_THREAD; ++q) {
             const uint32_t j = p0 + threadIdx.x * per + q;
-            uint32_t c0 = 0, nc = 0, cls = 0;
+            uint32_t c0 = 0, nc = 0, hh = 0;
             if (q < per && j < p1) {
                 const bool is_out = j < d;
-                const uint32_t y = is_out ? __ldg(col + row.beg + j) : __ldg(inlist + ib + j - d);
-                partner_of(ptrp, heavy, d, hx, y, is_out, skip_heavy, c0, nc, cls, t);
+                uint32_t y, qpos = 0;
+                if (is_out) {
+                    y = __ldg(col + row.beg + j);
+                } else {
+                    const uint2 e = __ldg(inlist + ib + j - d);
+                    y = e.x;
+                    qpos = e.y;
+                }
+                partner_of(ptrp, pc, d, hx, x, y, is_out, qpos, c0, nc, hh, t);
             }
             pc0[q] = c0;
-            pncc[q] = (nc << 1) | cls;
-            mine += nc != 0;
+            pncc[q] = (nc << 1) | hh;
+            if (nc) mine += (1ull << 32) | nc;
         }
-        uint32_t nlive;
-        uint32_t r = block_excl_scan(mine, wt, &nlive);  // also orders the set build
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan(mine, wt, &tot);  // also orders the set build
+        uint32_t r = (uint32_t)(ex >> 32), pre = (uint32_t)ex;
 #pragma unroll
         for (uint32_t q = 0; q < PB_PER_THREAD; ++q) {
-            if (pncc[q] >> 1) {
+            const uint32_t nc = pncc[q] >> 1;
+            if (nc) {
                 s_c0[r] = pc0[q];
-                s_ncc[r] = pncc[q];
+                s_pre[r] = pre | (pncc[q] & 1u ? PRE_CLS : 0u);
                 ++r;
+                pre += nc;
             }
         }
-        const uint32_t ngroups = (nlive + 31) / 32;
+        const uint32_t nlive = (uint32_t)(tot >> 32), total = (uint32_t)tot;
         __syncthreads();  // partners and set are complete
         for (;;) {
-            uint32_t grp = 0;
-            if (lane == 0) grp = atomicAdd(&s_next, 1u);
-            grp = __shfl_sync(FULL, grp, 0);
-            if (grp >= ngroups) break;
-            const uint32_t i = grp * 32 + lane;
-            uint32_t c0 = 0, nc = 0, cls = 0;
-            if (i < nlive) {
-                c0 = s_c0[i];
-                nc = s_ncc[i] >> 1;
-                cls = s_ncc[i] & 1u;
-            }
+            uint32_t u = 0;
+            if (lane == 0) u = atomicAdd(&s_next, 1u);
+            u = __shfl_sync(FULL, u, 0);
+            if (u * UNIT >= total) break;
             if (slots)
-                stream_chunks<false>(col4, set, tab, c0, nc, cls, 0u, s_base[w], nullptr, t);
+                stream_unit(col4, set, s_c0, s_pre, nlive, total, u * UNIT, pc, t);
             else
-                stream_chunks<false>(col4, SortedRow{col + row.beg, d}, tab, c0, nc, cls, 0u, s_base[w], nullptr, t);
+                stream_unit(col4, SortedRow{col + row.beg, d}, s_c0, s_pre, nlive, total, u * UNIT, pc, t);
         }
         if (bv.k != 0) flush_graph_counts(t, bv, g);
         __syncthreads();  // every warp is done with this owner

@@ -32,47 +32,15 @@ uint64_t scan_scratch_elems(uint64_t len);
 
 // In-place exclusive prefix sum of a[0, len).  If total is non-NULL the
 // sum of all elements is written there (device pointer).  scratch holds
-// scan_scratch_elems(len) uint32.  With dyn_items non-NULL only the first
-// dyn_bins * ceil(*dyn_items / RX_TILE) elements (at most len) are scanned:
-// the digit histograms of a radix pass over a device-counted item list.
-void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s,
-                   const unsigned long long *dyn_items = nullptr, uint32_t dyn_bins = 0);
+// scan_scratch_elems(len) uint32.
+void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s);
 
-// Source of the items of a radix pass.
-struct ItemSource {
-    // PLAIN: items as they are; SAMPLE_ORIENT: canonical keys, kept ones
-    // oriented; ORIENT: canonical keys already sampled, all oriented
-    enum Kind { PLAIN = 0, SAMPLE_ORIENT = 1, ORIENT = 2 } kind;
-    const uint64_t *in;                 // PLAIN: items; SAMPLE_ORIENT / ORIENT: canonical keys
-    uint64_t n_host;                    // item count when n_dev is NULL
-    const unsigned long long *n_dev;    // device item count (e.g. m_p), or NULL
-    const uint32_t *deg;                // SAMPLE_ORIENT / ORIENT: sampled degrees
-    uint64_t seed_mix, thr;             // SAMPLE_ORIENT: keep test (single graph)
-    BatchView bv;                       // SAMPLE_ORIENT over a batch union (bv.k > 0)
-};
-
-// Optional by-product of the last radix pass over oriented edges
-// (src << 32 | dst): the in-lists, every pair appended to its dst's list.  P
-// has n + 2 entries; on entry P[0] = 0 and P[1 + v] = the start of v's
-// in-list; afterwards the in-list of vertex v is inlist[P[v] .. P[v + 1])
-// (in no particular order).
-struct InListArgs {
-    uint32_t *P;
-    uint32_t *inlist;
-    uint32_t n;
-};
-
-// One stable LSD radix pass over 64-bit items on bits [shift, shift+width),
-// width <= 8.  Tiles of RX_TILE items; hist holds (1 << width) * ntiles
-// uint32 (digit-major), ntiles = ceil(n_max / RX_TILE).  If dplus is
-// non-NULL the count kernel also histograms (item >> 32) into it.  The
-// scatter writes the full items to out, or when out_low32 is non-NULL only
-// their low 32 bits there, at position + padoff[item >> 32] when padoff is
-// non-NULL.  With `in` non-NULL the scatter also fills the in-lists
-// described above.
-void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
-                uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
-                const InListArgs *in, cudaStream_t s, const uint32_t *padoff = nullptr);
+// One stable LSD radix pass over the n 64-bit items of `in` on bits
+// [shift, shift + width), width <= 8, into out.  hist holds
+// (1 << width) * ceil(n / RX_TILE) uint32; scan_scratch as for
+// scan_excl_u32 on that many.
+void radix_pass(const uint64_t *in, uint64_t n, int shift, int width, uint32_t *hist, uint32_t *scan_scratch,
+                uint64_t *out, cudaStream_t s);
 
 // Padded rows.  The column array of the counting kernels stores every row
 // from a 16-byte boundary, padded with SENT up to a multiple of 4 entries,
@@ -92,32 +60,6 @@ __device__ __forceinline__ PaddedRow padded_row(const uint32_t *__restrict__ ptr
     return PaddedRow{a & ~3u, (b & ~3u) - (a & ~3u) - (a & 3u)};
 }
 
-// Degree-oriented CSR of the sampled graph (single graph or batch union):
-// stable LSD radix sort of (src << 32 | dst) on the src bits (at least two
-// passes), the first pass sampling and orienting the canonical keys, the
-// last one also filling the in-lists (every kept edge, under its dst; their
-// sizes deg - d+ are known after the first pass) and writing the columns
-// straight into the padded layout.  rowptr [n + 1] and inptr [n + 2] are zeroed here;
-// *col = colp (padded columns, colp_capacity entries), ptrp [n + 2] its row
-// pointers, and the in-lists are placed in bufA / bufB.
-struct CsrArgs {
-    const uint64_t *ekey;
-    uint64_t m;
-    uint32_t n;
-    int nbits;  // bits of a vertex id
-    const uint32_t *deg;
-    uint64_t seed_mix, thr;  // single graph
-    BatchView bv;            // batch union (bv.k > 0)
-    const unsigned long long *m_sampled_dev;
-    uint64_t *bufA, *bufB;
-    uint32_t *rowptr, *inptr, *hist, *scan;
-    uint32_t *colp, *ptrp;
-    // NULL, or the kept keys already compacted in canonical order
-    // (m_sampled_dev of them, not in bufA): the first pass then only orients
-    const uint64_t *kept = nullptr;
-};
-void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t s);
-
 // Canonical keys from raw pairs: (min << 32 | max), self-loops become
 // ~0ull; endpoints >= n raise ERR_ENDPOINT; pairs that are not strictly
 // increasing in order are counted into st->unsorted.
@@ -129,11 +71,73 @@ void canon_keys(const uint32_t *pairs, uint64_t m_in, uint32_t n, uint64_t *keys
 void unique_keys(const uint64_t *keys, uint64_t m_in, uint64_t *out, uint32_t *tile_cnt,
                  uint32_t *scan_scratch, DevState *st, cudaStream_t s);
 
+// ---------------------------------------------------------------- csr.cu
+// Rank relabeling at graph creation (see csr.cu).  rank = (full degree, id)
+// within the vertex's graph (batch unions: degree capped at 65535 for the
+// rank, and every graph keeps its id range).
+struct Relabeled {
+    uint64_t *rel;   // [m] canonical keys in rank ids, sorted
+    uint64_t *orig;  // [m] the original canonical key of each rel key
+    uint32_t *perm;  // [n] original id of each rank id
+    uint32_t *rank;  // [n] rank id of each original id
+};
+struct RelabelScratch {
+    uint64_t *kA, *kB;  // [m] each
+    uint64_t *vA, *vB;  // [n] each
+    uint32_t *deg;      // [n]
+    uint32_t *hist;     // radix histograms for max(m, n) items
+    uint32_t *scan;     // scan scratch for those
+};
+// voff / k: batch union offsets (k = 0: one graph).  Returns out.rel.
+uint64_t *relabel(const uint64_t *ekey, uint64_t m, uint32_t n, const uint32_t *voff, uint32_t k,
+                  const Relabeled &out, const RelabelScratch &sc, cudaStream_t s);
+
+// The sampled, oriented CSR of one count (single graph or batch union).
+struct RowsArgs {
+    const uint64_t *rel, *orig;  // relabeled keys and their original keys [m]
+    uint64_t m;
+    uint32_t n;
+    uint64_t seed_mix, thr;      // single graph
+    BatchView bv;                // batch union (bv.k > 0)
+    uint32_t *deg;               // [n] sampled degrees
+    uint32_t *rowptr;            // [n + 1] kept out-degrees, then row offsets
+    uint32_t *inptr;             // [n + 1] in-list offsets (in-list of v: inlist[inptr[v] .. inptr[v + 1]))
+    uint32_t *ptrp;              // [n + 2] padded row pointers (see SENT)
+    uint32_t *colp;              // [colp_capacity(n, m)] padded columns
+    uint2 *inlist;               // [m] in-list entries (source, padded position of the edge in its row)
+    uint32_t *keepw;             // [ceil(m / 32)] keep bits
+    uint32_t *tile_cnt;          // [ceil(m / RX_TILE) + 1]
+    uint32_t *scan;              // scan scratch for max(n + 1, tiles)
+    uint32_t *spread;            // [hot_size(n)] per-vertex counters in hot_index order
+    DevState *st;
+};
+// Counters that every edge bumps at its target (in-degrees, in-list
+// cursors) are kept at hot_index(v): the id rotated within hot_bits(n) bits,
+// so that consecutive ids (the hubs are the top ranks) land 4 KiB apart in
+// different L2 slices instead of all on a few.
+inline int hot_bits(uint32_t n)
+{
+    int b = 1;
+    while (b < 32 && (1ull << b) < n) ++b;
+    return b;
+}
+inline uint64_t hot_size(uint32_t n) { return 1ull << hot_bits(n); }
+__host__ __device__ __forceinline__ uint32_t hot_index(uint32_t v, int bits)
+{
+    const int r = bits < 10 ? bits : 10;
+    const uint32_t mask = bits >= 32 ? 0xffffffffu : (1u << bits) - 1u;
+    return r == bits ? v : (((v << r) | (v >> (bits - r))) & mask);
+}
+// Sampling (Section 3.1), sampled degrees, kept out-degrees, keep bits.
+void sample_rows(const RowsArgs &a, cudaStream_t s);
+// After sample_rows (and the partition): the padded CSR and the in-lists.
+void build_rows(const RowsArgs &a, cudaStream_t s);
+
 // ---------------------------------------------------------------- count.cu
 // Schedule of the intersection kernels (isect.cu); any choice gives the same
 // counts.  warp_max: owners with 2 <= d+ <= warp_max are resolved by one warp
 // (32 .. 256); seg_w / seg_b: most partners per work item of the warp / block
-// kernels (seg_w in [SEG_MIN, 1024], seg_b in [256, 2048], powers of two);
+// kernels (seg_w in [SEG_MIN, 1024], seg_b in [256, 1024], powers of two);
 // work_w / work_b: an owner of out-degree d gets items of the largest power
 // of two <= seg_w (seg_b) partners with partners * d <= work_w (work_b), but
 // at least SEG_MIN (256), which bounds the list entries an item streams.
@@ -141,7 +145,7 @@ constexpr uint32_t SEG_MIN = 64;
 struct IsectConfig {
     uint32_t warp_max = 256;
     uint32_t seg_w = 512;
-    uint32_t seg_b = 2048;
+    uint32_t seg_b = 1024;
     uint32_t work_w = 1u << 14;
     uint32_t work_b = 1u << 19;
 };
@@ -156,7 +160,7 @@ struct CountBuffers {
     uint32_t *col;          // padded CSR columns (see SENT / ptrp)
     uint32_t *ptrp;         // [n + 2] padded row pointers
     uint32_t *inptr;        // [n + 2] in-list offsets
-    uint32_t *inlist;       // in-lists
+    const uint2 *inlist;    // in-list entries (source, padded position of the edge)
     uint64_t *items;        // owner work items [items_cap]
     uint64_t items_cap;
     DevState *st;
@@ -164,17 +168,7 @@ struct CountBuffers {
     IsectConfig cfg;        // intersection schedule
 };
 
-// Sampling and sampled degrees.  With tile_cnt non-NULL (single graph only)
-// the kept edges of every RX_TILE-key tile are also counted there.
-void sample_degree(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, cudaStream_t s,
-                   uint32_t *tile_cnt = nullptr);
-// After sample_degree with tile_cnt: the kept keys, in canonical order, to
-// out (tile_cnt is scanned in place; scan_scratch as for scan_excl_u32).
-void kept_scatter(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out, uint32_t *tile_cnt,
-                  uint32_t *scan_scratch, cudaStream_t s);
 void partition(const CountBuffers &b, cudaStream_t s);
-void compact_kept(const CountBuffers &b, uint64_t seed_mix, uint64_t thr, uint64_t *out,
-                  uint32_t *tile_cnt, uint32_t *scan_scratch, cudaStream_t s);
 // Capacity (entries) of the owner work-item array for a graph of n, m.
 uint64_t items_capacity(uint32_t n, uint64_t m);
 void build_items(const CountBuffers &b, cudaStream_t s);
@@ -193,10 +187,12 @@ void finalize_batch(const CountBuffers &b, const double *p_dev, tc_result *out_d
 struct UnionScratch {
     uint64_t m_cap = 0;
     uint32_t n_cap = 0, k_cap = 0;
-    uint64_t *ekey = nullptr, *bufA = nullptr, *bufB = nullptr, *items = nullptr;
+    uint64_t *rel = nullptr, *orig = nullptr;  // union keys in rank ids (sorted) and their original keys
+    uint2 *inlist = nullptr;
+    uint64_t *items = nullptr;
     uint64_t items_cap = 0;
     uint32_t *deg = nullptr, *rowptr = nullptr, *inptr = nullptr, *hist = nullptr, *scan = nullptr;
-    uint32_t *colp = nullptr, *ptrp = nullptr;
+    uint32_t *colp = nullptr, *ptrp = nullptr, *keepw = nullptr, *tile_cnt = nullptr, *spread = nullptr;
     uint8_t *heavy = nullptr;
     DevState *st = nullptr;
     uint64_t *eoff = nullptr, *thr = nullptr, *seed_mix = nullptr;
@@ -210,9 +206,9 @@ struct UnionScratch {
 // was allocated, bytes the total).
 bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32_t k_cap, std::vector<void *> &allocs,
                          uint64_t &bytes);
-// The count of k graphs whose union (m edges, n vertices) sits in u.ekey,
-// with u.eoff / u.voff / u.thr / u.seed_mix / u.p filled: per-graph results
-// land in u.res_dev.
+// The count of k graphs whose union (m edges, n vertices) sits in u.rel /
+// u.orig (rank order, see csr.cu), with u.eoff / u.voff / u.thr /
+// u.seed_mix / u.p filled: per-graph results land in u.res_dev.
 void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const IsectConfig &cfg, cudaStream_t s);
 
 // ---------------------------------------------------------------- heavy.cu

@@ -31,7 +31,10 @@ constexpr uint64_t NA_HIST = NA_TILES << RX_MAX_BITS;  // uint32 entries
 constexpr uint64_t NA_SCAN = (NA_HIST > NA_N + 2 ? NA_HIST : NA_N + 2) / SC_CHUNK + 2;
 constexpr uint64_t NA_ITEMS = NA_N + 2 * NA_M / SEG_MIN + NA_M / 1024 + 2 * NA_M / 256 + 256;  // >= items_capacity(N, M)
 constexpr uint64_t NA_COLP = NA_M + 3 * NA_M + 4;  // >= colp_capacity(N, M)
-constexpr uint64_t NA_BYTES = 3 * na_round(8 * NA_M)                     // ekey, bufA, bufB
+static_assert(NA_N <= NA_M, "the vertex sort reuses the key buffers");
+constexpr uint64_t NA_BYTES = 4 * na_round(8 * NA_M)                     // ekey (then rel), orig, bufA, bufB
+                              + 3 * na_round(4 * NA_N)                   // perm, rank, spread
+                              + na_round(4 * (NA_M / 32 + 1)) + na_round(4 * (NA_TILES + 1))  // keepw, tile_cnt
                               + na_round(4 * NA_HIST) + na_round(4 * NA_SCAN)
                               + 2 * na_round(4 * (NA_N + 2))             // deg, rowptr
                               + na_round(NA_N)                           // heavy
@@ -86,16 +89,11 @@ int na_bits(uint32_t n)
 }
 
 // Digit widths of the radix passes over `bits` bits (at most 8 each, as even
-// as possible; at least two passes when asked).  Returns the pass count.
-int na_widths(int bits, bool at_least_two, int w[4])
+// as possible).  Returns the pass count.
+int na_widths(int bits, int w[4])
 {
-    int P = (bits + RX_MAX_BITS - 1) / RX_MAX_BITS;
+    const int P = (bits + RX_MAX_BITS - 1) / RX_MAX_BITS;
     for (int i = 0; i < P; ++i) w[i] = bits / P + (i < bits % P ? 1 : 0);
-    if (at_least_two && P == 1) {
-        w[0] = (bits + 1) / 2;
-        w[1] = bits / 2;
-        P = 2;
-    }
     return P;
 }
 
@@ -113,6 +111,12 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
 
     Carver c{(unsigned char *)base};
     uint64_t *ekey = c.take<uint64_t>(NA_M);
+    uint64_t *orig = c.take<uint64_t>(NA_M);
+    uint32_t *perm = c.take<uint32_t>(NA_N);
+    uint32_t *rank = c.take<uint32_t>(NA_N);
+    uint32_t *spread = c.take<uint32_t>(NA_N);  // hot_size(n) <= NA_N
+    uint32_t *keepw = c.take<uint32_t>(NA_M / 32 + 1);
+    uint32_t *tile_cnt = c.take<uint32_t>(NA_TILES + 1);
     uint64_t *bufA = c.take<uint64_t>(NA_M);
     uint64_t *bufB = c.take<uint64_t>(NA_M);
     uint32_t *hist = c.take<uint32_t>(NA_HIST);
@@ -139,11 +143,10 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
         for (int half = 0; half < 2; ++half) {
             int shift = half ? 32 : 0;
             int wd[4];
-            const int np = na_widths(nbits, false, wd);
+            const int np = na_widths(nbits, wd);
             for (int k = 0; k < np; ++k) {
                 const int w = wd[k];
-                ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
-                radix_pass(src, m_in, shift, w, hist, scan, nullptr, b, nullptr, nullptr, s);
+                radix_pass(a, m_in, shift, w, hist, scan, b, s);
                 std::swap(a, b);
                 shift += w;
             }
@@ -158,6 +161,11 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
         m = hs.m_canon;
     }
 
+    // ---- rank relabeling (csr.cu): rel keys replace the canonical keys; the
+    // vertex sort and the key sort both ping-pong between bufA and bufB
+    relabel(ekey, m, n, nullptr, 0, Relabeled{ekey, orig, perm, rank},
+            RelabelScratch{bufA, bufB, bufA, bufB, deg, hist, scan}, s);
+
     // ---- the count (Sections 3.1-3.2), every buffer inside the array
     const uint64_t seed_mix = splitmix64(seed), thr = (uint64_t)(p * 9007199254740992.0);
     CountBuffers cb;
@@ -167,36 +175,36 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     cb.deg = deg;
     cb.heavy = heavy;
     cb.rowptr = rowptr;
-    cb.col = nullptr;
+    cb.col = colp;
     cb.ptrp = ptrp;
     cb.inptr = inptr;
-    cb.inlist = nullptr;
+    cb.inlist = reinterpret_cast<uint2 *>(bufA);
     cb.items = items;
     cb.items_cap = items_capacity(n, m);
     cb.st = st;
+    RowsArgs ra;
+    ra.rel = ekey;
+    ra.orig = orig;
+    ra.m = m;
+    ra.n = n;
+    ra.seed_mix = seed_mix;
+    ra.thr = thr;
+    ra.deg = deg;
+    ra.rowptr = rowptr;
+    ra.inptr = inptr;
+    ra.ptrp = ptrp;
+    ra.colp = colp;
+    ra.inlist = reinterpret_cast<uint2 *>(bufA);
+    ra.keepw = keepw;
+    ra.tile_cnt = tile_cnt;
+    ra.scan = scan;
+    ra.spread = spread;
+    ra.st = st;
     cudaMemsetAsync(st, 0, sizeof(DevState), s);
-    cudaMemsetAsync(deg, 0, (size_t)n * 4, s);
-    sample_degree(cb, seed_mix, thr, s);
+    sample_rows(ra, s);
     partition(cb, s);
     if (m > 0) {
-        CsrArgs a;
-        a.ekey = ekey;
-        a.m = m;
-        a.n = n;
-        a.nbits = na_bits(n);
-        a.deg = deg;
-        a.seed_mix = seed_mix;
-        a.thr = thr;
-        a.m_sampled_dev = &st->m_sampled;
-        a.bufA = bufA;
-        a.bufB = bufB;
-        a.rowptr = rowptr;
-        a.inptr = inptr;
-        a.hist = hist;
-        a.scan = scan;
-        a.colp = colp;
-        a.ptrp = ptrp;
-        csr_build(a, &cb.col, &cb.inlist, s);
+        build_rows(ra, s);
         build_items(cb, s);
         // every out-degree is at most sqrt(2 m) <= 725 here: the smallest
         // table of the large-owner kernel (8192 slots) always suffices

@@ -1,12 +1,6 @@
 // Data-movement primitives of libtc: device-wide exclusive scan, stable LSD
-// radix passes over 64-bit items, and the canonicalisation of raw edge lists.
-//
-// The CSR of the sampled graph is built by a stable radix sort of the
-// oriented kept edges (src << 32 | dst) on the src bits only.  The first pass
-// reads the canonical edge list directly and fuses the edge sampling of
-// Section 3.1 and the degree orientation into its loader, so the kept-edge
-// list is never materialised.  Because the canonical list is sorted by
-// (min, max), a stable sort on src alone leaves every row sorted by dst.
+// radix passes over 64-bit items (graph creation: canonical order and rank
+// order), and the canonicalisation of raw edge lists.
 #include "kernels.h"
 
 namespace tcg {
@@ -18,23 +12,11 @@ namespace tcg {
 constexpr int SC_THREADS = 1024;
 constexpr int SC_ITEMS = SC_CHUNK / SC_THREADS;  // 4
 
-// Effective scan length: len, or for a device-counted item list the digit
-// histograms of its tiles only.
-__device__ __forceinline__ uint64_t scan_len(uint64_t len, const unsigned long long *dyn_items, uint32_t dyn_bins)
-{
-    if (!dyn_items) return len;
-    const uint64_t l = (uint64_t)dyn_bins * ((*dyn_items + RX_TILE - 1) / RX_TILE);
-    return l < len ? l : len;
-}
-
 __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ a, uint64_t len,
-                                                            uint32_t *__restrict__ part,
-                                                            const unsigned long long *dyn_items, uint32_t dyn_bins)
+                                                            uint32_t *__restrict__ part)
 {
     __shared__ uint32_t wt[33];
-    len = scan_len(len, dyn_items, dyn_bins);
     const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
-    if (base >= len) return;  // uniform across the block
     uint32_t s = 0;
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
@@ -47,11 +29,9 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__re
 
 // One block scans the per-block sums in place (exclusive); writes the
 // grand total to total_out when non-NULL.
-__global__ void __launch_bounds__(SC_THREADS) k_scan_spine(uint32_t *part, uint64_t len, uint32_t *total_out,
-                                                           const unsigned long long *dyn_items, uint32_t dyn_bins)
+__global__ void __launch_bounds__(SC_THREADS) k_scan_spine(uint32_t *part, uint64_t nparts, uint32_t *total_out)
 {
     __shared__ uint32_t wt[33];
-    const uint64_t nparts = (scan_len(len, dyn_items, dyn_bins) + SC_CHUNK - 1) / SC_CHUNK;
     uint32_t carry = 0;
     for (uint64_t base = 0; base < nparts; base += SC_THREADS) {
         uint64_t i = base + threadIdx.x;
@@ -64,13 +44,10 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_spine(uint32_t *part, uint6
     if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
-__global__ void __launch_bounds__(SC_THREADS) k_scan_down(uint32_t *a, uint64_t len, const uint32_t *__restrict__ part,
-                                                          const unsigned long long *dyn_items, uint32_t dyn_bins)
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down(uint32_t *a, uint64_t len, const uint32_t *__restrict__ part)
 {
     __shared__ uint32_t wt[33];
-    len = scan_len(len, dyn_items, dyn_bins);
     const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
-    if (base >= len) return;  // uniform across the block
     uint32_t carry = part[blockIdx.x];
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
@@ -85,90 +62,38 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_down(uint32_t *a, uint64_t 
 
 uint64_t scan_scratch_elems(uint64_t len) { return ceil_div(len, SC_CHUNK) + 1; }
 
-void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s,
-                   const unsigned long long *dyn_items, uint32_t dyn_bins)
+void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s)
 {
     if (len == 0) {
         if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
         return;
     }
     const uint64_t nb = ceil_div(len, SC_CHUNK);
-    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch, dyn_items, dyn_bins); note_launch();
-    k_scan_spine<<<1, SC_THREADS, 0, s>>>(scratch, len, total, dyn_items, dyn_bins); note_launch();
-    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch, dyn_items, dyn_bins); note_launch();
+    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
+    k_scan_spine<<<1, SC_THREADS, 0, s>>>(scratch, nb, total); note_launch();
+    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
 }
 
 // ======================================================================
 // Stable LSD radix pass.
 // ======================================================================
 
-// Loads item i of a pass; returns false when the item does not take part
-// (an edge that the sampling drops).
-// g: the batch graph of item i (batch unions only).
-__device__ __forceinline__ bool load_item(const ItemSource &src, uint64_t i, uint64_t &item, uint32_t g)
-{
-    if (src.kind == ItemSource::PLAIN) {
-        item = ld_stream_u64(src.in + i);
-        return true;
-    }
-    const uint64_t key = ld_stream_u64(src.in + i);
-    if (src.kind == ItemSource::ORIENT) {
-        item = orient(key, src.deg);
-        return true;
-    }
-    if (src.bv.k == 0) {
-        if (!keep_edge(key, src.seed_mix, src.thr)) return false;
-    } else {
-        const uint64_t vo = __ldg(src.bv.voff + g);
-        if (!keep_edge(key - ((vo << 32) | vo), __ldg(src.bv.seed_mix + g), __ldg(src.bv.thr + g))) return false;
-    }
-    item = orient(key, src.deg);
-    return true;
-}
-
-// Batch graph of item i for every lane of a full warp (indices consecutive
-// across lanes); 0 unless the source samples a batch union.
-__device__ __forceinline__ uint32_t item_graph(const ItemSource &src, uint64_t i, uint64_t n)
-{
-    if (src.kind != ItemSource::SAMPLE_ORIENT || src.bv.k == 0) return 0;
-    return find_part_warp(src.bv.eoff, src.bv.k, i < n ? i : n - 1);
-}
-
-// Per-tile digit counts (per-warp shared histograms, summed at the end), plus
-// the out-degree histogram (first pass).
-__global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int shift, int width,
-                                                            uint32_t *__restrict__ hist, uint32_t ntiles,
-                                                            uint32_t *__restrict__ dplus)
+// Per-tile digit counts (per-warp shared histograms, summed at the end).
+__global__ void __launch_bounds__(RX_THREADS) k_radix_count(const uint64_t *__restrict__ in, uint64_t n, int shift,
+                                                            int width, uint32_t *__restrict__ hist, uint32_t ntiles)
 {
     constexpr int NW = RX_THREADS / 32;
     __shared__ uint32_t cnt[NW][RX_BINS];
-    const uint64_t n = src.n_dev ? *src.n_dev : src.n_host;
     const uint32_t tile = blockIdx.x;
-    if (src.n_dev) {  // device-counted items: only their tiles have histograms
-        const uint64_t nt = (n + RX_TILE - 1) / RX_TILE;
-        if (tile >= nt) return;  // uniform across the block
-        ntiles = (uint32_t)nt;
-    }
     const int nb = 1 << width;
     const unsigned warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < NW * RX_BINS; i += RX_THREADS) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const uint64_t base = (uint64_t)tile * RX_TILE;
-    if (base < n) {
-        const uint32_t mask = (uint32_t)nb - 1;
-        for (int j = 0; j < RX_ITEMS; ++j) {
-            const uint64_t i = base + (uint64_t)j * RX_THREADS + threadIdx.x;
-            uint64_t item = 0;
-            const uint32_t g = item_graph(src, i, n);
-            const bool valid = i < n && load_item(src, i, item, g);
-            if (valid) atomicAdd(&cnt[warp][(uint32_t)(item >> shift) & mask], 1u);
-            if (dplus) {
-                // runs of one source are common (canonical order): one atomic per run
-                const uint32_t x = valid ? (uint32_t)(item >> 32) : 0xffffffffu;
-                const unsigned peers = __match_any_sync(FULL, x);
-                if (valid && lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(dplus + x, (uint32_t)__popc(peers));
-            }
-        }
+    const uint32_t mask = (uint32_t)nb - 1;
+    for (int j = 0; j < RX_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * RX_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[warp][(uint32_t)(ld_stream_u64(in + i) >> shift) & mask], 1u);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < nb; d += RX_THREADS) {
@@ -182,13 +107,10 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_count(ItemSource src, int 
 // Stable scatter of one tile: rank every item within its digit (warp
 // order, then item order), sort the tile by digit in shared memory, and
 // write each digit's run to its global offset with consecutive threads on
-// consecutive positions.  With in-lists, each item is also appended to its
-// dst's list; a thread issues all its appends before writing any entry.
-__global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, int shift, int width,
-                                                              const uint32_t *__restrict__ offs, uint32_t ntiles,
-                                                              uint64_t *__restrict__ out,
-                                                              uint32_t *__restrict__ out_low32, InListArgs in,
-                                                              const uint32_t *__restrict__ padoff)
+// consecutive positions.
+__global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(const uint64_t *__restrict__ in, uint64_t n, int shift,
+                                                              int width, const uint32_t *__restrict__ offs,
+                                                              uint32_t ntiles, uint64_t *__restrict__ out)
 {
     constexpr int NW = RX_THREADS / 32;
     static_assert(RX_BINS == RX_THREADS, "one digit per thread in the tile scan");
@@ -197,11 +119,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
     __shared__ uint32_t tstart[RX_BINS];  // first local position of each digit in the sorted tile
     __shared__ uint32_t tbase[RX_BINS];   // global position of each digit's run
     __shared__ uint32_t wt[33];
-    const uint64_t n = src.n_dev ? *src.n_dev : src.n_host;
     const uint32_t tile = blockIdx.x;
     const uint64_t base = (uint64_t)tile * RX_TILE;
-    if (base >= n) return;  // uniform across the block
-    if (src.n_dev) ntiles = (uint32_t)((n + RX_TILE - 1) / RX_TILE);  // histogram stride of this pass
     const int nb = 1 << width;
     const uint32_t mask = (uint32_t)nb - 1;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
@@ -215,9 +134,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
 #pragma unroll
     for (int j = 0; j < RX_ITEMS; ++j) {  // all loads first
         const uint64_t i = seg + (uint64_t)j * 32 + lane;
-        items[j] = 0;
-        const uint32_t g = item_graph(src, i, n);
-        packed[j] = (i < n && load_item(src, i, items[j], g)) ? 0u : 0xffffffffu;
+        items[j] = i < n ? ld_stream_u64(in + i) : 0;
+        packed[j] = i < n ? 0u : 0xffffffffu;
     }
     __syncthreads();
 #pragma unroll
@@ -246,7 +164,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
             }
         }
     }
-    uint32_t count;  // valid items of the tile
+    uint32_t count;  // items of the tile
     const uint32_t start = block_excl_scan(tot, wt, &count);
     tstart[threadIdx.x] = start;
     __syncthreads();
@@ -257,40 +175,22 @@ __global__ void __launch_bounds__(RX_THREADS) k_radix_scatter(ItemSource src, in
         s_items[tstart[d] + whist[warp][d] + r] = items[j];
     }
     __syncthreads();
-    uint32_t q[RX_ITEMS];
-#pragma unroll
-    for (int k = 0; k < RX_ITEMS; ++k) {
-        const uint32_t i = threadIdx.x + k * RX_THREADS;
-        q[k] = 0xffffffffu;
-        if (i < count) {
-            const uint64_t item = s_items[i];
-            const uint32_t d = (uint32_t)(item >> shift) & mask;
-            const uint32_t pos = tbase[d] + (i - tstart[d]);
-            if (out_low32)
-                out_low32[padoff ? pos + __ldg(padoff + (item >> 32)) : pos] = (uint32_t)item;
-            else
-                out[pos] = item;
-            if (in.P) q[k] = atomicAdd(in.P + (uint32_t)item + 1, 1u);
-        }
-    }
-    if (in.P) {
-#pragma unroll
-        for (int k = 0; k < RX_ITEMS; ++k)
-            if (q[k] != 0xffffffffu) in.inlist[q[k]] = (uint32_t)(s_items[threadIdx.x + k * RX_THREADS] >> 32);
+    for (uint32_t i = threadIdx.x; i < count; i += RX_THREADS) {
+        const uint64_t item = s_items[i];
+        const uint32_t d = (uint32_t)(item >> shift) & mask;
+        out[tbase[d] + (i - tstart[d])] = item;
     }
 }
 
-void radix_pass(const ItemSource &src, uint64_t n_max, int shift, int width, uint32_t *hist,
-                uint32_t *scan_scratch, uint32_t *dplus, uint64_t *out, uint32_t *out_low32,
-                const InListArgs *in, cudaStream_t s, const uint32_t *padoff)
+void radix_pass(const uint64_t *in, uint64_t n, int shift, int width, uint32_t *hist, uint32_t *scan_scratch,
+                uint64_t *out, cudaStream_t s)
 {
-    const InListArgs inl = in ? *in : InListArgs{nullptr, nullptr, 0};
-    const uint64_t ntiles = ceil_div(n_max, RX_TILE);
+    const uint64_t ntiles = ceil_div(n, RX_TILE);
     if (ntiles == 0) return;
-    k_radix_count<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, dplus); note_launch();
-    scan_excl_u32(hist, ntiles << width, nullptr, scan_scratch, s, src.n_dev, 1u << width);
-    k_radix_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(src, shift, width, hist, (uint32_t)ntiles, out,
-                                                            out_low32, inl, padoff); note_launch();
+    k_radix_count<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(in, n, shift, width, hist, (uint32_t)ntiles); note_launch();
+    scan_excl_u32(hist, ntiles << width, nullptr, scan_scratch, s);
+    k_radix_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(in, n, shift, width, hist, (uint32_t)ntiles, out);
+    note_launch();
 }
 
 // ======================================================================
@@ -397,101 +297,4 @@ void unique_keys(const uint64_t *keys, uint64_t m_in, uint64_t *out, uint32_t *t
 
 }  // namespace tcg
 
-namespace tcg {
 
-// ======================================================================
-// Padded rows (see SENT in kernels.h).
-// ======================================================================
-
-__device__ __forceinline__ uint32_t pad_of(uint32_t d) { return (4u - (d & 3u)) & 3u; }
-
-// Once the out-degrees d+ are counted (dplus): ptrp[x] = pad count of row x,
-// and P[1 + x] = in-degree deg - d+ of x (x < n); ptrp[n] = P[n + 1] = 0,
-// P[0] = 0.
-__global__ void k_row_counts(const uint32_t *__restrict__ dplus, const uint32_t *__restrict__ deg, uint32_t n,
-                             uint32_t *__restrict__ ptrp, uint32_t *__restrict__ P)
-{
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
-        const uint32_t dp = x < n ? dplus[x] : 0u;
-        ptrp[x] = pad_of(dp);
-        P[x + 1] = x < n ? deg[x] - dp : 0u;
-        if (x == 0) P[0] = 0;
-    }
-}
-
-// ptrp holds the exclusive scan of the pad counts and rowptr the row
-// offsets: write each row's padding and turn ptrp into padded starts
-// tagged with the pad count.
-__global__ void k_pad_finish(const uint32_t *__restrict__ rowptr, uint32_t n, uint32_t *__restrict__ ptrp,
-                             uint32_t *__restrict__ colp)
-{
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
-        const uint32_t start = rowptr[x] + ptrp[x];
-        if (x == n) {
-            ptrp[x] = start;
-            continue;
-        }
-        const uint32_t d = rowptr[x + 1] - rowptr[x], pad = pad_of(d);
-        for (uint32_t i = 0; i < pad; ++i) colp[start + d + i] = SENT;
-        ptrp[x] = start | pad;
-    }
-}
-
-void csr_build(const CsrArgs &a, uint32_t **col, uint32_t **inlist, cudaStream_t s)
-{
-    cudaMemsetAsync(a.rowptr, 0, ((size_t)a.n + 1) * 4, s);
-    cudaMemsetAsync(a.inptr, 0, ((size_t)a.n + 2) * 4, s);
-    // digit widths: at most RX_MAX_BITS each, as even as possible, >= 2 passes
-    int P = (a.nbits + RX_MAX_BITS - 1) / RX_MAX_BITS, widths[8];
-    for (int i = 0; i < P; ++i) widths[i] = a.nbits / P + (i < a.nbits % P ? 1 : 0);
-    if (P == 1) {
-        widths[0] = (a.nbits + 1) / 2;
-        widths[1] = a.nbits / 2;
-        P = 2;
-    }
-    uint64_t *bufs[2] = {a.bufA, a.bufB};
-    const uint64_t *in = a.ekey;
-    int cur = 0, shift = 32;
-    for (int p = 0; p < P; ++p) {
-        const bool last = p + 1 == P;
-        ItemSource src;
-        if (p == 0 && a.kept) {
-            src = ItemSource{ItemSource::ORIENT, a.kept, 0, a.m_sampled_dev, a.deg, 0, 0};
-        } else if (p == 0) {
-            src = ItemSource{ItemSource::SAMPLE_ORIENT, a.ekey, a.m, nullptr, a.deg, a.seed_mix, a.thr};
-            src.bv = a.bv;
-        } else {
-            src = ItemSource{ItemSource::PLAIN, in, 0, a.m_sampled_dev, nullptr, 0, 0};
-        }
-        uint64_t *out = bufs[cur];
-        InListArgs il{a.inptr, nullptr, a.n};
-        if (last) {
-            // padded columns in colp, the in-lists in the output buffer (the
-            // input buffer is still being read)
-            *col = a.colp;
-            *inlist = reinterpret_cast<uint32_t *>(out);
-            il.inlist = *inlist;
-        }
-        radix_pass(src, a.m, shift, widths[p], a.hist, a.scan, p == 0 ? a.rowptr : nullptr, last ? nullptr : out,
-                   last ? *col : nullptr, last ? &il : nullptr, s, last ? a.ptrp : nullptr);
-        if (p == 0) {
-            // out-degrees are complete: pad offsets and in-list offsets for
-            // the last pass
-            k_row_counts<<<grid_for((uint64_t)a.n + 1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.deg, a.n, a.ptrp,
-                                                                                   a.inptr);
-            note_launch();
-            scan_excl_u32(a.ptrp, (uint64_t)a.n + 1, nullptr, a.scan, s);
-            scan_excl_u32(a.inptr + 1, (uint64_t)a.n + 1, nullptr, a.scan, s);
-        }
-        in = out;
-        cur ^= 1;
-        shift += widths[p];
-    }
-    scan_excl_u32(a.rowptr, (uint64_t)a.n + 1, nullptr, a.scan, s);
-    k_pad_finish<<<grid_for((uint64_t)a.n + 1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp, a.colp);
-    note_launch();
-}
-
-}  // namespace tcg

@@ -2,9 +2,9 @@
 //
 // A request is (graph, p, seed): one instance of the problem of Section 1
 // with the sample of Section 3.1.  Registered graphs stay resident in device
-// memory as canonical edge lists (sorted u << 32 | v keys, the upper-triangle
-// CSR of the graph), with a pinned host copy from which an evicted graph is
-// uploaded again.  A worker thread owns the count slots; each slot holds the
+// memory in rank order (csr.cu: the sorted canonical keys in rank ids, then
+// the original key of each), with a pinned host copy from which an evicted
+// graph is uploaded again.  A worker thread owns the count slots; each slot holds the
 // scratch of one batched count (union_count, batch.cu) and its own stream.
 // When a slot is free the worker admits the longest first-come prefix of the
 // queue that fits the slot and the HBM budget, gathers the requests' edge
@@ -33,10 +33,12 @@ namespace {
 
 constexpr uint32_t MAX_SLOTS = 8;
 
-// out[i] = key i of the union: request g's canonical keys, both endpoints
-// shifted by voff[g] (keys stay sorted because the vertex ranges increase).
+// Key i of the union: request g's rank-order keys and their original keys
+// (src[g] holds m_g of each, one after the other), both endpoints shifted by
+// voff[g] (keys stay sorted because the vertex ranges increase).
 __global__ void k_gather(const uint64_t *const *__restrict__ src, const uint64_t *__restrict__ eoff,
-                         const uint32_t *__restrict__ voff, uint32_t k, uint64_t m, uint64_t *__restrict__ out)
+                         const uint32_t *__restrict__ voff, uint32_t k, uint64_t m, uint64_t *__restrict__ rel,
+                         uint64_t *__restrict__ orig)
 {
     const unsigned lane = lane_id();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -44,8 +46,10 @@ __global__ void k_gather(const uint64_t *const *__restrict__ src, const uint64_t
         const uint64_t i = base + lane, ii = i < m ? i : m - 1;
         const uint32_t g = find_part_warp(eoff, k, ii);
         if (i >= m) continue;
-        const uint64_t vo = __ldg(voff + g);
-        out[i] = __ldg(src[g] + (i - __ldg(eoff + g))) + ((vo << 32) | vo);
+        const uint64_t vo = __ldg(voff + g), e0 = __ldg(eoff + g), mg = __ldg(eoff + g + 1) - e0;
+        const uint64_t *sg = src[g];
+        rel[i] = __ldg(sg + (i - e0)) + ((vo << 32) | vo);
+        orig[i] = __ldg(sg + mg + (i - e0)) + ((vo << 32) | vo);
     }
 }
 
@@ -64,7 +68,7 @@ double now_us(std::chrono::steady_clock::time_point t0)
 struct GraphEntry {
     uint64_t m = 0;
     uint32_t n = 0;
-    uint64_t *host = nullptr;   // pinned canonical keys [m]
+    uint64_t *host = nullptr;   // pinned keys [2 m]: rank-order keys, then their original keys
     uint64_t *dev = nullptr;    // resident copy (NULL when evicted or m == 0)
     uint64_t dev_bytes = 0;     // bytes charged to the budget while resident
     bool resident = false;      // charged (upload may still be in flight)
@@ -256,12 +260,12 @@ tc_status enqueue_wave(tc_server *srv, uint32_t si, const std::vector<GraphEntry
     cudaStream_t s = sl.s;
     for (uint64_t *ptr : frees) cudaFreeAsync(ptr, s);
     for (GraphEntry *g : uploads) {
-        if (cudaMallocAsync((void **)&g->dev, g->m * 8, s) != cudaSuccess) {
+        if (cudaMallocAsync((void **)&g->dev, g->m * 16, s) != cudaSuccess) {
             cudaGetLastError();
             g->dev = nullptr;
             return TC_ENOMEM;
         }
-        cudaMemcpyAsync(g->dev, g->host, g->m * 8, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(g->dev, g->host, g->m * 16, cudaMemcpyHostToDevice, s);
         cudaEventRecord(g->ready, s);
         g->upload_slot = (int)si;
         g->upload_wave = sl.serial;
@@ -294,7 +298,8 @@ tc_status enqueue_wave(tc_server *srv, uint32_t si, const std::vector<GraphEntry
     cudaMemcpyAsync(sl.u.thr, sl.h_thr, k * 8ull, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(sl.u.seed_mix, sl.h_seed_mix, k * 8ull, cudaMemcpyHostToDevice, s);
     if (m > 0) {
-        k_gather<<<grid_for(m, 256, 152 * 8), 256, 0, s>>>(sl.d_src, sl.u.eoff, sl.u.voff, k, m, sl.u.ekey);
+        k_gather<<<grid_for(m, 256, 152 * 8), 256, 0, s>>>(sl.d_src, sl.u.eoff, sl.u.voff, k, m, sl.u.rel,
+                                                            sl.u.orig);
         note_launch();
     }
     union_count(sl.u, m, (uint32_t)n, k, IsectConfig{}, s);
@@ -546,8 +551,7 @@ tc_status tc_server_add_graph(tc_server *srv, const uint32_t *edges, uint64_t m_
             const int P = (nbits + RX_MAX_BITS - 1) / RX_MAX_BITS;
             for (int i = 0; i < P; ++i) {
                 const int w = nbits / P + (i < nbits % P ? 1 : 0);
-                ItemSource src{ItemSource::PLAIN, a, m_in, nullptr, nullptr, 0, 0};
-                radix_pass(src, m_in, shift, w, hist, scan, nullptr, b, nullptr, nullptr, s);
+                radix_pass(a, m_in, shift, w, hist, scan, b, s);
                 std::swap(a, b);
                 shift += w;
             }
@@ -560,15 +564,27 @@ tc_status tc_server_add_graph(tc_server *srv, const uint32_t *edges, uint64_t m_
         if (!ok) return drop(TC_ECUDA);
         if (hs.err & ERR_ENDPOINT) return drop(TC_EINVAL);
         m = hs.m_canon;
-        canon = b;
+        if (m > 0) {
+            // rank relabeling (csr.cu) into one block: rel keys, then original keys
+            const uint64_t hl = std::max<uint64_t>(ceil_div(std::max<uint64_t>(m, n), RX_TILE), 1) << RX_MAX_BITS;
+            uint64_t *blk = (uint64_t *)talloc(m * 16), *kb = (uint64_t *)talloc(m * 8);
+            uint64_t *va = (uint64_t *)talloc((uint64_t)n * 8), *vb = (uint64_t *)talloc((uint64_t)n * 8);
+            uint32_t *perm = (uint32_t *)talloc((uint64_t)n * 4), *rank = (uint32_t *)talloc((uint64_t)n * 4);
+            uint32_t *deg = (uint32_t *)talloc((uint64_t)n * 4), *hist2 = (uint32_t *)talloc(hl * 4);
+            uint32_t *scan2 = (uint32_t *)talloc(scan_scratch_elems(std::max<uint64_t>(hl, (uint64_t)n + 2)) * 4);
+            if (!blk || !kb || !va || !vb || !perm || !rank || !deg || !hist2 || !scan2) return drop(TC_ENOMEM);
+            const RelabelScratch sc{a, kb, va, vb, deg, hist2, scan2};
+            relabel(b, m, n, nullptr, 0, Relabeled{blk, blk + m, perm, rank}, sc, s);
+            canon = blk;
+        }
     }
     g->m = m;
-    g->dev_bytes = m * 8;
+    g->dev_bytes = m * 16;
     if (m > srv->slot_edges || n > srv->slot_vertices) return drop(TC_EINVAL);
     if (g->dev_bytes > srv->budget - srv->slot_bytes) return drop(TC_ENOMEM);
     if (m > 0) {
-        if (!pinned(&g->host, m)) return drop(TC_ENOMEM);
-        cudaMemcpyAsync(g->host, canon, m * 8, cudaMemcpyDeviceToHost, s);
+        if (!pinned(&g->host, 2 * m)) return drop(TC_ENOMEM);
+        cudaMemcpyAsync(g->host, canon, m * 16, cudaMemcpyDeviceToHost, s);
     }
     // resident right away if that needs no eviction
     bool keep = false;
@@ -578,8 +594,8 @@ tc_status tc_server_add_graph(tc_server *srv, const uint32_t *edges, uint64_t m_
         if (keep) srv->resident_bytes += g->dev_bytes;  // reserve
     }
     if (keep) {
-        if (cudaMallocAsync((void **)&g->dev, m * 8, s) == cudaSuccess) {
-            cudaMemcpyAsync(g->dev, canon, m * 8, cudaMemcpyDeviceToDevice, s);
+        if (cudaMallocAsync((void **)&g->dev, m * 16, s) == cudaSuccess) {
+            cudaMemcpyAsync(g->dev, canon, m * 16, cudaMemcpyDeviceToDevice, s);
         } else {
             cudaGetLastError();
             g->dev = nullptr;

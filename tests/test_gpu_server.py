@@ -118,8 +118,9 @@ def test_budget_evicts_and_results_stay_the_same(tc):
     with tc.Server(1 << 40, **slot) as probe:
         slot_bytes = probe.stats()["slot_bytes"]
     # room for the largest graph and a little more: most graphs must be
-    # evicted and uploaded again as the requests cycle through them
-    sizes = [len(oracle.canonicalize(e, n)) * 8 for e, n in graphs]
+    # evicted and uploaded again as the requests cycle through them (a
+    # resident graph holds 16 bytes per canonical edge)
+    sizes = [len(oracle.canonicalize(e, n)) * 16 for e, n in graphs]
     room = max(sizes) + 200_000
     reqs = requests(300, len(graphs), 3)
     alone = Alone(tc, graphs)
@@ -189,9 +190,9 @@ def test_server_errors(tc):
             srv.poll(t)  # released by wait
     with tc.Server(1 << 30, slots=1, slot_edges=1 << 16, slot_vertices=1 << 16, slot_requests=8) as probe:
         slot_bytes = probe.stats()["slot_bytes"]
-    with tc.Server(slot_bytes + 1000, slots=1, slot_edges=1 << 16, slot_vertices=1 << 16, slot_requests=8) as srv:
+    with tc.Server(slot_bytes + 2000, slots=1, slot_edges=1 << 16, slot_vertices=1 << 16, slot_requests=8) as srv:
         with pytest.raises(tc.TCError) as e:
-            srv.add_graph(gen.complete(40), 40)  # 780 edges * 8 bytes > the 1000 left
+            srv.add_graph(gen.complete(40), 40)  # 780 edges * 16 bytes > the 2000 left
         assert e.value.status == tc.TC_ENOMEM
-        gid = srv.add_graph(gen.complete(12), 12)  # 66 edges fit
+        gid = srv.add_graph(gen.complete(12), 12)  # 66 edges * 16 bytes fit
         assert srv.wait(srv.submit(gid, 1.0, 3))["estimate"] == 220.0
