@@ -94,6 +94,7 @@ struct tc_graph {
     uint32_t *hist = nullptr;   // [RX_BINS * ntiles(m)]
     uint32_t *scan = nullptr;   // scan scratch
     HeavyBuffers hb;            // dense heavy block (hb.hcap == 0: not used)
+    CoreBuffers core;           // dense core of the top ranks (core.hb.hcap == 0: not used)
     DevState *st = nullptr;
     tc_result *res_dev = nullptr;
     // pinned host
@@ -150,6 +151,11 @@ tc_status status_of_err(unsigned err)
 bool bad_p(double p) { return !(p > 0.0 && p <= 1.0); }
 
 uint64_t threshold_of(double p) { return (uint64_t)(p * 9007199254740992.0); }
+
+// Dense core of the top CORE_SIZE ranks for graphs of at least
+// CORE_MIN_EDGES edges, used by counts that keep about that many.
+constexpr uint32_t CORE_SIZE = 8192;
+constexpr double CORE_MIN_EDGES = 33554432.0;
 
 CountBuffers buffers_of(tc_graph *g)
 {
@@ -229,19 +235,23 @@ tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bo
 {
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
     const RowsArgs ra = rows_of(g, seed_mix, thr);
-    const CountBuffers b = buffers_of(g);
+    // the core block pays off once the sample is large: its cost is fixed,
+    // the intersections it replaces grow with the sample
+    const CoreBuffers *core = (g->core.hb.hcap && p * (double)g->m >= CORE_MIN_EDGES) ? &g->core : nullptr;
+    CountBuffers b = buffers_of(g);
+    if (core) b.core_base = core->base;
     record(g, timing, 0);
     enqueue_sample(g, ra);
     record(g, timing, 1);
     if (g->m > 0) {
         build_rows(ra, g->stream);
-        if (g->hb.hcap) heavy_prepare(b, g->hb, g->stream);
+        if (g->hb.hcap) heavy_prepare(b, g->hb, core, g->stream);
         build_items(b, g->stream);
     }
     record(g, timing, 2);
     if (g->m > 0) intersect(b, g->smem_bytes, g->stream);
     record(g, timing, 3);
-    if (g->m > 0 && g->hb.hcap) heavy_contract(b, g->hb, g->stream);
+    if (g->m > 0 && g->hb.hcap) heavy_contract(b, g->hb, core, g->stream);
     record(g, timing, 4);
     finalize(b, p, g->res_dev, g->stream);
     record(g, timing, 5);
@@ -452,6 +462,21 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
             if (g->hb.UT) g->release(g->hb.UT);
             g->hb.U = g->hb.UT = nullptr;
             g->hb.hcap = 0;
+        }
+    }
+    // dense core: the top CORE_SIZE ranks (2 x 128 MiB of bf16), with the heavy block
+    if (g->hb.hcap && (double)m >= CORE_MIN_EDGES && n >= 2 * CORE_SIZE) {
+        CoreBuffers &c = g->core;
+        const uint64_t bytes = (uint64_t)CORE_SIZE * CORE_SIZE * 2;
+        c.hb.U = (uint16_t *)g->alloc(bytes);
+        c.hb.UT = c.hb.U ? (uint16_t *)g->alloc(bytes) : nullptr;
+        c.hb.hcap = CORE_SIZE;
+        c.base = n - CORE_SIZE;
+        if (!c.hb.U || !c.hb.UT || !heavy_make_maps(c.hb)) {
+            if (c.hb.U) g->release(c.hb.U);
+            if (c.hb.UT) g->release(c.hb.UT);
+            c.hb.U = c.hb.UT = nullptr;
+            c.hb.hcap = 0;
         }
     }
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {

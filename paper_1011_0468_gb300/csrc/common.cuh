@@ -37,6 +37,11 @@ struct DevState {
     unsigned long long m_canon;    // canonical edges (create only)
     unsigned int unsorted;         // create: adjacent pairs out of order
     unsigned int light_lim;        // 1 + the largest light vertex with an edge (0: none); ids above are heavy
+    unsigned long long t_core;     // triangles inside the dense core (all three ids >= the core base)
+    unsigned int core_on;          // 1: the core block counts the triangles inside the core
+    unsigned int heavy_below;      // heavy vertices below the core base
+    unsigned int cursor_core;      // work cursor of the core contraction
+    unsigned int pad2;
 };
 
 // A batch of independent graphs laid out as one disjoint union: graph g owns

@@ -70,9 +70,13 @@ __global__ void k_finalize(const DevState *st, uint64_t m, uint32_t n, double p,
     out->m_sampled = st->m_sampled;
     out->n = n;
     out->n_heavy = st->n_heavy;
-    out->t_light = st->t_light;
+    // with the core block on, the triangles inside the core that have a light
+    // vertex are its count minus the all-heavy ones (every heavy vertex is in
+    // the core, so all of T_H lies inside it)
+    const unsigned long long t_light = st->t_light + (st->core_on ? st->t_core - st->t_heavy : 0ull);
+    out->t_light = t_light;
     out->t_heavy = st->t_heavy;
-    out->estimate = __dadd_rn(__ddiv_rn((double)st->t_light, p3), __ddiv_rn((double)st->t_heavy, p3));
+    out->estimate = __dadd_rn(__ddiv_rn((double)t_light, p3), __ddiv_rn((double)st->t_heavy, p3));
     out->src_elems = st->src_elems;
     out->nbr_elems = st->nbr_elems;
     out->partners = st->partners;

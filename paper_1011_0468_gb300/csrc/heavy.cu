@@ -26,8 +26,10 @@ namespace tcg {
 // Ranking and packing
 // ======================================================================
 
+// Lists the heavy vertices and counts those below core_base (the core
+// block needs every heavy vertex inside the core).
 __global__ void k_heavy_list(const uint8_t *__restrict__ heavy, uint32_t n, uint32_t *__restrict__ hlist,
-                             uint32_t hlist_cap, DevState *st)
+                             uint32_t hlist_cap, uint32_t core_base, DevState *st)
 {
     const unsigned lane = lane_id();
     const uint64_t wstride = (uint64_t)gridDim.x * blockDim.x;
@@ -42,6 +44,8 @@ __global__ void k_heavy_list(const uint8_t *__restrict__ heavy, uint32_t n, uint
             const uint32_t pos = off + __popc(mask & lanemask_lt());
             if (pos < hlist_cap) hlist[pos] = (uint32_t)u;
         }
+        const unsigned below = __ballot_sync(FULL, f && u < core_base);
+        if (lane == 0 && below) atomicAdd(&st->heavy_below, (unsigned)__popc(below));
     }
 }
 
@@ -53,12 +57,15 @@ constexpr int HR_THREADS = 256;
 // dense path runs: 2 <= h <= hcap.
 __global__ void __launch_bounds__(HR_THREADS) k_heavy_rank(const uint32_t *__restrict__ hlist,
                                                            uint32_t *__restrict__ hidx, uint32_t hcap,
-                                                           uint32_t hlist_cap, DevState *st)
+                                                           uint32_t hlist_cap, bool core, DevState *st)
 {
     __shared__ unsigned long long s_key[HR_THREADS];
     const uint32_t h = st->n_heavy;
     const bool dense = h >= 2 && h <= hcap && h <= hlist_cap && st->h_listed == h;
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->dense = dense ? 1u : 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->dense = dense ? 1u : 0u;
+        st->core_on = (core && dense && st->heavy_below == 0) ? 1u : 0u;
+    }
     if (!dense || blockIdx.x * HR_THREADS >= h) return;  // uniform per block
     const uint32_t i = blockIdx.x * HR_THREADS + threadIdx.x;
     unsigned long long mine = ~0ull;
@@ -113,6 +120,28 @@ __global__ void k_heavy_pack(const uint32_t *__restrict__ ptrp, const uint32_t *
             const uint32_t w = col[q];
             if (!heavy[w]) continue;  // an edge to a light vertex: not in U
             const uint32_t c = hidx[w];
+            if (r >= hcap || c >= hcap) continue;
+            U[(uint64_t)r * hcap + c] = ONE;
+            UT[(uint64_t)c * hcap + r] = ONE;
+        }
+    }
+}
+
+// One warp per core row v (ids base .. base + hcap - 1 that exist): U[v - base][w - base] =
+// U^T[w - base][v - base] = 1 for every out-neighbour w (all inside the core).
+__global__ void k_core_pack(const uint32_t *__restrict__ ptrp, const uint32_t *__restrict__ col, uint32_t n,
+                            uint32_t base, uint16_t *__restrict__ U, uint16_t *__restrict__ UT, uint32_t hcap,
+                            DevState *st)
+{
+    if (!st->core_on) return;
+    const unsigned lane = lane_id();
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    constexpr uint16_t ONE = 0x3f80;  // bf16 1.0
+    for (uint32_t v = base + gw; v < n; v += nw) {
+        const PaddedRow row = padded_row(ptrp, v);
+        const uint32_t r = v - base;
+        for (uint32_t q = row.beg + lane; q < row.beg + row.d; q += 32) {
+            const uint32_t c = col[q] - base;  // col[q] > v >= base
             if (r >= hcap || c >= hcap) continue;
             U[(uint64_t)r * hcap + c] = ONE;
             UT[(uint64_t)c * hcap + r] = ONE;
@@ -244,17 +273,27 @@ __device__ __forceinline__ void tile_of(uint32_t t, uint32_t T, uint32_t &I, uin
     K = t + o;
 }
 
+// One contraction: which matrix order, which tile cursor and which output
+// counter (the heavy block and the core block run the same kernel).
+struct DenseJob {
+    const unsigned *enable;      // runs iff *enable != 0
+    const unsigned *h_dev;       // matrix order on the device, or NULL: h_host
+    uint32_t h_host;
+    unsigned *cursor;            // tile work cursor (zero on entry)
+    unsigned long long *out;     // += sum_{i<k} U_ik (U U)_ik
+};
+
 __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constant__ CUtensorMap mapA,
                                                             const __grid_constant__ CUtensorMap mapB,
                                                             const uint16_t *__restrict__ U, uint32_t hcap,
-                                                            DevState *st)
+                                                            DenseJob job, DevState *st)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
     __shared__ uint32_t s_tmem, s_tile, s_abort;
     __shared__ unsigned long long s_sum[4];
-    if (!st->dense) return;  // uniform: written before this launch
-    const uint32_t h = st->n_heavy;
+    if (!*job.enable) return;  // uniform: written before this launch
+    const uint32_t h = job.h_dev ? *job.h_dev : job.h_host;
     const uint32_t T = (h + TC_TILE - 1) / TC_TILE, ntiles = T * (T + 1) / 2;
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -282,7 +321,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
     uint32_t it_prod = 0, it_mma = 0, tiles_done = 0;
     unsigned long long flops_k = 0;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&st->cursor[3], 1u);
+        if (threadIdx.x == 0) s_tile = atomicAdd(job.cursor, 1u);
         __syncthreads();
         const uint32_t t = s_tile;
         if (t >= ntiles || s_abort) break;
@@ -358,7 +397,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
         __syncthreads();  // TMEM is read: the next tile may overwrite it
         if (threadIdx.x == 0) {
             const unsigned long long tot = s_sum[0] + s_sum[1] + s_sum[2] + s_sum[3];
-            if (tot) atomicAdd(&st->t_heavy, tot);
+            if (tot) atomicAdd(job.out, tot);
         }
         ++tiles_done;
     }
@@ -414,27 +453,46 @@ bool heavy_make_maps(HeavyBuffers &hb)
     return true;
 }
 
-void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s)
+void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s)
 {
     if (hb.hcap == 0 || hb.hlist_cap == 0 || b.n == 0) return;  // no dense block: DevState::dense stays 0
-    k_heavy_list<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.heavy, b.n, hb.hlist, hb.hlist_cap, b.st);
+    const bool with_core = core && core->hb.hcap != 0;
+    k_heavy_list<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.heavy, b.n, hb.hlist, hb.hlist_cap,
+                                                             with_core ? core->base : 0u, b.st);
     note_launch();
-    k_heavy_rank<<<(unsigned)ceil_div(hb.hlist_cap, HR_THREADS), HR_THREADS, 0, s>>>(hb.hlist, hb.hidx,
-                                                                                   hb.hcap, hb.hlist_cap, b.st);
+    k_heavy_rank<<<(unsigned)ceil_div(hb.hlist_cap, HR_THREADS), HR_THREADS, 0, s>>>(hb.hlist, hb.hidx, hb.hcap,
+                                                                                   hb.hlist_cap, with_core, b.st);
     note_launch();
     k_heavy_clear<<<152 * 8, 256, 0, s>>>(hb.U, hb.UT, hb.hcap, b.st);
     note_launch();
     k_heavy_pack<<<152 * 4, 256, 0, s>>>(b.ptrp, b.col, b.heavy, hb.hlist, hb.hidx, hb.U, hb.UT, hb.hcap, b.st);
     note_launch();
+    if (with_core) {
+        const uint64_t bytes = (uint64_t)core->hb.hcap * core->hb.hcap * 2;
+        cudaMemsetAsync(core->hb.U, 0, bytes, s);
+        cudaMemsetAsync(core->hb.UT, 0, bytes, s);
+        k_core_pack<<<152 * 8, 256, 0, s>>>(b.ptrp, b.col, b.n, core->base, core->hb.U, core->hb.UT, core->hb.hcap,
+                                            b.st);
+        note_launch();
+    }
 }
 
-void heavy_contract(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s)
+void heavy_contract(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s)
 {
     cudaFuncSetAttribute(k_heavy_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     const CUtensorMap *ma = reinterpret_cast<const CUtensorMap *>(hb.mapA);
     const CUtensorMap *mb = reinterpret_cast<const CUtensorMap *>(hb.mapB);
-    k_heavy_tc<<<152, TC_THREADS, TC_SMEM, s>>>(*ma, *mb, hb.U, hb.hcap, b.st);
+    const DenseJob heavy_job{&b.st->dense, &b.st->n_heavy, 0, &b.st->cursor[3], &b.st->t_heavy};
+    k_heavy_tc<<<152, TC_THREADS, TC_SMEM, s>>>(*ma, *mb, hb.U, hb.hcap, heavy_job, b.st);
     note_launch();
+    if (core && core->hb.hcap != 0) {
+        const CUtensorMap *ca = reinterpret_cast<const CUtensorMap *>(core->hb.mapA);
+        const CUtensorMap *cb = reinterpret_cast<const CUtensorMap *>(core->hb.mapB);
+        const uint32_t order = std::min<uint32_t>(core->hb.hcap, b.n - core->base);
+        const DenseJob core_job{&b.st->core_on, nullptr, order, &b.st->cursor_core, &b.st->t_core};
+        k_heavy_tc<<<152, TC_THREADS, TC_SMEM, s>>>(*ca, *cb, core->hb.U, core->hb.hcap, core_job, b.st);
+        note_launch();
+    }
 }
 
 }  // namespace tcg

@@ -222,8 +222,9 @@ __device__ __forceinline__ void flush_tally(const Tally &t, unsigned long long *
 // Pair classes and what the kernels need to finish them.
 struct PairCtx {
     const uint8_t *heavy;
-    uint32_t lim;  // DevState::light_lim
-    bool dense;    // the tensor path counts the all-heavy triangles
+    uint32_t lim;      // DevState::light_lim
+    bool dense;        // the tensor path counts the all-heavy triangles
+    uint32_t core_lo;  // pairs whose lower endpoint is at or above this id are the core block's
 };
 
 // Partner y of owner x (out-degree d, heavy flag hx): the chunk range of the
@@ -239,13 +240,13 @@ __device__ __forceinline__ void partner_of(const uint32_t *__restrict__ ptrp, co
     const PaddedRow py = padded_row(ptrp, y);
     uint32_t len, b;
     if (is_out) {  // pair (x -> y)
-        len = (py.d >= 1 && py.d <= d) ? py.d : 0u;
+        len = (py.d >= 1 && py.d <= d && x < pc.core_lo) ? py.d : 0u;
         c0 = py.beg >> 2;
         nc = (len + 3) >> 2;
         b = y;
     } else {  // pair (y -> x): the entries of N+(y) after x
         const uint32_t end = py.beg + py.d;
-        len = (py.d >= 2 && py.d < d && qpos + 1 < end) ? end - qpos - 1 : 0u;
+        len = (py.d >= 2 && py.d < d && qpos + 1 < end && y < pc.core_lo) ? end - qpos - 1 : 0u;
         c0 = (qpos + 1) >> 2;
         nc = len ? ((end + 3) >> 2) - c0 : 0u;
         b = x;
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
                                                            const uint2 *__restrict__ inlist,
                                                            const uint64_t *__restrict__ items, uint64_t wm_cap,
                                                            const uint8_t *__restrict__ heavy, DevState *st,
-                                                           BatchView bv, IsectConfig cfg)
+                                                           BatchView bv, IsectConfig cfg, uint32_t core_base)
 {
     __shared__ uint2 s_tab[PW_WARPS][WTAB / 2];
     __shared__ uint32_t s_base[PW_WARPS][32];
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
     const unsigned upto = 0xffffffffu >> (31 - lane);
     const uint32_t nitems = (uint32_t)min((unsigned long long)st->nlist[0], (unsigned long long)wm_cap);
-    const PairCtx pc{heavy, st->light_lim, st->dense != 0};
+    const PairCtx pc{heavy, st->light_lim, st->dense != 0, st->core_on ? core_base : 0xffffffffu};
     const uint4 *col4 = reinterpret_cast<const uint4 *>(col);
     uint2 *tab = s_tab[w];
     const bool batch = bv.k != 0;
@@ -586,7 +587,8 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const u
                                                                       uint64_t wm_cap,
                                                                       const uint8_t *__restrict__ heavy,
                                                                       DevState *st, uint32_t tab_slots,
-                                                                      uint64_t cap, BatchView bv, IsectConfig cfg)
+                                                                      uint64_t cap, BatchView bv, IsectConfig cfg,
+                                                                      uint32_t core_base)
 {
     extern __shared__ uint2 tab[];
     __shared__ uint32_t s_c0[SEG_B];
@@ -598,7 +600,7 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const u
     const uint32_t b = DYN ? 2 : 1;
     const uint32_t nitems =
         (uint32_t)min((unsigned long long)st->nlist[b], (unsigned long long)(DYN ? cap - wm_cap : wm_cap));
-    const PairCtx pc{heavy, st->light_lim, st->dense != 0};
+    const PairCtx pc{heavy, st->light_lim, st->dense != 0, st->core_on ? core_base : 0xffffffffu};
     const uint4 *col4 = reinterpret_cast<const uint4 *>(col);
     Tally t;
     for (;;) {
@@ -712,14 +714,15 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
     const uint64_t wm = wm_capacity(b.n, b.m);
     intersect_prepare(dyn_smem_bytes);
     k_probe_warp<<<152 * 4, PW_THREADS, 0, s>>>(b.ptrp, b.col, b.inptr, b.inlist, b.items, wm, b.heavy, b.st, b.bv,
-                                                b.cfg);
+                                                b.cfg, b.core_base);
     note_launch();
     k_probe_block<false><<<152 * 4, PB_THREADS, MID_TAB * 4, s>>>(b.ptrp, b.col, b.inptr, b.inlist, b.items, wm,
-                                                                   b.heavy, b.st, MID_TAB, b.items_cap, b.bv, b.cfg);
+                                                                   b.heavy, b.st, MID_TAB, b.items_cap, b.bv, b.cfg,
+                                                                   b.core_base);
     note_launch();
     k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.ptrp, b.col, b.inptr, b.inlist, b.items, wm,
                                                                 b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
-                                                                b.items_cap, b.bv, b.cfg);
+                                                                b.items_cap, b.bv, b.cfg, b.core_base);
     note_launch();
 }
 

@@ -166,6 +166,7 @@ struct CountBuffers {
     DevState *st;
     BatchView bv;           // k > 0: the graph is a batch union
     IsectConfig cfg;        // intersection schedule
+    uint32_t core_base = 0xffffffffu;  // base of the dense core of this count (see CoreBuffers), or none
 };
 
 void partition(const CountBuffers &b, cudaStream_t s);
@@ -228,9 +229,21 @@ struct HeavyBuffers {
 };
 
 bool heavy_make_maps(HeavyBuffers &hb);
-// after the CSR: list, rank and pack the heavy vertices; sets DevState::dense
-void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s);
-// T_H += sum_{i<k} U_ik (U U)_ik on tcgen05 (no-op unless DevState::dense)
-void heavy_contract(const CountBuffers &b, const HeavyBuffers &hb, cudaStream_t s);
+// The dense core: the vertices with the top `hcap` ids (ranks), base = n -
+// hcap; U is their strictly upper 0/1 matrix, U[v - base][w - base] = 1 for
+// every kept edge v -> w inside the core.  Every triangle whose lowest
+// vertex is in the core lies in the core, so when the core block runs
+// (DevState::core_on) the intersection kernels skip the pairs whose lower
+// endpoint is in it and the contraction counts those triangles (t_core).
+struct CoreBuffers {
+    HeavyBuffers hb;  // hlist / hidx unused; hcap = core size
+    uint32_t base = 0;
+};
+// after the CSR: list, rank and pack the heavy vertices; sets DevState::dense,
+// and DevState::core_on when core (may be NULL) is to run for this count
+void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s);
+// T_H += sum_{i<k} U_ik (U U)_ik on tcgen05 (no-op unless DevState::dense),
+// and t_core likewise over the core matrix when DevState::core_on
+void heavy_contract(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s);
 
 }  // namespace tcg
