@@ -121,6 +121,7 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
     u.keepw = (uint32_t *)dev_alloc_track(allocs, bytes, (m1 + 31) / 32 * 4);
     u.tile_cnt = (uint32_t *)dev_alloc_track(allocs, bytes, (ceil_div(m1, RX_TILE) + 1) * 4);
     u.spread = (uint32_t *)dev_alloc_track(allocs, bytes, hot_size(n_cap) * 4);
+    u.inend = (uint32_t *)dev_alloc_track(allocs, bytes, (uint64_t)n_cap * 4);
     u.deg = (uint32_t *)dev_alloc_track(allocs, bytes, (uint64_t)n_cap * 4);
     u.rowptr = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)n_cap + 1) * 4);
     u.inptr = (uint32_t *)dev_alloc_track(allocs, bytes, ((uint64_t)n_cap + 2) * 4);
@@ -146,7 +147,7 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     u.smem_bytes = (int)(slots * 4);
     intersect_prepare(u.smem_bytes);
-    return u.rel && u.orig && u.inlist && u.keepw && u.tile_cnt && u.spread && u.deg && u.rowptr && u.inptr && u.colp &&
+    return u.rel && u.orig && u.inlist && u.keepw && u.tile_cnt && u.spread && u.inend && u.deg && u.rowptr && u.inptr && u.colp &&
            u.ptrp && u.heavy && u.items && u.hist && u.scan &&
            u.st && u.eoff && u.voff && u.thr && u.seed_mix && u.p && u.counters && u.res_dev;
 }
@@ -165,6 +166,7 @@ void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const Isec
     cb.col = u.colp;
     cb.ptrp = u.ptrp;
     cb.inptr = u.inptr;
+    cb.inend = u.inend;
     cb.inlist = u.inlist;
     cb.items = u.items;
     cb.items_cap = items_capacity(n, std::max<uint64_t>(m, 1));
@@ -182,6 +184,7 @@ void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const Isec
     ra.deg = u.deg;
     ra.rowptr = u.rowptr;
     ra.inptr = u.inptr;
+    ra.inend = u.inend;
     ra.ptrp = u.ptrp;
     ra.colp = u.colp;
     ra.inlist = u.inlist;

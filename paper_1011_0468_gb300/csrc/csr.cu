@@ -226,8 +226,9 @@ void sample_rows(const RowsArgs &a, cudaStream_t s)
 __device__ __forceinline__ uint32_t pad_of(uint32_t d) { return (4u - (d & 3u)) & 3u; }
 
 // dplus holds the kept out-degrees: ptrp[x] = pad count of row x and
-// P[x] = in-degree deg - d+ of x (x < n); ptrp[n] = P[n] = 0.
-__global__ void k_row_counts(const uint32_t *__restrict__ dplus, const uint32_t *__restrict__ deg, uint32_t n,
+// P[x] = in-degree deg - d+ of x (x < n), the room of x's in-list; ptrp[n]
+// = P[n] = 0.  deg[x] is replaced by d+ (the partition has used it).
+__global__ void k_row_counts(const uint32_t *__restrict__ dplus, uint32_t *__restrict__ deg, uint32_t n,
                              uint32_t *__restrict__ ptrp, uint32_t *__restrict__ P)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -235,6 +236,7 @@ __global__ void k_row_counts(const uint32_t *__restrict__ dplus, const uint32_t 
         const uint32_t dp = x < n ? dplus[x] : 0u;
         ptrp[x] = pad_of(dp);
         P[x] = x < n ? deg[x] - dp : 0u;
+        if (x < n) deg[x] = dp;
     }
 }
 
@@ -249,11 +251,14 @@ __global__ void k_cursors(const uint32_t *__restrict__ P, uint32_t n, int hbits,
 // Writes every kept edge (u -> v) at its place in the padded rows (its
 // index among the kept edges, which is its CSR position, plus the padding
 // before row u) and appends (u, that position) to v's in-list (cursors at
-// hot_index).
+// hot_index) when v is the pair's owner and u's row goes on past v: 2 <=
+// d+(u) < d+(v) (dplus).
 __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict__ rel, uint64_t m,
                                                       const uint32_t *__restrict__ keepw,
                                                       const uint32_t *__restrict__ tile_off,
                                                       const uint32_t *__restrict__ padoff,
+                                                      const uint32_t *__restrict__ rowptr,
+                                                      const uint32_t *__restrict__ dplus,
                                                       uint32_t *__restrict__ colp, uint32_t *__restrict__ cursor,
                                                       int hbits, uint2 *__restrict__ inlist)
 {
@@ -284,19 +289,25 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
             const uint64_t i = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
             const uint64_t r = ld_stream_u64(rel + i);
             const uint32_t u = (uint32_t)(r >> 32), v = (uint32_t)r;
-            const uint32_t pos = base + s_pre[wi] + __popc(word & lt) + __ldg(padoff + u);
+            const uint32_t k = base + s_pre[wi] + __popc(word & lt);  // CSR position
+            const uint32_t pos = k + __ldg(padoff + u);
             colp[pos] = v;
-            const uint32_t q = atomicAdd(cursor + hot_index(v, hbits), 1u);
-            inlist[q] = make_uint2(u, pos);
+            const uint32_t du = __ldg(dplus + u);
+            if (du >= 2 && k + 1 < __ldg(rowptr + u + 1) && du < __ldg(dplus + v)) {
+                const uint32_t q = atomicAdd(cursor + hot_index(v, hbits), 1u);
+                inlist[q] = make_uint2(u, pos);
+            }
         }
         __syncthreads();  // s_word / s_pre are rewritten for the next tile
     }
 }
 
 // Row x's padding (SENT) and ptrp[x] = padded start | pad count; ptrp holds
-// the exclusive scan of the pad counts and rowptr the row offsets.
+// the exclusive scan of the pad counts and rowptr the row offsets.  Also the
+// end of x's in-list (its cursor at hot_index) into inend[x].
 __global__ void k_pad_finish(const uint32_t *__restrict__ rowptr, uint32_t n, uint32_t *__restrict__ ptrp,
-                             uint32_t *__restrict__ colp)
+                             uint32_t *__restrict__ colp, const uint32_t *__restrict__ cursor, int hbits,
+                             uint32_t *__restrict__ inend)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
@@ -305,6 +316,7 @@ __global__ void k_pad_finish(const uint32_t *__restrict__ rowptr, uint32_t n, ui
             ptrp[x] = start;
             continue;
         }
+        inend[x] = cursor[hot_index((uint32_t)x, hbits)];
         const uint32_t d = rowptr[x + 1] - rowptr[x], pad = pad_of(d);
         for (uint32_t i = 0; i < pad; ++i) colp[start + d + i] = SENT;
         ptrp[x] = start | pad;
@@ -323,13 +335,17 @@ void build_rows(const RowsArgs &a, cudaStream_t s)
     if (a.m > 0) {
         const uint64_t nt = ceil_div(a.m, RX_TILE);
         scan_excl_u32(a.tile_cnt, nt, nullptr, a.scan, s);
-        k_cursors<<<grid_for(a.n, 256, 152 * 8), 256, 0, s>>>(a.inptr, a.n, hb, a.spread);
-        note_launch();
-        k_rows_scatter<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.m, a.keepw, a.tile_cnt, a.ptrp, a.colp,
-                                                                  a.spread, hb, a.inlist);
+    }
+    k_cursors<<<grid_for(a.n, 256, 152 * 8), 256, 0, s>>>(a.inptr, a.n, hb, a.spread);
+    note_launch();
+    if (a.m > 0) {
+        const uint64_t nt = ceil_div(a.m, RX_TILE);
+        k_rows_scatter<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.m, a.keepw, a.tile_cnt, a.ptrp, a.rowptr,
+                                                                  a.deg, a.colp, a.spread, hb,
+                                                                  a.inlist);
         note_launch();
     }
-    k_pad_finish<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp, a.colp);
+    k_pad_finish<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp, a.colp, a.spread, hb, a.inend);
     note_launch();
 }
 

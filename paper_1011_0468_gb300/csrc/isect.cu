@@ -74,7 +74,8 @@ __device__ __forceinline__ void split_item(uint64_t item, bool batch, uint32_t &
     g = batch ? (uint32_t)(item >> 48) : 0u;
 }
 
-__global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ inptr, uint32_t n,
+__global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ inptr,
+                        const uint32_t *__restrict__ inend, uint32_t n,
                         uint64_t *__restrict__ items, uint64_t wm_cap, uint64_t cap, DevState *st, BatchView bv,
                         IsectConfig cfg)
 {
@@ -86,7 +87,7 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
         uint32_t d = 0, np = 0;
         if (x < n) {
             d = rowptr[x + 1] - rowptr[x];
-            if (d >= 2) np = d + (inptr[x + 1] - inptr[x]);
+            if (d >= 2) np = d + (inend[x] - inptr[x]);
         }
         const uint32_t gx = batch ? find_part_warp(bv.voff, bv.k, (uint32_t)(x < n ? x : n - 1)) : 0u;
         const uint32_t b = bucket_of(d, cfg.warp_max), seg = seg_len(d, b, cfg);
@@ -118,7 +119,7 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
 void build_items(const CountBuffers &b, cudaStream_t s)
 {
     const uint64_t wm = wm_capacity(b.n, b.m);
-    k_items<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.inptr, b.n, b.items, wm, b.items_cap, b.st,
+    k_items<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.inptr, b.inend, b.n, b.items, wm, b.items_cap, b.st,
                                                           b.bv, b.cfg);
     note_launch();
 }
@@ -370,6 +371,7 @@ constexpr uint32_t WTAB = 1024;  // per-warp table slots, >= 4 * WARP_MAX
 __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__restrict__ ptrp,
                                                            const uint32_t *__restrict__ col,
                                                            const uint32_t *__restrict__ inptr,
+                                                           const uint32_t *__restrict__ inend,
                                                            const uint2 *__restrict__ inlist,
                                                            const uint64_t *__restrict__ items, uint64_t wm_cap,
                                                            const uint8_t *__restrict__ heavy, DevState *st,
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
             if (slots && d >= 2) {
                 hx = heavy[x];
                 ib = inptr[x];
-                const uint32_t np = d + (inptr[x + 1] - ib);
+                const uint32_t np = d + (inend[x] - ib);
                 const uint32_t sl = seg_len(d, 0, cfg);
                 p0 = seg * sl;
                 npart = np > p0 ? min(np - p0, sl) : 0u;
@@ -582,6 +584,7 @@ template <bool DYN>
 __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const uint32_t *__restrict__ ptrp,
                                                                       const uint32_t *__restrict__ col,
                                                                       const uint32_t *__restrict__ inptr,
+                                                                      const uint32_t *__restrict__ inend,
                                                                       const uint2 *__restrict__ inlist,
                                                                       const uint64_t *__restrict__ items,
                                                                       uint64_t wm_cap,
@@ -625,7 +628,7 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const u
                 bucket_insert(tab, set.mask, set.shift, __ldg(col + row.beg + i));
         }
         if (seg == 0 && threadIdx.x == 0) t.table += d;
-        const uint32_t ib = inptr[x], np = d + (inptr[x + 1] - ib);
+        const uint32_t ib = inptr[x], np = d + (inend[x] - ib);
         const uint32_t sl = seg_len(d, 1, cfg);
         const uint32_t p0 = seg * sl, p1 = min(np, p0 + sl);
         const uint32_t per = sl / PB_THREADS;  // <= PB_PER_THREAD
@@ -713,14 +716,14 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
     if (b.n == 0 || b.m == 0) return;
     const uint64_t wm = wm_capacity(b.n, b.m);
     intersect_prepare(dyn_smem_bytes);
-    k_probe_warp<<<152 * 4, PW_THREADS, 0, s>>>(b.ptrp, b.col, b.inptr, b.inlist, b.items, wm, b.heavy, b.st, b.bv,
+    k_probe_warp<<<152 * 4, PW_THREADS, 0, s>>>(b.ptrp, b.col, b.inptr, b.inend, b.inlist, b.items, wm, b.heavy, b.st, b.bv,
                                                 b.cfg, b.core_base);
     note_launch();
-    k_probe_block<false><<<152 * 4, PB_THREADS, MID_TAB * 4, s>>>(b.ptrp, b.col, b.inptr, b.inlist, b.items, wm,
+    k_probe_block<false><<<152 * 4, PB_THREADS, MID_TAB * 4, s>>>(b.ptrp, b.col, b.inptr, b.inend, b.inlist, b.items, wm,
                                                                    b.heavy, b.st, MID_TAB, b.items_cap, b.bv, b.cfg,
                                                                    b.core_base);
     note_launch();
-    k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.ptrp, b.col, b.inptr, b.inlist, b.items, wm,
+    k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.ptrp, b.col, b.inptr, b.inend, b.inlist, b.items, wm,
                                                                 b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
                                                                 b.items_cap, b.bv, b.cfg, b.core_base);
     note_launch();

@@ -101,7 +101,8 @@ struct RowsArgs {
     BatchView bv;                // batch union (bv.k > 0)
     uint32_t *deg;               // [n] sampled degrees
     uint32_t *rowptr;            // [n + 1] kept out-degrees, then row offsets
-    uint32_t *inptr;             // [n + 1] in-list offsets (in-list of v: inlist[inptr[v] .. inptr[v + 1]))
+    uint32_t *inptr;             // [n + 1] in-list starts
+    uint32_t *inend;             // [n] in-list ends: the in-list of v is inlist[inptr[v] .. inend[v])
     uint32_t *ptrp;              // [n + 2] padded row pointers (see SENT)
     uint32_t *colp;              // [colp_capacity(n, m)] padded columns
     uint2 *inlist;               // [m] in-list entries (source, padded position of the edge in its row)
@@ -159,7 +160,8 @@ struct CountBuffers {
     uint32_t *rowptr;       // [n + 1]
     uint32_t *col;          // padded CSR columns (see SENT / ptrp)
     uint32_t *ptrp;         // [n + 2] padded row pointers
-    uint32_t *inptr;        // [n + 2] in-list offsets
+    uint32_t *inptr;        // [n + 1] in-list starts
+    uint32_t *inend;        // [n] in-list ends
     const uint2 *inlist;    // in-list entries (source, padded position of the edge)
     uint64_t *items;        // owner work items [items_cap]
     uint64_t items_cap;
@@ -194,6 +196,7 @@ struct UnionScratch {
     uint64_t items_cap = 0;
     uint32_t *deg = nullptr, *rowptr = nullptr, *inptr = nullptr, *hist = nullptr, *scan = nullptr;
     uint32_t *colp = nullptr, *ptrp = nullptr, *keepw = nullptr, *tile_cnt = nullptr, *spread = nullptr;
+    uint32_t *inend = nullptr;
     uint8_t *heavy = nullptr;
     DevState *st = nullptr;
     uint64_t *eoff = nullptr, *thr = nullptr, *seed_mix = nullptr;

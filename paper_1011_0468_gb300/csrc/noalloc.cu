@@ -33,7 +33,7 @@ constexpr uint64_t NA_ITEMS = NA_N + 2 * NA_M / SEG_MIN + NA_M / 1024 + 2 * NA_M
 constexpr uint64_t NA_COLP = NA_M + 3 * NA_M + 4;  // >= colp_capacity(N, M)
 static_assert(NA_N <= NA_M, "the vertex sort reuses the key buffers");
 constexpr uint64_t NA_BYTES = 4 * na_round(8 * NA_M)                     // ekey (then rel), orig, bufA, bufB
-                              + 3 * na_round(4 * NA_N)                   // perm, rank, spread
+                              + 4 * na_round(4 * NA_N)                   // perm, rank, spread, inend
                               + na_round(4 * (NA_M / 32 + 1)) + na_round(4 * (NA_TILES + 1))  // keepw, tile_cnt
                               + na_round(4 * NA_HIST) + na_round(4 * NA_SCAN)
                               + 2 * na_round(4 * (NA_N + 2))             // deg, rowptr
@@ -115,6 +115,7 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     uint32_t *perm = c.take<uint32_t>(NA_N);
     uint32_t *rank = c.take<uint32_t>(NA_N);
     uint32_t *spread = c.take<uint32_t>(NA_N);  // hot_size(n) <= NA_N
+    uint32_t *inend = c.take<uint32_t>(NA_N);
     uint32_t *keepw = c.take<uint32_t>(NA_M / 32 + 1);
     uint32_t *tile_cnt = c.take<uint32_t>(NA_TILES + 1);
     uint64_t *bufA = c.take<uint64_t>(NA_M);
@@ -178,6 +179,7 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     cb.col = colp;
     cb.ptrp = ptrp;
     cb.inptr = inptr;
+    cb.inend = inend;
     cb.inlist = reinterpret_cast<uint2 *>(bufA);
     cb.items = items;
     cb.items_cap = items_capacity(n, m);
@@ -192,6 +194,7 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     ra.deg = deg;
     ra.rowptr = rowptr;
     ra.inptr = inptr;
+    ra.inend = inend;
     ra.ptrp = ptrp;
     ra.colp = colp;
     ra.inlist = reinterpret_cast<uint2 *>(bufA);
