@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
     uint2 *tab = s_tab[w];
     const bool batch = bv.k != 0;
     uint32_t cur_g = 0;  // graph whose counts this warp holds (batch)
+    uint32_t table_of = 0xffffffffu;  // owner whose set the table holds (single-item packs), else ~0
     Tally t;
     for (;;) {
         uint32_t first = 0;
@@ -450,9 +451,14 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
                 flush_graph_counts(t, bv, cur_g);
                 cur_g = ga;
             }
-            for (uint32_t i = lane; i < total_buckets; i += 32) tab[i] = make_uint2(EMPTY, EMPTY);
+            // consecutive segments of one owner reuse its set
+            const uint32_t xa = __shfl_sync(FULL, s_x[w][lane], a);
+            const bool reuse = b == a + 1 && xa == table_of;
+            table_of = b == a + 1 ? xa : 0xffffffffu;
+            if (!reuse)
+                for (uint32_t i = lane; i < total_buckets; i += 32) tab[i] = make_uint2(EMPTY, EMPTY);
             // insert the pack's out-lists, one entry per lane per step
-            {
+            if (!reuse) {
                 const uint32_t c = in_pack ? d : 0u;
                 const uint32_t ic = warp_incl_scan(c), tot = __shfl_sync(FULL, ic, 31);
                 s_pre[w][lane] = ic - c;
