@@ -85,6 +85,8 @@ struct tc_graph {
     uint32_t *inptr = nullptr;  // [n + 2] in-list starts
     uint32_t *inend = nullptr;  // [n] in-list ends
     uint2 *inlist = nullptr;    // [m] in-list entries
+    uint32_t *olist = nullptr;  // [m] out-lists
+    uint32_t *ocnt = nullptr;   // [n] out-list lengths
     uint32_t *colp = nullptr;   // [colp_capacity(n, m)] rows padded to 16 bytes
     uint32_t *ptrp = nullptr;   // [n + 2] padded row pointers
     uint32_t *keepw = nullptr;  // [ceil(m / 32)] keep bits
@@ -172,6 +174,8 @@ CountBuffers buffers_of(tc_graph *g)
     b.inptr = g->inptr;
     b.inend = g->inend;
     b.inlist = g->inlist;
+    b.olist = g->olist;
+    b.ocnt = g->ocnt;
     b.items = g->items;
     b.items_cap = g->items_cap;
     b.st = g->st;
@@ -194,6 +198,8 @@ RowsArgs rows_of(tc_graph *g, uint64_t seed_mix, uint64_t thr)
     a.ptrp = g->ptrp;
     a.colp = g->colp;
     a.inlist = g->inlist;
+    a.olist = g->olist;
+    a.ocnt = g->ocnt;
     a.keepw = g->keepw;
     a.tile_cnt = g->tile_cnt;
     a.scan = g->scan;
@@ -424,6 +430,8 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     g->heavy = (uint8_t *)g->alloc((uint64_t)n);
     g->inptr = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
     g->inend = (uint32_t *)g->alloc((uint64_t)n * 4);
+    g->olist = (uint32_t *)g->alloc(m1 * 4);
+    g->ocnt = (uint32_t *)g->alloc((uint64_t)n * 4);
     g->colp = (uint32_t *)g->alloc(colp_capacity(n, m) * 4);
     g->ptrp = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
     g->keepw = (uint32_t *)g->alloc((m1 + 31) / 32 * 4);
@@ -431,7 +439,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     g->spread = (uint32_t *)g->alloc(hot_size(n) * 4);
     g->items_cap = items_capacity(n, m);
     g->items = (uint64_t *)g->alloc(g->items_cap * 8);
-    if (!g->rowptr || !g->heavy || !g->inptr || !g->inend || !g->colp || !g->ptrp || !g->keepw || !g->tile_cnt || !g->spread ||
+    if (!g->rowptr || !g->heavy || !g->inptr || !g->inend || !g->olist || !g->ocnt || !g->colp || !g->ptrp || !g->keepw || !g->tile_cnt || !g->spread ||
         !g->items) {
         free_graph(g);
         return TC_ENOMEM;

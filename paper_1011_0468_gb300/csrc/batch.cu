@@ -118,6 +118,8 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
     u.rel = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
     u.orig = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
     u.inlist = (uint2 *)dev_alloc_track(allocs, bytes, m1 * 8);
+    u.olist = (uint32_t *)dev_alloc_track(allocs, bytes, m1 * 4);
+    u.ocnt = (uint32_t *)dev_alloc_track(allocs, bytes, (uint64_t)n_cap * 4);
     u.keepw = (uint32_t *)dev_alloc_track(allocs, bytes, (m1 + 31) / 32 * 4);
     u.tile_cnt = (uint32_t *)dev_alloc_track(allocs, bytes, (ceil_div(m1, RX_TILE) + 1) * 4);
     u.spread = (uint32_t *)dev_alloc_track(allocs, bytes, hot_size(n_cap) * 4);
@@ -147,7 +149,7 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     u.smem_bytes = (int)(slots * 4);
     intersect_prepare(u.smem_bytes);
-    return u.rel && u.orig && u.inlist && u.keepw && u.tile_cnt && u.spread && u.inend && u.deg && u.rowptr && u.inptr && u.colp &&
+    return u.rel && u.orig && u.inlist && u.olist && u.ocnt && u.keepw && u.tile_cnt && u.spread && u.inend && u.deg && u.rowptr && u.inptr && u.colp &&
            u.ptrp && u.heavy && u.items && u.hist && u.scan &&
            u.st && u.eoff && u.voff && u.thr && u.seed_mix && u.p && u.counters && u.res_dev;
 }
@@ -168,6 +170,8 @@ void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const Isec
     cb.inptr = u.inptr;
     cb.inend = u.inend;
     cb.inlist = u.inlist;
+    cb.olist = u.olist;
+    cb.ocnt = u.ocnt;
     cb.items = u.items;
     cb.items_cap = items_capacity(n, std::max<uint64_t>(m, 1));
     cb.st = u.st;
@@ -188,6 +192,8 @@ void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const Isec
     ra.ptrp = u.ptrp;
     ra.colp = u.colp;
     ra.inlist = u.inlist;
+    ra.olist = u.olist;
+    ra.ocnt = u.ocnt;
     ra.keepw = u.keepw;
     ra.tile_cnt = u.tile_cnt;
     ra.scan = u.scan;

@@ -229,14 +229,17 @@ __device__ __forceinline__ uint32_t pad_of(uint32_t d) { return (4u - (d & 3u)) 
 // P[x] = in-degree deg - d+ of x (x < n), the room of x's in-list; ptrp[n]
 // = P[n] = 0.  deg[x] is replaced by d+ (the partition has used it).
 __global__ void k_row_counts(const uint32_t *__restrict__ dplus, uint32_t *__restrict__ deg, uint32_t n,
-                             uint32_t *__restrict__ ptrp, uint32_t *__restrict__ P)
+                             uint32_t *__restrict__ ptrp, uint32_t *__restrict__ P, uint32_t *__restrict__ ocnt)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
         const uint32_t dp = x < n ? dplus[x] : 0u;
         ptrp[x] = pad_of(dp);
         P[x] = x < n ? deg[x] - dp : 0u;
-        if (x < n) deg[x] = dp;
+        if (x < n) {
+            deg[x] = dp;
+            ocnt[x] = 0;
+        }
     }
 }
 
@@ -250,9 +253,11 @@ __global__ void k_cursors(const uint32_t *__restrict__ P, uint32_t n, int hbits,
 
 // Writes every kept edge (u -> v) at its place in the padded rows (its
 // index among the kept edges, which is its CSR position, plus the padding
-// before row u) and appends (u, that position) to v's in-list (cursors at
-// hot_index) when v is the pair's owner and u's row goes on past v: 2 <=
-// d+(u) < d+(v) (dplus).
+// before row u) and, when u's row goes on past v (else the pair closes no
+// triangle), hands the pair to its owner (isect.cu): to v's in-list as (u,
+// that position) if d+(u) < d+(v) (cursors at hot_index), else, if d+(v) >=
+// 1, to u's out-list (ocnt: per-row counts, one atomic per run of u in a
+// warp).  Within a list the order is that of the atomics.
 __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict__ rel, uint64_t m,
                                                       const uint32_t *__restrict__ keepw,
                                                       const uint32_t *__restrict__ tile_off,
@@ -260,7 +265,8 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
                                                       const uint32_t *__restrict__ rowptr,
                                                       const uint32_t *__restrict__ dplus,
                                                       uint32_t *__restrict__ colp, uint32_t *__restrict__ cursor,
-                                                      int hbits, uint2 *__restrict__ inlist)
+                                                      int hbits, uint2 *__restrict__ inlist,
+                                                      uint32_t *__restrict__ olist, uint32_t *__restrict__ ocnt)
 {
     constexpr int WORDS = RX_TILE / 32;  // 128 keep words per tile
     __shared__ uint32_t s_word[WORDS], s_pre[WORDS];
@@ -285,17 +291,34 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
         for (int j = 0; j < RX_ITEMS; ++j) {
             const uint32_t wi = j * 8 + warp;  // word of this warp's 32 edges
             const uint32_t word = s_word[wi];
-            if (!((word >> lane) & 1u)) continue;
-            const uint64_t i = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
-            const uint64_t r = ld_stream_u64(rel + i);
-            const uint32_t u = (uint32_t)(r >> 32), v = (uint32_t)r;
-            const uint32_t k = base + s_pre[wi] + __popc(word & lt);  // CSR position
-            const uint32_t pos = k + __ldg(padoff + u);
-            colp[pos] = v;
-            const uint32_t du = __ldg(dplus + u);
-            if (du >= 2 && k + 1 < __ldg(rowptr + u + 1) && du < __ldg(dplus + v)) {
-                const uint32_t q = atomicAdd(cursor + hot_index(v, hbits), 1u);
-                inlist[q] = make_uint2(u, pos);
+            uint32_t u = 0, v = 0, k = 0;
+            bool out = false;
+            if ((word >> lane) & 1u) {
+                const uint64_t i = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
+                const uint64_t r = ld_stream_u64(rel + i);
+                u = (uint32_t)(r >> 32);
+                v = (uint32_t)r;
+                k = base + s_pre[wi] + __popc(word & lt);  // CSR position
+                const uint32_t pos = k + __ldg(padoff + u);
+                colp[pos] = v;
+                if (k + 1 < __ldg(rowptr + u + 1)) {  // so d+(u) >= 2
+                    const uint32_t du = __ldg(dplus + u), dv = __ldg(dplus + v);
+                    if (du < dv) {
+                        const uint32_t q = atomicAdd(cursor + hot_index(v, hbits), 1u);
+                        inlist[q] = make_uint2(u, pos);
+                    } else {
+                        out = dv >= 1;
+                    }
+                }
+            }
+            const unsigned act = __ballot_sync(FULL, out);
+            if (out) {
+                const unsigned grp = __match_any_sync(act, u);  // lanes of this warp with the same row
+                const int lead = __ffs(grp) - 1;
+                uint32_t q = 0;
+                if ((int)lane == lead) q = atomicAdd(ocnt + u, (unsigned)__popc(grp));
+                q = __shfl_sync(grp, q, lead) + __popc(grp & lt);
+                olist[__ldg(rowptr + u) + q] = v;
             }
         }
         __syncthreads();  // s_word / s_pre are rewritten for the next tile
@@ -327,7 +350,7 @@ void build_rows(const RowsArgs &a, cudaStream_t s)
 {
     const uint64_t n1 = (uint64_t)a.n + 1;
     const int hb = hot_bits(a.n);
-    k_row_counts<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.deg, a.n, a.ptrp, a.inptr);
+    k_row_counts<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.deg, a.n, a.ptrp, a.inptr, a.ocnt);
     note_launch();
     scan_excl_u32(a.ptrp, n1, nullptr, a.scan, s);
     scan_excl_u32(a.inptr, n1, nullptr, a.scan, s);
@@ -342,7 +365,7 @@ void build_rows(const RowsArgs &a, cudaStream_t s)
         const uint64_t nt = ceil_div(a.m, RX_TILE);
         k_rows_scatter<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.m, a.keepw, a.tile_cnt, a.ptrp, a.rowptr,
                                                                   a.deg, a.colp, a.spread, hb,
-                                                                  a.inlist);
+                                                                  a.inlist, a.olist, a.ocnt);
         note_launch();
     }
     k_pad_finish<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp, a.colp, a.spread, hb, a.inend);

@@ -16,10 +16,12 @@
 //   owner x, partner u in in-list(x), d+(u) < d+(x): stream the part of
 //     N+(u) ranked above x (rows are sorted by rank and the in-list entry
 //     holds the position of x in N+(u))
-// so each pair reads at most min(d+(a), d+(b)) entries.
+// so each pair reads at most min(d+(a), d+(b)) entries.  The compaction
+// (csr.cu) hands every pair that can close a triangle to its owner: the
+// out-list of x holds its out-partners, the in-list its in-partners.
 //
 // Work items are (segment << 32 | owner); a segment is a run of the owner's
-// partner sequence (its d+(x) out-neighbours, then its in-list).  Owners
+// partner sequence (its out-list, then its in-list).  Owners
 // are bucketed by d+(x), which sizes their hash set: 2..256 (one warp per
 // item), 257..1024 (one block, 8192-slot table), > 1024 (one block, larger
 // table, or a binary search of the sorted row when even that is too
@@ -75,7 +77,7 @@ __device__ __forceinline__ void split_item(uint64_t item, bool batch, uint32_t &
 }
 
 __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__restrict__ inptr,
-                        const uint32_t *__restrict__ inend, uint32_t n,
+                        const uint32_t *__restrict__ inend, const uint32_t *__restrict__ ocnt, uint32_t n,
                         uint64_t *__restrict__ items, uint64_t wm_cap, uint64_t cap, DevState *st, BatchView bv,
                         IsectConfig cfg)
 {
@@ -87,7 +89,7 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
         uint32_t d = 0, np = 0;
         if (x < n) {
             d = rowptr[x + 1] - rowptr[x];
-            if (d >= 2) np = d + (inend[x] - inptr[x]);
+            if (d >= 2) np = ocnt[x] + (inend[x] - inptr[x]);
         }
         const uint32_t gx = batch ? find_part_warp(bv.voff, bv.k, (uint32_t)(x < n ? x : n - 1)) : 0u;
         const uint32_t b = bucket_of(d, cfg.warp_max), seg = seg_len(d, b, cfg);
@@ -119,8 +121,8 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
 void build_items(const CountBuffers &b, cudaStream_t s)
 {
     const uint64_t wm = wm_capacity(b.n, b.m);
-    k_items<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.inptr, b.inend, b.n, b.items, wm, b.items_cap, b.st,
-                                                          b.bv, b.cfg);
+    k_items<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.inptr, b.inend, b.ocnt, b.n, b.items, wm, b.items_cap,
+                                                          b.st, b.bv, b.cfg);
     note_launch();
 }
 
@@ -370,6 +372,9 @@ constexpr uint32_t WTAB = 1024;  // per-warp table slots, >= 4 * WARP_MAX
 // the same number of partners and list entries costs.
 __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__restrict__ ptrp,
                                                            const uint32_t *__restrict__ col,
+                                                           const uint32_t *__restrict__ rowptr,
+                                                           const uint32_t *__restrict__ olist,
+                                                           const uint32_t *__restrict__ ocnt,
                                                            const uint32_t *__restrict__ inptr,
                                                            const uint32_t *__restrict__ inend,
                                                            const uint2 *__restrict__ inlist,
@@ -380,10 +385,11 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
     __shared__ uint2 s_tab[PW_WARPS][WTAB / 2];
     __shared__ uint32_t s_base[PW_WARPS][32];
     __shared__ uint32_t s_tinfo[PW_WARPS][32];
-    // the 32 items of the current grab, by lane: row start, in-list start,
-    // first partner, owner, and out-degree | heavy flag << 31
-    __shared__ uint32_t s_beg[PW_WARPS][32], s_ib[PW_WARPS][32], s_p0[PW_WARPS][32], s_dh[PW_WARPS][32];
-    __shared__ uint32_t s_x[PW_WARPS][32];
+    // the 32 items of the current grab, by lane: row start, out-list start
+    // and length, in-list start, first partner, owner, and out-degree |
+    // heavy flag << 31
+    __shared__ uint32_t s_beg[PW_WARPS][32], s_ob[PW_WARPS][32], s_oc[PW_WARPS][32], s_ib[PW_WARPS][32];
+    __shared__ uint32_t s_p0[PW_WARPS][32], s_dh[PW_WARPS][32], s_x[PW_WARPS][32];
     __shared__ uint32_t s_ti[PW_WARPS][32], s_pre[PW_WARPS][32];  // table info; prefix within the pack
     __shared__ unsigned long long red[33];
     const unsigned lane = lane_id(), w = threadIdx.x >> 5;
@@ -410,11 +416,13 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
             const PaddedRow row = padded_row(ptrp, x);
             d = row.d;
             slots = d <= cfg.warp_max && d <= WARP_MAX ? table_slots(d, WTAB) : 0u;
-            uint32_t hx = 0, ib = 0, p0 = 0;
+            uint32_t hx = 0, ob = 0, oc = 0, ib = 0, p0 = 0;
             if (slots && d >= 2) {
                 hx = heavy[x];
+                ob = rowptr[x];
+                oc = ocnt[x];
                 ib = inptr[x];
-                const uint32_t np = d + (inend[x] - ib);
+                const uint32_t np = oc + (inend[x] - ib);
                 const uint32_t sl = seg_len(d, 0, cfg);
                 p0 = seg * sl;
                 npart = np > p0 ? min(np - p0, sl) : 0u;
@@ -425,6 +433,8 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
                 slots = 0;
             }
             s_beg[w][lane] = row.beg;
+            s_ob[w][lane] = ob;
+            s_oc[w][lane] = oc;
             s_ib[w][lane] = ib;
             s_p0[w][lane] = p0;
             s_dh[w][lane] = d | (hx << 31);
@@ -493,13 +503,13 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
                     uint32_t c0 = 0, nc = 0, hh = 0, ti = 0;
                     if (q < tot) {
                         const uint32_t dh = s_dh[w][L], Ld = dh & 0x7fffffffu;
-                        const uint32_t j = s_p0[w][L] + (q - s_pre[w][L]);
-                        const bool is_out = j < Ld;
+                        const uint32_t j = s_p0[w][L] + (q - s_pre[w][L]), oc = s_oc[w][L];
+                        const bool is_out = j < oc;
                         uint32_t y, qpos = 0;
                         if (is_out) {
-                            y = __ldg(col + s_beg[w][L] + j);
+                            y = __ldg(olist + s_ob[w][L] + j);
                         } else {
-                            const uint2 e = __ldg(inlist + s_ib[w][L] + j - Ld);
+                            const uint2 e = __ldg(inlist + s_ib[w][L] + j - oc);
                             y = e.x;
                             qpos = e.y;
                         }
@@ -589,6 +599,9 @@ __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, cons
 template <bool DYN>
 __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const uint32_t *__restrict__ ptrp,
                                                                       const uint32_t *__restrict__ col,
+                                                                      const uint32_t *__restrict__ rowptr,
+                                                                      const uint32_t *__restrict__ olist,
+                                                                      const uint32_t *__restrict__ ocnt,
                                                                       const uint32_t *__restrict__ inptr,
                                                                       const uint32_t *__restrict__ inend,
                                                                       const uint2 *__restrict__ inlist,
@@ -634,7 +647,7 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const u
                 bucket_insert(tab, set.mask, set.shift, __ldg(col + row.beg + i));
         }
         if (seg == 0 && threadIdx.x == 0) t.table += d;
-        const uint32_t ib = inptr[x], np = d + (inend[x] - ib);
+        const uint32_t ob = rowptr[x], oc = ocnt[x], ib = inptr[x], np = oc + (inend[x] - ib);
         const uint32_t sl = seg_len(d, 1, cfg);
         const uint32_t p0 = seg * sl, p1 = min(np, p0 + sl);
         const uint32_t per = sl / PB_THREADS;  // <= PB_PER_THREAD
@@ -646,12 +659,12 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const u
             const uint32_t j = p0 + threadIdx.x * per + q;
             uint32_t c0 = 0, nc = 0, hh = 0;
             if (q < per && j < p1) {
-                const bool is_out = j < d;
+                const bool is_out = j < oc;
                 uint32_t y, qpos = 0;
                 if (is_out) {
-                    y = __ldg(col + row.beg + j);
+                    y = __ldg(olist + ob + j);
                 } else {
-                    const uint2 e = __ldg(inlist + ib + j - d);
+                    const uint2 e = __ldg(inlist + ib + j - oc);
                     y = e.x;
                     qpos = e.y;
                 }
@@ -722,14 +735,16 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
     if (b.n == 0 || b.m == 0) return;
     const uint64_t wm = wm_capacity(b.n, b.m);
     intersect_prepare(dyn_smem_bytes);
-    k_probe_warp<<<152 * 4, PW_THREADS, 0, s>>>(b.ptrp, b.col, b.inptr, b.inend, b.inlist, b.items, wm, b.heavy, b.st, b.bv,
-                                                b.cfg, b.core_base);
+    k_probe_warp<<<152 * 4, PW_THREADS, 0, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr, b.inend, b.inlist,
+                                                b.items, wm, b.heavy, b.st, b.bv, b.cfg, b.core_base);
     note_launch();
-    k_probe_block<false><<<152 * 4, PB_THREADS, MID_TAB * 4, s>>>(b.ptrp, b.col, b.inptr, b.inend, b.inlist, b.items, wm,
+    k_probe_block<false><<<152 * 4, PB_THREADS, MID_TAB * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
+                                                                   b.inend, b.inlist, b.items, wm,
                                                                    b.heavy, b.st, MID_TAB, b.items_cap, b.bv, b.cfg,
                                                                    b.core_base);
     note_launch();
-    k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.ptrp, b.col, b.inptr, b.inend, b.inlist, b.items, wm,
+    k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
+                                                                b.inend, b.inlist, b.items, wm,
                                                                 b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
                                                                 b.items_cap, b.bv, b.cfg, b.core_base);
     note_launch();

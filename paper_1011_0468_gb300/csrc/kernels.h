@@ -106,6 +106,8 @@ struct RowsArgs {
     uint32_t *ptrp;              // [n + 2] padded row pointers (see SENT)
     uint32_t *colp;              // [colp_capacity(n, m)] padded columns
     uint2 *inlist;               // [m] in-list entries (source, padded position of the edge in its row)
+    uint32_t *olist;             // [m] out-lists: the live out-partners of x at olist[rowptr[x] ..]
+    uint32_t *ocnt;              // [n] their number
     uint32_t *keepw;             // [ceil(m / 32)] keep bits
     uint32_t *tile_cnt;          // [ceil(m / RX_TILE) + 1]
     uint32_t *scan;              // scan scratch for max(n + 1, tiles)
@@ -163,6 +165,8 @@ struct CountBuffers {
     uint32_t *inptr;        // [n + 1] in-list starts
     uint32_t *inend;        // [n] in-list ends
     const uint2 *inlist;    // in-list entries (source, padded position of the edge)
+    const uint32_t *olist;  // out-lists (RowsArgs::olist)
+    const uint32_t *ocnt;   // [n]
     uint64_t *items;        // owner work items [items_cap]
     uint64_t items_cap;
     DevState *st;
@@ -192,6 +196,7 @@ struct UnionScratch {
     uint32_t n_cap = 0, k_cap = 0;
     uint64_t *rel = nullptr, *orig = nullptr;  // union keys in rank ids (sorted) and their original keys
     uint2 *inlist = nullptr;
+    uint32_t *olist = nullptr, *ocnt = nullptr;
     uint64_t *items = nullptr;
     uint64_t items_cap = 0;
     uint32_t *deg = nullptr, *rowptr = nullptr, *inptr = nullptr, *hist = nullptr, *scan = nullptr;

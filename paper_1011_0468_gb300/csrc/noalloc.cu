@@ -33,7 +33,7 @@ constexpr uint64_t NA_ITEMS = NA_N + 2 * NA_M / SEG_MIN + NA_M / 1024 + 2 * NA_M
 constexpr uint64_t NA_COLP = NA_M + 3 * NA_M + 4;  // >= colp_capacity(N, M)
 static_assert(NA_N <= NA_M, "the vertex sort reuses the key buffers");
 constexpr uint64_t NA_BYTES = 4 * na_round(8 * NA_M)                     // ekey (then rel), orig, bufA, bufB
-                              + 4 * na_round(4 * NA_N)                   // perm, rank, spread, inend
+                              + 5 * na_round(4 * NA_N)                   // perm, rank, spread, inend, ocnt
                               + na_round(4 * (NA_M / 32 + 1)) + na_round(4 * (NA_TILES + 1))  // keepw, tile_cnt
                               + na_round(4 * NA_HIST) + na_round(4 * NA_SCAN)
                               + 2 * na_round(4 * (NA_N + 2))             // deg, rowptr
@@ -116,6 +116,7 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     uint32_t *rank = c.take<uint32_t>(NA_N);
     uint32_t *spread = c.take<uint32_t>(NA_N);  // hot_size(n) <= NA_N
     uint32_t *inend = c.take<uint32_t>(NA_N);
+    uint32_t *ocnt = c.take<uint32_t>(NA_N);
     uint32_t *keepw = c.take<uint32_t>(NA_M / 32 + 1);
     uint32_t *tile_cnt = c.take<uint32_t>(NA_TILES + 1);
     uint64_t *bufA = c.take<uint64_t>(NA_M);
@@ -181,6 +182,8 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     cb.inptr = inptr;
     cb.inend = inend;
     cb.inlist = reinterpret_cast<uint2 *>(bufA);
+    cb.olist = reinterpret_cast<uint32_t *>(bufB);  // free after the sorts; m <= NA_M entries
+    cb.ocnt = ocnt;
     cb.items = items;
     cb.items_cap = items_capacity(n, m);
     cb.st = st;
@@ -198,6 +201,8 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     ra.ptrp = ptrp;
     ra.colp = colp;
     ra.inlist = reinterpret_cast<uint2 *>(bufA);
+    ra.olist = reinterpret_cast<uint32_t *>(bufB);
+    ra.ocnt = ocnt;
     ra.keepw = keepw;
     ra.tile_cnt = tile_cnt;
     ra.scan = scan;
