@@ -305,7 +305,7 @@ void tc_server_destroy(tc_server *srv);
  *   cuda_stream  stream for the work (NULL = default); the call blocks
  *                until the result is in *out_host.
  * All scratch lives in one fixed __device__ array inside the library
- * (about 20 MiB), held by every GPU that loads it until the process exits.
+ * (about 24 MiB), held by every GPU that loads it until the process exits.
  * The first call on a device looks up that array's device address; make
  * this first call before any stream capture.  Calls share the array (each
  * clears what must start at zero), so calls that overlap on the GPU race:

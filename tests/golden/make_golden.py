@@ -8,9 +8,11 @@ touches the CUDA library.  Run from the repository root:
 chung_lu_4m: Chung-Lu power-law graph, n = 2^22 vertices, exactly 2^26
 undirected edges, degree exponent 2.1, maximum expected degree 1e5, seed 1
 (the multi-million-edge social-network shape of the paper's Table 1).  The
-oracle result is stored for p = 1 (exact count) and p in {0.1, 0.01} with
-seeds 1..3, with a checksum of the generated edge list so that a changed
-generator is detected instead of compared against stale numbers.
+oracle result is stored for p = 1 (exact count), p in {0.1, 0.01} with
+seeds 1..3, and p = 0.7 and 0.55 (samples that still keep more than 2^25
+edges), with a checksum of the generated edge list so that a changed
+generator is detected instead of compared against stale numbers.  Runs
+already stored for the same checksum are kept, not recomputed.
 """
 import json
 import os
@@ -27,7 +29,7 @@ import oracle  # noqa: E402
 
 WORKLOADS = {
     "chung_lu_4m": dict(kind="chung_lu", n=1 << 22, m=1 << 26, gamma=2.1, wmax=1e5, seed=1,
-                        runs=[(1.0, 1)] + [(p, s) for p in (0.1, 0.01) for s in (1, 2, 3)]),
+                        runs=[(1.0, 1)] + [(p, s) for p in (0.1, 0.01) for s in (1, 2, 3)] + [(0.7, 1), (0.55, 2)]),
 }
 
 
@@ -54,7 +56,13 @@ def main(names):
         rec = {"workload": name, "spec": {k: v for k, v in spec.items() if k != "runs"},
                "m": int(len(edges)), "checksum": checksum(edges), "runs": []}
         print(name, "generated", len(edges), "edges in %.1fs" % (time.time() - t0), flush=True)
+        path = os.path.join(HERE, name + ".json")
+        old = json.load(open(path)) if os.path.exists(path) else {}
+        stored = {(r["p"], r["seed"]): r for r in old.get("runs", [])} if old.get("checksum") == rec["checksum"] else {}
         for p, seed in spec["runs"]:
+            if (p, seed) in stored:
+                rec["runs"].append(stored[(p, seed)])
+                continue
             t0 = time.time()
             r = oracle.run(edges, spec["n"], p, seed)
             r["p"], r["seed"] = p, seed
@@ -62,7 +70,7 @@ def main(names):
             r["oracle_seconds"] = round(time.time() - t0, 2)
             rec["runs"].append(r)
             print(name, p, seed, r, flush=True)
-        with open(os.path.join(HERE, name + ".json"), "w") as f:
+        with open(path, "w") as f:
             json.dump(rec, f, indent=1)
 
 
