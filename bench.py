@@ -85,12 +85,13 @@ def make_graph():
 
 def recorded_traffic():
     """DRAM bytes of the intersection kernels from the committed ncu capture
-    (profiles/traffic.json), or None when the kernel source has changed."""
+    (profiles/traffic.json), or None when a source it depends on has changed
+    (sha1 of the listed files, concatenated in order)."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
-        if hashlib.sha1(src).hexdigest()[:12] != rec["source_sha1_12"]:
+        src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in rec["sources"])
+        if hashlib.sha1(src).hexdigest()[:12] != rec["sources_sha1_12"]:
             return None
         return float(rec["dram_bytes"])
     except Exception:
