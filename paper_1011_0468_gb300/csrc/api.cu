@@ -82,7 +82,8 @@ struct tc_graph {
     uint32_t *deg = nullptr;    // [n]
     uint32_t *rowptr = nullptr; // [n + 1]
     uint8_t *heavy = nullptr;   // [n]
-    uint32_t *inptr = nullptr;  // [n + 2] in-list starts
+    uint32_t *inptr = nullptr;  // [n + 2] in-list reservations (static: full in-degrees)
+    uint32_t *frow = nullptr;   // [n + 1] row offsets of the full graph in rel (static)
     uint32_t *inend = nullptr;  // [n] in-list ends
     uint2 *inlist = nullptr;    // [m] in-list entries
     uint32_t *olist = nullptr;  // [m] out-lists
@@ -174,6 +175,8 @@ CountBuffers buffers_of(tc_graph *g)
     b.inptr = g->inptr;
     b.inend = g->inend;
     b.inlist = g->inlist;
+    b.static_rows = true;
+    b.spread = g->spread;
     b.olist = g->olist;
     b.ocnt = g->ocnt;
     b.items = g->items;
@@ -182,7 +185,18 @@ CountBuffers buffers_of(tc_graph *g)
     return b;
 }
 
-RowsArgs rows_of(tc_graph *g, uint64_t seed_mix, uint64_t thr)
+// m_lo: a lower bound on m_p below which the sample falls with probability
+// under e^-60 (Chernoff, m_p ~ Binomial(m, p)); only vertices whose full
+// degree^2 exceeds it can be heavy.  A sample below it is still counted
+// exactly (k_in_fallback).
+uint64_t sample_floor(uint64_t m, double p, uint64_t thr)
+{
+    if (thr >= (1ull << 53)) return m;
+    const double mean = p * (double)m, lo = mean - std::sqrt(120.0 * mean) - 1.0;
+    return lo > 0.0 ? (uint64_t)lo : 0ull;
+}
+
+RowsArgs rows_of(tc_graph *g, uint64_t seed_mix, uint64_t thr, uint64_t m_lo)
 {
     RowsArgs a;
     a.rel = g->rel;
@@ -205,6 +219,8 @@ RowsArgs rows_of(tc_graph *g, uint64_t seed_mix, uint64_t thr)
     a.scan = g->scan;
     a.spread = g->spread;
     a.st = g->st;
+    a.frow = g->frow;
+    a.m_lo = m_lo;
     return a;
 }
 
@@ -213,7 +229,9 @@ void enqueue_sample(tc_graph *g, const RowsArgs &ra)
 {
     cudaMemsetAsync(g->st, 0, sizeof(DevState), g->stream);
     sample_rows(ra, g->stream);
-    partition(buffers_of(g), g->stream);
+    CountBuffers b = buffers_of(g);
+    b.all_kept = ra.thr >= (1ull << 53);
+    partition(b, g->stream);
 }
 
 cudaEvent_t &ring_event(tc_graph *g, uint64_t count, int i)
@@ -243,7 +261,7 @@ void ring_times(tc_graph *g, uint64_t count, float *ms)
 tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bool timing)
 {
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
-    const RowsArgs ra = rows_of(g, seed_mix, thr);
+    const RowsArgs ra = rows_of(g, seed_mix, thr, sample_floor(g->m, p, thr));
     // the core block pays off once the sample is large: its cost is fixed,
     // the intersections it replaces grow with the sample
     const CoreBuffers *core = (g->core.hb.hcap && p * (double)g->m >= CORE_MIN_EDGES) ? &g->core : nullptr;
@@ -430,6 +448,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     g->heavy = (uint8_t *)g->alloc((uint64_t)n);
     g->inptr = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
     g->inend = (uint32_t *)g->alloc((uint64_t)n * 4);
+    g->frow = (uint32_t *)g->alloc(((uint64_t)n + 1) * 4);
     g->olist = (uint32_t *)g->alloc(m1 * 4);
     g->ocnt = (uint32_t *)g->alloc((uint64_t)n * 4);
     g->colp = (uint32_t *)g->alloc(colp_capacity(n, m) * 4);
@@ -439,11 +458,13 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     g->spread = (uint32_t *)g->alloc(hot_size(n) * 4);
     g->items_cap = items_capacity(n, m);
     g->items = (uint64_t *)g->alloc(g->items_cap * 8);
-    if (!g->rowptr || !g->heavy || !g->inptr || !g->inend || !g->olist || !g->ocnt || !g->colp || !g->ptrp || !g->keepw || !g->tile_cnt || !g->spread ||
-        !g->items) {
+    if (!g->rowptr || !g->heavy || !g->inptr || !g->inend || !g->frow || !g->olist || !g->ocnt || !g->colp || !g->ptrp ||
+        !g->keepw || !g->tile_cnt || !g->spread || !g->items) {
         free_graph(g);
         return TC_ENOMEM;
     }
+    // static rows (g->deg still holds the full degrees by original id)
+    static_rows(g->rel, m, n, g->perm, g->deg, g->frow, g->inptr, g->scan, s);
     // hash set of the owners with d+ > 1024: every out-degree of the
     // degree-oriented graph is at most sqrt(2 m_p); a set of >= 4 d+ slots
     // up to 32768 slots (128 KiB) stays on chip, larger rows are searched in
@@ -572,7 +593,7 @@ tc_status tc_graph_export_sample(tc_graph *g, double p, uint64_t seed, uint32_t 
 {
     if (!g || bad_p(p)) return TC_EINVAL;
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
-    enqueue_sample(g, rows_of(g, seed_mix, thr));
+    enqueue_sample(g, rows_of(g, seed_mix, thr, 0));  // every vertex with an edge: exact degrees
     cudaMemcpyAsync(g->st_host, g->st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream);
     tc_status st = sync_graph(g);
     if (st != TC_OK) return st;
@@ -617,7 +638,7 @@ tc_status tc_graph_export_csr(tc_graph *g, double p, uint64_t seed, uint32_t *ro
 {
     if (!g || bad_p(p)) return TC_EINVAL;
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
-    const RowsArgs ra = rows_of(g, seed_mix, thr);
+    const RowsArgs ra = rows_of(g, seed_mix, thr, sample_floor(g->m, p, thr));
     enqueue_sample(g, ra);
     if (g->m > 0) build_rows(ra, g->stream);
     cudaMemcpyAsync(g->st_host, g->st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream);

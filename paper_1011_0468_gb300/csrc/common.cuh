@@ -41,7 +41,8 @@ struct DevState {
     unsigned int core_on;          // 1: the core block counts the triangles inside the core
     unsigned int heavy_below;      // heavy vertices below the core base
     unsigned int cursor_core;      // work cursor of the core contraction
-    unsigned int pad2;
+    unsigned int cand_lo;          // single graph: rank ids below this cannot be heavy (see k_sample_keep)
+    unsigned int cand_all;         // 1: the sample fell below the bound, every in-degree was counted
 };
 
 // A batch of independent graphs laid out as one disjoint union: graph g owns

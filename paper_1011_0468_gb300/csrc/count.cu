@@ -53,9 +53,44 @@ __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevSta
     if (lane_id() == 0 && h) atomicAdd(&st->n_heavy, h);
 }
 
+// Single graph with static rows: only rank ids at or above DevState::cand_lo
+// can be heavy (k_sample_keep); their sampled degree is the kept out-degree
+// (rowptr) plus the kept in-degree (spread, or the static one when every edge
+// is kept).  The rest are light, and light_lim is at least cand_lo.
+__global__ void k_partition_cand(const uint32_t *__restrict__ dplus, const uint32_t *__restrict__ spread, int hbits,
+                                 const uint32_t *__restrict__ inres, bool all_kept, uint32_t n, DevState *st,
+                                 uint32_t *__restrict__ deg, uint8_t *__restrict__ heavy)
+{
+    const unsigned long long mp = st->m_sampled;
+    const uint32_t cand = st->cand_all ? 0u : st->cand_lo;
+    uint32_t h = 0, lim = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        uint32_t d = dplus[u];
+        uint8_t f = 0;
+        if (u >= cand) {
+            d += all_kept ? inres[u + 1] - inres[u] : spread[hot_index((uint32_t)u, hbits)];
+            f = (unsigned long long)d * d > mp;
+            if (!f && d) lim = (uint32_t)u + 1;
+        }
+        deg[u] = d;
+        heavy[u] = f;
+        h += f;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) lim = max(lim, min(cand, n));
+    if (lim) atomicMax(&st->light_lim, lim);
+    h = warp_sum(h);
+    if (lane_id() == 0 && h) atomicAdd(&st->n_heavy, h);
+}
+
 void partition(const CountBuffers &b, cudaStream_t s)
 {
-    k_partition<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.deg, b.n, b.st, b.heavy, b.bv);
+    if (b.static_rows) {
+        k_partition_cand<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.spread, hot_bits(b.n), b.inptr,
+                                                                     b.all_kept, b.n, b.st, b.deg, b.heavy);
+    } else {
+        k_partition<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.deg, b.n, b.st, b.heavy, b.bv);
+    }
     note_launch();
 }
 

@@ -204,9 +204,200 @@ __global__ void k_degrees(const uint32_t *__restrict__ dplus, const uint32_t *__
         deg[x] = dplus[x] + spread[hot_index((uint32_t)x, hbits)];
 }
 
+// ---------------------------------------------------------------------
+// Single graph.  Static rows (at creation): frow, the row offsets of the
+// full graph in the rank-order key list, and inres, the offsets of the
+// in-list reservations (full in-degrees = full degree - out-degree).  Per
+// count the kept out-degrees are popcounts of the keep bits over each row,
+// and kept in-degrees are counted only for the vertices that can be heavy.
+// ---------------------------------------------------------------------
+
+// Full out-degree of every rank id (one atomic per run of a source in a warp).
+__global__ void k_full_outdeg(const uint64_t *__restrict__ rel, uint64_t m, uint32_t *__restrict__ outd)
+{
+    const unsigned lane = lane_id();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m; base += stride) {
+        const uint64_t i = base + lane;
+        const uint32_t u = i < m ? (uint32_t)(ld_stream_u64(rel + i) >> 32) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(FULL, u);
+        if (i < m && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(outd + u, (unsigned)__popc(peers));
+    }
+}
+
+// ind[x] = full degree of rank id x - its out-degree; ind[n] = 0.
+__global__ void k_full_indeg(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ deg_orig,
+                             const uint32_t *__restrict__ outd, uint32_t n, uint32_t *__restrict__ ind)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride)
+        ind[x] = x < n ? __ldg(deg_orig + __ldg(perm + x)) - outd[x] : 0u;
+}
+
+void static_rows(const uint64_t *rel, uint64_t m, uint32_t n, const uint32_t *perm, const uint32_t *deg_orig,
+                 uint32_t *frow, uint32_t *inres, uint32_t *scan, cudaStream_t s)
+{
+    const uint64_t n1 = (uint64_t)n + 1;
+    cudaMemsetAsync(frow, 0, n1 * 4, s);
+    if (m > 0) {
+        k_full_outdeg<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(rel, m, frow);
+        note_launch();
+    }
+    k_full_indeg<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(perm, deg_orig, frow, n, inres);
+    note_launch();
+    scan_excl_u32(frow, n1, nullptr, scan, s);
+    scan_excl_u32(inres, n1, nullptr, scan, s);
+}
+
+// Smallest rank id whose full degree d has d^2 > m_lo (n if none): full
+// degrees grow with the rank.
+__device__ uint32_t cand_lo_of(const uint32_t *__restrict__ frow, const uint32_t *__restrict__ inres, uint32_t n,
+                               uint64_t m_lo)
+{
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        const unsigned long long d = (frow[mid + 1] - frow[mid]) + (inres[mid + 1] - inres[mid]);
+        if (d * d > m_lo) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// The Section 3.1 keep test of every edge (on its original key): keep bits
+// (32-edge words in list order), kept edges per RX_TILE tile and m_p.  With
+// m_p >= m_lo a heavy vertex has full degree^2 > m_lo, so the kept in-degrees
+// are counted (spread, at hot_index) only for rank ids at or above that
+// bound (DevState::cand_lo), from the kept edges' rank-order keys.  At p = 1
+// every edge is kept: no hashing, and the in-degrees are the static ones.
+__global__ void __launch_bounds__(256) k_sample_keep(const uint64_t *__restrict__ rel,
+                                                     const uint64_t *__restrict__ orig, uint64_t m,
+                                                     uint64_t seed_mix, uint64_t thr, uint32_t n,
+                                                     const uint32_t *__restrict__ frow,
+                                                     const uint32_t *__restrict__ inres, uint64_t m_lo,
+                                                     uint32_t *__restrict__ spread, int hbits,
+                                                     uint32_t *__restrict__ keepw, uint32_t *__restrict__ tile_cnt,
+                                                     DevState *st)
+{
+    __shared__ uint32_t wt[33];
+    __shared__ uint32_t s_cand;
+    const unsigned lane = lane_id();
+    const bool all = thr >= (1ull << 53);
+    if (threadIdx.x == 0) {
+        s_cand = cand_lo_of(frow, inres, n, m_lo);
+        if (blockIdx.x == 0) st->cand_lo = s_cand;
+    }
+    __syncthreads();
+    const uint32_t cand = s_cand;
+    const bool count_in = !all && cand < n;
+    const uint64_t nt = (m + RX_TILE - 1) / RX_TILE;
+    uint32_t kept_total = 0;
+    for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        uint32_t c = 0;
+        constexpr int SU = 4;  // edges per thread in flight
+#pragma unroll 1
+        for (int j0 = 0; j0 < RX_ITEMS; j0 += SU) {
+            bool f[SU];
+            if (all) {
+#pragma unroll
+                for (int q = 0; q < SU; ++q) f[q] = tile * RX_TILE + (uint64_t)(j0 + q) * 256 + threadIdx.x < m;
+            } else {
+                uint64_t o[SU];
+#pragma unroll
+                for (int q = 0; q < SU; ++q) {
+                    const uint64_t i = tile * RX_TILE + (uint64_t)(j0 + q) * 256 + threadIdx.x;
+                    o[q] = ld_stream_u64(orig + (i < m ? i : m - 1));
+                }
+#pragma unroll
+                for (int q = 0; q < SU; ++q) {
+                    const uint64_t i = tile * RX_TILE + (uint64_t)(j0 + q) * 256 + threadIdx.x;
+                    f[q] = i < m && keep_edge(o[q], seed_mix, thr);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < SU; ++q) {
+                const uint64_t i = tile * RX_TILE + (uint64_t)(j0 + q) * 256 + threadIdx.x;
+                const unsigned word = __ballot_sync(FULL, f[q]);
+                if (lane == 0 && i - lane < m) keepw[(i - lane) >> 5] = word;
+                c += f[q];
+            }
+            if (count_in) {
+#pragma unroll
+                for (int q = 0; q < SU; ++q) {
+                    const uint64_t i = tile * RX_TILE + (uint64_t)(j0 + q) * 256 + threadIdx.x;
+                    if (f[q]) {
+                        const uint32_t v = (uint32_t)ld_stream_u64(rel + i);
+                        if (v >= cand) atomicAdd(spread + hot_index(v, hbits), 1u);
+                    }
+                }
+            }
+        }
+        kept_total += c;
+        c = block_sum(c, wt);
+        if (threadIdx.x == 0) tile_cnt[tile] = c;
+    }
+    kept_total = warp_sum(kept_total);
+    if (lane == 0 && kept_total) atomicAdd(&st->m_sampled, (unsigned long long)kept_total);
+}
+
+// Only if the sample came out below m_lo (the candidates might then miss a
+// heavy vertex): the kept in-degrees of the rank ids below cand_lo too, and
+// DevState::cand_all for the partition.
+__global__ void __launch_bounds__(256) k_in_fallback(const uint64_t *__restrict__ rel, uint64_t m,
+                                                     const uint32_t *__restrict__ keepw, uint64_t m_lo,
+                                                     uint32_t *__restrict__ spread, int hbits, DevState *st)
+{
+    if (st->m_sampled >= m_lo) return;
+    const uint32_t cand = st->cand_lo;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->cand_all = 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        if (!((keepw[i >> 5] >> (i & 31)) & 1u)) continue;
+        const uint32_t v = (uint32_t)rel[i];
+        if (v < cand) atomicAdd(spread + hot_index(v, hbits), 1u);
+    }
+}
+
+// Kept out-degree of every rank id: the keep bits over its row; dplus[n] = 0.
+__global__ void k_out_degrees(const uint32_t *__restrict__ frow, const uint32_t *__restrict__ keepw, uint32_t n,
+                              uint32_t *__restrict__ dplus)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
+        uint32_t d = 0;
+        if (x < n) {
+            const uint32_t b = frow[x], e = frow[x + 1];
+            if (b < e) {
+                const uint32_t wb = b >> 5, we = (e - 1) >> 5;
+                for (uint32_t w = wb; w <= we; ++w) {
+                    uint32_t word = __ldg(keepw + w);
+                    if (w == wb) word &= 0xffffffffu << (b & 31);
+                    if (w == we) word &= 0xffffffffu >> (31 - ((e - 1) & 31));
+                    d += __popc(word);
+                }
+            }
+        }
+        dplus[x] = d;
+    }
+}
+
 void sample_rows(const RowsArgs &a, cudaStream_t s)
 {
     const int hb = hot_bits(a.n);
+    if (a.frow) {
+        cudaMemsetAsync(a.spread, 0, hot_size(a.n) * 4, s);
+        if (a.m > 0) {
+            const uint64_t nt = ceil_div(a.m, RX_TILE);
+            k_sample_keep<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.orig, a.m, a.seed_mix, a.thr, a.n, a.frow,
+                                                                     a.inptr, a.m_lo, a.spread, hb, a.keepw,
+                                                                     a.tile_cnt, a.st);
+            note_launch();
+            k_in_fallback<<<152 * 4, 256, 0, s>>>(a.rel, a.m, a.keepw, a.m_lo, a.spread, hb, a.st);
+            note_launch();
+        }
+        k_out_degrees<<<grid_for((uint64_t)a.n + 1, 256, 152 * 8), 256, 0, s>>>(a.frow, a.keepw, a.n, a.rowptr);
+        note_launch();
+        return;
+    }
     cudaMemsetAsync(a.rowptr, 0, ((size_t)a.n + 1) * 4, s);
     cudaMemsetAsync(a.spread, 0, hot_size(a.n) * 4, s);
     if (a.m > 0) {
@@ -235,7 +426,7 @@ __global__ void k_row_counts(const uint32_t *__restrict__ dplus, uint32_t *__res
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= n; x += stride) {
         const uint32_t dp = x < n ? dplus[x] : 0u;
         ptrp[x] = pad_of(dp);
-        P[x] = x < n ? deg[x] - dp : 0u;
+        if (P) P[x] = x < n ? deg[x] - dp : 0u;
         if (x < n) {
             deg[x] = dp;
             ocnt[x] = 0;
@@ -350,10 +541,12 @@ void build_rows(const RowsArgs &a, cudaStream_t s)
 {
     const uint64_t n1 = (uint64_t)a.n + 1;
     const int hb = hot_bits(a.n);
-    k_row_counts<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.deg, a.n, a.ptrp, a.inptr, a.ocnt);
+    // single graph: the in-list reservations are the static ones (inptr)
+    k_row_counts<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.deg, a.n, a.ptrp, a.frow ? nullptr : a.inptr,
+                                                          a.ocnt);
     note_launch();
     scan_excl_u32(a.ptrp, n1, nullptr, a.scan, s);
-    scan_excl_u32(a.inptr, n1, nullptr, a.scan, s);
+    if (!a.frow) scan_excl_u32(a.inptr, n1, nullptr, a.scan, s);
     scan_excl_u32(a.rowptr, n1, nullptr, a.scan, s);
     if (a.m > 0) {
         const uint64_t nt = ceil_div(a.m, RX_TILE);

@@ -113,7 +113,17 @@ struct RowsArgs {
     uint32_t *scan;              // scan scratch for max(n + 1, tiles)
     uint32_t *spread;            // [hot_size(n)] per-vertex counters in hot_index order
     DevState *st;
+    // single graph: the static rows (csr.cu static_rows; inptr then holds the
+    // static in-list reservations) and the lower bound on m_p that picks the
+    // vertices whose in-degrees are counted; nullptr: union path
+    const uint32_t *frow = nullptr;
+    uint64_t m_lo = 0;
 };
+// Static rows of a single graph at creation: frow[0..n] (row offsets of rel)
+// and inres[0..n] (in-list reservation offsets: full in-degrees).  perm and
+// deg_orig: rank -> original id and the full degree by original id.
+void static_rows(const uint64_t *rel, uint64_t m, uint32_t n, const uint32_t *perm, const uint32_t *deg_orig,
+                 uint32_t *frow, uint32_t *inres, uint32_t *scan, cudaStream_t s);
 // Counters that every edge bumps at its target (in-degrees, in-list
 // cursors) are kept at hot_index(v): the id rotated within hot_bits(n) bits,
 // so that consecutive ids (the hubs are the top ranks) land 4 KiB apart in
@@ -173,6 +183,11 @@ struct CountBuffers {
     BatchView bv;           // k > 0: the graph is a batch union
     IsectConfig cfg;        // intersection schedule
     uint32_t core_base = 0xffffffffu;  // base of the dense core of this count (see CoreBuffers), or none
+    // single graph with static rows: kept out-degrees sit in rowptr, in-degrees
+    // of the candidates in spread (or static when all_kept), inptr the static
+    // reservations
+    bool static_rows = false, all_kept = false;
+    const uint32_t *spread = nullptr;
 };
 
 void partition(const CountBuffers &b, cudaStream_t s);
