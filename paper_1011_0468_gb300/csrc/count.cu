@@ -56,8 +56,10 @@ __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevSta
 // Single graph with static rows: only rank ids at or above DevState::cand_lo
 // can be heavy (k_sample_keep); their sampled degree is the kept out-degree
 // (rowptr) plus the kept in-degree (spread, or the static one when every edge
-// is kept).  The rest are light, and light_lim is at least cand_lo.
-__global__ void k_partition_cand(const uint32_t *__restrict__ dplus, const uint32_t *__restrict__ spread, int hbits,
+// is kept).  The rest are light, and light_lim is at least cand_lo.  Each
+// counter of spread then becomes its vertex's in-list cursor (the static
+// reservation inres).
+__global__ void k_partition_cand(const uint32_t *__restrict__ dplus, uint32_t *__restrict__ spread, int hbits,
                                  const uint32_t *__restrict__ inres, bool all_kept, uint32_t n, DevState *st,
                                  uint32_t *__restrict__ deg, uint8_t *__restrict__ heavy)
 {
@@ -68,11 +70,13 @@ __global__ void k_partition_cand(const uint32_t *__restrict__ dplus, const uint3
     for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
         uint32_t d = dplus[u];
         uint8_t f = 0;
+        uint32_t *sp = spread + hot_index((uint32_t)u, hbits);
         if (u >= cand) {
-            d += all_kept ? inres[u + 1] - inres[u] : spread[hot_index((uint32_t)u, hbits)];
+            d += all_kept ? inres[u + 1] - inres[u] : *sp;
             f = (unsigned long long)d * d > mp;
             if (!f && d) lim = (uint32_t)u + 1;
         }
+        *sp = inres[u];  // u's in-list cursor from here on (the compaction appends at it)
         deg[u] = d;
         heavy[u] = f;
         h += f;
@@ -86,7 +90,8 @@ __global__ void k_partition_cand(const uint32_t *__restrict__ dplus, const uint3
 void partition(const CountBuffers &b, cudaStream_t s)
 {
     if (b.static_rows) {
-        k_partition_cand<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.spread, hot_bits(b.n), b.inptr,
+        k_partition_cand<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.spread,
+                                                                     hot_bits(b.n), b.inptr,
                                                                      b.all_kept, b.n, b.st, b.deg, b.heavy);
     } else {
         k_partition<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.deg, b.n, b.st, b.heavy, b.bv);

@@ -442,13 +442,73 @@ __global__ void k_cursors(const uint32_t *__restrict__ P, uint32_t n, int hbits,
         spread[hot_index((uint32_t)x, hbits)] = P[x];
 }
 
+// One kept edge per live lane: (u -> v) at list index i, CSR position k.
+// All lanes of the warp call it (the out-list appends are warp-aggregated).
+struct ScatterArgs {
+    const uint64_t *rel;
+    const uint32_t *padoff, *rowptr, *dplus;
+    uint32_t *colp, *cursor, *olist, *ocnt;
+    uint2 *inlist;
+    int hbits;
+};
+
+__device__ __forceinline__ void scatter_edge(const ScatterArgs &a, bool live, uint64_t i, uint32_t k, unsigned lt)
+{
+    uint32_t u = 0, v = 0;
+    bool out = false;
+    if (live) {
+        const uint64_t r = ld_stream_u64(a.rel + i);
+        u = (uint32_t)(r >> 32);
+        v = (uint32_t)r;
+        const uint32_t pos = k + __ldg(a.padoff + u);
+        a.colp[pos] = v;
+        if (k + 1 < __ldg(a.rowptr + u + 1)) {  // so d+(u) >= 2
+            const uint32_t du = __ldg(a.dplus + u), dv = __ldg(a.dplus + v);
+            if (du < dv) {
+                const uint32_t q = atomicAdd(a.cursor + hot_index(v, a.hbits), 1u);
+                a.inlist[q] = make_uint2(u, pos);
+            } else {
+                out = dv >= 1;
+            }
+        }
+    }
+    const unsigned act = __ballot_sync(FULL, out);
+    if (out) {
+        const unsigned grp = __match_any_sync(act, u);  // lanes of this warp with the same row
+        const int lead = __ffs(grp) - 1;
+        uint32_t q = 0;
+        if ((int)lane_id() == lead) q = atomicAdd(a.ocnt + u, (unsigned)__popc(grp));
+        q = __shfl_sync(grp, q, lead) + __popc(grp & lt);
+        a.olist[__ldg(a.rowptr + u) + q] = v;
+    }
+}
+
+// Position of the k-th (from 0) set bit of w; k < popcount(w).
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t w, uint32_t k)
+{
+    uint32_t pos = 0;
+#pragma unroll
+    for (uint32_t s = 16; s >= 1; s >>= 1) {
+        const uint32_t c = __popc(w & ((1u << s) - 1u));
+        if (k >= c) {
+            k -= c;
+            w >>= s;
+            pos += s;
+        }
+    }
+    return pos;
+}
+
 // Writes every kept edge (u -> v) at its place in the padded rows (its
 // index among the kept edges, which is its CSR position, plus the padding
 // before row u) and, when u's row goes on past v (else the pair closes no
 // triangle), hands the pair to its owner (isect.cu): to v's in-list as (u,
 // that position) if d+(u) < d+(v) (cursors at hot_index), else, if d+(v) >=
 // 1, to u's out-list (ocnt: per-row counts, one atomic per run of u in a
-// warp).  Within a list the order is that of the atomics.
+// warp).  Within a list the order is that of the atomics.  A tile with at
+// most half its edges kept hands its kept edges to the threads one after
+// another (the word and bit of kept edge e found from the word prefixes)
+// instead of one edge slot per thread.
 __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict__ rel, uint64_t m,
                                                       const uint32_t *__restrict__ keepw,
                                                       const uint32_t *__restrict__ tile_off,
@@ -462,7 +522,9 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
     constexpr int WORDS = RX_TILE / 32;  // 128 keep words per tile
     __shared__ uint32_t s_word[WORDS], s_pre[WORDS];
     __shared__ uint32_t wt[33];
+    const ScatterArgs a{rel, padoff, rowptr, dplus, colp, cursor, olist, ocnt, inlist, hbits};
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
     const uint64_t nt = (m + RX_TILE - 1) / RX_TILE;
     for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         const uint64_t w0 = tile * WORDS, nw = (m + 31) / 32;
@@ -477,39 +539,28 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
         if (threadIdx.x < WORDS) s_pre[threadIdx.x] = ex;
         __syncthreads();
         const uint32_t base = tile_off[tile];
-        const unsigned lt = lanemask_lt();
-#pragma unroll 4
-        for (int j = 0; j < RX_ITEMS; ++j) {
-            const uint32_t wi = j * 8 + warp;  // word of this warp's 32 edges
-            const uint32_t word = s_word[wi];
-            uint32_t u = 0, v = 0, k = 0;
-            bool out = false;
-            if ((word >> lane) & 1u) {
-                const uint64_t i = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
-                const uint64_t r = ld_stream_u64(rel + i);
-                u = (uint32_t)(r >> 32);
-                v = (uint32_t)r;
-                k = base + s_pre[wi] + __popc(word & lt);  // CSR position
-                const uint32_t pos = k + __ldg(padoff + u);
-                colp[pos] = v;
-                if (k + 1 < __ldg(rowptr + u + 1)) {  // so d+(u) >= 2
-                    const uint32_t du = __ldg(dplus + u), dv = __ldg(dplus + v);
-                    if (du < dv) {
-                        const uint32_t q = atomicAdd(cursor + hot_index(v, hbits), 1u);
-                        inlist[q] = make_uint2(u, pos);
-                    } else {
-                        out = dv >= 1;
+        if (tot <= RX_TILE / 2) {
+            for (uint32_t e0 = 0; e0 < tot; e0 += 256) {
+                const uint32_t e = e0 + threadIdx.x;
+                const bool live = e < tot;
+                uint64_t i = 0;
+                if (live) {
+                    uint32_t lo = 0, hi = WORDS - 1;  // last word with s_pre <= e holds kept edge e
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if (s_pre[mid] <= e) lo = mid; else hi = mid - 1;
                     }
+                    i = tile * RX_TILE + lo * 32 + nth_set_bit(s_word[lo], e - s_pre[lo]);
                 }
+                scatter_edge(a, live, i, base + e, lt);
             }
-            const unsigned act = __ballot_sync(FULL, out);
-            if (out) {
-                const unsigned grp = __match_any_sync(act, u);  // lanes of this warp with the same row
-                const int lead = __ffs(grp) - 1;
-                uint32_t q = 0;
-                if ((int)lane == lead) q = atomicAdd(ocnt + u, (unsigned)__popc(grp));
-                q = __shfl_sync(grp, q, lead) + __popc(grp & lt);
-                olist[__ldg(rowptr + u) + q] = v;
+        } else {
+#pragma unroll 4
+            for (int j = 0; j < RX_ITEMS; ++j) {
+                const uint32_t wi = j * 8 + warp;  // word of this warp's 32 edges
+                const uint32_t word = s_word[wi];
+                const uint64_t i = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
+                scatter_edge(a, (word >> lane) & 1u, i, base + s_pre[wi] + __popc(word & lt), lt);
             }
         }
         __syncthreads();  // s_word / s_pre are rewritten for the next tile
@@ -545,15 +596,16 @@ void build_rows(const RowsArgs &a, cudaStream_t s)
     k_row_counts<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.deg, a.n, a.ptrp, a.frow ? nullptr : a.inptr,
                                                           a.ocnt);
     note_launch();
-    scan_excl_u32(a.ptrp, n1, nullptr, a.scan, s);
+    scan_excl_pair(a.ptrp, a.rowptr, n1, a.scan, s);
     if (!a.frow) scan_excl_u32(a.inptr, n1, nullptr, a.scan, s);
-    scan_excl_u32(a.rowptr, n1, nullptr, a.scan, s);
     if (a.m > 0) {
         const uint64_t nt = ceil_div(a.m, RX_TILE);
         scan_excl_u32(a.tile_cnt, nt, nullptr, a.scan, s);
     }
-    k_cursors<<<grid_for(a.n, 256, 152 * 8), 256, 0, s>>>(a.inptr, a.n, hb, a.spread);
-    note_launch();
+    if (!a.frow) {  // single graph: the partition set the cursors
+        k_cursors<<<grid_for(a.n, 256, 152 * 8), 256, 0, s>>>(a.inptr, a.n, hb, a.spread);
+        note_launch();
+    }
     if (a.m > 0) {
         const uint64_t nt = ceil_div(a.m, RX_TILE);
         k_rows_scatter<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.m, a.keepw, a.tile_cnt, a.ptrp, a.rowptr,

@@ -34,6 +34,9 @@ uint64_t scan_scratch_elems(uint64_t len);
 // sum of all elements is written there (device pointer).  scratch holds
 // scan_scratch_elems(len) uint32.
 void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s);
+// Exclusive prefix sums of a[0, len) and b[0, len) in one pass; the sum of b
+// must stay below 2^32.  scratch as for scan_excl_u32.
+void scan_excl_pair(uint32_t *a, uint32_t *b, uint64_t len, uint32_t *scratch, cudaStream_t s);
 
 // One stable LSD radix pass over the n 64-bit items of `in` on bits
 // [shift, shift + width), width <= 8, into out.  hist holds
@@ -187,7 +190,7 @@ struct CountBuffers {
     // of the candidates in spread (or static when all_kept), inptr the static
     // reservations
     bool static_rows = false, all_kept = false;
-    const uint32_t *spread = nullptr;
+    uint32_t *spread = nullptr;
 };
 
 void partition(const CountBuffers &b, cudaStream_t s);

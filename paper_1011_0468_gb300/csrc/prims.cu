@@ -60,7 +60,69 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_down(uint32_t *a, uint64_t 
     }
 }
 
-uint64_t scan_scratch_elems(uint64_t len) { return ceil_div(len, SC_CHUNK) + 1; }
+// Two arrays scanned together: (a << 32 | b) per element, so that one pass
+// scans both (the sums of b stay below 2^32).
+__global__ void __launch_bounds__(SC_THREADS) k_scan2_reduce(const uint32_t *__restrict__ a,
+                                                             const uint32_t *__restrict__ b, uint64_t len,
+                                                             unsigned long long *__restrict__ part)
+{
+    __shared__ unsigned long long wt[33];
+    const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * SC_THREADS + threadIdx.x;
+        if (i < len) s += ((unsigned long long)a[i] << 32) | b[i];
+    }
+    s = block_sum(s, wt);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan2_spine(unsigned long long *part, uint64_t nparts)
+{
+    __shared__ unsigned long long wt[33];
+    unsigned long long carry = 0;
+    for (uint64_t base = 0; base < nparts; base += SC_THREADS) {
+        const uint64_t i = base + threadIdx.x;
+        const unsigned long long x = i < nparts ? part[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = block_excl_scan(x, wt, &tot);
+        if (i < nparts) part[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan2_down(uint32_t *a, uint32_t *b, uint64_t len,
+                                                           const unsigned long long *__restrict__ part)
+{
+    __shared__ unsigned long long wt[33];
+    const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
+    unsigned long long carry = part[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SC_ITEMS; ++j) {
+        const uint64_t i = base + (uint64_t)j * SC_THREADS + threadIdx.x;
+        const unsigned long long x = i < len ? ((unsigned long long)a[i] << 32) | b[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = carry + block_excl_scan(x, wt, &tot);
+        if (i < len) {
+            a[i] = (uint32_t)(ex >> 32);
+            b[i] = (uint32_t)ex;
+        }
+        carry += tot;
+    }
+}
+
+uint64_t scan_scratch_elems(uint64_t len) { return 2 * (ceil_div(len, SC_CHUNK) + 1); }
+
+void scan_excl_pair(uint32_t *a, uint32_t *b, uint64_t len, uint32_t *scratch, cudaStream_t s)
+{
+    if (len == 0) return;
+    const uint64_t nb = ceil_div(len, SC_CHUNK);
+    unsigned long long *part = reinterpret_cast<unsigned long long *>(scratch);
+    k_scan2_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, b, len, part); note_launch();
+    k_scan2_spine<<<1, SC_THREADS, 0, s>>>(part, nb); note_launch();
+    k_scan2_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, b, len, part); note_launch();
+}
 
 void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s)
 {
