@@ -291,8 +291,11 @@ __global__ void __launch_bounds__(256) k_sample_keep(const uint64_t *__restrict_
     const bool count_in = !all && cand < n;
     const uint64_t nt = (m + RX_TILE - 1) / RX_TILE;
     uint32_t kept_total = 0;
+    // keep test of a full tile: (h >> 11) < thr  <=>  h < thr * 2^11 (thr < 2^53 here)
+    const uint64_t thr11 = all ? 0ull : thr << 11;
     for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         uint32_t c = 0;
+        const bool full = (tile + 1) * RX_TILE <= m;
         constexpr int SU = 4;  // edges per thread in flight
 #pragma unroll 1
         for (int j0 = 0; j0 < RX_ITEMS; j0 += SU) {
@@ -300,6 +303,13 @@ __global__ void __launch_bounds__(256) k_sample_keep(const uint64_t *__restrict_
             if (all) {
 #pragma unroll
                 for (int q = 0; q < SU; ++q) f[q] = tile * RX_TILE + (uint64_t)(j0 + q) * 256 + threadIdx.x < m;
+            } else if (full) {
+                const uint64_t *ot = orig + tile * RX_TILE + threadIdx.x;
+                uint64_t o[SU];
+#pragma unroll
+                for (int q = 0; q < SU; ++q) o[q] = ld_stream_u64(ot + (j0 + q) * 256);
+#pragma unroll
+                for (int q = 0; q < SU; ++q) f[q] = splitmix64(o[q] ^ seed_mix) < thr11;
             } else {
                 uint64_t o[SU];
 #pragma unroll
@@ -315,9 +325,9 @@ __global__ void __launch_bounds__(256) k_sample_keep(const uint64_t *__restrict_
             }
 #pragma unroll
             for (int q = 0; q < SU; ++q) {
-                const uint64_t i = tile * RX_TILE + (uint64_t)(j0 + q) * 256 + threadIdx.x;
                 const unsigned word = __ballot_sync(FULL, f[q]);
-                if (lane == 0 && i - lane < m) keepw[(i - lane) >> 5] = word;
+                const uint64_t w = tile * (RX_TILE / 32) + (uint64_t)(j0 + q) * 8 + (threadIdx.x >> 5);
+                if (lane == 0 && w * 32 < m) keepw[w] = word;
                 c += f[q];
             }
             if (count_in) {
