@@ -493,7 +493,7 @@ tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, 
     if (!b || !p || !seed) return TC_EINVAL;
     tc_status st = stage_params(b, p, seed);
     if (st != TC_OK) return st;
-    const uint32_t warp_maxes[3] = {64, 128, 256}, seg_ws[2] = {256, 512}, seg_bs[2] = {512, 1024};
+    const uint32_t warp_maxes[3] = {64, 128, 256}, seg_ws[2] = {256, 512}, seg_bs[2] = {256, 512};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();

@@ -23,15 +23,16 @@
 // Work items are (segment << 32 | owner); a segment is a run of the owner's
 // partner sequence (its out-list, then its in-list).  Owners
 // are bucketed by d+(x), which sizes their hash set: 2..256 (one warp per
-// item), 257..1024 (one block, 8192-slot table), > 1024 (one block, larger
-// table, or a binary search of the sorted row when even that is too
-// small).  Owners with d+ < 2 close no triangle.  Rows are stored padded to
+// item), 257..1024 (one 128-thread block, 4096-slot table, eight blocks per
+// SM so that one block's item setup overlaps the others' streaming), > 1024
+// (one block, larger table, or a binary search of the sorted row when even
+// that is too small).  Owners with d+ < 2 close no triangle.  Rows are stored padded to
 // 16 bytes (kernels.h), so the partners' lists stream as uint4 chunks.
 #include "kernels.h"
 
 namespace tcg {
 
-constexpr uint32_t SEG_B = 1024;     // largest partners per block item (IsectConfig::seg_b is capped here)
+constexpr uint32_t SEG_B = 512;      // largest partners per block item (IsectConfig::seg_b is capped here)
 constexpr uint32_t WARP_MAX = 256;   // largest warp-owner out-degree (IsectConfig::warp_max)
 constexpr uint32_t MID_MAX = 1024;
 constexpr uint32_t EMPTY = 0xffffffffu;
@@ -530,10 +531,10 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
 
 // ---------------------------------------------------------------- block items
 
-constexpr int PB_THREADS = 256;
+constexpr int PB_THREADS = 128;
 constexpr int PB_WARPS = PB_THREADS / 32;
 constexpr uint32_t PB_PER_THREAD = SEG_B / PB_THREADS;  // partner slots set up per thread (at most)
-constexpr uint32_t MID_TAB = 8192;                      // >= 8 * MID_MAX slots (dynamic shared memory)
+constexpr uint32_t MID_TAB = 4096;                      // >= 4 * MID_MAX slots (dynamic shared memory)
 constexpr uint32_t UNIT = 128;                          // chunks per unit of block streaming
 constexpr uint32_t PRE_CLS = 0x80000000u;               // class bit beside a partner's chunk prefix
 
@@ -597,7 +598,7 @@ __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, cons
 // counter, so they finish within one unit of each other.  The owner's hash
 // set sits in dynamic shared memory (tab_slots slots).
 template <bool DYN>
-__global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 4) k_probe_block(const uint32_t *__restrict__ ptrp,
+__global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 8) k_probe_block(const uint32_t *__restrict__ ptrp,
                                                                       const uint32_t *__restrict__ col,
                                                                       const uint32_t *__restrict__ rowptr,
                                                                       const uint32_t *__restrict__ olist,
@@ -738,7 +739,7 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
     k_probe_warp<<<152 * 4, PW_THREADS, 0, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr, b.inend, b.inlist,
                                                 b.items, wm, b.heavy, b.st, b.bv, b.cfg, b.core_base);
     note_launch();
-    k_probe_block<false><<<152 * 4, PB_THREADS, MID_TAB * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
+    k_probe_block<false><<<152 * 8, PB_THREADS, MID_TAB * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
                                                                    b.inend, b.inlist, b.items, wm,
                                                                    b.heavy, b.st, MID_TAB, b.items_cap, b.bv, b.cfg,
                                                                    b.core_base);

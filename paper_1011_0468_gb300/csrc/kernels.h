@@ -153,7 +153,7 @@ void build_rows(const RowsArgs &a, cudaStream_t s);
 // Schedule of the intersection kernels (isect.cu); any choice gives the same
 // counts.  warp_max: owners with 2 <= d+ <= warp_max are resolved by one warp
 // (32 .. 256); seg_w / seg_b: most partners per work item of the warp / block
-// kernels (seg_w in [SEG_MIN, 1024], seg_b in [256, 1024], powers of two);
+// kernels (seg_w in [SEG_MIN, 1024], seg_b in [256, 512], powers of two);
 // work_w / work_b: an owner of out-degree d gets items of the largest power
 // of two <= seg_w (seg_b) partners with partners * d <= work_w (work_b), but
 // at least SEG_MIN (256), which bounds the list entries an item streams.
@@ -161,7 +161,7 @@ constexpr uint32_t SEG_MIN = 64;
 struct IsectConfig {
     uint32_t warp_max = 256;
     uint32_t seg_w = 512;
-    uint32_t seg_b = 1024;
+    uint32_t seg_b = 512;
     uint32_t work_w = 1u << 14;
     uint32_t work_b = 1u << 19;
 };
