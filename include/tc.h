@@ -81,11 +81,18 @@ typedef struct {
 
 /* Optional device allocator used for every device allocation the library
    makes (for example a framework's caching allocator).  alloc returns NULL
-   on failure.  Pass NULLs to restore cudaMalloc/cudaFree.  Not thread-safe
-   with concurrent graph creation/destruction. */
+   on failure.  Pass NULLs to restore the default: a stream-ordered memory
+   pool of the library's own per device (cudaMallocFromPoolAsync /
+   cudaFreeAsync on the graph's stream, or cudaMalloc / cudaFree where no pool
+   can be made).  Not thread-safe with concurrent graph creation/destruction. */
 typedef void *(*tc_alloc_fn)(uint64_t bytes, void *stream, void *ctx);
 typedef void (*tc_free_fn)(void *ptr, void *stream, void *ctx);
 void tc_set_allocator(tc_alloc_fn alloc, tc_free_fn free_fn, void *ctx);
+
+/* The default pool keeps the memory of destroyed graphs for the next ones.
+   This synchronizes the current device and returns that memory to the
+   system.  TC_ECUDA on a CUDA error. */
+tc_status tc_release_cached_memory(void);
 
 /*
  * Build a graph from m_in uint32 pairs (Section 4.1 canonical simple graph).

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -18,12 +19,48 @@ tc_alloc_fn g_alloc = nullptr;
 tc_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
 
+// Default device memory: a stream-ordered pool of the library's own per
+// device.  Blocks are allocated and freed in order on the graph's stream, and
+// freed blocks stay in the pool for the next graph (no release threshold)
+// until tc_release_cached_memory.  Where a pool cannot be made, cudaMalloc.
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[64] = {};
+bool g_pool_failed[64] = {};
+
+cudaMemPool_t pool_of_current_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pool[dev] && !g_pool_failed[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        uint64_t keep = ~0ull;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess &&
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess) {
+            g_pool[dev] = pool;
+        } else {
+            cudaGetLastError();
+            g_pool_failed[dev] = true;
+        }
+    }
+    return g_pool[dev];
+}
+
 void *dev_alloc(uint64_t bytes, cudaStream_t s)
 {
     bytes = std::max<uint64_t>(bytes, 256);
     if (g_alloc) return g_alloc(bytes, s, g_alloc_ctx);
     void *p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaMemPool_t pool = pool_of_current_device();
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -35,6 +72,8 @@ void dev_free(void *p, cudaStream_t s)
     if (!p) return;
     if (g_free)
         g_free(p, s, g_alloc_ctx);
+    else if (pool_of_current_device())
+        cudaFreeAsync(p, s);
     else
         cudaFree(p);
 }
@@ -332,6 +371,17 @@ const char *tc_status_str(tc_status s)
 
 int tc_version(void) { return 100; }
 
+tc_status tc_release_cached_memory(void)
+{
+    cudaMemPool_t pool = pool_of_current_device();
+    if (!pool) return TC_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(pool, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    return TC_OK;
+}
+
 uint64_t tc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int edges_on_device,
@@ -368,7 +418,15 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     if (m_in > 0) {
         const uint32_t *dpairs = edges;
         void *tmp_pairs = nullptr;
-        if (!edges_on_device) {
+        // pinned host memory mapped into the device's address space is read
+        // in place by the first kernel (over the host link); other host
+        // memory is copied first
+        cudaPointerAttributes pa;
+        if (!edges_on_device && cudaPointerGetAttributes(&pa, edges) == cudaSuccess &&
+            pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+            dpairs = (const uint32_t *)pa.devicePointer;
+        } else if (!edges_on_device) {
+            cudaGetLastError();
             tmp_pairs = g->alloc(m_in * 8);
             if (!tmp_pairs) { free_graph(g); return TC_ENOMEM; }
             cudaMemcpyAsync(tmp_pairs, edges, m_in * 8, cudaMemcpyHostToDevice, s);

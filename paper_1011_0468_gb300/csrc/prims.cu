@@ -259,13 +259,24 @@ void radix_pass(const uint64_t *in, uint64_t n, int shift, int width, uint32_t *
 // Canonicalisation of raw pairs (graph creation).
 // ======================================================================
 
+// pairs may be device memory or pinned host memory mapped into the device's
+// address space (read once, one pair per lane; its predecessor comes from
+// the next lower lane).
+template <bool ALIGNED8>
 __global__ void k_canon_keys(const uint32_t *__restrict__ pairs, uint64_t m_in, uint32_t n,
                              uint64_t *__restrict__ keys, DevState *st)
 {
     unsigned bad = 0, unsorted = 0;
+    const unsigned lane = lane_id();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_in; i += stride) {
-        const uint2 e = make_uint2(pairs[2 * i], pairs[2 * i + 1]);  // 4-byte alignment suffices
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m_in; base += stride) {
+        const uint64_t i = base + lane;
+        uint2 e = make_uint2(0, 0);
+        if (i < m_in)
+            e = ALIGNED8 ? reinterpret_cast<const uint2 *>(pairs)[i] : make_uint2(pairs[2 * i], pairs[2 * i + 1]);
+        uint2 q = make_uint2(__shfl_up_sync(FULL, e.x, 1), __shfl_up_sync(FULL, e.y, 1));
+        if (lane == 0 && i > 0 && i < m_in) q = make_uint2(pairs[2 * i - 2], pairs[2 * i - 1]);
+        if (i >= m_in) continue;
         uint64_t k;
         if (e.x >= n || e.y >= n) {
             bad = 1;
@@ -282,7 +293,6 @@ __global__ void k_canon_keys(const uint32_t *__restrict__ pairs, uint64_t m_in, 
         if (e.x >= e.y) {
             unsorted++;
         } else if (i > 0) {
-            const uint2 q = make_uint2(pairs[2 * i - 2], pairs[2 * i - 1]);
             if (!(q.x < e.x || (q.x == e.x && q.y < e.y))) unsorted++;
         }
     }
@@ -296,7 +306,11 @@ void canon_keys(const uint32_t *pairs, uint64_t m_in, uint32_t n, uint64_t *keys
 {
     if (m_in == 0) return;
     const uint64_t blocks = std::min<uint64_t>(ceil_div(m_in, 256), 152ull * 16);
-    k_canon_keys<<<(unsigned)blocks, 256, 0, s>>>(pairs, m_in, n, keys, st); note_launch();
+    if ((reinterpret_cast<uintptr_t>(pairs) & 7u) == 0)
+        k_canon_keys<true><<<(unsigned)blocks, 256, 0, s>>>(pairs, m_in, n, keys, st);
+    else
+        k_canon_keys<false><<<(unsigned)blocks, 256, 0, s>>>(pairs, m_in, n, keys, st);
+    note_launch();
 }
 
 constexpr int UQ_THREADS = 1024;

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("tc_graph_export_edges", ctypes.c_int, [_vp, _u32p]),
     ("tc_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tc_version", ctypes.c_int, []),
+    ("tc_release_cached_memory", ctypes.c_int, []),
     ("tc_launch_count", ctypes.c_uint64, []),
     ("tc_count_noalloc", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
                                         ctypes.POINTER(tc_result), _vp]),
@@ -176,6 +177,12 @@ def tc_status_str(s: int) -> str:
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 _torch_hooks = None
+
+
+def release_cached_memory() -> None:
+    """Return to the system the device memory that the library's default pool
+    keeps from destroyed graphs (tc_release_cached_memory)."""
+    _check(lib().tc_release_cached_memory(), "tc_release_cached_memory")
 
 
 def use_torch_allocator(on: bool = True) -> None:

@@ -153,6 +153,27 @@ def test_device_input(tc):
         assert_same(g.count(0.5, 5), oracle.run(want_edges, n, 0.5, 5))
 
 
+def test_pinned_host_input(tc):
+    """Pinned host pairs are read in place by the device (8-byte aligned, and
+    4 bytes off alignment), raw and already canonical."""
+    import torch
+    rng = np.random.default_rng(9)
+    n = 4000
+    raw = rng.integers(0, n, size=(70_000, 2)).astype(np.uint32)
+    canon = oracle.canonicalize(raw, n)
+    for edges in (raw, canon):
+        want_edges = oracle.canonicalize(edges, n)
+        buf = torch.zeros(2 * len(edges) + 1, dtype=torch.int32).pin_memory()
+        for off in (0, 1):  # in uint32 units
+            buf[off:off + 2 * len(edges)] = torch.from_numpy(edges.reshape(-1).view(np.int32))
+            g = tc.Graph.from_address(buf.data_ptr() + 4 * off, len(edges), n, on_device=False)
+            try:
+                assert np.array_equal(g.export_edges(), want_edges), off
+                assert_same(g.count(0.7, 3), oracle.run(want_edges, n, 0.7, 3))
+            finally:
+                g.close()
+
+
 def test_empty_and_tiny(tc):
     for edges, n in ((np.zeros((0, 2), np.uint32), 1), (np.zeros((0, 2), np.uint32), 100_000),
                      (np.array([[0, 1]], np.uint32), 2), (gen.complete(3), 3)):
