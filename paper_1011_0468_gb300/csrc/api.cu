@@ -406,14 +406,17 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     }
     g->st = (DevState *)g->alloc(sizeof(DevState));
     g->res_dev = (tc_result *)g->alloc(sizeof(tc_result));
-    if (!g->st || !g->res_dev) {
+    g->deg = (uint32_t *)g->alloc((uint64_t)n * 4);
+    if (!g->st || !g->res_dev || !g->deg) {
         free_graph(g);
         return TC_ENOMEM;
     }
     cudaMemsetAsync(g->st, 0, sizeof(DevState), s);
+    cudaMemsetAsync(g->deg, 0, (size_t)n * 4, s);
 
     // ---- canonical keys
     uint64_t m = 0;
+    bool deg_ready = m_in == 0;  // g->deg holds the full degrees
     uint64_t *canon = nullptr;  // canonical keys (original ids), sorted [m]
     if (m_in > 0) {
         const uint32_t *dpairs = edges;
@@ -434,7 +437,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
         }
         uint64_t *keys = (uint64_t *)g->alloc(m_in * 8);
         if (!keys) { free_graph(g); return TC_ENOMEM; }
-        canon_keys(dpairs, m_in, n, keys, g->st, s);
+        canon_keys(dpairs, m_in, n, keys, g->st, s, g->deg);  // full degrees if the list is canonical
         cudaMemcpyAsync(g->st_host, g->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); free_graph(g); return TC_ECUDA; }
         if (tmp_pairs) g->release(tmp_pairs);
@@ -442,6 +445,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
         if (g->st_host->unsorted == 0) {
             canon = keys;  // already canonical: every pair u < v, strictly increasing
             m = m_in;
+            deg_ready = true;
         } else {
             // sort by (u, v) on the used bits only, then drop repeats/self-loops
             uint64_t *keys2 = (uint64_t *)g->alloc(m_in * 8);
@@ -480,7 +484,6 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     g->perm = (uint32_t *)g->alloc((uint64_t)n * 4);
     g->rank = (uint32_t *)g->alloc((uint64_t)n * 4);
     g->inlist = (uint2 *)g->alloc(m1 * 8);
-    g->deg = (uint32_t *)g->alloc((uint64_t)n * 4);
     g->hist = (uint32_t *)g->alloc(hist_len * 4);
     g->scan = (uint32_t *)g->alloc(scan_scratch_elems(std::max<uint64_t>(hist_len, (uint64_t)n + 2)) * 4);
     if (!g->rel || !g->orig || !g->perm || !g->rank || !g->inlist || !g->deg || !g->hist || !g->scan) {
@@ -495,7 +498,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
             return TC_ENOMEM;
         }
         const RelabelScratch sc{reinterpret_cast<uint64_t *>(g->inlist), kB, vA, vB, g->deg, g->hist, g->scan};
-        relabel(canon, m, n, nullptr, 0, Relabeled{g->rel, g->orig, g->perm, g->rank}, sc, s);
+        relabel(canon, m, n, nullptr, 0, Relabeled{g->rel, g->orig, g->perm, g->rank}, sc, s, deg_ready);
         if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); free_graph(g); return TC_ECUDA; }
         g->release(kB);
         g->release(vA);

@@ -22,11 +22,17 @@ namespace tcg {
 
 __global__ void k_full_degree(const uint64_t *__restrict__ ekey, uint64_t m, uint32_t *__restrict__ deg)
 {
+    const unsigned lane = lane_id();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        const uint64_t k = ekey[i];
-        atomicAdd(deg + (k >> 32), 1u);
-        atomicAdd(deg + (uint32_t)k, 1u);
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m; base += stride) {
+        const uint64_t i = base + lane;
+        const uint64_t k = i < m ? ekey[i] : ~0ull;
+        const uint32_t u = (uint32_t)(k >> 32);
+        const unsigned peers = __match_any_sync(FULL, u);  // keys are sorted: runs of a lower endpoint
+        if (i < m) {
+            if (lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(deg + u, (unsigned)__popc(peers));
+            atomicAdd(deg + (uint32_t)k, 1u);
+        }
     }
 }
 
@@ -111,12 +117,14 @@ static int bits_of(uint64_t x)
 }
 
 uint64_t *relabel(const uint64_t *ekey, uint64_t m, uint32_t n, const uint32_t *voff, uint32_t k,
-                  const Relabeled &out, const RelabelScratch &sc, cudaStream_t s)
+                  const Relabeled &out, const RelabelScratch &sc, cudaStream_t s, bool deg_ready)
 {
-    cudaMemsetAsync(sc.deg, 0, (size_t)n * 4, s);
-    if (m > 0) {
-        k_full_degree<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(ekey, m, sc.deg);
-        note_launch();
+    if (!deg_ready) {
+        cudaMemsetAsync(sc.deg, 0, (size_t)n * 4, s);
+        if (m > 0) {
+            k_full_degree<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(ekey, m, sc.deg);
+            note_launch();
+        }
     }
     k_vertex_items<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(sc.deg, n, voff, k, sc.vA);
     note_launch();

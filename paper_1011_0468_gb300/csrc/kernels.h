@@ -65,9 +65,11 @@ __device__ __forceinline__ PaddedRow padded_row(const uint32_t *__restrict__ ptr
 
 // Canonical keys from raw pairs: (min << 32 | max), self-loops become
 // ~0ull; endpoints >= n raise ERR_ENDPOINT; pairs that are not strictly
-// increasing in order are counted into st->unsorted.
-void canon_keys(const uint32_t *pairs, uint64_t m_in, uint32_t n, uint64_t *keys, DevState *st,
-                cudaStream_t s);
+// increasing in order are counted into st->unsorted.  With deg (zeroed, [n]),
+// also counts the endpoints of the valid pairs: the full degrees when
+// st->unsorted stays 0.
+void canon_keys(const uint32_t *pairs, uint64_t m_in, uint32_t n, uint64_t *keys, DevState *st, cudaStream_t s,
+                uint32_t *deg = nullptr);
 
 // Stable removal of repeats and ~0ull from sorted keys; the count goes to
 // st->m_canon.  tile_cnt holds ceil(m_in / RX_TILE) + 1 uint32.
@@ -91,9 +93,10 @@ struct RelabelScratch {
     uint32_t *hist;     // radix histograms for max(m, n) items
     uint32_t *scan;     // scan scratch for those
 };
-// voff / k: batch union offsets (k = 0: one graph).  Returns out.rel.
+// voff / k: batch union offsets (k = 0: one graph).  deg_ready: sc.deg
+// already holds the full degrees (from canon_keys).  Returns out.rel.
 uint64_t *relabel(const uint64_t *ekey, uint64_t m, uint32_t n, const uint32_t *voff, uint32_t k,
-                  const Relabeled &out, const RelabelScratch &sc, cudaStream_t s);
+                  const Relabeled &out, const RelabelScratch &sc, cudaStream_t s, bool deg_ready = false);
 
 // The sampled, oriented CSR of one count (single graph or batch union).
 struct RowsArgs {

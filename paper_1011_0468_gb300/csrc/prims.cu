@@ -261,10 +261,12 @@ void radix_pass(const uint64_t *in, uint64_t n, int shift, int width, uint32_t *
 
 // pairs may be device memory or pinned host memory mapped into the device's
 // address space (read once, one pair per lane; its predecessor comes from
-// the next lower lane).
+// the next lower lane).  With deg, also the degree of every endpoint of a
+// valid pair (one atomic per run of a lower endpoint in a warp): the full
+// degrees when the list turns out canonical.
 template <bool ALIGNED8>
 __global__ void k_canon_keys(const uint32_t *__restrict__ pairs, uint64_t m_in, uint32_t n,
-                             uint64_t *__restrict__ keys, DevState *st)
+                             uint64_t *__restrict__ keys, DevState *st, uint32_t *__restrict__ deg)
 {
     unsigned bad = 0, unsorted = 0;
     const unsigned lane = lane_id();
@@ -276,6 +278,15 @@ __global__ void k_canon_keys(const uint32_t *__restrict__ pairs, uint64_t m_in, 
             e = ALIGNED8 ? reinterpret_cast<const uint2 *>(pairs)[i] : make_uint2(pairs[2 * i], pairs[2 * i + 1]);
         uint2 q = make_uint2(__shfl_up_sync(FULL, e.x, 1), __shfl_up_sync(FULL, e.y, 1));
         if (lane == 0 && i > 0 && i < m_in) q = make_uint2(pairs[2 * i - 2], pairs[2 * i - 1]);
+        if (deg) {
+            const bool ok = i < m_in && e.x < n && e.y < n && e.x != e.y;
+            const uint32_t u = ok ? min(e.x, e.y) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(FULL, u);
+            if (ok) {
+                if (lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(deg + u, (unsigned)__popc(peers));
+                atomicAdd(deg + max(e.x, e.y), 1u);
+            }
+        }
         if (i >= m_in) continue;
         uint64_t k;
         if (e.x >= n || e.y >= n) {
@@ -301,15 +312,15 @@ __global__ void k_canon_keys(const uint32_t *__restrict__ pairs, uint64_t m_in, 
     if (unsorted && lane_id() == 0) atomicAdd(&st->unsorted, unsorted);
 }
 
-void canon_keys(const uint32_t *pairs, uint64_t m_in, uint32_t n, uint64_t *keys, DevState *st,
-                cudaStream_t s)
+void canon_keys(const uint32_t *pairs, uint64_t m_in, uint32_t n, uint64_t *keys, DevState *st, cudaStream_t s,
+                uint32_t *deg)
 {
     if (m_in == 0) return;
     const uint64_t blocks = std::min<uint64_t>(ceil_div(m_in, 256), 152ull * 16);
     if ((reinterpret_cast<uintptr_t>(pairs) & 7u) == 0)
-        k_canon_keys<true><<<(unsigned)blocks, 256, 0, s>>>(pairs, m_in, n, keys, st);
+        k_canon_keys<true><<<(unsigned)blocks, 256, 0, s>>>(pairs, m_in, n, keys, st, deg);
     else
-        k_canon_keys<false><<<(unsigned)blocks, 256, 0, s>>>(pairs, m_in, n, keys, st);
+        k_canon_keys<false><<<(unsigned)blocks, 256, 0, s>>>(pairs, m_in, n, keys, st, deg);
     note_launch();
 }
 
