@@ -69,17 +69,6 @@ __global__ void k_rank_of(const uint64_t *__restrict__ sorted, uint32_t n, uint3
     }
 }
 
-__global__ void k_relabel_keys(const uint64_t *__restrict__ ekey, uint64_t m, const uint32_t *__restrict__ rank,
-                               uint64_t *__restrict__ rel)
-{
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        const uint64_t k = ekey[i];
-        const uint32_t a = __ldg(rank + (k >> 32)), b = __ldg(rank + (uint32_t)k);
-        rel[i] = ((uint64_t)min(a, b) << 32) | max(a, b);
-    }
-}
-
 __global__ void k_original_keys(const uint64_t *__restrict__ rel, uint64_t m, const uint32_t *__restrict__ perm,
                                 uint64_t *__restrict__ orig)
 {
@@ -116,6 +105,179 @@ static int bits_of(uint64_t x)
     return b;
 }
 
+// ---- keys in rank order without a key sort: every canonical edge goes to
+// the row of its lower rank (rows counted and placed with atomics), then
+// each row is sorted by its higher rank: a bitonic network in registers for
+// rows of up to 16 entries, a warp in shared memory up to 1024, a block for
+// the rest.
+
+__device__ __forceinline__ void rank_pair(uint64_t key, const uint32_t *__restrict__ rank, uint32_t &u, uint32_t &v)
+{
+    const uint32_t a = __ldg(rank + (key >> 32)), b = __ldg(rank + (uint32_t)key);
+    u = min(a, b);
+    v = max(a, b);
+}
+
+__global__ void k_row_count(const uint64_t *__restrict__ ekey, uint64_t m, const uint32_t *__restrict__ rank,
+                            uint32_t *__restrict__ cnt)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        uint32_t u, v;
+        rank_pair(ekey[i], rank, u, v);
+        atomicAdd(cnt + u, 1u);
+    }
+}
+
+// cur[u] starts at the row's first slot.
+__global__ void k_row_place(const uint64_t *__restrict__ ekey, uint64_t m, const uint32_t *__restrict__ rank,
+                            uint32_t *__restrict__ cur, uint64_t *__restrict__ rows)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        uint32_t u, v;
+        rank_pair(ekey[i], rank, u, v);
+        rows[atomicAdd(cur + u, 1u)] = ((uint64_t)u << 32) | v;
+    }
+}
+
+constexpr uint32_t ROW_SMALL = 16, ROW_MID = 1024, ROW_SMEM = 32768;
+
+// Ascending bitonic network over N (a power of two) register values.
+template <int N>
+__device__ __forceinline__ void bitonic_regs(uint32_t (&a)[N])
+{
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const uint32_t x = a[i], y = a[l];
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[l] = x;
+                    }
+                }
+            }
+}
+
+template <int N>
+__device__ __forceinline__ void sort_row_regs(const uint64_t *__restrict__ rows, uint32_t b, uint32_t len, uint32_t u,
+                                              uint64_t *__restrict__ rel)
+{
+    uint32_t a[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = (uint32_t)i < len ? (uint32_t)rows[b + i] : 0xffffffffu;
+    bitonic_regs<N>(a);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if ((uint32_t)i < len) rel[b + i] = ((uint64_t)u << 32) | a[i];
+}
+
+// Rows of up to ROW_SMALL entries, one thread each; longer rows are listed
+// (mid rows from the front of list, the rest from its back; cnt[0], cnt[1]).
+__global__ void k_rows_small(const uint64_t *__restrict__ rows, const uint32_t *__restrict__ frow, uint32_t n,
+                             uint64_t *__restrict__ rel, uint32_t *__restrict__ list, uint32_t cap,
+                             uint32_t *__restrict__ cnt)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const uint32_t b = frow[x], len = frow[x + 1] - b, u = (uint32_t)x;
+        if (len == 0) continue;
+        if (len == 1)
+            rel[b] = rows[b];
+        else if (len <= 8)
+            sort_row_regs<8>(rows, b, len, u, rel);
+        else if (len <= ROW_SMALL)
+            sort_row_regs<16>(rows, b, len, u, rel);
+        else if (len <= ROW_MID)
+            list[atomicAdd(cnt, 1u)] = u;
+        else
+            list[cap - 1 - atomicAdd(cnt + 1, 1u)] = u;
+    }
+}
+
+// Ascending bitonic sort of a[0, P) (P a power of two) by `threads`
+// cooperating threads with index t; sync() between steps.
+template <class Sync>
+__device__ __forceinline__ void bitonic_shared(uint32_t *a, uint32_t P, uint32_t t, uint32_t threads, Sync sync)
+{
+    for (uint32_t k = 2; k <= P; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = t; i < P; i += threads) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const uint32_t x = a[i], y = a[l];
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[l] = x;
+                    }
+                }
+            }
+            sync();
+        }
+}
+
+struct WarpSync {
+    __device__ void operator()() const { __syncwarp(); }
+};
+struct BlockSync {
+    __device__ void operator()() const { __syncthreads(); }
+};
+
+__device__ __forceinline__ uint32_t pow2_at_least(uint32_t x)
+{
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Listed rows of up to ROW_MID entries: one warp each, in shared memory.
+__global__ void __launch_bounds__(256) k_rows_mid(const uint64_t *__restrict__ rows, const uint32_t *__restrict__ frow,
+                                                  const uint32_t *__restrict__ list, const uint32_t *__restrict__ cnt,
+                                                  uint64_t *__restrict__ rel)
+{
+    __shared__ uint32_t s_v[8][ROW_MID];
+    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
+    uint32_t *a = s_v[w];
+    const uint32_t rows_n = cnt[0];
+    for (uint32_t r = blockIdx.x * 8 + w; r < rows_n; r += gridDim.x * 8) {
+        const uint32_t u = list[r], b = frow[u], len = frow[u + 1] - b, P = pow2_at_least(len);
+        for (uint32_t i = lane; i < P; i += 32) a[i] = i < len ? (uint32_t)rows[b + i] : 0xffffffffu;
+        __syncwarp();
+        bitonic_shared(a, P, lane, 32, WarpSync());
+        for (uint32_t i = lane; i < len; i += 32) rel[b + i] = ((uint64_t)u << 32) | a[i];
+        __syncwarp();
+    }
+}
+
+// Listed rows longer than ROW_MID: one block each, in dynamic shared memory
+// up to ROW_SMEM entries, else in global memory (the row's 8 * len bytes of
+// gscratch hold its padded 32-bit values: the padded length is below 2 len).
+__global__ void __launch_bounds__(1024) k_rows_large(const uint64_t *__restrict__ rows,
+                                                     const uint32_t *__restrict__ frow,
+                                                     const uint32_t *__restrict__ list, uint32_t cap,
+                                                     const uint32_t *__restrict__ cnt, uint64_t *__restrict__ rel,
+                                                     uint32_t *__restrict__ gscratch)
+{
+    extern __shared__ uint32_t s_big[];
+    const uint32_t rows_n = cnt[1];
+    for (uint32_t r = blockIdx.x; r < rows_n; r += gridDim.x) {
+        const uint32_t u = list[cap - 1 - r], b = frow[u], len = frow[u + 1] - b, P = pow2_at_least(len);
+        uint32_t *a = P <= ROW_SMEM ? s_big : gscratch + 2 * (uint64_t)b;
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) a[i] = i < len ? (uint32_t)rows[b + i] : 0xffffffffu;
+        __syncthreads();
+        bitonic_shared(a, P, threadIdx.x, blockDim.x, BlockSync());  // orders global writes of the block too
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) rel[b + i] = ((uint64_t)u << 32) | a[i];
+        __syncthreads();
+    }
+}
+
 uint64_t *relabel(const uint64_t *ekey, uint64_t m, uint32_t n, const uint32_t *voff, uint32_t k,
                   const Relabeled &out, const RelabelScratch &sc, cudaStream_t s, bool deg_ready)
 {
@@ -134,12 +296,35 @@ uint64_t *relabel(const uint64_t *ekey, uint64_t m, uint32_t n, const uint32_t *
     k_rank_of<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(sorted, n, out.perm, out.rank);
     note_launch();
     if (m == 0) return out.rel;
-    k_relabel_keys<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(ekey, m, out.rank, sc.kA);
+    // rows in rank order: offsets (vB), cursors (vA), unsorted rows in
+    // out.orig (ekey may be out.rel), sorted into out.rel; the lists of long
+    // rows go to hist (m / 17 + 1 <= its length), their counts to scan
+    uint32_t *frow = reinterpret_cast<uint32_t *>(sc.vB), *cur = reinterpret_cast<uint32_t *>(sc.vA);
+    cudaMemsetAsync(frow, 0, ((size_t)n + 1) * 4, s);
+    k_row_count<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(ekey, m, out.rank, frow);
     note_launch();
-    const int nb = bits_of(n);
-    uint64_t *r = sort_bits(sc.kA, sc.kB, m, 0, nb, sc.hist, sc.scan, s);
-    r = sort_bits(r, r == sc.kA ? sc.kB : sc.kA, m, 32, 32 + nb, sc.hist, sc.scan, s);
-    cudaMemcpyAsync(out.rel, r, m * 8, cudaMemcpyDeviceToDevice, s);
+    scan_excl_u32(frow, (uint64_t)n + 1, nullptr, sc.scan, s);
+    cudaMemcpyAsync(cur, frow, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+    k_row_place<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(ekey, m, out.rank, cur, out.orig);
+    note_launch();
+    const uint32_t cap = (uint32_t)(m / (ROW_SMALL + 1) + 1);
+    cudaMemsetAsync(sc.scan, 0, 8, s);
+    k_rows_small<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(out.orig, frow, n, out.rel, sc.hist, cap, sc.scan);
+    note_launch();
+    k_rows_mid<<<152 * 8, 256, 0, s>>>(out.orig, frow, sc.hist, sc.scan, out.rel);
+    note_launch();
+    static bool large_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !large_set[dev]) {
+        if (cudaFuncSetAttribute(k_rows_large, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(ROW_SMEM * 4)) ==
+                cudaSuccess &&
+            dev >= 0 && dev < 64)
+            large_set[dev] = true;
+    }
+    k_rows_large<<<152, 1024, ROW_SMEM * 4, s>>>(out.orig, frow, sc.hist, cap, sc.scan, out.rel,
+                                                  reinterpret_cast<uint32_t *>(sc.kB));
+    note_launch();
     k_original_keys<<<grid_for(m, 256, 152 * 16), 256, 0, s>>>(out.rel, m, out.perm, out.orig);
     note_launch();
     return out.rel;
