@@ -118,14 +118,19 @@ __device__ __forceinline__ void rank_pair(uint64_t key, const uint32_t *__restri
     v = max(a, b);
 }
 
+// Keys come grouped by their original source, whose rank is the lower one
+// for most of its edges: one atomic per run of a row in a warp.
 __global__ void k_row_count(const uint64_t *__restrict__ ekey, uint64_t m, const uint32_t *__restrict__ rank,
                             uint32_t *__restrict__ cnt)
 {
+    const unsigned lane = lane_id();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint32_t u, v;
-        rank_pair(ekey[i], rank, u, v);
-        atomicAdd(cnt + u, 1u);
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m; base += stride) {
+        const uint64_t i = base + lane;
+        uint32_t u = 0xffffffffu, v;
+        if (i < m) rank_pair(ekey[i], rank, u, v);
+        const unsigned grp = __match_any_sync(FULL, u);
+        if (i < m && lane == (unsigned)(__ffs(grp) - 1)) atomicAdd(cnt + u, (unsigned)__popc(grp));
     }
 }
 
@@ -133,11 +138,18 @@ __global__ void k_row_count(const uint64_t *__restrict__ ekey, uint64_t m, const
 __global__ void k_row_place(const uint64_t *__restrict__ ekey, uint64_t m, const uint32_t *__restrict__ rank,
                             uint32_t *__restrict__ cur, uint64_t *__restrict__ rows)
 {
+    const unsigned lane = lane_id();
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint32_t u, v;
-        rank_pair(ekey[i], rank, u, v);
-        rows[atomicAdd(cur + u, 1u)] = ((uint64_t)u << 32) | v;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m; base += stride) {
+        const uint64_t i = base + lane;
+        uint32_t u = 0xffffffffu, v = 0;
+        if (i < m) rank_pair(ekey[i], rank, u, v);
+        const unsigned grp = __match_any_sync(FULL, u);
+        const int lead = __ffs(grp) - 1;
+        uint32_t q = 0;
+        if (i < m && (int)lane == lead) q = atomicAdd(cur + u, (unsigned)__popc(grp));
+        q = __shfl_sync(FULL, q, lead) + __popc(grp & lanemask_lt());
+        if (i < m) rows[q] = ((uint64_t)u << 32) | v;
     }
 }
 
@@ -223,9 +235,6 @@ __device__ __forceinline__ void bitonic_shared(uint32_t *a, uint32_t P, uint32_t
         }
 }
 
-struct WarpSync {
-    __device__ void operator()() const { __syncwarp(); }
-};
 struct BlockSync {
     __device__ void operator()() const { __syncthreads(); }
 };
@@ -237,22 +246,82 @@ __device__ __forceinline__ uint32_t pow2_at_least(uint32_t x)
     return p;
 }
 
-// Listed rows of up to ROW_MID entries: one warp each, in shared memory.
+// Ascending bitonic sort of P = 32 V values held by a warp: value t of lane
+// l sits at position l + 32 t.  Partners less than 32 apart are exchanged by
+// shuffles, the others inside a lane's registers.
+template <int V>
+__device__ __forceinline__ void bitonic_warp(uint32_t (&a)[V])
+{
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32 * V; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int jt = j / 32;
+#pragma unroll
+                for (int t = 0; t < V; ++t) {
+                    if ((t & jt) == 0) {
+                        const bool up = (((uint32_t)lane + 32u * t) & (uint32_t)k) == 0;
+                        const uint32_t x = a[t], y = a[t | jt];
+                        if ((x > y) == up) {
+                            a[t] = y;
+                            a[t | jt] = x;
+                        }
+                    }
+                }
+            } else {
+                const bool lower = (lane & (unsigned)j) == 0;
+#pragma unroll
+                for (int t = 0; t < V; ++t) {
+                    const bool up = (((uint32_t)lane + 32u * t) & (uint32_t)k) == 0;
+                    const uint32_t o = __shfl_xor_sync(FULL, a[t], j);
+                    a[t] = (lower == up) ? min(a[t], o) : max(a[t], o);
+                }
+            }
+        }
+}
+
+template <int V>
+__device__ __forceinline__ void sort_row_warp(const uint64_t *__restrict__ rows, uint32_t b, uint32_t len, uint32_t u,
+                                              uint64_t *__restrict__ rel)
+{
+    const unsigned lane = lane_id();
+    uint32_t a[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+        const uint32_t i = lane + 32u * t;
+        a[t] = i < len ? (uint32_t)rows[b + i] : 0xffffffffu;
+    }
+    bitonic_warp<V>(a);
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+        const uint32_t i = lane + 32u * t;
+        if (i < len) rel[b + i] = ((uint64_t)u << 32) | a[t];
+    }
+}
+
+// Listed rows of up to ROW_MID entries: one warp each, in registers.
 __global__ void __launch_bounds__(256) k_rows_mid(const uint64_t *__restrict__ rows, const uint32_t *__restrict__ frow,
                                                   const uint32_t *__restrict__ list, const uint32_t *__restrict__ cnt,
                                                   uint64_t *__restrict__ rel)
 {
-    __shared__ uint32_t s_v[8][ROW_MID];
-    const unsigned lane = lane_id(), w = threadIdx.x >> 5;
-    uint32_t *a = s_v[w];
+    static_assert(ROW_MID == 32 * 32, "at most 32 values per lane");
     const uint32_t rows_n = cnt[0];
-    for (uint32_t r = blockIdx.x * 8 + w; r < rows_n; r += gridDim.x * 8) {
-        const uint32_t u = list[r], b = frow[u], len = frow[u + 1] - b, P = pow2_at_least(len);
-        for (uint32_t i = lane; i < P; i += 32) a[i] = i < len ? (uint32_t)rows[b + i] : 0xffffffffu;
-        __syncwarp();
-        bitonic_shared(a, P, lane, 32, WarpSync());
-        for (uint32_t i = lane; i < len; i += 32) rel[b + i] = ((uint64_t)u << 32) | a[i];
-        __syncwarp();
+    for (uint32_t r = blockIdx.x * 8 + (threadIdx.x >> 5); r < rows_n; r += gridDim.x * 8) {
+        const uint32_t u = list[r], b = frow[u], len = frow[u + 1] - b;
+        if (len <= 32)
+            sort_row_warp<1>(rows, b, len, u, rel);
+        else if (len <= 64)
+            sort_row_warp<2>(rows, b, len, u, rel);
+        else if (len <= 128)
+            sort_row_warp<4>(rows, b, len, u, rel);
+        else if (len <= 256)
+            sort_row_warp<8>(rows, b, len, u, rel);
+        else if (len <= 512)
+            sort_row_warp<16>(rows, b, len, u, rel);
+        else
+            sort_row_warp<32>(rows, b, len, u, rel);
     }
 }
 
