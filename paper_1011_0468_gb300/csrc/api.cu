@@ -270,6 +270,7 @@ void enqueue_sample(tc_graph *g, const RowsArgs &ra)
     sample_rows(ra, g->stream);
     CountBuffers b = buffers_of(g);
     b.all_kept = ra.thr >= (1ull << 53);
+    b.core_base = ra.core_base;
     partition(b, g->stream);
 }
 
@@ -300,16 +301,19 @@ void ring_times(tc_graph *g, uint64_t count, float *ms)
 tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bool timing)
 {
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
-    const RowsArgs ra = rows_of(g, seed_mix, thr, sample_floor(g->m, p, thr));
+    RowsArgs ra = rows_of(g, seed_mix, thr, sample_floor(g->m, p, thr));
     // the core block pays off once the sample is large: its cost is fixed,
     // the intersections it replaces grow with the sample
     const CoreBuffers *core = (g->core.hb.hcap && p * (double)g->m >= CORE_MIN_EDGES) ? &g->core : nullptr;
+    ra.heavy = g->hb.hcap ? g->heavy : nullptr;
+    if (core) ra.core_base = core->base;
     CountBuffers b = buffers_of(g);
     if (core) b.core_base = core->base;
     record(g, timing, 0);
     enqueue_sample(g, ra);
     record(g, timing, 1);
     if (g->m > 0) {
+        if (g->hb.hcap) heavy_decide(b, g->hb, core, g->stream);
         build_rows(ra, g->stream);
         if (g->hb.hcap) heavy_prepare(b, g->hb, core, g->stream);
         build_items(b, g->stream);

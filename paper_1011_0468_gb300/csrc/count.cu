@@ -60,9 +60,10 @@ __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevSta
 // counter of spread then becomes its vertex's in-list cursor (the static
 // reservation inres).
 __global__ void k_partition_cand(const uint32_t *__restrict__ dplus, uint32_t *__restrict__ spread, int hbits,
-                                 const uint32_t *__restrict__ inres, bool all_kept, uint32_t n, DevState *st,
-                                 uint32_t *__restrict__ deg, uint8_t *__restrict__ heavy)
+                                 const uint32_t *__restrict__ inres, bool all_kept, uint32_t n, uint32_t core_base,
+                                 DevState *st, uint32_t *__restrict__ deg, uint8_t *__restrict__ heavy)
 {
+    uint32_t below = 0;  // heavy vertices below the dense core's base
     const unsigned long long mp = st->m_sampled;
     const uint32_t cand = st->cand_all ? 0u : st->cand_lo;
     uint32_t h = 0, lim = 0;
@@ -80,7 +81,10 @@ __global__ void k_partition_cand(const uint32_t *__restrict__ dplus, uint32_t *_
         deg[u] = d;
         heavy[u] = f;
         h += f;
+        below += f && u < core_base;
     }
+    below = warp_sum(below);
+    if (lane_id() == 0 && below) atomicAdd(&st->heavy_below, below);
     if (blockIdx.x == 0 && threadIdx.x == 0) lim = max(lim, min(cand, n));
     if (lim) atomicMax(&st->light_lim, lim);
     h = warp_sum(h);
@@ -92,7 +96,8 @@ void partition(const CountBuffers &b, cudaStream_t s)
     if (b.static_rows) {
         k_partition_cand<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.spread,
                                                                      hot_bits(b.n), b.inptr,
-                                                                     b.all_kept, b.n, b.st, b.deg, b.heavy);
+                                                                     b.all_kept, b.n, b.core_base, b.st, b.deg,
+                                                                     b.heavy);
     } else {
         k_partition<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.deg, b.n, b.st, b.heavy, b.bv);
     }

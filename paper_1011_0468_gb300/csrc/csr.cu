@@ -722,6 +722,10 @@ struct ScatterArgs {
     uint32_t *colp, *cursor, *olist, *ocnt;
     uint2 *inlist;
     int hbits;
+    // pairs left to the dense blocks: heavy flags and light_lim when the
+    // heavy block runs (else lim = EMPTY), the core's base when it runs
+    const uint8_t *heavy;
+    uint32_t lim, core_lo;
 };
 
 __device__ __forceinline__ void scatter_edge(const ScatterArgs &a, bool live, uint64_t i, uint32_t k, unsigned lt)
@@ -734,7 +738,9 @@ __device__ __forceinline__ void scatter_edge(const ScatterArgs &a, bool live, ui
         v = (uint32_t)r;
         const uint32_t pos = k + __ldg(a.padoff + u);
         a.colp[pos] = v;
-        if (k + 1 < __ldg(a.rowptr + u + 1)) {  // so d+(u) >= 2
+        const bool dense_pair =
+            u >= a.core_lo || (v >= a.lim && __ldg(a.heavy + u) && __ldg(a.heavy + v));  // see ScatterArgs
+        if (!dense_pair && k + 1 < __ldg(a.rowptr + u + 1)) {  // so d+(u) >= 2
             const uint32_t du = __ldg(a.dplus + u), dv = __ldg(a.dplus + v);
             if (du < dv) {
                 const uint32_t q = atomicAdd(a.cursor + hot_index(v, a.hbits), 1u);
@@ -789,12 +795,16 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
                                                       const uint32_t *__restrict__ dplus,
                                                       uint32_t *__restrict__ colp, uint32_t *__restrict__ cursor,
                                                       int hbits, uint2 *__restrict__ inlist,
-                                                      uint32_t *__restrict__ olist, uint32_t *__restrict__ ocnt)
+                                                      uint32_t *__restrict__ olist, uint32_t *__restrict__ ocnt,
+                                                      const uint8_t *__restrict__ heavy, uint32_t core_base,
+                                                      const DevState *st)
 {
     constexpr int WORDS = RX_TILE / 32;  // 128 keep words per tile
     __shared__ uint32_t s_word[WORDS], s_pre[WORDS];
     __shared__ uint32_t wt[33];
-    const ScatterArgs a{rel, padoff, rowptr, dplus, colp, cursor, olist, ocnt, inlist, hbits};
+    const bool dense = heavy && st->dense;
+    const ScatterArgs a{rel,   padoff, rowptr, dplus, colp, cursor, olist, ocnt, inlist, hbits, heavy,
+                        dense ? st->light_lim : 0xffffffffu, dense && st->core_on ? core_base : 0xffffffffu};
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     const uint64_t nt = (m + RX_TILE - 1) / RX_TILE;
@@ -882,7 +892,8 @@ void build_rows(const RowsArgs &a, cudaStream_t s)
         const uint64_t nt = ceil_div(a.m, RX_TILE);
         k_rows_scatter<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.m, a.keepw, a.tile_cnt, a.ptrp, a.rowptr,
                                                                   a.deg, a.colp, a.spread, hb,
-                                                                  a.inlist, a.olist, a.ocnt);
+                                                                  a.inlist, a.olist, a.ocnt, a.heavy, a.core_base,
+                                                                  a.st);
         note_launch();
     }
     k_pad_finish<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp, a.colp, a.spread, hb, a.inend);

@@ -26,10 +26,9 @@ namespace tcg {
 // Ranking and packing
 // ======================================================================
 
-// Lists the heavy vertices and counts those below core_base (the core
-// block needs every heavy vertex inside the core).
+// Lists the heavy vertices.
 __global__ void k_heavy_list(const uint8_t *__restrict__ heavy, uint32_t n, uint32_t *__restrict__ hlist,
-                             uint32_t hlist_cap, uint32_t core_base, DevState *st)
+                             uint32_t hlist_cap, DevState *st)
 {
     const unsigned lane = lane_id();
     const uint64_t wstride = (uint64_t)gridDim.x * blockDim.x;
@@ -44,28 +43,42 @@ __global__ void k_heavy_list(const uint8_t *__restrict__ heavy, uint32_t n, uint
             const uint32_t pos = off + __popc(mask & lanemask_lt());
             if (pos < hlist_cap) hlist[pos] = (uint32_t)u;
         }
-        const unsigned below = __ballot_sync(FULL, f && u < core_base);
-        if (lane == 0 && below) atomicAdd(&st->heavy_below, (unsigned)__popc(below));
     }
+}
+
+// Whether the dense path runs (2 <= h <= hcap, all listed) and whether the
+// core block counts the top ranks (every heavy vertex inside the core:
+// heavy_below, counted by the partition).  Decided right after the
+// partition, so that the compaction already leaves out the pairs these
+// blocks count.
+__global__ void k_heavy_decide(uint32_t hcap, uint32_t hlist_cap, bool core, DevState *st)
+{
+    const uint32_t h = st->n_heavy;
+    const bool dense = hcap != 0 && h >= 2 && h <= hcap && h <= hlist_cap;
+    st->dense = dense ? 1u : 0u;
+    st->core_on = (core && dense && st->heavy_below == 0) ? 1u : 0u;
+}
+
+void heavy_decide(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s)
+{
+    if (hb.hcap == 0 || hb.hlist_cap == 0 || b.n == 0) return;  // no dense block: DevState::dense stays 0
+    k_heavy_decide<<<1, 1, 0, s>>>(hb.hcap, hb.hlist_cap, core && core->hb.hcap != 0, b.st);
+    note_launch();
 }
 
 constexpr int HR_THREADS = 256;
 
 // Dense index of each heavy vertex = the number of heavy vertices with a
 // smaller id (O(h^2) comparisons, h <= 2 m_p^(1/2)), so that every edge
-// between heavy vertices lands above the diagonal.  Also decides whether the
-// dense path runs: 2 <= h <= hcap.
+// between heavy vertices lands above the diagonal (only when the dense path
+// runs).
 __global__ void __launch_bounds__(HR_THREADS) k_heavy_rank(const uint32_t *__restrict__ hlist,
                                                            uint32_t *__restrict__ hidx, uint32_t hcap,
-                                                           uint32_t hlist_cap, bool core, DevState *st)
+                                                           uint32_t hlist_cap, DevState *st)
 {
     __shared__ unsigned long long s_key[HR_THREADS];
     const uint32_t h = st->n_heavy;
-    const bool dense = h >= 2 && h <= hcap && h <= hlist_cap && st->h_listed == h;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->dense = dense ? 1u : 0u;
-        st->core_on = (core && dense && st->heavy_below == 0) ? 1u : 0u;
-    }
+    const bool dense = st->dense != 0;  // k_heavy_decide
     if (!dense || blockIdx.x * HR_THREADS >= h) return;  // uniform per block
     const uint32_t i = blockIdx.x * HR_THREADS + threadIdx.x;
     unsigned long long mine = ~0ull;
@@ -457,11 +470,10 @@ void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuff
 {
     if (hb.hcap == 0 || hb.hlist_cap == 0 || b.n == 0) return;  // no dense block: DevState::dense stays 0
     const bool with_core = core && core->hb.hcap != 0;
-    k_heavy_list<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.heavy, b.n, hb.hlist, hb.hlist_cap,
-                                                             with_core ? core->base : 0u, b.st);
+    k_heavy_list<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.heavy, b.n, hb.hlist, hb.hlist_cap, b.st);
     note_launch();
     k_heavy_rank<<<(unsigned)ceil_div(hb.hlist_cap, HR_THREADS), HR_THREADS, 0, s>>>(hb.hlist, hb.hidx, hb.hcap,
-                                                                                   hb.hlist_cap, with_core, b.st);
+                                                                                   hb.hlist_cap, b.st);
     note_launch();
     k_heavy_clear<<<152 * 8, 256, 0, s>>>(hb.U, hb.UT, hb.hcap, b.st);
     note_launch();

@@ -124,6 +124,11 @@ struct RowsArgs {
     // vertices whose in-degrees are counted; nullptr: union path
     const uint32_t *frow = nullptr;
     uint64_t m_lo = 0;
+    // pairs the dense blocks count (DevState::dense / core_on) are left out
+    // of the owners' lists: both ends heavy (flags) with the upper end at or
+    // above light_lim, or the lower end at or above core_base
+    const uint8_t *heavy = nullptr;
+    uint32_t core_base = 0xffffffffu;
 };
 // Static rows of a single graph at creation: frow[0..n] (row offsets of rel)
 // and inres[0..n] (in-list reservation offsets: full in-degrees).  perm and
@@ -270,6 +275,9 @@ struct CoreBuffers {
 };
 // after the CSR: list, rank and pack the heavy vertices; sets DevState::dense,
 // and DevState::core_on when core (may be NULL) is to run for this count
+// Decides DevState::dense and core_on right after the partition (before the
+// compaction, which leaves out the pairs these blocks count).
+void heavy_decide(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s);
 void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s);
 // T_H += sum_{i<k} U_ik (U U)_ik on tcgen05 (no-op unless DevState::dense),
 // and t_core likewise over the core matrix when DevState::core_on
