@@ -539,7 +539,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     g->smem_bytes = (int)(slots * 4);
     // dense heavy block: at most 2 m^(1/2) heavy vertices, padded to the
-    // 128-row tile and capped at 32768 (2 x 2 GiB of bf16).  Graphs below
+    // 128-row tile and capped at 32768 (2 x 1 GiB of fp8).  Graphs below
     // 2^20 edges, or without room for the block, have the intersection
     // kernels count the heavy class instead.
     if (m >= (1ull << 20)) {
@@ -552,8 +552,8 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
             free_graph(g);
             return TC_ENOMEM;
         }
-        g->hb.U = (uint16_t *)g->alloc(hcap * hcap * 2);
-        g->hb.UT = g->hb.U ? (uint16_t *)g->alloc(hcap * hcap * 2) : nullptr;
+        g->hb.U = (uint8_t *)g->alloc(hcap * hcap);
+        g->hb.UT = g->hb.U ? (uint8_t *)g->alloc(hcap * hcap) : nullptr;
         g->hb.hcap = (uint32_t)hcap;
         if (!g->hb.U || !g->hb.UT || !heavy_make_maps(g->hb)) {
             if (g->hb.U) g->release(g->hb.U);
@@ -562,12 +562,12 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
             g->hb.hcap = 0;
         }
     }
-    // dense core: the top CORE_SIZE ranks (2 x 128 MiB of bf16), with the heavy block
+    // dense core: the top CORE_SIZE ranks (2 x 64 MiB of fp8), with the heavy block
     if (g->hb.hcap && (double)m >= CORE_MIN_EDGES && n >= 2 * CORE_SIZE) {
         CoreBuffers &c = g->core;
-        const uint64_t bytes = (uint64_t)CORE_SIZE * CORE_SIZE * 2;
-        c.hb.U = (uint16_t *)g->alloc(bytes);
-        c.hb.UT = c.hb.U ? (uint16_t *)g->alloc(bytes) : nullptr;
+        const uint64_t bytes = (uint64_t)CORE_SIZE * CORE_SIZE;
+        c.hb.U = (uint8_t *)g->alloc(bytes);
+        c.hb.UT = c.hb.U ? (uint8_t *)g->alloc(bytes) : nullptr;
         c.hb.hcap = CORE_SIZE;
         c.base = n - CORE_SIZE;
         if (!c.hb.U || !c.hb.UT || !heavy_make_maps(c.hb)) {

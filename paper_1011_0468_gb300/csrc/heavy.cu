@@ -8,14 +8,15 @@
 // term of
 //     T_H = sum_{i < k} U[i][k] * (U U)[i][k],
 // the matrix-product route of Alon, Yuster and Zwick that the paper builds
-// on.  U and U^T are packed as bf16 0/1 matrices and the product runs on
-// tcgen05 (kind::f16, FP32 accumulation in tensor memory), exact because
-// every partial sum is an integer no larger than h < 2^24.  Only output
-// tiles on or above the diagonal, and only the j-tiles between them, are
-// multiplied; the epilogue masks D = U U with U and sums.
+// on.  U and U^T are packed as fp8 e4m3 0/1 matrices (one byte per entry)
+// and the product runs on tcgen05 (kind::f8f6f4, FP32 accumulation in tensor
+// memory), exact because 0 and 1 are exact in e4m3 and every partial sum is
+// an integer no larger than h < 2^24.  Only output tiles on or above the
+// diagonal, and only the j-tiles between them, are multiplied; the epilogue
+// masks D = U U with U and sums.
 //
-// sm_103a has no INT8 tcgen05 MMA (.kind::i8 is rejected for this target),
-// hence bf16 operands.
+// sm_103a has no INT8 tcgen05 MMA (.kind::i8 is rejected for this target);
+// fp8 has the same operand bytes and twice the bf16 rate.
 #include <cuda.h>
 
 #include "kernels.h"
@@ -100,11 +101,11 @@ __global__ void __launch_bounds__(HR_THREADS) k_heavy_rank(const uint32_t *__res
 }
 
 // Zero the used corner [0, hp) x [0, hp) of U and U^T, hp = h rounded up to 128.
-__global__ void k_heavy_clear(uint16_t *__restrict__ U, uint16_t *__restrict__ UT, uint32_t hcap, DevState *st)
+__global__ void k_heavy_clear(uint8_t *__restrict__ U, uint8_t *__restrict__ UT, uint32_t hcap, DevState *st)
 {
     if (!st->dense) return;
     const uint32_t hp = (st->n_heavy + 127) & ~127u;
-    const uint64_t per_row = hp / 8;  // uint4 per row
+    const uint64_t per_row = hp / 16;  // uint4 per row
     const uint64_t total = (uint64_t)hp * per_row;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
@@ -118,14 +119,14 @@ __global__ void k_heavy_clear(uint16_t *__restrict__ U, uint16_t *__restrict__ U
 // for every heavy out-neighbour w.
 __global__ void k_heavy_pack(const uint32_t *__restrict__ ptrp, const uint32_t *__restrict__ col,
                              const uint8_t *__restrict__ heavy, const uint32_t *__restrict__ hlist,
-                             const uint32_t *__restrict__ hidx, uint16_t *__restrict__ U, uint16_t *__restrict__ UT,
+                             const uint32_t *__restrict__ hidx, uint8_t *__restrict__ U, uint8_t *__restrict__ UT,
                              uint32_t hcap, DevState *st)
 {
     if (!st->dense) return;
     const uint32_t h = st->n_heavy;
     const unsigned lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    constexpr uint16_t ONE = 0x3f80;  // bf16 1.0
+    constexpr uint8_t ONE = TC_ONE;
     for (uint32_t i = gw; i < h; i += nw) {
         const uint32_t v = hlist[i], r = hidx[v];
         const PaddedRow row = padded_row(ptrp, v);
@@ -143,13 +144,13 @@ __global__ void k_heavy_pack(const uint32_t *__restrict__ ptrp, const uint32_t *
 // One warp per core row v (ids base .. base + hcap - 1 that exist): U[v - base][w - base] =
 // U^T[w - base][v - base] = 1 for every out-neighbour w (all inside the core).
 __global__ void k_core_pack(const uint32_t *__restrict__ ptrp, const uint32_t *__restrict__ col, uint32_t n,
-                            uint32_t base, uint16_t *__restrict__ U, uint16_t *__restrict__ UT, uint32_t hcap,
+                            uint32_t base, uint8_t *__restrict__ U, uint8_t *__restrict__ UT, uint32_t hcap,
                             DevState *st)
 {
     if (!st->core_on) return;
     const unsigned lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    constexpr uint16_t ONE = 0x3f80;  // bf16 1.0
+    constexpr uint8_t ONE = TC_ONE;
     for (uint32_t v = base + gw; v < n; v += nw) {
         const PaddedRow row = padded_row(ptrp, v);
         const uint32_t r = v - base;
@@ -168,9 +169,9 @@ __global__ void k_core_pack(const uint32_t *__restrict__ ptrp, const uint32_t *_
 
 constexpr int TC_THREADS = 128;  // 4 warps: TMA producer (warp 0), MMA issuer (warp 1), all 4 epilogue
 constexpr int TC_STAGES = 4;
-constexpr uint32_t TC_TILE = 128;                        // M = N = 128
-constexpr uint32_t TC_KC = 64;                           // bf16 elements per K chunk = one 128-B row
-constexpr uint32_t TC_TILE_BYTES = TC_TILE * TC_KC * 2;  // 16 KiB per operand tile
+constexpr uint32_t TC_TILE = 128;                    // M = N = 128
+constexpr uint32_t TC_KC = 128;                      // fp8 elements per K chunk = one 128-B row
+constexpr uint32_t TC_TILE_BYTES = TC_TILE * TC_KC;  // 16 KiB per operand tile
 constexpr uint32_t TC_STAGE_BYTES = 2 * TC_TILE_BYTES;
 constexpr uint32_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;  // + alignment slack
 constexpr uint32_t TC_TMEM_COLS = 128;
@@ -241,13 +242,15 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor: D f32, A and B bf16, both K-major, M = N = 128.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((TC_TILE >> 3) << 17) | ((TC_TILE >> 4) << 24);
+// Instruction descriptor: D f32 (bits 4-5 = 1), A and B e4m3 (type fields at
+// bits 7-9 and 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t TC_IDESC = (1u << 4) | ((TC_TILE >> 3) << 17) | ((TC_TILE >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+// D (+)= A B^T over 32 fp8 elements of K (32 bytes of each operand row).
+__device__ __forceinline__ void mma_fp8(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate)
 {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             tmem),
         "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
         : "memory");
@@ -298,7 +301,7 @@ struct DenseJob {
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constant__ CUtensorMap mapA,
                                                             const __grid_constant__ CUtensorMap mapB,
-                                                            const uint16_t *__restrict__ U, uint32_t hcap,
+                                                            const uint8_t *__restrict__ U, uint32_t hcap,
                                                             DenseJob job, DevState *st)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -368,12 +371,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
                 const uint32_t a = base + s * TC_STAGE_BYTES;
                 const uint64_t da = sw128_desc(a), db = sw128_desc(a + TC_TILE_BYTES);
 #pragma unroll
-                for (uint32_t kk = 0; kk < TC_KC / 16; ++kk)  // 16 bf16 = 32 B per MMA
-                    mma_bf16(tmem, da + 2 * kk, db + 2 * kk, (c > c0 || kk > 0) ? 1u : 0u);
+                for (uint32_t kk = 0; kk < TC_KC / 32; ++kk)  // 32 fp8 = 32 B per MMA
+                    mma_fp8(tmem, da + 2 * kk, db + 2 * kk, (c > c0 || kk > 0) ? 1u : 0u);
                 mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
             }
             mma_commit(&done);  // accumulator complete
-            flops_k += c1 - c0;
+            flops_k += (c1 - c0) * (TC_KC / 64);  // in 64-wide K units
         }
         __syncwarp();
         // epilogue: rows 32 w .. 32 w + 31 of the tile, D masked by U
@@ -386,20 +389,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
         unsigned long long sum = 0;
         if (__all_sync(FULL, ok)) {
             const uint32_t row = I * TC_TILE + warp * 32 + lane;
-            const uint16_t *urow = U + (uint64_t)row * hcap + (uint64_t)K * TC_TILE;
+            const uint8_t *urow = U + (uint64_t)row * hcap + (uint64_t)K * TC_TILE;
 #pragma unroll 1
             for (uint32_t q = 0; q < TC_TILE / 32; ++q) {
                 uint32_t r[32];
                 tmem_ld32(tmem + ((warp * 32u) << 16) + q * 32, r);
                 const uint4 *m4 = reinterpret_cast<const uint4 *>(urow + q * 32);
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
+                for (int v = 0; v < 2; ++v) {
                     const uint4 mv = m4[v];
                     const uint32_t w[4] = {mv.x, mv.y, mv.z, mv.w};
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const uint32_t bits = (w[e >> 1] >> ((e & 1) * 16)) & 0xffffu;
-                        if (bits) sum += (uint32_t)__uint_as_float(r[v * 8 + e]);
+                    for (int e = 0; e < 16; ++e) {
+                        const uint32_t byte = (w[e >> 2] >> ((e & 3) * 8)) & 0xffu;
+                        if (byte) sum += (uint32_t)__uint_as_float(r[v * 16 + e]);
                     }
                 }
             }
@@ -452,13 +455,13 @@ bool heavy_make_maps(HeavyBuffers &hb)
     EncodeTiledFn enc = encode_fn();
     if (!enc || !hb.U || !hb.UT || hb.hcap == 0) return false;
     const cuuint64_t dims[2] = {hb.hcap, hb.hcap};
-    const cuuint64_t strides[1] = {(cuuint64_t)hb.hcap * 2};
+    const cuuint64_t strides[1] = {(cuuint64_t)hb.hcap};
     const cuuint32_t box[2] = {TC_KC, TC_TILE};
     const cuuint32_t estr[2] = {1, 1};
     CUtensorMap *maps[2] = {reinterpret_cast<CUtensorMap *>(hb.mapA), reinterpret_cast<CUtensorMap *>(hb.mapB)};
     void *bufs[2] = {hb.U, hb.UT};
     for (int i = 0; i < 2; ++i) {
-        if (enc(maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, bufs[i], dims, strides, box, estr,
+        if (enc(maps[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, bufs[i], dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
@@ -480,7 +483,7 @@ void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuff
     k_heavy_pack<<<152 * 4, 256, 0, s>>>(b.ptrp, b.col, b.heavy, hb.hlist, hb.hidx, hb.U, hb.UT, hb.hcap, b.st);
     note_launch();
     if (with_core) {
-        const uint64_t bytes = (uint64_t)core->hb.hcap * core->hb.hcap * 2;
+        const uint64_t bytes = (uint64_t)core->hb.hcap * core->hb.hcap;
         cudaMemsetAsync(core->hb.U, 0, bytes, s);
         cudaMemsetAsync(core->hb.UT, 0, bytes, s);
         k_core_pack<<<152 * 8, 256, 0, s>>>(b.ptrp, b.col, b.n, core->base, core->hb.U, core->hb.UT, core->hb.hcap,

@@ -247,13 +247,16 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
 void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const IsectConfig &cfg, cudaStream_t s);
 
 // ---------------------------------------------------------------- heavy.cu
-// Dense heavy block: U and U^T (hcap x hcap bf16, row stride hcap), the
+// Dense heavy block: U and U^T (hcap x hcap fp8, row stride hcap), the
 // heavy vertex list and each heavy vertex's dense index, and the TMA
 // descriptors of U and U^T (CUtensorMap storage).  hcap == 0 disables the
 // dense path (the intersection kernels then count the heavy class).
+// U and U^T hold 0 and 1 as fp8 e4m3 bytes (1.0 = 0x38): the tensor cores
+// multiply them exactly (fp32 sums of at most hcap <= 32768 ones).
+constexpr uint8_t TC_ONE = 0x38;
 struct HeavyBuffers {
-    uint16_t *U = nullptr;
-    uint16_t *UT = nullptr;
+    uint8_t *U = nullptr;
+    uint8_t *UT = nullptr;
     uint32_t hcap = 0;
     uint32_t *hlist = nullptr;
     uint32_t hlist_cap = 0;
