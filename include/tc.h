@@ -124,6 +124,17 @@ uint64_t tc_graph_device_bytes(const tc_graph *g); /* device memory held */
 #define TC_TIMING_RING 256
 tc_status tc_graph_set_timing(tc_graph *g, int on);
 
+/* The sampled in-degrees of a count are computed only for the vertices whose
+   full degree^2 exceeds a lower bound m_lo on the number of kept edges m_p
+   (by default p m - (120 p m)^(1/2) - 1, or m at p = 1; a sample below it
+   has probability under e^-60).  A sample that still falls below m_lo is
+   counted exactly by a fallback that computes every in-degree.  This sets
+   m_lo for the graph's later counts (m_lo >= 0), or restores the default
+   (m_lo < 0): for diagnostics and tests of both paths (m_lo = 0 makes every
+   vertex with an edge a candidate; m_lo > m forces the fallback).  Results
+   never depend on it.  TC_EINVAL for a NULL graph. */
+tc_status tc_graph_set_sample_floor(tc_graph *g, int64_t m_lo);
+
 /* After tc_graph_sync: copy the phase times (8 floats per count, layout of
    tc_result.ms) of the counts completed since the last drain, oldest first,
    at most max_counts of them (older ones beyond the ring are lost).  Returns

@@ -147,6 +147,7 @@ struct tc_graph {
     std::vector<cudaEvent_t> ring;
     uint64_t ring_head = 0;  // next slot to record
     uint64_t ring_tail = 0;  // oldest undrained count
+    int64_t sample_floor = -1;  // lower bound on m_p for the degree candidates (< 0: the default)
     std::vector<void *> allocs;
 
     void *alloc(uint64_t b)
@@ -301,7 +302,8 @@ void ring_times(tc_graph *g, uint64_t count, float *ms)
 tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bool timing)
 {
     const uint64_t seed_mix = splitmix64(seed), thr = threshold_of(p);
-    RowsArgs ra = rows_of(g, seed_mix, thr, sample_floor(g->m, p, thr));
+    RowsArgs ra = rows_of(g, seed_mix, thr,
+                          g->sample_floor >= 0 ? (uint64_t)g->sample_floor : sample_floor(g->m, p, thr));
     // the core block pays off once the sample is large: its cost is fixed,
     // the intersections it replaces grow with the sample
     const CoreBuffers *core = (g->core.hb.hcap && p * (double)g->m >= CORE_MIN_EDGES) ? &g->core : nullptr;
@@ -590,6 +592,13 @@ void tc_graph_destroy(tc_graph *g) { free_graph(g); }
 uint64_t tc_graph_num_edges(const tc_graph *g) { return g ? g->m : 0; }
 uint32_t tc_graph_num_vertices(const tc_graph *g) { return g ? g->n : 0; }
 uint64_t tc_graph_device_bytes(const tc_graph *g) { return g ? g->bytes : 0; }
+
+tc_status tc_graph_set_sample_floor(tc_graph *g, int64_t m_lo)
+{
+    if (!g) return TC_EINVAL;
+    g->sample_floor = m_lo < 0 ? -1 : m_lo;
+    return TC_OK;
+}
 
 tc_status tc_graph_set_timing(tc_graph *g, int on)
 {

@@ -68,6 +68,7 @@ SIGNATURES = [
     ("tc_graph_num_vertices", ctypes.c_uint32, [_vp]),
     ("tc_graph_device_bytes", ctypes.c_uint64, [_vp]),
     ("tc_graph_set_timing", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("tc_graph_set_sample_floor", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("tc_graph_timing_drain", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32]),
     ("tc_count", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(tc_result)]),
     ("tc_count_async", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp]),
@@ -278,6 +279,11 @@ class Graph:
 
     def set_timing(self, on: bool = True):
         tc_graph_set_timing(self.handle, on)
+
+    def set_sample_floor(self, m_lo: int):
+        """Lower bound on m_p that picks the vertices whose sampled in-degrees are
+        counted (tc_graph_set_sample_floor); m_lo < 0 restores the default."""
+        _check(lib().tc_graph_set_sample_floor(self.handle, int(m_lo)), "tc_graph_set_sample_floor")
 
     def timing_drain(self, max_counts: int = 256) -> np.ndarray:
         """Phase times (counts x 8, ms) of the timed counts since the last drain."""

@@ -174,6 +174,22 @@ def test_pinned_host_input(tc):
                 g.close()
 
 
+def test_degree_candidates_and_fallback(tc):
+    """Sampled in-degrees are counted only for the vertices that can be heavy
+    (a lower bound on m_p decides them); a bound of 0 makes every vertex a
+    candidate, a bound above m sends every sample p < 1 through the exact
+    fallback.  All three give the oracle's counts."""
+    n = 40000
+    e = gen.chung_lu(n, 400_000, 2.1, 4000.0, 13)
+    canon = oracle.canonicalize(e, n)
+    want = {p: oracle.run(canon, n, p, 5) for p in (1.0, 0.5, 0.1)}
+    with tc.Graph(e, n) as g:
+        for floor in (-1, 0, len(canon) + 1, -1):
+            g.set_sample_floor(floor)
+            for p, w in want.items():
+                assert_same(g.count(p, 5), w)
+
+
 def test_empty_and_tiny(tc):
     for edges, n in ((np.zeros((0, 2), np.uint32), 1), (np.zeros((0, 2), np.uint32), 100_000),
                      (np.array([[0, 1]], np.uint32), 2), (gen.complete(3), 3)):
