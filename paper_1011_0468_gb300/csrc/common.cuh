@@ -88,6 +88,20 @@ __device__ __forceinline__ uint32_t find_part_warp(const T *off, uint32_t k, T i
     return g0 + find_part(off + g0, g1 - g0 + 1, i);
 }
 
+// The same from a known part g_start <= the answer for lane 0 (parts are
+// walked forward from it): for consecutive items that advance slowly.
+template <typename T>
+__device__ __forceinline__ uint32_t find_part_warp_from(const T *off, uint32_t k, T i, uint32_t g_start)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    uint32_t g = g_start;
+    if (lane == 0 || lane == 31)
+        while (g + 1 < k && off[g + 1] <= i) ++g;
+    const uint32_t g0 = __shfl_sync(0xffffffffu, g, 0), g1 = __shfl_sync(0xffffffffu, g, 31);
+    if (g0 == g1) return g0;
+    return g0 + find_part(off + g0, g1 - g0 + 1, i);
+}
+
 // ---------------------------------------------------------------- splitmix64
 // Steele, Lea and Flood's splitmix64 in the form Vigna published:
 // z = x + golden gamma, then two xor-shift-multiply rounds and a final

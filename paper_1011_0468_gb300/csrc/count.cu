@@ -33,21 +33,29 @@ __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevSta
         }
         if (lim) atomicMax(&st->light_lim, lim);
     } else {
-        // batch: each vertex against its own graph's m_p
+        // batch: each vertex against its own graph's m_p; every warp takes a
+        // contiguous run of 32-vertex groups, so its graph only moves forward
         const unsigned lane = lane_id();
-        for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
-            const uint64_t u = base + lane;
+        const uint64_t groups = ((uint64_t)n + 31) / 32, nwarps = stride / 32;
+        const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+        const uint64_t g_lo = groups * wid / nwarps, g_hi = groups * (wid + 1) / nwarps;
+        uint32_t gw = g_lo < g_hi ? find_part(bv.voff, bv.k, (uint32_t)(g_lo * 32)) : 0u, lim = 0;
+        for (uint64_t grp = g_lo; grp < g_hi; ++grp) {
+            const uint64_t u = grp * 32 + lane;
             const uint32_t uu = (uint32_t)(u < n ? u : n - 1);
-            const uint32_t g = find_part_warp(bv.voff, bv.k, uu);
+            const uint32_t g = find_part_warp_from(bv.voff, bv.k, uu, gw);
+            gw = __shfl_sync(FULL, g, 31);
             const unsigned long long d = deg[uu], mp = bv.m_p[g];
             const bool f = u < n && d * d > mp;
             if (u < n) heavy[u] = f;
             h += f;
-            if (u < n && !f && d) atomicMax(&st->light_lim, uu + 1);
+            if (u < n && !f && d) lim = uu + 1;
             const unsigned peers = __match_any_sync(FULL, g);
             const unsigned c = __popc(__ballot_sync(FULL, f) & peers);
             if (c && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(bv.n_heavy + g, c);
         }
+        lim = __reduce_max_sync(FULL, lim);
+        if (lane == 0 && lim) atomicMax(&st->light_lim, lim);
     }
     h = warp_sum(h);
     if (lane_id() == 0 && h) atomicAdd(&st->n_heavy, h);

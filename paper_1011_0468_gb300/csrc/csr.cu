@@ -415,27 +415,36 @@ __global__ void __launch_bounds__(256) k_sample_rows(const uint64_t *__restrict_
                                                      DevState *st, BatchView bv)
 {
     __shared__ uint32_t wt[33];
+    __shared__ uint32_t s_g;  // batch: graph of the tile's first edge
     const unsigned lane = lane_id();
     const uint64_t nt = (m + RX_TILE - 1) / RX_TILE;
     uint32_t kept_total = 0;
     for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         uint32_t c = 0;
+        if (bv.k != 0) {
+            if (threadIdx.x == 0) s_g = find_part(bv.eoff, bv.k, tile * RX_TILE);
+            __syncthreads();
+        }
+        uint32_t gw = bv.k != 0 ? s_g : 0u;  // parts advance with the warp's edges
 #pragma unroll 4
         for (int j = 0; j < RX_ITEMS; ++j) {
             const uint64_t i = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
             const uint64_t ii = i < m ? i : m - 1;
-            const uint64_t r = ld_stream_u64(rel + ii), o = ld_stream_u64(orig + ii);
+            const uint64_t o = ld_stream_u64(orig + ii);
             bool f;
             uint32_t g = 0;
             if (bv.k == 0) {
                 f = i < m && keep_edge(o, seed_mix, thr);
             } else {
-                g = find_part_warp(bv.eoff, bv.k, ii);
+                g = find_part_warp_from(bv.eoff, bv.k, ii, gw);
+                gw = __shfl_sync(FULL, g, 31);
                 const uint64_t vo = __ldg(bv.voff + g);
                 f = i < m && keep_edge(o - ((vo << 32) | vo), __ldg(bv.seed_mix + g), __ldg(bv.thr + g));
             }
             const unsigned word = __ballot_sync(FULL, f);
             if (lane == 0 && i - lane < m) keepw[(i - lane) >> 5] = word;
+            if (word == 0) continue;  // warp-uniform
+            const uint64_t r = f ? ld_stream_u64(rel + i) : 0ull;  // rank-order keys of the kept edges only
             const uint32_t u = f ? (uint32_t)(r >> 32) : 0xffffffffu;
             const unsigned peers = __match_any_sync(FULL, u);
             if (f) {
@@ -449,6 +458,7 @@ __global__ void __launch_bounds__(256) k_sample_rows(const uint64_t *__restrict_
                 if (cg && lane == (unsigned)(__ffs(gp) - 1)) atomicAdd(bv.m_p + g, (unsigned long long)cg);
             }
         }
+        if (bv.k != 0) __syncthreads();  // s_g is rewritten for the next tile
         kept_total += c;
         c = block_sum(c, wt);
         if (threadIdx.x == 0) tile_cnt[tile] = c;
