@@ -261,6 +261,7 @@ RowsArgs rows_of(tc_graph *g, uint64_t seed_mix, uint64_t thr, uint64_t m_lo)
     a.st = g->st;
     a.frow = g->frow;
     a.m_lo = m_lo;
+    a.heavy = g->heavy;
     return a;
 }
 
@@ -307,7 +308,6 @@ tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bo
     // the core block pays off once the sample is large: its cost is fixed,
     // the intersections it replaces grow with the sample
     const CoreBuffers *core = (g->core.hb.hcap && p * (double)g->m >= CORE_MIN_EDGES) ? &g->core : nullptr;
-    ra.heavy = g->hb.hcap ? g->heavy : nullptr;
     if (core) ra.core_base = core->base;
     CountBuffers b = buffers_of(g);
     if (core) b.core_base = core->base;

@@ -194,6 +194,7 @@ void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const Isec
     ra.inlist = u.inlist;
     ra.olist = u.olist;
     ra.ocnt = u.ocnt;
+    ra.heavy = u.heavy;
     ra.keepw = u.keepw;
     ra.tile_cnt = u.tile_cnt;
     ra.scan = u.scan;

@@ -732,8 +732,8 @@ struct ScatterArgs {
     uint32_t *colp, *cursor, *olist, *ocnt;
     uint2 *inlist;
     int hbits;
-    // pairs left to the dense blocks: heavy flags and light_lim when the
-    // heavy block runs (else lim = EMPTY), the core's base when it runs
+    // heavy flags; pairs left to the dense blocks: light_lim when the heavy
+    // block runs (else lim = EMPTY), the core's base when it runs
     const uint8_t *heavy;
     uint32_t lim, core_lo;
 };
@@ -752,9 +752,10 @@ __device__ __forceinline__ void scatter_edge(const ScatterArgs &a, bool live, ui
             u >= a.core_lo || (v >= a.lim && __ldg(a.heavy + u) && __ldg(a.heavy + v));  // see ScatterArgs
         if (!dense_pair && k + 1 < __ldg(a.rowptr + u + 1)) {  // so d+(u) >= 2
             const uint32_t du = __ldg(a.dplus + u), dv = __ldg(a.dplus + v);
-            if (du < dv) {
+            if (du < dv) {  // entry: position of v in u's row; entries after it | u's heavy flag << 31
                 const uint32_t q = atomicAdd(a.cursor + hot_index(v, a.hbits), 1u);
-                a.inlist[q] = make_uint2(u, pos);
+                const uint32_t after = __ldg(a.rowptr + u + 1) - k - 1;
+                a.inlist[q] = make_uint2(pos, after | ((uint32_t)__ldg(a.heavy + u) << 31));
             } else {
                 out = dv >= 1;
             }
@@ -812,7 +813,7 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
     constexpr int WORDS = RX_TILE / 32;  // 128 keep words per tile
     __shared__ uint32_t s_word[WORDS], s_pre[WORDS];
     __shared__ uint32_t wt[33];
-    const bool dense = heavy && st->dense;
+    const bool dense = st->dense != 0;
     const ScatterArgs a{rel,   padoff, rowptr, dplus, colp, cursor, olist, ocnt, inlist, hbits, heavy,
                         dense ? st->light_lim : 0xffffffffu, dense && st->core_on ? core_base : 0xffffffffu};
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;

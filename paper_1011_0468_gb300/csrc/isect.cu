@@ -231,31 +231,36 @@ struct PairCtx {
     uint32_t core_lo;  // pairs whose lower endpoint is at or above this id are the core block's
 };
 
-// Partner y of owner x (out-degree d, heavy flag hx): the chunk range of the
-// part of y's padded out-list to stream and whether both endpoints of the
-// pair are heavy (hh).  For an in-list partner, qpos is the padded position
-// of x in y's row.  The range is empty when the pair is resolved by the
-// other endpoint, closes no triangle, or (dense) can close no triangle with
-// a light vertex.  Also counts the streamed list entries into the tally.
+// Partner of owner x (out-degree d, heavy flag hx): the chunk range of the
+// part of the partner's padded out-list to stream and whether both
+// endpoints of the pair are heavy (hh).  An out-list partner is y; an
+// in-list partner is its entry e (csr.cu): e.x is the padded position of x in
+// the partner's row, e.y the number of entries after it (>= 1), with the
+// partner's heavy flag in bit 31.  The range is empty when the pair is
+// resolved by the other endpoint, closes no triangle, or (dense) can close
+// no triangle with a light vertex.  Also counts the streamed list entries
+// into the tally.
 __device__ __forceinline__ void partner_of(const uint32_t *__restrict__ ptrp, const PairCtx &pc, uint32_t d,
-                                           uint32_t hx, uint32_t x, uint32_t y, bool is_out, uint32_t qpos,
+                                           uint32_t hx, uint32_t x, uint32_t y, bool is_out, uint2 e,
                                            uint32_t &c0, uint32_t &nc, uint32_t &hh, Tally &t)
 {
-    const PaddedRow py = padded_row(ptrp, y);
     uint32_t len, b;
     if (is_out) {  // pair (x -> y)
+        const PaddedRow py = padded_row(ptrp, y);
         len = (py.d >= 1 && py.d <= d && x < pc.core_lo) ? py.d : 0u;
         c0 = py.beg >> 2;
         nc = (len + 3) >> 2;
         b = y;
-    } else {  // pair (y -> x): the entries of N+(y) after x
-        const uint32_t end = py.beg + py.d;
-        len = (py.d >= 2 && py.d < d && qpos + 1 < end && y < pc.core_lo) ? end - qpos - 1 : 0u;
-        c0 = (qpos + 1) >> 2;
-        nc = len ? ((end + 3) >> 2) - c0 : 0u;
+        hh = (len && hx) ? (uint32_t)__ldg(pc.heavy + y) : 0u;
+    } else {  // pair (partner -> x): the entries of the partner's row after x
+        // the compaction appended it only for 2 <= d+(partner) < d, a row
+        // that goes on past x and a partner below the core
+        len = e.y & 0x7fffffffu;
+        c0 = (e.x + 1) >> 2;
+        nc = ((e.x + 1 + len + 3) >> 2) - c0;
         b = x;
+        hh = hx ? e.y >> 31 : 0u;
     }
-    hh = (len && hx) ? (uint32_t)__ldg(pc.heavy + y) : 0u;
     if (hh && pc.dense && b >= pc.lim) len = nc = 0;  // every third vertex would be heavy
     t.stream += len;
     t.partners += len != 0;
@@ -506,16 +511,14 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
                         const uint32_t dh = s_dh[w][L], Ld = dh & 0x7fffffffu;
                         const uint32_t j = s_p0[w][L] + (q - s_pre[w][L]), oc = s_oc[w][L];
                         const bool is_out = j < oc;
-                        uint32_t y, qpos = 0;
-                        if (is_out) {
+                        uint32_t y = 0;
+                        uint2 e = make_uint2(0, 0);
+                        if (is_out)
                             y = __ldg(olist + s_ob[w][L] + j);
-                        } else {
-                            const uint2 e = __ldg(inlist + s_ib[w][L] + j - oc);
-                            y = e.x;
-                            qpos = e.y;
-                        }
+                        else
+                            e = __ldg(inlist + s_ib[w][L] + j - oc);
                         ti = s_ti[w][L];
-                        partner_of(ptrp, pc, Ld, dh >> 31, s_x[w][L], y, is_out, qpos, c0, nc, hh, t);
+                        partner_of(ptrp, pc, Ld, dh >> 31, s_x[w][L], y, is_out, e, c0, nc, hh, t);
                     }
                     stream_chunks<true>(col4, BucketSet{tab, 0, 0}, tab, c0, nc, hh, ti, s_base[w], s_tinfo[w], pc, t);
                     before += __popc(sts);
@@ -661,15 +664,13 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 8) k_probe_block(const u
             uint32_t c0 = 0, nc = 0, hh = 0;
             if (q < per && j < p1) {
                 const bool is_out = j < oc;
-                uint32_t y, qpos = 0;
-                if (is_out) {
+                uint32_t y = 0;
+                uint2 e = make_uint2(0, 0);
+                if (is_out)
                     y = __ldg(olist + ob + j);
-                } else {
-                    const uint2 e = __ldg(inlist + ib + j - oc);
-                    y = e.x;
-                    qpos = e.y;
-                }
-                partner_of(ptrp, pc, d, hx, x, y, is_out, qpos, c0, nc, hh, t);
+                else
+                    e = __ldg(inlist + ib + j - oc);
+                partner_of(ptrp, pc, d, hx, x, y, is_out, e, c0, nc, hh, t);
             }
             pc0[q] = c0;
             pncc[q] = (nc << 1) | hh;

@@ -124,9 +124,10 @@ struct RowsArgs {
     // vertices whose in-degrees are counted; nullptr: union path
     const uint32_t *frow = nullptr;
     uint64_t m_lo = 0;
-    // pairs the dense blocks count (DevState::dense / core_on) are left out
-    // of the owners' lists: both ends heavy (flags) with the upper end at or
-    // above light_lim, or the lower end at or above core_base
+    // heavy flags (partition); the in-list entries carry the source's flag.
+    // Pairs the dense blocks count (DevState::dense / core_on) are left out of
+    // the owners' lists: both ends heavy with the upper end at or above
+    // light_lim, or the lower end at or above core_base
     const uint8_t *heavy = nullptr;
     uint32_t core_base = 0xffffffffu;
 };

@@ -203,6 +203,7 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     ra.inlist = reinterpret_cast<uint2 *>(bufA);
     ra.olist = reinterpret_cast<uint32_t *>(bufB);
     ra.ocnt = ocnt;
+    ra.heavy = heavy;
     ra.keepw = keepw;
     ra.tile_cnt = tile_cnt;
     ra.scan = scan;
