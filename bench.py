@@ -75,6 +75,24 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max_ms(ms: float, ws: int, device) -> float:
+    """Max over the ranks of a per-rank time: the job ends with its slowest
+    replica (one collective; ws == 1 returns ms)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws: int, steps: int, counts_per_step: int, m: int, elapsed_ms: float) -> float:
+    """Whole-job input edges per second: every replica counts its own copy of
+    the workload (weak scaling), all within elapsed_ms."""
+    return ws * steps * counts_per_step * m / (elapsed_ms / 1000.0)
+
+
 def make_graph():
     import gen
     w = WORKLOAD
@@ -258,12 +276,8 @@ def our_arm(args):
     g.set_timing(False)
     results = [tc.tc_result.from_address(res_buf[j].data_ptr()).as_dict() for j in range(len(ps))]
     barrier()
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
-    value = ws * args.steps * len(ps) * m / (elapsed_ms / 1000.0)
+    elapsed_ms = reduce_max_ms(elapsed_ms, ws, "cuda")
+    value = job_throughput(ws, args.steps, len(ps), m, elapsed_ms)
 
     # ---- roofline of the dominant launch group: the intersection kernels
     # (k_probe_warp + k_probe_block) of the p = 1 count, timed live per count
@@ -316,8 +330,8 @@ def our_arm(args):
             h.count_async(p, k + 1, out_host[j].data_ptr())
         h.sync()
         h.close()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = ws * e2e_steps * len(ps) * m / e2e_s
+    e2e_s = reduce_max_ms(1000.0 * (time.perf_counter() - t0), ws, "cuda") / 1000.0
+    e2e_value = job_throughput(ws, e2e_steps, len(ps), m, 1000.0 * e2e_s)
 
     g.close()
     if rank == 0:
