@@ -94,6 +94,16 @@ void tc_set_allocator(tc_alloc_fn alloc, tc_free_fn free_fn, void *ctx);
    system.  TC_ECUDA on a CUDA error. */
 tc_status tc_release_cached_memory(void);
 
+/* Failure detection of the device-side waits.  Every wait of the tensor-core
+   kernels on an mbarrier gives up after a time limit, sets an error bit
+   (TC_ETIMEOUT for the count) and lets the kernel release what it holds and
+   return, so the context stays usable.  This runs that same wait, for
+   limit_us microseconds (1 .. 10^6), on a barrier that nothing arrives at,
+   in one small kernel on the current device.  Returns TC_ETIMEOUT when the
+   wait gave up (the expected outcome), TC_OK if it completed (a defect),
+   TC_EINVAL for a limit out of range, TC_ECUDA on a CUDA error. */
+tc_status tc_check_bounded_wait(uint32_t limit_us);
+
 /*
  * Build a graph from m_in uint32 pairs (Section 4.1 canonical simple graph).
  *   edges           m_in pairs; host memory (edges_on_device = 0, any host

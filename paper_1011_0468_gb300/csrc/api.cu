@@ -377,6 +377,13 @@ const char *tc_status_str(tc_status s)
 
 int tc_version(void) { return 100; }
 
+tc_status tc_check_bounded_wait(uint32_t limit_us)
+{
+    if (limit_us == 0 || limit_us > 1000000u) return TC_EINVAL;
+    const int r = wait_check(limit_us);
+    return r == 1 ? TC_ETIMEOUT : (r == 0 ? TC_OK : TC_ECUDA);
+}
+
 tc_status tc_release_cached_memory(void)
 {
     cudaMemPool_t pool = pool_of_current_device();

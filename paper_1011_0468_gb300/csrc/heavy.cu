@@ -209,14 +209,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Wait until the phase of the given parity has completed; false after
-// TC_WAIT_NS without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// limit_ns (TC_WAIT_NS in the kernels) without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns = TC_WAIT_NS)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > TC_WAIT_NS) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
+// The kernels' bounded wait on a barrier that nothing arrives at (phase 0
+// of a fresh barrier with one expected arrival never completes): it must
+// give up after limit_ns and say so (*gave_up = 1).
+__global__ void k_wait_check(unsigned long long limit_ns, unsigned *gave_up)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *gave_up = mbar_wait(&bar, 0u, limit_ns) ? 0u : 1u;
     }
 }
 
@@ -490,6 +503,24 @@ void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuff
                                             b.st);
         note_launch();
     }
+}
+
+int wait_check(uint32_t limit_us)
+{
+    unsigned *flag = nullptr, host = 2;
+    if (cudaMalloc(&flag, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    k_wait_check<<<1, 32>>>((unsigned long long)limit_us * 1000ull, flag);
+    note_launch();
+    const bool ok = cudaMemcpy(&host, flag, sizeof(unsigned), cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(flag);
+    if (!ok) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int)host;
 }
 
 void heavy_contract(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s)

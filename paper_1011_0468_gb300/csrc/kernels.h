@@ -282,6 +282,10 @@ struct CoreBuffers {
 // Decides DevState::dense and core_on right after the partition (before the
 // compaction, which leaves out the pairs these blocks count).
 void heavy_decide(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s);
+// Runs the tensor kernels' bounded mbarrier wait on a barrier nothing
+// arrives at, for limit_us: 1 when it gave up (as it must), 0 when it
+// completed, -1 on a CUDA error.
+int wait_check(uint32_t limit_us);
 void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s);
 // T_H += sum_{i<k} U_ik (U U)_ik on tcgen05 (no-op unless DevState::dense),
 // and t_core likewise over the core matrix when DevState::core_on

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("tc_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tc_version", ctypes.c_int, []),
     ("tc_release_cached_memory", ctypes.c_int, []),
+    ("tc_check_bounded_wait", ctypes.c_int, [ctypes.c_uint32]),
     ("tc_launch_count", ctypes.c_uint64, []),
     ("tc_count_noalloc", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
                                         ctypes.POINTER(tc_result), _vp]),

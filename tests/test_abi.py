@@ -61,6 +61,9 @@ def test_argument_errors_without_device(lib):
     assert lib.tc_graph_sync(None) == tc.TC_EINVAL
     lib.tc_graph_destroy(None)  # NULL-safe
     assert lib.tc_graph_num_edges(None) == 0
+    assert lib.tc_graph_set_sample_floor(None, 0) == tc.TC_EINVAL
+    for limit in (0, 1000001):  # bounded-wait check: limits out of range
+        assert lib.tc_check_bounded_wait(limit) == tc.TC_EINVAL
 
 
 def test_result_struct_layout():

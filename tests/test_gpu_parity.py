@@ -190,6 +190,16 @@ def test_degree_candidates_and_fallback(tc):
                 assert_same(g.count(p, 5), w)
 
 
+def test_bounded_device_wait_gives_up_and_context_stays_usable(tc):
+    """The tensor kernels' mbarrier wait, on a barrier nothing arrives at,
+    gives up after its limit with TC_ETIMEOUT; the next count is exact."""
+    assert tc.lib().tc_check_bounded_wait(20000) == tc.TC_ETIMEOUT
+    n = 2000
+    e = gen.er(n, 20000, 1)
+    with tc.Graph(e, n) as g:
+        assert_same(g.count(0.5, 3), oracle.run(oracle.canonicalize(e, n), n, 0.5, 3))
+
+
 def test_empty_and_tiny(tc):
     for edges, n in ((np.zeros((0, 2), np.uint32), 1), (np.zeros((0, 2), np.uint32), 100_000),
                      (np.array([[0, 1]], np.uint32), 2), (gen.complete(3), 3)):
