@@ -167,14 +167,21 @@ __global__ void k_core_pack(const uint32_t *__restrict__ ptrp, const uint32_t *_
 // tcgen05 contraction
 // ======================================================================
 
-constexpr int TC_THREADS = 128;  // 4 warps: TMA producer (warp 0), MMA issuer (warp 1), all 4 epilogue
+// Roles: warp 0 TMA producer, warp 1 TMEM owner and MMA issuer, warps 2-5
+// epilogue (each reads the TMEM lane quarter warp % 4).
+constexpr int TC_THREADS = 192;
 constexpr int TC_STAGES = 4;
-constexpr uint32_t TC_TILE = 128;                    // M = N = 128
-constexpr uint32_t TC_KC = 128;                      // fp8 elements per K chunk = one 128-B row
-constexpr uint32_t TC_TILE_BYTES = TC_TILE * TC_KC;  // 16 KiB per operand tile
-constexpr uint32_t TC_STAGE_BYTES = 2 * TC_TILE_BYTES;
+constexpr uint32_t TC_TILE = 128;                       // M = 128 rows of U (a row panel)
+constexpr uint32_t TC_N = 256;                          // N = 256 columns (a column panel)
+constexpr uint32_t TC_KC = 128;                         // fp8 elements per K chunk = one 128-B row
+constexpr uint32_t TC_A_BYTES = TC_TILE * TC_KC;        // 16 KiB
+constexpr uint32_t TC_B_BYTES = TC_N * TC_KC;           // 32 KiB
+constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
 constexpr uint32_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;  // + alignment slack
-constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr uint32_t TC_ACCS = 2;                         // accumulators: a tile's epilogue overlaps the next MMAs
+constexpr uint32_t TC_TMEM_COLS = TC_ACCS * TC_N;       // 512: all of TMEM, one CTA per SM
+constexpr uint32_t TC_RING = 4;                         // tile hand-over slots
+constexpr uint32_t TC_NO_TILE = 0xffffffffu;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;  // bounded waits: 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -257,7 +264,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 
 // Instruction descriptor: D f32 (bits 4-5 = 1), A and B e4m3 (type fields at
 // bits 7-9 and 10-12 = 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-constexpr uint32_t TC_IDESC = (1u << 4) | ((TC_TILE >> 3) << 17) | ((TC_TILE >> 4) << 24);
+constexpr uint32_t TC_IDESC = (1u << 4) | ((TC_N >> 3) << 17) | ((TC_TILE >> 4) << 24);
 
 // D (+)= A B^T over 32 fp8 elements of K (32 bytes of each operand row).
 __device__ __forceinline__ void mma_fp8(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate)
@@ -275,6 +282,14 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 consecutive f32 columns of this warp's 32 TMEM lanes (no wait).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
     asm volatile(
@@ -285,22 +300,41 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
           "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Output tile t (heaviest first): tiles with K - I = o, o from T-1 down to 0.
-__device__ __forceinline__ void tile_of(uint32_t t, uint32_t T, uint32_t &I, uint32_t &K)
-{
-    uint32_t o = T - 1;
-    for (;;) {
-        const uint32_t cnt = T - o;  // tiles on this diagonal
-        if (t < cnt || o == 0) break;
-        t -= cnt;
-        --o;
+// Output tiles: row panel I (128 rows) by column panel P (256 columns),
+// every pair with 2P + 1 >= I (the others lie below the diagonal, where U is
+// zero).  o = 2P + 1 - I is the tile's distance from the diagonal in
+// 128-wide blocks; its j-chunks are [I, min(2P + 2, R)), so a larger o means
+// more work, and tiles are handed out from the largest o down.
+struct TileGrid {
+    int R, C;  // row panels (of 128) and column panels (of 256)
+    __device__ __forceinline__ int lo(int o) const { return o / 2; }
+    __device__ __forceinline__ int hi(int o) const
+    {
+        const int x = R + o - 2;
+        return min(C - 1, x >= 0 ? x / 2 : -1);
     }
-    I = t;
-    K = t + o;
-}
+    __device__ uint32_t count() const
+    {
+        uint32_t n = 0;
+        for (int o = 2 * C - 1; o >= 0; --o) n += (uint32_t)max(0, hi(o) - lo(o) + 1);
+        return n;
+    }
+    // t-th tile (t < count()), packed as I << 16 | P
+    __device__ uint32_t tile(uint32_t t) const
+    {
+        for (int o = 2 * C - 1; o >= 0; --o) {
+            const uint32_t cnt = (uint32_t)max(0, hi(o) - lo(o) + 1);
+            if (t < cnt) {
+                const int P = lo(o) + (int)t;
+                return (uint32_t)(2 * P + 1 - o) << 16 | (uint32_t)P;
+            }
+            t -= cnt;
+        }
+        return TC_NO_TILE;
+    }
+};
 
 // One contraction: which matrix order, which tile cursor and which output
 // counter (the heavy block and the core block run the same kernel).
@@ -312,22 +346,32 @@ struct DenseJob {
     unsigned long long *out;     // += sum_{i<k} U_ik (U U)_ik
 };
 
+// Persistent, warp-specialised: the producer takes tiles from the cursor
+// (heaviest first) and hands each one to the MMA warp and the epilogue
+// warps through a small ring; the MMA warp accumulates tile n in TMEM
+// accumulator n % 2 while the epilogue warps read tile n - 1 from the other
+// one.  Every wait is bounded: a stalled barrier sets ERR_TIMEOUT and the
+// roles leave their loops; the CTA then waits (bounded) for its own
+// outstanding copies and MMAs before it frees TMEM.
 __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constant__ CUtensorMap mapA,
                                                             const __grid_constant__ CUtensorMap mapB,
                                                             const uint8_t *__restrict__ U, uint32_t hcap,
                                                             DenseJob job, DevState *st)
 {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
-    __shared__ uint32_t s_tmem, s_tile, s_abort;
-    __shared__ unsigned long long s_sum[4];
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
+    __shared__ __align__(8) uint64_t tfull[TC_RING], tempty[TC_RING], afull[TC_ACCS], aempty[TC_ACCS], drain;
+    __shared__ uint32_t s_tile[TC_RING];
+    __shared__ uint32_t s_tmem, s_issued, s_consumed;
+    __shared__ volatile uint32_t s_abort;
     if (!*job.enable) return;  // uniform: written before this launch
     const uint32_t h = job.h_dev ? *job.h_dev : job.h_host;
-    const uint32_t T = (h + TC_TILE - 1) / TC_TILE, ntiles = T * (T + 1) / 2;
+    const uint32_t hp = (h + TC_TILE - 1) / TC_TILE * TC_TILE;
+    const TileGrid grid{(int)(hp / TC_TILE), (int)((hp / TC_TILE + 1) / 2)};
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "n"(TC_TMEM_COLS)
                      : "memory");
@@ -338,101 +382,177 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&done, 1);
+        for (uint32_t r = 0; r < TC_RING; ++r) {
+            mbar_init(&tfull[r], 1);
+            mbar_init(&tempty[r], 1 + 4);  // the MMA thread and the four epilogue warps
+        }
+        for (uint32_t a = 0; a < TC_ACCS; ++a) {
+            mbar_init(&afull[a], 1);
+            mbar_init(&aempty[a], 4);
+        }
+        mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
+        s_issued = 0;
+        s_consumed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    uint32_t it_prod = 0, it_mma = 0, tiles_done = 0;
-    unsigned long long flops_k = 0;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(job.cursor, 1u);
-        __syncthreads();
-        const uint32_t t = s_tile;
-        if (t >= ntiles || s_abort) break;
-        uint32_t I, K;
-        tile_of(t, T, I, K);
-        const uint32_t c0 = I * (TC_TILE / TC_KC), c1 = (K + 1) * (TC_TILE / TC_KC);  // j chunks [c0, c1)
-        if (warp == 0 && lane == 0) {
-            // TMA producer
-            for (uint32_t c = c0; c < c1; ++c, ++it_prod) {
-                const uint32_t s = it_prod % TC_STAGES, ph = (it_prod / TC_STAGES) & 1u;
-                if (!mbar_wait(&empty[s], ph ^ 1u)) {
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            const uint32_t ntiles = grid.count();
+            uint32_t it = 0;
+            for (uint32_t n = 0;; ++n) {
+                const uint32_t r = n % TC_RING, rph = (n / TC_RING) & 1u;
+                if (!mbar_wait(&tempty[r], rph ^ 1u)) {
                     atomicOr(&st->err, ERR_TIMEOUT);
                     s_abort = 1;
                     break;
                 }
-                mbar_expect_tx(&full[s], TC_STAGE_BYTES);
-                const uint32_t a = base + s * TC_STAGE_BYTES;
-                tma_load_2d(a, &mapA, &full[s], (int)(c * TC_KC), (int)(I * TC_TILE));
-                tma_load_2d(a + TC_TILE_BYTES, &mapB, &full[s], (int)(c * TC_KC), (int)(K * TC_TILE));
+                const uint32_t t = s_abort ? ntiles : atomicAdd(job.cursor, 1u);
+                const uint32_t tile = t < ntiles ? grid.tile(t) : TC_NO_TILE;
+                s_tile[r] = tile;
+                mbar_arrive(&tfull[r]);
+                if (tile == TC_NO_TILE) break;
+                const uint32_t I = tile >> 16, P = tile & 0xffffu, c1 = min(2 * P + 2, (uint32_t)grid.R);
+                bool ok = true;
+                for (uint32_t c = I; c < c1; ++c, ++it) {
+                    const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+                    const uint32_t a = base + s * TC_STAGE_BYTES;
+                    tma_load_2d(a, &mapA, &full[s], (int)(c * TC_KC), (int)(I * TC_TILE));
+                    tma_load_2d(a + TC_A_BYTES, &mapB, &full[s], (int)(c * TC_KC), (int)(P * TC_N));
+                }
+                if (!ok) {
+                    atomicOr(&st->err, ERR_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
             }
-        } else if (warp == 1 && lane == 0) {
-            // MMA issuer
-            for (uint32_t c = c0; c < c1; ++c, ++it_mma) {
-                const uint32_t s = it_mma % TC_STAGES, ph = (it_mma / TC_STAGES) & 1u;
-                if (!mbar_wait(&full[s], ph)) {
+            s_issued = it;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            uint32_t it = 0;
+            unsigned long long kunits = 0;
+            bool issued = false;
+            for (uint32_t n = 0;; ++n) {
+                const uint32_t r = n % TC_RING, rph = (n / TC_RING) & 1u;
+                if (!mbar_wait(&tfull[r], rph)) {
+                    atomicOr(&st->err, ERR_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                const uint32_t tile = s_tile[r];
+                mbar_arrive(&tempty[r]);
+                if (tile == TC_NO_TILE) break;
+                const uint32_t I = tile >> 16, P = tile & 0xffffu, c1 = min(2 * P + 2, (uint32_t)grid.R);
+                const uint32_t acc = n % TC_ACCS, aph = (n / TC_ACCS) & 1u;
+                if (!mbar_wait(&aempty[acc], aph ^ 1u)) {  // the epilogue has read this accumulator
                     atomicOr(&st->err, ERR_TIMEOUT);
                     s_abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a = base + s * TC_STAGE_BYTES;
-                const uint64_t da = sw128_desc(a), db = sw128_desc(a + TC_TILE_BYTES);
-#pragma unroll
-                for (uint32_t kk = 0; kk < TC_KC / 32; ++kk)  // 32 fp8 = 32 B per MMA
-                    mma_fp8(tmem, da + 2 * kk, db + 2 * kk, (c > c0 || kk > 0) ? 1u : 0u);
-                mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
-            }
-            mma_commit(&done);  // accumulator complete
-            flops_k += (c1 - c0) * (TC_KC / 64);  // in 64-wide K units
-        }
-        __syncwarp();
-        // epilogue: rows 32 w .. 32 w + 31 of the tile, D masked by U
-        const bool ok = mbar_wait(&done, tiles_done & 1u);
-        if (!ok) {
-            if (lane == 0) atomicOr(&st->err, ERR_TIMEOUT);
-            s_abort = 1;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned long long sum = 0;
-        if (__all_sync(FULL, ok)) {
-            const uint32_t row = I * TC_TILE + warp * 32 + lane;
-            const uint8_t *urow = U + (uint64_t)row * hcap + (uint64_t)K * TC_TILE;
-#pragma unroll 1
-            for (uint32_t q = 0; q < TC_TILE / 32; ++q) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((warp * 32u) << 16) + q * 32, r);
-                const uint4 *m4 = reinterpret_cast<const uint4 *>(urow + q * 32);
-#pragma unroll
-                for (int v = 0; v < 2; ++v) {
-                    const uint4 mv = m4[v];
-                    const uint32_t w[4] = {mv.x, mv.y, mv.z, mv.w};
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const uint32_t byte = (w[e >> 2] >> ((e & 3) * 8)) & 0xffu;
-                        if (byte) sum += (uint32_t)__uint_as_float(r[v * 16 + e]);
+                const uint32_t d = tmem + acc * TC_N;
+                bool ok = true;
+                for (uint32_t c = I; c < c1; ++c, ++it) {
+                    const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
+                    if (!mbar_wait(&full[s], ph)) {
+                        ok = false;
+                        break;
                     }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a = base + s * TC_STAGE_BYTES;
+                    const uint64_t da = sw128_desc(a), db = sw128_desc(a + TC_A_BYTES);
+#pragma unroll
+                    for (uint32_t kk = 0; kk < TC_KC / 32; ++kk)  // 32 fp8 = 32 B per MMA
+                        mma_fp8(d, da + 2 * kk, db + 2 * kk, (c > I || kk > 0) ? 1u : 0u);
+                    issued = true;
+                    mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
                 }
+                if (!ok) {
+                    atomicOr(&st->err, ERR_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                mma_commit(&afull[acc]);  // accumulator complete
+                kunits += (unsigned long long)(c1 - I) * (TC_N / TC_TILE) * (TC_KC / 64);  // 128x128x64 units
             }
+            s_consumed = it;
+            if (issued) {  // every MMA of this CTA has finished before TMEM is freed
+                mma_commit(&drain);
+                if (!mbar_wait(&drain, 0u)) atomicOr(&st->err, ERR_TIMEOUT);
+            }
+            if (kunits) atomicAdd(&st->heavy_kchunks, kunits);
         }
-        sum = warp_sum(sum);
-        if (lane == 0) s_sum[warp] = sum;
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // TMEM is read: the next tile may overwrite it
-        if (threadIdx.x == 0) {
-            const unsigned long long tot = s_sum[0] + s_sum[1] + s_sum[2] + s_sum[3];
-            if (tot) atomicAdd(job.out, tot);
+    } else {
+        // epilogue: rows 32 (warp % 4) .. + 31 of each tile, D masked by U
+        const uint32_t quarter = warp & 3u;
+        unsigned long long total = 0;
+        for (uint32_t n = 0;; ++n) {
+            const uint32_t r = n % TC_RING, rph = (n / TC_RING) & 1u;
+            if (!__all_sync(FULL, mbar_wait(&tfull[r], rph))) {
+                if (lane == 0) atomicOr(&st->err, ERR_TIMEOUT);
+                s_abort = 1;
+                break;
+            }
+            const uint32_t tile = s_tile[r];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[r]);
+            if (tile == TC_NO_TILE) break;
+            const uint32_t I = tile >> 16, P = tile & 0xffffu;
+            const uint32_t acc = n % TC_ACCS, aph = (n / TC_ACCS) & 1u;
+            if (!__all_sync(FULL, mbar_wait(&afull[acc], aph))) {
+                if (lane == 0) atomicOr(&st->err, ERR_TIMEOUT);
+                s_abort = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t row = I * TC_TILE + quarter * 32 + lane;  // < hp <= hcap
+            const uint8_t *urow = U + (uint64_t)row * hcap + (uint64_t)P * TC_N;
+            const uint32_t ncols = min(TC_N, hp - P * TC_N);  // 128 or 256: columns below hp only
+            const uint32_t taddr = tmem + ((quarter * 32u) << 16) + acc * TC_N;
+            float fsum = 0.f;  // integers below 2^24: at most 256 terms of at most hcap <= 32768
+#pragma unroll 1
+            for (uint32_t q = 0; q < ncols / 32; ++q) {
+                const uint4 *m4 = reinterpret_cast<const uint4 *>(urow + q * 32);
+                const uint4 m0 = m4[0], m1 = m4[1];
+                const bool any = (m0.x | m0.y | m0.z | m0.w | m1.x | m1.y | m1.z | m1.w) != 0;
+                if (!__any_sync(FULL, any)) continue;  // warp-uniform: the load below is .sync.aligned
+                uint32_t v[32];
+                tmem_ld32(taddr + q * 32, v);
+                tmem_wait_ld();
+                const uint32_t w[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    if ((w[e >> 2] >> ((e & 3) * 8)) & 0xffu) fsum += __uint_as_float(v[e]);
+            }
+            total += (unsigned long long)fsum;
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&aempty[acc]);  // the MMA warp may overwrite it
         }
-        ++tiles_done;
+        total = warp_sum(total);
+        if (lane == 0 && total) atomicAdd(job.out, total);
     }
-    if (warp == 1 && lane == 0 && flops_k) atomicAdd(&st->heavy_kchunks, flops_k);
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x == 0 && s_abort) {
+        // copies issued that no MMA consumed must land before the CTA exits
+        for (uint32_t i = s_consumed; i < s_issued; ++i) mbar_wait(&full[i % TC_STAGES], (i / TC_STAGES) & 1u);
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_TMEM_COLS)
                      : "memory");
     }
@@ -469,12 +589,12 @@ bool heavy_make_maps(HeavyBuffers &hb)
     if (!enc || !hb.U || !hb.UT || hb.hcap == 0) return false;
     const cuuint64_t dims[2] = {hb.hcap, hb.hcap};
     const cuuint64_t strides[1] = {(cuuint64_t)hb.hcap};
-    const cuuint32_t box[2] = {TC_KC, TC_TILE};
+    const cuuint32_t boxes[2][2] = {{TC_KC, TC_TILE}, {TC_KC, TC_N}};  // A: 128 rows of U, B: 256 rows of U^T
     const cuuint32_t estr[2] = {1, 1};
     CUtensorMap *maps[2] = {reinterpret_cast<CUtensorMap *>(hb.mapA), reinterpret_cast<CUtensorMap *>(hb.mapB)};
     void *bufs[2] = {hb.U, hb.UT};
     for (int i = 0; i < 2; ++i) {
-        if (enc(maps[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, bufs[i], dims, strides, box, estr,
+        if (enc(maps[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, bufs[i], dims, strides, boxes[i], estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
