@@ -304,32 +304,58 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 
 // Output tiles: row panel I (128 rows) by column panel P (256 columns),
 // every pair with 2P + 1 >= I (the others lie below the diagonal, where U is
-// zero).  o = 2P + 1 - I is the tile's distance from the diagonal in
-// 128-wide blocks; its j-chunks are [I, min(2P + 2, R)), so a larger o means
-// more work, and tiles are handed out from the largest o down.
+// zero); tile (I, P) multiplies the j-chunks [I, min(2P + 2, R)).  Tiles are
+// handed out in groups of TC_GI row panels by TC_GP column panels, so that
+// the CTAs running at the same time read the same few operand panels (a
+// group's operands fit in L2).  Groups go column group by column group from
+// the right (the longest tiles first), down each column group; inside a
+// group, column panels from the right, row panels from the top.
+constexpr int TC_GI = 16, TC_GP = 8;
+constexpr int TC_MAX_GROUPS = 256;  // hcap <= 32768: 16 row groups x 16 column groups
+
 struct TileGrid {
-    int R, C;  // row panels (of 128) and column panels (of 256)
-    __device__ __forceinline__ int lo(int o) const { return o / 2; }
-    __device__ __forceinline__ int hi(int o) const
+    int R, C;    // row panels (of 128) and column panels (of 256)
+    int Rg, Cg;  // row groups and column groups
+    __device__ __forceinline__ uint32_t group_tiles(int gi, int gp) const
     {
-        const int x = R + o - 2;
-        return min(C - 1, x >= 0 ? x / 2 : -1);
-    }
-    __device__ uint32_t count() const
-    {
+        const int i0 = gi * TC_GI, i1 = min(i0 + TC_GI, R);
         uint32_t n = 0;
-        for (int o = 2 * C - 1; o >= 0; --o) n += (uint32_t)max(0, hi(o) - lo(o) + 1);
+        for (int P = gp * TC_GP; P < min(gp * TC_GP + TC_GP, C); ++P) n += (uint32_t)max(0, min(i1, 2 * P + 2) - i0);
         return n;
     }
-    // t-th tile (t < count()), packed as I << 16 | P
-    __device__ uint32_t tile(uint32_t t) const
+    // pre[k] = tiles of the groups before group k (k = 0 .. Rg Cg), one warp
+    __device__ void prefix(uint32_t *pre, unsigned lane) const
     {
-        for (int o = 2 * C - 1; o >= 0; --o) {
-            const uint32_t cnt = (uint32_t)max(0, hi(o) - lo(o) + 1);
-            if (t < cnt) {
-                const int P = lo(o) + (int)t;
-                return (uint32_t)(2 * P + 1 - o) << 16 | (uint32_t)P;
+        const int G = Rg * Cg;
+        uint32_t carry = 0;
+        for (int k0 = 0; k0 < G; k0 += 32) {
+            const int k = k0 + (int)lane;
+            uint32_t x = k < G ? group_tiles(k % Rg, Cg - 1 - k / Rg) : 0u;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, x, d);
+                if ((int)lane >= d) x += y;
             }
+            if (k < G) pre[k + 1] = carry + x;
+            carry += __shfl_sync(FULL, x, 31);
+        }
+        if (lane == 0) pre[0] = 0;
+    }
+    // t-th tile (t < pre[Rg Cg]), packed as I << 16 | P
+    __device__ uint32_t tile(const uint32_t *pre, uint32_t t) const
+    {
+        int lo = 0, hi = Rg * Cg;  // pre[lo] <= t < pre[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pre[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        t -= pre[lo];
+        const int gi = lo % Rg, gp = Cg - 1 - lo / Rg;
+        const int i0 = gi * TC_GI, i1 = min(i0 + TC_GI, R);
+        for (int P = min(gp * TC_GP + TC_GP, C) - 1; P >= gp * TC_GP; --P) {
+            const uint32_t cnt = (uint32_t)max(0, min(i1, 2 * P + 2) - i0);
+            if (t < cnt) return (uint32_t)(i0 + (int)t) << 16 | (uint32_t)P;
             t -= cnt;
         }
         return TC_NO_TILE;
@@ -361,13 +387,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
     __shared__ __align__(8) uint64_t tfull[TC_RING], tempty[TC_RING], afull[TC_ACCS], aempty[TC_ACCS], drain;
-    __shared__ uint32_t s_tile[TC_RING];
+    __shared__ uint32_t s_tile[TC_RING], s_pre[TC_MAX_GROUPS + 1];
     __shared__ uint32_t s_tmem, s_issued, s_consumed;
     __shared__ volatile uint32_t s_abort;
     if (!*job.enable) return;  // uniform: written before this launch
     const uint32_t h = job.h_dev ? *job.h_dev : job.h_host;
     const uint32_t hp = (h + TC_TILE - 1) / TC_TILE * TC_TILE;
-    const TileGrid grid{(int)(hp / TC_TILE), (int)((hp / TC_TILE + 1) / 2)};
+    const int R = (int)(hp / TC_TILE), C = (R + 1) / 2;
+    const TileGrid grid{R, C, (R + TC_GI - 1) / TC_GI, (C + TC_GP - 1) / TC_GP};
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
@@ -396,6 +423,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
         s_issued = 0;
         s_consumed = 0;
     }
+    if (warp == 0) grid.prefix(s_pre, lane);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -403,7 +431,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
-            const uint32_t ntiles = grid.count();
+            const uint32_t ntiles = s_pre[grid.Rg * grid.Cg];
             uint32_t it = 0;
             for (uint32_t n = 0;; ++n) {
                 const uint32_t r = n % TC_RING, rph = (n / TC_RING) & 1u;
@@ -413,7 +441,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
                     break;
                 }
                 const uint32_t t = s_abort ? ntiles : atomicAdd(job.cursor, 1u);
-                const uint32_t tile = t < ntiles ? grid.tile(t) : TC_NO_TILE;
+                const uint32_t tile = t < ntiles ? grid.tile(s_pre, t) : TC_NO_TILE;
                 s_tile[r] = tile;
                 mbar_arrive(&tfull[r]);
                 if (tile == TC_NO_TILE) break;
