@@ -101,19 +101,24 @@ def make_graph():
     return gen.cached("chung_lu", gen.chung_lu, w["n"], w["m"], w["gamma"], w["wmax"], w["graph_seed"])
 
 
-def recorded_traffic():
-    """DRAM bytes of the intersection kernels from the committed ncu capture
-    (profiles/traffic.json), or None when a source it depends on has changed
-    (sha1 of the listed files, concatenated in order)."""
+def recorded_traffic(workload, kernel):
+    """DRAM bytes per launch of the roofline kernel on this workload from the
+    committed ncu capture (profiles/traffic.json), or None when there is no
+    record or a source it depends on has changed (sha1 of the listed files,
+    concatenated in order)."""
     import hashlib
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in rec["sources"])
-        if hashlib.sha1(src).hexdigest()[:12] != rec["sources_sha1_12"]:
-            return None
-        return float(rec["dram_bytes"])
+        recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["records"]
+        for rec in recs:
+            if rec["workload"] != workload or rec["kernel"] != kernel:
+                continue
+            src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in rec["sources"])
+            if hashlib.sha1(src).hexdigest()[:12] != rec["sources_sha1_12"]:
+                return None
+            return float(rec["dram_bytes"])
     except Exception:
-        return None
+        pass
+    return None
 
 
 def measured_peaks():
@@ -290,7 +295,7 @@ def our_arm(args):
     b_isect = 4.0 * (results[j1]["src_elems"] + results[j1]["nbr_elems"])
     achieved = b_isect / t_isect / 1e9 if t_isect > 0 else 0.0
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic = recorded_traffic()
+    traffic = recorded_traffic(WORKLOAD["workload"], "k_probe_warp+k_probe_block")
     roofline = {"bound": "hbm", "kernel": "k_probe_warp+k_probe_block (p=1 count)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src, "traffic": traffic,
@@ -312,11 +317,14 @@ def our_arm(args):
                     "achieved": flops / t_heavy / 1e12 if t_heavy > 0 else 0.0, "peak": tf,
                     "unit": "TFLOP/s", "frac": (flops / t_heavy / 1e12) / tf if t_heavy > 0 else 0.0,
                     "peak_source": peak_src + " bf16 burst x 2 (fp8 e4m3 operands; kernel of a few ms inside one count)",
-                    "traffic": None, "executed_flops_per_launch": flops,
+                    "traffic": recorded_traffic(WORKLOAD["workload"], "k_heavy_tc"),
+                    "executed_flops_per_launch": flops,
                     "useful_flops_per_launch": h * (h - 1) * (h - 2) / 3.0, "launch_ms": t_heavy * 1000.0,
                     "phase_ms": {str(p): {"sample": float(per_leg[p][0]), "csr": float(per_leg[p][1]),
                                           "intersect": float(per_leg[p][2]), "heavy": float(per_leg[p][3])}
                                  for p in ps}}
+        if roofline["traffic"] and t_heavy > 0:
+            roofline["traffic_gbs"] = roofline["traffic"] / t_heavy / 1e9
 
     # ---- end to end through the C ABI from pinned host memory
     e2e_steps = max(1, min(5, args.steps))
