@@ -13,6 +13,12 @@ whole job.  The edge list (512 MiB) is larger than L2, so no L2 flush is
 needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload chung_lu|rmat26|dense_core|batch|serve]
+
+Other workloads: rmat26 is the largest graph (R-MAT scale 26, edge factor
+16: the library canonicalises the 2^30 raw draws into about 10^9 edges; one
+step counts p = 1 and 0.05); dense_core stresses the tensor-core heavy block;
+batch and serve time the batched and served forms against the plain path.
 
 With N > 1 (torchrun, one process per GPU) every rank counts its own replica
 of the workload (no data-path collective); time is the max over ranks.
@@ -37,6 +43,10 @@ WORKLOADS = {
     # the headline workload: power-law graph shaped like the paper's social networks
     "chung_lu": {"workload": "chung_lu_n4M_m64M_gamma2.1", "kind": "chung_lu", "n": 1 << 22, "m": 1 << 26,
                  "gamma": 2.1, "wmax": 1e5, "graph_seed": 1, "p_sweep": [1.0, 0.1, 0.01]},
+    # the largest graph: R-MAT scale 26, edge factor 16; the library gets the
+    # 2^30 raw draws and canonicalises them itself (about 10^9 distinct edges)
+    "rmat26": {"workload": "rmat_s26_ef16", "kind": "rmat", "n": 1 << 26, "scale": 26, "edge_factor": 16,
+               "abc": (0.57, 0.19, 0.19), "graph_seed": 1, "p_sweep": [1.0, 0.05], "oracle_draws": 1 << 26},
     # heavy-block stress: 16384-vertex core at pair density 0.7 (all heavy) in a
     # sparse 2^20-vertex graph; measures the tensor-core contraction
     "dense_core": {"workload": "dense_core_n1M_core16384_q0.7", "kind": "dense_core", "n": 1 << 20,
@@ -93,9 +103,13 @@ def job_throughput(ws: int, steps: int, counts_per_step: int, m: int, elapsed_ms
     return ws * steps * counts_per_step * m / (elapsed_ms / 1000.0)
 
 
-def make_graph():
+def make_graph(out=None):
+    """The workload's input pairs: a canonical edge list, or for R-MAT the raw
+    draws (written into out when given, e.g. a pinned host array)."""
     import gen
     w = WORKLOAD
+    if w["kind"] == "rmat":
+        return gen.rmat_draws(w["scale"], w["edge_factor"], *w["abc"], seed=w["graph_seed"], out=out)
     if w["kind"] == "dense_core":
         return gen.cached("planted_core", gen.planted_core, w["n"], w["core"], w["q"], w["m_rest"], w["graph_seed"])
     return gen.cached("chung_lu", gen.chung_lu, w["n"], w["m"], w["gamma"], w["wmax"], w["graph_seed"])
@@ -181,43 +195,58 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(edges, n):
-    """The oracle (one thread) on the p = 0.1 leg of the sweep, seed 1."""
+def oracle_sample(edges, n):
+    """The oracle's bounded sample of the workload: (canonical edges, p, what
+    it is).  R-MAT: the subgraph of the first oracle_draws raw draws,
+    canonicalised by the oracle, at the sweep's smallest p (the whole graph
+    takes hours single-threaded); otherwise the whole graph at p = 0.1."""
     import oracle
     oracle.build()
+    w = WORKLOAD
+    if w["kind"] == "rmat":
+        k = w["oracle_draws"]
+        canon = oracle.canonicalize(edges[:k], n)
+        p = min(w["p_sweep"])
+        return canon, p, ("the subgraph of the first %d of the %d raw draws (%d distinct edges, canonicalised "
+                          "by the oracle), p=%g" % (k, len(edges), len(canon), p))
+    return edges, 0.1, "the full graph at p=0.1 (one of the sweep legs; the p=1 leg takes minutes)"
+
+
+def cpu_baseline(edges, n):
+    """The oracle (one thread) on its bounded sample of the workload, seed 1."""
+    import oracle
+    canon, p, what = oracle_sample(edges, n)
     t0 = time.perf_counter()
-    oracle.run(edges, n, 0.1, 1)
+    oracle.run(canon, n, p, 1)
     dt = time.perf_counter() - t0
-    return {"value": len(edges) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "CPU oracle, 1 thread, full %s graph at p=0.1 seed 1 (one of the three sweep legs; "
-                      "the p=1 leg takes minutes single-threaded): %.2f s for %d input edges" %
-                      (WORKLOAD["workload"], dt, len(edges))}
+    return {"value": len(canon) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "CPU oracle, 1 thread, %s: %s, seed 1: %.2f s for %d input edges" %
+                      (WORKLOAD["workload"], what, dt, len(canon))}
 
 
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    oracle.build()
-    edges = make_graph()
     n = WORKLOAD["n"]
+    edges, p, what = oracle_sample(make_graph(), n)
+    import oracle
     for i in range(args.warmup):
-        oracle.run(edges, n, 0.1, i + 1)
+        oracle.run(edges, n, p, i + 1)
     times = []
     for k in range(args.steps):
         t0 = time.perf_counter()
-        oracle.run(edges, n, 0.1, k + 1)
+        oracle.run(edges, n, p, k + 1)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = args.steps * len(edges) / total
-    sample = ("CPU oracle, 1 thread: each step is the p=0.1 leg (seed = step + 1) on the full %s graph"
-              % WORKLOAD["workload"])
+    sample = ("CPU oracle, 1 thread: each step is %s (seed = step + 1) of the %s workload"
+              % (what, WORKLOAD["workload"]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": {"workload": WORKLOAD["workload"], "n": n, "m": len(edges),
-                                            "p_sweep": [0.1]},
+                                            "p_sweep": [p]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -239,15 +268,21 @@ def our_arm(args):
     tc.lib()
     tc.use_torch_allocator(True)
 
-    edges = make_graph()
-    n, m = WORKLOAD["n"], len(edges)
-    ps = WORKLOAD["p_sweep"]
-    host = torch.from_numpy(edges).pin_memory()
+    n, ps = WORKLOAD["n"], WORKLOAD["p_sweep"]
+    if WORKLOAD["kind"] == "rmat":  # raw draws straight into pinned memory
+        w = WORKLOAD
+        host = torch.empty((w["edge_factor"] << w["scale"], 2), dtype=torch.int32, pin_memory=True)
+        edges = make_graph(out=host.numpy().view(np.uint32))
+    else:
+        edges = make_graph()
+        host = torch.from_numpy(edges).pin_memory()
+    m_in = len(edges)
     stream = torch.cuda.Stream()
     res_buf = torch.zeros((len(ps), ctypes.sizeof(tc.tc_result)), dtype=torch.uint8, pin_memory=True)
 
-    g = tc.Graph.from_address(host.data_ptr(), m, n, on_device=False, stream=stream)
-    assert g.m == m
+    g = tc.Graph.from_address(host.data_ptr(), m_in, n, on_device=False, stream=stream)
+    m = g.m  # distinct undirected edges: the unit of the metric
+    assert WORKLOAD["kind"] == "rmat" or m == m_in
 
     def step(k):
         for j, p in enumerate(ps):
@@ -333,7 +368,7 @@ def our_arm(args):
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        h = tc.Graph.from_address(host.data_ptr(), m, n, on_device=False, stream=stream)
+        h = tc.Graph.from_address(host.data_ptr(), m_in, n, on_device=False, stream=stream)
         for j, p in enumerate(ps):
             h.count_async(p, k + 1, out_host[j].data_ptr())
         h.sync()
@@ -344,19 +379,19 @@ def our_arm(args):
     g.close()
     if rank == 0:
         cpu = None
-        if ws == 1 and not args.no_cpu_baseline and WORKLOAD["kind"] == "chung_lu":
+        if ws == 1 and not args.no_cpu_baseline and WORKLOAD["kind"] in ("chung_lu", "rmat"):
             cpu = cpu_baseline(edges, n)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD["workload"], "n": n, "m": m, "p_sweep": ps,
+                "config": {"workload": WORKLOAD["workload"], "n": n, "m": m, "m_input_pairs": m_in, "p_sweep": ps,
                            "counts_per_step": len(ps), "parallelism": "replicas" if ws > 1 else "single",
-                           "l2": "inputs larger than L2 (512 MiB edge list)"},
+                           "l2": "inputs larger than L2 (%d MiB edge list)" % (8 * m >> 20)},
                 "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(8 * m),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(8 * m_in),
                         "d2h_bytes_per_step": int(len(ps) * ctypes.sizeof(tc.tc_result)),
-                        "steps": e2e_steps, "includes": "tc_graph_create from pinned host edges + 3 counts "
-                                                        "+ result copies + destroy"},
+                        "steps": e2e_steps, "includes": "tc_graph_create from pinned host pairs + %d counts "
+                                                        "+ result copies + destroy" % len(ps)},
                 "gpu_launches": int(launches), "clocks": clocks.summary(),
                 "results": [{k: r[k] for k in ("m_sampled", "n_heavy", "t_light", "t_heavy", "estimate")}
                             for r in results],

@@ -7,7 +7,10 @@ shape: Erdos-Renyi G(n, m), Chung-Lu power-law graphs and R-MAT graphs (in C,
 (complete graphs, wheels, stars, trees, cycles, complete bipartite graphs).
 
 Every function returns a canonical edge list: a ``(m, 2)`` uint32 numpy array
-of pairs ``(u, v)`` with ``u < v``, sorted, without duplicates or self-loops.
+of pairs ``(u, v)`` with ``u < v``, sorted, without duplicates or self-loops;
+the one exception, ``rmat_draws``, returns the raw draws of an R-MAT graph
+(whose canonical form is ``rmat``'s output) for inputs too large to
+deduplicate quickly on the host.
 Nothing here counts triangles or samples edges for the method; the outputs
 are inputs to both the CPU oracle and the CUDA library.
 """
@@ -49,6 +52,11 @@ def _load():
         lib.gen_rmat.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_uint64, u32p]
         lib.gen_rmat.restype = ctypes.c_int64
+        lib.gen_rmat_perm.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p]
+        lib.gen_rmat_perm.restype = ctypes.c_int
+        lib.gen_rmat_draws.argtypes = [ctypes.c_uint32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_uint64, u32p, ctypes.c_uint64, ctypes.c_uint64, u32p]
+        lib.gen_rmat_draws.restype = ctypes.c_int
         lib.gen_planted_core.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint64,
                                          ctypes.c_uint64, u32p]
         lib.gen_planted_core.restype = ctypes.c_int64
@@ -89,6 +97,36 @@ def rmat(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: floa
     if r < 0:
         raise ValueError("gen_rmat failed (%d)" % r)
     return np.ascontiguousarray(out[:r])
+
+
+def rmat_draws(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+               seed: int = 1, out: np.ndarray | None = None, threads: int | None = None) -> np.ndarray:
+    """The edge_factor * 2**scale raw draws of rmat(scale, edge_factor, a, b,
+    c, seed) as (u, v) pairs in draw order, ids permuted, self-loops and
+    repeats included: symmetrising and deduplicating them gives rmat's graph.
+    Filled by several threads (each draw depends only on its index); out, if
+    given, is a (draws, 2) uint32 array (e.g. in pinned memory)."""
+    from concurrent.futures import ThreadPoolExecutor
+    draws = edge_factor << scale
+    if out is None:
+        out = np.empty((draws, 2), dtype=np.uint32)
+    assert out.shape == (draws, 2) and out.dtype == np.uint32 and out.flags.c_contiguous
+    lib = _load()
+    perm = np.empty(1 << scale, dtype=np.uint32)
+    if lib.gen_rmat_perm(scale, seed, _ptr(perm)) != 0:
+        raise ValueError("gen_rmat_perm failed")
+    threads = threads or max(1, min(64, os.cpu_count() or 1))
+    step = -(-draws // (4 * threads))
+
+    def fill(e0):
+        e1 = min(draws, e0 + step)
+        sub = out[e0:e1]
+        return lib.gen_rmat_draws(scale, a, b, c, seed, _ptr(perm), e0, e1, _ptr(sub))
+
+    with ThreadPoolExecutor(threads) as ex:
+        if any(r != 0 for r in ex.map(fill, range(0, draws, step))):
+            raise ValueError("gen_rmat_draws failed")
+    return out
 
 
 def planted_core(n: int, core: int, q: float, m_rest: int, seed: int) -> np.ndarray:

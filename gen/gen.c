@@ -333,40 +333,92 @@ int64_t gen_planted_core(uint32_t n, uint32_t core, double q, uint64_t m_rest, u
 
 /* ------------------------------------------------------- R-MAT */
 
+/* quadrant thresholds on 16-bit uniforms: four levels per 64-bit draw */
+typedef struct {
+    uint32_t ta, tb, tc;
+} g_rmat_t;
+
+static int g_rmat_thresholds(double a, double b, double c, g_rmat_t *t)
+{
+    if (a < 0 || b < 0 || c < 0 || a + b + c > 1.0) return -1;
+    t->ta = (uint32_t)(a * 65536.0);
+    t->tb = (uint32_t)((a + b) * 65536.0);
+    t->tc = (uint32_t)((a + b + c) * 65536.0);
+    return 0;
+}
+
+/* Draw e: `scale` levels of the adjacency quadtree, each taking quadrant
+   (0,0), (0,1), (1,0), (1,1) with probabilities a, b, c, 1-a-b-c; the
+   positions before the vertex permutation. */
+static inline void g_rmat_draw(uint32_t scale, const g_rmat_t *t, uint64_t seed, uint64_t e, uint32_t *pu,
+                               uint32_t *pv)
+{
+    uint32_t u = 0, v = 0;
+    uint64_t r = 0;
+    for (uint32_t l = 0; l < scale; ++l) {
+        if ((l & 3) == 0) r = g_rand(seed, 3 + l / 4, e);
+        uint32_t x = (uint32_t)(r & 0xffff);
+        r >>= 16;
+        uint32_t ubit = x >= t->tb, vbit = (x >= t->ta && x < t->tb) || x >= t->tc;
+        u = (u << 1) | ubit;
+        v = (v << 1) | vbit;
+    }
+    *pu = u;
+    *pv = v;
+}
+
+/* The seeded vertex permutation of an R-MAT graph (perm holds 2^scale). */
+int gen_rmat_perm(uint32_t scale, uint64_t seed, uint32_t *perm)
+{
+    if (scale < 1 || scale > 31) return -1;
+    g_perm(perm, 1u << scale, seed, 11);
+    return 0;
+}
+
+/*
+ * Draws [e0, e1) of the R-MAT graph as raw pairs (perm[u], perm[v]) in draw
+ * order, self-loops and repeats included (out_pairs holds 2 (e1 - e0)
+ * uint32).  Symmetrising, deduplicating and dropping self-loops over all
+ * edge_factor 2^scale draws gives exactly gen_rmat's graph.  Disjoint ranges
+ * may be filled concurrently.
+ */
+int gen_rmat_draws(uint32_t scale, double a, double b, double c, uint64_t seed, const uint32_t *perm,
+                   uint64_t e0, uint64_t e1, uint32_t *out_pairs)
+{
+    g_rmat_t t;
+    if (scale < 1 || scale > 31 || g_rmat_thresholds(a, b, c, &t)) return -1;
+    for (uint64_t e = e0; e < e1; ++e) {
+        uint32_t u, v;
+        g_rmat_draw(scale, &t, seed, e, &u, &v);
+        out_pairs[2 * (e - e0)] = perm[u];
+        out_pairs[2 * (e - e0) + 1] = perm[v];
+    }
+    return 0;
+}
+
 /*
  * R-MAT graph with 2^scale vertices and edge_factor * 2^scale generated
- * edges: each edge descends `scale` levels of the adjacency quadtree, taking
- * quadrant (0,0), (0,1), (1,0), (1,1) with probabilities a, b, c, 1-a-b-c.
- * Vertex ids are then scrambled by a seeded permutation (as Graph500 does),
- * the result is symmetrised (u, v) -> (min, max) and deduplicated, and
- * self-loops are dropped.  out_pairs must hold 2 * edge_factor * 2^scale
- * uint32.  Returns the number of distinct undirected edges.
+ * edges (g_rmat_draw).  Vertex ids are then scrambled by a seeded
+ * permutation (as Graph500 does), the result is symmetrised (u, v) ->
+ * (min, max) and deduplicated, and self-loops are dropped.  out_pairs must
+ * hold 2 * edge_factor * 2^scale uint32.  Returns the number of distinct
+ * undirected edges.
  */
 int64_t gen_rmat(uint32_t scale, uint32_t edge_factor, double a, double b, double c,
                  uint64_t seed, uint32_t *out_pairs)
 {
-    if (scale < 1 || scale > 31 || a < 0 || b < 0 || c < 0 || a + b + c > 1.0) return -1;
+    g_rmat_t t;
+    if (scale < 1 || scale > 31 || g_rmat_thresholds(a, b, c, &t)) return -1;
     const uint32_t n = 1u << scale;
     const uint64_t draws = (uint64_t)edge_factor << scale;
     uint32_t *perm = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
     uint64_t *keys = (uint64_t *)malloc((draws ? draws : 1) * sizeof(uint64_t));
     if (!perm || !keys) { free(perm); free(keys); return -3; }
     g_perm(perm, n, seed, 11);
-    /* quadrant thresholds on 16-bit uniforms: four levels per 64-bit draw */
-    const uint32_t ta = (uint32_t)(a * 65536.0), tb = (uint32_t)((a + b) * 65536.0),
-                   tc = (uint32_t)((a + b + c) * 65536.0);
     uint64_t cnt = 0;
     for (uint64_t e = 0; e < draws; ++e) {
-        uint32_t u = 0, v = 0;
-        uint64_t r = 0;
-        for (uint32_t l = 0; l < scale; ++l) {
-            if ((l & 3) == 0) r = g_rand(seed, 3 + l / 4, e);
-            uint32_t x = (uint32_t)(r & 0xffff);
-            r >>= 16;
-            uint32_t ubit = x >= tb, vbit = (x >= ta && x < tb) || x >= tc;
-            u = (u << 1) | ubit;
-            v = (v << 1) | vbit;
-        }
+        uint32_t u, v;
+        g_rmat_draw(scale, &t, seed, e, &u, &v);
         u = perm[u];
         v = perm[v];
         if (u == v) continue;

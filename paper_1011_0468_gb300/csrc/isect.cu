@@ -534,9 +534,8 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
 
 // ---------------------------------------------------------------- block items
 
-constexpr int PB_THREADS = 128;
-constexpr int PB_WARPS = PB_THREADS / 32;
-constexpr uint32_t PB_PER_THREAD = SEG_B / PB_THREADS;  // partner slots set up per thread (at most)
+constexpr int PB_THREADS = 128;       // mid owners: eight CTAs per SM, one small table each
+constexpr int PB_DYN_THREADS = 1024;  // large owners: one CTA per SM around one table of up to 128 KiB
 constexpr uint32_t MID_TAB = 4096;                      // >= 4 * MID_MAX slots (dynamic shared memory)
 constexpr uint32_t UNIT = 128;                          // chunks per unit of block streaming
 constexpr uint32_t PRE_CLS = 0x80000000u;               // class bit beside a partner's chunk prefix
@@ -601,7 +600,7 @@ __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, cons
 // counter, so they finish within one unit of each other.  The owner's hash
 // set sits in dynamic shared memory (tab_slots slots).
 template <bool DYN>
-__global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 8) k_probe_block(const uint32_t *__restrict__ ptrp,
+__global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8) k_probe_block(const uint32_t *__restrict__ ptrp,
                                                                       const uint32_t *__restrict__ col,
                                                                       const uint32_t *__restrict__ rowptr,
                                                                       const uint32_t *__restrict__ olist,
@@ -616,6 +615,8 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 8) k_probe_block(const u
                                                                       uint64_t cap, BatchView bv, IsectConfig cfg,
                                                                       uint32_t core_base)
 {
+    constexpr uint32_t NT = DYN ? PB_DYN_THREADS : PB_THREADS;
+    constexpr uint32_t PER_MAX = (SEG_B + NT - 1) / NT;  // partner slots set up per thread (at most)
     extern __shared__ uint2 tab[];
     __shared__ uint32_t s_c0[SEG_B];
     __shared__ uint32_t s_pre[SEG_B];  // chunk prefix | PRE_CLS (both endpoints heavy)
@@ -645,21 +646,21 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 8) k_probe_block(const u
         const uint32_t slots = table_slots(d, tab_slots);
         const BucketSet set{tab, slots ? (slots >> 1) - 1 : 0u, slots ? bucket_shift(slots) : 0u};
         if (slots) {
-            for (uint32_t i = threadIdx.x; i < (slots >> 1); i += PB_THREADS) tab[i] = make_uint2(EMPTY, EMPTY);
+            for (uint32_t i = threadIdx.x; i < (slots >> 1); i += NT) tab[i] = make_uint2(EMPTY, EMPTY);
             __syncthreads();
-            for (uint32_t i = threadIdx.x; i < d; i += PB_THREADS)
+            for (uint32_t i = threadIdx.x; i < d; i += NT)
                 bucket_insert(tab, set.mask, set.shift, __ldg(col + row.beg + i));
         }
         if (seg == 0 && threadIdx.x == 0) t.table += d;
         const uint32_t ob = rowptr[x], oc = ocnt[x], ib = inptr[x], np = oc + (inend[x] - ib);
         const uint32_t sl = seg_len(d, 1, cfg);
         const uint32_t p0 = seg * sl, p1 = min(np, p0 + sl);
-        const uint32_t per = sl / PB_THREADS;  // <= PB_PER_THREAD
+        const uint32_t per = (sl + NT - 1) / NT;  // <= PER_MAX
         // set up this thread's `per` consecutive partners
-        uint32_t pc0[PB_PER_THREAD], pncc[PB_PER_THREAD];
+        uint32_t pc0[PER_MAX], pncc[PER_MAX];
         unsigned long long mine = 0;  // live partners << 32 | their chunks
 #pragma unroll
-        for (uint32_t q = 0; q < PB_PER_THREAD; ++q) {
+        for (uint32_t q = 0; q < PER_MAX; ++q) {
             const uint32_t j = p0 + threadIdx.x * per + q;
             uint32_t c0 = 0, nc = 0, hh = 0;
             if (q < per && j < p1) {
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(PB_THREADS, DYN ? 1 : 8) k_probe_block(const u
         const unsigned long long ex = block_excl_scan(mine, wt, &tot);  // also orders the set build
         uint32_t r = (uint32_t)(ex >> 32), pre = (uint32_t)ex;
 #pragma unroll
-        for (uint32_t q = 0; q < PB_PER_THREAD; ++q) {
+        for (uint32_t q = 0; q < PER_MAX; ++q) {
             const uint32_t nc = pncc[q] >> 1;
             if (nc) {
                 s_c0[r] = pc0[q];
@@ -745,7 +746,7 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
                                                                    b.heavy, b.st, MID_TAB, b.items_cap, b.bv, b.cfg,
                                                                    b.core_base);
     note_launch();
-    k_probe_block<true><<<152, PB_THREADS, dyn_smem_bytes, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
+    k_probe_block<true><<<152, PB_DYN_THREADS, dyn_smem_bytes, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
                                                                 b.inend, b.inlist, b.items, wm,
                                                                 b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
                                                                 b.items_cap, b.bv, b.cfg, b.core_base);

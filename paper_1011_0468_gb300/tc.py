@@ -303,17 +303,19 @@ class Graph:
     def sync(self):
         tc_graph_sync(self.handle)
 
-    def export_sample(self, p: float, seed: int):
-        """(kept pairs in canonical order, heavy flags, sampled degrees)."""
+    def export_sample(self, p: float, seed: int, pairs: bool = True):
+        """(kept pairs in canonical order, heavy flags, sampled degrees); with
+        pairs=False the first item is None and the kept pairs are not copied."""
         m, n = self.m, self.n
-        kept = np.empty((max(m, 1), 2), dtype=np.uint32)
+        kept = np.empty((max(m, 1), 2), dtype=np.uint32) if pairs else None
         heavy = np.empty(max(n, 1), dtype=np.uint8)
         deg = np.empty(max(n, 1), dtype=np.uint32)
         mp = ctypes.c_uint64(0)
         _check(lib().tc_graph_export_sample(self.handle, p, seed & 0xFFFFFFFFFFFFFFFF,
-                                            kept.ctypes.data_as(_u32p), heavy.ctypes.data_as(_u8p),
-                                            deg.ctypes.data_as(_u32p), ctypes.byref(mp)), "tc_graph_export_sample")
-        return kept[:mp.value], heavy[:n], deg[:n]
+                                            kept.ctypes.data_as(_u32p) if pairs else None,
+                                            heavy.ctypes.data_as(_u8p), deg.ctypes.data_as(_u32p),
+                                            ctypes.byref(mp)), "tc_graph_export_sample")
+        return (kept[:mp.value] if pairs else None), heavy[:n], deg[:n]
 
     def export_csr(self, p: float, seed: int):
         """(rowptr[n+1], col[m_p]) of the degree-oriented sampled graph."""

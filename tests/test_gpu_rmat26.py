@@ -1,0 +1,89 @@
+"""Full-size parity on the largest graph: R-MAT, scale 26, edge factor 16,
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), seed 1, about 10^9 undirected edges.
+
+The library is given the 2^30 raw draws (ids permuted; repeats, reversed
+repeats and self-loops included) and canonicalises them itself on the GPU.
+Expected values come from tests/golden/rmat_s26.json, written by
+tests/golden/make_golden.py from the CPU oracle on the graph deduplicated on
+the host:
+- the number of canonical edges, the exact degree of every vertex and the
+  heavy flags of the whole graph (p = 1);
+- at p = 0.05 (seeds 1 and 2): m_p, the per-class counts, the estimate, and
+  checksums of the kept edges and heavy flags;
+- at p = 1 the per-class counts, when the oracle's hours-long run is stored.
+"""
+import importlib.util
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden", "rmat_s26.json")
+
+
+def _make_golden():
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(HERE, "golden", "make_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.fixture(scope="module")
+def rmat():
+    from paper_1011_0468_gb300 import _build, tc
+    _build.build()
+    rec = json.load(open(GOLDEN))
+    s = rec["spec"]
+    draws = gen.rmat_draws(s["scale"], s["edge_factor"], s["a"], s["b"], s["c"], s["seed"])
+    g = tc.Graph(draws, s["n"])
+    del draws
+    yield rec, g
+    g.close()
+
+
+def test_canonical_graph_degrees_and_partition(rmat):
+    rec, g = rmat
+    mg = _make_golden()
+    assert g.m == rec["m"]
+    _, heavy, deg = g.export_sample(1.0, 1, pairs=False)
+    assert int(deg.max()) == rec["max_degree"]
+    assert mg.deg_checksum(deg) == rec["deg_checksum"]
+    assert int(heavy.sum()) == rec["n_heavy"]
+    assert mg.heavy_checksum(heavy) == rec["heavy_checksum"]
+
+
+def test_stored_oracle_counts(rmat):
+    rec, g = rmat
+    for r in rec["runs"]:
+        got = g.count(r["p"], r["seed"])
+        for k in ("m_sampled", "n_heavy", "t_light", "t_heavy"):
+            assert got[k] == r[k], (r["p"], r["seed"], k, got[k], r[k])
+        assert got["estimate"] == float.fromhex(r["estimate_hex"])
+
+
+def test_sampled_edges_and_flags(rmat):
+    rec, g = rmat
+    mg = _make_golden()
+    runs = [r for r in rec["runs"] if "kept_checksum" in r and r["p"] < 1.0]
+    assert runs
+    for r in runs[:1]:  # one export: it copies the whole graph's keys to the host
+        kept, heavy, _ = g.export_sample(r["p"], r["seed"])
+        assert len(kept) == r["m_sampled"]
+        assert mg.checksum(kept) == r["kept_checksum"]
+        assert mg.heavy_checksum(heavy) == r["heavy_checksum"]
+
+
+def test_exact_count_properties_at_p1(rmat):
+    """At p = 1 every edge is kept and the estimate is the integer count."""
+    rec, g = rmat
+    got = g.count(1.0, 1)
+    assert got["m_sampled"] == rec["m"] and got["n_heavy"] == rec["n_heavy"]
+    assert got["estimate"] == float(got["t_light"] + got["t_heavy"])
+    again = g.count(1.0, 2)  # the seed does not matter at p = 1
+    assert (again["m_sampled"], again["t_light"], again["t_heavy"]) == (got["m_sampled"], got["t_light"],
+                                                                        got["t_heavy"])
