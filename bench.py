@@ -75,6 +75,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of Poisson arrivals")
+    ap.add_argument("--rmat-scale", type=int, default=None,
+                    help="rmat26: another R-MAT scale (e.g. a smaller case for profiling)")
     return ap.parse_args()
 
 
@@ -638,7 +640,11 @@ def serve_arm(args):
 def main():
     global WORKLOAD
     args = parse_args()
-    WORKLOAD = WORKLOADS[args.workload]
+    WORKLOAD = dict(WORKLOADS[args.workload])
+    if args.rmat_scale is not None and WORKLOAD["kind"] == "rmat":
+        sc = args.rmat_scale
+        WORKLOAD.update(scale=sc, n=1 << sc, workload="rmat_s%d_ef%d" % (sc, WORKLOAD["edge_factor"]),
+                        oracle_draws=min(WORKLOAD["oracle_draws"], WORKLOAD["edge_factor"] << sc))
     if WORKLOAD["kind"] == "serve":
         if args.impl == "ours":
             serve_arm(args)

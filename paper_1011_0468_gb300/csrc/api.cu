@@ -138,6 +138,7 @@ struct tc_graph {
     uint32_t *scan = nullptr;   // scan scratch
     HeavyBuffers hb;            // dense heavy block (hb.hcap == 0: not used)
     CoreBuffers core;           // dense core of the top ranks (core.hb.hcap == 0: not used)
+    double core_w[CORE_LEVELS_MAX] = {};  // p = 1 probe entries inside the top CORE_MIN << k ranks
     DevState *st = nullptr;
     tc_result *res_dev = nullptr;
     // pinned host
@@ -196,10 +197,29 @@ bool bad_p(double p) { return !(p > 0.0 && p <= 1.0); }
 
 uint64_t threshold_of(double p) { return (uint64_t)(p * 9007199254740992.0); }
 
-// Dense core of the top CORE_SIZE ranks for graphs of at least
-// CORE_MIN_EDGES edges, used by counts that keep about that many.
-constexpr uint32_t CORE_SIZE = 8192;
+// Dense core of the top ranks for graphs of at least CORE_MIN_EDGES edges:
+// K = CORE_MIN << k ranks, k < CORE_LEVELS.  Its cost is fixed (about
+// K^3 / 3 executed tensor flops, the 128 x 256 tiles on and above the
+// diagonal with the K chunks between, and the clearing of 2 K^2 bytes); the probe work it
+// takes over is measured per graph at creation (core_work) and shrinks as
+// p^2 with sampling (both lists of a pair thin out by p).  The graph keeps
+// the size that gains most at p = 1; each count uses the size, up to that,
+// that gains most at its p, or none.
+constexpr uint32_t CORE_MIN = 8192;
+constexpr int CORE_LEVELS = CORE_LEVELS_MAX;  // 8192 .. 65536 ranks
 constexpr double CORE_MIN_EDGES = 33554432.0;
+constexpr double CORE_PROBE_RATE = 5.0e11;    // streamed entries per second of the probe kernels
+constexpr double CORE_TC_RATE = 3.5e15;       // executed fp8 flops per second of the contraction
+constexpr double CORE_CLEAR_RATE = 5.0e12;    // bytes per second of clearing U and U^T
+
+double core_cost_s(double K) { return (K * K * K / 3.0) / CORE_TC_RATE + 2.0 * K * K / CORE_CLEAR_RATE; }
+
+// Seconds the core of CORE_MIN << k ranks saves at sampling rate p (w_cum:
+// p = 1 probe entries inside each core size).
+double core_gain(const double *w_cum, int k, double p)
+{
+    return p * p * w_cum[k] / CORE_PROBE_RATE - core_cost_s((double)(CORE_MIN << k));
+}
 
 CountBuffers buffers_of(tc_graph *g)
 {
@@ -307,7 +327,19 @@ tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bo
                           g->sample_floor >= 0 ? (uint64_t)g->sample_floor : sample_floor(g->m, p, thr));
     // the core block pays off once the sample is large: its cost is fixed,
     // the intersections it replaces grow with the sample
-    const CoreBuffers *core = (g->core.hb.hcap && p * (double)g->m >= CORE_MIN_EDGES) ? &g->core : nullptr;
+    CoreBuffers core_p = g->core;
+    const CoreBuffers *core = nullptr;
+    if (g->core.hb.hcap) {
+        double best = 0.0;
+        for (int k = 0; k < CORE_LEVELS && (CORE_MIN << k) <= g->core.hb.hcap; ++k) {
+            const double gain = core_gain(g->core_w, k, p);
+            if (gain > best) {
+                best = gain;
+                core_p.base = g->n - (CORE_MIN << k);
+                core = &core_p;
+            }
+        }
+    }
     if (core) ra.core_base = core->base;
     CountBuffers b = buffers_of(g);
     if (core) b.core_base = core->base;
@@ -571,14 +603,39 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
             g->hb.hcap = 0;
         }
     }
-    // dense core: the top CORE_SIZE ranks (2 x 64 MiB of fp8), with the heavy block
-    if (g->hb.hcap && (double)m >= CORE_MIN_EDGES && n >= 2 * CORE_SIZE) {
+    // dense core, with the heavy block: the size that gains most at p = 1
+    // (2 x K^2 bytes of fp8, 128 MiB for K = 8192, 8 GiB for 65536)
+    int core_k = -1;
+    if (g->hb.hcap && (double)m >= CORE_MIN_EDGES && n >= 2 * CORE_MIN) {
+        int levels = 0;
+        while (levels < CORE_LEVELS && (uint64_t)2 * (CORE_MIN << levels) <= n) ++levels;
+        unsigned long long *w_dev = (unsigned long long *)g->alloc(CORE_LEVELS_MAX * 8);
+        unsigned long long w[CORE_LEVELS_MAX] = {};
+        if (w_dev) {
+            core_work(g->rel, g->frow, g->inptr, n, m, CORE_MIN, levels, w_dev, s);
+            cudaMemcpyAsync(w, w_dev, sizeof(w), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            g->release(w_dev);
+        }
+        double acc = 0.0, best = 0.0;
+        for (int k = 0; k < levels; ++k) {
+            acc += (double)w[k];
+            g->core_w[k] = acc;
+            const double gain = core_gain(g->core_w, k, 1.0);
+            if (gain > best) {
+                best = gain;
+                core_k = k;
+            }
+        }
+    }
+    if (core_k >= 0) {
         CoreBuffers &c = g->core;
-        const uint64_t bytes = (uint64_t)CORE_SIZE * CORE_SIZE;
+        const uint32_t K = CORE_MIN << core_k;
+        const uint64_t bytes = (uint64_t)K * K;
         c.hb.U = (uint8_t *)g->alloc(bytes);
         c.hb.UT = c.hb.U ? (uint8_t *)g->alloc(bytes) : nullptr;
-        c.hb.hcap = CORE_SIZE;
-        c.base = n - CORE_SIZE;
+        c.hb.hcap = K;
+        c.base = n - K;
         if (!c.hb.U || !c.hb.UT || !heavy_make_maps(c.hb)) {
             if (c.hb.U) g->release(c.hb.U);
             if (c.hb.UT) g->release(c.hb.UT);

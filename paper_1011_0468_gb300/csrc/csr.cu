@@ -521,6 +521,50 @@ void static_rows(const uint64_t *rel, uint64_t m, uint32_t n, const uint32_t *pe
     scan_excl_u32(inres, n1, nullptr, scan, s);
 }
 
+// Probe work of the p = 1 count among the top ranks, the candidates of the
+// dense core: for every edge a -> b of the full graph (rank ids, rows in
+// rank order) with a >= n - (core_min << (levels - 1)), the entries its pair
+// streams: the part of a's row after b when a's row is the shorter, else b's
+// whole row.  w[k] += that for the smallest core core_min << k holding a.
+// Pairs of two heavy vertices (full degree d, d^2 > m) are left out: the
+// heavy block takes them whether or not a core runs.
+__global__ void k_core_work(const uint64_t *__restrict__ rel, const uint32_t *__restrict__ frow,
+                            const uint32_t *__restrict__ inres, uint32_t n, uint64_t lo, uint64_t m,
+                            uint32_t core_min, int levels, unsigned long long *__restrict__ w)
+{
+    __shared__ unsigned long long s_w[CORE_LEVELS_MAX];
+    if (threadIdx.x < CORE_LEVELS_MAX) s_w[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const uint64_t e = rel[i];
+        const uint32_t a = (uint32_t)(e >> 32), b = (uint32_t)e;
+        const uint32_t fa = frow[a], da = frow[a + 1] - fa, db = frow[b + 1] - frow[b];
+        const uint64_t fda = da + (inres[a + 1] - inres[a]), fdb = db + (inres[b + 1] - inres[b]);
+        if (fda * fda > m && fdb * fdb > m) continue;
+        const uint32_t pos = (uint32_t)(i - fa);
+        const uint32_t str = da < db ? da - pos - 1 : db;
+        int k = 0;
+        while (k + 1 < levels && n - a > (core_min << k)) ++k;
+        if (str) atomicAdd(&s_w[k], (unsigned long long)str);
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)levels && s_w[threadIdx.x]) atomicAdd(w + threadIdx.x, s_w[threadIdx.x]);
+}
+
+void core_work(const uint64_t *rel, const uint32_t *frow, const uint32_t *inres, uint32_t n, uint64_t m,
+               uint32_t core_min, int levels, unsigned long long *w, cudaStream_t s)
+{
+    cudaMemsetAsync(w, 0, CORE_LEVELS_MAX * sizeof(unsigned long long), s);
+    const uint64_t span = (uint64_t)core_min << (levels - 1);
+    if (m == 0 || levels < 1 || levels > CORE_LEVELS_MAX || span > n) return;
+    uint32_t lo_row = n - (uint32_t)span, lo = 0;
+    cudaMemcpyAsync(&lo, frow + lo_row, 4, cudaMemcpyDeviceToHost, s);  // first edge of the top rows
+    if (cudaStreamSynchronize(s) != cudaSuccess) return;
+    k_core_work<<<grid_for(m - lo, 256, 152 * 8), 256, 0, s>>>(rel, frow, inres, n, lo, m, core_min, levels, w);
+    note_launch();
+}
+
 // Smallest rank id whose full degree d has d^2 > m_lo (n if none): full
 // degrees grow with the rank.
 __device__ uint32_t cand_lo_of(const uint32_t *__restrict__ frow, const uint32_t *__restrict__ inres, uint32_t n,

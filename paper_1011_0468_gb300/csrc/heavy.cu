@@ -311,7 +311,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 // the right (the longest tiles first), down each column group; inside a
 // group, column panels from the right, row panels from the top.
 constexpr int TC_GI = 16, TC_GP = 8;
-constexpr int TC_MAX_GROUPS = 256;  // hcap <= 32768: 16 row groups x 16 column groups
+constexpr int TC_MAX_GROUPS = 1024;  // order <= 65536: 32 row groups x 32 column groups
 
 struct TileGrid {
     int R, C;    // row panels (of 128) and column panels (of 256)
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
             const uint8_t *urow = U + (uint64_t)row * hcap + (uint64_t)P * TC_N;
             const uint32_t ncols = min(TC_N, hp - P * TC_N);  // 128 or 256: columns below hp only
             const uint32_t taddr = tmem + ((quarter * 32u) << 16) + acc * TC_N;
-            float fsum = 0.f;  // integers below 2^24: at most 256 terms of at most hcap <= 32768
+            float fsum = 0.f;  // integers up to 2^24, exact: at most 256 terms of at most h <= 65536
 #pragma unroll 1
             for (uint32_t q = 0; q < ncols / 32; ++q) {
                 const uint4 *m4 = reinterpret_cast<const uint4 *>(urow + q * 32);
@@ -643,8 +643,9 @@ void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuff
     note_launch();
     k_heavy_pack<<<152 * 4, 256, 0, s>>>(b.ptrp, b.col, b.heavy, hb.hlist, hb.hidx, hb.U, hb.UT, hb.hcap, b.st);
     note_launch();
-    if (with_core) {
-        const uint64_t bytes = (uint64_t)core->hb.hcap * core->hb.hcap;
+    if (with_core) {  // the rows of the core this count uses (its order may be below hcap)
+        const uint64_t order = std::min<uint64_t>(core->hb.hcap, b.n - core->base);
+        const uint64_t bytes = order * core->hb.hcap;
         cudaMemsetAsync(core->hb.U, 0, bytes, s);
         cudaMemsetAsync(core->hb.UT, 0, bytes, s);
         k_core_pack<<<152 * 8, 256, 0, s>>>(b.ptrp, b.col, b.n, core->base, core->hb.U, core->hb.UT, core->hb.hcap,

@@ -538,6 +538,8 @@ constexpr int PB_THREADS = 128;       // mid owners: eight CTAs per SM, one smal
 constexpr int PB_DYN_THREADS = 1024;  // large owners: one CTA per SM around one table of up to 128 KiB
 constexpr uint32_t MID_TAB = 4096;                      // >= 4 * MID_MAX slots (dynamic shared memory)
 constexpr uint32_t UNIT = 128;                          // chunks per unit of block streaming
+constexpr int NWIN_MID = 2;                             // windows in flight per warp step: mid owners
+constexpr int NWIN_DYN = 2;                             // and large owners
 constexpr uint32_t PRE_CLS = 0x80000000u;               // class bit beside a partner's chunk prefix
 
 // Streams chunks [wb0, min(wb0 + UNIT, total)) of an item's partner sequence
@@ -545,7 +547,7 @@ constexpr uint32_t PRE_CLS = 0x80000000u;               // class bit beside a pa
 // position s_pre[k] & ~PRE_CLS of the sequence (increasing in k); the warp
 // finds the partner covering wb0 by a 32-way search and then maps chunks to
 // partners window by window as stream_chunks does.
-template <class Set>
+template <int WIN, class Set>
 __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, const Set &set, const uint32_t *s_c0,
                                             const uint32_t *s_pre, uint32_t nlive, uint32_t total, uint32_t wb0,
                                             const PairCtx &pc, Tally &t)
@@ -566,11 +568,11 @@ __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, cons
     uint32_t before = lo + ((s_pre[lo] & ~PRE_CLS) < wb0 ? 1u : 0u);  // partners beginning before the window
     const uint32_t end = min(total, wb0 + UNIT);
     uint32_t hl = 0, hv = 0;
-    for (uint32_t wb = wb0; wb < end; wb += 32 * NWIN) {
-        uint32_t e[NWIN], k[NWIN], pk[NWIN];
-        uint4 q[NWIN];
+    for (uint32_t wb = wb0; wb < end; wb += 32 * WIN) {
+        uint32_t e[WIN], k[WIN], pk[WIN];
+        uint4 q[WIN];
 #pragma unroll
-        for (int i = 0; i < NWIN; ++i) {
+        for (int i = 0; i < WIN; ++i) {
             const uint32_t w0 = wb + 32u * i, kk = before + lane;
             const uint32_t pre = kk < nlive ? (s_pre[kk] & ~PRE_CLS) : 0xffffffffu;
             const unsigned sti = __reduce_or_sync(FULL, pre - w0 < 32u ? (1u << (pre - w0)) : 0u);
@@ -579,14 +581,14 @@ __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, cons
             before += __popc(sti);
         }
 #pragma unroll
-        for (int i = 0; i < NWIN; ++i) {
+        for (int i = 0; i < WIN; ++i) {
             if (e[i] < end) {
                 pk[i] = s_pre[k[i]];
                 q[i] = __ldg(col4 + (s_c0[k[i]] + (e[i] - (pk[i] & ~PRE_CLS))));
             }
         }
 #pragma unroll
-        for (int i = 0; i < NWIN; ++i) {
+        for (int i = 0; i < WIN; ++i) {
             if (e[i] < end) probe4(set, q[i], (pk[i] & PRE_CLS) != 0, pc, hl, hv);
         }
     }
@@ -698,9 +700,10 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
             u = __shfl_sync(FULL, u, 0);
             if (u * UNIT >= total) break;
             if (slots)
-                stream_unit(col4, set, s_c0, s_pre, nlive, total, u * UNIT, pc, t);
+                stream_unit<DYN ? NWIN_DYN : NWIN_MID>(col4, set, s_c0, s_pre, nlive, total, u * UNIT, pc, t);
             else
-                stream_unit(col4, SortedRow{col + row.beg, d}, s_c0, s_pre, nlive, total, u * UNIT, pc, t);
+                stream_unit<DYN ? NWIN_DYN : NWIN_MID>(col4, SortedRow{col + row.beg, d}, s_c0, s_pre, nlive, total,
+                                                   u * UNIT, pc, t);
         }
         if (bv.k != 0) flush_graph_counts(t, bv, g);
         __syncthreads();  // every warp is done with this owner

@@ -136,6 +136,14 @@ struct RowsArgs {
 // deg_orig: rank -> original id and the full degree by original id.
 void static_rows(const uint64_t *rel, uint64_t m, uint32_t n, const uint32_t *perm, const uint32_t *deg_orig,
                  uint32_t *frow, uint32_t *inres, uint32_t *scan, cudaStream_t s);
+
+// Dense-core candidates: w[k] (k < levels <= CORE_LEVELS_MAX, device) = the
+// entries the p = 1 intersections stream for the pairs (not both heavy)
+// whose lower end lies in the top core_min << k ranks but not in the top
+// core_min << (k - 1).  inres: the full in-degree offsets (static rows).
+constexpr int CORE_LEVELS_MAX = 4;
+void core_work(const uint64_t *rel, const uint32_t *frow, const uint32_t *inres, uint32_t n, uint64_t m,
+               uint32_t core_min, int levels, unsigned long long *w, cudaStream_t s);
 // Counters that every edge bumps at its target (in-degrees, in-list
 // cursors) are kept at hot_index(v): the id rotated within hot_bits(n) bits,
 // so that consecutive ids (the hubs are the top ranks) land 4 KiB apart in
@@ -253,7 +261,8 @@ void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const Isec
 // descriptors of U and U^T (CUtensorMap storage).  hcap == 0 disables the
 // dense path (the intersection kernels then count the heavy class).
 // U and U^T hold 0 and 1 as fp8 e4m3 bytes (1.0 = 0x38): the tensor cores
-// multiply them exactly (fp32 sums of at most hcap <= 32768 ones).
+// multiply them exactly (fp32 sums of at most 65536 ones: hcap <= 32768 for
+// the heavy block, <= 65536 for the core).
 constexpr uint8_t TC_ONE = 0x38;
 struct HeavyBuffers {
     uint8_t *U = nullptr;
@@ -267,9 +276,10 @@ struct HeavyBuffers {
 };
 
 bool heavy_make_maps(HeavyBuffers &hb);
-// The dense core: the vertices with the top `hcap` ids (ranks), base = n -
-// hcap; U is their strictly upper 0/1 matrix, U[v - base][w - base] = 1 for
-// every kept edge v -> w inside the core.  Every triangle whose lowest
+// The dense core: the vertices with the top n - base ids (ranks), at most
+// hcap of them (a count may use fewer than the graph allocated); U (row
+// stride hcap) is their strictly upper 0/1 matrix, U[v - base][w - base] = 1
+// for every kept edge v -> w inside the core.  Every triangle whose lowest
 // vertex is in the core lies in the core, so when the core block runs
 // (DevState::core_on) the intersection kernels skip the pairs whose lower
 // endpoint is in it and the contraction counts those triangles (t_core).
