@@ -532,9 +532,7 @@ __global__ void k_core_work(const uint64_t *__restrict__ rel, const uint32_t *__
                             const uint32_t *__restrict__ inres, uint32_t n, uint64_t lo, uint64_t m,
                             uint32_t core_min, int levels, unsigned long long *__restrict__ w)
 {
-    __shared__ unsigned long long s_w[CORE_LEVELS_MAX];
-    if (threadIdx.x < CORE_LEVELS_MAX) s_w[threadIdx.x] = 0;
-    __syncthreads();
+    unsigned long long acc[CORE_LEVELS_MAX] = {};  // this thread's sums, reduced once at the end
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         const uint64_t e = rel[i];
@@ -544,12 +542,17 @@ __global__ void k_core_work(const uint64_t *__restrict__ rel, const uint32_t *__
         if (fda * fda > m && fdb * fdb > m) continue;
         const uint32_t pos = (uint32_t)(i - fa);
         const uint32_t str = da < db ? da - pos - 1 : db;
-        int k = 0;
-        while (k + 1 < levels && n - a > (core_min << k)) ++k;
-        if (str) atomicAdd(&s_w[k], (unsigned long long)str);
+#pragma unroll
+        for (int k = 0; k < CORE_LEVELS_MAX; ++k)  // the smallest core holding a
+            if (k < levels && (k + 1 == levels || n - a <= (core_min << k)) &&
+                (k == 0 || n - a > (core_min << (k - 1))))
+                acc[k] += str;
     }
-    __syncthreads();
-    if (threadIdx.x < (unsigned)levels && s_w[threadIdx.x]) atomicAdd(w + threadIdx.x, s_w[threadIdx.x]);
+#pragma unroll
+    for (int k = 0; k < CORE_LEVELS_MAX; ++k) {
+        const unsigned long long v = warp_sum(acc[k]);
+        if (lane_id() == 0 && v) atomicAdd(w + k, v);
+    }
 }
 
 void core_work(const uint64_t *rel, const uint32_t *frow, const uint32_t *inres, uint32_t n, uint64_t m,
