@@ -75,7 +75,8 @@ typedef struct {
     uint64_t src_elems; /* list elements loaded into hash sets */
     uint64_t nbr_elems; /* list elements streamed through them */
     uint64_t partners;  /* oriented pairs resolved */
-    uint64_t heavy_mma_flops; /* tensor-core flops of the dense heavy block (0 when not used) */
+    uint64_t heavy_mma_flops; /* executed tensor-core flops of the dense heavy block and,
+                                 when the count uses it, the dense core (0 when neither runs) */
     float ms[8];
 } tc_result;
 
@@ -116,6 +117,11 @@ tc_status tc_check_bounded_wait(uint32_t limit_us);
  * Errors: TC_EINVAL for NULL out, NULL edges with m_in > 0, n == 0, n or m
  * beyond the size limits, an endpoint >= n (nothing stays allocated);
  * TC_ENOMEM; TC_ECUDA.  Blocks until the graph is ready.
+ * For graphs of at least 2^25 edges, creation also measures the probe work
+ * of a p = 1 count among the top ranks and, where it pays, keeps a dense
+ * core of the top 8192 to 65536 ranks (2 K^2 bytes of device memory) whose
+ * triangles the tensor cores count; each count decides from its p whether
+ * and at what size to use it.  The counts do not depend on that choice.
  */
 tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int edges_on_device,
                           void *cuda_stream, tc_graph **out);
