@@ -151,6 +151,17 @@ tc_status tc_graph_set_timing(tc_graph *g, int on);
    never depend on it.  TC_EINVAL for a NULL graph. */
 tc_status tc_graph_set_sample_floor(tc_graph *g, int64_t m_lo);
 
+/* The dense core of the top ranks (see tc_graph_create) for the graph's later
+   counts: ranks < 0 restores the default (each count chooses from its p),
+   0 turns it off, and 8192, 16384, 32768 or 65536 makes every count use a
+   core of that many ranks, allocating 2 ranks^2 bytes of device memory if
+   creation kept a smaller one (after waiting for the graph's pending work).
+   For diagnostics and tests; results never depend on it.  TC_EINVAL for a
+   NULL graph, another size, a size above n / 2, or a graph without the dense
+   path (fewer than 2^25 edges); TC_ENOMEM if the core cannot be allocated
+   (the default is then restored); TC_ECUDA. */
+tc_status tc_graph_set_core_ranks(tc_graph *g, int64_t ranks);
+
 /* After tc_graph_sync: copy the phase times (8 floats per count, layout of
    tc_result.ms) of the counts completed since the last drain, oldest first,
    at most max_counts of them (older ones beyond the ring are lost).  Returns

@@ -139,6 +139,7 @@ struct tc_graph {
     HeavyBuffers hb;            // dense heavy block (hb.hcap == 0: not used)
     CoreBuffers core;           // dense core of the top ranks (core.hb.hcap == 0: not used)
     double core_w[CORE_LEVELS_MAX] = {};  // p = 1 probe entries inside the top CORE_MIN << k ranks
+    int64_t core_force = -1;    // dense core of every count: < 0 chosen per count, 0 none, else that many ranks
     DevState *st = nullptr;
     tc_result *res_dev = nullptr;
     // pinned host
@@ -329,7 +330,10 @@ tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bo
     // the intersections it replaces grow with the sample
     CoreBuffers core_p = g->core;
     const CoreBuffers *core = nullptr;
-    if (g->core.hb.hcap) {
+    if (g->core_force > 0 && g->core.hb.hcap >= (uint64_t)g->core_force) {
+        core_p.base = g->n - (uint32_t)g->core_force;
+        core = &core_p;
+    } else if (g->core_force < 0 && g->core.hb.hcap) {
         double best = 0.0;
         for (int k = 0; k < CORE_LEVELS && (CORE_MIN << k) <= g->core.hb.hcap; ++k) {
             const double gain = core_gain(g->core_w, k, p);
@@ -661,6 +665,41 @@ tc_status tc_graph_set_sample_floor(tc_graph *g, int64_t m_lo)
 {
     if (!g) return TC_EINVAL;
     g->sample_floor = m_lo < 0 ? -1 : m_lo;
+    return TC_OK;
+}
+
+tc_status tc_graph_set_core_ranks(tc_graph *g, int64_t ranks)
+{
+    if (!g) return TC_EINVAL;
+    if (ranks <= 0) {
+        g->core_force = ranks < 0 ? -1 : 0;
+        return TC_OK;
+    }
+    bool level = false;
+    for (int k = 0; k < CORE_LEVELS; ++k) level |= ranks == (int64_t)(CORE_MIN << k);
+    if (!level || 2 * (uint64_t)ranks > g->n || g->hb.hcap == 0 || (double)g->m < CORE_MIN_EDGES) return TC_EINVAL;
+    if (g->core.hb.hcap < (uint64_t)ranks) {  // a larger core than creation kept
+        if (sync_graph(g) != TC_OK) return TC_ECUDA;
+        CoreBuffers &c = g->core;
+        if (c.hb.U) g->release(c.hb.U);
+        if (c.hb.UT) g->release(c.hb.UT);
+        c.hb.U = c.hb.UT = nullptr;
+        c.hb.hcap = 0;
+        const uint64_t bytes = (uint64_t)ranks * (uint64_t)ranks;
+        c.hb.U = (uint8_t *)g->alloc(bytes);
+        c.hb.UT = c.hb.U ? (uint8_t *)g->alloc(bytes) : nullptr;
+        c.hb.hcap = (uint32_t)ranks;
+        c.base = g->n - (uint32_t)ranks;
+        if (!c.hb.U || !c.hb.UT || !heavy_make_maps(c.hb)) {
+            if (c.hb.U) g->release(c.hb.U);
+            if (c.hb.UT) g->release(c.hb.UT);
+            c.hb.U = c.hb.UT = nullptr;
+            c.hb.hcap = 0;
+            g->core_force = -1;
+            return TC_ENOMEM;
+        }
+    }
+    g->core_force = ranks;
     return TC_OK;
 }
 

@@ -69,6 +69,7 @@ SIGNATURES = [
     ("tc_graph_device_bytes", ctypes.c_uint64, [_vp]),
     ("tc_graph_set_timing", ctypes.c_int, [_vp, ctypes.c_int]),
     ("tc_graph_set_sample_floor", ctypes.c_int, [_vp, ctypes.c_int64]),
+    ("tc_graph_set_core_ranks", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("tc_graph_timing_drain", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32]),
     ("tc_count", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(tc_result)]),
     ("tc_count_async", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp]),
@@ -285,6 +286,11 @@ class Graph:
         """Lower bound on m_p that picks the vertices whose sampled in-degrees are
         counted (tc_graph_set_sample_floor); m_lo < 0 restores the default."""
         _check(lib().tc_graph_set_sample_floor(self.handle, int(m_lo)), "tc_graph_set_sample_floor")
+
+    def set_core_ranks(self, ranks: int):
+        """Dense core of the later counts (tc_graph_set_core_ranks): < 0 chosen
+        per count (the default), 0 none, else 8192 .. 65536 top ranks."""
+        _check(lib().tc_graph_set_core_ranks(self.handle, int(ranks)), "tc_graph_set_core_ranks")
 
     def timing_drain(self, max_counts: int = 256) -> np.ndarray:
         """Phase times (counts x 8, ms) of the timed counts since the last drain."""

@@ -62,6 +62,7 @@ def test_argument_errors_without_device(lib):
     lib.tc_graph_destroy(None)  # NULL-safe
     assert lib.tc_graph_num_edges(None) == 0
     assert lib.tc_graph_set_sample_floor(None, 0) == tc.TC_EINVAL
+    assert lib.tc_graph_set_core_ranks(None, 8192) == tc.TC_EINVAL
     for limit in (0, 1000001):  # bounded-wait check: limits out of range
         assert lib.tc_check_bounded_wait(limit) == tc.TC_EINVAL
 

@@ -96,3 +96,30 @@ def test_async_sweep_matches_blocking(workload, graph):
         want = by_key[(p, 1)]
         assert (got["t_light"], got["t_heavy"], got["m_sampled"]) == (want["t_light"], want["t_heavy"],
                                                                        want["m_sampled"])
+
+
+def test_forced_dense_core_sizes_match_the_oracle(workload, graph):
+    """The dense core changes which kernels count the triangles among the top
+    ranks, never the counts: no core, and cores of 8192, 32768 and 65536
+    ranks, at p = 1 and 0.1, all give the stored oracle results."""
+    from paper_1011_0468_gb300 import tc
+    rec, _ = workload
+    by_key = {(r["p"], r["seed"]): r for r in rec["runs"]}
+    flops = {}
+    try:
+        for ranks in (0, 8192, 32768, 65536):
+            graph.set_core_ranks(ranks)
+            for p in (1.0, 0.1):
+                got = graph.count(p, 1)
+                want = by_key[(p, 1)]
+                for k in ("m_sampled", "n_heavy", "t_light", "t_heavy"):
+                    assert got[k] == want[k], (ranks, p, k, got[k], want[k])
+                assert got["estimate"] == float.fromhex(want["estimate_hex"])
+                if p == 1.0:
+                    flops[ranks] = got["heavy_mma_flops"]
+        assert flops[0] < flops[8192] < flops[32768] < flops[65536]  # the cores ran
+        for bad in (12345, 4096, 1 << 20):
+            with pytest.raises(tc.TCError):
+                graph.set_core_ranks(bad)
+    finally:
+        graph.set_core_ranks(-1)
