@@ -624,17 +624,31 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
     __shared__ uint32_t s_pre[SEG_B];  // chunk prefix | PRE_CLS (both endpoints heavy)
     __shared__ unsigned long long wt[33];
     __shared__ unsigned long long red[33];
-    __shared__ uint32_t s_idx, s_next;
+    __shared__ uint32_t s_idx, s_next, s_left, s_built;
     const unsigned lane = lane_id();
     const uint32_t b = DYN ? 2 : 1;
     const uint32_t nitems =
         (uint32_t)min((unsigned long long)st->nlist[b], (unsigned long long)(DYN ? cap - wm_cap : wm_cap));
+    // large owners take up to 8 consecutive items per grab (at least 8 grabs
+    // per block): an owner's items are consecutive, and the table is rebuilt
+    // only when the owner changes
+    const uint32_t run = DYN ? max(1u, min(8u, nitems / (gridDim.x * 8u))) : 1u;
+    if (threadIdx.x == 0) {
+        s_left = 0;
+        s_built = 0xffffffffu;  // owner whose set the table holds
+    }
     const PairCtx pc{heavy, st->light_lim, st->dense != 0, st->core_on ? core_base : 0xffffffffu};
     const uint4 *col4 = reinterpret_cast<const uint4 *>(col);
     Tally t;
     for (;;) {
         if (threadIdx.x == 0) {
-            s_idx = atomicAdd(&st->cursor[b], 1u);
+            if (s_left == 0) {
+                s_idx = atomicAdd(&st->cursor[b], run);
+                s_left = run;
+            } else {
+                ++s_idx;
+            }
+            --s_left;
             s_next = 0;
         }
         __syncthreads();
@@ -647,7 +661,7 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
         const uint32_t hx = heavy[x];
         const uint32_t slots = table_slots(d, tab_slots);
         const BucketSet set{tab, slots ? (slots >> 1) - 1 : 0u, slots ? bucket_shift(slots) : 0u};
-        if (slots) {
+        if (slots && !(DYN && s_built == x)) {
             for (uint32_t i = threadIdx.x; i < (slots >> 1); i += NT) tab[i] = make_uint2(EMPTY, EMPTY);
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < d; i += NT)
@@ -707,6 +721,7 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
         }
         if (bv.k != 0) flush_graph_counts(t, bv, g);
         __syncthreads();  // every warp is done with this owner
+        if (threadIdx.x == 0) s_built = slots ? x : 0xffffffffu;
     }
     flush_tally(t, red, st);
 }
