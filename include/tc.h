@@ -158,8 +158,9 @@ tc_status tc_graph_set_sample_floor(tc_graph *g, int64_t m_lo);
    creation kept a smaller one (after waiting for the graph's pending work).
    For diagnostics and tests; results never depend on it.  TC_EINVAL for a
    NULL graph, another size, a size above n / 2, or a graph without the dense
-   path (fewer than 2^25 edges); TC_ENOMEM if the core cannot be allocated
-   (the default is then restored); TC_ECUDA. */
+   path (fewer than 2^25 edges); TC_ENOMEM if the larger core cannot be
+   allocated (the smaller one is already released: later counts run without
+   a core until a size that fits is set); TC_ECUDA. */
 tc_status tc_graph_set_core_ranks(tc_graph *g, int64_t ranks);
 
 /* After tc_graph_sync: copy the phase times (8 floats per count, layout of
