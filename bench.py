@@ -637,14 +637,21 @@ def serve_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def select_workload(name: str, rmat_scale=None) -> dict:
+    """A copy of WORKLOADS[name]; for R-MAT, rmat_scale (if given) replaces the
+    scale, the vertex count, the name and caps the oracle's sample."""
+    w = dict(WORKLOADS[name])
+    if rmat_scale is not None and w["kind"] == "rmat":
+        sc = int(rmat_scale)
+        w.update(scale=sc, n=1 << sc, workload="rmat_s%d_ef%d" % (sc, w["edge_factor"]),
+                 oracle_draws=min(w["oracle_draws"], w["edge_factor"] << sc))
+    return w
+
+
 def main():
     global WORKLOAD
     args = parse_args()
-    WORKLOAD = dict(WORKLOADS[args.workload])
-    if args.rmat_scale is not None and WORKLOAD["kind"] == "rmat":
-        sc = args.rmat_scale
-        WORKLOAD.update(scale=sc, n=1 << sc, workload="rmat_s%d_ef%d" % (sc, WORKLOAD["edge_factor"]),
-                        oracle_draws=min(WORKLOAD["oracle_draws"], WORKLOAD["edge_factor"] << sc))
+    WORKLOAD = select_workload(args.workload, args.rmat_scale)
     if WORKLOAD["kind"] == "serve":
         if args.impl == "ours":
             serve_arm(args)
