@@ -100,14 +100,19 @@ def rmat(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: floa
 
 
 def rmat_draws(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: float = 0.19,
-               seed: int = 1, out: np.ndarray | None = None, threads: int | None = None) -> np.ndarray:
+               seed: int = 1, out: np.ndarray | None = None, threads: int | None = None,
+               count: int | None = None) -> np.ndarray:
     """The edge_factor * 2**scale raw draws of rmat(scale, edge_factor, a, b,
     c, seed) as (u, v) pairs in draw order, ids permuted, self-loops and
     repeats included: symmetrising and deduplicating them gives rmat's graph.
     Filled by several threads (each draw depends only on its index); out, if
-    given, is a (draws, 2) uint32 array (e.g. in pinned memory)."""
+    given, is a (draws, 2) uint32 array (e.g. in pinned memory).  count, if
+    given, stops after the first `count` draws (the same draws as the first
+    rows of the full output)."""
     from concurrent.futures import ThreadPoolExecutor
     draws = edge_factor << scale
+    if count is not None:
+        draws = min(draws, int(count))
     if out is None:
         out = np.empty((draws, 2), dtype=np.uint32)
     assert out.shape == (draws, 2) and out.dtype == np.uint32 and out.flags.c_contiguous

@@ -33,6 +33,7 @@
  * triangle is therefore seen exactly once, at its two smallest ids, and is
  * put into the heavy class iff all three vertices are heavy.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -152,25 +153,21 @@ static int cmp_u32(const void *a, const void *b)
 }
 
 /*
- * Plain triangle enumeration over sorted adjacency lists.  For each edge
- * (u, v), u < v, the common neighbours w > v are found by merging N(u) and
- * N(v).  A triangle goes to *t_heavy iff heavy[u], heavy[v] and heavy[w]
- * are all set, otherwise to *t_light (Section 3.2).  Returns 0, or -2 if
- * memory runs out.
+ * The full symmetric adjacency N(u) of a simple graph as sorted lists:
+ * N(u) = adj[start[u] .. start[u+1]).  start holds n+1 entries, adj 2*m.
+ * Built by a counting sort on the first endpoint, each list then sorted.
+ * Returns 0, or -2 if memory runs out.
  */
-int oracle_count_classes(const uint32_t *pairs, uint64_t m, uint32_t n, const uint8_t *heavy,
-                         uint64_t *t_light, uint64_t *t_heavy)
+int oracle_adjacency(const uint32_t *pairs, uint64_t m, uint32_t n, uint64_t *start, uint32_t *adj)
 {
-    uint64_t *start = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
-    uint64_t *fill = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
-    uint32_t *adj = (uint32_t *)malloc((m ? 2 * m : 1) * sizeof(uint32_t));
-    if (!start || !fill || !adj) { free(start); free(fill); free(adj); return -2; }
-    /* full symmetric adjacency N(u), by counting sort, each list sorted */
+    memset(start, 0, ((size_t)n + 1) * sizeof(uint64_t));
     for (uint64_t i = 0; i < m; ++i) {
         start[pairs[2 * i] + 1]++;
         start[pairs[2 * i + 1] + 1]++;
     }
     for (uint32_t u = 0; u < n; ++u) start[u + 1] += start[u];
+    uint64_t *fill = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    if (!fill) return -2;
     memcpy(fill, start, ((size_t)n + 1) * sizeof(uint64_t));
     for (uint64_t i = 0; i < m; ++i) {
         uint32_t a = pairs[2 * i], b = pairs[2 * i + 1];
@@ -180,9 +177,22 @@ int oracle_count_classes(const uint32_t *pairs, uint64_t m, uint32_t n, const ui
     free(fill);
     for (uint32_t u = 0; u < n; ++u)
         qsort(adj + start[u], start[u + 1] - start[u], sizeof(uint32_t), cmp_u32);
+    return 0;
+}
 
+/*
+ * Triangle enumeration over the sorted lists, for the triangles whose
+ * smallest vertex u lies in [u_lo, u_hi).  For each edge (u, v), u < v, the
+ * common neighbours w > v are found by merging N(u) and N(v).  A triangle
+ * goes to *t_heavy iff heavy[u], heavy[v] and heavy[w] are all set,
+ * otherwise to *t_light (Section 3.2).  Every triangle is seen once, at its
+ * smallest vertex, so the counts of disjoint ranges add up.
+ */
+void oracle_count_range(const uint64_t *start, const uint32_t *adj, const uint8_t *heavy,
+                        uint32_t u_lo, uint32_t u_hi, uint64_t *t_light, uint64_t *t_heavy)
+{
     uint64_t tl = 0, th = 0;
-    for (uint32_t u = 0; u < n; ++u) {
+    for (uint32_t u = u_lo; u < u_hi; ++u) {
         for (uint64_t a = start[u]; a < start[u + 1]; ++a) {
             uint32_t v = adj[a];
             if (v <= u) continue;
@@ -204,11 +214,25 @@ int oracle_count_classes(const uint32_t *pairs, uint64_t m, uint32_t n, const ui
             }
         }
     }
-    free(start);
-    free(adj);
     *t_light = tl;
     *t_heavy = th;
-    return 0;
+}
+
+/*
+ * Both classes of the whole graph: the adjacency, then the enumeration over
+ * every vertex.  Returns 0, or -2 if memory runs out.
+ */
+int oracle_count_classes(const uint32_t *pairs, uint64_t m, uint32_t n, const uint8_t *heavy,
+                         uint64_t *t_light, uint64_t *t_heavy)
+{
+    uint64_t *start = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint32_t *adj = (uint32_t *)malloc((m ? 2 * m : 1) * sizeof(uint32_t));
+    if (!start || !adj) { free(start); free(adj); return -2; }
+    int rc = oracle_adjacency(pairs, m, n, start, adj);
+    if (rc == 0) oracle_count_range(start, adj, heavy, 0, n, t_light, t_heavy);
+    free(start);
+    free(adj);
+    return rc;
 }
 
 /* ------------------------------------------------------- whole method */
@@ -237,8 +261,23 @@ double oracle_estimate(uint64_t t_light, uint64_t t_heavy, double p)
  * and the heavy flags when non-NULL.  Returns 0, -1 on a bad p, -2 when
  * memory runs out.
  */
+int oracle_run_partition(const uint32_t *pairs, uint64_t m, uint32_t n, double p, uint64_t seed,
+                         int partition_original, uint32_t *kept_out, uint8_t *heavy_out, oracle_result *res);
+
 int oracle_run(const uint32_t *pairs, uint64_t m, uint32_t n, double p, uint64_t seed,
                uint32_t *kept_out, uint8_t *heavy_out, oracle_result *res)
+{
+    return oracle_run_partition(pairs, m, n, p, seed, 0, kept_out, heavy_out, res);
+}
+
+/*
+ * The same with the choice of graph for the degree partition of Section 3.2:
+ * partition_original = 0 splits the sampled graph (deg_p^2 > m_p, the
+ * default reading), 1 splits the original graph (deg^2 > m over the whole
+ * canonical edge list) and classifies the sampled triangles by those flags.
+ */
+int oracle_run_partition(const uint32_t *pairs, uint64_t m, uint32_t n, double p, uint64_t seed,
+                         int partition_original, uint32_t *kept_out, uint8_t *heavy_out, oracle_result *res)
 {
     if (!(p > 0.0 && p <= 1.0)) return -1;
     uint32_t *kept = kept_out ? kept_out : (uint32_t *)malloc((m ? 2 * m : 1) * sizeof(uint32_t));
@@ -249,13 +288,254 @@ int oracle_run(const uint32_t *pairs, uint64_t m, uint32_t n, double p, uint64_t
     res->m = m;
     res->n = n;
     res->m_sampled = oracle_sample(pairs, m, p, seed, kept);
-    oracle_degrees(kept, res->m_sampled, n, deg);
-    res->n_heavy = oracle_partition(deg, n, res->m_sampled, heavy);
+    if (partition_original) {
+        oracle_degrees(pairs, m, n, deg);
+        res->n_heavy = oracle_partition(deg, n, m, heavy);
+    } else {
+        oracle_degrees(kept, res->m_sampled, n, deg);
+        res->n_heavy = oracle_partition(deg, n, res->m_sampled, heavy);
+    }
     rc = oracle_count_classes(kept, res->m_sampled, n, heavy, &res->t_light, &res->t_heavy);
     res->estimate = oracle_estimate(res->t_light, res->t_heavy, p);
 done:
     if (!kept_out) free(kept);
     if (!heavy_out) free(heavy);
     free(deg);
+    return rc;
+}
+
+/* ------------------------------------------------------- choice of p */
+
+/*
+ * Section 3.3: the sparsification rate that balances the O(mp) pass over
+ * the kept edges against the O((mp)^(3/2) log n / (eps^2 t p^3)) triple
+ * samples, p = (m^(1/2) ln n / (t eps^2))^(2/5), clamped to at most 1.
+ * t is a pilot estimate of the triangle count.  Returns 1 when t <= 0 (no
+ * triangle seen: do not sparsify), -1 for eps <= 0, m == 0 or n < 2.
+ */
+double oracle_suggest_p(uint64_t m, uint32_t n, double t, double eps)
+{
+    if (!(eps > 0.0) || m == 0 || n < 2) return -1.0;
+    if (!(t > 0.0)) return 1.0;
+    double x = sqrt((double)m) * log((double)n) / (t * eps * eps);
+    double p = pow(x, 0.4);
+    return p < 1.0 ? p : 1.0;
+}
+
+/* ------------------------------------------------------- triple sampling */
+
+/* floor(a * b / 2^64): a 64-bit hash a mapped to a uniform index in [0, b). */
+static uint64_t mulhi64(uint64_t a, uint64_t b)
+{
+    return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+}
+
+/* Is w in the sorted list a[0 .. len)? */
+static int sorted_contains(const uint32_t *a, uint64_t len, uint32_t w)
+{
+    uint64_t lo = 0, hi = len;
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) / 2;
+        if (a[mid] < w) lo = mid + 1; else hi = mid;
+    }
+    return lo < len && a[lo] == w;
+}
+
+/*
+ * The class of every vertex (path[u] = 1: heavy in the hybrid mode, its
+ * triples are 2-paths) and the prefix counts of U: pre[u] = triples of the
+ * vertices before u (n + 1 entries), qpre (aligned with adj) for heavy
+ * rows.  Returns the number of heavy vertices.
+ */
+static uint32_t triple_universe(const uint64_t *start, const uint32_t *adj, uint32_t n, uint64_t mp, int hybrid,
+                                uint64_t *pre, uint64_t *qpre, uint8_t *path)
+{
+    uint32_t h = 0;
+    pre[0] = 0;
+    for (uint32_t u = 0; u < n; ++u) {
+        uint64_t d = start[u + 1] - start[u], cnt;
+        path[u] = hybrid && d * d > mp;
+        h += path[u];
+        if (path[u]) {
+            cnt = 0;
+            for (uint64_t j = start[u]; j < start[u + 1]; ++j) {
+                uint32_t v = adj[j];
+                qpre[j] = cnt;  /* 2-paths through the earlier neighbours of u */
+                cnt += start[v + 1] - start[v];
+            }
+        } else {
+            cnt = d * (d - (d > 0)) / 2;
+        }
+        pre[u + 1] = pre[u] + cnt;
+    }
+    return h;
+}
+
+/*
+ * Triple r of U (0 <= r < |U|, see oracle_triples): its vertex u, its pair
+ * (v, w) (a wedge v-u-w, or the 2-path u - v - w at a heavy u), and whether
+ * it is a triangle.  pre[u] = triples of the vertices before u; qpre[j] for
+ * a heavy u's list position j = 2-paths through the earlier neighbours.
+ */
+static int triple_at(const uint64_t *start, const uint32_t *adj, const uint64_t *pre, const uint64_t *qpre,
+                     const uint8_t *path, uint32_t n, uint64_t r, uint32_t *pu, uint32_t *pv, uint32_t *pw)
+{
+    /* the vertex u with pre[u] <= r < pre[u + 1] */
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        if (pre[mid] <= r) lo = mid; else hi = mid;
+    }
+    uint32_t u = lo;
+    uint64_t k = r - pre[u];
+    const uint32_t *nu = adj + start[u];
+    uint64_t du = start[u + 1] - start[u];
+    *pu = u;
+    if (!path[u]) {
+        /* wedge k: b = the largest b >= 1 with b (b - 1) / 2 <= k */
+        uint64_t b = 1, bhi = du;
+        while (bhi - b > 1) {
+            uint64_t mid = b + (bhi - b) / 2;
+            if (mid * (mid - 1) / 2 <= k) b = mid; else bhi = mid;
+        }
+        uint64_t a = k - b * (b - 1) / 2;
+        *pv = nu[a];
+        *pw = nu[b];
+        return sorted_contains(adj + start[*pv], start[*pv + 1] - start[*pv], *pw);
+    }
+    /* 2-path k: j = the last neighbour position with qpre <= k */
+    uint64_t j = 0, jhi = du;
+    while (jhi - j > 1) {
+        uint64_t mid = j + (jhi - j) / 2;
+        if (qpre[start[u] + mid] <= k) j = mid; else jhi = mid;
+    }
+    uint32_t v = nu[j];
+    uint32_t w = adj[start[v] + (k - qpre[start[u] + j])];
+    *pv = v;
+    *pw = w;
+    return w != u && sorted_contains(nu, du, w);
+}
+
+typedef struct {
+    uint64_t m, m_sampled;
+    uint32_t n, n_heavy;   /* n_heavy: vertices whose triples are 2-paths (0 in the simple mode) */
+    uint64_t universe;     /* |U| */
+    uint64_t samples;      /* s */
+    uint64_t closed_wedge; /* sampled wedges that are triangles */
+    uint64_t closed_path;  /* sampled 2-paths that are triangles */
+    double estimate;
+} oracle_triple_result;
+
+/*
+ * Triple sampling (Section 3.2), after the edge sparsification of Section
+ * 3.1 when p < 1 (the hybrid of Section 3.3).
+ *
+ * U is a set of vertex triples that holds every triangle of the (sampled)
+ * graph, built vertex by vertex:
+ *   - a light vertex u (every vertex in the simple mode) contributes its
+ *     wedges: the C(d, 2) unordered pairs {N(u)[a], N(u)[b]}, a < b, of its
+ *     neighbours (at most deg(u)^2 of them);
+ *   - in the hybrid mode a heavy vertex u (deg^2 > m, Section 3.2 on the
+ *     sampled graph) contributes the triples of u with the edges at its
+ *     neighbours, sum over v in N(u) of deg(v) of them: the 2-paths
+ *     u - v - w, w in N(v) (w = u included; it never closes).
+ * Vertices are taken in id order and neighbour lists are sorted by id; a
+ * vertex's wedges are numbered in the order b = 1, 2, ..., a = 0 .. b - 1
+ * (index b (b - 1) / 2 + a), its 2-paths by v's position in N(u) and then
+ * w's position in N(v).  A wedge {v, w} at u is a triangle iff vw is an
+ * edge, a 2-path u - v - w iff w != u and uw is an edge.  Every triangle
+ * is in U once per light corner (one wedge) and twice per heavy corner (two
+ * 2-paths), so with weight 1 per closed wedge and 1/2 per closed 2-path the
+ * weights of U sum to 3 t.
+ *
+ * Sample i (0 <= i < s) is the triple of index floor(h_i |U| / 2^64),
+ * h_i = splitmix64(i ^ splitmix64(~seed)): s independent uniform draws
+ * from U.  The estimate is |U| (2 c_w + c_p) / (6 s), which has expected
+ * value t (c_w, c_p: closed wedges and 2-paths among the samples),
+ * divided by p^3 for the sparsified graph.  s = 0 draws m_p samples (the
+ * paper sizes the number of queries like the graph).
+ *
+ * pairs: the canonical edge list (m pairs); the sample of Section 3.1 with
+ * (p, seed) is drawn from it first, and the same seed drives the triples.
+ * hybrid: 0 for the simple mode, 1 for the hybrid mode.  Returns 0, -1 on a
+ * bad p, -2 when memory runs out.
+ */
+int oracle_triples(const uint32_t *pairs, uint64_t m, uint32_t n, double p, uint64_t seed, uint64_t samples,
+                   int hybrid, oracle_triple_result *res)
+{
+    if (!(p > 0.0 && p <= 1.0)) return -1;
+    uint32_t *kept = (uint32_t *)malloc((m ? 2 * m : 1) * sizeof(uint32_t));
+    uint64_t *start = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint32_t *adj = (uint32_t *)malloc((m ? 2 * m : 1) * sizeof(uint32_t));
+    uint64_t *pre = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint64_t *qpre = (uint64_t *)malloc((m ? 2 * m : 1) * sizeof(uint64_t));
+    uint8_t *path = (uint8_t *)malloc((size_t)n ? n : 1);
+    int rc = 0;
+    if (!kept || !start || !adj || !pre || !qpre || !path) { rc = -2; goto done; }
+    memset(res, 0, sizeof(*res));
+    res->m = m;
+    res->n = n;
+    res->m_sampled = oracle_sample(pairs, m, p, seed, kept);
+    uint64_t mp = res->m_sampled;
+    if (oracle_adjacency(kept, mp, n, start, adj)) { rc = -2; goto done; }
+
+    res->n_heavy = triple_universe(start, adj, n, mp, hybrid, pre, qpre, path);
+    res->universe = pre[n];
+    res->samples = samples ? samples : mp;
+    uint64_t s = res->samples;
+    if (res->universe == 0 || s == 0) goto rescale;
+
+    uint64_t tmix = oracle_splitmix64(~seed);
+    for (uint64_t i = 0; i < s; ++i) {
+        uint64_t r = mulhi64(oracle_splitmix64(i ^ tmix), res->universe);
+        uint32_t u, v, w;
+        int closed = triple_at(start, adj, pre, qpre, path, n, r, &u, &v, &w);
+        if (closed && path[u]) res->closed_path++;
+        else if (closed) res->closed_wedge++;
+    }
+rescale:
+    if (res->universe && s) {
+        double raw = ((double)res->universe * (double)(2 * res->closed_wedge + res->closed_path)) / (6.0 * (double)s);
+        double p3 = p * p * p;
+        res->estimate = raw / p3;
+    }
+done:
+    free(kept);
+    free(start);
+    free(adj);
+    free(pre);
+    free(qpre);
+    free(path);
+    return rc;
+}
+
+/*
+ * Every triple of U in index order, for tests on small graphs (no edge
+ * sampling: pairs is the whole canonical graph).  out_u / out_v / out_w /
+ * out_closed hold |U| entries (ask with cap = 0 first: returns |U|).
+ * Returns |U|, or -2 when memory runs out, -3 when cap < |U|.
+ */
+int64_t oracle_triple_enumerate(const uint32_t *pairs, uint64_t m, uint32_t n, int hybrid, uint64_t cap,
+                                uint32_t *out_u, uint32_t *out_v, uint32_t *out_w, uint8_t *out_closed)
+{
+    uint64_t *start = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint32_t *adj = (uint32_t *)malloc((m ? 2 * m : 1) * sizeof(uint32_t));
+    uint64_t *pre = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint64_t *qpre = (uint64_t *)malloc((m ? 2 * m : 1) * sizeof(uint64_t));
+    uint8_t *path = (uint8_t *)malloc((size_t)n ? n : 1);
+    int64_t rc = 0;
+    if (!start || !adj || !pre || !qpre || !path || oracle_adjacency(pairs, m, n, start, adj)) { rc = -2; goto done; }
+    triple_universe(start, adj, n, m, hybrid, pre, qpre, path);
+    rc = (int64_t)pre[n];
+    if (cap == 0) goto done;
+    if (cap < pre[n]) { rc = -3; goto done; }
+    for (uint64_t r = 0; r < pre[n]; ++r)
+        out_closed[r] = (uint8_t)triple_at(start, adj, pre, qpre, path, n, r, out_u + r, out_v + r, out_w + r);
+done:
+    free(start);
+    free(adj);
+    free(pre);
+    free(qpre);
+    free(path);
     return rc;
 }

@@ -42,7 +42,8 @@ WORKLOADS = {
     "chung_lu_4m": dict(kind="chung_lu", n=1 << 22, m=1 << 26, gamma=2.1, wmax=1e5, seed=1,
                         runs=[(1.0, 1)] + [(p, s) for p in (0.1, 0.01) for s in (1, 2, 3)] + [(0.7, 1), (0.55, 2)]),
     "rmat_s26": dict(kind="rmat", n=1 << 26, scale=26, edge_factor=16, a=0.57, b=0.19, c=0.19, seed=1,
-                     runs=[(0.05, 1), (0.05, 2), (0.25, 1), (0.5, 1)], sample_checksums=True),
+                     runs=[(0.05, 1), (0.05, 2), (0.25, 1), (0.5, 1), (1.0, 1)], sample_checksums=True,
+                     threads={1.0: os.cpu_count() or 1}),
 }
 
 
@@ -80,7 +81,7 @@ def main(names):
         spec = WORKLOADS[name]
         t0 = time.time()
         edges = make_graph(spec)
-        rec = {"workload": name, "spec": {k: v for k, v in spec.items() if k not in ("runs", "sample_checksums")},
+        rec = {"workload": name, "spec": {k: v for k, v in spec.items() if k not in ("runs", "sample_checksums", "threads")},
                "m": int(len(edges)), "checksum": checksum(edges), "runs": []}
         print(name, "generated", len(edges), "edges in %.1fs" % (time.time() - t0), flush=True)
         if spec.get("sample_checksums"):  # the whole graph's degrees and partition (p = 1)
@@ -99,13 +100,16 @@ def main(names):
                 continue
             t0 = time.time()
             want = bool(spec.get("sample_checksums"))
-            r = oracle.run(edges, spec["n"], p, seed, want_sample=want)
+            threads = spec.get("threads", {}).get(p, 1)
+            r = oracle.run(edges, spec["n"], p, seed, want_sample=want, threads=threads)
             if want:
                 r["kept_checksum"] = checksum(r.pop("kept"))
                 r["heavy_checksum"] = heavy_checksum(r.pop("heavy"))
             r["p"], r["seed"] = p, seed
             r["estimate_hex"] = float(r["estimate"]).hex()
             r["oracle_seconds"] = round(time.time() - t0, 2)
+            if threads > 1:
+                r["oracle_threads"] = threads
             rec["runs"].append(r)
             print(name, p, seed, r, flush=True)
             with open(path, "w") as f:  # after every run: the long ones come last
