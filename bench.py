@@ -1,24 +1,28 @@
 #!/usr/bin/env python
 """Throughput benchmark of the edge-sampled, degree-partitioned triangle count.
 
-Workload: Chung-Lu power-law graph, n = 2^22 vertices, 2^26 undirected
-edges, degree exponent 2.1, maximum expected degree 1e5, seed 1 (synthetic
-stand-in for the paper's multi-million-edge social graphs).  One step counts
-the graph at p = 1.0, 0.1 and 0.01 (seed = step index + 1 each): sampling,
-degree partition, degree-oriented CSR, light and heavy class counts and the
-rescaled estimate, all on the GPU.
+Default workload: the largest graph, R-MAT scale 26, edge factor 16,
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), seed 1: the library canonicalises
+the 2^30 raw draws (pinned host memory) into m = 1,051,928,416 undirected
+edges.  One step counts the graph at p = 1.0 and p = 0.05 (seed = step
+index + 1 each): sampling, degree partition, degree-oriented CSR, light and
+heavy class counts and the rescaled estimate, all on the GPU.
 
 Metric: input edges processed by the sampler per second (sampled edges/s),
-whole job.  The edge list (512 MiB) is larger than L2, so no L2 flush is
-needed between steps.
+whole job.  The graph (8 GiB of keys in rank order, plus their original
+keys) is far larger than L2, so no L2 flush is needed between steps.
+
+The default single-GPU run also measures, as extra keys of the same line,
+the batched form (10,000 uneven graphs in one launch against one call per
+graph: "batched") and the served form (a Poisson request stream against one
+blocking call per request: "served"); --no-extras skips them.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload chung_lu|rmat26|dense_core|batch|serve]
+                    [--workload rmat26|chung_lu|dense_core|batch|serve]
 
-Other workloads: rmat26 is the largest graph (R-MAT scale 26, edge factor
-16: the library canonicalises the 2^30 raw draws into about 10^9 edges; one
-step counts p = 1 and 0.05); dense_core stresses the tensor-core heavy block;
-batch and serve time the batched and served forms against the plain path.
+Other workloads: chung_lu is the 2^22-vertex, 2^26-edge power-law graph
+(p = 1, 0.1, 0.01 per step); dense_core stresses the tensor-core heavy
+block; batch and serve time the batched and served forms alone.
 
 With N > 1 (torchrun, one process per GPU) every rank counts its own replica
 of the workload (no data-path collective); time is the max over ranks.
@@ -61,7 +65,8 @@ WORKLOADS = {
               "slot_edges": 1 << 25, "slot_vertices": 1 << 24, "slot_requests": 4096,
               "saturation_requests": 30000, "graph_seed": 2},
 }
-WORKLOAD = WORKLOADS["chung_lu"]
+DEFAULT_WORKLOAD = "rmat26"
+WORKLOAD = WORKLOADS[DEFAULT_WORKLOAD]
 METRIC = "sampled edges/s"
 UNIT = "edges/s"
 
@@ -73,8 +78,12 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of Poisson arrivals")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and served comparisons of the default single-GPU run")
+    ap.add_argument("--extras-serve-duration", type=float, default=10.0,
+                    help="seconds of Poisson arrivals of the served comparison inside the default run")
     ap.add_argument("--rmat-scale", type=int, default=None,
                     help="rmat26: another R-MAT scale (e.g. a smaller case for profiling)")
     return ap.parse_args()
@@ -105,13 +114,14 @@ def job_throughput(ws: int, steps: int, counts_per_step: int, m: int, elapsed_ms
     return ws * steps * counts_per_step * m / (elapsed_ms / 1000.0)
 
 
-def make_graph(out=None):
+def make_graph(out=None, count=None):
     """The workload's input pairs: a canonical edge list, or for R-MAT the raw
-    draws (written into out when given, e.g. a pinned host array)."""
+    draws (written into out when given, e.g. a pinned host array; only the
+    first `count` draws when count is given)."""
     import gen
     w = WORKLOAD
     if w["kind"] == "rmat":
-        return gen.rmat_draws(w["scale"], w["edge_factor"], *w["abc"], seed=w["graph_seed"], out=out)
+        return gen.rmat_draws(w["scale"], w["edge_factor"], *w["abc"], seed=w["graph_seed"], out=out, count=count)
     if w["kind"] == "dense_core":
         return gen.cached("planted_core", gen.planted_core, w["n"], w["core"], w["q"], w["m_rest"], w["graph_seed"])
     return gen.cached("chung_lu", gen.chung_lu, w["n"], w["m"], w["gamma"], w["wmax"], w["graph_seed"])
@@ -210,7 +220,7 @@ def oracle_sample(edges, n):
         canon = oracle.canonicalize(edges[:k], n)
         p = min(w["p_sweep"])
         return canon, p, ("the subgraph of the first %d of the %d raw draws (%d distinct edges, canonicalised "
-                          "by the oracle), p=%g" % (k, len(edges), len(canon), p))
+                          "by the oracle), p=%g" % (k, w["edge_factor"] << w["scale"], len(canon), p))
     return edges, 0.1, "the full graph at p=0.1 (one of the sweep legs; the p=1 leg takes minutes)"
 
 
@@ -231,7 +241,8 @@ def reference_arm(args):
     if rank != 0:
         return
     n = WORKLOAD["n"]
-    edges, p, what = oracle_sample(make_graph(), n)
+    count = WORKLOAD.get("oracle_draws") if WORKLOAD["kind"] == "rmat" else None
+    edges, p, what = oracle_sample(make_graph(count=count), n)
     import oracle
     for i in range(args.warmup):
         oracle.run(edges, n, p, i + 1)
@@ -249,6 +260,10 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": {"workload": WORKLOAD["workload"], "n": n, "m": len(edges),
                                             "p_sweep": [p]},
+            "same_config": False,
+            "note": ("the oracle takes hours on the whole graph at every p of the sweep, so each step is a "
+                     "bounded sample: %s; the GPU arm counts the whole graph at p in %s"
+                     % (what, WORKLOAD["p_sweep"])),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -383,6 +398,18 @@ def our_arm(args):
         cpu = None
         if ws == 1 and not args.no_cpu_baseline and WORKLOAD["kind"] in ("chung_lu", "rmat"):
             cpu = cpu_baseline(edges, n)
+        extras = {}
+        if ws == 1 and not args.no_extras and WORKLOAD["kind"] in ("chung_lu", "rmat"):
+            # the batched and served forms against the plain path, on the same
+            # GPU, after the single graph's memory is returned
+            del edges, host
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            tc.release_cached_memory()
+            extras["batched"] = run_batch(WORKLOADS["batch"], steps=max(1, min(5, args.steps)), warmup=2)
+            torch.cuda.empty_cache()
+            tc.release_cached_memory()
+            extras["served"] = run_serve(WORKLOADS["serve"], args.extras_serve_duration)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -398,6 +425,7 @@ def our_arm(args):
                 "results": [{k: r[k] for k in ("m_sampled", "n_heavy", "t_light", "t_heavy", "estimate")}
                             for r in results],
                 "kept_edges_per_s": ws * args.steps * sum(r["m_sampled"] for r in results) / (elapsed_ms / 1e3)}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -416,16 +444,15 @@ def make_batch_graphs(count: int, seed: int = 1):
     return specs, graphs
 
 
-def batch_arm(args):
+def run_batch(w, steps: int, warmup: int, plain_steps: int = 3) -> dict:
     """Batched counting (tc_batch_*) against the plain one-count-per-graph
-    path on the same GPU, same graphs, same (p, seed): graphs per second."""
+    path on the same GPU, same graphs, same (p, seed): the result line (a
+    dict) of workload w (WORKLOADS["batch"])."""
     import numpy as np
     import torch
     from paper_1011_0468_gb300 import tc
 
-    torch.cuda.set_device(0)
     tc.lib()
-    w = WORKLOAD
     specs, graphs = make_batch_graphs(w["graphs"], w["graph_seed"])
     k = len(graphs)
     p = np.array([s["p"] for s in specs], dtype=np.float64)
@@ -433,13 +460,13 @@ def batch_arm(args):
     batch = tc.Batch([(g, s["n"]) for g, s in zip(graphs, specs)])
     m_total = batch.m
     schedule = batch.autotune(p, seeds)
-    for i in range(args.warmup):
+    for i in range(warmup):
         batch.count(p, seeds + np.uint64(i))
     l0 = tc.tc_launch_count()
     with ClockSampler(0) as clocks:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i in range(args.steps):
+        for i in range(steps):
             res = batch.count(p, seeds + np.uint64(i))
         t_batch = time.perf_counter() - t0
     launches = tc.tc_launch_count() - l0
@@ -454,7 +481,7 @@ def batch_arm(args):
             o.count_async(float(p[j]), int(seeds[j]), buf[j].data_ptr())
         for o in objs:
             o.sync()
-    plain_steps = max(1, min(args.steps, 3))
+    plain_steps = max(1, min(steps, plain_steps))
     t0 = time.perf_counter()
     for i in range(plain_steps):
         for j, o in enumerate(objs):
@@ -472,20 +499,26 @@ def batch_arm(args):
     for o in objs:
         o.close()
 
-    value = args.steps * k / t_batch
+    value = steps * k / t_batch
     plain_value = plain_steps * k / t_plain
-    line = {"metric": "batched graphs/s", "value": value, "unit": "graphs/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000 * t_batch / args.steps, "higher_is_better": True,
+    line = {"metric": "batched graphs/s", "value": value, "unit": "graphs/s", "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": 1000 * t_batch / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": w["workload"], "graphs": k, "m_total": int(m_total),
                        "n_total": int(sum(s["n"] for s in specs)), "schedule": schedule},
-            "edges_per_s": args.steps * m_total / t_batch,
+            "edges_per_s": steps * m_total / t_batch,
             "plain": {"value": plain_value, "unit": "graphs/s", "ms_per_step": 1000 * t_plain / plain_steps,
                       "path": "one tc_count_async per graph, graphs resident"},
             "speedup_vs_plain": value / plain_value, "identical_to_plain": identical,
             "gpu_launches": int(launches), "clocks": clocks.summary(),
             "t_total_estimate_sum": float(np.sum(res["estimate"]))}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def batch_arm(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(run_batch(WORKLOAD, args.steps, args.warmup)), flush=True)
 
 
 def serve_requests(w, n_small, duration, seed=7):
@@ -518,10 +551,11 @@ def _pct(x, q):
     return float(np.percentile(np.asarray(x), q)) if len(x) else None
 
 
-def serve_arm(args):
-    """Served counting (tc_server_*) under a Poisson request stream, against
-    the plain path (one blocking tc_count per request, in arrival order) on
-    the same stream; then both at saturation."""
+def run_serve(w, duration: float) -> dict:
+    """Served counting (tc_server_*) under a Poisson request stream of
+    `duration` seconds, against the plain path (one blocking tc_count per
+    request, in arrival order) on the same stream; then both at saturation.
+    Returns the result line (a dict) of workload w (WORKLOADS["serve"])."""
     import queue
     import threading
     import numpy as np
@@ -529,15 +563,13 @@ def serve_arm(args):
     import gen
     from paper_1011_0468_gb300 import tc
 
-    torch.cuda.set_device(0)
     tc.lib()
-    w = WORKLOAD
     specs, small = make_batch_graphs(w["small_graphs"], w["graph_seed"])
     L = w["large"]
     large = [gen.cached("chung_lu", gen.chung_lu, L["n"], L["m"], L["gamma"], L["wmax"], 100 + i)
              for i in range(w["large_graphs"])]
     pool = [(g, s["n"]) for g, s in zip(small, specs)] + [(g, L["n"]) for g in large]
-    t_arr, gid, p, sd = serve_requests(w, len(small), args.duration)
+    t_arr, gid, p, sd = serve_requests(w, len(small), duration)
     R = len(t_arr)
     KEYS = ("m_sampled", "n_heavy", "t_light", "t_heavy", "estimate")
 
@@ -617,7 +649,7 @@ def serve_arm(args):
             "warmup": 1, "ms_per_step": 1000.0 * span, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": w["workload"], "requests": R, "rate_per_s": w["rate"],
-                       "duration_s": args.duration, "pool_graphs": len(pool),
+                       "duration_s": duration, "pool_graphs": len(pool),
                        "pool_input_edges": int(edges.sum()), "large_frac": w["large_frac"],
                        "budget_bytes": w["budget"], "slots": w["slots"], "slot_edges": w["slot_edges"],
                        "slot_requests": w["slot_requests"]},
@@ -634,7 +666,13 @@ def serve_arm(args):
                        "resident_bytes": st["resident_bytes"], "slot_bytes": st["slot_bytes"],
                        "uploads": st["uploads"], "evictions": st["evictions"], "add_graph_s": t_add},
             "gpu_launches": int(launches), "clocks": clocks.summary()}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def serve_arm(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(run_serve(WORKLOAD, args.duration)), flush=True)
 
 
 def select_workload(name: str, rmat_scale=None) -> dict:

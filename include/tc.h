@@ -151,6 +151,22 @@ tc_status tc_graph_set_timing(tc_graph *g, int on);
    never depend on it.  TC_EINVAL for a NULL graph. */
 tc_status tc_graph_set_sample_floor(tc_graph *g, int64_t m_lo);
 
+/* Which graph the degree partition of Section 3.2 splits, for the graph's
+   later counts (and tc_graph_export_sample):
+     TC_PARTITION_SAMPLED   (the default) the sampled graph: heavy <=>
+                            deg_p^2 > m_p;
+     TC_PARTITION_ORIGINAL  the whole graph before sparsification: heavy <=>
+                            deg^2 > m, and the sampled triangles are split
+                            into t_light / t_heavy by those flags.
+   The paper states the partition for "the graph" and runs it on the
+   sparsified graph in its hybrid; the second reading is offered as an
+   option.  t_light + t_heavy and the estimate are the same under both.
+   Batched and served counts always use the sampled graph.  TC_EINVAL for a
+   NULL graph or an unknown mode. */
+#define TC_PARTITION_SAMPLED 0
+#define TC_PARTITION_ORIGINAL 1
+tc_status tc_graph_set_partition(tc_graph *g, int mode);
+
 /* The dense core of the top ranks (see tc_graph_create) for the graph's later
    counts: ranks < 0 restores the default (each count chooses from its p),
    0 turns it off, and 8192, 16384, 32768 or 65536 makes every count use a
@@ -177,13 +193,42 @@ int tc_graph_timing_drain(tc_graph *g, float *ms_out, uint32_t max_counts);
 tc_status tc_count(tc_graph *g, double p, uint64_t seed, tc_result *out);
 
 /*
- * Same computation, enqueued on the graph's stream without waiting.  The
- * result (including the float64 estimate, computed on the device) is
- * written to *out when the stream reaches that point; *out should be pinned
- * host memory (cudaMallocHost) for the copy to be asynchronous.  Call
- * tc_graph_sync before reading it.  ms[] is not filled.
+ * Same computation, enqueued without waiting.  The result (including the
+ * float64 estimate, computed on the device) is written to *out when the
+ * stream reaches that point; *out should be pinned host memory
+ * (cudaMallocHost) for the copy to be asynchronous.  ms[] is not filled.
+ *   cuda_stream  NULL (or the graph's own stream): the count is enqueued on
+ *                the graph's stream.  Another cudaStream_t: the count runs
+ *                there, after the work already enqueued for the graph, and
+ *                the graph's stream waits for it, so tc_graph_sync (or a
+ *                synchronisation of cuda_stream) makes *out valid.  The
+ *                stream must belong to the graph's device.
+ * Counts of one graph share its scratch: they are ordered, never
+ * concurrent, whichever streams they are given.
+ * Errors: TC_EINVAL (NULL graph or out, p not in (0, 1] or NaN), TC_ECUDA.
  */
-tc_status tc_count_async(tc_graph *g, double p, uint64_t seed, tc_result *out);
+tc_status tc_count_async(tc_graph *g, double p, uint64_t seed, tc_result *out, void *cuda_stream);
+
+/*
+ * Batched count over graphs already resident (Sections 3.1-3.2 for each
+ * graph with its own p[i] and seed[i]): the k graphs are gathered into one
+ * disjoint union on the device (their stored keys, no input is read again)
+ * and counted by one launch sequence; out[i] (host memory) receives exactly
+ * what tc_count(graphs[i], p[i], seed[i]) returns, except that ms[] and the
+ * work counters (src_elems, nbr_elems, partners, heavy_mma_flops) are zero.
+ * The heavy class of every graph is counted by the intersection kernels.
+ *   graphs   k graph handles of the current device (a graph may appear more
+ *            than once, e.g. with several p); k in 1 .. 65535, at most
+ *            2^32 - 2 edges and fewer than 2^32 - 1 vertices in total.
+ * The call allocates the union's scratch (about 40 bytes per edge) on a
+ * stream of its own, blocks until the results are in out, and frees it.
+ * It does not touch the graphs' scratch, so it may run while other counts
+ * of the same graphs are pending.
+ * Errors: TC_EINVAL (NULL pointers, a NULL graph, p[i] outside (0, 1], size
+ * limits), TC_ENOMEM, TC_ECUDA, TC_ETIMEOUT.
+ */
+tc_status tc_count_batch(tc_graph *const *graphs, const double *p, const uint64_t *seed, uint32_t k,
+                         tc_result *out);
 
 /* Wait for all enqueued work of the graph; reports a device-side error or
    timeout raised by that work. */
@@ -362,6 +407,50 @@ void tc_server_destroy(tc_server *srv);
 #define TC_NOALLOC_MAX_VERTICES (1u << 18)
 tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, uint32_t n, double p, uint64_t seed,
                            tc_result *out_host, void *cuda_stream);
+
+/*
+ * Triple sampling (Section 3.2), on the sample of Section 3.1 (the hybrid
+ * algorithm of Section 3.3 when p < 1): the "Simple" and "Hybrid" columns
+ * of the paper's experiments.  The edge sample is the one tc_count draws
+ * for (p, seed).  On the sampled graph, U is a set of vertex triples that
+ * holds every triangle, taken vertex by vertex in id order with neighbour
+ * lists sorted by id:
+ *   TC_TRIPLES_SIMPLE  every vertex contributes its wedges: the C(d, 2)
+ *                      pairs {N(u)[a], N(u)[b]}, a < b, numbered
+ *                      b (b - 1) / 2 + a;
+ *   TC_TRIPLES_HYBRID  light vertices (deg_p^2 <= m_p) contribute their
+ *                      wedges, heavy ones their 2-paths u - v - w (v in
+ *                      N(u), w in N(v), numbered by v's position, then w's):
+ *                      sum over v in N(u) of deg_p(v) of them.
+ * A wedge v-u-w is a triangle iff vw is an edge; a 2-path iff w != u and uw
+ * is an edge.  Every triangle is in U once per light corner and twice per
+ * heavy corner.  Sample i (0 <= i < s) is the triple of index
+ * floor(h_i |U| / 2^64), h_i = splitmix64(i ^ splitmix64(~seed)): s
+ * independent uniform draws.  estimate = |U| (2 closed_wedge +
+ * closed_path) / (6 s) / p^3 in float64, an unbiased estimate of t.
+ *   samples   s; 0 draws m_p samples (as many queries as kept edges).
+ *   out       host memory; ms is the device time of the call.
+ * The first call on a graph builds and keeps the symmetric adjacency of the
+ * whole graph in original ids (8 m + 4 n bytes); every call uses 12 m +
+ * 12 n bytes more of scratch, also kept for later calls (released by
+ * tc_graph_destroy).  Blocks until *out is filled.
+ * Errors: TC_EINVAL (NULL graph or out, p outside (0, 1], an unknown mode,
+ * graphs of 2^31 edges or more), TC_ENOMEM, TC_ECUDA.
+ */
+#define TC_TRIPLES_SIMPLE 0
+#define TC_TRIPLES_HYBRID 1
+typedef struct {
+    uint64_t m, m_sampled;
+    uint32_t n, n_heavy;   /* n_heavy: vertices whose triples are 2-paths (0 in the simple mode) */
+    uint64_t universe;     /* |U| */
+    uint64_t samples;      /* s */
+    uint64_t closed_wedge; /* sampled wedges that are triangles */
+    uint64_t closed_path;  /* sampled 2-paths that are triangles */
+    double estimate;
+    uint32_t mode;         /* TC_TRIPLES_SIMPLE or TC_TRIPLES_HYBRID */
+    float ms;
+} tc_triple_result;
+tc_status tc_count_triples(tc_graph *g, double p, uint64_t seed, uint64_t samples, int mode, tc_triple_result *out);
 
 /* Static description of a status code. */
 const char *tc_status_str(tc_status s);

@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 
 using namespace tcg;
@@ -97,6 +99,15 @@ std::vector<int> pass_widths(int bits)
 
 constexpr int NUM_EVENTS = 6;
 
+// Host-side NVTX range (shows each phase's enqueue in a profiler timeline;
+// a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 std::atomic<unsigned long long> g_launches{0};
 
 }  // namespace
@@ -150,6 +161,10 @@ struct tc_graph {
     uint64_t ring_head = 0;  // next slot to record
     uint64_t ring_tail = 0;  // oldest undrained count
     int64_t sample_floor = -1;  // lower bound on m_p for the degree candidates (< 0: the default)
+    cudaEvent_t join_in = nullptr, join_out = nullptr;  // order a count on a caller's stream with the graph's
+    int partition = TC_PARTITION_SAMPLED;  // which graph the degree partition splits
+    TripleBuffers tri;          // triple sampling (built by the first tc_count_triples)
+    bool tri_ready = false;
     std::vector<void *> allocs;
 
     void *alloc(uint64_t b)
@@ -182,6 +197,8 @@ void free_graph(tc_graph *g)
     if (g->res_host) cudaFreeHost(g->res_host);
     if (g->st_host) cudaFreeHost(g->st_host);
     for (auto &e : g->ring) cudaEventDestroy(e);
+    if (g->join_in) cudaEventDestroy(g->join_in);
+    if (g->join_out) cudaEventDestroy(g->join_out);
     cudaGetLastError();
     delete g;
 }
@@ -243,6 +260,10 @@ CountBuffers buffers_of(tc_graph *g)
     b.items = g->items;
     b.items_cap = g->items_cap;
     b.st = g->st;
+    if (g->partition == TC_PARTITION_ORIGINAL) {
+        b.frow = g->frow;
+        b.m_orig = g->m;
+    }
     return b;
 }
 
@@ -347,19 +368,30 @@ tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bo
     if (core) ra.core_base = core->base;
     CountBuffers b = buffers_of(g);
     if (core) b.core_base = core->base;
+    NvtxRange whole("tc_count");
     record(g, timing, 0);
-    enqueue_sample(g, ra);
+    {
+        NvtxRange r("tc_count: sample + partition");
+        enqueue_sample(g, ra);
+    }
     record(g, timing, 1);
     if (g->m > 0) {
+        NvtxRange r("tc_count: oriented CSR");
         if (g->hb.hcap) heavy_decide(b, g->hb, core, g->stream);
         build_rows(ra, g->stream);
         if (g->hb.hcap) heavy_prepare(b, g->hb, core, g->stream);
         build_items(b, g->stream);
     }
     record(g, timing, 2);
-    if (g->m > 0) intersect(b, g->smem_bytes, g->stream);
+    if (g->m > 0) {
+        NvtxRange r("tc_count: light wedges (intersections)");
+        intersect(b, g->smem_bytes, g->stream);
+    }
     record(g, timing, 3);
-    if (g->m > 0 && g->hb.hcap) heavy_contract(b, g->hb, core, g->stream);
+    if (g->m > 0 && g->hb.hcap) {
+        NvtxRange r("tc_count: heavy block (tensor cores)");
+        heavy_contract(b, g->hb, core, g->stream);
+    }
     record(g, timing, 4);
     finalize(b, p, g->res_dev, g->stream);
     record(g, timing, 5);
@@ -668,6 +700,13 @@ tc_status tc_graph_set_sample_floor(tc_graph *g, int64_t m_lo)
     return TC_OK;
 }
 
+tc_status tc_graph_set_partition(tc_graph *g, int mode)
+{
+    if (!g || (mode != TC_PARTITION_SAMPLED && mode != TC_PARTITION_ORIGINAL)) return TC_EINVAL;
+    g->partition = mode;
+    return TC_OK;
+}
+
 tc_status tc_graph_set_core_ranks(tc_graph *g, int64_t ranks)
 {
     if (!g) return TC_EINVAL;
@@ -753,10 +792,172 @@ tc_status tc_count(tc_graph *g, double p, uint64_t seed, tc_result *out)
     return TC_OK;
 }
 
-tc_status tc_count_async(tc_graph *g, double p, uint64_t seed, tc_result *out)
+tc_status tc_count_async(tc_graph *g, double p, uint64_t seed, tc_result *out, void *cuda_stream)
 {
     if (!g || !out || bad_p(p)) return TC_EINVAL;
-    return enqueue_count(g, p, seed, out, g->timing != 0 && !g->ring.empty());
+    const bool timing = g->timing != 0 && !g->ring.empty();
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!s || s == g->stream) return enqueue_count(g, p, seed, out, timing);
+    // the count runs on the caller's stream, after the graph's pending work,
+    // and the graph's stream waits for it (so tc_graph_sync covers it)
+    if (!g->join_in) {
+        if (cudaEventCreateWithFlags(&g->join_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&g->join_out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (g->join_in) cudaEventDestroy(g->join_in);
+            g->join_in = g->join_out = nullptr;
+            return TC_ECUDA;
+        }
+    }
+    cudaStream_t own = g->stream;
+    cudaEventRecord(g->join_in, own);
+    cudaStreamWaitEvent(s, g->join_in, 0);
+    g->stream = s;
+    const tc_status st = enqueue_count(g, p, seed, out, timing);
+    g->stream = own;
+    cudaEventRecord(g->join_out, s);
+    cudaStreamWaitEvent(own, g->join_out, 0);
+    if (st != TC_OK) return st;
+    return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ECUDA;
+}
+
+tc_status tc_count_batch(tc_graph *const *graphs, const double *p, const uint64_t *seed, uint32_t k, tc_result *out)
+{
+    if (!graphs || !p || !seed || !out || k == 0 || k > 0xffffu) return TC_EINVAL;
+    std::vector<uint64_t> eoff(k + 1, 0), thr(k), mix(k);
+    std::vector<uint32_t> voff(k + 1, 0);
+    std::vector<const uint64_t *> src(2 * (size_t)k);
+    uint64_t n_total = 0;
+    for (uint32_t i = 0; i < k; ++i) {
+        const tc_graph *g = graphs[i];
+        if (!g || bad_p(p[i])) return TC_EINVAL;
+        eoff[i + 1] = eoff[i] + g->m;
+        n_total += g->n;
+        if (n_total >= 0xffffffffull) return TC_EINVAL;
+        voff[i + 1] = (uint32_t)n_total;
+        thr[i] = threshold_of(p[i]);
+        mix[i] = splitmix64(seed[i]);
+        src[i] = g->rel;
+        src[k + i] = g->orig;
+    }
+    const uint64_t m = eoff[k];
+    if (m > 0xfffffffeull) return TC_EINVAL;
+    NvtxRange whole("tc_count_batch");
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    UnionScratch u;
+    std::vector<void *> allocs;
+    uint64_t bytes = 0;
+    const uint64_t **d_src = nullptr;
+    DevState st_host;
+    tc_status st = TC_OK;
+    if (!union_scratch_alloc(u, m, (uint32_t)n_total, k, allocs, bytes) ||
+        cudaMalloc((void **)&d_src, 2 * (size_t)k * sizeof(void *)) != cudaSuccess) {
+        cudaGetLastError();
+        st = TC_ENOMEM;
+    }
+    if (d_src) allocs.push_back((void *)d_src);
+    if (st == TC_OK) {
+        cudaMemcpyAsync(u.eoff, eoff.data(), (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(u.voff, voff.data(), (k + 1) * 4ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(u.thr, thr.data(), k * 8ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(u.seed_mix, mix.data(), k * 8ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(u.p, p, k * 8ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_src, src.data(), 2 * (size_t)k * sizeof(void *), cudaMemcpyHostToDevice, s);
+        gather_graphs(d_src, d_src + k, u.eoff, u.voff, k, m, u.rel, u.orig, s);
+        union_count(u, m, (uint32_t)n_total, k, IsectConfig{}, s);
+        cudaMemcpyAsync(out, u.res_dev, k * sizeof(tc_result), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&st_host, u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            st = TC_ECUDA;
+        } else {
+            st = status_of_err(st_host.err);
+        }
+    }
+    cudaStreamSynchronize(s);
+    for (void *q : allocs) cudaFree(q);
+    cudaStreamDestroy(s);
+    cudaGetLastError();
+    return st;
+}
+
+tc_status tc_count_triples(tc_graph *g, double p, uint64_t seed, uint64_t samples, int mode, tc_triple_result *out)
+{
+    if (!g || !out || bad_p(p) || (mode != TC_TRIPLES_SIMPLE && mode != TC_TRIPLES_HYBRID)) return TC_EINVAL;
+    if (2 * g->m > 0xffffffffull) return TC_EINVAL;
+    NvtxRange whole("tc_count_triples");
+    if (sync_graph(g) == TC_ECUDA) return TC_ECUDA;
+    const uint32_t n = g->n;
+    const uint64_t m = g->m, len = std::max<uint64_t>(2 * m, 1);
+    TripleBuffers &tb = g->tri;
+    if (!g->tri_ready) {
+        NvtxRange r("tc_count_triples: symmetric adjacency");
+        tb.n = n;
+        tb.m = m;
+        tb.hcap = (uint32_t)(2.0 * std::sqrt((double)m)) + 2;
+        tb.soff = (uint32_t *)g->alloc(((uint64_t)n + 1) * 4);
+        tb.snbr = (uint32_t *)g->alloc(len * 4);
+        tb.off_p = (uint32_t *)g->alloc(((uint64_t)n + 1) * 4);
+        tb.nbr_p = (uint32_t *)g->alloc(len * 4);
+        tb.qpre = (uint32_t *)g->alloc(len * 4);
+        tb.cnt = (unsigned long long *)g->alloc(((uint64_t)n + 1) * 8);
+        tb.scan64 = (unsigned long long *)g->alloc((ceil_div((uint64_t)n + 1, SC_CHUNK) + 1) * 8);
+        tb.scan32 = (uint32_t *)g->alloc(scan_scratch_elems((uint64_t)n + 1) * 4);
+        tb.hlist = (uint32_t *)g->alloc((uint64_t)tb.hcap * 4);
+        tb.dev = (TripleDev *)g->alloc(sizeof(TripleDev));
+        tb.res = (tc_triple_result *)g->alloc(sizeof(tc_triple_result));
+        const uint64_t hist_len = std::max<uint64_t>(ceil_div(len, RX_TILE), 1) << RX_MAX_BITS;
+        uint64_t *ka = (uint64_t *)g->alloc(len * 8), *kb = (uint64_t *)g->alloc(len * 8);
+        uint32_t *hist = (uint32_t *)g->alloc(hist_len * 4);
+        uint32_t *hscan = (uint32_t *)g->alloc(scan_scratch_elems(hist_len) * 4);
+        auto drop_all = [&]() {
+            for (void *q : {(void *)ka, (void *)kb, (void *)hist, (void *)hscan, (void *)tb.soff, (void *)tb.snbr,
+                            (void *)tb.off_p, (void *)tb.nbr_p, (void *)tb.qpre, (void *)tb.cnt, (void *)tb.scan64,
+                            (void *)tb.scan32, (void *)tb.hlist, (void *)tb.dev, (void *)tb.res})
+                if (q) g->release(q);
+            tb = TripleBuffers{};
+        };
+        if (!tb.soff || !tb.snbr || !tb.off_p || !tb.nbr_p || !tb.qpre || !tb.cnt || !tb.scan64 || !tb.scan32 ||
+            !tb.hlist || !tb.dev || !tb.res || !ka || !kb || !hist || !hscan) {
+            drop_all();
+            return TC_ENOMEM;
+        }
+        triples_build(g->orig, m, n, g->nbits, tb, ka, kb, hist, hscan, g->stream);
+        if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+            cudaGetLastError();
+            drop_all();
+            return TC_ECUDA;
+        }
+        g->release(ka);
+        g->release(kb);
+        g->release(hist);
+        g->release(hscan);
+        g->tri_ready = true;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    if (timed) cudaEventRecord(e0, g->stream);
+    triples_count(tb, splitmix64(seed), threshold_of(p), seed, samples, mode == TC_TRIPLES_HYBRID, p, tb.res,
+                  g->stream);
+    if (timed) cudaEventRecord(e1, g->stream);
+    tc_triple_result host;
+    cudaMemcpyAsync(&host, tb.res, sizeof(host), cudaMemcpyDeviceToHost, g->stream);
+    const cudaError_t e = cudaStreamSynchronize(g->stream);
+    float ms = 0.0f;
+    if (timed && e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    host.ms = ms;
+    *out = host;
+    return TC_OK;
 }
 
 tc_status tc_graph_sync(tc_graph *g)

@@ -210,6 +210,33 @@ void union_count(UnionScratch &u, uint64_t m, uint32_t n, uint32_t k, const Isec
     finalize_batch(cb, u.p, u.res_dev, s);
 }
 
+// Key i of a union of resident graphs: graph g's rank-order key and its
+// original key (rel_src[g], orig_src[g], m_g keys each), both endpoints
+// shifted by voff[g]; keys stay sorted because the vertex ranges increase.
+__global__ void k_gather_graphs(const uint64_t *const *__restrict__ rel_src, const uint64_t *const *__restrict__ orig_src,
+                                const uint64_t *__restrict__ eoff, const uint32_t *__restrict__ voff, uint32_t k,
+                                uint64_t m, uint64_t *__restrict__ rel, uint64_t *__restrict__ orig)
+{
+    const unsigned lane = lane_id();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < m; base += stride) {
+        const uint64_t i = base + lane, ii = i < m ? i : m - 1;
+        const uint32_t g = find_part_warp(eoff, k, ii);
+        if (i >= m) continue;
+        const uint64_t vo = __ldg(voff + g), j = i - __ldg(eoff + g), shift = (vo << 32) | vo;
+        rel[i] = __ldg(rel_src[g] + j) + shift;
+        orig[i] = __ldg(orig_src[g] + j) + shift;
+    }
+}
+
+void gather_graphs(const uint64_t *const *rel_src, const uint64_t *const *orig_src, const uint64_t *eoff,
+                   const uint32_t *voff, uint32_t k, uint64_t m, uint64_t *rel, uint64_t *orig, cudaStream_t s)
+{
+    if (m == 0) return;
+    k_gather_graphs<<<grid_for(m, 256, 152 * 8), 256, 0, s>>>(rel_src, orig_src, eoff, voff, k, m, rel, orig);
+    note_launch();
+}
+
 }  // namespace tcg
 
 struct tc_batch {

@@ -67,9 +67,15 @@ __global__ void k_partition(const uint32_t *__restrict__ deg, uint32_t n, DevSta
 // is kept).  The rest are light, and light_lim is at least cand_lo.  Each
 // counter of spread then becomes its vertex's in-list cursor (the static
 // reservation inres).
+// With m_orig != 0 the flags come from the whole graph instead (the
+// alternative reading of Section 3.2): heavy <=> (full degree)^2 > m_orig,
+// the full degree being the static row length (frow) plus the static
+// in-degree (inres).  Those vertices are a suffix of the rank order, so
+// every light vertex counts toward light_lim.
 __global__ void k_partition_cand(const uint32_t *__restrict__ dplus, uint32_t *__restrict__ spread, int hbits,
                                  const uint32_t *__restrict__ inres, bool all_kept, uint32_t n, uint32_t core_base,
-                                 DevState *st, uint32_t *__restrict__ deg, uint8_t *__restrict__ heavy)
+                                 DevState *st, uint32_t *__restrict__ deg, uint8_t *__restrict__ heavy,
+                                 const uint32_t *__restrict__ frow, unsigned long long m_orig)
 {
     uint32_t below = 0;  // heavy vertices below the dense core's base
     const unsigned long long mp = st->m_sampled;
@@ -80,8 +86,12 @@ __global__ void k_partition_cand(const uint32_t *__restrict__ dplus, uint32_t *_
         uint32_t d = dplus[u];
         uint8_t f = 0;
         uint32_t *sp = spread + hot_index((uint32_t)u, hbits);
-        if (u >= cand) {
-            d += all_kept ? inres[u + 1] - inres[u] : *sp;
+        if (u >= cand) d += all_kept ? inres[u + 1] - inres[u] : *sp;
+        if (m_orig) {
+            const unsigned long long full = (frow[u + 1] - frow[u]) + (inres[u + 1] - inres[u]);
+            f = full * full > m_orig;
+            if (!f) lim = (uint32_t)u + 1;
+        } else if (u >= cand) {
             f = (unsigned long long)d * d > mp;
             if (!f && d) lim = (uint32_t)u + 1;
         }
@@ -105,7 +115,7 @@ void partition(const CountBuffers &b, cudaStream_t s)
         k_partition_cand<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.rowptr, b.spread,
                                                                      hot_bits(b.n), b.inptr,
                                                                      b.all_kept, b.n, b.core_base, b.st, b.deg,
-                                                                     b.heavy);
+                                                                     b.heavy, b.frow, b.frow ? b.m_orig : 0ull);
     } else {
         k_partition<<<grid_for(b.n, 256, 152 * 8), 256, 0, s>>>(b.deg, b.n, b.st, b.heavy, b.bv);
     }

@@ -34,6 +34,9 @@ uint64_t scan_scratch_elems(uint64_t len);
 // sum of all elements is written there (device pointer).  scratch holds
 // scan_scratch_elems(len) uint32.
 void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch, cudaStream_t s);
+// The same over 64-bit values; scratch holds ceil(len / SC_CHUNK) + 1 of them.
+void scan_excl_u64(unsigned long long *a, uint64_t len, unsigned long long *total, unsigned long long *scratch,
+                   cudaStream_t s);
 // Exclusive prefix sums of a[0, len) and b[0, len) in one pass; the sum of b
 // must stay below 2^32.  scratch as for scan_excl_u32.
 void scan_excl_pair(uint32_t *a, uint32_t *b, uint64_t len, uint32_t *scratch, cudaStream_t s);
@@ -208,6 +211,10 @@ struct CountBuffers {
     // reservations
     bool static_rows = false, all_kept = false;
     uint32_t *spread = nullptr;
+    // single graph: partition on the whole graph's degrees (deg^2 > m_orig)
+    // when frow is set, else on the sample's
+    const uint32_t *frow = nullptr;
+    uint64_t m_orig = 0;
 };
 
 void partition(const CountBuffers &b, cudaStream_t s);
@@ -250,6 +257,11 @@ struct UnionScratch {
 // was allocated, bytes the total).
 bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32_t k_cap, std::vector<void *> &allocs,
                          uint64_t &bytes);
+// Union of resident graphs: rel / orig [m] <- graph g's rank-order keys
+// rel_src[g] and original keys orig_src[g] (device pointer arrays, k
+// entries), shifted by voff[g]; eoff / voff as for BatchView.
+void gather_graphs(const uint64_t *const *rel_src, const uint64_t *const *orig_src, const uint64_t *eoff,
+                   const uint32_t *voff, uint32_t k, uint64_t m, uint64_t *rel, uint64_t *orig, cudaStream_t s);
 // The count of k graphs whose union (m edges, n vertices) sits in u.rel /
 // u.orig (rank order, see csr.cu), with u.eoff / u.voff / u.thr /
 // u.seed_mix / u.p filled: per-graph results land in u.res_dev.
@@ -300,5 +312,36 @@ void heavy_prepare(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuff
 // T_H += sum_{i<k} U_ik (U U)_ik on tcgen05 (no-op unless DevState::dense),
 // and t_core likewise over the core matrix when DevState::core_on
 void heavy_contract(const CountBuffers &b, const HeavyBuffers &hb, const CoreBuffers *core, cudaStream_t s);
+
+// ---------------------------------------------------------------- triples.cu
+// Triple sampling (Sections 3.2-3.3) over the symmetric adjacency of a graph
+// in its original ids (see triples.cu for U and the estimator).
+struct TripleDev {
+    unsigned long long m_p, universe, samples, closed_wedge, closed_path;
+    unsigned int n_heavy, nlist, err, pad;
+};
+struct TripleBuffers {
+    uint32_t n = 0;
+    uint64_t m = 0;
+    uint32_t *soff = nullptr;   // [n + 1] the whole graph: row offsets of the symmetric adjacency
+    uint32_t *snbr = nullptr;   // [2 m] neighbours, every row sorted by id
+    uint32_t *off_p = nullptr;  // [n + 1] the same for the sample of a count (p < 1)
+    uint32_t *nbr_p = nullptr;  // [2 m]
+    uint32_t *qpre = nullptr;   // [2 m] heavy rows: 2-paths through the earlier neighbours
+    unsigned long long *cnt = nullptr;     // [n + 1] triples per vertex, then their exclusive prefix
+    unsigned long long *scan64 = nullptr;  // scan scratch for n + 1 (64-bit)
+    uint32_t *scan32 = nullptr;            // scan scratch for n + 1 (32-bit)
+    uint32_t *hlist = nullptr;  // heavy vertices of a count [hcap]
+    uint32_t hcap = 0;          // > the number of heavy vertices of any sample (2 m^(1/2) + 2)
+    TripleDev *dev = nullptr;
+    tc_triple_result *res = nullptr;
+};
+// soff / snbr from the m original keys (any order); tmpA / tmpB hold 2 m
+// keys each, hist / scan the radix scratch for 2 m items; nbits covers n.
+void triples_build(const uint64_t *orig, uint64_t m, uint32_t n, int nbits, TripleBuffers &tb, uint64_t *tmpA,
+                   uint64_t *tmpB, uint32_t *hist, uint32_t *scan, cudaStream_t s);
+// One triple-sampling count into *out_dev (thr >= 2^53: every edge kept).
+void triples_count(const TripleBuffers &tb, uint64_t seed_mix, uint64_t thr, uint64_t seed, uint64_t samples,
+                   bool hybrid, double p, tc_triple_result *out_dev, cudaStream_t s);
 
 }  // namespace tcg

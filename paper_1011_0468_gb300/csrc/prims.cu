@@ -12,12 +12,13 @@ namespace tcg {
 constexpr int SC_THREADS = 1024;
 constexpr int SC_ITEMS = SC_CHUNK / SC_THREADS;  // 4
 
-__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__restrict__ a, uint64_t len,
-                                                            uint32_t *__restrict__ part)
+template <typename T>
+__global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const T *__restrict__ a, uint64_t len,
+                                                            T *__restrict__ part)
 {
-    __shared__ uint32_t wt[33];
+    __shared__ T wt[33];
     const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
-    uint32_t s = 0;
+    T s = 0;
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
         uint64_t i = base + (uint64_t)j * SC_THREADS + threadIdx.x;
@@ -29,32 +30,34 @@ __global__ void __launch_bounds__(SC_THREADS) k_scan_reduce(const uint32_t *__re
 
 // One block scans the per-block sums in place (exclusive); writes the
 // grand total to total_out when non-NULL.
-__global__ void __launch_bounds__(SC_THREADS) k_scan_spine(uint32_t *part, uint64_t nparts, uint32_t *total_out)
+template <typename T>
+__global__ void __launch_bounds__(SC_THREADS) k_scan_spine(T *part, uint64_t nparts, T *total_out)
 {
-    __shared__ uint32_t wt[33];
-    uint32_t carry = 0;
+    __shared__ T wt[33];
+    T carry = 0;
     for (uint64_t base = 0; base < nparts; base += SC_THREADS) {
         uint64_t i = base + threadIdx.x;
-        uint32_t x = i < nparts ? part[i] : 0u;
-        uint32_t tot;
-        uint32_t ex = block_excl_scan(x, wt, &tot);
+        T x = i < nparts ? part[i] : T(0);
+        T tot;
+        T ex = block_excl_scan(x, wt, &tot);
         if (i < nparts) part[i] = carry + ex;
         carry += tot;
     }
     if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
-__global__ void __launch_bounds__(SC_THREADS) k_scan_down(uint32_t *a, uint64_t len, const uint32_t *__restrict__ part)
+template <typename T>
+__global__ void __launch_bounds__(SC_THREADS) k_scan_down(T *a, uint64_t len, const T *__restrict__ part)
 {
-    __shared__ uint32_t wt[33];
+    __shared__ T wt[33];
     const uint64_t base = (uint64_t)blockIdx.x * SC_CHUNK;
-    uint32_t carry = part[blockIdx.x];
+    T carry = part[blockIdx.x];
 #pragma unroll
     for (int j = 0; j < SC_ITEMS; ++j) {
         uint64_t i = base + (uint64_t)j * SC_THREADS + threadIdx.x;
-        uint32_t x = i < len ? a[i] : 0u;
-        uint32_t tot;
-        uint32_t ex = block_excl_scan(x, wt, &tot);
+        T x = i < len ? a[i] : T(0);
+        T tot;
+        T ex = block_excl_scan(x, wt, &tot);
         if (i < len) a[i] = carry + ex;
         carry += tot;
     }
@@ -131,9 +134,22 @@ void scan_excl_u32(uint32_t *a, uint64_t len, uint32_t *total, uint32_t *scratch
         return;
     }
     const uint64_t nb = ceil_div(len, SC_CHUNK);
-    k_scan_reduce<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
-    k_scan_spine<<<1, SC_THREADS, 0, s>>>(scratch, nb, total); note_launch();
-    k_scan_down<<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
+    k_scan_reduce<uint32_t><<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
+    k_scan_spine<uint32_t><<<1, SC_THREADS, 0, s>>>(scratch, nb, total); note_launch();
+    k_scan_down<uint32_t><<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
+}
+
+void scan_excl_u64(unsigned long long *a, uint64_t len, unsigned long long *total, unsigned long long *scratch,
+                   cudaStream_t s)
+{
+    if (len == 0) {
+        if (total) cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+        return;
+    }
+    const uint64_t nb = ceil_div(len, SC_CHUNK);
+    k_scan_reduce<unsigned long long><<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
+    k_scan_spine<unsigned long long><<<1, SC_THREADS, 0, s>>>(scratch, nb, total); note_launch();
+    k_scan_down<unsigned long long><<<(unsigned)nb, SC_THREADS, 0, s>>>(a, len, scratch); note_launch();
 }
 
 // ======================================================================

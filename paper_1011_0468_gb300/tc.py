@@ -47,6 +47,20 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 _vp = ctypes.c_void_p
 
 
+class tc_triple_result(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_uint64), ("m_sampled", ctypes.c_uint64), ("n", ctypes.c_uint32),
+                ("n_heavy", ctypes.c_uint32), ("universe", ctypes.c_uint64), ("samples", ctypes.c_uint64),
+                ("closed_wedge", ctypes.c_uint64), ("closed_path", ctypes.c_uint64), ("estimate", ctypes.c_double),
+                ("mode", ctypes.c_uint32), ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+TC_TRIPLES_SIMPLE, TC_TRIPLES_HYBRID = 0, 1
+_TRIPLE_MODES = {"simple": TC_TRIPLES_SIMPLE, "hybrid": TC_TRIPLES_HYBRID}
+
+
 class tc_request_info(ctypes.Structure):
     _fields_ = [("res", tc_result), ("status", ctypes.c_int32), ("wave_size", ctypes.c_uint32),
                 ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
@@ -70,13 +84,18 @@ SIGNATURES = [
     ("tc_graph_set_timing", ctypes.c_int, [_vp, ctypes.c_int]),
     ("tc_graph_set_sample_floor", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("tc_graph_set_core_ranks", ctypes.c_int, [_vp, ctypes.c_int64]),
+    ("tc_graph_set_partition", ctypes.c_int, [_vp, ctypes.c_int]),
     ("tc_graph_timing_drain", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32]),
     ("tc_count", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(tc_result)]),
-    ("tc_count_async", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp]),
+    ("tc_count_async", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp, _vp]),
+    ("tc_count_batch", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_double), _u64p, ctypes.c_uint32,
+                                      _vp]),
     ("tc_graph_sync", ctypes.c_int, [_vp]),
     ("tc_graph_export_sample", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _u32p, _u8p, _u32p, _u64p]),
     ("tc_graph_export_csr", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _u32p, _u32p, _u64p]),
     ("tc_graph_export_edges", ctypes.c_int, [_vp, _u32p]),
+    ("tc_count_triples", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.POINTER(tc_triple_result)]),
     ("tc_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tc_version", ctypes.c_int, []),
     ("tc_release_cached_memory", ctypes.c_int, []),
@@ -161,8 +180,25 @@ def tc_count(g: int, p: float, seed: int) -> tc_result:
     return r
 
 
-def tc_count_async(g: int, p: float, seed: int, out_addr: int) -> None:
-    _check(lib().tc_count_async(g, p, seed & 0xFFFFFFFFFFFFFFFF, out_addr), "tc_count_async")
+def tc_count_async(g: int, p: float, seed: int, out_addr: int, stream=None) -> None:
+    """Enqueue a count; out_addr: address of a tc_result (pinned host memory).
+    stream: None for the graph's stream, else a torch.cuda.Stream or a raw
+    cudaStream_t to run the count on."""
+    _check(lib().tc_count_async(g, p, seed & 0xFFFFFFFFFFFFFFFF, out_addr, _stream_handle(stream)),
+           "tc_count_async")
+
+
+def tc_count_batch(graphs, p, seed) -> np.ndarray:
+    """One batched count over resident graphs (Graph objects or handles),
+    each with its own p and seed: a numpy array of RESULT_DTYPE."""
+    k = len(graphs)
+    hs = (_vp * max(k, 1))(*[g.handle if isinstance(g, Graph) else g for g in graphs])
+    pa = np.ascontiguousarray(np.broadcast_to(np.asarray(p, dtype=np.float64), (k,)))
+    sa = np.ascontiguousarray(np.broadcast_to(np.asarray(seed, dtype=np.uint64), (k,)))
+    out = np.zeros(max(k, 1), dtype=RESULT_DTYPE)
+    _check(lib().tc_count_batch(hs, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), sa.ctypes.data_as(_u64p),
+                                k, out.ctypes.data), "tc_count_batch")
+    return out[:k]
 
 
 def tc_graph_sync(g: int) -> None:
@@ -287,6 +323,12 @@ class Graph:
         counted (tc_graph_set_sample_floor); m_lo < 0 restores the default."""
         _check(lib().tc_graph_set_sample_floor(self.handle, int(m_lo)), "tc_graph_set_sample_floor")
 
+    def set_partition(self, mode: str):
+        """Graph split by the degree partition of the later counts
+        (tc_graph_set_partition): "sampled" (default) or "original"."""
+        _check(lib().tc_graph_set_partition(self.handle, {"sampled": 0, "original": 1}[mode]),
+               "tc_graph_set_partition")
+
     def set_core_ranks(self, ranks: int):
         """Dense core of the later counts (tc_graph_set_core_ranks): < 0 chosen
         per count (the default), 0 none, else 8192 .. 65536 top ranks."""
@@ -303,11 +345,19 @@ class Graph:
     def count(self, p: float, seed: int) -> dict:
         return tc_count(self.handle, p, seed).as_dict()
 
-    def count_async(self, p: float, seed: int, out_addr: int) -> None:
-        tc_count_async(self.handle, p, seed, out_addr)
+    def count_async(self, p: float, seed: int, out_addr: int, stream=None) -> None:
+        tc_count_async(self.handle, p, seed, out_addr, stream)
 
     def sync(self):
         tc_graph_sync(self.handle)
+
+    def count_triples(self, p: float, seed: int, samples: int = 0, mode: str = "hybrid") -> dict:
+        """Triple sampling (tc_count_triples): mode "simple" or "hybrid";
+        samples = 0 draws m_p samples."""
+        r = tc_triple_result()
+        _check(lib().tc_count_triples(self.handle, p, seed & 0xFFFFFFFFFFFFFFFF, int(samples), _TRIPLE_MODES[mode],
+                                      ctypes.byref(r)), "tc_count_triples")
+        return r.as_dict()
 
     def export_sample(self, p: float, seed: int, pairs: bool = True):
         """(kept pairs in canonical order, heavy flags, sampled degrees); with

@@ -56,3 +56,18 @@ def test_rmat_oracle_sample_is_the_canonical_prefix(monkeypatch):
     v = np.maximum(draws[:1 << 14, 0], draws[:1 << 14, 1]).astype(np.uint64)
     keys = np.unique((u << np.uint64(32) | v)[u != v])
     assert np.array_equal(canon[:, 0].astype(np.uint64) << np.uint64(32) | canon[:, 1], keys)
+
+
+def test_default_workload_is_the_largest_graph():
+    """The default run (what the driver times) is R-MAT scale 26 with the
+    batched and served comparisons as extra keys."""
+    assert bench.DEFAULT_WORKLOAD == "rmat26"
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        args = bench.parse_args()
+    finally:
+        sys.argv = old
+    assert args.workload == "rmat26" and args.gpus == 1 and not args.no_extras
+    w = bench.WORKLOADS["rmat26"]
+    assert (w["scale"], w["edge_factor"], w["p_sweep"]) == (26, 16, [1.0, 0.05])

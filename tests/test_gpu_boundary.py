@@ -1,0 +1,158 @@
+"""C-ABI entry points around the single count: a count on the caller's
+stream (tc_count_async), one batched count over graphs that are already
+resident (tc_count_batch), and allocation failure (tc_set_allocator ->
+TC_ENOMEM, nothing left allocated).  Results are compared with tc_count and
+with the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("m", "m_sampled", "n_heavy", "t_light", "t_heavy", "estimate")
+
+
+def _tc():
+    from paper_1011_0468_gb300 import tc
+    return tc
+
+
+def test_count_async_on_a_callers_stream():
+    import torch
+    tc = _tc()
+    e = gen.chung_lu(30000, 300000, 2.1, 3000.0, 12)
+    own = torch.cuda.Stream()
+    other = torch.cuda.Stream()
+    ps = [(1.0, 1), (0.3, 5), (0.05, 9)]
+    buf = torch.zeros((len(ps), ctypes.sizeof(tc.tc_result)), dtype=torch.uint8, pin_memory=True)
+    with tc.Graph(e, 30000, stream=own) as g:
+        for j, (p, seed) in enumerate(ps):
+            g.count_async(p, seed, buf[j].data_ptr(), stream=other if j % 2 == 0 else None)
+        g.sync()  # covers the counts enqueued on the other stream
+        got = [tc.tc_result.from_address(buf[j].data_ptr()).as_dict() for j in range(len(ps))]
+        for (p, seed), r in zip(ps, got):
+            want = oracle.run(e, 30000, p, seed)
+            assert all(r[k] == want[k] for k in KEYS), (p, seed)
+            assert g.count(p, seed)["estimate"] == r["estimate"]
+        # a count on a stream the caller synchronises itself
+        out = torch.zeros(ctypes.sizeof(tc.tc_result), dtype=torch.uint8, pin_memory=True)
+        g.count_async(0.5, 3, out.data_ptr(), stream=other)
+        other.synchronize()
+        r = tc.tc_result.from_address(out.data_ptr()).as_dict()
+        want = oracle.run(e, 30000, 0.5, 3)
+        assert all(r[k] == want[k] for k in KEYS)
+
+
+def test_count_batch_over_resident_graphs():
+    tc = _tc()
+    graphs = [(gen.chung_lu(20000, 160000, 2.1, 2500.0, 3), 20000),
+              (gen.er(5000, 40000, 4), 5000),
+              (gen.complete(60), 60),
+              (gen.wheel(9), 10),
+              (gen.planted_core(60000, 1400, 0.85, 250000, 5), 60000),  # m >= 2^20: alone it uses the tensor cores
+              (np.zeros((0, 2), np.uint32), 7)]
+    objs = [tc.Graph(e, n) for e, n in graphs]
+    try:
+        # every graph once, the first two again with other (p, seed)
+        sel = list(range(len(objs))) + [0, 1, 4]
+        p = [1.0, 0.3, 1.0, 0.5, 1.0, 0.2, 0.1, 1.0, 0.6]
+        seed = [1, 2, 3, 4, 5, 6, 7, 8, 9]
+        res = tc.tc_count_batch([objs[i] for i in sel], p, seed)
+        for j, i in enumerate(sel):
+            single = objs[i].count(p[j], seed[j])
+            for k in KEYS:
+                assert res[k][j] == single[k], (j, i, k)
+            if i != 4:  # the planted core's oracle run takes a while; its single count is exact already
+                want = oracle.run(graphs[i][0], graphs[i][1], p[j], seed[j])
+                for k in KEYS:
+                    assert res[k][j] == want[k], (j, i, k)
+        with pytest.raises(tc.TCError) as ei:
+            tc.tc_count_batch([objs[0]], [1.5], [1])
+        assert ei.value.status == tc.TC_EINVAL
+    finally:
+        for o in objs:
+            o.close()
+
+
+def test_allocation_failure_returns_enomem_and_leaks_nothing():
+    """A caller's allocator that fails at its k-th call: graph creation
+    returns TC_ENOMEM and has given back every block it got, for every k."""
+    import torch
+    tc = _tc()
+    L = tc.lib()
+    live = {}
+    state = {"calls": 0, "fail_at": 0}
+
+    def _alloc(nbytes, stream, ctx):
+        state["calls"] += 1
+        if state["calls"] == state["fail_at"]:
+            return None
+        p = torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                               int(stream) if stream else None)
+        live[int(p)] = int(nbytes)
+        return p
+
+    def _free(ptr, stream, ctx):
+        live.pop(int(ptr))
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    hooks = (tc._ALLOC_T(_alloc), tc._FREE_T(_free))
+    e = gen.planted_core(60000, 1400, 0.85, 250000, 5)  # above 2^20 edges: heavy block buffers too
+    L.tc_set_allocator(ctypes.cast(hooks[0], ctypes.c_void_p), ctypes.cast(hooks[1], ctypes.c_void_p), None)
+    try:
+        with tc.Graph(e, 60000) as g:  # count the allocations of a successful creation
+            total = state["calls"]
+            want = g.count(1.0, 1)
+        assert total >= 10 and not live
+        failed = 0
+        for k in range(1, total + 1):
+            state["calls"], state["fail_at"] = 0, k
+            try:
+                g = tc.Graph(e, 60000)
+            except tc.TCError as ex:
+                assert ex.status == tc.TC_ENOMEM, k
+                failed += 1
+            else:  # the optional dense blocks are dropped when their memory is refused
+                got = g.count(1.0, 1)
+                g.close()
+                assert all(got[q] == want[q] for q in KEYS), k
+            assert not live, (k, live)
+        assert failed >= total // 2
+        state["fail_at"] = 0
+        with tc.Graph(e, 60000) as g:  # and the library still works
+            got = g.count(1.0, 1)
+        assert all(got[k] == want[k] for k in KEYS)
+        assert not live
+    finally:
+        L.tc_set_allocator(None, None, None)
+
+
+def test_partition_on_the_original_degrees():
+    """tc_graph_set_partition(TC_PARTITION_ORIGINAL) splits the whole
+    graph's vertices (deg^2 > m) and classifies the sampled triangles by
+    those flags, as the oracle's partition="original" does; the estimate is
+    the same as with the sampled partition."""
+    tc = _tc()
+    L = tc.lib()
+    cases = [(gen.chung_lu(20000, 200000, 2.1, 3000.0, 3), 20000),
+             (gen.planted_core(60000, 1400, 0.85, 250000, 5), 60000),  # dense heavy block on the tensor cores
+             (gen.wheel(4), 5), (gen.wheel(7), 8)]
+    for e, n in cases:
+        with tc.Graph(e, n) as g:
+            for p, seed in ((1.0, 1), (0.5, 2), (0.2, 3)):
+                assert L.tc_graph_set_partition(g.handle, 1) == tc.TC_OK
+                got = g.count(p, seed)
+                want = oracle.run(e, n, p, seed, partition="original")
+                assert all(got[k] == want[k] for k in KEYS), (n, p, seed)
+                kept, heavy, _ = g.export_sample(p, seed, pairs=False)
+                ref = oracle.run(e, n, p, seed, want_sample=True, partition="original")
+                assert np.array_equal(heavy, ref["heavy"])
+                assert L.tc_graph_set_partition(g.handle, 0) == tc.TC_OK
+                plain = g.count(p, seed)
+                assert plain["estimate"] == got["estimate"]
+                assert plain["t_light"] + plain["t_heavy"] == got["t_light"] + got["t_heavy"]
+            assert L.tc_graph_set_partition(g.handle, 2) == tc.TC_EINVAL
