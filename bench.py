@@ -127,11 +127,13 @@ def make_graph(out=None, count=None):
     return gen.cached("chung_lu", gen.chung_lu, w["n"], w["m"], w["gamma"], w["wmax"], w["graph_seed"])
 
 
-def recorded_traffic(workload, kernel):
+def recorded_traffic(workload, kernel, algorithmic_bytes=None):
     """DRAM bytes per launch of the roofline kernel on this workload from the
     committed ncu capture (profiles/traffic.json), or None when there is no
     record or a source it depends on has changed (sha1 of the listed files,
-    concatenated in order)."""
+    concatenated in order).  A record captured on a smaller case of the same
+    graph family (scale_by_algorithmic_bytes) gives its ratio of DRAM bytes
+    to algorithmic bytes times this launch's algorithmic_bytes."""
     import hashlib
     try:
         recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["records"]
@@ -141,6 +143,10 @@ def recorded_traffic(workload, kernel):
             src = b"".join(open(os.path.join(ROOT, f), "rb").read() for f in rec["sources"])
             if hashlib.sha1(src).hexdigest()[:12] != rec["sources_sha1_12"]:
                 return None
+            if rec.get("scale_by_algorithmic_bytes"):
+                if not algorithmic_bytes:
+                    return None
+                return float(rec["dram_bytes"]) / float(rec["algorithmic_bytes"]) * float(algorithmic_bytes)
             return float(rec["dram_bytes"])
     except Exception:
         pass
@@ -347,7 +353,7 @@ def our_arm(args):
     b_isect = 4.0 * (results[j1]["src_elems"] + results[j1]["nbr_elems"])
     achieved = b_isect / t_isect / 1e9 if t_isect > 0 else 0.0
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic = recorded_traffic(WORKLOAD["workload"], "k_probe_warp+k_probe_block")
+    traffic = recorded_traffic(WORKLOAD["workload"], "k_probe_warp+k_probe_block", b_isect)
     roofline = {"bound": "hbm", "kernel": "k_probe_warp+k_probe_block (p=1 count)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_src, "traffic": traffic,

@@ -235,6 +235,49 @@ tc_status tc_count_batch(tc_graph *const *graphs, const double *p, const uint64_
 tc_status tc_graph_sync(tc_graph *g);
 
 /*
+ * Choosing p (Section 3.3).  The hybrid's running time is a pass over the
+ * m p kept edges plus the triple samples, O((m p)^(3/2) log n / (eps^2 t
+ * p^3)); balancing the two gives
+ *     p = (m^(1/2) ln n / (t eps^2))^(2/5),
+ * clamped to at most 1.  t is a pilot estimate of the triangle count.
+ * Returns 1 when t <= 0 (no triangle seen: do not sparsify), -1 for
+ * eps <= 0 (or NaN), m == 0 or n < 2.  Host arithmetic only.
+ */
+double tc_suggest_p(uint64_t m, uint32_t n, double t, double eps);
+
+/*
+ * Several counts of one graph in one call (the p-sweep of the paper's
+ * remarks in Section 4): count i uses (p[i], seed[i]); they are enqueued
+ * back to back on the graph's stream and the call blocks once, at the end.
+ * out[i] (host memory) is exactly what tc_count(g, p[i], seed[i]) returns,
+ * except ms[].  Errors: TC_EINVAL (NULL pointers, k == 0, a p[i] outside
+ * (0, 1]), TC_ENOMEM (pinned staging), TC_ECUDA, TC_ETIMEOUT.
+ */
+tc_status tc_count_sweep(tc_graph *g, const double *p, const uint64_t *seed, uint32_t k, tc_result *out);
+
+/*
+ * Vary p until the estimate stabilises (Section 4, remarks): counts at
+ * p_i = min(1, p0 growth^i), i = 0, 1, ... up to p = 1 or max_counts of them
+ * (one tc_count_sweep, all with the same seed); the result is the first
+ * count i >= 1 whose estimate differs from count i - 1 by at most
+ * tol |estimate_i|, else the last one.  *p_used and *counts_used (may be
+ * NULL) receive its p and the number of counts run.  Errors: TC_EINVAL
+ * (p0 outside (0, 1], growth <= 1, tol < 0 or NaN, max_counts 0 or > 64),
+ * and those of tc_count_sweep.
+ */
+tc_status tc_count_adaptive(tc_graph *g, double p0, double growth, double tol, uint64_t seed, uint32_t max_counts,
+                            tc_result *out, double *p_used, uint32_t *counts_used);
+
+/*
+ * A pilot count at pilot_p, then the count at tc_suggest_p(m, n,
+ * pilot estimate, eps) (Section 3.3), both with seed.  *out is the second
+ * count's result (the pilot's when m == 0 or n < 2), *p_used (may be NULL)
+ * its p.  Errors: TC_EINVAL (NULL, pilot_p outside (0, 1], eps <= 0), and
+ * those of tc_count.
+ */
+tc_status tc_count_auto(tc_graph *g, double eps, double pilot_p, uint64_t seed, tc_result *out, double *p_used);
+
+/*
  * Test and inspection entry points (not on the hot path).  They run the
  * sampling and partition of tc_count for (p, seed) and copy intermediate
  * results to host memory:

@@ -885,6 +885,80 @@ tc_status tc_count_batch(tc_graph *const *graphs, const double *p, const uint64_
     return st;
 }
 
+double tc_suggest_p(uint64_t m, uint32_t n, double t, double eps)
+{
+    if (!(eps > 0.0) || m == 0 || n < 2) return -1.0;
+    if (!(t > 0.0)) return 1.0;
+    // balance p m against m^(3/2) ln n / (p^(3/2) t eps^2)
+    const double x = std::sqrt((double)m) * std::log((double)n) / (t * eps * eps);
+    const double p = std::pow(x, 0.4);
+    return p < 1.0 ? p : 1.0;
+}
+
+tc_status tc_count_sweep(tc_graph *g, const double *p, const uint64_t *seed, uint32_t k, tc_result *out)
+{
+    if (!g || !p || !seed || !out || k == 0) return TC_EINVAL;
+    for (uint32_t i = 0; i < k; ++i)
+        if (bad_p(p[i])) return TC_EINVAL;
+    NvtxRange whole("tc_count_sweep");
+    tc_result *stage = nullptr;
+    if (cudaMallocHost((void **)&stage, (size_t)k * sizeof(tc_result)) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ENOMEM;
+    }
+    tc_status st = TC_OK;
+    for (uint32_t i = 0; i < k && st == TC_OK; ++i) st = enqueue_count(g, p[i], seed[i], stage + i, false);
+    const tc_status sy = sync_graph(g);
+    if (st == TC_OK) st = sy;
+    if (st == TC_OK) std::copy(stage, stage + k, out);
+    cudaFreeHost(stage);
+    return st;
+}
+
+tc_status tc_count_adaptive(tc_graph *g, double p0, double growth, double tol, uint64_t seed, uint32_t max_counts,
+                            tc_result *out, double *p_used, uint32_t *counts_used)
+{
+    if (!g || !out || bad_p(p0) || !(growth > 1.0) || !(tol >= 0.0) || max_counts == 0 || max_counts > 64)
+        return TC_EINVAL;
+    std::vector<double> ps;
+    for (double q = p0; ps.size() < max_counts; q *= growth) {
+        ps.push_back(q < 1.0 ? q : 1.0);
+        if (q >= 1.0) break;
+    }
+    std::vector<uint64_t> seeds(ps.size(), seed);
+    std::vector<tc_result> res(ps.size());
+    const tc_status st = tc_count_sweep(g, ps.data(), seeds.data(), (uint32_t)ps.size(), res.data());
+    if (st != TC_OK) return st;
+    size_t pick = ps.size() - 1;
+    for (size_t i = 1; i < ps.size(); ++i) {
+        if (std::fabs(res[i].estimate - res[i - 1].estimate) <= tol * std::fabs(res[i].estimate)) {
+            pick = i;
+            break;
+        }
+    }
+    *out = res[pick];
+    if (p_used) *p_used = ps[pick];
+    if (counts_used) *counts_used = (uint32_t)ps.size();
+    return TC_OK;
+}
+
+tc_status tc_count_auto(tc_graph *g, double eps, double pilot_p, uint64_t seed, tc_result *out, double *p_used)
+{
+    if (!g || !out || bad_p(pilot_p) || !(eps > 0.0)) return TC_EINVAL;
+    tc_result pilot;
+    tc_status st = tc_count(g, pilot_p, seed, &pilot);
+    if (st != TC_OK) return st;
+    const double p = tc_suggest_p(g->m, g->n, pilot.estimate, eps);
+    if (p <= 0.0) {  // no edges or a single vertex: the pilot is the count
+        *out = pilot;
+        if (p_used) *p_used = pilot_p;
+        return TC_OK;
+    }
+    st = tc_count(g, p, seed, out);
+    if (st == TC_OK && p_used) *p_used = p;
+    return st;
+}
+
 tc_status tc_count_triples(tc_graph *g, double p, uint64_t seed, uint64_t samples, int mode, tc_triple_result *out)
 {
     if (!g || !out || bad_p(p) || (mode != TC_TRIPLES_SIMPLE && mode != TC_TRIPLES_HYBRID)) return TC_EINVAL;

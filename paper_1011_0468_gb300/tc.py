@@ -96,6 +96,13 @@ SIGNATURES = [
     ("tc_graph_export_edges", ctypes.c_int, [_vp, _u32p]),
     ("tc_count_triples", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                         ctypes.POINTER(tc_triple_result)]),
+    ("tc_suggest_p", ctypes.c_double, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double, ctypes.c_double]),
+    ("tc_count_sweep", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _u64p, ctypes.c_uint32, _vp]),
+    ("tc_count_adaptive", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                         ctypes.c_uint32, ctypes.POINTER(tc_result), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_uint32)]),
+    ("tc_count_auto", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                     ctypes.POINTER(tc_result), ctypes.POINTER(ctypes.c_double)]),
     ("tc_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tc_version", ctypes.c_int, []),
     ("tc_release_cached_memory", ctypes.c_int, []),
@@ -186,6 +193,12 @@ def tc_count_async(g: int, p: float, seed: int, out_addr: int, stream=None) -> N
     cudaStream_t to run the count on."""
     _check(lib().tc_count_async(g, p, seed & 0xFFFFFFFFFFFFFFFF, out_addr, _stream_handle(stream)),
            "tc_count_async")
+
+
+def tc_suggest_p(m: int, n: int, t: float, eps: float) -> float:
+    """Section 3.3's p = (m^(1/2) ln n / (t eps^2))^(2/5), at most 1; 1 when
+    t <= 0; -1 for bad arguments (host arithmetic in libtc)."""
+    return float(lib().tc_suggest_p(m, n, t, eps))
 
 
 def tc_count_batch(graphs, p, seed) -> np.ndarray:
@@ -350,6 +363,29 @@ class Graph:
 
     def sync(self):
         tc_graph_sync(self.handle)
+
+    def count_sweep(self, p, seed) -> np.ndarray:
+        """Counts at several (p, seed) in one call (tc_count_sweep)."""
+        pa = np.ascontiguousarray(np.atleast_1d(np.asarray(p, dtype=np.float64)))
+        sa = np.ascontiguousarray(np.broadcast_to(np.asarray(seed, dtype=np.uint64), pa.shape))
+        out = np.zeros(len(pa), dtype=RESULT_DTYPE)
+        _check(lib().tc_count_sweep(self.handle, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    sa.ctypes.data_as(_u64p), len(pa), out.ctypes.data), "tc_count_sweep")
+        return out
+
+    def count_adaptive(self, p0: float, growth: float, tol: float, seed: int, max_counts: int = 16):
+        """(result, p used, counts run) of tc_count_adaptive."""
+        r, pu, cu = tc_result(), ctypes.c_double(0), ctypes.c_uint32(0)
+        _check(lib().tc_count_adaptive(self.handle, p0, growth, tol, seed & 0xFFFFFFFFFFFFFFFF, max_counts,
+                                       ctypes.byref(r), ctypes.byref(pu), ctypes.byref(cu)), "tc_count_adaptive")
+        return r.as_dict(), pu.value, cu.value
+
+    def count_auto(self, eps: float, pilot_p: float, seed: int):
+        """(result, p used) of tc_count_auto: pilot count, suggested p, count."""
+        r, pu = tc_result(), ctypes.c_double(0)
+        _check(lib().tc_count_auto(self.handle, eps, pilot_p, seed & 0xFFFFFFFFFFFFFFFF, ctypes.byref(r),
+                                   ctypes.byref(pu)), "tc_count_auto")
+        return r.as_dict(), pu.value
 
     def count_triples(self, p: float, seed: int, samples: int = 0, mode: str = "hybrid") -> dict:
         """Triple sampling (tc_count_triples): mode "simple" or "hybrid";

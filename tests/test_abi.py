@@ -97,3 +97,17 @@ def test_server_argument_errors_without_device(lib):
     assert lib.tc_server_poll(None, 1, ctypes.byref(info)) == tc.TC_EINVAL
     assert lib.tc_server_wait(None, 1, 0, ctypes.byref(info)) == tc.TC_EINVAL
     lib.tc_server_destroy(None)  # NULL-safe
+
+
+def test_suggest_p_host_arithmetic_matches_the_oracle(lib):
+    """tc_suggest_p (host code of libtc, no device) against the oracle's
+    statement of Section 3.3's p, which the oracle tests pin to the balance
+    equation."""
+    import oracle
+    from paper_1011_0468_gb300 import tc
+    for m, n, t, eps in [(10 ** 6, 10 ** 5, 1e7, 0.1), (48709772, 5284457, 3.1e8, 0.05),
+                         (1051928416, 1 << 26, 4.9e10, 0.01), (20000, 2000, 1300.0, 0.2),
+                         (1000, 100, 1e-3, 0.1), (1000, 100, 0.0, 0.1)]:
+        assert tc.tc_suggest_p(m, n, t, eps) == oracle.suggest_p(m, n, t, eps)
+    for bad in ((0, 100, 10.0, 0.1), (1000, 1, 10.0, 0.1), (1000, 100, 10.0, 0.0), (1000, 100, 10.0, float("nan"))):
+        assert tc.tc_suggest_p(*bad) == -1.0

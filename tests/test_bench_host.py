@@ -71,3 +71,15 @@ def test_default_workload_is_the_largest_graph():
     assert args.workload == "rmat26" and args.gpus == 1 and not args.no_extras
     w = bench.WORKLOADS["rmat26"]
     assert (w["scale"], w["edge_factor"], w["p_sweep"]) == (26, 16, [1.0, 0.05])
+
+
+def test_traffic_record_scaled_from_a_smaller_case(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "a.cu").write_text("kernel source")
+    sha = hashlib.sha1(b"kernel source").hexdigest()[:12]
+    rec = {"records": [{"kernel": "k_x", "workload": "big", "sources": ["a.cu"], "sources_sha1_12": sha,
+                        "dram_bytes": 80, "algorithmic_bytes": 100, "scale_by_algorithmic_bytes": True}]}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_traffic("big", "k_x", 1000.0) == 800.0
+    assert bench.recorded_traffic("big", "k_x") is None

@@ -156,3 +156,36 @@ def test_partition_on_the_original_degrees():
                 assert plain["estimate"] == got["estimate"]
                 assert plain["t_light"] + plain["t_heavy"] == got["t_light"] + got["t_heavy"]
             assert L.tc_graph_set_partition(g.handle, 2) == tc.TC_EINVAL
+
+
+def test_sweep_adaptive_and_auto_counts():
+    """tc_count_sweep gives each (p, seed) the oracle's result; the adaptive
+    count picks the first p of the ladder p0 growth^i whose estimate is
+    within tol of the previous one; the auto count runs the pilot and then
+    the count at Section 3.3's p."""
+    tc = _tc()
+    e, n = gen.chung_lu(40000, 400000, 2.1, 4000.0, 8), 40000
+    with tc.Graph(e, n) as g:
+        ps = [0.02, 0.05, 0.1, 0.3, 1.0]
+        res = g.count_sweep(ps, [3, 4, 5, 6, 7])
+        for j, (p, seed) in enumerate(zip(ps, [3, 4, 5, 6, 7])):
+            want = oracle.run(e, n, p, seed)
+            assert all(res[k][j] == want[k] for k in KEYS), p
+        for p0, growth, tol in ((0.01, 2.0, 0.05), (0.05, 1.5, 0.01), (0.2, 3.0, 0.0)):
+            got, p_used, runs = g.count_adaptive(p0, growth, tol, 9)
+            ladder, q = [], p0
+            while True:
+                ladder.append(min(q, 1.0))
+                if q >= 1.0 or len(ladder) == 16:
+                    break
+                q *= growth
+            ests = [oracle.run(e, n, q, 9)["estimate"] for q in ladder]
+            pick = next((i for i in range(1, len(ladder)) if abs(ests[i] - ests[i - 1]) <= tol * abs(ests[i])),
+                        len(ladder) - 1)
+            assert runs == len(ladder) and p_used == ladder[pick]
+            assert got["estimate"] == ests[pick]
+        got, p_used = g.count_auto(0.1, 0.05, 12)
+        pilot = oracle.run(e, n, 0.05, 12)
+        assert p_used == oracle.suggest_p(len(e), n, pilot["estimate"], 0.1)
+        want = oracle.run(e, n, p_used, 12)
+        assert all(got[k] == want[k] for k in KEYS)
