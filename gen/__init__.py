@@ -171,6 +171,22 @@ def cached(kind: str, fn, *args) -> np.ndarray:
     return out
 
 
+def adjacency_stream(edges, n: int):
+    """The symmetric adjacency of a canonical edge list in the stream layout
+    of Section 5.2 (the edges of each vertex given together, in order):
+    (off, adj) with off[n + 1] uint64 offsets and adj[2 m] uint32
+    neighbours, every list sorted by id."""
+    e = np.asarray(edges, dtype=np.uint32).reshape(-1, 2)
+    src = np.concatenate([e[:, 0], e[:, 1]]).astype(np.uint64)
+    dst = np.concatenate([e[:, 1], e[:, 0]]).astype(np.uint64)
+    order = np.argsort((src << np.uint64(32)) | dst, kind="stable")
+    adj = dst[order].astype(np.uint32)
+    counts = np.bincount(src.astype(np.int64), minlength=n)[:n] if len(src) else np.zeros(n, dtype=np.int64)
+    off = np.zeros(n + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(counts, dtype=np.uint64)
+    return off, adj
+
+
 # ---------------------------------------------------------------- closed forms
 
 def canonical(pairs) -> np.ndarray:

@@ -48,6 +48,13 @@ class OracleResult(ctypes.Structure):
                 ("t_heavy", ctypes.c_uint64), ("estimate", ctypes.c_double)]
 
 
+class StreamResult(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_uint64), ("n", ctypes.c_uint32), ("n_heavy", ctypes.c_uint32),
+                ("candidates", ctypes.c_uint64), ("sampled_entries", ctypes.c_uint64), ("universe", ctypes.c_uint64),
+                ("samples", ctypes.c_uint64), ("closed_wedge", ctypes.c_uint64), ("closed_pair", ctypes.c_uint64),
+                ("estimate", ctypes.c_double)]
+
+
 class TripleResult(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint64), ("m_sampled", ctypes.c_uint64), ("n", ctypes.c_uint32),
                 ("n_heavy", ctypes.c_uint32), ("universe", ctypes.c_uint64), ("samples", ctypes.c_uint64),
@@ -105,6 +112,9 @@ def _load():
         lib.oracle_triple_enumerate.argtypes = [_u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                                 ctypes.c_uint64, _u32p, _u32p, _u32p, _u8p]
         lib.oracle_triple_enumerate.restype = ctypes.c_int64
+        lib.oracle_stream_triples.argtypes = [_u64p, _u32p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                              ctypes.c_double, ctypes.POINTER(StreamResult)]
+        lib.oracle_stream_triples.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -302,3 +312,24 @@ def triple_enumerate(canon, n: int, mode: str = "hybrid"):
         if r != size:
             raise MemoryError("oracle_triple_enumerate")
     return u[:size], v[:size], w[:size], c[:size]
+
+
+def stream_triples(off, adj, n: int, seed: int, samples: int = 0, c: float = 3.0) -> dict:
+    """Section 5.2, three passes over a symmetric adjacency stream (off[n+1]
+    uint64, adj[2m] uint32, lists sorted): heavy candidates from sampled
+    entries, then s uniform triples of U (wedges of the other vertices,
+    pairs of an edge and a heavy vertex), then the check of their third
+    edges.  Returns m, n, n_heavy, candidates, sampled_entries, universe,
+    samples, closed_wedge, closed_pair, estimate."""
+    o = np.ascontiguousarray(off, dtype=np.uint64)
+    a = np.ascontiguousarray(adj, dtype=np.uint32)
+    if len(o) != n + 1 or (len(a) and int(o[-1]) != len(a)):
+        raise ValueError("off must hold n + 1 offsets ending at len(adj)")
+    if len(a) == 0:
+        a = np.zeros(1, dtype=np.uint32)
+    res = StreamResult()
+    rc = _load().oracle_stream_triples(o.ctypes.data_as(_u64p), a.ctypes.data_as(_u32p), n,
+                                       seed & 0xFFFFFFFFFFFFFFFF, int(samples), float(c), ctypes.byref(res))
+    if rc:
+        raise MemoryError("oracle_stream_triples")
+    return {k: getattr(res, k) for k, _ in StreamResult._fields_}

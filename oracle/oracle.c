@@ -539,3 +539,208 @@ done:
     free(path);
     return rc;
 }
+
+/* ------------------------------------------------------- semi-streaming */
+
+typedef struct {
+    uint64_t m;
+    uint32_t n;
+    uint32_t n_heavy;      /* candidates with deg^2 > m */
+    uint64_t candidates;   /* distinct endpoints of the sampled entries */
+    uint64_t sampled_entries;
+    uint64_t universe;     /* |U| */
+    uint64_t samples;      /* s */
+    uint64_t closed_wedge; /* sampled wedges that are triangles */
+    uint64_t closed_pair;  /* sampled (edge, heavy vertex) pairs that are triangles */
+    double estimate;
+} oracle_stream_result;
+
+static int cmp_u64_key(const void *a, const void *b) { return cmp_u64(a, b); }
+
+/*
+ * Section 5.2: triangle counting over an adjacency-list stream in three
+ * passes (the edges of each vertex given together, in order).  The stream
+ * is the symmetric adjacency of a simple graph: off[n + 1], adj[2 m], every
+ * list sorted by id.
+ *   Pass 1 (heavy vertices): stream entry j (0 <= j < 2 m) is sampled iff
+ *     (splitmix64(j ^ splitmix64(seed + 1)) >> 11) < floor(q 2^53),
+ *     q = min(1, c m^(1/2) ln n / (2 m)), about c m^(1/2) ln n entries; both
+ *     endpoints of a sampled entry are candidates, and the candidates with
+ *     deg^2 > m form H (a vertex of degree > m^(1/2) has 2 deg of the 2 m
+ *     entries, so it is missed with probability about n^-c).
+ *   U: the wedges of the vertices outside H (C(d, 2) each, in vertex order,
+ *     wedge b (b - 1) / 2 + a of N(u)), then the pairs (edge e, H[i]) of
+ *     every edge (the entries u < v in stream order) and every vertex of H,
+ *     index |U_L| + e |H| + i.  A wedge closes iff its third edge exists, a
+ *     pair iff H[i] is neither endpoint and joins both.  Every triangle is
+ *     in U once per corner: three times.
+ *   Pass 2 (queries): sample i (0 <= i < s) is U's triple of index
+ *     floor(h_i |U| / 2^64), h_i = splitmix64(i ^ splitmix64(~seed)); its
+ *     list entries are read from the stream and its third edges become
+ *     queries.
+ *   Pass 3 (checks): the queries are sorted and merged against the stream's
+ *     edges in one pass (the offline check of Section 4.2).
+ * estimate = |U| (c_w + c_p) / (3 s), c_w and c_p the closed wedges and
+ * pairs among the samples.  s = 0 draws m samples.  Returns 0, -2 when
+ * memory runs out.
+ */
+int oracle_stream_triples(const uint64_t *off, const uint32_t *adj, uint32_t n, uint64_t seed, uint64_t samples,
+                          double c, oracle_stream_result *res)
+{
+    memset(res, 0, sizeof(*res));
+    const uint64_t len = off[n], m = len / 2;
+    res->m = m;
+    res->n = n;
+    uint8_t *cand = (uint8_t *)calloc((size_t)n ? n : 1, 1);
+    uint32_t *hlist = (uint32_t *)malloc(((size_t)n ? n : 1) * sizeof(uint32_t));
+    uint64_t *wpre = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint64_t *uppre = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    int rc = 0;
+    uint64_t *qs = NULL;
+    uint8_t *found = NULL;
+    uint32_t *sv = NULL, *sw = NULL, *sh = NULL;
+    uint8_t *stype = NULL;
+    if (!cand || !hlist || !wpre || !uppre) { rc = -2; goto done; }
+
+    /* pass 1: candidates from the sampled entries, H = those of degree^2 > m */
+    double q = 0.0;
+    if (m > 0 && n > 1) {
+        q = c * sqrt((double)m) * log((double)n) / (2.0 * (double)m);
+        if (q > 1.0) q = 1.0;
+    }
+    uint64_t thr = (uint64_t)(q * 9007199254740992.0);
+    uint64_t hmix = oracle_splitmix64(seed + 1);
+    for (uint32_t u = 0; u < n; ++u) {
+        for (uint64_t j = off[u]; j < off[u + 1]; ++j) {
+            if ((oracle_splitmix64(j ^ hmix) >> 11) < thr) {
+                res->sampled_entries++;
+                cand[u] = 1;
+                cand[adj[j]] = 1;
+            }
+        }
+    }
+    uint32_t h = 0;
+    for (uint32_t u = 0; u < n; ++u) {
+        uint64_t d = off[u + 1] - off[u];
+        res->candidates += cand[u];
+        if (cand[u] && d * d > m) hlist[h++] = u;
+    }
+    res->n_heavy = h;
+
+    /* U: wedge counts of the vertices outside H, edges (u < v entries) */
+    uint32_t hi = 0;
+    wpre[0] = uppre[0] = 0;
+    for (uint32_t u = 0; u < n; ++u) {
+        uint64_t d = off[u + 1] - off[u], up = 0;
+        int heavy = hi < h && hlist[hi] == u;
+        hi += heavy;
+        for (uint64_t j = off[u]; j < off[u + 1]; ++j) up += adj[j] > u;
+        wpre[u + 1] = wpre[u] + (heavy ? 0 : d * (d - (d > 0)) / 2);
+        uppre[u + 1] = uppre[u] + up;
+    }
+    uint64_t UL = wpre[n];
+    res->universe = UL + uppre[n] * h;
+    res->samples = samples ? samples : m;
+    uint64_t s = res->samples;
+    if (res->universe == 0 || s == 0) goto rescale;
+
+    /* pass 2: the samples' list entries, and their third edges as queries */
+    stype = (uint8_t *)malloc(s);
+    sv = (uint32_t *)malloc(s * sizeof(uint32_t));
+    sw = (uint32_t *)malloc(s * sizeof(uint32_t));
+    sh = (uint32_t *)malloc(s * sizeof(uint32_t));
+    qs = (uint64_t *)malloc(2 * s * sizeof(uint64_t));
+    if (!stype || !sv || !sw || !sh || !qs) { rc = -2; goto done; }
+    uint64_t tmix = oracle_splitmix64(~seed), nq = 0;
+    for (uint64_t i = 0; i < s; ++i) {
+        uint64_t r = mulhi64(oracle_splitmix64(i ^ tmix), res->universe);
+        if (r < UL) {
+            uint32_t lo = 0, hi2 = n;  /* wpre[u] <= r < wpre[u + 1] */
+            while (hi2 - lo > 1) {
+                uint32_t mid = lo + (hi2 - lo) / 2;
+                if (wpre[mid] <= r) lo = mid; else hi2 = mid;
+            }
+            uint32_t u = lo;
+            uint64_t k = r - wpre[u], d = off[u + 1] - off[u];
+            uint64_t b = 1, bhi = d;
+            while (bhi - b > 1) {
+                uint64_t mid = b + (bhi - b) / 2;
+                if (mid * (mid - 1) / 2 <= k) b = mid; else bhi = mid;
+            }
+            uint64_t a = k - b * (b - 1) / 2;
+            uint32_t v = adj[off[u] + a], w = adj[off[u] + b];
+            stype[i] = 0;
+            sv[i] = v;
+            sw[i] = w;
+            qs[nq++] = ((uint64_t)(v < w ? v : w) << 32) | (v < w ? w : v);
+        } else {
+            uint64_t k = r - UL, e = k / h;
+            uint32_t hv = hlist[k % h];
+            uint32_t lo = 0, hi2 = n;  /* uppre[x] <= e < uppre[x + 1] */
+            while (hi2 - lo > 1) {
+                uint32_t mid = lo + (hi2 - lo) / 2;
+                if (uppre[mid] <= e) lo = mid; else hi2 = mid;
+            }
+            uint32_t x = lo;
+            uint64_t kk = e - uppre[x];
+            uint64_t d = off[x + 1] - off[x], up = uppre[x + 1] - uppre[x];
+            uint32_t y = adj[off[x] + (d - up) + kk];  /* the entries above x are the list's tail */
+            stype[i] = 1;
+            sv[i] = x;
+            sw[i] = y;
+            sh[i] = hv;
+            if (hv != x && hv != y) {
+                qs[nq++] = ((uint64_t)(hv < x ? hv : x) << 32) | (hv < x ? x : hv);
+                qs[nq++] = ((uint64_t)(hv < y ? hv : y) << 32) | (hv < y ? y : hv);
+            }
+        }
+    }
+
+    /* pass 3: sort the distinct queries, one merge pass over the edges */
+    qsort(qs, nq, sizeof(uint64_t), cmp_u64_key);
+    uint64_t nd = 0;
+    for (uint64_t i = 0; i < nq; ++i)
+        if (i == 0 || qs[i] != qs[i - 1]) qs[nd++] = qs[i];
+    found = (uint8_t *)calloc(nd ? nd : 1, 1);
+    if (!found) { rc = -2; goto done; }
+    uint64_t qi = 0;
+    for (uint32_t u = 0; u < n && qi < nd; ++u) {
+        for (uint64_t j = off[u]; j < off[u + 1] && qi < nd; ++j) {
+            if (adj[j] <= u) continue;
+            uint64_t key = ((uint64_t)u << 32) | adj[j];
+            while (qi < nd && qs[qi] < key) ++qi;
+            if (qi < nd && qs[qi] == key) found[qi] = 1;
+        }
+    }
+    for (uint64_t i = 0; i < s; ++i) {
+        if (stype[i] == 0) {
+            uint32_t v = sv[i], w = sw[i];
+            uint64_t key = ((uint64_t)(v < w ? v : w) << 32) | (v < w ? w : v);
+            uint64_t *p = (uint64_t *)bsearch(&key, qs, nd, sizeof(uint64_t), cmp_u64_key);
+            res->closed_wedge += found[p - qs];
+        } else {
+            uint32_t x = sv[i], y = sw[i], hv = sh[i];
+            if (hv == x || hv == y) continue;
+            uint64_t k1 = ((uint64_t)(hv < x ? hv : x) << 32) | (hv < x ? x : hv);
+            uint64_t k2 = ((uint64_t)(hv < y ? hv : y) << 32) | (hv < y ? y : hv);
+            uint64_t *p1 = (uint64_t *)bsearch(&k1, qs, nd, sizeof(uint64_t), cmp_u64_key);
+            uint64_t *p2 = (uint64_t *)bsearch(&k2, qs, nd, sizeof(uint64_t), cmp_u64_key);
+            res->closed_pair += found[p1 - qs] && found[p2 - qs];
+        }
+    }
+rescale:
+    if (res->universe && s)
+        res->estimate = ((double)res->universe * (double)(res->closed_wedge + res->closed_pair)) / (3.0 * (double)s);
+done:
+    free(cand);
+    free(hlist);
+    free(wpre);
+    free(uppre);
+    free(qs);
+    free(found);
+    free(sv);
+    free(sw);
+    free(sh);
+    free(stype);
+    return rc;
+}
