@@ -179,6 +179,33 @@ tc_status tc_graph_set_partition(tc_graph *g, int mode);
    a core until a size that fits is set); TC_ECUDA. */
 tc_status tc_graph_set_core_ranks(tc_graph *g, int64_t ranks);
 
+/* Schedule of the intersection kernels of the light class (Section 3.2's
+   wedge closures).  Every oriented pair is resolved by its owner, the
+   endpoint with the longer out-list (see tc_result); owners are bucketed by
+   out-degree d+ into one warp per owner (d+ <= warp_max), a 128-thread block
+   per owner (warp_max < d+ <= 1024) and a 1024-thread block per owner
+   (d+ > 1024), and an owner's partners are cut into work items.
+     warp_max            32 .. 256
+     seg_w, seg_b, seg_l most partners per item of the three kernels: powers
+                         of two in [64, 1024], [256, 512], [256, 4096]
+     work_w, work_b, work_l  an item of an owner with out-degree d holds the
+                         largest power of two <= seg partners whose product
+                         with d stays <= work (at least 64 or 256 partners);
+                         each >= 4096
+     run_b               items a mid-owner block takes per grab, 1 .. 8
+                         (consecutive items of one owner share its hash set)
+   Results never depend on the schedule; only the time does.
+   tc_graph_set_schedule(g, NULL) restores the default.  TC_EINVAL for a
+   NULL graph or a value out of range. */
+typedef struct {
+    uint32_t warp_max;
+    uint32_t seg_w, seg_b, seg_l;
+    uint32_t work_w, work_b, work_l;
+    uint32_t run_b;
+} tc_schedule;
+tc_status tc_graph_set_schedule(tc_graph *g, const tc_schedule *s);
+tc_status tc_graph_get_schedule(const tc_graph *g, tc_schedule *out);
+
 /* After tc_graph_sync: copy the phase times (8 floats per count, layout of
    tc_result.ms) of the counts completed since the last drain, oldest first,
    at most max_counts of them (older ones beyond the ring are lost).  Returns
@@ -494,6 +521,58 @@ typedef struct {
     float ms;
 } tc_triple_result;
 tc_status tc_count_triples(tc_graph *g, double p, uint64_t seed, uint64_t samples, int mode, tc_triple_result *out);
+
+/*
+ * Semi-streaming count (Section 5.2) for graphs whose edges stay in host
+ * memory: three passes over an adjacency-list stream, with only vertex
+ * arrays, the samples and a query table on the device.
+ *   offsets, adj  host memory: the symmetric adjacency of a simple graph,
+ *                 offsets[n + 1] (offsets[0] = 0) and adj[offsets[n]]; the
+ *                 neighbours of u are adj[offsets[u] .. offsets[u + 1]),
+ *                 sorted by id, and every edge appears in both endpoints'
+ *                 lists (m = offsets[n] / 2).  Pinned memory that is mapped
+ *                 into the device is read in place; other host memory is
+ *                 copied through the device in chunks of chunk_entries
+ *                 (0: 2^26) entries, three times.
+ *   Pass 1 finds the heavy vertices as the paper does: stream entry j is
+ *   sampled iff (splitmix64(j ^ splitmix64(seed + 1)) >> 11) <
+ *   floor(q 2^53), q = min(1, heavy_factor m^(1/2) ln n / (2 m)), both ends
+ *   of a sampled entry are candidates, and H = the candidates with
+ *   deg^2 > m (a vertex of degree above m^(1/2) is missed with probability
+ *   about n^-heavy_factor; one that is missed is simply treated as light).
+ *   U holds the wedges of the vertices outside H (C(d, 2) each, in vertex
+ *   order, wedge b (b - 1) / 2 + a of the sorted list) and then the pairs
+ *   (edge e, H[i]) of every edge (the entries u < v in stream order) with
+ *   every vertex of H, index |U_L| + e |H| + i; every triangle is in U three
+ *   times.  Sample i is U's triple floor(h_i |U| / 2^64), h_i =
+ *   splitmix64(i ^ splitmix64(~seed)); pass 2 reads the samples' list
+ *   entries and puts their third edges in a device hash table, pass 3 marks
+ *   the queries that are edges of the stream.
+ *   estimate = |U| (closed_wedge + closed_pair) / (3 s), an unbiased
+ *   estimate of t (given H).
+ *   samples       s (0: m), at most 2^30.
+ * Blocks; device memory is allocated and freed by the call (about 40 n +
+ * 70 s bytes, plus two chunk buffers when the stream is copied).
+ * Errors: TC_EINVAL (NULL pointers with data, offsets not starting at 0 or
+ * decreasing, an odd or too large offsets[n] (2^33 or more entries), a list
+ * that is not sorted, has a self-loop or an id >= n, a stream that is not
+ * symmetric, s > 2^30, heavy_factor <= 0), TC_ENOMEM, TC_ECUDA.
+ */
+typedef struct {
+    uint64_t m;
+    uint32_t n, n_heavy;      /* n_heavy: |H| */
+    uint64_t candidates;      /* distinct ends of the sampled entries */
+    uint64_t sampled_entries; /* stream entries sampled in pass 1 */
+    uint64_t universe;        /* |U| */
+    uint64_t samples;         /* s */
+    uint64_t closed_wedge, closed_pair;
+    double estimate;
+    uint64_t bytes_streamed;  /* adjacency bytes read over the three passes */
+    uint32_t passes;
+    float ms;
+} tc_stream_result;
+tc_status tc_stream_count(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t seed, uint64_t samples,
+                          double heavy_factor, uint64_t chunk_entries, void *cuda_stream, tc_stream_result *out);
 
 /* Static description of a status code. */
 const char *tc_status_str(tc_status s);

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtc.so")
 SOURCES = ["prims.cu", "csr.cu", "count.cu", "isect.cu", "heavy.cu", "batch.cu", "server.cu", "api.cu", "noalloc.cu",
-           "triples.cu"]
+           "triples.cu", "stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

@@ -136,7 +136,7 @@ struct tc_graph {
     uint32_t *frow = nullptr;   // [n + 1] row offsets of the full graph in rel (static)
     uint32_t *inend = nullptr;  // [n] in-list ends
     uint2 *inlist = nullptr;    // [m] in-list entries
-    uint32_t *olist = nullptr;  // [m] out-lists
+    uint2 *olist = nullptr;     // [m] out-lists
     uint32_t *ocnt = nullptr;   // [n] out-list lengths
     uint32_t *colp = nullptr;   // [colp_capacity(n, m)] rows padded to 16 bytes
     uint32_t *ptrp = nullptr;   // [n + 2] padded row pointers
@@ -163,6 +163,7 @@ struct tc_graph {
     int64_t sample_floor = -1;  // lower bound on m_p for the degree candidates (< 0: the default)
     cudaEvent_t join_in = nullptr, join_out = nullptr;  // order a count on a caller's stream with the graph's
     int partition = TC_PARTITION_SAMPLED;  // which graph the degree partition splits
+    IsectConfig cfg;            // schedule of the intersection kernels
     TripleBuffers tri;          // triple sampling (built by the first tc_count_triples)
     bool tri_ready = false;
     std::vector<void *> allocs;
@@ -260,6 +261,7 @@ CountBuffers buffers_of(tc_graph *g)
     b.items = g->items;
     b.items_cap = g->items_cap;
     b.st = g->st;
+    b.cfg = g->cfg;
     if (g->partition == TC_PARTITION_ORIGINAL) {
         b.frow = g->frow;
         b.m_orig = g->m;
@@ -591,7 +593,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     g->inptr = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
     g->inend = (uint32_t *)g->alloc((uint64_t)n * 4);
     g->frow = (uint32_t *)g->alloc(((uint64_t)n + 1) * 4);
-    g->olist = (uint32_t *)g->alloc(m1 * 4);
+    g->olist = (uint2 *)g->alloc(m1 * 8);
     g->ocnt = (uint32_t *)g->alloc((uint64_t)n * 4);
     g->colp = (uint32_t *)g->alloc(colp_capacity(n, m) * 4);
     g->ptrp = (uint32_t *)g->alloc(((uint64_t)n + 2) * 4);
@@ -697,6 +699,39 @@ tc_status tc_graph_set_sample_floor(tc_graph *g, int64_t m_lo)
 {
     if (!g) return TC_EINVAL;
     g->sample_floor = m_lo < 0 ? -1 : m_lo;
+    return TC_OK;
+}
+
+tc_status tc_graph_set_schedule(tc_graph *g, const tc_schedule *s)
+{
+    if (!g) return TC_EINVAL;
+    if (!s) {
+        g->cfg = IsectConfig{};
+        return TC_OK;
+    }
+    auto pow2_in = [](uint32_t v, uint32_t lo, uint32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; };
+    if (s->warp_max < 32 || s->warp_max > 256 || !pow2_in(s->seg_w, 64, 1024) || !pow2_in(s->seg_b, 256, 512) ||
+        !pow2_in(s->seg_l, 256, 4096) || s->work_w < 4096 || s->work_b < 4096 || s->work_l < 4096 || s->run_b < 1 ||
+        s->run_b > 8)
+        return TC_EINVAL;
+    IsectConfig c;
+    c.warp_max = s->warp_max;
+    c.seg_w = s->seg_w;
+    c.seg_b = s->seg_b;
+    c.seg_l = s->seg_l;
+    c.work_w = s->work_w;
+    c.work_b = s->work_b;
+    c.work_l = s->work_l;
+    c.run_b = s->run_b;
+    g->cfg = c;
+    return TC_OK;
+}
+
+tc_status tc_graph_get_schedule(const tc_graph *g, tc_schedule *out)
+{
+    if (!g || !out) return TC_EINVAL;
+    const IsectConfig &c = g->cfg;
+    *out = tc_schedule{c.warp_max, c.seg_w, c.seg_b, c.seg_l, c.work_w, c.work_b, c.work_l, c.run_b};
     return TC_OK;
 }
 
@@ -1031,6 +1066,36 @@ tc_status tc_count_triples(tc_graph *g, double p, uint64_t seed, uint64_t sample
     }
     host.ms = ms;
     *out = host;
+    return TC_OK;
+}
+
+tc_status tc_stream_count(const uint64_t *offsets, const uint32_t *adj, uint32_t n, uint64_t seed, uint64_t samples,
+                          double heavy_factor, uint64_t chunk_entries, void *cuda_stream, tc_stream_result *out)
+{
+    if (!offsets || !out || n == 0 || n == 0xffffffffu || !(heavy_factor > 0.0)) return TC_EINVAL;
+    if (offsets[0] != 0) return TC_EINVAL;
+    for (uint32_t u = 0; u < n; ++u)
+        if (offsets[u + 1] < offsets[u]) return TC_EINVAL;
+    const uint64_t len = offsets[n];
+    if ((len & 1) || len >= (1ull << 33) || (len > 0 && !adj)) return TC_EINVAL;
+    NvtxRange whole("tc_stream_count");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    if (timed) cudaEventRecord(e0, s);
+    tc_stream_result r;
+    const tc_status st = stream_count(offsets, adj, n, seed, samples, heavy_factor, chunk_entries, s, &r);
+    float ms = 0.0f;
+    if (timed) {
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGetLastError();
+    if (st != TC_OK) return st;
+    r.ms = ms;
+    *out = r;
     return TC_OK;
 }
 

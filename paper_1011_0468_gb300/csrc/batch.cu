@@ -118,7 +118,7 @@ bool union_scratch_alloc(UnionScratch &u, uint64_t m_cap, uint32_t n_cap, uint32
     u.rel = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
     u.orig = (uint64_t *)dev_alloc_track(allocs, bytes, m1 * 8);
     u.inlist = (uint2 *)dev_alloc_track(allocs, bytes, m1 * 8);
-    u.olist = (uint32_t *)dev_alloc_track(allocs, bytes, m1 * 4);
+    u.olist = (uint2 *)dev_alloc_track(allocs, bytes, m1 * 8);
     u.ocnt = (uint32_t *)dev_alloc_track(allocs, bytes, (uint64_t)n_cap * 4);
     u.keepw = (uint32_t *)dev_alloc_track(allocs, bytes, (m1 + 31) / 32 * 4);
     u.tile_cnt = (uint32_t *)dev_alloc_track(allocs, bytes, (ceil_div(m1, RX_TILE) + 1) * 4);

@@ -776,8 +776,8 @@ __global__ void k_cursors(const uint32_t *__restrict__ P, uint32_t n, int hbits,
 struct ScatterArgs {
     const uint64_t *rel;
     const uint32_t *padoff, *rowptr, *dplus;
-    uint32_t *colp, *cursor, *olist, *ocnt;
-    uint2 *inlist;
+    uint32_t *colp, *cursor, *ocnt;
+    uint2 *inlist, *olist;
     int hbits;
     // heavy flags; pairs left to the dense blocks: light_lim when the heavy
     // block runs (else lim = EMPTY), the core's base when it runs
@@ -789,6 +789,7 @@ __device__ __forceinline__ void scatter_edge(const ScatterArgs &a, bool live, ui
 {
     uint32_t u = 0, v = 0;
     bool out = false;
+    uint2 ev = make_uint2(0, 0);
     if (live) {
         const uint64_t r = ld_stream_u64(a.rel + i);
         u = (uint32_t)(r >> 32);
@@ -803,8 +804,10 @@ __device__ __forceinline__ void scatter_edge(const ScatterArgs &a, bool live, ui
                 const uint32_t q = atomicAdd(a.cursor + hot_index(v, a.hbits), 1u);
                 const uint32_t after = __ldg(a.rowptr + u + 1) - k - 1;
                 a.inlist[q] = make_uint2(pos, after | ((uint32_t)__ldg(a.heavy + u) << 31));
-            } else {
-                out = dv >= 1;
+            } else if (dv >= 1) {  // entry: v's padded row, d+(v) | v's flag << 31 (if u is heavy)
+                out = true;
+                ev = make_uint2(__ldg(a.rowptr + v) + __ldg(a.padoff + v),
+                                dv | (__ldg(a.heavy + u) ? (uint32_t)__ldg(a.heavy + v) << 31 : 0u));
             }
         }
     }
@@ -815,7 +818,7 @@ __device__ __forceinline__ void scatter_edge(const ScatterArgs &a, bool live, ui
         uint32_t q = 0;
         if ((int)lane_id() == lead) q = atomicAdd(a.ocnt + u, (unsigned)__popc(grp));
         q = __shfl_sync(grp, q, lead) + __popc(grp & lt);
-        a.olist[__ldg(a.rowptr + u) + q] = v;
+        a.olist[__ldg(a.rowptr + u) + q] = ev;
     }
 }
 
@@ -853,7 +856,7 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
                                                       const uint32_t *__restrict__ dplus,
                                                       uint32_t *__restrict__ colp, uint32_t *__restrict__ cursor,
                                                       int hbits, uint2 *__restrict__ inlist,
-                                                      uint32_t *__restrict__ olist, uint32_t *__restrict__ ocnt,
+                                                      uint2 *__restrict__ olist, uint32_t *__restrict__ ocnt,
                                                       const uint8_t *__restrict__ heavy, uint32_t core_base,
                                                       const DevState *st)
 {
@@ -861,7 +864,7 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
     __shared__ uint32_t s_word[WORDS], s_pre[WORDS];
     __shared__ uint32_t wt[33];
     const bool dense = st->dense != 0;
-    const ScatterArgs a{rel,   padoff, rowptr, dplus, colp, cursor, olist, ocnt, inlist, hbits, heavy,
+    const ScatterArgs a{rel,   padoff, rowptr, dplus, colp, cursor, ocnt, inlist, olist, hbits, heavy,
                         dense ? st->light_lim : 0xffffffffu, dense && st->core_on ? core_base : 0xffffffffu};
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();

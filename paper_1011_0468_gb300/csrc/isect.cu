@@ -28,11 +28,14 @@
 // (one block, larger table, or a binary search of the sorted row when even
 // that is too small).  Owners with d+ < 2 close no triangle.  Rows are stored padded to
 // 16 bytes (kernels.h), so the partners' lists stream as uint4 chunks.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace tcg {
 
-constexpr uint32_t SEG_B = 512;      // largest partners per block item (IsectConfig::seg_b is capped here)
+constexpr uint32_t SEG_B = 512;      // largest partners per mid-owner item (IsectConfig::seg_b is capped here)
+constexpr uint32_t SEG_L = 4096;     // largest partners per large-owner item (IsectConfig::seg_l)
 constexpr uint32_t WARP_MAX = 256;   // largest warp-owner out-degree (IsectConfig::warp_max)
 constexpr uint32_t MID_MAX = 1024;
 constexpr uint32_t EMPTY = 0xffffffffu;
@@ -57,8 +60,9 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t warp_max)
 // Partners per item of an owner of out-degree d in bucket b (see IsectConfig).
 __device__ __forceinline__ uint32_t seg_len(uint32_t d, uint32_t b, const IsectConfig &cfg)
 {
-    const uint32_t floor = b == 0 ? SEG_MIN : 256u, work = b == 0 ? cfg.work_w : cfg.work_b;
-    uint32_t s = b == 0 ? cfg.seg_w : min(cfg.seg_b, SEG_B);
+    const uint32_t floor = b == 0 ? SEG_MIN : 256u;
+    const uint32_t work = b == 0 ? cfg.work_w : (b == 1 ? cfg.work_b : cfg.work_l);
+    uint32_t s = b == 0 ? cfg.seg_w : (b == 1 ? min(cfg.seg_b, SEG_B) : min(cfg.seg_l, SEG_L));
     while (s > floor && (uint64_t)s * d > work) s >>= 1;
     return s;
 }
@@ -231,27 +235,29 @@ struct PairCtx {
     uint32_t core_lo;  // pairs whose lower endpoint is at or above this id are the core block's
 };
 
-// Partner of owner x (out-degree d, heavy flag hx): the chunk range of the
-// part of the partner's padded out-list to stream and whether both
-// endpoints of the pair are heavy (hh).  An out-list partner is y; an
-// in-list partner is its entry e (csr.cu): e.x is the padded position of x in
-// the partner's row, e.y the number of entries after it (>= 1), with the
-// partner's heavy flag in bit 31.  The range is empty when the pair is
+// Partner of owner x (heavy flag hx): the chunk range of the part of the
+// partner's padded out-list to stream and whether both endpoints of the pair
+// are heavy (hh), from its list entry e (csr.cu).  Out-list partner y: e.x is
+// the padded start of y's row, e.y = d+(y) with y's heavy flag in bit 31.
+// In-list partner: e.x is the padded position of x in the partner's row, e.y
+// the number of entries after it (>= 1), with the partner's heavy flag in
+// bit 31.  The range is empty when the pair is
 // resolved by the other endpoint, closes no triangle, or (dense) can close
 // no triangle with a light vertex.  Also counts the streamed list entries
 // into the tally.
-__device__ __forceinline__ void partner_of(const uint32_t *__restrict__ ptrp, const PairCtx &pc, uint32_t d,
-                                           uint32_t hx, uint32_t x, uint32_t y, bool is_out, uint2 e,
+__device__ __forceinline__ void partner_of(const PairCtx &pc, uint32_t hx, uint32_t x, bool is_out, uint2 e,
                                            uint32_t &c0, uint32_t &nc, uint32_t &hh, Tally &t)
 {
     uint32_t len, b;
-    if (is_out) {  // pair (x -> y)
-        const PaddedRow py = padded_row(ptrp, y);
-        len = (py.d >= 1 && py.d <= d && x < pc.core_lo) ? py.d : 0u;
-        c0 = py.beg >> 2;
+    if (is_out) {  // pair (x -> y): e.x is the padded start of y's row, e.y = d+(y) | y's heavy flag << 31
+        // (the compaction appended it only for 1 <= d+(y) <= d+(x) and a row of
+        // x that goes on past y, and never a pair both of whose ends the dense
+        // block counts)
+        len = x < pc.core_lo ? e.y & 0x7fffffffu : 0u;
+        c0 = e.x >> 2;
         nc = (len + 3) >> 2;
-        b = y;
-        hh = (len && hx) ? (uint32_t)__ldg(pc.heavy + y) : 0u;
+        b = 0;
+        hh = hx ? e.y >> 31 : 0u;
     } else {  // pair (partner -> x): the entries of the partner's row after x
         // the compaction appended it only for 2 <= d+(partner) < d, a row
         // that goes on past x and a partner below the core
@@ -379,7 +385,7 @@ constexpr uint32_t WTAB = 1024;  // per-warp table slots, >= 4 * WARP_MAX
 __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__restrict__ ptrp,
                                                            const uint32_t *__restrict__ col,
                                                            const uint32_t *__restrict__ rowptr,
-                                                           const uint32_t *__restrict__ olist,
+                                                           const uint2 *__restrict__ olist,
                                                            const uint32_t *__restrict__ ocnt,
                                                            const uint32_t *__restrict__ inptr,
                                                            const uint32_t *__restrict__ inend,
@@ -508,17 +514,12 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
                     const uint32_t q = wb + lane;
                     uint32_t c0 = 0, nc = 0, hh = 0, ti = 0;
                     if (q < tot) {
-                        const uint32_t dh = s_dh[w][L], Ld = dh & 0x7fffffffu;
+                        const uint32_t dh = s_dh[w][L];
                         const uint32_t j = s_p0[w][L] + (q - s_pre[w][L]), oc = s_oc[w][L];
                         const bool is_out = j < oc;
-                        uint32_t y = 0;
-                        uint2 e = make_uint2(0, 0);
-                        if (is_out)
-                            y = __ldg(olist + s_ob[w][L] + j);
-                        else
-                            e = __ldg(inlist + s_ib[w][L] + j - oc);
+                        const uint2 e = is_out ? __ldg(olist + s_ob[w][L] + j) : __ldg(inlist + s_ib[w][L] + j - oc);
                         ti = s_ti[w][L];
-                        partner_of(ptrp, pc, Ld, dh >> 31, s_x[w][L], y, is_out, e, c0, nc, hh, t);
+                        partner_of(pc, dh >> 31, s_x[w][L], is_out, e, c0, nc, hh, t);
                     }
                     stream_chunks<true>(col4, BucketSet{tab, 0, 0}, tab, c0, nc, hh, ti, s_base[w], s_tinfo[w], pc, t);
                     before += __popc(sts);
@@ -605,7 +606,7 @@ template <bool DYN>
 __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8) k_probe_block(const uint32_t *__restrict__ ptrp,
                                                                       const uint32_t *__restrict__ col,
                                                                       const uint32_t *__restrict__ rowptr,
-                                                                      const uint32_t *__restrict__ olist,
+                                                                      const uint2 *__restrict__ olist,
                                                                       const uint32_t *__restrict__ ocnt,
                                                                       const uint32_t *__restrict__ inptr,
                                                                       const uint32_t *__restrict__ inend,
@@ -618,10 +619,14 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
                                                                       uint32_t core_base)
 {
     constexpr uint32_t NT = DYN ? PB_DYN_THREADS : PB_THREADS;
-    constexpr uint32_t PER_MAX = (SEG_B + NT - 1) / NT;  // partner slots set up per thread (at most)
+    constexpr uint32_t SEG = DYN ? SEG_L : SEG_B;        // partners per item (at most)
+    constexpr uint32_t PER_MAX = (SEG + NT - 1) / NT;    // partner slots set up per thread (at most)
+    // dynamic shared memory: the hash set (tab_slots slots), then the live
+    // partners of the current item (seg_cap of each array)
     extern __shared__ uint2 tab[];
-    __shared__ uint32_t s_c0[SEG_B];
-    __shared__ uint32_t s_pre[SEG_B];  // chunk prefix | PRE_CLS (both endpoints heavy)
+    const uint32_t seg_cap = DYN ? min(cfg.seg_l, SEG_L) : min(cfg.seg_b, SEG_B);
+    uint32_t *s_c0 = reinterpret_cast<uint32_t *>(tab) + tab_slots;
+    uint32_t *s_pre = s_c0 + seg_cap;  // chunk prefix | PRE_CLS (both endpoints heavy)
     __shared__ unsigned long long wt[33];
     __shared__ unsigned long long red[33];
     __shared__ uint32_t s_idx, s_next, s_left, s_built;
@@ -629,10 +634,10 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
     const uint32_t b = DYN ? 2 : 1;
     const uint32_t nitems =
         (uint32_t)min((unsigned long long)st->nlist[b], (unsigned long long)(DYN ? cap - wm_cap : wm_cap));
-    // large owners take up to 8 consecutive items per grab (at least 8 grabs
-    // per block): an owner's items are consecutive, and the table is rebuilt
-    // only when the owner changes
-    const uint32_t run = DYN ? max(1u, min(8u, nitems / (gridDim.x * 8u))) : 1u;
+    // a block takes consecutive items per grab (large owners up to 8, mid
+    // owners up to cfg.run_b, at least 8 grabs per block): an owner's items
+    // are consecutive, and the table is rebuilt only when the owner changes
+    const uint32_t run = max(1u, min(DYN ? 8u : min(cfg.run_b, 8u), nitems / (gridDim.x * 8u)));
     if (threadIdx.x == 0) {
         s_left = 0;
         s_built = 0xffffffffu;  // owner whose set the table holds
@@ -661,7 +666,7 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
         const uint32_t hx = heavy[x];
         const uint32_t slots = table_slots(d, tab_slots);
         const BucketSet set{tab, slots ? (slots >> 1) - 1 : 0u, slots ? bucket_shift(slots) : 0u};
-        if (slots && !(DYN && s_built == x)) {
+        if (slots && s_built != x) {
             for (uint32_t i = threadIdx.x; i < (slots >> 1); i += NT) tab[i] = make_uint2(EMPTY, EMPTY);
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < d; i += NT)
@@ -669,7 +674,7 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
         }
         if (seg == 0 && threadIdx.x == 0) t.table += d;
         const uint32_t ob = rowptr[x], oc = ocnt[x], ib = inptr[x], np = oc + (inend[x] - ib);
-        const uint32_t sl = seg_len(d, 1, cfg);
+        const uint32_t sl = seg_len(d, DYN ? 2 : 1, cfg);
         const uint32_t p0 = seg * sl, p1 = min(np, p0 + sl);
         const uint32_t per = (sl + NT - 1) / NT;  // <= PER_MAX
         // set up this thread's `per` consecutive partners
@@ -681,13 +686,8 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
             uint32_t c0 = 0, nc = 0, hh = 0;
             if (q < per && j < p1) {
                 const bool is_out = j < oc;
-                uint32_t y = 0;
-                uint2 e = make_uint2(0, 0);
-                if (is_out)
-                    y = __ldg(olist + ob + j);
-                else
-                    e = __ldg(inlist + ib + j - oc);
-                partner_of(ptrp, pc, d, hx, x, y, is_out, e, c0, nc, hh, t);
+                const uint2 e = is_out ? __ldg(olist + ob + j) : __ldg(inlist + ib + j - oc);
+                partner_of(pc, hx, x, is_out, e, c0, nc, hh, t);
             }
             pc0[q] = c0;
             pncc[q] = (nc << 1) | hh;
@@ -739,15 +739,16 @@ void intersect_prepare(int dyn_smem_bytes)
     const bool known = dev >= 0 && dev < 64;
     if (!known || !mid_set[dev]) {
         if (cudaFuncSetAttribute(k_probe_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(MID_TAB * 4)) == cudaSuccess &&
+                                 (int)(MID_TAB * 4 + 2 * SEG_B * 4)) == cudaSuccess &&
             known)
             mid_set[dev] = true;
     }
-    if (!known || dyn_smem_bytes > set_bytes[dev]) {
-        if (cudaFuncSetAttribute(k_probe_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem_bytes) ==
+    const int dyn = dyn_smem_bytes + (int)(2 * SEG_L * 4);
+    if (!known || dyn > set_bytes[dev]) {
+        if (cudaFuncSetAttribute(k_probe_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) ==
                 cudaSuccess &&
             known)
-            set_bytes[dev] = dyn_smem_bytes;
+            set_bytes[dev] = dyn;
     }
 }
 
@@ -759,12 +760,13 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
     k_probe_warp<<<152 * 4, PW_THREADS, 0, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr, b.inend, b.inlist,
                                                 b.items, wm, b.heavy, b.st, b.bv, b.cfg, b.core_base);
     note_launch();
-    k_probe_block<false><<<152 * 8, PB_THREADS, MID_TAB * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
+    const uint32_t seg_b = std::min(b.cfg.seg_b, SEG_B), seg_l = std::min(b.cfg.seg_l, SEG_L);
+    k_probe_block<false><<<152 * 8, PB_THREADS, MID_TAB * 4 + 2 * seg_b * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
                                                                    b.inend, b.inlist, b.items, wm,
                                                                    b.heavy, b.st, MID_TAB, b.items_cap, b.bv, b.cfg,
                                                                    b.core_base);
     note_launch();
-    k_probe_block<true><<<152, PB_DYN_THREADS, dyn_smem_bytes, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
+    k_probe_block<true><<<152, PB_DYN_THREADS, dyn_smem_bytes + 2 * seg_l * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
                                                                 b.inend, b.inlist, b.items, wm,
                                                                 b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
                                                                 b.items_cap, b.bv, b.cfg, b.core_base);

@@ -115,7 +115,8 @@ struct RowsArgs {
     uint32_t *ptrp;              // [n + 2] padded row pointers (see SENT)
     uint32_t *colp;              // [colp_capacity(n, m)] padded columns
     uint2 *inlist;               // [m] in-list entries (source, padded position of the edge in its row)
-    uint32_t *olist;             // [m] out-lists: the live out-partners of x at olist[rowptr[x] ..]
+    uint2 *olist;                // [m] out-lists: the live out-partners v of x at olist[rowptr[x] ..], each
+                                 // as (padded start of v's row, d+(v) | v's heavy flag << 31 when x is heavy)
     uint32_t *ocnt;              // [n] their number
     uint32_t *keepw;             // [ceil(m / 32)] keep bits
     uint32_t *tile_cnt;          // [ceil(m / RX_TILE) + 1]
@@ -172,11 +173,15 @@ void build_rows(const RowsArgs &a, cudaStream_t s);
 // ---------------------------------------------------------------- count.cu
 // Schedule of the intersection kernels (isect.cu); any choice gives the same
 // counts.  warp_max: owners with 2 <= d+ <= warp_max are resolved by one warp
-// (32 .. 256); seg_w / seg_b: most partners per work item of the warp / block
-// kernels (seg_w in [SEG_MIN, 1024], seg_b in [256, 512], powers of two);
-// work_w / work_b: an owner of out-degree d gets items of the largest power
-// of two <= seg_w (seg_b) partners with partners * d <= work_w (work_b), but
-// at least SEG_MIN (256), which bounds the list entries an item streams.
+// (32 .. 256); seg_w / seg_b / seg_l: most partners per work item of the warp
+// kernel, the mid-owner blocks (warp_max < d+ <= 1024) and the large-owner
+// blocks (d+ > 1024) (seg_w in [SEG_MIN, 1024], seg_b in [256, 512], seg_l in
+// [256, 4096], powers of two); work_w / work_b / work_l: an owner of
+// out-degree d gets items of the largest power of two <= seg (of its kernel)
+// partners with partners * d <= work, but at least SEG_MIN (warp) or 256
+// (blocks), which bounds the list entries an item streams; run_b: items a
+// mid-owner block takes per work-cursor grab (1 .. 8; consecutive items of
+// one owner then share its hash set).
 constexpr uint32_t SEG_MIN = 64;
 struct IsectConfig {
     uint32_t warp_max = 256;
@@ -184,6 +189,9 @@ struct IsectConfig {
     uint32_t seg_b = 512;
     uint32_t work_w = 1u << 14;
     uint32_t work_b = 1u << 19;
+    uint32_t seg_l = 4096;
+    uint32_t work_l = 1u << 25;
+    uint32_t run_b = 1;
 };
 
 struct CountBuffers {
@@ -198,7 +206,7 @@ struct CountBuffers {
     uint32_t *inptr;        // [n + 1] in-list starts
     uint32_t *inend;        // [n] in-list ends
     const uint2 *inlist;    // in-list entries (source, padded position of the edge)
-    const uint32_t *olist;  // out-lists (RowsArgs::olist)
+    const uint2 *olist;     // out-lists (RowsArgs::olist)
     const uint32_t *ocnt;   // [n]
     uint64_t *items;        // owner work items [items_cap]
     uint64_t items_cap;
@@ -238,7 +246,8 @@ struct UnionScratch {
     uint32_t n_cap = 0, k_cap = 0;
     uint64_t *rel = nullptr, *orig = nullptr;  // union keys in rank ids (sorted) and their original keys
     uint2 *inlist = nullptr;
-    uint32_t *olist = nullptr, *ocnt = nullptr;
+    uint2 *olist = nullptr;
+    uint32_t *ocnt = nullptr;
     uint64_t *items = nullptr;
     uint64_t items_cap = 0;
     uint32_t *deg = nullptr, *rowptr = nullptr, *inptr = nullptr, *hist = nullptr, *scan = nullptr;
@@ -343,5 +352,11 @@ void triples_build(const uint64_t *orig, uint64_t m, uint32_t n, int nbits, Trip
 // One triple-sampling count into *out_dev (thr >= 2^53: every edge kept).
 void triples_count(const TripleBuffers &tb, uint64_t seed_mix, uint64_t thr, uint64_t seed, uint64_t samples,
                    bool hybrid, double p, tc_triple_result *out_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------- stream.cu
+// Section 5.2's three passes over a host-resident adjacency stream (see
+// stream.cu); res receives everything but ms.  Blocks.
+tc_status stream_count(const uint64_t *off_host, const uint32_t *adj_host, uint32_t n, uint64_t seed,
+                       uint64_t samples, double c, uint64_t chunk_entries, cudaStream_t s, tc_stream_result *res);
 
 }  // namespace tcg

@@ -182,7 +182,7 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     cb.inptr = inptr;
     cb.inend = inend;
     cb.inlist = reinterpret_cast<uint2 *>(bufA);
-    cb.olist = reinterpret_cast<uint32_t *>(bufB);  // free after the sorts; m <= NA_M entries
+    cb.olist = reinterpret_cast<uint2 *>(bufB);  // free after the sorts; m <= NA_M entries of 8 bytes
     cb.ocnt = ocnt;
     cb.items = items;
     cb.items_cap = items_capacity(n, m);
@@ -201,7 +201,7 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     ra.ptrp = ptrp;
     ra.colp = colp;
     ra.inlist = reinterpret_cast<uint2 *>(bufA);
-    ra.olist = reinterpret_cast<uint32_t *>(bufB);
+    ra.olist = reinterpret_cast<uint2 *>(bufB);
     ra.ocnt = ocnt;
     ra.heavy = heavy;
     ra.keepw = keepw;

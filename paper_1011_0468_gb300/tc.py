@@ -61,6 +61,22 @@ TC_TRIPLES_SIMPLE, TC_TRIPLES_HYBRID = 0, 1
 _TRIPLE_MODES = {"simple": TC_TRIPLES_SIMPLE, "hybrid": TC_TRIPLES_HYBRID}
 
 
+class tc_schedule(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint32) for k in ("warp_max", "seg_w", "seg_b", "seg_l", "work_w", "work_b", "work_l",
+                                               "run_b")]
+
+
+class tc_stream_result(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_uint64), ("n", ctypes.c_uint32), ("n_heavy", ctypes.c_uint32),
+                ("candidates", ctypes.c_uint64), ("sampled_entries", ctypes.c_uint64), ("universe", ctypes.c_uint64),
+                ("samples", ctypes.c_uint64), ("closed_wedge", ctypes.c_uint64), ("closed_pair", ctypes.c_uint64),
+                ("estimate", ctypes.c_double), ("bytes_streamed", ctypes.c_uint64), ("passes", ctypes.c_uint32),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class tc_request_info(ctypes.Structure):
     _fields_ = [("res", tc_result), ("status", ctypes.c_int32), ("wave_size", ctypes.c_uint32),
                 ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
@@ -85,6 +101,8 @@ SIGNATURES = [
     ("tc_graph_set_sample_floor", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("tc_graph_set_core_ranks", ctypes.c_int, [_vp, ctypes.c_int64]),
     ("tc_graph_set_partition", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("tc_graph_set_schedule", ctypes.c_int, [_vp, ctypes.POINTER(tc_schedule)]),
+    ("tc_graph_get_schedule", ctypes.c_int, [_vp, ctypes.POINTER(tc_schedule)]),
     ("tc_graph_timing_drain", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32]),
     ("tc_count", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(tc_result)]),
     ("tc_count_async", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp, _vp]),
@@ -103,6 +121,8 @@ SIGNATURES = [
                                          ctypes.POINTER(ctypes.c_uint32)]),
     ("tc_count_auto", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                      ctypes.POINTER(tc_result), ctypes.POINTER(ctypes.c_double)]),
+    ("tc_stream_count", ctypes.c_int, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                                       ctypes.c_uint64, _vp, ctypes.POINTER(tc_stream_result)]),
     ("tc_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("tc_version", ctypes.c_int, []),
     ("tc_release_cached_memory", ctypes.c_int, []),
@@ -199,6 +219,30 @@ def tc_suggest_p(m: int, n: int, t: float, eps: float) -> float:
     """Section 3.3's p = (m^(1/2) ln n / (t eps^2))^(2/5), at most 1; 1 when
     t <= 0; -1 for bad arguments (host arithmetic in libtc)."""
     return float(lib().tc_suggest_p(m, n, t, eps))
+
+
+def tc_stream_count(offsets, adj, n: int, seed: int, samples: int = 0, heavy_factor: float = 3.0,
+                    chunk_entries: int = 0, stream=None) -> dict:
+    """Semi-streaming count (Section 5.2) over a host-resident symmetric
+    adjacency: offsets (n + 1 uint64) and adj (uint32), numpy arrays or
+    pinned CPU tensors (read in place by the device)."""
+    def addr(a, dtype):
+        try:
+            import torch
+            if isinstance(a, torch.Tensor):
+                return a.data_ptr(), a
+        except ImportError:
+            pass
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        return arr.ctypes.data, arr
+    oa, ok = addr(offsets, np.uint64)
+    aa, ak = addr(adj, np.uint32)
+    r = tc_stream_result()
+    _check(lib().tc_stream_count(oa, aa if len(ak) else None, n, seed & 0xFFFFFFFFFFFFFFFF, int(samples),
+                                 float(heavy_factor), int(chunk_entries), _stream_handle(stream), ctypes.byref(r)),
+           "tc_stream_count")
+    del ok, ak
+    return r.as_dict()
 
 
 def tc_count_batch(graphs, p, seed) -> np.ndarray:
@@ -341,6 +385,23 @@ class Graph:
         (tc_graph_set_partition): "sampled" (default) or "original"."""
         _check(lib().tc_graph_set_partition(self.handle, {"sampled": 0, "original": 1}[mode]),
                "tc_graph_set_partition")
+
+    def schedule(self) -> dict:
+        """The intersection schedule of the later counts (tc_graph_get_schedule)."""
+        s = tc_schedule()
+        _check(lib().tc_graph_get_schedule(self.handle, ctypes.byref(s)), "tc_graph_get_schedule")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def set_schedule(self, **kw):
+        """Change fields of the intersection schedule (tc_graph_set_schedule);
+        no arguments restores the default.  Counts never depend on it."""
+        if not kw:
+            _check(lib().tc_graph_set_schedule(self.handle, None), "tc_graph_set_schedule")
+            return
+        cur = self.schedule()
+        cur.update(kw)
+        s = tc_schedule(**cur)
+        _check(lib().tc_graph_set_schedule(self.handle, ctypes.byref(s)), "tc_graph_set_schedule")
 
     def set_core_ranks(self, ranks: int):
         """Dense core of the later counts (tc_graph_set_core_ranks): < 0 chosen
