@@ -467,8 +467,9 @@ void tc_server_destroy(tc_server *srv);
  *                until the result is in *out_host.
  * All scratch lives in one fixed __device__ array inside the library
  * (about 24 MiB), held by every GPU that loads it until the process exits.
- * The first call on a device looks up that array's device address; make
- * this first call before any stream capture.  Calls share the array (each
+ * The first call on a device looks up that array's device address (kept for
+ * the process; a device reset between calls is not supported); make this
+ * first call before any stream capture.  Calls share the array (each
  * clears what must start at zero), so calls that overlap on the GPU race:
  * serialise them.  Nothing is allocated: no cudaMalloc, no cudaFree, no
  * allocator callback.

@@ -153,7 +153,7 @@ __global__ void k_row_place(const uint64_t *__restrict__ ekey, uint64_t m, const
     }
 }
 
-constexpr uint32_t ROW_SMALL = 16, ROW_MID = 1024, ROW_SMEM = 32768;
+constexpr uint32_t ROW_SMALL = 16, ROW_SMEM = 32768;  // ROW_MID: kernels.h
 
 // Ascending bitonic network over N (a power of two) register values.
 template <int N>

@@ -547,7 +547,9 @@ constexpr uint32_t PRE_CLS = 0x80000000u;               // class bit beside a pa
 // through set.  Live partner k has its chunks at s_c0[k] .. and begins at
 // position s_pre[k] & ~PRE_CLS of the sequence (increasing in k); the warp
 // finds the partner covering wb0 by a 32-way search and then maps chunks to
-// partners window by window as stream_chunks does.
+// partners window by window as stream_chunks does, except that a window
+// lying inside one partner (a long list) reads that partner's chunks
+// directly.
 template <int WIN, class Set>
 __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, const Set &set, const uint32_t *s_c0,
                                             const uint32_t *s_pre, uint32_t nlive, uint32_t total, uint32_t wb0,
@@ -569,24 +571,35 @@ __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, cons
     uint32_t before = lo + ((s_pre[lo] & ~PRE_CLS) < wb0 ? 1u : 0u);  // partners beginning before the window
     const uint32_t end = min(total, wb0 + UNIT);
     uint32_t hl = 0, hv = 0;
+    // the partner that covers the window start (before - 1) and where the
+    // next one begins: a window that lies inside one partner needs no mapping
+    uint32_t cur = before ? before - 1 : 0u, cur_pk = s_pre[cur], cur_c0 = s_c0[cur];
+    uint32_t nxt = before < nlive ? s_pre[before] & ~PRE_CLS : total;
     for (uint32_t wb = wb0; wb < end; wb += 32 * WIN) {
-        uint32_t e[WIN], k[WIN], pk[WIN];
+        uint32_t e[WIN], pk[WIN];
         uint4 q[WIN];
 #pragma unroll
         for (int i = 0; i < WIN; ++i) {
-            const uint32_t w0 = wb + 32u * i, kk = before + lane;
+            const uint32_t w0 = wb + 32u * i;
+            e[i] = w0 + lane;
+            if (before != 0 && w0 + 32u <= nxt) {  // warp-uniform: the whole window is in partner cur
+                pk[i] = cur_pk;
+                if (e[i] < end) q[i] = __ldg(col4 + (cur_c0 + (e[i] - (cur_pk & ~PRE_CLS))));
+                continue;
+            }
+            const uint32_t kk = before + lane;
             const uint32_t pre = kk < nlive ? (s_pre[kk] & ~PRE_CLS) : 0xffffffffu;
             const unsigned sti = __reduce_or_sync(FULL, pre - w0 < 32u ? (1u << (pre - w0)) : 0u);
-            e[i] = w0 + lane;
-            k[i] = before + __popc(sti & upto) - 1;
+            const uint32_t k = before + __popc(sti & upto) - 1;
             before += __popc(sti);
-        }
-#pragma unroll
-        for (int i = 0; i < WIN; ++i) {
             if (e[i] < end) {
-                pk[i] = s_pre[k[i]];
-                q[i] = __ldg(col4 + (s_c0[k[i]] + (e[i] - (pk[i] & ~PRE_CLS))));
+                pk[i] = s_pre[k];
+                q[i] = __ldg(col4 + (s_c0[k] + (e[i] - (pk[i] & ~PRE_CLS))));
             }
+            cur = before - 1;  // covers the next window's start
+            cur_pk = s_pre[cur];
+            cur_c0 = s_c0[cur];
+            nxt = before < nlive ? s_pre[before] & ~PRE_CLS : total;
         }
 #pragma unroll
         for (int i = 0; i < WIN; ++i) {

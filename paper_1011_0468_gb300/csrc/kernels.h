@@ -135,6 +135,9 @@ struct RowsArgs {
     const uint8_t *heavy = nullptr;
     uint32_t core_base = 0xffffffffu;
 };
+// Rank-order rows (relabel) of up to ROW_MID keys are sorted by one warp in
+// registers; longer rows by a block, with global scratch beyond shared memory.
+constexpr uint32_t ROW_MID = 1024;
 // Static rows of a single graph at creation: frow[0..n] (row offsets of rel)
 // and inres[0..n] (in-list reservation offsets: full in-degrees).  perm and
 // deg_orig: rank -> original id and the full degree by original id.

@@ -32,6 +32,14 @@ constexpr uint64_t NA_SCAN = 2 * ((NA_HIST > NA_N + 2 ? NA_HIST : NA_N + 2) / SC
 constexpr uint64_t NA_ITEMS = NA_N + 2 * NA_M / SEG_MIN + NA_M / 1024 + 2 * NA_M / 256 + 256;  // >= items_capacity(N, M)
 constexpr uint64_t NA_COLP = NA_M + 3 * NA_M + 4;  // >= colp_capacity(N, M)
 static_assert(NA_N <= NA_M, "the vertex sort reuses the key buffers");
+// A rank-order row (out-degree d of the degree order) has d(d - 1) / 2 <= m,
+// so with m <= NA_M every row has fewer than NA_DMAX keys: at most ROW_MID,
+// the rows one warp sorts in registers.  The long-row path of the relabeling
+// (which would use RelabelScratch::kB as global scratch, here the same
+// memory as other buffers) is therefore never taken.
+constexpr uint64_t NA_DMAX = 725;
+static_assert(NA_DMAX * (NA_DMAX - 1) / 2 > NA_M, "rows stay below NA_DMAX keys");
+static_assert(NA_DMAX <= ROW_MID, "every row is sorted by the warp path");
 constexpr uint64_t NA_BYTES = 4 * na_round(8 * NA_M)                     // ekey (then rel), orig, bufA, bufB
                               + 5 * na_round(4 * NA_N)                   // perm, rank, spread, inend, ocnt
                               + na_round(4 * (NA_M / 32 + 1)) + na_round(4 * (NA_TILES + 1))  // keepw, tile_cnt
@@ -164,7 +172,8 @@ extern "C" tc_status tc_count_noalloc(const uint32_t *edges_dev, uint64_t m_in, 
     }
 
     // ---- rank relabeling (csr.cu): rel keys replace the canonical keys; the
-    // vertex sort and the key sort both ping-pong between bufA and bufB
+    // vertex sort and the key sort both ping-pong between bufA and bufB.  The
+    // long-row scratch (kB = bufB) is never touched: see NA_DMAX.
     relabel(ekey, m, n, nullptr, 0, Relabeled{ekey, orig, perm, rank},
             RelabelScratch{bufA, bufB, bufA, bufB, deg, hist, scan}, s);
 
