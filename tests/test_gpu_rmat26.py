@@ -11,8 +11,10 @@ the host:
 - at p = 0.05 (seeds 1 and 2), 0.25 and 0.5: m_p, the per-class counts, the
   estimate, and checksums of the kept edges and heavy flags (at 0.25 and 0.5
   the counts choose a dense core of the top ranks, so these pin it too);
-- p = 1, which the oracle would need about eight hours for, is checked by
-  properties that hold at any size.
+- at p = 1, the exact count: T_L, T_H and n_heavy of the whole graph (the
+  oracle's enumeration split over host threads by smallest vertex), where
+  the 65536-rank dense core and the large-owner kernel carry most of the
+  work; properties that hold at any size are checked as well.
 """
 import importlib.util
 import json
