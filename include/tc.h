@@ -194,6 +194,13 @@ tc_status tc_graph_set_core_ranks(tc_graph *g, int64_t ranks);
                          each >= 4096
      run_b               items a mid-owner block takes per grab, 1 .. 8
                          (consecutive items of one owner share its hash set)
+     mid_max             owners with warp_max < d+ <= mid_max go to the
+                         128-thread blocks, larger ones to the 1024-thread
+                         blocks (512 .. 1024)
+     lookup              membership test of the block kernels: bit 0 for the
+                         128-thread blocks, bit 1 for the 1024-thread blocks;
+                         0 a hash set of the owner's list in shared memory, 1
+                         a binary search of the owner's sorted row
    Results never depend on the schedule; only the time does.
    tc_graph_set_schedule(g, NULL) restores the default.  TC_EINVAL for a
    NULL graph or a value out of range. */
@@ -202,9 +209,19 @@ typedef struct {
     uint32_t seg_w, seg_b, seg_l;
     uint32_t work_w, work_b, work_l;
     uint32_t run_b;
+    uint32_t mid_max;
+    uint32_t lookup;
 } tc_schedule;
 tc_status tc_graph_set_schedule(tc_graph *g, const tc_schedule *s);
 tc_status tc_graph_get_schedule(const tc_graph *g, tc_schedule *out);
+/* Choose the graph's schedule by timing counts at (p, seed): a coordinate
+   search over warp_max (64 / 128 / 256), mid_max (512 / 1024), seg_w,
+   seg_b (256 / 512), seg_l (1024 / 2048 / 4096) and lookup (0 .. 3), from
+   the current schedule, keeping each improvement.  The choice stays with the
+   graph; desc (may be NULL) receives it with the strategy of each owner
+   bucket.  Runs about 16 x 3 counts; results never depend on it.  TC_EINVAL
+   for a NULL graph or p outside (0, 1]; TC_ECUDA, TC_ETIMEOUT. */
+tc_status tc_graph_autotune(tc_graph *g, double p, uint64_t seed, char *desc, uint32_t desc_len);
 
 /* After tc_graph_sync: copy the phase times (8 floats per count, layout of
    tc_result.ms) of the counts completed since the last drain, oldest first,
@@ -360,13 +377,17 @@ tc_status tc_batch_create(const uint32_t *edges, const uint64_t *m_per_graph, co
 tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_result *out);
 
 /*
- * Autotune the batch's intersection schedule: time the candidate schedules
- * (warp-per-owner cutoff on the owner's out-degree 64 / 128 / 256, work-item
- * sizes of the warp and block kernels) on this batch with these (p, seed),
- * keep the fastest for the batch's later counts and remember it for batches
- * of the same shape (log2 of edges, vertices, graphs and average degree)
- * created later in this process.  Counts are identical under every
- * schedule.  desc (may be NULL) receives a short description of the choice.
+ * Autotune the batch's intersection schedule (see tc_schedule): a coordinate
+ * search, one axis at a time, timing each candidate on this batch with these
+ * (p, seed): the owners' split between one warp and one block (warp_max 64 /
+ * 128 / 256), between the 128- and 1024-thread blocks (mid_max 512 / 1024),
+ * the work-item sizes of the warp and mid-owner kernels, and the membership
+ * test of each block kernel (a shared-memory hash set or a binary search of
+ * the owner's sorted row).  The fastest is kept for the batch's later counts
+ * and remembered for batches of the same shape (log2 of edges, vertices,
+ * graphs and average degree) created later in this process.  Counts are
+ * identical under every schedule.  desc (may be NULL) receives the choice,
+ * with the strategy of each owner bucket.
  */
 tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, char *desc, uint32_t desc_len);
 void tc_batch_destroy(tc_batch *b); /* NULL-safe */

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -712,7 +713,7 @@ tc_status tc_graph_set_schedule(tc_graph *g, const tc_schedule *s)
     auto pow2_in = [](uint32_t v, uint32_t lo, uint32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; };
     if (s->warp_max < 32 || s->warp_max > 256 || !pow2_in(s->seg_w, 64, 1024) || !pow2_in(s->seg_b, 256, 512) ||
         !pow2_in(s->seg_l, 256, 4096) || s->work_w < 4096 || s->work_b < 4096 || s->work_l < 4096 || s->run_b < 1 ||
-        s->run_b > 8)
+        s->run_b > 8 || s->mid_max < 512 || s->mid_max > 1024 || s->lookup > 3)
         return TC_EINVAL;
     IsectConfig c;
     c.warp_max = s->warp_max;
@@ -723,7 +724,75 @@ tc_status tc_graph_set_schedule(tc_graph *g, const tc_schedule *s)
     c.work_b = s->work_b;
     c.work_l = s->work_l;
     c.run_b = s->run_b;
+    c.mid_max = s->mid_max;
+    c.lookup = s->lookup;
     g->cfg = c;
+    return TC_OK;
+}
+
+tc_status tc_graph_autotune(tc_graph *g, double p, uint64_t seed, char *desc, uint32_t desc_len)
+{
+    if (!g || bad_p(p)) return TC_EINVAL;
+    if (sync_graph(g) == TC_ECUDA) return TC_ECUDA;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    // device time of a count under schedule c: one warm-up, then the best of two
+    auto time_of = [&](const IsectConfig &c, float &ms) {
+        g->cfg = c;
+        ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, g->stream);
+            tc_status r = enqueue_count(g, p, seed, g->res_host, false);
+            cudaEventRecord(e1, g->stream);
+            if (r == TC_OK) r = sync_graph(g);
+            if (r != TC_OK) return r;
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep) ms = std::min(ms, t);
+        }
+        return TC_OK;
+    };
+    struct Axis {
+        uint32_t IsectConfig::*field;
+        std::vector<uint32_t> values;
+    };
+    const Axis axes[] = {{&IsectConfig::warp_max, {64, 128, 256}},
+                         {&IsectConfig::mid_max, {512, 1024}},
+                         {&IsectConfig::seg_w, {256, 512}},
+                         {&IsectConfig::seg_b, {256, 512}},
+                         {&IsectConfig::seg_l, {1024, 2048, 4096}},
+                         {&IsectConfig::lookup, {0, 1, 2, 3}}};
+    IsectConfig best = g->cfg;
+    float best_ms = 1e30f;
+    tc_status st = time_of(best, best_ms);
+    for (const Axis &a : axes) {
+        for (uint32_t v : a.values) {
+            if (st != TC_OK || best.*(a.field) == v) continue;
+            IsectConfig c = best;
+            c.*(a.field) = v;
+            float ms = 0;
+            st = time_of(c, ms);
+            if (st == TC_OK && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    g->cfg = best;
+    if (st != TC_OK) return st;
+    if (desc && desc_len)
+        snprintf(desc, desc_len,
+                 "warp_max=%u mid_max=%u seg_w=%u seg_b=%u seg_l=%u lookup=%u: warp per owner (d+<=%u, hash sets), "
+                 "128-thread block per owner (d+<=%u, %s), 1024-thread block per owner (%s); count_ms=%.3f",
+                 best.warp_max, best.mid_max, best.seg_w, best.seg_b, best.seg_l, best.lookup, best.warp_max,
+                 best.mid_max, (best.lookup & 1u) ? "binary search" : "hash set",
+                 (best.lookup & 2u) ? "binary search" : "hash set", best_ms);
     return TC_OK;
 }
 
@@ -731,7 +800,8 @@ tc_status tc_graph_get_schedule(const tc_graph *g, tc_schedule *out)
 {
     if (!g || !out) return TC_EINVAL;
     const IsectConfig &c = g->cfg;
-    *out = tc_schedule{c.warp_max, c.seg_w, c.seg_b, c.seg_l, c.work_w, c.work_b, c.work_l, c.run_b};
+    *out = tc_schedule{c.warp_max, c.seg_w, c.seg_b, c.seg_l, c.work_w, c.work_b, c.work_l, c.run_b, c.mid_max,
+                       c.lookup};
     return TC_OK;
 }
 

@@ -521,41 +521,60 @@ tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, 
     if (!b || !p || !seed) return TC_EINVAL;
     tc_status st = stage_params(b, p, seed);
     if (st != TC_OK) return st;
-    const uint32_t warp_maxes[3] = {64, 128, 256}, seg_ws[2] = {256, 512}, seg_bs[2] = {256, 512};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
         return TC_ECUDA;
     }
+    // time of one batched count under schedule c (capture + warm-up, then the
+    // best of two replays)
+    auto time_of = [&](const IsectConfig &c, float &ms) {
+        b->cfg = c;
+        drop_exec(b);
+        tc_status r = run_once(b);
+        ms = 1e30f;
+        for (int rep = 0; rep < 2 && r == TC_OK; ++rep) {
+            cudaEventRecord(e0, b->stream);
+            add_launches(b->launches_per_run);
+            cudaGraphLaunch(b->exec, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                r = TC_ECUDA;
+                break;
+            }
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+        }
+        return r;
+    };
+    // coordinate search, one axis at a time from the current schedule: the
+    // warp / block split of the owners, the mid / large split, the items'
+    // sizes and the membership test of each block kernel
+    struct Axis {
+        uint32_t IsectConfig::*field;
+        std::vector<uint32_t> values;
+    };
+    const Axis axes[] = {{&IsectConfig::warp_max, {64, 128, 256}}, {&IsectConfig::mid_max, {512, 1024}},
+                         {&IsectConfig::seg_w, {256, 512}},       {&IsectConfig::seg_b, {256, 512}},
+                         {&IsectConfig::lookup, {0, 1, 2, 3}}};
     IsectConfig best = b->cfg;
     float best_ms = 1e30f;
-    for (uint32_t wm : warp_maxes)
-        for (uint32_t sw : seg_ws)
-            for (uint32_t sb : seg_bs) {
-                if (st != TC_OK) break;
-                b->cfg = IsectConfig{wm, sw, sb};
-                drop_exec(b);
-                st = run_once(b);  // capture + warm-up
-                if (st != TC_OK) break;
-                float ms = 1e30f;
-                for (int rep = 0; rep < 2; ++rep) {
-                    cudaEventRecord(e0, b->stream);
-                    add_launches(b->launches_per_run);
-                    cudaGraphLaunch(b->exec, b->stream);
-                    cudaEventRecord(e1, b->stream);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) {
-                        st = TC_ECUDA;
-                        break;
-                    }
-                    float t = 0;
-                    cudaEventElapsedTime(&t, e0, e1);
-                    ms = std::min(ms, t);
-                }
-                if (st == TC_OK && ms < best_ms) {
-                    best_ms = ms;
-                    best = b->cfg;
-                }
+    st = time_of(best, best_ms);
+    for (const Axis &a : axes) {
+        for (uint32_t v : a.values) {
+            if (st != TC_OK || best.*(a.field) == v) continue;
+            IsectConfig c = best;
+            c.*(a.field) = v;
+            float ms = 0;
+            st = time_of(c, ms);
+            if (st == TC_OK && ms < best_ms) {
+                best_ms = ms;
+                best = c;
             }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaGetLastError();
@@ -567,7 +586,11 @@ tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, 
         g_tuned[shape_signature(b)] = best;
     }
     if (desc && desc_len)
-        snprintf(desc, desc_len, "warp_max=%u seg_w=%u seg_b=%u best_ms=%.3f", best.warp_max, best.seg_w, best.seg_b,
+        snprintf(desc, desc_len,
+                 "warp_max=%u seg_w=%u seg_b=%u mid_max=%u lookup=%u: warp per owner (d+<=%u, hash sets), "
+                 "128-thread block per owner (d+<=%u, %s), 1024-thread block per owner (%s); best_ms=%.3f",
+                 best.warp_max, best.seg_w, best.seg_b, best.mid_max, best.lookup, best.warp_max, best.mid_max,
+                 (best.lookup & 1u) ? "binary search" : "hash set", (best.lookup & 2u) ? "binary search" : "hash set",
                  best_ms);
     return TC_OK;
 }

@@ -38,6 +38,7 @@ constexpr uint32_t SEG_B = 512;      // largest partners per mid-owner item (Ise
 constexpr uint32_t SEG_L = 4096;     // largest partners per large-owner item (IsectConfig::seg_l)
 constexpr uint32_t WARP_MAX = 256;   // largest warp-owner out-degree (IsectConfig::warp_max)
 constexpr uint32_t MID_MAX = 1024;
+constexpr uint32_t MID_MIN = 512;    // smallest IsectConfig::mid_max
 constexpr uint32_t EMPTY = 0xffffffffu;
 constexpr uint32_t GRAB = 8;  // warp items taken per work-cursor atomic (at most 32)
 constexpr int NWIN = 2;  // 32-chunk windows in flight per warp step
@@ -48,13 +49,13 @@ static uint64_t wm_capacity(uint32_t n, uint64_t m) { return (uint64_t)n + 2 * m
 
 uint64_t items_capacity(uint32_t n, uint64_t m)
 {
-    // large items (d+ > MID_MAX, at most m / MID_MAX owners) after the rest
-    return wm_capacity(n, m) + m / MID_MAX + 2 * m / 256 + 64;
+    // large items (d+ > mid_max >= MID_MIN, at most m / MID_MIN owners) after the rest
+    return wm_capacity(n, m) + m / MID_MIN + 2 * m / 256 + 64;
 }
 
-__device__ __forceinline__ uint32_t bucket_of(uint32_t d, uint32_t warp_max)
+__device__ __forceinline__ uint32_t bucket_of(uint32_t d, const IsectConfig &cfg)
 {
-    return d <= warp_max ? 0u : (d <= MID_MAX ? 1u : 2u);
+    return d <= cfg.warp_max ? 0u : (d <= min(max(cfg.mid_max, MID_MIN), MID_MAX) ? 1u : 2u);
 }
 
 // Partners per item of an owner of out-degree d in bucket b (see IsectConfig).
@@ -97,7 +98,7 @@ __global__ void k_items(const uint32_t *__restrict__ rowptr, const uint32_t *__r
             if (d >= 2) np = ocnt[x] + (inend[x] - inptr[x]);
         }
         const uint32_t gx = batch ? find_part_warp(bv.voff, bv.k, (uint32_t)(x < n ? x : n - 1)) : 0u;
-        const uint32_t b = bucket_of(d, cfg.warp_max), seg = seg_len(d, b, cfg);
+        const uint32_t b = bucket_of(d, cfg), seg = seg_len(d, b, cfg);
         uint32_t nseg = (np + seg - 1) / seg;
         if (batch && nseg > 0x10000u) {  // segment index must fit 16 bits
             atomicOr(&st->err, ERR_OVERFLOW);
@@ -677,7 +678,9 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
         const PaddedRow row = padded_row(ptrp, x);
         const uint32_t d = row.d;
         const uint32_t hx = heavy[x];
-        const uint32_t slots = table_slots(d, tab_slots);
+        // the owner's hash set, unless the schedule asks this kernel for a
+        // binary search of the sorted row (or the set would not fit)
+        const uint32_t slots = ((cfg.lookup >> (DYN ? 1 : 0)) & 1u) ? 0u : table_slots(d, tab_slots);
         const BucketSet set{tab, slots ? (slots >> 1) - 1 : 0u, slots ? bucket_shift(slots) : 0u};
         if (slots && s_built != x) {
             for (uint32_t i = threadIdx.x; i < (slots >> 1); i += NT) tab[i] = make_uint2(EMPTY, EMPTY);

@@ -184,7 +184,12 @@ void build_rows(const RowsArgs &a, cudaStream_t s);
 // partners with partners * d <= work, but at least SEG_MIN (warp) or 256
 // (blocks), which bounds the list entries an item streams; run_b: items a
 // mid-owner block takes per work-cursor grab (1 .. 8; consecutive items of
-// one owner then share its hash set).
+// one owner then share its hash set); mid_max: owners with warp_max < d+ <=
+// mid_max go to the 128-thread blocks, larger ones to the 1024-thread blocks
+// (512 .. 1024); lookup: how the block kernels test membership in the
+// owner's list, bit 0 for the mid-owner blocks, bit 1 for the large-owner
+// blocks: 0 a shared-memory hash set, 1 a binary search of the owner's
+// sorted row.
 constexpr uint32_t SEG_MIN = 64;
 struct IsectConfig {
     uint32_t warp_max = 256;
@@ -195,6 +200,8 @@ struct IsectConfig {
     uint32_t seg_l = 4096;
     uint32_t work_l = 1u << 25;
     uint32_t run_b = 1;
+    uint32_t mid_max = 1024;
+    uint32_t lookup = 0;
 };
 
 struct CountBuffers {

@@ -29,7 +29,7 @@ constexpr uint64_t na_round(uint64_t b) { return (b + NA_ALIGN - 1) / NA_ALIGN *
 constexpr uint64_t NA_TILES = (NA_M + RX_TILE - 1) / RX_TILE;
 constexpr uint64_t NA_HIST = NA_TILES << RX_MAX_BITS;  // uint32 entries
 constexpr uint64_t NA_SCAN = 2 * ((NA_HIST > NA_N + 2 ? NA_HIST : NA_N + 2) / SC_CHUNK + 2);
-constexpr uint64_t NA_ITEMS = NA_N + 2 * NA_M / SEG_MIN + NA_M / 1024 + 2 * NA_M / 256 + 256;  // >= items_capacity(N, M)
+constexpr uint64_t NA_ITEMS = NA_N + 2 * NA_M / SEG_MIN + NA_M / 512 + 2 * NA_M / 256 + 256;  // >= items_capacity(N, M)
 constexpr uint64_t NA_COLP = NA_M + 3 * NA_M + 4;  // >= colp_capacity(N, M)
 static_assert(NA_N <= NA_M, "the vertex sort reuses the key buffers");
 // A rank-order row (out-degree d of the degree order) has d(d - 1) / 2 <= m,

@@ -13,6 +13,7 @@
 // the union gives every request its own vertex range, counters and (p,
 // seed), each result equals the one tc_count returns for that graph alone.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -77,6 +78,10 @@ struct GraphEntry {
     cudaEvent_t ready = nullptr;  // recorded after each re-upload
     int upload_slot = -1;
     uint64_t upload_wave = 0;
+    // a wave of one request on this graph, captured once per slot while the
+    // resident copy stays in place (kernels baked for its m, n and address)
+    cudaGraphExec_t exec[MAX_SLOTS] = {};
+    unsigned long long exec_launches[MAX_SLOTS] = {};
 };
 
 struct Req {
@@ -95,22 +100,38 @@ struct Record {
 struct Slot {
     UnionScratch u;
     cudaStream_t s = nullptr;
-    // pinned staging of one wave's parameters and results
-    uint64_t *h_eoff = nullptr, *h_thr = nullptr, *h_seed_mix = nullptr;
-    const uint64_t **h_src = nullptr;
-    uint32_t *h_voff = nullptr;
-    double *h_p = nullptr;
+    // one wave's parameters, packed for a single copy (wave_params), pinned
+    // staging and its device twin, and the pinned results
+    unsigned char *h_params = nullptr, *d_params = nullptr;
     tc_result *h_res = nullptr;
     DevState *h_st = nullptr;
-    const uint64_t **d_src = nullptr;
+    cudaEvent_t done_ev = nullptr;  // recorded when the wave's results are on the host
     // wave in flight
     std::vector<Req> wave;
     std::vector<GraphEntry *> wave_graphs;
-    bool busy = false, finished = false;
+    bool busy = false;  // a wave is in flight (its end: done_ev)
     tc_status launch_status = TC_OK;
     double t_admit = 0;
     uint64_t serial = 0;
 };
+
+// Byte offsets of a wave's parameters in one block (k requests): eoff[k + 1],
+// src[k], p[k], thr[k], seed mixes[k] (8 bytes each), then voff[k + 1].
+struct WaveLayout {
+    uint64_t eoff, src, p, thr, mix, voff, bytes;
+};
+WaveLayout wave_layout(uint32_t k)
+{
+    WaveLayout L;
+    L.eoff = 0;
+    L.src = L.eoff + (k + 1ull) * 8;
+    L.p = L.src + k * 8ull;
+    L.thr = L.p + k * 8ull;
+    L.mix = L.thr + k * 8ull;
+    L.voff = L.mix + k * 8ull;
+    L.bytes = L.voff + (k + 1ull) * 4;
+    return L;
+}
 
 struct CallbackCtx {
     tc_server *srv;
@@ -146,6 +167,8 @@ struct tc_server {
     bool stop = false;
     tc_server_stats stats{};
 
+    std::atomic<uint64_t> arrivals{0};  // submissions so far (read by the polling worker)
+
     std::mutex ingest_mu;
     cudaStream_t ingest = nullptr;
     std::thread worker;
@@ -159,8 +182,8 @@ void CUDART_CB on_slot_done(void *arg)
     // runs on a CUDA callback thread: no CUDA calls here
     CallbackCtx *c = static_cast<CallbackCtx *>(arg);
     {
+        // a wake-up only: the worker tells a finished wave by its done_ev
         std::lock_guard<std::mutex> lock(c->srv->mu);
-        c->srv->slots[c->slot].finished = true;
     }
     c->srv->work_cv.notify_all();
 }
@@ -193,14 +216,14 @@ void complete_wave(tc_server *srv, uint32_t si)
     sl.wave.clear();
     sl.wave_graphs.clear();
     sl.busy = false;
-    sl.finished = false;
     srv->done_cv.notify_all();
 }
 
 // Under the lock: admit the longest queue prefix that fits slot si and the
 // budget.  Graphs to (re)upload go to `uploads`, device copies to free to
 // `frees`.  Returns false if nothing could be admitted.
-bool form_wave(tc_server *srv, uint32_t si, std::vector<GraphEntry *> &uploads, std::vector<uint64_t *> &frees)
+bool form_wave(tc_server *srv, uint32_t si, std::vector<GraphEntry *> &uploads, std::vector<uint64_t *> &frees,
+               std::vector<cudaGraphExec_t> &dead)
 {
     Slot &sl = srv->slots[si];
     const uint64_t room = srv->budget - srv->slot_bytes;
@@ -226,6 +249,11 @@ bool form_wave(tc_server *srv, uint32_t si, std::vector<GraphEntry *> &uploads, 
                 }
                 if (v->dev) frees.push_back(v->dev);
                 v->dev = nullptr;
+                for (cudaGraphExec_t &e : v->exec)  // its captured waves name the old copy
+                    if (e) {
+                        dead.push_back(e);
+                        e = nullptr;
+                    }
                 v->resident = false;
                 srv->resident_bytes -= v->dev_bytes;
                 --srv->stats.resident_graphs;
@@ -254,10 +282,11 @@ bool form_wave(tc_server *srv, uint32_t si, std::vector<GraphEntry *> &uploads, 
 
 // Outside the lock (worker thread only): enqueue the wave of slot si.
 tc_status enqueue_wave(tc_server *srv, uint32_t si, const std::vector<GraphEntry *> &uploads,
-                       const std::vector<uint64_t *> &frees)
+                       const std::vector<uint64_t *> &frees, const std::vector<cudaGraphExec_t> &dead)
 {
     Slot &sl = srv->slots[si];
     cudaStream_t s = sl.s;
+    for (cudaGraphExec_t e : dead) cudaGraphExecDestroy(e);  // their graphs ran no wave in flight
     for (uint64_t *ptr : frees) cudaFreeAsync(ptr, s);
     for (GraphEntry *g : uploads) {
         if (cudaMallocAsync((void **)&g->dev, g->m * 16, s) != cudaSuccess) {
@@ -279,32 +308,87 @@ tc_status enqueue_wave(tc_server *srv, uint32_t si, const std::vector<GraphEntry
             const Slot &o = srv->slots[g->upload_slot];
             if (o.busy && o.serial == g->upload_wave) cudaStreamWaitEvent(s, g->ready, 0);
         }
+    }
+    // the wave's parameters in one pinned block, copied once
+    const WaveLayout L = wave_layout(k);
+    UnionScratch u = sl.u;
+    uint64_t *h_eoff = reinterpret_cast<uint64_t *>(sl.h_params + L.eoff);
+    uint32_t *h_voff = reinterpret_cast<uint32_t *>(sl.h_params + L.voff);
+    const uint64_t **h_src = reinterpret_cast<const uint64_t **>(sl.h_params + L.src);
+    double *h_p = reinterpret_cast<double *>(sl.h_params + L.p);
+    uint64_t *h_thr = reinterpret_cast<uint64_t *>(sl.h_params + L.thr);
+    uint64_t *h_mix = reinterpret_cast<uint64_t *>(sl.h_params + L.mix);
+    for (uint32_t j = 0; j < k; ++j) {
+        GraphEntry *g = sl.wave_graphs[j];
         const Req &r = sl.wave[j];
-        sl.h_eoff[j] = m;
-        sl.h_voff[j] = (uint32_t)n;
-        sl.h_src[j] = g->dev;
-        sl.h_p[j] = r.p;
-        sl.h_thr[j] = (uint64_t)(r.p * 9007199254740992.0);
-        sl.h_seed_mix[j] = splitmix64(r.seed);
+        h_eoff[j] = m;
+        h_voff[j] = (uint32_t)n;
+        h_src[j] = g->dev;
+        h_p[j] = r.p;
+        h_thr[j] = (uint64_t)(r.p * 9007199254740992.0);
+        h_mix[j] = splitmix64(r.seed);
         m += g->m;
         n += g->n;
     }
-    sl.h_eoff[k] = m;
-    sl.h_voff[k] = (uint32_t)n;
-    cudaMemcpyAsync(sl.u.eoff, sl.h_eoff, (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(sl.u.voff, sl.h_voff, (k + 1) * 4ull, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(sl.d_src, sl.h_src, k * 8ull, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(sl.u.p, sl.h_p, k * 8ull, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(sl.u.thr, sl.h_thr, k * 8ull, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(sl.u.seed_mix, sl.h_seed_mix, k * 8ull, cudaMemcpyHostToDevice, s);
-    if (m > 0) {
-        k_gather<<<grid_for(m, 256, 152 * 8), 256, 0, s>>>(sl.d_src, sl.u.eoff, sl.u.voff, k, m, sl.u.rel,
-                                                            sl.u.orig);
+    h_eoff[k] = m;
+    h_voff[k] = (uint32_t)n;
+    u.eoff = reinterpret_cast<uint64_t *>(sl.d_params + L.eoff);
+    u.voff = reinterpret_cast<uint32_t *>(sl.d_params + L.voff);
+    u.p = reinterpret_cast<double *>(sl.d_params + L.p);
+    u.thr = reinterpret_cast<uint64_t *>(sl.d_params + L.thr);
+    u.seed_mix = reinterpret_cast<uint64_t *>(sl.d_params + L.mix);
+    if (k == 1 && m > 0) {
+        // a wave of one request counts the resident copy in place (its keys
+        // are already the union's: one graph at vertex offset 0), as one
+        // CUDA graph captured the first time this graph comes alone to this
+        // slot: parameters in, the count, results out
+        GraphEntry *g = sl.wave_graphs[0];
+        u.rel = g->dev;
+        u.orig = g->dev + m;
+        if (!g->exec[si]) {
+            const unsigned long long l0 = tc_launch_count();
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                cudaMemcpyAsync(sl.d_params, sl.h_params, L.bytes, cudaMemcpyHostToDevice, s);
+                union_count(u, m, (uint32_t)n, 1, IsectConfig{}, s);
+                cudaMemcpyAsync(sl.h_res, u.res_dev, sizeof(tc_result), cudaMemcpyDeviceToHost, s);
+                cudaMemcpyAsync(sl.h_st, u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+                if (cudaStreamEndCapture(s, &graph) == cudaSuccess && graph) {
+                    if (cudaGraphInstantiate(&g->exec[si], graph, 0) != cudaSuccess) g->exec[si] = nullptr;
+                    cudaGraphDestroy(graph);
+                }
+            }
+            cudaGetLastError();
+            g->exec_launches[si] = tc_launch_count() - l0;  // counted once, at capture
+        } else {
+            add_launches(g->exec_launches[si]);
+        }
+        if (g->exec[si]) {
+            if (cudaGraphLaunch(g->exec[si], s) != cudaSuccess) {
+                cudaGetLastError();
+                return TC_ECUDA;
+            }
+            cudaEventRecord(sl.done_ev, s);
+            if (cudaLaunchHostFunc(s, on_slot_done, &srv->cb[si]) != cudaSuccess) {
+                cudaGetLastError();
+                return TC_ECUDA;
+            }
+            return TC_OK;
+        }
+    }
+    cudaMemcpyAsync(sl.d_params, sl.h_params, L.bytes, cudaMemcpyHostToDevice, s);
+    if (k == 1 && m > 0) {
+        u.rel = sl.wave_graphs[0]->dev;
+        u.orig = sl.wave_graphs[0]->dev + m;
+    } else if (m > 0) {
+        k_gather<<<grid_for(m, 256, 152 * 8), 256, 0, s>>>(
+            reinterpret_cast<const uint64_t *const *>(sl.d_params + L.src), u.eoff, u.voff, k, m, u.rel, u.orig);
         note_launch();
     }
-    union_count(sl.u, m, (uint32_t)n, k, IsectConfig{}, s);
+    union_count(u, m, (uint32_t)n, k, IsectConfig{}, s);
     cudaMemcpyAsync(sl.h_res, sl.u.res_dev, k * sizeof(tc_result), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(sl.h_st, sl.u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(sl.done_ev, s);
     if (cudaGetLastError() != cudaSuccess) return TC_ECUDA;
     if (cudaLaunchHostFunc(s, on_slot_done, &srv->cb[si]) != cudaSuccess) {
         cudaGetLastError();
@@ -319,27 +403,32 @@ void worker_main(tc_server *srv)
     std::unique_lock<std::mutex> lock(srv->mu);
     for (;;) {
         for (uint32_t i = 0; i < srv->nslots; ++i)
-            if (srv->slots[i].busy && srv->slots[i].finished) complete_wave(srv, i);
+            if (srv->slots[i].busy && cudaEventQuery(srv->slots[i].done_ev) == cudaSuccess) complete_wave(srv, i);
+        cudaGetLastError();  // cudaErrorNotReady of the waves still running
         bool any_busy = false;
         for (uint32_t i = 0; i < srv->nslots; ++i) any_busy |= srv->slots[i].busy;
         if (srv->stop && !any_busy) break;
         bool launched = false;
         if (!srv->stop) {
-            for (uint32_t i = 0; i < srv->nslots && !srv->queue.empty(); ++i) {
+            // slots are tried from the one the head request's graph maps to, so
+            // that its single-request waves keep using the same captured launch
+            const uint32_t first = srv->queue.empty() ? 0u : srv->queue.front().gid % srv->nslots;
+            for (uint32_t j = 0; j < srv->nslots && !srv->queue.empty(); ++j) {
+                const uint32_t i = (first + j) % srv->nslots;
                 Slot &sl = srv->slots[i];
                 if (sl.busy) continue;
                 std::vector<GraphEntry *> uploads;
                 std::vector<uint64_t *> frees;
-                if (!form_wave(srv, i, uploads, frees)) break;  // the head waits for memory
+                std::vector<cudaGraphExec_t> dead;
+                if (!form_wave(srv, i, uploads, frees, dead)) break;  // the head waits for memory
                 sl.busy = true;
-                sl.finished = false;
                 sl.serial = ++srv->wave_serial;
                 sl.t_admit = now_us(srv->t0);
                 srv->stats.waves += 1;
                 srv->stats.max_wave = std::max<uint64_t>(srv->stats.max_wave, sl.wave.size());
                 srv->stats.queued = srv->queue.size();
                 lock.unlock();
-                const tc_status st = enqueue_wave(srv, i, uploads, frees);
+                const tc_status st = enqueue_wave(srv, i, uploads, frees, dead);
                 if (st != TC_OK) cudaStreamSynchronize(sl.s);  // no callback will come
                 lock.lock();
                 if (st != TC_OK) {
@@ -357,7 +446,28 @@ void worker_main(tc_server *srv)
                 launched = true;
             }
         }
-        if (!launched) srv->work_cv.wait(lock);
+        if (launched) continue;
+        // waves in flight: poll their completion events for up to 2 ms before
+        // sleeping (the host callback of each wave still wakes a sleeping
+        // worker), so that a finished wave and a new request are seen at once
+        bool in_flight = false;
+        for (uint32_t i = 0; i < srv->nslots; ++i) in_flight |= srv->slots[i].busy;
+        if (in_flight && !srv->stop) {
+            const uint64_t seen = srv->arrivals.load(std::memory_order_acquire);
+            const auto until = std::chrono::steady_clock::now() + std::chrono::milliseconds(2);
+            bool progressed = false;
+            lock.unlock();  // busy is written by this thread only
+            while (!progressed && std::chrono::steady_clock::now() < until) {
+                for (uint32_t i = 0; i < srv->nslots && !progressed; ++i)
+                    progressed = srv->slots[i].busy && cudaEventQuery(srv->slots[i].done_ev) == cudaSuccess;
+                progressed |= srv->arrivals.load(std::memory_order_acquire) != seen;
+                if (!progressed) std::this_thread::yield();
+            }
+            cudaGetLastError();
+            lock.lock();
+            if (progressed) continue;
+        }
+        srv->work_cv.wait(lock);
     }
 }
 
@@ -379,6 +489,8 @@ void free_server(tc_server *srv)
     }
     for (auto &g : srv->graphs) {
         if (g->dev) cudaFreeAsync(g->dev, srv->ingest);
+        for (cudaGraphExec_t e : g->exec)
+            if (e) cudaGraphExecDestroy(e);
         if (g->host) cudaFreeHost(g->host);
         if (g->ready) cudaEventDestroy(g->ready);
     }
@@ -388,14 +500,10 @@ void free_server(tc_server *srv)
     }
     for (uint32_t i = 0; i < srv->nslots; ++i) {
         Slot &sl = srv->slots[i];
-        cudaFreeHost(sl.h_eoff);
-        cudaFreeHost(sl.h_thr);
-        cudaFreeHost(sl.h_seed_mix);
-        cudaFreeHost(sl.h_src);
-        cudaFreeHost(sl.h_voff);
-        cudaFreeHost(sl.h_p);
+        cudaFreeHost(sl.h_params);
         cudaFreeHost(sl.h_res);
         cudaFreeHost(sl.h_st);
+        if (sl.done_ev) cudaEventDestroy(sl.done_ev);
         if (sl.s) cudaStreamDestroy(sl.s);
     }
     for (void *p : srv->allocs) cudaFree(p);
@@ -443,27 +551,26 @@ tc_status tc_server_create(uint64_t budget_bytes, uint32_t slots, uint64_t slot_
         Slot &sl = srv->slots[i];
         srv->nslots = i + 1;
         srv->cb[i] = CallbackCtx{srv, i};
-        if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done_ev, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             free_server(srv);
             return TC_ECUDA;
         }
-        const uint64_t k = slot_requests;
-        if (!pinned(&sl.h_eoff, k + 1) || !pinned(&sl.h_thr, k) || !pinned(&sl.h_seed_mix, k) ||
-            !pinned(&sl.h_src, k) || !pinned(&sl.h_voff, k + 1) || !pinned(&sl.h_p, k) || !pinned(&sl.h_res, k) ||
-            !pinned(&sl.h_st, 1)) {
+        const uint64_t k = slot_requests, pbytes = wave_layout((uint32_t)k).bytes;
+        if (!pinned(&sl.h_params, pbytes) || !pinned(&sl.h_res, k) || !pinned(&sl.h_st, 1)) {
             free_server(srv);
             return TC_ENOMEM;
         }
-        void *dsrc = nullptr;
-        if (cudaMalloc(&dsrc, k * 8) != cudaSuccess) {
+        void *dparams = nullptr;
+        if (cudaMalloc(&dparams, pbytes) != cudaSuccess) {
             cudaGetLastError();
             free_server(srv);
             return TC_ENOMEM;
         }
-        srv->allocs.push_back(dsrc);
-        srv->slot_bytes += k * 8;
-        sl.d_src = (const uint64_t **)dsrc;
+        srv->allocs.push_back(dparams);
+        srv->slot_bytes += pbytes;
+        sl.d_params = (unsigned char *)dparams;
         if (!union_scratch_alloc(sl.u, slot_edges, slot_vertices, slot_requests, srv->allocs, srv->slot_bytes)) {
             free_server(srv);
             return TC_ENOMEM;
@@ -643,6 +750,7 @@ tc_status tc_server_submit(tc_server *srv, uint32_t gid, double p, uint64_t seed
         rec.info.t_submit_us = t;
         srv->records.emplace(id, rec);
         srv->queue.push_back(Req{id, gid, p, seed, t});
+        srv->arrivals.fetch_add(1, std::memory_order_release);
         ++srv->stats.submitted;
         srv->stats.queued = srv->queue.size();
         *ticket = id;

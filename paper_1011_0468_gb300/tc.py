@@ -63,7 +63,7 @@ _TRIPLE_MODES = {"simple": TC_TRIPLES_SIMPLE, "hybrid": TC_TRIPLES_HYBRID}
 
 class tc_schedule(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint32) for k in ("warp_max", "seg_w", "seg_b", "seg_l", "work_w", "work_b", "work_l",
-                                               "run_b")]
+                                               "run_b", "mid_max", "lookup")]
 
 
 class tc_stream_result(ctypes.Structure):
@@ -103,6 +103,7 @@ SIGNATURES = [
     ("tc_graph_set_partition", ctypes.c_int, [_vp, ctypes.c_int]),
     ("tc_graph_set_schedule", ctypes.c_int, [_vp, ctypes.POINTER(tc_schedule)]),
     ("tc_graph_get_schedule", ctypes.c_int, [_vp, ctypes.POINTER(tc_schedule)]),
+    ("tc_graph_autotune", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_char_p, ctypes.c_uint32]),
     ("tc_graph_timing_drain", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32]),
     ("tc_count", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(tc_result)]),
     ("tc_count_async", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp, _vp]),
@@ -402,6 +403,12 @@ class Graph:
         cur.update(kw)
         s = tc_schedule(**cur)
         _check(lib().tc_graph_set_schedule(self.handle, ctypes.byref(s)), "tc_graph_set_schedule")
+
+    def autotune(self, p: float, seed: int) -> str:
+        """tc_graph_autotune: time schedules at (p, seed), keep the fastest."""
+        desc = ctypes.create_string_buffer(512)
+        _check(lib().tc_graph_autotune(self.handle, p, seed & 0xFFFFFFFFFFFFFFFF, desc, 512), "tc_graph_autotune")
+        return desc.value.decode()
 
     def set_core_ranks(self, ranks: int):
         """Dense core of the later counts (tc_graph_set_core_ranks): < 0 chosen

@@ -79,7 +79,8 @@ def test_autotuned_schedule_gives_identical_counts(tc):
     with tc.Batch(graphs) as b:
         before = b.count(p, seed)
         desc = b.autotune(p, seed)
-        assert "warp_max=" in desc
+        assert "warp_max=" in desc and "mid_max=" in desc
+        assert "warp per owner" in desc and ("hash set" in desc or "binary search" in desc)
         after = b.count(p, seed)
     for key in KEYS:
         assert np.array_equal(before[key], after[key]), key

@@ -189,3 +189,29 @@ def test_sweep_adaptive_and_auto_counts():
         assert p_used == oracle.suggest_p(len(e), n, pilot["estimate"], 0.1)
         want = oracle.run(e, n, p_used, 12)
         assert all(got[k] == want[k] for k in KEYS)
+
+
+def test_schedules_and_strategies_give_identical_counts():
+    """Every owner-bucket strategy (hash set or binary search of the sorted
+    row, per block kernel), both mid / large splits and the item sizes give
+    the oracle's counts; tc_graph_autotune keeps a schedule that does too."""
+    tc = _tc()
+    e, n = gen.planted_core(40000, 2500, 0.9, 300000, 2), 40000  # owners above 1024 and below
+    with tc.Graph(e, n) as g:
+        want = {p: oracle.run(e, n, p, 5) for p in (1.0, 0.4)}
+        for sched in (dict(lookup=1), dict(lookup=2), dict(lookup=3), dict(mid_max=512),
+                      dict(mid_max=512, lookup=3, warp_max=64), dict(seg_l=1024, seg_b=256, seg_w=256)):
+            g.set_schedule()
+            g.set_schedule(**sched)
+            for p in (1.0, 0.4):
+                got = g.count(p, 5)
+                assert all(got[k] == want[p][k] for k in KEYS), (sched, p)
+        g.set_schedule()
+        desc = g.autotune(1.0, 5)
+        assert "warp per owner" in desc and ("hash set" in desc or "binary search" in desc)
+        got = g.count(0.4, 5)
+        assert all(got[k] == want[0.4][k] for k in KEYS)
+        s = g.schedule()
+        assert 512 <= s["mid_max"] <= 1024 and s["lookup"] <= 3
+        with pytest.raises(tc.TCError):
+            g.set_schedule(mid_max=256)
