@@ -521,7 +521,30 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
         }
         uint64_t *keys = (uint64_t *)g->alloc(m_in * 8);
         if (!keys) { free_graph(g); return TC_ENOMEM; }
-        canon_keys(dpairs, m_in, n, keys, g->st, s, g->deg);  // full degrees if the list is canonical
+        // the degrees are counted on the way only when the list may be
+        // canonical already (then they are the full degrees); a prefix out of
+        // order shows it is not, and the degrees are taken after deduplication
+        bool maybe_canonical = true;
+        {
+            const uint64_t cnt = std::min<uint64_t>(m_in, 1u << 16);
+            std::vector<uint32_t> head;
+            const uint32_t *hp = edges;
+            if (edges_on_device) {
+                head.resize(2 * cnt);
+                if (cudaMemcpyAsync(head.data(), edges, cnt * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess) {
+                    cudaGetLastError();
+                    free_graph(g);
+                    return TC_ECUDA;
+                }
+                hp = head.data();
+            }
+            for (uint64_t i = 0; i < cnt && maybe_canonical; ++i) {
+                const uint32_t a = hp[2 * i], b = hp[2 * i + 1];
+                maybe_canonical = a < b && (i == 0 || hp[2 * i - 2] < a || (hp[2 * i - 2] == a && hp[2 * i - 1] < b));
+            }
+        }
+        canon_keys(dpairs, m_in, n, keys, g->st, s, maybe_canonical ? g->deg : nullptr);
         cudaMemcpyAsync(g->st_host, g->st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); free_graph(g); return TC_ECUDA; }
         if (tmp_pairs) g->release(tmp_pairs);

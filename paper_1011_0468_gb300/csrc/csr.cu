@@ -804,10 +804,9 @@ __device__ __forceinline__ void scatter_edge(const ScatterArgs &a, bool live, ui
                 const uint32_t q = atomicAdd(a.cursor + hot_index(v, a.hbits), 1u);
                 const uint32_t after = __ldg(a.rowptr + u + 1) - k - 1;
                 a.inlist[q] = make_uint2(pos, after | ((uint32_t)__ldg(a.heavy + u) << 31));
-            } else if (dv >= 1) {  // entry: v's padded row, d+(v) | v's flag << 31 (if u is heavy)
+            } else if (dv >= 1) {  // entry: v, d+(v) | v's flag << 31 (if u is heavy)
                 out = true;
-                ev = make_uint2(__ldg(a.rowptr + v) + __ldg(a.padoff + v),
-                                dv | (__ldg(a.heavy + u) ? (uint32_t)__ldg(a.heavy + v) << 31 : 0u));
+                ev = make_uint2(v, dv | (__ldg(a.heavy + u) ? (uint32_t)__ldg(a.heavy + v) << 31 : 0u));
             }
         }
     }

@@ -238,24 +238,25 @@ struct PairCtx {
 
 // Partner of owner x (heavy flag hx): the chunk range of the part of the
 // partner's padded out-list to stream and whether both endpoints of the pair
-// are heavy (hh), from its list entry e (csr.cu).  Out-list partner y: e.x is
-// the padded start of y's row, e.y = d+(y) with y's heavy flag in bit 31.
+// are heavy (hh), from its list entry e (csr.cu).  Out-list partner y: e.x = y
+// (its padded row starts at ptrp[y]), e.y = d+(y) with y's heavy flag in bit 31.
 // In-list partner: e.x is the padded position of x in the partner's row, e.y
 // the number of entries after it (>= 1), with the partner's heavy flag in
 // bit 31.  The range is empty when the pair is
 // resolved by the other endpoint, closes no triangle, or (dense) can close
 // no triangle with a light vertex.  Also counts the streamed list entries
 // into the tally.
-__device__ __forceinline__ void partner_of(const PairCtx &pc, uint32_t hx, uint32_t x, bool is_out, uint2 e,
-                                           uint32_t &c0, uint32_t &nc, uint32_t &hh, Tally &t)
+__device__ __forceinline__ void partner_of(const uint32_t *__restrict__ ptrp, const PairCtx &pc, uint32_t hx,
+                                           uint32_t x, bool is_out, uint2 e, uint32_t &c0, uint32_t &nc, uint32_t &hh,
+                                           Tally &t)
 {
     uint32_t len, b;
-    if (is_out) {  // pair (x -> y): e.x is the padded start of y's row, e.y = d+(y) | y's heavy flag << 31
+    if (is_out) {  // pair (x -> y): e.x = y, e.y = d+(y) | y's heavy flag << 31
         // (the compaction appended it only for 1 <= d+(y) <= d+(x) and a row of
         // x that goes on past y, and never a pair both of whose ends the dense
         // block counts)
         len = x < pc.core_lo ? e.y & 0x7fffffffu : 0u;
-        c0 = e.x >> 2;
+        c0 = (__ldg(ptrp + e.x) & ~3u) >> 2;
         nc = (len + 3) >> 2;
         b = 0;
         hh = hx ? e.y >> 31 : 0u;
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(PW_THREADS, 4) k_probe_warp(const uint32_t *__
                         const bool is_out = j < oc;
                         const uint2 e = is_out ? __ldg(olist + s_ob[w][L] + j) : __ldg(inlist + s_ib[w][L] + j - oc);
                         ti = s_ti[w][L];
-                        partner_of(pc, dh >> 31, s_x[w][L], is_out, e, c0, nc, hh, t);
+                        partner_of(ptrp, pc, dh >> 31, s_x[w][L], is_out, e, c0, nc, hh, t);
                     }
                     stream_chunks<true>(col4, BucketSet{tab, 0, 0}, tab, c0, nc, hh, ti, s_base[w], s_tinfo[w], pc, t);
                     before += __popc(sts);
@@ -703,7 +704,7 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
             if (q < per && j < p1) {
                 const bool is_out = j < oc;
                 const uint2 e = is_out ? __ldg(olist + ob + j) : __ldg(inlist + ib + j - oc);
-                partner_of(pc, hx, x, is_out, e, c0, nc, hh, t);
+                partner_of(ptrp, pc, hx, x, is_out, e, c0, nc, hh, t);
             }
             pc0[q] = c0;
             pncc[q] = (nc << 1) | hh;

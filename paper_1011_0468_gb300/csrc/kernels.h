@@ -116,7 +116,7 @@ struct RowsArgs {
     uint32_t *colp;              // [colp_capacity(n, m)] padded columns
     uint2 *inlist;               // [m] in-list entries (source, padded position of the edge in its row)
     uint2 *olist;                // [m] out-lists: the live out-partners v of x at olist[rowptr[x] ..], each
-                                 // as (padded start of v's row, d+(v) | v's heavy flag << 31 when x is heavy)
+                                 // as (v, d+(v) | v's heavy flag << 31 when x is heavy)
     uint32_t *ocnt;              // [n] their number
     uint32_t *keepw;             // [ceil(m / 32)] keep bits
     uint32_t *tile_cnt;          // [ceil(m / RX_TILE) + 1]
