@@ -821,6 +821,67 @@ __device__ __forceinline__ void scatter_edge(const ScatterArgs &a, bool live, ui
     }
 }
 
+// The same for N kept-or-not edges of a thread at once, in phases: every
+// edge's key and the random reads it needs, then the in-list cursor atomics,
+// then the writes, so that the reads and atomics of the N edges are in flight
+// together instead of one edge's chain after another.
+template <int N>
+__device__ __forceinline__ void scatter_edges(const ScatterArgs &a, const bool (&live)[N], const uint64_t (&i)[N],
+                                              const uint32_t (&k)[N], unsigned lt)
+{
+    uint32_t u[N], v[N], pos[N], du[N], dv[N], row_end[N];
+    bool cand[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        u[j] = v[j] = pos[j] = du[j] = dv[j] = row_end[j] = 0;
+        cand[j] = false;
+        if (live[j]) {
+            const uint64_t r = ld_stream_u64(a.rel + i[j]);
+            u[j] = (uint32_t)(r >> 32);
+            v[j] = (uint32_t)r;
+            pos[j] = k[j] + __ldg(a.padoff + u[j]);
+            row_end[j] = __ldg(a.rowptr + u[j] + 1);
+            const bool dense_pair =
+                u[j] >= a.core_lo || (v[j] >= a.lim && __ldg(a.heavy + u[j]) && __ldg(a.heavy + v[j]));
+            cand[j] = !dense_pair && k[j] + 1 < row_end[j];  // so d+(u) >= 2
+            if (cand[j]) {
+                du[j] = __ldg(a.dplus + u[j]);
+                dv[j] = __ldg(a.dplus + v[j]);
+            }
+        }
+    }
+    uint32_t q[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        q[j] = 0;
+        if (cand[j] && du[j] < dv[j]) q[j] = atomicAdd(a.cursor + hot_index(v[j], a.hbits), 1u);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        if (live[j]) a.colp[pos[j]] = v[j];
+        bool out = false;
+        uint2 ev = make_uint2(0, 0);
+        if (cand[j]) {
+            const uint32_t hu = __ldg(a.heavy + u[j]);
+            if (du[j] < dv[j]) {  // entry: position of v in u's row; entries after it | u's heavy flag << 31
+                a.inlist[q[j]] = make_uint2(pos[j], (row_end[j] - k[j] - 1) | (hu << 31));
+            } else if (dv[j] >= 1) {  // entry: v, d+(v) | v's flag << 31 (if u is heavy)
+                out = true;
+                ev = make_uint2(v[j], dv[j] | (hu ? (uint32_t)__ldg(a.heavy + v[j]) << 31 : 0u));
+            }
+        }
+        const unsigned act = __ballot_sync(FULL, out);
+        if (out) {
+            const unsigned grp = __match_any_sync(act, u[j]);  // lanes of this warp with the same row
+            const int lead = __ffs(grp) - 1;
+            uint32_t qo = 0;
+            if ((int)lane_id() == lead) qo = atomicAdd(a.ocnt + u[j], (unsigned)__popc(grp));
+            qo = __shfl_sync(grp, qo, lead) + __popc(grp & lt);
+            a.olist[__ldg(a.rowptr + u[j]) + qo] = ev;
+        }
+    }
+}
+
 // Position of the k-th (from 0) set bit of w; k < popcount(w).
 __device__ __forceinline__ uint32_t nth_set_bit(uint32_t w, uint32_t k)
 {
@@ -897,12 +958,21 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
                 scatter_edge(a, live, i, base + e, lt);
             }
         } else {
-#pragma unroll 4
-            for (int j = 0; j < RX_ITEMS; ++j) {
-                const uint32_t wi = j * 8 + warp;  // word of this warp's 32 edges
-                const uint32_t word = s_word[wi];
-                const uint64_t i = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
-                scatter_edge(a, (word >> lane) & 1u, i, base + s_pre[wi] + __popc(word & lt), lt);
+            constexpr int NB = 4;  // edges of a thread in flight together
+            for (int j0 = 0; j0 < RX_ITEMS; j0 += NB) {
+                bool live[NB];
+                uint64_t i[NB];
+                uint32_t k[NB];
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj) {
+                    const int j = j0 + jj;
+                    const uint32_t wi = j * 8 + warp;  // word of this warp's 32 edges
+                    const uint32_t word = s_word[wi];
+                    live[jj] = (word >> lane) & 1u;
+                    i[jj] = tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x;
+                    k[jj] = base + s_pre[wi] + __popc(word & lt);
+                }
+                scatter_edges<NB>(a, live, i, k, lt);
             }
         }
         __syncthreads();  // s_word / s_pre are rewritten for the next tile
