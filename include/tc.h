@@ -197,10 +197,18 @@ tc_status tc_graph_set_core_ranks(tc_graph *g, int64_t ranks);
      mid_max             owners with warp_max < d+ <= mid_max go to the
                          128-thread blocks, larger ones to the 1024-thread
                          blocks (512 .. 1024)
-     lookup              membership test of the block kernels: bit 0 for the
-                         128-thread blocks, bit 1 for the 1024-thread blocks;
-                         0 a hash set of the owner's list in shared memory, 1
-                         a binary search of the owner's sorted row
+     lookup              membership test of the block kernels (0 .. 15): bits
+                         0 and 2 for the 128-thread blocks, bits 1 and 3 for
+                         the 1024-thread blocks.  Bit 0 / 1: a binary search
+                         of the owner's sorted row.  Else bit 2 / 3: a bitmap
+                         in shared memory of the owner's rank window (from
+                         the owner to its largest out-neighbour).  Else a
+                         hash set of the owner's list in shared memory.
+                         Where the bitmap or the set does not fit the
+                         table's memory, the binary search.  The default
+                         is 8 (bitmaps for the 1024-thread blocks) on
+                         graphs where no window of those owners can exceed
+                         their table, else 0.
    Results never depend on the schedule; only the time does.
    tc_graph_set_schedule(g, NULL) restores the default.  TC_EINVAL for a
    NULL graph or a value out of range. */
@@ -216,10 +224,11 @@ tc_status tc_graph_set_schedule(tc_graph *g, const tc_schedule *s);
 tc_status tc_graph_get_schedule(const tc_graph *g, tc_schedule *out);
 /* Choose the graph's schedule by timing counts at (p, seed): a coordinate
    search over warp_max (64 / 128 / 256), mid_max (512 / 1024), seg_w,
-   seg_b (256 / 512), seg_l (1024 / 2048 / 4096) and lookup (0 .. 3), from
-   the current schedule, keeping each improvement.  The choice stays with the
+   seg_b (256 / 512), seg_l (1024 / 2048 / 4096) and the membership test
+   of each block kernel (hash set, bitmap, binary search), from the current
+   schedule, keeping each improvement.  The choice stays with the
    graph; desc (may be NULL) receives it with the strategy of each owner
-   bucket.  Runs about 16 x 3 counts; results never depend on it.  TC_EINVAL
+   bucket.  Runs about 18 x 3 counts; results never depend on it.  TC_EINVAL
    for a NULL graph or p outside (0, 1]; TC_ECUDA, TC_ETIMEOUT. */
 tc_status tc_graph_autotune(tc_graph *g, double p, uint64_t seed, char *desc, uint32_t desc_len);
 
@@ -382,8 +391,8 @@ tc_status tc_batch_count(tc_batch *b, const double *p, const uint64_t *seed, tc_
  * (p, seed): the owners' split between one warp and one block (warp_max 64 /
  * 128 / 256), between the 128- and 1024-thread blocks (mid_max 512 / 1024),
  * the work-item sizes of the warp and mid-owner kernels, and the membership
- * test of each block kernel (a shared-memory hash set or a binary search of
- * the owner's sorted row).  The fastest is kept for the batch's later counts
+ * test of each block kernel (a shared-memory hash set, a shared-memory bitmap
+ * of the owner's rank window, or a binary search of the owner's sorted row).  The fastest is kept for the batch's later counts
  * and remembered for batches of the same shape (log2 of edges, vertices,
  * graphs and average degree) created later in this process.  Counts are
  * identical under every schedule.  desc (may be NULL) receives the choice,

@@ -165,6 +165,7 @@ struct tc_graph {
     cudaEvent_t join_in = nullptr, join_out = nullptr;  // order a count on a caller's stream with the graph's
     int partition = TC_PARTITION_SAMPLED;  // which graph the degree partition splits
     IsectConfig cfg;            // schedule of the intersection kernels
+    uint32_t lookup_auto = LOOKUP_DEFAULT;  // its default lookup field on this graph
     TripleBuffers tri;          // triple sampling (built by the first tc_count_triples)
     bool tri_ready = false;
     std::vector<void *> allocs;
@@ -290,6 +291,7 @@ RowsArgs rows_of(tc_graph *g, uint64_t seed_mix, uint64_t thr, uint64_t m_lo)
     a.n = g->n;
     a.seed_mix = seed_mix;
     a.thr = thr;
+    a.scatter4 = thr >= (3ull << 51);  // p >= 0.75: nearly every compaction tile is full
     a.deg = g->deg;
     a.rowptr = g->rowptr;
     a.inptr = g->inptr;
@@ -641,6 +643,21 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     uint64_t slots = 8192;
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;
     g->smem_bytes = (int)(slots * 4);
+    // the rank-window bitmaps of the large owners by default when none can
+    // exceed the table: an owner x of that kernel has d+(x) > 512 in any
+    // sample, and every vertex ranked above it has a full degree >= that of
+    // x, so its window holds at most #{v : deg(v) > 512} ranks
+    {
+        unsigned long long *cnt = (unsigned long long *)g->alloc(8), wide = ~0ull;
+        if (cnt) {
+            count_above(g->deg, n, 512, cnt, s);
+            cudaMemcpyAsync(&wide, cnt, 8, cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); free_graph(g); return TC_ECUDA; }
+            g->release(cnt);
+        }
+        if (wide <= slots * 32) g->lookup_auto |= LOOKUP_BITMAP_LARGE;
+        g->cfg.lookup = g->lookup_auto;
+    }
     // dense heavy block: at most 2 m^(1/2) heavy vertices, padded to the
     // 128-row tile and capped at 32768 (2 x 1 GiB of fp8).  Graphs below
     // 2^20 edges, or without room for the block, have the intersection
@@ -731,12 +748,13 @@ tc_status tc_graph_set_schedule(tc_graph *g, const tc_schedule *s)
     if (!g) return TC_EINVAL;
     if (!s) {
         g->cfg = IsectConfig{};
+        g->cfg.lookup = g->lookup_auto;
         return TC_OK;
     }
     auto pow2_in = [](uint32_t v, uint32_t lo, uint32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; };
     if (s->warp_max < 32 || s->warp_max > 256 || !pow2_in(s->seg_w, 64, 1024) || !pow2_in(s->seg_b, 256, 512) ||
         !pow2_in(s->seg_l, 256, 4096) || s->work_w < 4096 || s->work_b < 4096 || s->work_l < 4096 || s->run_b < 1 ||
-        s->run_b > 8 || s->mid_max < 512 || s->mid_max > 1024 || s->lookup > 3)
+        s->run_b > 8 || s->mid_max < 512 || s->mid_max > 1024 || s->lookup > 15)
         return TC_EINVAL;
     IsectConfig c;
     c.warp_max = s->warp_max;
@@ -786,22 +804,33 @@ tc_status tc_graph_autotune(tc_graph *g, double p, uint64_t seed, char *desc, ui
                          {&IsectConfig::mid_max, {512, 1024}},
                          {&IsectConfig::seg_w, {256, 512}},
                          {&IsectConfig::seg_b, {256, 512}},
-                         {&IsectConfig::seg_l, {1024, 2048, 4096}},
-                         {&IsectConfig::lookup, {0, 1, 2, 3}}};
+                         {&IsectConfig::seg_l, {1024, 2048, 4096}}};
     IsectConfig best = g->cfg;
     float best_ms = 1e30f;
     tc_status st = time_of(best, best_ms);
+    auto consider = [&](const IsectConfig &c) {
+        float ms = 0;
+        st = time_of(c, ms);
+        if (st == TC_OK && ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    };
     for (const Axis &a : axes) {
         for (uint32_t v : a.values) {
             if (st != TC_OK || best.*(a.field) == v) continue;
             IsectConfig c = best;
             c.*(a.field) = v;
-            float ms = 0;
-            st = time_of(c, ms);
-            if (st == TC_OK && ms < best_ms) {
-                best_ms = ms;
-                best = c;
-            }
+            consider(c);
+        }
+    }
+    // the membership test of each block kernel: hash set, bitmap, binary search
+    for (int k = 0; k < 2; ++k) {
+        for (uint32_t v : {0u, 4u, 1u}) {
+            IsectConfig c = best;
+            c.lookup = lookup_with(best.lookup, k, v);
+            if (st != TC_OK || c.lookup == best.lookup) continue;
+            consider(c);
         }
     }
     cudaEventDestroy(e0);
@@ -814,8 +843,7 @@ tc_status tc_graph_autotune(tc_graph *g, double p, uint64_t seed, char *desc, ui
                  "warp_max=%u mid_max=%u seg_w=%u seg_b=%u seg_l=%u lookup=%u: warp per owner (d+<=%u, hash sets), "
                  "128-thread block per owner (d+<=%u, %s), 1024-thread block per owner (%s); count_ms=%.3f",
                  best.warp_max, best.mid_max, best.seg_w, best.seg_b, best.seg_l, best.lookup, best.warp_max,
-                 best.mid_max, (best.lookup & 1u) ? "binary search" : "hash set",
-                 (best.lookup & 2u) ? "binary search" : "hash set", best_ms);
+                 best.mid_max, lookup_name(best.lookup, 0), lookup_name(best.lookup, 1), best_ms);
     return TC_OK;
 }
 

@@ -557,22 +557,32 @@ tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, 
         std::vector<uint32_t> values;
     };
     const Axis axes[] = {{&IsectConfig::warp_max, {64, 128, 256}}, {&IsectConfig::mid_max, {512, 1024}},
-                         {&IsectConfig::seg_w, {256, 512}},       {&IsectConfig::seg_b, {256, 512}},
-                         {&IsectConfig::lookup, {0, 1, 2, 3}}};
+                         {&IsectConfig::seg_w, {256, 512}},       {&IsectConfig::seg_b, {256, 512}}};
     IsectConfig best = b->cfg;
     float best_ms = 1e30f;
     st = time_of(best, best_ms);
+    auto consider = [&](const IsectConfig &c) {
+        float ms = 0;
+        st = time_of(c, ms);
+        if (st == TC_OK && ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    };
     for (const Axis &a : axes) {
         for (uint32_t v : a.values) {
             if (st != TC_OK || best.*(a.field) == v) continue;
             IsectConfig c = best;
             c.*(a.field) = v;
-            float ms = 0;
-            st = time_of(c, ms);
-            if (st == TC_OK && ms < best_ms) {
-                best_ms = ms;
-                best = c;
-            }
+            consider(c);
+        }
+    }
+    for (int k = 0; k < 2; ++k) {  // the membership test of each block kernel
+        for (uint32_t v : {0u, 4u, 1u}) {
+            IsectConfig c = best;
+            c.lookup = lookup_with(best.lookup, k, v);
+            if (st != TC_OK || c.lookup == best.lookup) continue;
+            consider(c);
         }
     }
     cudaEventDestroy(e0);
@@ -590,8 +600,7 @@ tc_status tc_batch_autotune(tc_batch *b, const double *p, const uint64_t *seed, 
                  "warp_max=%u seg_w=%u seg_b=%u mid_max=%u lookup=%u: warp per owner (d+<=%u, hash sets), "
                  "128-thread block per owner (d+<=%u, %s), 1024-thread block per owner (%s); best_ms=%.3f",
                  best.warp_max, best.seg_w, best.seg_b, best.mid_max, best.lookup, best.warp_max, best.mid_max,
-                 (best.lookup & 1u) ? "binary search" : "hash set", (best.lookup & 2u) ? "binary search" : "hash set",
-                 best_ms);
+                 lookup_name(best.lookup, 0), lookup_name(best.lookup, 1), best_ms);
     return TC_OK;
 }
 

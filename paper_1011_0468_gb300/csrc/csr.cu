@@ -506,6 +506,23 @@ __global__ void k_full_indeg(const uint32_t *__restrict__ perm, const uint32_t *
         ind[x] = x < n ? __ldg(deg_orig + __ldg(perm + x)) - outd[x] : 0u;
 }
 
+__global__ void k_count_above(const uint32_t *__restrict__ deg, uint32_t n, uint32_t thr,
+                              unsigned long long *__restrict__ out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t c = 0;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) c += deg[v] > thr;
+    c = __reduce_add_sync(FULL, c);
+    if (lane_id() == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+
+void count_above(const uint32_t *deg, uint32_t n, uint32_t thr, unsigned long long *out, cudaStream_t s)
+{
+    cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (n) k_count_above<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(deg, n, thr, out);
+    note_launch();
+}
+
 void static_rows(const uint64_t *rel, uint64_t m, uint32_t n, const uint32_t *perm, const uint32_t *deg_orig,
                  uint32_t *frow, uint32_t *inres, uint32_t *scan, cudaStream_t s)
 {
@@ -908,6 +925,7 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint32_t w, uint32_t k)
 // most half its edges kept hands its kept edges to the threads one after
 // another (the word and bit of kept edge e found from the word prefixes)
 // instead of one edge slot per thread.
+template <int NB>
 __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict__ rel, uint64_t m,
                                                       const uint32_t *__restrict__ keepw,
                                                       const uint32_t *__restrict__ tile_off,
@@ -957,8 +975,15 @@ __global__ void __launch_bounds__(256) k_rows_scatter(const uint64_t *__restrict
                 }
                 scatter_edge(a, live, i, base + e, lt);
             }
-        } else {
-            constexpr int NB = 4;  // edges of a thread in flight together
+        } else if (NB == 1) {
+#pragma unroll 4
+            for (int j = 0; j < RX_ITEMS; ++j) {
+                const uint32_t wi = j * 8 + warp;  // word of this warp's 32 edges
+                const uint32_t word = s_word[wi];
+                scatter_edge(a, (word >> lane) & 1u, tile * RX_TILE + (uint64_t)j * 256 + threadIdx.x,
+                             base + s_pre[wi] + __popc(word & lt), lt);
+            }
+        } else {  // NB edges of a thread in flight together
             for (int j0 = 0; j0 < RX_ITEMS; j0 += NB) {
                 bool live[NB];
                 uint64_t i[NB];
@@ -1020,10 +1045,10 @@ void build_rows(const RowsArgs &a, cudaStream_t s)
     }
     if (a.m > 0) {
         const uint64_t nt = ceil_div(a.m, RX_TILE);
-        k_rows_scatter<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.m, a.keepw, a.tile_cnt, a.ptrp, a.rowptr,
-                                                                  a.deg, a.colp, a.spread, hb,
-                                                                  a.inlist, a.olist, a.ocnt, a.heavy, a.core_base,
-                                                                  a.st);
+        auto kern = a.scatter4 ? k_rows_scatter<4> : k_rows_scatter<1>;
+        kern<<<grid_for(nt, 1, 152 * 8), 256, 0, s>>>(a.rel, a.m, a.keepw, a.tile_cnt, a.ptrp, a.rowptr, a.deg, a.colp,
+                                                       a.spread, hb, a.inlist, a.olist, a.ocnt, a.heavy, a.core_base,
+                                                       a.st);
         note_launch();
     }
     k_pad_finish<<<grid_for(n1, 256, 152 * 8), 256, 0, s>>>(a.rowptr, a.n, a.ptrp, a.colp, a.spread, hb, a.inend);

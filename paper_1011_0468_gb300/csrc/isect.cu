@@ -186,6 +186,22 @@ __device__ __forceinline__ uint32_t table_slots(uint32_t d, uint32_t cap)
 // Shift of the bucket hash for a table of `slots` slots (slots / 2 buckets).
 __device__ __forceinline__ uint32_t bucket_shift(uint32_t slots) { return 32u - (31u - __clz(slots >> 1)); }
 
+// Bitmap of an owner's list over its rank window: vertex base + i is in the
+// set iff bit i of bm is set (i < bits).  The rows are sorted by rank, so an
+// owner x with largest out-neighbour `last` needs last - x bits from base =
+// x + 1; every streamed entry is ranked above x (or is SENT, or an entry of
+// an in-partner's row before x, which all fall outside the window).  One
+// 4-byte shared load and no probe loop per lookup.
+struct BitmapSet {
+    const uint32_t *bm;
+    uint32_t base, bits;
+    __device__ __forceinline__ uint32_t contains(uint32_t y) const
+    {
+        const uint32_t o = y - base;
+        return o < bits ? (bm[o >> 5] >> (o & 31u)) & 1u : 0u;
+    }
+};
+
 // Fallback for rows whose hash set does not fit on chip: binary search of
 // the sorted row in global memory.
 struct SortedRow {
@@ -615,9 +631,13 @@ __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, cons
 // thread sets up its share of the partners; the live ones are compacted
 // into shared memory with the prefix of their chunk counts, and the warps
 // take the item's chunk sequence UNIT chunks at a time from a shared
-// counter, so they finish within one unit of each other.  The owner's hash
-// set sits in dynamic shared memory (tab_slots slots).
-template <bool DYN>
+// counter, so they finish within one unit of each other.  The owner's set
+// sits in dynamic shared memory (tab_slots 4-byte slots): a bitmap of its
+// rank window (BM) or a hash set, or, where that does not fit or the
+// schedule asks for it, the owner's sorted row is binary-searched instead.
+// (A kernel holds two of the three lookups: with all three inlined into the
+// streaming loop the 64-register budget spills.)
+template <bool DYN, bool BM>
 __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8) k_probe_block(const uint32_t *__restrict__ ptrp,
                                                                       const uint32_t *__restrict__ col,
                                                                       const uint32_t *__restrict__ rowptr,
@@ -679,15 +699,34 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
         const PaddedRow row = padded_row(ptrp, x);
         const uint32_t d = row.d;
         const uint32_t hx = heavy[x];
-        // the owner's hash set, unless the schedule asks this kernel for a
-        // binary search of the sorted row (or the set would not fit)
-        const uint32_t slots = ((cfg.lookup >> (DYN ? 1 : 0)) & 1u) ? 0u : table_slots(d, tab_slots);
+        // the owner's set: a binary search of the sorted row if the schedule
+        // asks this kernel for one; else (BM) a bitmap of the rank window if
+        // it fits the table's memory, or (!BM) a hash set if it fits; else
+        // the binary search
+        const bool bsearch = (cfg.lookup >> (DYN ? 1 : 0)) & 1u;
+        uint32_t bits = 0;
+        if (BM && !bsearch) {
+            bits = __ldg(col + row.beg + d - 1) - x;  // up to the largest out-neighbour (d >= 2)
+            if (bits > tab_slots * 32u || (uint64_t)x + 1 + bits > (uint64_t)SENT) bits = 0;
+        }
+        const bool bitmap = bits != 0;
+        const uint32_t slots = BM || bsearch ? 0u : table_slots(d, tab_slots);
         const BucketSet set{tab, slots ? (slots >> 1) - 1 : 0u, slots ? bucket_shift(slots) : 0u};
-        if (slots && s_built != x) {
-            for (uint32_t i = threadIdx.x; i < (slots >> 1); i += NT) tab[i] = make_uint2(EMPTY, EMPTY);
-            __syncthreads();
-            for (uint32_t i = threadIdx.x; i < d; i += NT)
-                bucket_insert(tab, set.mask, set.shift, __ldg(col + row.beg + i));
+        uint32_t *bm = reinterpret_cast<uint32_t *>(tab);
+        if ((slots || bitmap) && s_built != x) {
+            if (bitmap) {
+                for (uint32_t i = threadIdx.x; i < (bits + 31) / 32; i += NT) bm[i] = 0u;
+                __syncthreads();
+                for (uint32_t i = threadIdx.x; i < d; i += NT) {
+                    const uint32_t o = __ldg(col + row.beg + i) - (x + 1);
+                    atomicOr(bm + (o >> 5), 1u << (o & 31u));
+                }
+            } else {
+                for (uint32_t i = threadIdx.x; i < (slots >> 1); i += NT) tab[i] = make_uint2(EMPTY, EMPTY);
+                __syncthreads();
+                for (uint32_t i = threadIdx.x; i < d; i += NT)
+                    bucket_insert(tab, set.mask, set.shift, __ldg(col + row.beg + i));
+            }
         }
         if (seg == 0 && threadIdx.x == 0) t.table += d;
         const uint32_t ob = rowptr[x], oc = ocnt[x], ib = inptr[x], np = oc + (inend[x] - ib);
@@ -730,7 +769,10 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
             if (lane == 0) u = atomicAdd(&s_next, 1u);
             u = __shfl_sync(FULL, u, 0);
             if (u * UNIT >= total) break;
-            if (slots)
+            if (BM && bitmap)
+                stream_unit<DYN ? NWIN_DYN : NWIN_MID>(col4, BitmapSet{bm, x + 1, bits}, s_c0, s_pre, nlive, total,
+                                                   u * UNIT, pc, t);
+            else if (!BM && slots)
                 stream_unit<DYN ? NWIN_DYN : NWIN_MID>(col4, set, s_c0, s_pre, nlive, total, u * UNIT, pc, t);
             else
                 stream_unit<DYN ? NWIN_DYN : NWIN_MID>(col4, SortedRow{col + row.beg, d}, s_c0, s_pre, nlive, total,
@@ -738,7 +780,7 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
         }
         if (bv.k != 0) flush_graph_counts(t, bv, g);
         __syncthreads();  // every warp is done with this owner
-        if (threadIdx.x == 0) s_built = slots ? x : 0xffffffffu;
+        if (threadIdx.x == 0) s_built = slots || bitmap ? x : 0xffffffffu;
     }
     flush_tally(t, red, st);
 }
@@ -755,14 +797,19 @@ void intersect_prepare(int dyn_smem_bytes)
     cudaGetDevice(&dev);
     const bool known = dev >= 0 && dev < 64;
     if (!known || !mid_set[dev]) {
-        if (cudaFuncSetAttribute(k_probe_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(MID_TAB * 4 + 2 * SEG_B * 4)) == cudaSuccess &&
+        const int mid = (int)(MID_TAB * 4 + 2 * SEG_B * 4);
+        if (cudaFuncSetAttribute(k_probe_block<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mid) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_probe_block<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mid) ==
+                cudaSuccess &&
             known)
             mid_set[dev] = true;
     }
     const int dyn = dyn_smem_bytes + (int)(2 * SEG_L * 4);
     if (!known || dyn > set_bytes[dev]) {
-        if (cudaFuncSetAttribute(k_probe_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) ==
+        if (cudaFuncSetAttribute(k_probe_block<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_probe_block<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) ==
                 cudaSuccess &&
             known)
             set_bytes[dev] = dyn;
@@ -778,15 +825,16 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
                                                 b.items, wm, b.heavy, b.st, b.bv, b.cfg, b.core_base);
     note_launch();
     const uint32_t seg_b = std::min(b.cfg.seg_b, SEG_B), seg_l = std::min(b.cfg.seg_l, SEG_L);
-    k_probe_block<false><<<152 * 8, PB_THREADS, MID_TAB * 4 + 2 * seg_b * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
-                                                                   b.inend, b.inlist, b.items, wm,
-                                                                   b.heavy, b.st, MID_TAB, b.items_cap, b.bv, b.cfg,
-                                                                   b.core_base);
+    auto kmid = (b.cfg.lookup & 4u) ? k_probe_block<false, true> : k_probe_block<false, false>;
+    kmid<<<152 * 8, PB_THREADS, MID_TAB * 4 + 2 * seg_b * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
+                                                                 b.inend, b.inlist, b.items, wm, b.heavy, b.st, MID_TAB,
+                                                                 b.items_cap, b.bv, b.cfg, b.core_base);
     note_launch();
-    k_probe_block<true><<<152, PB_DYN_THREADS, dyn_smem_bytes + 2 * seg_l * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
-                                                                b.inend, b.inlist, b.items, wm,
-                                                                b.heavy, b.st, (uint32_t)(dyn_smem_bytes / 4),
-                                                                b.items_cap, b.bv, b.cfg, b.core_base);
+    auto klarge = (b.cfg.lookup & 8u) ? k_probe_block<true, true> : k_probe_block<true, false>;
+    klarge<<<152, PB_DYN_THREADS, dyn_smem_bytes + 2 * seg_l * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt,
+                                                                      b.inptr, b.inend, b.inlist, b.items, wm, b.heavy,
+                                                                      b.st, (uint32_t)(dyn_smem_bytes / 4),
+                                                                      b.items_cap, b.bv, b.cfg, b.core_base);
     note_launch();
 }
 

@@ -134,6 +134,10 @@ struct RowsArgs {
     // light_lim, or the lower end at or above core_base
     const uint8_t *heavy = nullptr;
     uint32_t core_base = 0xffffffffu;
+    // tiles with more than half their edges kept: scatter four edges of a
+    // thread at a time (pays where nearly every tile is full, p >= 0.75; it
+    // costs occupancy, 54 registers against 40, where most tiles are sparse)
+    bool scatter4 = false;
 };
 // Rank-order rows (relabel) of up to ROW_MID keys are sorted by one warp in
 // registers; longer rows by a block, with global scratch beyond shared memory.
@@ -141,6 +145,8 @@ constexpr uint32_t ROW_MID = 1024;
 // Static rows of a single graph at creation: frow[0..n] (row offsets of rel)
 // and inres[0..n] (in-list reservation offsets: full in-degrees).  perm and
 // deg_orig: rank -> original id and the full degree by original id.
+// *out = the number of v < n with deg[v] > thr.
+void count_above(const uint32_t *deg, uint32_t n, uint32_t thr, unsigned long long *out, cudaStream_t s);
 void static_rows(const uint64_t *rel, uint64_t m, uint32_t n, const uint32_t *perm, const uint32_t *deg_orig,
                  uint32_t *frow, uint32_t *inres, uint32_t *scan, cudaStream_t s);
 
@@ -187,10 +193,16 @@ void build_rows(const RowsArgs &a, cudaStream_t s);
 // one owner then share its hash set); mid_max: owners with warp_max < d+ <=
 // mid_max go to the 128-thread blocks, larger ones to the 1024-thread blocks
 // (512 .. 1024); lookup: how the block kernels test membership in the
-// owner's list, bit 0 for the mid-owner blocks, bit 1 for the large-owner
-// blocks: 0 a shared-memory hash set, 1 a binary search of the owner's
-// sorted row.
+// owner's list, bits 0 and 2 for the mid-owner blocks, bits 1 and 3 for the
+// large-owner blocks: bit 0 / 1 a binary search of the owner's sorted row;
+// else bit 2 / 3 a shared-memory bitmap of the owner's rank window, or the
+// binary search where the window does not fit the table's memory; else a
+// shared-memory hash set, or the binary search where it does not fit.  A
+// graph's default sets bit 3 when no large owner's window can exceed the
+// table (LOOKUP_BITMAP_LARGE, tc_graph_create).
 constexpr uint32_t SEG_MIN = 64;
+constexpr uint32_t LOOKUP_DEFAULT = 0;
+constexpr uint32_t LOOKUP_BITMAP_LARGE = 8;
 struct IsectConfig {
     uint32_t warp_max = 256;
     uint32_t seg_w = 512;
@@ -201,8 +213,18 @@ struct IsectConfig {
     uint32_t work_l = 1u << 25;
     uint32_t run_b = 1;
     uint32_t mid_max = 1024;
-    uint32_t lookup = 0;
+    uint32_t lookup = LOOKUP_DEFAULT;
 };
+
+// The membership test of block kernel k (0: mid owners, 1: large owners)
+// under lookup, for the schedule descriptions; and the lookup field with
+// kernel k's bits set to v (0 hash set, 1 binary search, 4 bitmap).
+inline const char *lookup_name(uint32_t lookup, int k)
+{
+    const uint32_t m = lookup >> k;
+    return (m & 1u) ? "binary search" : ((m & 4u) ? "rank-window bitmap, else binary search" : "hash set");
+}
+inline uint32_t lookup_with(uint32_t lookup, int k, uint32_t v) { return (lookup & ~(5u << k)) | (v << k); }
 
 struct CountBuffers {
     const uint64_t *ekey;   // canonical keys [m]

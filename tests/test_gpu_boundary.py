@@ -192,26 +192,65 @@ def test_sweep_adaptive_and_auto_counts():
 
 
 def test_schedules_and_strategies_give_identical_counts():
-    """Every owner-bucket strategy (hash set or binary search of the sorted
-    row, per block kernel), both mid / large splits and the item sizes give
-    the oracle's counts; tc_graph_autotune keeps a schedule that does too."""
+    """Every owner-bucket strategy (hash set, rank-window bitmap or binary
+    search of the sorted row, per block kernel), both mid / large splits and
+    the item sizes give the oracle's counts; tc_graph_autotune keeps a
+    schedule that does too."""
     tc = _tc()
     e, n = gen.planted_core(40000, 2500, 0.9, 300000, 2), 40000  # owners above 1024 and below
     with tc.Graph(e, n) as g:
         want = {p: oracle.run(e, n, p, 5) for p in (1.0, 0.4)}
-        for sched in (dict(lookup=1), dict(lookup=2), dict(lookup=3), dict(mid_max=512),
-                      dict(mid_max=512, lookup=3, warp_max=64), dict(seg_l=1024, seg_b=256, seg_w=256)):
+        for sched in (dict(lookup=1), dict(lookup=2), dict(lookup=3), dict(lookup=4), dict(lookup=8),
+                      dict(lookup=12), dict(lookup=13), dict(lookup=14), dict(mid_max=512),
+                      dict(mid_max=512, lookup=12, warp_max=32), dict(mid_max=512, lookup=3, warp_max=64),
+                      dict(seg_l=1024, seg_b=256, seg_w=256)):
             g.set_schedule()
             g.set_schedule(**sched)
             for p in (1.0, 0.4):
                 got = g.count(p, 5)
                 assert all(got[k] == want[p][k] for k in KEYS), (sched, p)
+        # no large owner's window can exceed its table here (2500 vertices of
+        # degree > 512): the default takes the bitmaps for those owners
         g.set_schedule()
+        assert g.schedule()["lookup"] == 8
         desc = g.autotune(1.0, 5)
-        assert "warp per owner" in desc and ("hash set" in desc or "binary search" in desc)
+        assert "warp per owner" in desc and any(w in desc for w in ("hash set", "bitmap", "binary search"))
         got = g.count(0.4, 5)
         assert all(got[k] == want[0.4][k] for k in KEYS)
         s = g.schedule()
-        assert 512 <= s["mid_max"] <= 1024 and s["lookup"] <= 3
+        assert 512 <= s["mid_max"] <= 1024 and s["lookup"] <= 15
         with pytest.raises(tc.TCError):
             g.set_schedule(mid_max=256)
+        with pytest.raises(tc.TCError):
+            g.set_schedule(lookup=16)
+
+
+def test_bitmap_window_too_wide_falls_back_to_binary_search():
+    """Owners whose rank window (owner to largest out-neighbour) exceeds the
+    mid-owner table's 131072 bits binary-search their sorted row, the others
+    take the bitmap.  140,000 filler vertices on a circulant graph (i ~ i + 1
+    .. i + 21, degree 42 and up), 50 hubs joined to 20,000 fillers each, and
+    200 owners of degree 40 (38 fillers and 2 hubs): every owner's
+    neighbours rank above it, so with warp_max = 32 it is a mid owner whose
+    window reaches a hub about 140,000 ranks up.  Counts equal the oracle's
+    under the hash sets and under the bitmaps."""
+    tc = _tc()
+    rng = np.random.default_rng(21)
+    nf, nh, no = 140000, 50, 200
+    f0, h0 = no, no + nf  # ids: owners, fillers, hubs
+    i = np.arange(nf)
+    circ = np.stack([np.repeat(i, 21), (np.repeat(i, 21) + np.tile(np.arange(1, 22), nf)) % nf], axis=1) + f0
+    hub = np.stack([np.repeat(np.arange(nh), 20000) + h0, rng.integers(0, nf, nh * 20000) + f0], axis=1)
+    own = np.stack([np.repeat(np.arange(no), 40),
+                    np.concatenate([np.concatenate([rng.choice(nf, 38, replace=False) + f0,
+                                                    rng.choice(nh, 2, replace=False) + h0]) for _ in range(no)])],
+                   axis=1)
+    e, n = gen.canonical(np.concatenate([circ, hub, own])), no + nf + nh
+    with tc.Graph(e, n) as g:
+        for p in (1.0, 0.7):
+            want = oracle.run(e, n, p, 3)
+            assert want["t_light"] > 0
+            for lookup in (0, 12):
+                g.set_schedule(warp_max=32, mid_max=1024, lookup=lookup)
+                got = g.count(p, 3)
+                assert all(got[k] == want[k] for k in KEYS), (p, lookup)
