@@ -204,8 +204,10 @@ tc_status tc_graph_set_core_ranks(tc_graph *g, int64_t ranks);
                          in shared memory of the owner's rank window (from
                          the owner to its largest out-neighbour).  Else a
                          hash set of the owner's list in shared memory.
-                         Where the bitmap or the set does not fit the
-                         table's memory, the binary search.  The default
+                         Where the bitmap does not fit the table's memory,
+                         the hash set (128-thread blocks) or the binary
+                         search (1024-thread blocks); where the set does
+                         not fit, the binary search.  The default
                          is 8 (bitmaps for the 1024-thread blocks) on
                          graphs where no window of those owners can exceed
                          their table, else 0.

@@ -632,11 +632,13 @@ __device__ __forceinline__ void stream_unit(const uint4 *__restrict__ col4, cons
 // into shared memory with the prefix of their chunk counts, and the warps
 // take the item's chunk sequence UNIT chunks at a time from a shared
 // counter, so they finish within one unit of each other.  The owner's set
-// sits in dynamic shared memory (tab_slots 4-byte slots): a bitmap of its
-// rank window (BM) or a hash set, or, where that does not fit or the
-// schedule asks for it, the owner's sorted row is binary-searched instead.
-// (A kernel holds two of the three lookups: with all three inlined into the
-// streaming loop the 64-register budget spills.)
+// sits in dynamic shared memory (tab_slots 4-byte slots): a hash set, or
+// where it does not fit or the schedule asks for it a binary search of the
+// owner's sorted row (!BM); a bitmap of its rank window, or where that does
+// not fit the hash set (BM, mid owners: their set always fits) or the
+// binary search (BM, large owners).  A kernel holds two of the three
+// lookups: with all three inlined into the streaming loop the 64-register
+// budget spills.
 template <bool DYN, bool BM>
 __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8) k_probe_block(const uint32_t *__restrict__ ptrp,
                                                                       const uint32_t *__restrict__ col,
@@ -699,18 +701,18 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
         const PaddedRow row = padded_row(ptrp, x);
         const uint32_t d = row.d;
         const uint32_t hx = heavy[x];
-        // the owner's set: a binary search of the sorted row if the schedule
-        // asks this kernel for one; else (BM) a bitmap of the rank window if
-        // it fits the table's memory, or (!BM) a hash set if it fits; else
-        // the binary search
-        const bool bsearch = (cfg.lookup >> (DYN ? 1 : 0)) & 1u;
+        // the owner's set (BM kernels run only without the schedule's
+        // binary-search bit)
+        constexpr bool HASH = !BM || !DYN, SORTED = !BM || DYN;
+        const bool bsearch = !BM && ((cfg.lookup >> (DYN ? 1 : 0)) & 1u);
         uint32_t bits = 0;
-        if (BM && !bsearch) {
+        if (BM) {
             bits = __ldg(col + row.beg + d - 1) - x;  // up to the largest out-neighbour (d >= 2)
             if (bits > tab_slots * 32u || (uint64_t)x + 1 + bits > (uint64_t)SENT) bits = 0;
         }
         const bool bitmap = bits != 0;
-        const uint32_t slots = BM || bsearch ? 0u : table_slots(d, tab_slots);
+        const uint32_t slots = !HASH || bitmap || bsearch ? 0u : table_slots(d, tab_slots);
+        if (!SORTED && !bitmap && !slots && threadIdx.x == 0) atomicOr(&st->err, ERR_OVERFLOW);  // never: see above
         const BucketSet set{tab, slots ? (slots >> 1) - 1 : 0u, slots ? bucket_shift(slots) : 0u};
         uint32_t *bm = reinterpret_cast<uint32_t *>(tab);
         if ((slots || bitmap) && s_built != x) {
@@ -769,14 +771,15 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
             if (lane == 0) u = atomicAdd(&s_next, 1u);
             u = __shfl_sync(FULL, u, 0);
             if (u * UNIT >= total) break;
-            if (BM && bitmap)
+            if (BM && bitmap) {
                 stream_unit<DYN ? NWIN_DYN : NWIN_MID>(col4, BitmapSet{bm, x + 1, bits}, s_c0, s_pre, nlive, total,
                                                    u * UNIT, pc, t);
-            else if (!BM && slots)
+            } else if (HASH && slots) {
                 stream_unit<DYN ? NWIN_DYN : NWIN_MID>(col4, set, s_c0, s_pre, nlive, total, u * UNIT, pc, t);
-            else
+            } else if constexpr (SORTED) {
                 stream_unit<DYN ? NWIN_DYN : NWIN_MID>(col4, SortedRow{col + row.beg, d}, s_c0, s_pre, nlive, total,
                                                    u * UNIT, pc, t);
+            }
         }
         if (bv.k != 0) flush_graph_counts(t, bv, g);
         __syncthreads();  // every warp is done with this owner
@@ -825,12 +828,12 @@ void intersect(const CountBuffers &b, int dyn_smem_bytes, cudaStream_t s)
                                                 b.items, wm, b.heavy, b.st, b.bv, b.cfg, b.core_base);
     note_launch();
     const uint32_t seg_b = std::min(b.cfg.seg_b, SEG_B), seg_l = std::min(b.cfg.seg_l, SEG_L);
-    auto kmid = (b.cfg.lookup & 4u) ? k_probe_block<false, true> : k_probe_block<false, false>;
+    auto kmid = (b.cfg.lookup & 5u) == 4u ? k_probe_block<false, true> : k_probe_block<false, false>;
     kmid<<<152 * 8, PB_THREADS, MID_TAB * 4 + 2 * seg_b * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt, b.inptr,
                                                                  b.inend, b.inlist, b.items, wm, b.heavy, b.st, MID_TAB,
                                                                  b.items_cap, b.bv, b.cfg, b.core_base);
     note_launch();
-    auto klarge = (b.cfg.lookup & 8u) ? k_probe_block<true, true> : k_probe_block<true, false>;
+    auto klarge = (b.cfg.lookup & 10u) == 8u ? k_probe_block<true, true> : k_probe_block<true, false>;
     klarge<<<152, PB_DYN_THREADS, dyn_smem_bytes + 2 * seg_l * 4, s>>>(b.ptrp, b.col, b.rowptr, b.olist, b.ocnt,
                                                                       b.inptr, b.inend, b.inlist, b.items, wm, b.heavy,
                                                                       b.st, (uint32_t)(dyn_smem_bytes / 4),

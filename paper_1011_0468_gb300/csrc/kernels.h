@@ -195,11 +195,12 @@ void build_rows(const RowsArgs &a, cudaStream_t s);
 // (512 .. 1024); lookup: how the block kernels test membership in the
 // owner's list, bits 0 and 2 for the mid-owner blocks, bits 1 and 3 for the
 // large-owner blocks: bit 0 / 1 a binary search of the owner's sorted row;
-// else bit 2 / 3 a shared-memory bitmap of the owner's rank window, or the
-// binary search where the window does not fit the table's memory; else a
-// shared-memory hash set, or the binary search where it does not fit.  A
-// graph's default sets bit 3 when no large owner's window can exceed the
-// table (LOOKUP_BITMAP_LARGE, tc_graph_create).
+// else bit 2 / 3 a shared-memory bitmap of the owner's rank window, where
+// the window does not fit the table's memory the hash set (mid owners) or
+// the binary search (large owners); else a shared-memory hash set, or the
+// binary search where it does not fit.  A graph's default sets bit 3 when
+// no large owner's window can exceed the table (LOOKUP_BITMAP_LARGE,
+// tc_graph_create).
 constexpr uint32_t SEG_MIN = 64;
 constexpr uint32_t LOOKUP_DEFAULT = 0;
 constexpr uint32_t LOOKUP_BITMAP_LARGE = 8;
@@ -222,7 +223,9 @@ struct IsectConfig {
 inline const char *lookup_name(uint32_t lookup, int k)
 {
     const uint32_t m = lookup >> k;
-    return (m & 1u) ? "binary search" : ((m & 4u) ? "rank-window bitmap, else binary search" : "hash set");
+    return (m & 1u) ? "binary search"
+                    : ((m & 4u) ? (k ? "rank-window bitmap, else binary search" : "rank-window bitmap, else hash set")
+                                : "hash set");
 }
 inline uint32_t lookup_with(uint32_t lookup, int k, uint32_t v) { return (lookup & ~(5u << k)) | (v << k); }
 

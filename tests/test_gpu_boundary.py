@@ -225,15 +225,15 @@ def test_schedules_and_strategies_give_identical_counts():
             g.set_schedule(lookup=16)
 
 
-def test_bitmap_window_too_wide_falls_back_to_binary_search():
+def test_bitmap_window_too_wide_falls_back_to_the_hash_set():
     """Owners whose rank window (owner to largest out-neighbour) exceeds the
-    mid-owner table's 131072 bits binary-search their sorted row, the others
-    take the bitmap.  140,000 filler vertices on a circulant graph (i ~ i + 1
-    .. i + 21, degree 42 and up), 50 hubs joined to 20,000 fillers each, and
-    200 owners of degree 40 (38 fillers and 2 hubs): every owner's
-    neighbours rank above it, so with warp_max = 32 it is a mid owner whose
-    window reaches a hub about 140,000 ranks up.  Counts equal the oracle's
-    under the hash sets and under the bitmaps."""
+    mid-owner table's 131072 bits take the hash set, the others the bitmap.
+    140,000 filler vertices on a circulant graph (i ~ i + 1 .. i + 21, degree
+    42 and up), 50 hubs joined to 20,000 fillers each, and 200 owners of
+    degree 40 (38 fillers and 2 hubs): every owner's neighbours rank above
+    it, so with warp_max = 32 it is a mid owner whose window reaches a hub
+    about 140,000 ranks up.  Counts equal the oracle's under the hash sets
+    and under the bitmaps."""
     tc = _tc()
     rng = np.random.default_rng(21)
     nf, nh, no = 140000, 50, 200
