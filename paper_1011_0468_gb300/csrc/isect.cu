@@ -136,23 +136,52 @@ void build_items(const CountBuffers &b, cudaStream_t s)
 // Shared-memory hash set of an out-list: buckets of two slots (one 8-byte
 // load per lookup), filled in slot order, with linear probing over buckets.
 // At most an eighth of the slots are used where the table fits (a quarter
-// otherwise), so a lookup almost always ends at its first bucket: y is
-// absent as soon as a bucket without y has a free slot.  Both loops are
-// bounded by the table size.
+// otherwise), so a lookup almost always ends at its first bucket.  A full
+// bucket holds its two keys in increasing order, or in decreasing order once
+// some key has overflowed from it into the following buckets: a lookup that
+// misses in a full bucket goes on only then, and ends at the first bucket
+// with a free slot.  (A full bucket is common: about 9% of the buckets at a
+// quarter of the slots used; one that overflowed is rare.)  Every change to
+// a bucket is one 8-byte compare-and-swap; a bucket changes at most three
+// times (empty, one key, two keys in order, swapped), which bounds the retry
+// loops.  The probe loops are bounded by the table size.
 // ======================================================================
 
 __device__ __forceinline__ uint32_t bucket_hash(uint32_t y, uint32_t shift) { return (y * 0x9e3779b1u) >> shift; }
 
+__device__ __forceinline__ unsigned long long bucket_pack(uint32_t lo, uint32_t hi)
+{
+    return ((unsigned long long)hi << 32) | lo;
+}
+
 // nb = 2^k buckets: mask = nb - 1, shift = 32 - k.
 __device__ __forceinline__ void bucket_insert(uint2 *tab, uint32_t mask, uint32_t shift, uint32_t y)
 {
-    uint32_t b = bucket_hash(y, shift);
+    unsigned long long *t64 = reinterpret_cast<unsigned long long *>(tab);
+    const uint32_t home = bucket_hash(y, shift);
+    uint32_t b = home;
     for (uint32_t it = 0; it <= mask; ++it) {
-        uint32_t *slot = reinterpret_cast<uint32_t *>(tab + b);
-        uint32_t prev = atomicCAS(slot, EMPTY, y);
-        if (prev == EMPTY || prev == y) return;
-        prev = atomicCAS(slot + 1, EMPTY, y);
-        if (prev == EMPTY || prev == y) return;
+        unsigned long long cur = ~0ull;  // first guess: empty
+        for (int tries = 0; tries < 8; ++tries) {
+            const uint32_t k0 = (uint32_t)cur, k1 = (uint32_t)(cur >> 32);
+            if (k0 == y || k1 == y) return;
+            if (k1 != EMPTY) break;  // full: probe on
+            const unsigned long long want =
+                k0 == EMPTY ? bucket_pack(y, EMPTY) : (k0 < y ? bucket_pack(k0, y) : bucket_pack(y, k0));
+            const unsigned long long prev = atomicCAS(t64 + b, cur, want);
+            if (prev == cur) {
+                if (b != home) {  // overflowed: the (full) home bucket takes the decreasing order
+                    unsigned long long h = atomicOr(t64 + home, 0ull);
+                    for (int t2 = 0; t2 < 4 && (uint32_t)h < (uint32_t)(h >> 32); ++t2) {
+                        const unsigned long long p2 = atomicCAS(t64 + home, h, bucket_pack((uint32_t)(h >> 32), (uint32_t)h));
+                        if (p2 == h) break;
+                        h = p2;
+                    }
+                }
+                return;
+            }
+            cur = prev;
+        }
         b = (b + 1) & mask;
     }
 }
@@ -165,6 +194,9 @@ struct BucketSet {
         uint32_t b = bucket_hash(y, shift);
         uint2 v = tab[b];
         bool hit = v.x == y || v.y == y;
+        // a hit, a free slot (EMPTY is the largest value; an empty bucket has
+        // v.x == v.y) or a full bucket without overflow
+        if (hit || v.x <= v.y) return hit;
         for (uint32_t it = 0; !hit && v.y != EMPTY && it < mask; ++it) {
             b = (b + 1) & mask;
             v = tab[b];
@@ -296,14 +328,20 @@ template <class Set>
 __device__ __forceinline__ void probe4(const Set &set, const uint4 &q, bool hh, const PairCtx &pc, uint32_t &hl,
                                        uint32_t &hv)
 {
+    // the lookups are the same for every pair (no divergence between the
+    // lanes of heavy-heavy pairs and the others); only the hits of a
+    // heavy-heavy pair look at the third vertex's class
+    const uint32_t y[4] = {q.x, q.y, q.z, q.w};
+    uint32_t h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = set.contains(y[i]);
     if (!hh) {
-        hl += set.contains(q.x) + set.contains(q.y) + set.contains(q.z) + set.contains(q.w);
+        hl += h[0] + h[1] + h[2] + h[3];
         return;
     }
-    const uint32_t y[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        if (set.contains(y[i])) {
+        if (h[i]) {
             if (y[i] >= pc.lim || __ldg(pc.heavy + y[i])) ++hv; else ++hl;
         }
     }
