@@ -230,9 +230,23 @@ tc_status tc_graph_get_schedule(const tc_graph *g, tc_schedule *out);
    of each block kernel (hash set, bitmap, binary search), from the current
    schedule, keeping each improvement.  The choice stays with the
    graph; desc (may be NULL) receives it with the strategy of each owner
-   bucket.  Runs about 18 x 3 counts; results never depend on it.  TC_EINVAL
-   for a NULL graph or p outside (0, 1]; TC_ECUDA, TC_ETIMEOUT. */
+   bucket.  Runs about 18 x 3 counts; results never depend on it.  On a
+   graph with a dense core (tc_graph_create) it then measures the core's
+   cost model under the chosen schedule, with two counts each without the
+   core and with the allocated one: the probe kernels' rate in streamed list
+   entries per second, and the contraction's in flops per second (from the
+   time the core adds to the CSR and heavy phases).  Later counts choose
+   their core size from these rates instead of the built-in GB300 figures
+   (5e11 entries/s, 3.5e15 flop/s).  TC_EINVAL for a NULL graph or p outside
+   (0, 1]; TC_ECUDA, TC_ETIMEOUT. */
 tc_status tc_graph_autotune(tc_graph *g, double p, uint64_t seed, char *desc, uint32_t desc_len);
+
+/* The dense-core cost model of g: the rates it uses (any pointer may be
+   NULL) and the core size in ranks that a count at p chooses by default
+   (0: none; tc_graph_set_core_ranks overrides it).  TC_EINVAL for a NULL
+   graph or p outside (0, 1]. */
+tc_status tc_graph_get_core_model(const tc_graph *g, double p, double *probe_entries_per_s,
+                                  double *contraction_flops_per_s, uint32_t *core_ranks);
 
 /* After tc_graph_sync: copy the phase times (8 floats per count, layout of
    tc_result.ms) of the counts completed since the last drain, oldest first,
@@ -266,19 +280,23 @@ tc_status tc_count_async(tc_graph *g, double p, uint64_t seed, tc_result *out, v
 
 /*
  * Batched count over graphs already resident (Sections 3.1-3.2 for each
- * graph with its own p[i] and seed[i]): the k graphs are gathered into one
+ * graph with its own p[i] and seed[i]).  Graphs with a dense heavy block of
+ * their own (2^20 edges or more, see tc_graph_create) are counted on their
+ * own path, on their stream after its pending work, so that their heavy
+ * class runs on the tensor cores; the other graphs are gathered into one
  * disjoint union on the device (their stored keys, no input is read again)
- * and counted by one launch sequence; out[i] (host memory) receives exactly
- * what tc_count(graphs[i], p[i], seed[i]) returns, except that ms[] and the
- * work counters (src_elems, nbr_elems, partners, heavy_mma_flops) are zero.
- * The heavy class of every graph is counted by the intersection kernels.
+ * and counted by one launch sequence, their heavy class by the intersection
+ * kernels.  out[i] (host memory) receives exactly what tc_count(graphs[i],
+ * p[i], seed[i]) returns, except that ms[] is zero, and so are the work
+ * counters (src_elems, nbr_elems, partners, heavy_mma_flops) of the graphs
+ * counted in the union.
  *   graphs   k graph handles of the current device (a graph may appear more
  *            than once, e.g. with several p); k in 1 .. 65535, at most
- *            2^32 - 2 edges and fewer than 2^32 - 1 vertices in total.
- * The call allocates the union's scratch (about 40 bytes per edge) on a
- * stream of its own, blocks until the results are in out, and frees it.
- * It does not touch the graphs' scratch, so it may run while other counts
- * of the same graphs are pending.
+ *            2^32 - 2 edges and fewer than 2^32 - 1 vertices in total in
+ *            the union.
+ * The union's scratch (about 40 bytes per edge) is allocated on a stream of
+ * its own and freed before the call returns; it blocks until the results
+ * are in out.  The union does not touch the graphs' scratch.
  * Errors: TC_EINVAL (NULL pointers, a NULL graph, p[i] outside (0, 1], size
  * limits), TC_ENOMEM, TC_ECUDA, TC_ETIMEOUT.
  */

@@ -151,6 +151,9 @@ struct tc_graph {
     HeavyBuffers hb;            // dense heavy block (hb.hcap == 0: not used)
     CoreBuffers core;           // dense core of the top ranks (core.hb.hcap == 0: not used)
     double core_w[CORE_LEVELS_MAX] = {};  // p = 1 probe entries inside the top CORE_MIN << k ranks
+    // rates of the dense-core cost model: measured GB300 defaults until
+    // tc_graph_autotune measures them on this graph
+    double probe_rate = 0.0, tc_rate = 0.0;
     int64_t core_force = -1;    // dense core of every count: < 0 chosen per count, 0 none, else that many ranks
     DevState *st = nullptr;
     tc_result *res_dev = nullptr;
@@ -233,13 +236,29 @@ constexpr double CORE_PROBE_RATE = 5.0e11;    // streamed entries per second of 
 constexpr double CORE_TC_RATE = 3.5e15;       // executed fp8 flops per second of the contraction
 constexpr double CORE_CLEAR_RATE = 5.0e12;    // bytes per second of clearing U and U^T
 
-double core_cost_s(double K) { return (K * K * K / 3.0) / CORE_TC_RATE + 2.0 * K * K / CORE_CLEAR_RATE; }
+double core_cost_s(double K, double tc_rate) { return (K * K * K / 3.0) / tc_rate + 2.0 * K * K / CORE_CLEAR_RATE; }
 
 // Seconds the core of CORE_MIN << k ranks saves at sampling rate p (w_cum:
-// p = 1 probe entries inside each core size).
-double core_gain(const double *w_cum, int k, double p)
+// p = 1 probe entries inside each core size), at the given rates.
+double core_gain(const double *w_cum, int k, double p, double probe_rate, double tc_rate)
 {
-    return p * p * w_cum[k] / CORE_PROBE_RATE - core_cost_s((double)(CORE_MIN << k));
+    return p * p * w_cum[k] / probe_rate - core_cost_s((double)(CORE_MIN << k), tc_rate);
+}
+
+// The core size (ranks) a count of g at p uses by default: the one up to
+// the allocated size that gains most, or 0.
+uint32_t core_ranks_for(const tc_graph *g, double p)
+{
+    double best = 0.0;
+    uint32_t ranks = 0;
+    for (int k = 0; k < CORE_LEVELS && (CORE_MIN << k) <= g->core.hb.hcap; ++k) {
+        const double gain = core_gain(g->core_w, k, p, g->probe_rate, g->tc_rate);
+        if (gain > best) {
+            best = gain;
+            ranks = CORE_MIN << k;
+        }
+    }
+    return ranks;
 }
 
 CountBuffers buffers_of(tc_graph *g)
@@ -360,14 +379,10 @@ tc_status enqueue_count(tc_graph *g, double p, uint64_t seed, tc_result *dst, bo
         core_p.base = g->n - (uint32_t)g->core_force;
         core = &core_p;
     } else if (g->core_force < 0 && g->core.hb.hcap) {
-        double best = 0.0;
-        for (int k = 0; k < CORE_LEVELS && (CORE_MIN << k) <= g->core.hb.hcap; ++k) {
-            const double gain = core_gain(g->core_w, k, p);
-            if (gain > best) {
-                best = gain;
-                core_p.base = g->n - (CORE_MIN << k);
-                core = &core_p;
-            }
+        const uint32_t ranks = core_ranks_for(g, p);
+        if (ranks) {
+            core_p.base = g->n - ranks;
+            core = &core_p;
         }
     }
     if (core) ra.core_base = core->base;
@@ -416,6 +431,55 @@ tc_status sync_graph(tc_graph *g)
         return TC_ECUDA;
     }
     return status_of_err(g->st_host->err);
+}
+
+// The union count of tc_count_batch: k graphs (their keys at src[j] and
+// src[k + j]) into out[0 .. k) (pinned host memory); blocks until done.
+tc_status count_union_of(const std::vector<const uint64_t *> &src, const std::vector<uint64_t> &eoff,
+                         const std::vector<uint32_t> &voff, const std::vector<uint64_t> &thr,
+                         const std::vector<uint64_t> &mix, const std::vector<double> &p, uint32_t k, uint64_t m,
+                         uint32_t n_total, tc_result *out)
+{
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ECUDA;
+    }
+    UnionScratch u;
+    std::vector<void *> allocs;
+    uint64_t bytes = 0;
+    const uint64_t **d_src = nullptr;
+    DevState st_host;
+    tc_status st = TC_OK;
+    if (!union_scratch_alloc(u, m, n_total, k, allocs, bytes) ||
+        cudaMalloc((void **)&d_src, 2 * (size_t)k * sizeof(void *)) != cudaSuccess) {
+        cudaGetLastError();
+        st = TC_ENOMEM;
+    }
+    if (d_src) allocs.push_back((void *)d_src);
+    if (st == TC_OK) {
+        cudaMemcpyAsync(u.eoff, eoff.data(), (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(u.voff, voff.data(), (k + 1) * 4ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(u.thr, thr.data(), k * 8ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(u.seed_mix, mix.data(), k * 8ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(u.p, p.data(), k * 8ull, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_src, src.data(), 2 * (size_t)k * sizeof(void *), cudaMemcpyHostToDevice, s);
+        gather_graphs(d_src, d_src + k, u.eoff, u.voff, k, m, u.rel, u.orig, s);
+        union_count(u, m, n_total, k, IsectConfig{}, s);
+        cudaMemcpyAsync(out, u.res_dev, k * sizeof(tc_result), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&st_host, u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            st = TC_ECUDA;
+        } else {
+            st = status_of_err(st_host.err);
+        }
+    }
+    cudaStreamSynchronize(s);
+    for (void *q : allocs) cudaFree(q);
+    cudaStreamDestroy(s);
+    cudaGetLastError();
+    return st;
 }
 
 }  // namespace
@@ -479,6 +543,8 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
 
     tc_graph *g = new (std::nothrow) tc_graph;
     if (!g) return TC_ENOMEM;
+    g->probe_rate = CORE_PROBE_RATE;
+    g->tc_rate = CORE_TC_RATE;
     g->n = n;
     g->nbits = bits_for(n);
     g->stream = (cudaStream_t)cuda_stream;
@@ -700,7 +766,7 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
         for (int k = 0; k < levels; ++k) {
             acc += (double)w[k];
             g->core_w[k] = acc;
-            const double gain = core_gain(g->core_w, k, 1.0);
+            const double gain = core_gain(g->core_w, k, 1.0, g->probe_rate, g->tc_rate);
             if (gain > best) {
                 best = gain;
                 core_k = k;
@@ -838,12 +904,58 @@ tc_status tc_graph_autotune(tc_graph *g, double p, uint64_t seed, char *desc, ui
     cudaGetLastError();
     g->cfg = best;
     if (st != TC_OK) return st;
+    // the dense-core cost model measured on this graph under that schedule:
+    // the probe kernels' rate (streamed entries per second) from a count
+    // without the core, the contraction's (flops per second) from the time
+    // a count with the allocated core adds to the CSR and heavy phases
+    if (g->core.hb.hcap) {
+        const int timing0 = g->timing;
+        const int64_t force0 = g->core_force;
+        st = tc_graph_set_timing(g, 1);
+        float ms_none[8] = {}, ms_core[8] = {};
+        tc_result r_none{};
+        auto timed = [&](int64_t force, float *ms, tc_result *r) {
+            g->core_force = force;
+            for (int rep = 0; rep < 2 && st == TC_OK; ++rep) {  // a warm-up, then the measured count
+                st = enqueue_count(g, p, seed, g->res_host, true);
+                if (st == TC_OK) st = sync_graph(g);
+            }
+            if (st == TC_OK) {
+                ring_times(g, g->ring_head - 1, ms);
+                if (r) *r = *g->res_host;
+            }
+        };
+        const uint32_t K = (uint32_t)g->core.hb.hcap;
+        if (st == TC_OK) timed(0, ms_none, &r_none);
+        if (st == TC_OK) timed((int64_t)K, ms_core, nullptr);
+        g->core_force = force0;
+        g->timing = timing0;
+        if (st != TC_OK) return st;
+        if (ms_none[2] > 0.0f && r_none.nbr_elems > 0) {
+            g->probe_rate = (double)r_none.nbr_elems / (ms_none[2] * 1e-3);
+            const double Kd = (double)K;
+            const double extra = (ms_core[1] - ms_none[1] + ms_core[3] - ms_none[3]) * 1e-3 - 2.0 * Kd * Kd / CORE_CLEAR_RATE;
+            if (extra > 0.0) g->tc_rate = (Kd * Kd * Kd / 3.0) / extra;
+        }
+    }
     if (desc && desc_len)
         snprintf(desc, desc_len,
                  "warp_max=%u mid_max=%u seg_w=%u seg_b=%u seg_l=%u lookup=%u: warp per owner (d+<=%u, hash sets), "
-                 "128-thread block per owner (d+<=%u, %s), 1024-thread block per owner (%s); count_ms=%.3f",
+                 "128-thread block per owner (d+<=%u, %s), 1024-thread block per owner (%s); count_ms=%.3f; "
+                 "core model: probe %.3g entries/s, contraction %.3g flop/s, core at p=%g: %u ranks",
                  best.warp_max, best.mid_max, best.seg_w, best.seg_b, best.seg_l, best.lookup, best.warp_max,
-                 best.mid_max, lookup_name(best.lookup, 0), lookup_name(best.lookup, 1), best_ms);
+                 best.mid_max, lookup_name(best.lookup, 0), lookup_name(best.lookup, 1), best_ms, g->probe_rate,
+                 g->tc_rate, p, core_ranks_for(g, p));
+    return TC_OK;
+}
+
+tc_status tc_graph_get_core_model(const tc_graph *g, double p, double *probe_entries_per_s,
+                                  double *contraction_flops_per_s, uint32_t *core_ranks)
+{
+    if (!g || bad_p(p)) return TC_EINVAL;
+    if (probe_entries_per_s) *probe_entries_per_s = g->probe_rate;
+    if (contraction_flops_per_s) *contraction_flops_per_s = g->tc_rate;
+    if (core_ranks) *core_ranks = core_ranks_for(g, p);
     return TC_OK;
 }
 
@@ -980,64 +1092,56 @@ tc_status tc_count_async(tc_graph *g, double p, uint64_t seed, tc_result *out, v
 tc_status tc_count_batch(tc_graph *const *graphs, const double *p, const uint64_t *seed, uint32_t k, tc_result *out)
 {
     if (!graphs || !p || !seed || !out || k == 0 || k > 0xffffu) return TC_EINVAL;
-    std::vector<uint64_t> eoff(k + 1, 0), thr(k), mix(k);
-    std::vector<uint32_t> voff(k + 1, 0);
-    std::vector<const uint64_t *> src(2 * (size_t)k);
-    uint64_t n_total = 0;
+    // graphs with a dense heavy block of their own count on their own path
+    // (the block on the tensor cores); the others go into one union
+    std::vector<uint32_t> own, uni;
     for (uint32_t i = 0; i < k; ++i) {
+        if (!graphs[i] || bad_p(p[i])) return TC_EINVAL;
+        (graphs[i]->hb.hcap ? own : uni).push_back(i);
+    }
+    const uint32_t ku = (uint32_t)uni.size();
+    std::vector<uint64_t> eoff(ku + 1, 0), thr(ku), mix(ku);
+    std::vector<uint32_t> voff(ku + 1, 0);
+    std::vector<const uint64_t *> src(2 * (size_t)ku);
+    std::vector<double> pu(ku);
+    uint64_t n_total = 0;
+    for (uint32_t j = 0; j < ku; ++j) {
+        const uint32_t i = uni[j];
         const tc_graph *g = graphs[i];
-        if (!g || bad_p(p[i])) return TC_EINVAL;
-        eoff[i + 1] = eoff[i] + g->m;
+        eoff[j + 1] = eoff[j] + g->m;
         n_total += g->n;
         if (n_total >= 0xffffffffull) return TC_EINVAL;
-        voff[i + 1] = (uint32_t)n_total;
-        thr[i] = threshold_of(p[i]);
-        mix[i] = splitmix64(seed[i]);
-        src[i] = g->rel;
-        src[k + i] = g->orig;
+        voff[j + 1] = (uint32_t)n_total;
+        thr[j] = threshold_of(p[i]);
+        mix[j] = splitmix64(seed[i]);
+        pu[j] = p[i];
+        src[j] = g->rel;
+        src[ku + j] = g->orig;
     }
-    const uint64_t m = eoff[k];
+    const uint64_t m = eoff[ku];
     if (m > 0xfffffffeull) return TC_EINVAL;
     NvtxRange whole("tc_count_batch");
-    cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    tc_result *stage = nullptr;  // pinned: the own-path results, then the union's
+    if (cudaMallocHost((void **)&stage, (size_t)k * sizeof(tc_result)) != cudaSuccess) {
         cudaGetLastError();
-        return TC_ECUDA;
+        return TC_ENOMEM;
     }
-    UnionScratch u;
-    std::vector<void *> allocs;
-    uint64_t bytes = 0;
-    const uint64_t **d_src = nullptr;
-    DevState st_host;
     tc_status st = TC_OK;
-    if (!union_scratch_alloc(u, m, (uint32_t)n_total, k, allocs, bytes) ||
-        cudaMalloc((void **)&d_src, 2 * (size_t)k * sizeof(void *)) != cudaSuccess) {
-        cudaGetLastError();
-        st = TC_ENOMEM;
+    for (uint32_t j = 0; j < own.size() && st == TC_OK; ++j)
+        st = enqueue_count(graphs[own[j]], p[own[j]], seed[own[j]], stage + j, false);
+    if (st == TC_OK && ku) st = count_union_of(src, eoff, voff, thr, mix, pu, ku, m, (uint32_t)n_total, stage + own.size());
+    for (uint32_t j = 0; j < own.size(); ++j) {
+        const tc_status s2 = sync_graph(graphs[own[j]]);
+        if (st == TC_OK) st = s2;
     }
-    if (d_src) allocs.push_back((void *)d_src);
     if (st == TC_OK) {
-        cudaMemcpyAsync(u.eoff, eoff.data(), (k + 1) * 8ull, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(u.voff, voff.data(), (k + 1) * 4ull, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(u.thr, thr.data(), k * 8ull, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(u.seed_mix, mix.data(), k * 8ull, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(u.p, p, k * 8ull, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(d_src, src.data(), 2 * (size_t)k * sizeof(void *), cudaMemcpyHostToDevice, s);
-        gather_graphs(d_src, d_src + k, u.eoff, u.voff, k, m, u.rel, u.orig, s);
-        union_count(u, m, (uint32_t)n_total, k, IsectConfig{}, s);
-        cudaMemcpyAsync(out, u.res_dev, k * sizeof(tc_result), cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&st_host, u.st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
-        if (cudaStreamSynchronize(s) != cudaSuccess) {
-            cudaGetLastError();
-            st = TC_ECUDA;
-        } else {
-            st = status_of_err(st_host.err);
+        for (uint32_t j = 0; j < own.size(); ++j) {
+            out[own[j]] = stage[j];
+            for (float &t : out[own[j]].ms) t = 0.0f;
         }
+        for (uint32_t j = 0; j < ku; ++j) out[uni[j]] = stage[own.size() + j];
     }
-    cudaStreamSynchronize(s);
-    for (void *q : allocs) cudaFree(q);
-    cudaStreamDestroy(s);
-    cudaGetLastError();
+    cudaFreeHost(stage);
     return st;
 }
 

@@ -104,6 +104,8 @@ SIGNATURES = [
     ("tc_graph_set_schedule", ctypes.c_int, [_vp, ctypes.POINTER(tc_schedule)]),
     ("tc_graph_get_schedule", ctypes.c_int, [_vp, ctypes.POINTER(tc_schedule)]),
     ("tc_graph_autotune", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.c_char_p, ctypes.c_uint32]),
+    ("tc_graph_get_core_model", ctypes.c_int, [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint32)]),
     ("tc_graph_timing_drain", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_uint32]),
     ("tc_count", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(tc_result)]),
     ("tc_count_async", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_uint64, _vp, _vp]),
@@ -409,6 +411,14 @@ class Graph:
         desc = ctypes.create_string_buffer(512)
         _check(lib().tc_graph_autotune(self.handle, p, seed & 0xFFFFFFFFFFFFFFFF, desc, 512), "tc_graph_autotune")
         return desc.value.decode()
+
+    def core_model(self, p: float) -> dict:
+        """tc_graph_get_core_model: the rates of the dense-core cost model and
+        the core size a count at p uses by default (0: none)."""
+        pr, tr, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint32()
+        _check(lib().tc_graph_get_core_model(self.handle, p, ctypes.byref(pr), ctypes.byref(tr), ctypes.byref(k)),
+               "tc_graph_get_core_model")
+        return {"probe_entries_per_s": pr.value, "contraction_flops_per_s": tr.value, "core_ranks": k.value}
 
     def set_core_ranks(self, ranks: int):
         """Dense core of the later counts (tc_graph_set_core_ranks): < 0 chosen

@@ -66,6 +66,12 @@ def test_count_batch_over_resident_graphs():
             single = objs[i].count(p[j], seed[j])
             for k in KEYS:
                 assert res[k][j] == single[k], (j, i, k)
+            # the graph with a heavy block of its own counts on its own path
+            # (its work counters filled in; at p = 1 its heavy class runs on
+            # the tensor cores); the union reports no work
+            assert (res["partners"][j] > 0) == (i == 4), (j, i)
+            if i == 4 and p[j] == 1.0:
+                assert res["heavy_mma_flops"][j] > 0
             if i != 4:  # the planted core's oracle run takes a while; its single count is exact already
                 want = oracle.run(graphs[i][0], graphs[i][1], p[j], seed[j])
                 for k in KEYS:

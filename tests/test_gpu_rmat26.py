@@ -91,3 +91,23 @@ def test_exact_count_properties_at_p1(rmat):
     again = g.count(1.0, 2)  # the seed does not matter at p = 1
     assert (again["m_sampled"], again["t_light"], again["t_heavy"]) == (got["m_sampled"], got["t_light"],
                                                                         got["t_heavy"])
+
+
+def test_autotune_measures_the_core_cost_model(rmat):
+    """tc_graph_autotune replaces the built-in rates of the dense-core cost
+    model by rates measured on this graph; the counts (and the stored oracle
+    counts) stay the same under the tuned schedule and the core size the
+    measured model picks."""
+    rec, g = rmat
+    before = g.core_model(1.0)
+    assert before["core_ranks"] in (0, 8192, 16384, 32768, 65536)
+    desc = g.autotune(0.05, 1)
+    assert "core model" in desc
+    after = g.core_model(1.0)
+    assert 1e10 < after["probe_entries_per_s"] < 1e13 and 1e14 < after["contraction_flops_per_s"] < 1e16
+    assert after != before
+    for r in rec["runs"]:
+        got = g.count(r["p"], r["seed"])
+        for k in ("m_sampled", "n_heavy", "t_light", "t_heavy"):
+            assert got[k] == r[k], (r["p"], r["seed"], k, got[k], r[k])
+    g.set_schedule()
