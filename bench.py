@@ -86,6 +86,9 @@ def parse_args():
                     help="seconds of Poisson arrivals of the served comparison inside the default run")
     ap.add_argument("--rmat-scale", type=int, default=None,
                     help="rmat26: another R-MAT scale (e.g. a smaller case for profiling)")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="batch: only the batched counts (no autotune, no one-count-per-graph comparison), "
+                         "e.g. for a launch list")
     return ap.parse_args()
 
 
@@ -450,10 +453,11 @@ def make_batch_graphs(count: int, seed: int = 1):
     return specs, graphs
 
 
-def run_batch(w, steps: int, warmup: int, plain_steps: int = 3) -> dict:
+def run_batch(w, steps: int, warmup: int, plain_steps: int = 3, compare: bool = True) -> dict:
     """Batched counting (tc_batch_*) against the plain one-count-per-graph
     path on the same GPU, same graphs, same (p, seed): the result line (a
-    dict) of workload w (WORKLOADS["batch"])."""
+    dict) of workload w (WORKLOADS["batch"]).  compare=False: the batched
+    counts alone, under the default schedule."""
     import numpy as np
     import torch
     from paper_1011_0468_gb300 import tc
@@ -465,7 +469,7 @@ def run_batch(w, steps: int, warmup: int, plain_steps: int = 3) -> dict:
     seeds = np.array([s["seed"] for s in specs], dtype=np.uint64)
     batch = tc.Batch([(g, s["n"]) for g, s in zip(graphs, specs)])
     m_total = batch.m
-    schedule = batch.autotune(p, seeds)
+    schedule = batch.autotune(p, seeds) if compare else "default"
     for i in range(warmup):
         batch.count(p, seeds + np.uint64(i))
     l0 = tc.tc_launch_count()
@@ -477,6 +481,12 @@ def run_batch(w, steps: int, warmup: int, plain_steps: int = 3) -> dict:
         t_batch = time.perf_counter() - t0
     launches = tc.tc_launch_count() - l0
     batch.close()
+    if not compare:
+        return {"metric": "batched graphs/s", "value": steps * k / t_batch, "unit": "graphs/s", "n_gpus": 1,
+                "steps": steps, "warmup": warmup, "ms_per_step": 1000 * t_batch / steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": w["workload"], "graphs": k, "m_total": int(m_total), "schedule": schedule},
+                "gpu_launches": int(launches), "clocks": clocks.summary()}
 
     # plain path: the same graphs resident one per object, one count per call
     tc.use_torch_allocator(True)
@@ -524,7 +534,7 @@ def run_batch(w, steps: int, warmup: int, plain_steps: int = 3) -> dict:
 def batch_arm(args):
     import torch
     torch.cuda.set_device(0)
-    print(json.dumps(run_batch(WORKLOAD, args.steps, args.warmup)), flush=True)
+    print(json.dumps(run_batch(WORKLOAD, args.steps, args.warmup, compare=not args.no_plain)), flush=True)
 
 
 def serve_requests(w, n_small, duration, seed=7):
