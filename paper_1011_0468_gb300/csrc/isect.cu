@@ -10,8 +10,9 @@
 // DevState::light_lim are heavy, the rest are looked up).
 //
 // A pair (a -> b) is resolved by the endpoint with the LONGER out-list, the
-// "owner": its list is put into a shared-memory hash set and the shorter
-// list is streamed through it:
+// "owner": its list is put into a shared-memory set (a hash set, or for the
+// block kernels a bitmap of its rank window) and the shorter list is
+// streamed through it:
 //   owner x, partner v in N+(x) with d+(v) <= d+(x): stream N+(v)
 //   owner x, partner u in in-list(x), d+(u) < d+(x): stream the part of
 //     N+(u) ranked above x (rows are sorted by rank and the in-list entry
@@ -21,13 +22,15 @@
 // out-list of x holds its out-partners, the in-list its in-partners.
 //
 // Work items are (segment << 32 | owner); a segment is a run of the owner's
-// partner sequence (its out-list, then its in-list).  Owners
-// are bucketed by d+(x), which sizes their hash set: 2..256 (one warp per
-// item), 257..1024 (one 128-thread block, 4096-slot table, eight blocks per
-// SM so that one block's item setup overlaps the others' streaming), > 1024
-// (one block, larger table, or a binary search of the sorted row when even
-// that is too small).  Owners with d+ < 2 close no triangle.  Rows are stored padded to
-// 16 bytes (kernels.h), so the partners' lists stream as uint4 chunks.
+// partner sequence (its out-list, then its in-list).  Owners are bucketed
+// by d+(x), which sizes their set: 2..256 (one warp per item), 257..1024
+// (one 128-thread block, 4096-slot table, eight blocks per SM so that one
+// block's item setup overlaps the others' streaming), > 1024 (one
+// 1024-thread block, larger table, or a binary search of the sorted row
+// when even that is too small); the cutoffs and the set of each block
+// kernel follow the schedule (IsectConfig).  Owners with d+ < 2 close no
+// triangle.  Rows are stored padded to 16 bytes (kernels.h), so the
+// partners' lists stream as uint4 chunks.
 #include <algorithm>
 
 #include "kernels.h"
