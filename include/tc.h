@@ -518,8 +518,8 @@ void tc_server_destroy(tc_server *srv);
  * All scratch lives in one fixed __device__ array inside the library
  * (about 24 MiB), held by every GPU that loads it until the process exits.
  * The first call on a device looks up that array's device address (kept for
- * the process; a device reset between calls is not supported); make this
- * first call before any stream capture.  Calls share the array (each
+ * the process; a device reset between calls is not supported).  Calls
+ * share the array (each
  * clears what must start at zero), so calls that overlap on the GPU race:
  * serialise them.  Nothing is allocated: no cudaMalloc, no cudaFree, no
  * allocator callback.
