@@ -190,6 +190,15 @@ def test_sweep_adaptive_and_auto_counts():
                         len(ladder) - 1)
             assert runs == len(ladder) and p_used == ladder[pick]
             assert got["estimate"] == ests[pick]
+        # equal to the single counts, also on a graph with a heavy block
+        one = [g.count(p, s) for p, s in zip(ps, [3, 4, 5, 6, 7])]
+        assert all(res[k][j] == one[j][k] for j in range(len(ps)) for k in KEYS)
+        big = gen.planted_core(60000, 1400, 0.85, 250000, 5)
+        with tc.Graph(big, 60000) as g2:
+            res2 = g2.count_sweep([0.3, 1.0], [1, 2])
+            for j, (p, s) in enumerate(((0.3, 1), (1.0, 2))):
+                single = g2.count(p, s)
+                assert all(res2[k][j] == single[k] for k in KEYS), (p, s)
         got, p_used = g.count_auto(0.1, 0.05, 12)
         pilot = oracle.run(e, n, 0.05, 12)
         assert p_used == oracle.suggest_p(len(e), n, pilot["estimate"], 0.1)
