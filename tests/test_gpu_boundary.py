@@ -76,6 +76,11 @@ def test_count_batch_over_resident_graphs():
                 want = oracle.run(graphs[i][0], graphs[i][1], p[j], seed[j])
                 for k in KEYS:
                     assert res[k][j] == want[k], (j, i, k)
+        # only graphs with a heavy block of their own: no union at all
+        res = tc.tc_count_batch([objs[4], objs[4]], [1.0, 0.45], [11, 12])
+        for j, (p1, s1) in enumerate(((1.0, 11), (0.45, 12))):
+            single = objs[4].count(p1, s1)
+            assert all(res[k][j] == single[k] for k in KEYS), j
         with pytest.raises(tc.TCError) as ei:
             tc.tc_count_batch([objs[0]], [1.5], [1])
         assert ei.value.status == tc.TC_EINVAL
