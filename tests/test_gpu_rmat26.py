@@ -111,3 +111,22 @@ def test_autotune_measures_the_core_cost_model(rmat):
         for k in ("m_sampled", "n_heavy", "t_light", "t_heavy"):
             assert got[k] == r[k], (r["p"], r["seed"], k, got[k], r[k])
     g.set_schedule()
+
+
+def test_stored_counts_under_every_membership_test(rmat):
+    """The stored oracle counts at full size with hash sets for every block
+    owner (lookup 0), with bitmaps for both block kernels (12) and with
+    binary searches (3, on the samples up to p = 0.25: a search per lookup
+    is slow at p = 1): the default takes bitmaps for the large owners only."""
+    rec, g = rmat
+    try:
+        for lookup in (0, 12, 3):
+            g.set_schedule(lookup=lookup)
+            for r in rec["runs"]:
+                if lookup == 3 and r["p"] > 0.25:
+                    continue
+                got = g.count(r["p"], r["seed"])
+                for k in ("m_sampled", "n_heavy", "t_light", "t_heavy"):
+                    assert got[k] == r[k], (lookup, r["p"], r["seed"], k, got[k], r[k])
+    finally:
+        g.set_schedule()
