@@ -58,6 +58,23 @@ def test_stored_oracle_results(workload, graph):
         assert got["estimate"] == float.fromhex(r["estimate_hex"])
 
 
+def test_stored_results_under_every_membership_test(workload, graph):
+    """The stored oracle results with hash sets, rank-window bitmaps and
+    binary searches for the block owners, and with every owner in a warp
+    or in the 1024-thread blocks (warp_max 32, mid_max 512)."""
+    rec, _ = workload
+    try:
+        for sched in (dict(lookup=0), dict(lookup=12), dict(lookup=3), dict(warp_max=32, mid_max=512, lookup=12)):
+            graph.set_schedule()
+            graph.set_schedule(**sched)
+            for r in rec["runs"]:
+                got = graph.count(r["p"], r["seed"])
+                for k in ("m_sampled", "n_heavy", "t_light", "t_heavy"):
+                    assert got[k] == r[k], (sched, r["p"], r["seed"], k, got[k], r[k])
+    finally:
+        graph.set_schedule()
+
+
 def test_oracle_rerun_at_small_p(workload, graph):
     rec, edges = workload
     n = rec["spec"]["n"]
