@@ -395,6 +395,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_heavy_tc(const __grid_constan
     const uint32_t hp = (h + TC_TILE - 1) / TC_TILE * TC_TILE;
     const int R = (int)(hp / TC_TILE), C = (R + 1) / 2;
     const TileGrid grid{R, C, (R + TC_GI - 1) / TC_GI, (C + TC_GP - 1) / TC_GP};
+    if (grid.Rg * grid.Cg > TC_MAX_GROUPS) {  // an order above 65536 (the library never asks for one)
+        if (threadIdx.x == 0) atomicOr(&st->err, ERR_OVERFLOW);
+        return;
+    }
     const unsigned warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
