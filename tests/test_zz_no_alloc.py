@@ -2,12 +2,14 @@
 memory (a framework pool already owns the GPU, or a device allocation would
 synchronise it), must give the same results as the regular entry points
 (tc_graph_create + tc_count) on consecutive calls, which share one fixed
-scratch array inside the library.  Collected last on purpose.
+scratch array inside the library, and the oracle's.  Collected last on
+purpose.
 """
 import numpy as np
 import pytest
 
 import gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +44,7 @@ def test_no_alloc_matches_regular_entry_points_on_consecutive_calls():
         with tc.Graph(edges.astype(np.uint32), n) as g:
             want = g.count(p, seed)
         _same(got, want)
+        _same(got, oracle.run(oracle.canonicalize(edges.astype(np.uint32), n), n, p, seed))
         assert got["t_light"] + got["t_heavy"] > 0
 
 
