@@ -62,8 +62,9 @@ typedef struct tc_graph tc_graph;
    block, [4] total.  The work counters give the exact amount of list data
    the intersections read, for bandwidth accounting: every oriented pair
    (a -> b) is resolved by loading the longer of N+(a), N+(b) into an
-   on-chip hash set (src_elems counts those loads) and streaming the
-   shorter one through it (nbr_elems); partners counts the pairs. */
+   on-chip set, a hash set or a bitmap of its rank window (src_elems counts
+   those loads), and streaming the shorter one through it (nbr_elems);
+   partners counts the pairs. */
 typedef struct {
     uint64_t m;         /* canonical edges of the graph */
     uint64_t m_sampled; /* kept edges m_p */
@@ -72,7 +73,7 @@ typedef struct {
     uint64_t t_light;   /* sampled triangles with >= 1 light vertex */
     uint64_t t_heavy;   /* sampled triangles with 3 heavy vertices */
     double estimate;    /* t_light / p^3 + t_heavy / p^3 */
-    uint64_t src_elems; /* list elements loaded into hash sets */
+    uint64_t src_elems; /* list elements loaded into the on-chip sets */
     uint64_t nbr_elems; /* list elements streamed through them */
     uint64_t partners;  /* oriented pairs resolved */
     uint64_t heavy_mma_flops; /* executed tensor-core flops of the dense heavy block and,

@@ -701,10 +701,10 @@ tc_status tc_graph_create(const uint32_t *edges, uint64_t m_in, uint32_t n, int 
     }
     // static rows (g->deg still holds the full degrees by original id)
     static_rows(g->rel, m, n, g->perm, g->deg, g->frow, g->inptr, g->scan, s);
-    // hash set of the owners with d+ > 1024: every out-degree of the
-    // degree-oriented graph is at most sqrt(2 m_p); a set of >= 4 d+ slots
-    // up to 32768 slots (128 KiB) stays on chip, larger rows are searched in
-    // place
+    // table of the owners with d+ > 1024 (their hash set or rank-window
+    // bitmap): every out-degree of the degree-oriented graph is at most
+    // sqrt(2 m_p); a set of >= 4 d+ slots up to 32768 slots (128 KiB) stays
+    // on chip, larger rows are searched in place
     const uint64_t dmax = (uint64_t)std::sqrt(2.0 * (double)std::max<uint64_t>(m, 1)) + 2;
     uint64_t slots = 8192;
     while (slots < 4 * dmax && slots < 32768) slots <<= 1;

@@ -699,8 +699,8 @@ __global__ void __launch_bounds__(DYN ? PB_DYN_THREADS : PB_THREADS, DYN ? 1 : 8
     constexpr uint32_t NT = DYN ? PB_DYN_THREADS : PB_THREADS;
     constexpr uint32_t SEG = DYN ? SEG_L : SEG_B;        // partners per item (at most)
     constexpr uint32_t PER_MAX = (SEG + NT - 1) / NT;    // partner slots set up per thread (at most)
-    // dynamic shared memory: the hash set (tab_slots slots), then the live
-    // partners of the current item (seg_cap of each array)
+    // dynamic shared memory: the owner's set (tab_slots 4-byte slots), then
+    // the live partners of the current item (seg_cap of each array)
     extern __shared__ uint2 tab[];
     const uint32_t seg_cap = DYN ? min(cfg.seg_l, SEG_L) : min(cfg.seg_b, SEG_B);
     uint32_t *s_c0 = reinterpret_cast<uint32_t *>(tab) + tab_slots;
